@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark: reweighted events/s for leading-order event reweighting.
+
+One step = one pass of the whole hot path over one batch: for every event
+|M|^2 under the original parameters, the mass-shell move and |M'|^2 for each
+parameter point, r = |M'|^2/|M|^2, W' = r W and the cross sections
+sigma'_p = sum W'_p and sigma = sum W (arXiv:2312.07440, Sec. 3.2 steps 3-8,
+Eqs. 2-3).  Default workload: g g -> t tbar, 1,048,576 events, sqrt(s-hat)
+uniform in [400, 2000] GeV, massive RAMBO momenta (m_t = 173 GeV),
+lognormal weights, one point (m_t 175 GeV, alpha_s 0.120), FP64 amplitudes.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|fp32]
+  python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+
+Rank 0 prints one JSON line.  `value` is device-resident throughput
+(events x points / s, inputs already in HBM, L2 flushed between steps);
+`e2e` is the same metric through rw_reweight_host (pinned host buffers,
+host<->device copies inside the timed region).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2312_07440_gb300 import events as ev  # noqa: E402
+
+L2_BYTES = 129 * 2 ** 20
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# Plain-ALU peaks (no tensor cores on this path): FP32 = 152 SMs x 128 lanes
+# x 2 flop (FMA) x 2.07 GHz; FP64 = the GB300 nominal FP64 rate.
+ALU_PEAK_TFLOPS = {"fp32": SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12, "fp64": 1.25}
+METRIC = "reweighted events/s at stated rel err (plain FP64 vs mixed-precision/surrogate)"
+UNIT = "events*points/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gg_tt_1m", choices=list(ev.WORKLOADS))
+    ap.add_argument("--variant", default="default", help="point set variant (gg_ttg/gg_ttgg: default|mt)")
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--lane-bits", type=int, default=-1)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def source_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2312_07440_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, mode):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken
+    on the current kernel sources (profiles/*.md 'traffic:' lines)."""
+    sha = source_sha()
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    pat = re.compile(r"traffic:\s*workload=(\S+)\s+mode=(\S+)\s+sources=(\S+)\s+dram_bytes_per_launch=(\S+)")
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        for line in open(os.path.join(pdir, fn)):
+            m = pat.search(line)
+            if m and m.group(1) == workload and m.group(2) == mode and m.group(3) == sha:
+                return float(m.group(4))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, enabled=True):
+        self.p = None
+        self.gpu = gpu_index
+        if not enabled:
+            return
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_throughput(wl, pts, budget_s, chunk=65536, start_event=0):
+    """The oracle as it stands on the host cores, over whole chunks of the
+    workload until the time budget is spent.  Returns (events*points/s, n_events, cores)."""
+    import oracle
+    cores = oracle.set_threads(0)
+    P = pts.shape[0]
+    done, t_used = 0, 0.0
+    while done < wl.n_events and t_used < budget_s:
+        n = min(chunk, wl.n_events - done)
+        mom, w = ev.generate(wl, n, start=start_event + done)
+        t0 = time.perf_counter()
+        oracle.reweight(wl.process, ev.param_vector(), pts, mom, w)
+        t_used += time.perf_counter() - t0
+        done += n
+    return done * P / t_used, done, cores
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    wl = ev.WORKLOADS[args.workload]
+    pts = ev.reweight_points(args.workload, args.variant)
+    P = pts.shape[0]
+    cores = oracle.set_threads(0)
+    sample = 65536
+    mom, w = ev.generate(wl, sample)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.reweight(wl.process, ev.param_vector(), pts, mom, w)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = sample * P / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, wl, P),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample} events of {wl.name} per step, {P} point(s), "
+                                   f"CPU {cpu_model()}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, wl, P):
+    return {"workload": wl.name, "process": wl.process, "events": wl.n_events, "points": P,
+            "point_set": args.variant, "sqrt_s_range_gev": list(wl.sqrt_s), "mode": args.mode,
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"events sharded x{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2312_07440_gb300 import rwgt
+
+    rank, world, local = dist_info()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = ev.WORKLOADS[args.workload]
+    pts = ev.reweight_points(args.workload, args.variant)
+    P = pts.shape[0]
+    E = wl.n_events
+    N = ev.N_EXTERNAL[wl.process]
+    # weak scaling: rank r reweights its own batch, events [r E, (r+1) E)
+    mom_h, w_h = ev.generate(wl, E, start=rank * E)
+    mom = torch.from_numpy(mom_h).to(dev)
+    w = torch.from_numpy(w_h).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = rwgt.Context(local, stream.cuda_stream)
+    ctx.set_process(wl.process, args.mode)
+    ctx.set_params(ev.param_vector())
+    ctx.set_reweight_points(pts)
+    ctx.set_tuning(args.lane_bits, args.block)
+    nb = ctx.workspace_bytes(E)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    ctx.load_events(mom, w, E, ws, nb)
+    wnew = torch.empty((P, E), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        ctx.reweight_async(wnew, None, None, None)
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local, enabled=(rank == 0 and not args.no_clocks))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    per_step = [s.elapsed_time(e) * 1e-3 for s, e in zip(starts, ends)]
+    t_total = sum(per_step)
+    sig, sig_orig, nbad, _ = ctx.get_results(P)
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+        # the one exchange of the method: sum of the per-shard cross sections
+        ss = torch.tensor(list(sig) + [sig_orig], dtype=torch.float64, device=dev)
+        dist.all_reduce(ss)
+        sig, sig_orig = ss[:P].cpu().numpy(), float(ss[P])
+    t_step = t_total / args.steps
+    value = world * E * P / t_step
+
+    # accuracy of this run against the oracle on a sample of its events
+    acc = None
+    if rank == 0:
+        acc = accuracy_sample(wl, pts, mom_h, w_h, wnew, args.mode)
+
+    # end to end through the host entry point (rank 0 of each node does it on its own GPU)
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(ctx, torch, dev, mom_h, w_h, E, P, N, world, args)
+
+    info = rwgt.process_info(wl.process)
+    flops_event = (1 + P) * info.flops_hel_sum
+    achieved = E * flops_event / t_step / 1e12
+    peak = ALU_PEAK_TFLOPS[args.mode]
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": profiled_traffic(wl.name, args.mode),
+            "kernel": "k_reweight (fused: amplitudes, colour sum, helicity sum, ratio, W', sigma)",
+            "flops_per_event": flops_event,
+            "peak_source": ("FP64: GB300 nominal 1.25 TFLOP/s" if args.mode == "fp64" else
+                            "FP32: 152 SM x 128 lanes x 2 x 2.07 GHz (derived)")}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, cores = oracle_throughput(wl, pts, args.cpu_seconds, start_event=0)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {n} events of {wl.name} (chunks of 65536), {P} point(s), CPU {cpu_model()}"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "f32", "data": "synthetic",
+            "config": config_dict(args, wl, P),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clocks, "accuracy_vs_oracle": acc,
+            "sigma": [float(x) for x in sig], "sigma_orig": sig_orig, "n_bad": int(nbad),
+            "step_ms_min_median_max": [1e3 * min(per_step), 1e3 * statistics.median(per_step),
+                                       1e3 * max(per_step)],
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def accuracy_sample(wl, pts, mom_h, w_h, wnew, mode, n=2000):
+    import oracle
+    rng = np.random.default_rng(1)
+    idx = np.unique(rng.integers(0, wl.n_events, n))
+    o = oracle.reweight(wl.process, ev.param_vector(), pts, np.ascontiguousarray(mom_h[:, :, idx]), w_h[idx])
+    g = wnew[:, idx].cpu().numpy()
+    r = np.abs(g - o["wnew"]) / np.maximum(np.abs(o["wnew"]), 1e-300)
+    return {"quantity": "W' per event, relative", "events": int(len(idx)), "max": float(r.max()),
+            "median": float(np.median(r)), "p999": float(np.quantile(r, 0.999)),
+            "tolerance": 1e-12 if mode == "fp64" else 1e-5}
+
+
+def run_e2e(ctx, torch, dev, mom_h, w_h, E, P, N, world, args):
+    """rw_reweight_host from pinned host buffers: H2D momenta + weights,
+    reweight, D2H W' and the sums, every step."""
+    h_mom = torch.from_numpy(mom_h).pin_memory()
+    h_w = torch.from_numpy(w_h).pin_memory()
+    h_wnew = torch.empty((P, E), dtype=torch.float64).pin_memory()
+    nb = ctx.workspace_bytes_host(E)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    steps = max(3, args.steps // 2)
+    for _ in range(max(3, args.warmup)):
+        ctx.reweight_host(h_mom, h_w, E, h_wnew, P, ws, nb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.reweight_host(h_mom, h_w, E, h_wnew, P, ws, nb)
+    t = (time.perf_counter() - t0) / steps
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    # the device path's workspace pointers were re-attached by the host call
+    return {"value": world * E * P / t, "unit": UNIT, "h2d_bytes_per_step": int(8 * (4 * N * E + E)),
+            "d2h_bytes_per_step": int(8 * (P * E + P + 2)), "ms_per_step": 1e3 * t, "steps": steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

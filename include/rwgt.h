@@ -1,0 +1,154 @@
+/*
+ * rwgt.h -- C ABI of librwgt.so: leading-order event reweighting on one GPU.
+ *
+ * The library follows the reweighting procedure of arXiv:2312.07440,
+ * Sec. 3.2 ("Parallel LO scattering amplitudes and reweighting"):
+ *   1) input reweight parameters          -> rw_set_params, rw_set_reweight_points
+ *   2) parse events                        -> rw_load_events (device arrays)
+ *   3) evaluate original |M|^2             -> rw_eval_me(point = -1), or fused in rw_reweight*
+ *   4) overwrite physics parameters        -> the parameter points
+ *   5) evaluate new |M'|^2                 -> rw_eval_me(point = p), or fused
+ *   6) new weight W' = |M'|^2/|M|^2 W      (Sec. 2.2, Eq. 3)
+ *   7) repeat 4-6 for all parameter sets   (all points in one launch)
+ *   8) return new weights                  -> W'[P][E] and sigma'_p = sum_k W'_pk (Sec. 2.1, Eq. 2)
+ * The validity condition of Eq. 3 (|M|^2 != 0, Sec. 2.2) is reported, not
+ * fatal: an event with |M|^2 == 0 or non-finite gets r = W' = 0, is left out
+ * of sigma' and is counted; the call then returns RW_WARN_BAD_EVENTS.
+ *
+ * |M|^2 is the tree-level squared matrix element averaged over initial spins
+ * and colours and summed over final ones (1/n! for n identical outgoing
+ * gluons).  Processes: e+e- -> mu+mu- (photon + Z), g g -> t tbar,
+ * g g -> t tbar g, g g -> t tbar g g.
+ *
+ * Conventions
+ *  - Momenta: float64, structure of arrays mom[N][4][E] (particle, component
+ *    (E, px, py, pz), event), in GeV, partonic centre-of-mass frame, incoming
+ *    partons first.  Particle order: e-, e+, mu-, mu+  |  g, g, t, tbar, g, g.
+ *  - Weights: float64 w[E].  Outputs W'[P][E], r[P][E], |M|^2 [E] float64.
+ *  - A top-mass change moves each event onto the new mass shell (outgoing
+ *    3-momenta scaled by a common factor at fixed partonic energy) before
+ *    |M'|^2 is evaluated; an event the new masses do not fit gets |M'|^2 = 0.
+ *  - Ownership: the caller owns every event, output and workspace buffer
+ *    (device memory unless the name says h_); the context owns only itself
+ *    and a small pinned staging buffer.  Pointers passed to rw_load_events
+ *    must stay valid until the next rw_load_events or rw_destroy.
+ *  - Asynchrony: work is queued on the context's stream; only calls with
+ *    h_ outputs (and rw_reweight_host) synchronise that stream.
+ *  - Errors: every call returns RW_OK (0), a warning (> 0) or an error (< 0);
+ *    rw_last_error() describes the last failure.  A context is not
+ *    thread-safe; separate contexts are independent.
+ */
+#ifndef RWGT_H
+#define RWGT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RW_OK 0
+#define RW_WARN_BAD_EVENTS 1    /* some events had |M|^2 == 0 or non-finite */
+#define RW_ERR_NULL (-1)        /* a required pointer is NULL */
+#define RW_ERR_ARG (-2)         /* bad size, count or index */
+#define RW_ERR_MODE (-3)        /* process/precision combination not available */
+#define RW_ERR_PARAM (-4)       /* non-finite or unphysical model parameter */
+#define RW_ERR_CUDA (-5)        /* a CUDA runtime call failed (message in rw_last_error) */
+#define RW_ERR_STATE (-6)       /* call out of order (e.g. no process or events set) */
+#define RW_ERR_ALIGN (-7)       /* buffer not 8-byte (16-byte for workspace) aligned */
+#define RW_ERR_WORKSPACE (-8)   /* workspace smaller than rw_workspace_bytes() */
+
+/* processes */
+#define RW_EE_MUMU 0   /* e- e+ -> mu- mu+, 2 diagrams, 16 helicities */
+#define RW_GG_TT 1     /* g g -> t tbar, 3 diagrams, 2 colour orderings */
+#define RW_GG_TTG 2    /* g g -> t tbar g, 16 diagrams, 6 orderings */
+#define RW_GG_TTGG 3   /* g g -> t tbar g g, 123 diagrams, 24 orderings */
+
+/* precision modes of the amplitude arithmetic; momenta, propagator
+   invariants, r, W' and sigma are FP64 in every mode */
+#define RW_FP64 0
+#define RW_FP32 1
+
+#define RW_MAX_POINTS 256
+
+/* Model parameters (Sec. 3.2 step 1).  QCD processes use alpha_s and m_t
+   (w_t must be 0: every top propagator here is off shell; yt_scale, the top
+   Yukawa scale, enters no tree diagram of these processes).  e+e- -> mu+mu-
+   uses alpha_em_inv = 1/alpha, G_F [GeV^-2], m_Z, w_Z [GeV]; M_W and s_W are
+   derived: M_W^2 = M_Z^2/2 + sqrt(M_Z^4/4 - pi alpha M_Z^2/(sqrt2 G_F)). */
+typedef struct rw_params {
+  double alpha_s, m_t, w_t, yt_scale;
+  double alpha_em_inv, G_F, m_Z, w_Z;
+} rw_params;
+
+/* static description of a process (for flop accounting and checks) */
+typedef struct rw_process_info {
+  int n_external;      /* external particles N */
+  int n_helicities;    /* 2^N */
+  int n_colour_flows;  /* K: colour orderings (1 for e+e- -> mu+mu-) */
+  int n_diagrams;      /* tree Feynman diagrams */
+  int colour_den;      /* C = C_int / colour_den */
+  long long flops_hel_sum; /* amplitude + colour-sum flops of one helicity-summed |M|^2 */
+} rw_process_info;
+
+typedef struct rw_ctx rw_ctx;
+
+/* Create a context on CUDA device `device`, queuing work on `cuda_stream`
+   (a cudaStream_t; NULL = the legacy default stream).  *ctx is NULL on error. */
+int rw_create(rw_ctx** ctx, int device, void* cuda_stream);
+int rw_destroy(rw_ctx* ctx);
+/* description of the last error on this context (owned by the context) */
+const char* rw_last_error(const rw_ctx* ctx);
+
+int rw_process_info_get(int process, rw_process_info* out);
+
+/* Select process and precision mode.  Resets parameters and events. */
+int rw_set_process(rw_ctx* ctx, int process, int mode);
+/* Step 1: the original parameters of the event sample. */
+int rw_set_params(rw_ctx* ctx, const rw_params* orig);
+/* Steps 4/7: P modified parameter points (1 <= P <= RW_MAX_POINTS). */
+int rw_set_reweight_points(rw_ctx* ctx, const rw_params* pts, int P);
+/* Launch shape: lanes per event = 2^lane_bits (-1 = default), threads per
+   block (multiple of 32, <= 256; 0 = default). */
+int rw_set_tuning(rw_ctx* ctx, int lane_bits, int block);
+
+/* Device workspace needed for E events with the current points (bytes). */
+size_t rw_workspace_bytes(const rw_ctx* ctx, int64_t n_events);
+/* Step 2: attach a device event batch (SoA momenta [N][4][E], weights [E])
+   and a device workspace of at least rw_workspace_bytes(E), 16-byte aligned.
+   Clears the workspace counters (asynchronously). */
+int rw_load_events(rw_ctx* ctx, const double* d_mom, const double* d_w, int64_t n_events, void* d_workspace,
+                   size_t workspace_bytes);
+
+/* Steps 3/5: |M|^2 of every event under the original parameters
+   (point = -1) or under point p (momenta moved to its mass shell if m_t
+   differs).  d_me_out: device [E]. */
+int rw_eval_me(rw_ctx* ctx, int point, double* d_me_out);
+
+/* Steps 3-7 fused, no host synchronisation: W'[P][E], r[P][E], |M|^2 [E]
+   and |M'|^2 [P][E] are written where the pointer is not NULL; sigma'_p,
+   sigma and the bad-event count stay in the workspace (rw_get_results). */
+int rw_reweight_async(rw_ctx* ctx, double* d_wnew, double* d_ratio, double* d_me0, double* d_me_pts);
+/* Copy the last reweight's sigma'_p [P], sigma (original) and bad-event count
+   to the host; synchronises the stream.  Returns RW_WARN_BAD_EVENTS if any. */
+int rw_get_results(rw_ctx* ctx, double* h_sigma, double* h_sigma_orig, int64_t* h_n_bad);
+/* rw_reweight_async + rw_get_results. */
+int rw_reweight(rw_ctx* ctx, double* d_wnew, double* d_ratio, double* h_sigma, double* h_sigma_orig,
+                int64_t* h_n_bad);
+
+/* End to end from host memory: copies momenta [N][4][E] and weights [E] to
+   the device workspace, reweights, copies W'[P][E] back to h_wnew (may be
+   NULL) and the sums to h_sigma/h_sigma_orig/h_n_bad; synchronises.  The
+   device workspace must hold rw_workspace_bytes_host(E) bytes.  Host buffers
+   should be pinned (cudaHostAlloc) for full copy bandwidth. */
+size_t rw_workspace_bytes_host(const rw_ctx* ctx, int64_t n_events);
+int rw_reweight_host(rw_ctx* ctx, const double* h_mom, const double* h_w, int64_t n_events, double* h_wnew,
+                     double* h_sigma, double* h_sigma_orig, int64_t* h_n_bad, void* d_workspace,
+                     size_t workspace_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RWGT_H */

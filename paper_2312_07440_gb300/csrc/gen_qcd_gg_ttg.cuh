@@ -1,0 +1,125 @@
+// ---- generated by gen/qcd_gen.py: gg_ttg (g g -> t tbar + 1 g), do not edit ----
+// 16 Feynman diagrams, 6 colour orderings, 32 helicities.
+// colour matrix C = Cint / 9
+#pragma once
+#include "qcd.cuh"
+
+namespace rw { namespace gg_ttg {
+constexpr int NG = 3;
+constexpr int NEXT = 5;
+constexpr int K = 6;
+constexpr int NHEL = 32;
+constexpr int NDIAG = 16;
+constexpr int CDEN = 9;
+constexpr int IDENT = 1;  // identical outgoing gluons (1/IDENT!)
+constexpr unsigned OUTGOING_GLUONS = 4u;  // bit g: gluon g outgoing
+__host__ __device__ constexpr int cint(int i, int j) { constexpr int c[K * K] = {64, -8, -8, 1, 1, 10, -8, 64, 1, 10, -8, 1, -8, 1, 64, -8, 10, 1, 1, 10, -8, 64, 1, -8, 1, -8, 10, 1, 64, -8, 10, 1, 1, -8, -8, 64}; return c[i * K + j]; }
+constexpr int ORDER[K][NG] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1.
+template <class R, int LB>
+__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
+  R acc = R(0);
+  #pragma unroll 1
+  for (int i0 = 0; i0 < (LB > 0 ? 1 : 2); ++i0) {
+    const int h0 = LB > 0 ? ((lane >> (LB - 1 - 0)) & 1) : i0;
+    const cv<R> E0 = h0 ? X.eps[0][1] : X.eps[0][0];
+    #pragma unroll 1
+    for (int i1 = 0; i1 < (LB > 1 ? 1 : 2); ++i1) {
+      const int h1 = LB > 1 ? ((lane >> (LB - 1 - 1)) & 1) : i1;
+      const cv<R> E1 = h1 ? X.eps[1][1] : X.eps[1][0];
+      cv<R> J0_1 = vvv(E0, Kn.P[1], E1, Kn.P[2], Kn.cg[3]);
+      const cv<R> J1_0 = neg(J0_1);
+      #pragma unroll 1
+      for (int i2 = 0; i2 < (LB > 2 ? 1 : 2); ++i2) {
+        const int h2 = LB > 2 ? ((lane >> (LB - 1 - 2)) & 1) : i2;
+        const cv<R> E2 = h2 ? X.eps[2][1] : X.eps[2][0];
+        cv<R> J0_2 = vvv(E0, Kn.P[1], E2, Kn.P[4], Kn.cg[5]);
+        cv<R> J1_2 = vvv(E1, Kn.P[2], E2, Kn.P[4], Kn.cg[6]);
+        const cv<R> J2_0 = neg(J0_2);
+        const cv<R> J2_1 = neg(J1_2);
+        cv<R> J0_1_2 = vvv(E0, Kn.P[1], J1_2, Kn.P[6], Kn.cg[7]);
+        addto(J0_1_2, vvv(J0_1, Kn.P[3], E2, Kn.P[4], Kn.cg[7]));
+        vvvv_acc(J0_1_2, E0, E1, E2, Kn.c4[7]);
+        cv<R> J0_2_1 = vvv(E0, Kn.P[1], J2_1, Kn.P[6], Kn.cg[7]);
+        addto(J0_2_1, vvv(J0_2, Kn.P[5], E1, Kn.P[2], Kn.cg[7]));
+        vvvv_acc(J0_2_1, E0, E2, E1, Kn.c4[7]);
+        cv<R> J1_0_2 = vvv(E1, Kn.P[2], J0_2, Kn.P[5], Kn.cg[7]);
+        addto(J1_0_2, vvv(J1_0, Kn.P[3], E2, Kn.P[4], Kn.cg[7]));
+        vvvv_acc(J1_0_2, E1, E0, E2, Kn.c4[7]);
+        const cv<R> J1_2_0 = J0_2_1;
+        const cv<R> J2_0_1 = J1_0_2;
+        const cv<R> J2_1_0 = J0_1_2;
+        #pragma unroll 1
+        for (int i3 = 0; i3 < (LB > 3 ? 1 : 2); ++i3) {
+          const int h3 = LB > 3 ? ((lane >> (LB - 1 - 3)) & 1) : i3;
+          const sp<R> S_E = h3 ? X.v[1] : X.v[0];
+          sp<R> tS_0 = slash(E0, S_E);
+          const sp<R> S_0 = fprop(Kn.qc[1], Kn.mc[1], tS_0);
+          sp<R> tS_1 = slash(E1, S_E);
+          const sp<R> S_1 = fprop(Kn.qc[2], Kn.mc[2], tS_1);
+          sp<R> tS_2 = slash(E2, S_E);
+          const sp<R> S_2 = fprop(Kn.qc[4], Kn.mc[4], tS_2);
+          sp<R> tS_0_1 = slash(E0, S_1);
+          spadd(tS_0_1, slash(J0_1, S_E));
+          const sp<R> S_0_1 = fprop(Kn.qc[3], Kn.mc[3], tS_0_1);
+          sp<R> tS_0_2 = slash(E0, S_2);
+          spadd(tS_0_2, slash(J0_2, S_E));
+          const sp<R> S_0_2 = fprop(Kn.qc[5], Kn.mc[5], tS_0_2);
+          sp<R> tS_1_0 = slash(E1, S_0);
+          spadd(tS_1_0, slash(J1_0, S_E));
+          const sp<R> S_1_0 = fprop(Kn.qc[3], Kn.mc[3], tS_1_0);
+          sp<R> tS_1_2 = slash(E1, S_2);
+          spadd(tS_1_2, slash(J1_2, S_E));
+          const sp<R> S_1_2 = fprop(Kn.qc[6], Kn.mc[6], tS_1_2);
+          sp<R> tS_2_0 = slash(E2, S_0);
+          spadd(tS_2_0, slash(J2_0, S_E));
+          const sp<R> S_2_0 = fprop(Kn.qc[5], Kn.mc[5], tS_2_0);
+          sp<R> tS_2_1 = slash(E2, S_1);
+          spadd(tS_2_1, slash(J2_1, S_E));
+          const sp<R> S_2_1 = fprop(Kn.qc[6], Kn.mc[6], tS_2_1);
+          #pragma unroll 1
+          for (int i4 = 0; i4 < (LB > 4 ? 1 : 2); ++i4) {
+            const int h4 = LB > 4 ? ((lane >> (LB - 1 - 4)) & 1) : i4;
+            const sp<R> UB = h4 ? X.ub[1] : X.ub[0];
+            const cv<R> F_E = fcur(UB, S_E);
+            const cv<R> F_0 = fcur(UB, S_0);
+            const cv<R> F_1 = fcur(UB, S_1);
+            const cv<R> F_2 = fcur(UB, S_2);
+            const cv<R> F_0_1 = fcur(UB, S_0_1);
+            const cv<R> F_0_2 = fcur(UB, S_0_2);
+            const cv<R> F_1_0 = fcur(UB, S_1_0);
+            const cv<R> F_1_2 = fcur(UB, S_1_2);
+            const cv<R> F_2_0 = fcur(UB, S_2_0);
+            const cv<R> F_2_1 = fcur(UB, S_2_1);
+            const cx<R> A0 = dot(E0, F_1_2) + dot(J0_1, F_2) + dot(J0_1_2, F_E);
+            const cx<R> A1 = dot(E0, F_2_1) + dot(J0_2, F_1) + dot(J0_2_1, F_E);
+            const cx<R> A2 = dot(E1, F_0_2) + dot(J1_0, F_2) + dot(J1_0_2, F_E);
+            const cx<R> A3 = dot(E1, F_2_0) + dot(J1_2, F_0) + dot(J1_2_0, F_E);
+            const cx<R> A4 = dot(E2, F_0_1) + dot(J2_0, F_1) + dot(J2_0_1, F_E);
+            const cx<R> A5 = dot(E2, F_1_0) + dot(J2_1, F_0) + dot(J2_1_0, F_E);
+            R cs = R(0);
+            { const R zr = R(64) * R(0.5) * A0.r + R(-8) * A1.r + R(-8) * A2.r + R(1) * A3.r + R(1) * A4.r + R(10) * A5.r; const R zi = R(64) * R(0.5) * A0.i + R(-8) * A1.i + R(-8) * A2.i + R(1) * A3.i + R(1) * A4.i + R(10) * A5.i;
+              cs += A0.r * zr + A0.i * zi; }
+            { const R zr = R(64) * R(0.5) * A1.r + R(1) * A2.r + R(10) * A3.r + R(-8) * A4.r + R(1) * A5.r; const R zi = R(64) * R(0.5) * A1.i + R(1) * A2.i + R(10) * A3.i + R(-8) * A4.i + R(1) * A5.i;
+              cs += A1.r * zr + A1.i * zi; }
+            { const R zr = R(64) * R(0.5) * A2.r + R(-8) * A3.r + R(10) * A4.r + R(1) * A5.r; const R zi = R(64) * R(0.5) * A2.i + R(-8) * A3.i + R(10) * A4.i + R(1) * A5.i;
+              cs += A2.r * zr + A2.i * zi; }
+            { const R zr = R(64) * R(0.5) * A3.r + R(1) * A4.r + R(-8) * A5.r; const R zi = R(64) * R(0.5) * A3.i + R(1) * A4.i + R(-8) * A5.i;
+              cs += A3.r * zr + A3.i * zi; }
+            { const R zr = R(64) * R(0.5) * A4.r + R(-8) * A5.r; const R zi = R(64) * R(0.5) * A4.i + R(-8) * A5.i;
+              cs += A4.r * zr + A4.i * zi; }
+            { const R zr = R(64) * R(0.5) * A5.r; const R zi = R(64) * R(0.5) * A5.i;
+              cs += A5.r * zr + A5.i * zi; }
+            acc += R(2) * cs;
+          }
+        }
+      }
+    }
+  }
+  return acc;
+}
+
+// floating-point operations of one full helicity sum (all levels, all loop trips)
+constexpr long FLOPS_HEL_SUM = 84648;
+}}  // namespace

@@ -1,0 +1,270 @@
+// Device building blocks of the helicity amplitudes (HELAS-style, written for
+// sm_103a): complex arithmetic, external wavefunctions, colour-ordered
+// vertices and propagators.  Templated on the working precision R (double in
+// FP64 mode, float in FP32 mode).
+//
+// Conventions: metric (+,-,-,-); Dirac matrices in the chiral basis
+// gamma^mu = [[0, sigma^mu], [sigmabar^mu, 0]], spinors stored as
+// (L0, L1, R0, R1); all gluon momenta in the vertices are incoming.
+// The amplitudes are the colour-ordered partial amplitudes A(sigma) of the
+// decomposition M_ij = sum_sigma (t^{a_sigma1} ... t^{a_sigman})_ij A(sigma)
+// (t^a = lambda^a / 2) with the strong coupling stripped (g = 1).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace rw {
+
+template <class R>
+struct cx {
+  R r, i;
+};
+template <class R>
+struct cv {  // complex Lorentz vector, upper index
+  cx<R> c[4];
+};
+template <class R>
+struct sp {  // Dirac spinor (or a row spinor ubar)
+  cx<R> c[4];
+};
+
+template <class R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.r + b.r, a.i + b.i}; }
+template <class R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.r - b.r, a.i - b.i}; }
+template <class R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a) { return {-a.r, -a.i}; }
+template <class R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r};
+}
+template <class R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return {s * a.r, s * a.i}; }
+template <class R>
+__device__ __forceinline__ cx<R> conjg(cx<R> a) { return {a.r, -a.i}; }
+template <class R>
+__device__ __forceinline__ cx<R> times_i(cx<R> a) { return {-a.i, a.r}; }
+
+// a.b (Minkowski, no conjugation): 30 flops
+template <class R>
+__device__ __forceinline__ cx<R> dot(const cv<R>& a, const cv<R>& b) {
+  return a.c[0] * b.c[0] - a.c[1] * b.c[1] - a.c[2] * b.c[2] - a.c[3] * b.c[3];
+}
+// p.a with a real vector p: 14 flops
+template <class R>
+__device__ __forceinline__ cx<R> dotr(const R (&p)[4], const cv<R>& a) {
+  return {p[0] * a.c[0].r - p[1] * a.c[1].r - p[2] * a.c[2].r - p[3] * a.c[3].r,
+          p[0] * a.c[0].i - p[1] * a.c[1].i - p[2] * a.c[2].i - p[3] * a.c[3].i};
+}
+template <class R>
+__device__ __forceinline__ cv<R> neg(const cv<R>& a) {
+  return {{-a.c[0], -a.c[1], -a.c[2], -a.c[3]}};
+}
+template <class R>
+__device__ __forceinline__ void addto(cv<R>& a, const cv<R>& b) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) a.c[m] = a.c[m] + b.c[m];
+}
+template <class R>
+__device__ __forceinline__ void spadd(sp<R>& a, const sp<R>& b) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) a.c[m] = a.c[m] + b.c[m];
+}
+
+// Colour-ordered 3-gluon vertex and the off-shell gluon propagator,
+// c = -1/K^2 (Feynman gauge, g stripped), K = P1 + P2:
+//   out = c [ -J1 (2P1+P2).J2 + (J1.J2)(P1-P2) + J2 (2P2+P1).J1 ]     (156 flops)
+template <class R>
+__device__ __forceinline__ cv<R> vvv(const cv<R>& J1, const R (&P1)[4], const cv<R>& J2, const R (&P2)[4], R c) {
+  R a[4], b[4], d[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    a[m] = R(2) * P1[m] + P2[m];
+    b[m] = R(2) * P2[m] + P1[m];
+    d[m] = P1[m] - P2[m];
+  }
+  const cx<R> s1 = c * dotr(a, J2);
+  const cx<R> s2 = c * dotr(b, J1);
+  const cx<R> s12 = c * dot(J1, J2);
+  cv<R> o;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) o.c[m] = J2.c[m] * s2 - J1.c[m] * s1 + d[m] * s12;
+  return o;
+}
+
+// Colour-ordered 4-gluon vertex with the propagator c = +1/K^2:
+//   out += c [ 2 J2 (J1.J3) - J1 (J2.J3) - J3 (J1.J2) ]                 (193 flops)
+template <class R>
+__device__ __forceinline__ void vvvv_acc(cv<R>& o, const cv<R>& J1, const cv<R>& J2, const cv<R>& J3, R c) {
+  const cx<R> t13 = (R(2) * c) * dot(J1, J3);
+  const cx<R> t23 = c * dot(J2, J3);
+  const cx<R> t12 = c * dot(J1, J2);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) o.c[m] = o.c[m] + J2.c[m] * t13 - J1.c[m] * t23 - J3.c[m] * t12;
+}
+
+// Jslash psi = gamma^mu J_mu psi                                          (64 flops)
+template <class R>
+__device__ __forceinline__ sp<R> slash(const cv<R>& a, const sp<R>& s) {
+  const cx<R> ap = a.c[0] + a.c[3], am = a.c[0] - a.c[3];
+  const cx<R> bp = {a.c[1].r - a.c[2].i, a.c[1].i + a.c[2].r};  // a1 + i a2
+  const cx<R> bm = {a.c[1].r + a.c[2].i, a.c[1].i - a.c[2].r};  // a1 - i a2
+  sp<R> o;
+  o.c[0] = am * s.c[2] - bm * s.c[3];
+  o.c[1] = ap * s.c[3] - bp * s.c[2];
+  o.c[2] = ap * s.c[0] + bm * s.c[1];
+  o.c[3] = bp * s.c[0] + am * s.c[1];
+  return o;
+}
+
+// Top propagator applied to a spinor, with the factor folded in:
+//   (qc slash + mc) chi,  qc = c q, mc = c m,  c = -1/(q^2 - m^2)         (58 flops)
+template <class R>
+__device__ __forceinline__ sp<R> fprop(const R (&q)[4], R mc, const sp<R>& s) {
+  const R ap = q[0] + q[3], am = q[0] - q[3];
+  sp<R> o;
+  // (q1 - i q2) s3  and  (q1 + i q2) s2 etc.
+  o.c[0] = am * s.c[2] - cx<R>{q[1] * s.c[3].r + q[2] * s.c[3].i, q[1] * s.c[3].i - q[2] * s.c[3].r} + mc * s.c[0];
+  o.c[1] = ap * s.c[3] - cx<R>{q[1] * s.c[2].r - q[2] * s.c[2].i, q[1] * s.c[2].i + q[2] * s.c[2].r} + mc * s.c[1];
+  o.c[2] = ap * s.c[0] + cx<R>{q[1] * s.c[1].r + q[2] * s.c[1].i, q[1] * s.c[1].i - q[2] * s.c[1].r} + mc * s.c[2];
+  o.c[3] = am * s.c[1] + cx<R>{q[1] * s.c[0].r - q[2] * s.c[0].i, q[1] * s.c[0].i + q[2] * s.c[0].r} + mc * s.c[3];
+  return o;
+}
+
+// Fermion current ubar gamma^mu psi (upper index), ubar a row spinor       (72 flops)
+template <class R>
+__device__ __forceinline__ cv<R> fcur(const sp<R>& u, const sp<R>& s) {
+  // ubar_L sigma^mu psi_R + ubar_R sigmabar^mu psi_L
+  const cx<R> a = u.c[0] * s.c[2], b = u.c[1] * s.c[3], c = u.c[0] * s.c[3], d = u.c[1] * s.c[2];
+  const cx<R> a2 = u.c[2] * s.c[0], b2 = u.c[3] * s.c[1], c2 = u.c[2] * s.c[1], d2 = u.c[3] * s.c[0];
+  cv<R> o;
+  o.c[0] = (a + b) + (a2 + b2);
+  o.c[1] = (c + d) - (c2 + d2);
+  o.c[2] = times_i((d - c) - (d2 - c2));
+  o.c[3] = (a - b) - (a2 - b2);
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// External wavefunctions (computed in double from the FP64 momenta)
+// ---------------------------------------------------------------------------
+// Helicity eigen-2-spinors chi_{+-}(p) along pvec, with |p| + p_z formed
+// without cancellation; phi = 0 when p_T = 0.
+__device__ __forceinline__ void chi_pm(const double (&p)[4], cx<double> (&cp)[2], cx<double> (&cm)[2]) {
+  const double pt2 = p[1] * p[1] + p[2] * p[2];
+  const double pp = sqrt(pt2 + p[3] * p[3]);
+  const double ppz = p[3] >= 0.0 ? pp + p[3] : pt2 / (pp - p[3]);  // |p| + p_z
+  if (ppz > 0.0 && pp > 0.0) {
+    const double c = sqrt(ppz / (2.0 * pp));
+    const double s = 1.0 / sqrt(2.0 * pp * ppz);
+    cp[0] = {c, 0.0};
+    cp[1] = {p[1] * s, p[2] * s};
+    cm[0] = {-p[1] * s, p[2] * s};
+    cm[1] = {c, 0.0};
+  } else {  // along -z (or p = 0)
+    cp[0] = {0.0, 0.0};
+    cp[1] = {1.0, 0.0};
+    cm[0] = {-1.0, 0.0};
+    cm[1] = {0.0, 0.0};
+  }
+}
+
+template <class R>
+__device__ __forceinline__ cx<R> cast(cx<double> a) {
+  return {R(a.r), R(a.i)};
+}
+
+// ubar(p, lambda) for an outgoing fermion (row spinor), index 0: lambda=+1/2, 1: -1/2.
+// u(p,+) = (w- chi+, w+ chi+), u(p,-) = (w+ chi-, w- chi-), w+- = sqrt(E +- |p|),
+// w- = m / w+ (no cancellation); ubar = (u_R^*, u_L^*).
+template <class R>
+__device__ __forceinline__ void ubar_out(const double (&p)[4], double m, sp<R> (&ub)[2]) {
+  cx<double> cp[2], cm[2];
+  chi_pm(p, cp, cm);
+  const double pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  const double wp = sqrt(p[0] + pp);
+  const double wm = m > 0.0 ? m / wp : 0.0;
+  // lambda = +
+  ub[0].c[0] = cast<R>(conjg(wp * cp[0]));
+  ub[0].c[1] = cast<R>(conjg(wp * cp[1]));
+  ub[0].c[2] = cast<R>(conjg(wm * cp[0]));
+  ub[0].c[3] = cast<R>(conjg(wm * cp[1]));
+  // lambda = -
+  ub[1].c[0] = cast<R>(conjg(wm * cm[0]));
+  ub[1].c[1] = cast<R>(conjg(wm * cm[1]));
+  ub[1].c[2] = cast<R>(conjg(wp * cm[0]));
+  ub[1].c[3] = cast<R>(conjg(wp * cm[1]));
+}
+
+// v(p, lambda) for an outgoing antifermion: v(p,+) = (w+ chi-, -w- chi-),
+// v(p,-) = (w- chi+, -w+ chi+).
+template <class R>
+__device__ __forceinline__ void v_out(const double (&p)[4], double m, sp<R> (&v)[2]) {
+  cx<double> cp[2], cm[2];
+  chi_pm(p, cp, cm);
+  const double pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  const double wp = sqrt(p[0] + pp);
+  const double wm = m > 0.0 ? m / wp : 0.0;
+  v[0].c[0] = cast<R>(wp * cm[0]);
+  v[0].c[1] = cast<R>(wp * cm[1]);
+  v[0].c[2] = cast<R>(-wm * cm[0]);
+  v[0].c[3] = cast<R>(-wm * cm[1]);
+  v[1].c[0] = cast<R>(wm * cp[0]);
+  v[1].c[1] = cast<R>(wm * cp[1]);
+  v[1].c[2] = cast<R>(-wp * cp[0]);
+  v[1].c[3] = cast<R>(-wp * cp[1]);
+}
+
+// u(p, lambda) for an incoming fermion
+template <class R>
+__device__ __forceinline__ void u_in(const double (&p)[4], double m, sp<R> (&u)[2]) {
+  cx<double> cp[2], cm[2];
+  chi_pm(p, cp, cm);
+  const double pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  const double wp = sqrt(p[0] + pp);
+  const double wm = m > 0.0 ? m / wp : 0.0;
+  u[0].c[0] = cast<R>(wm * cp[0]);
+  u[0].c[1] = cast<R>(wm * cp[1]);
+  u[0].c[2] = cast<R>(wp * cp[0]);
+  u[0].c[3] = cast<R>(wp * cp[1]);
+  u[1].c[0] = cast<R>(wp * cm[0]);
+  u[1].c[1] = cast<R>(wp * cm[1]);
+  u[1].c[2] = cast<R>(wm * cm[0]);
+  u[1].c[3] = cast<R>(wm * cm[1]);
+}
+
+// vbar(p, lambda) = v^dagger gamma^0 for an incoming antifermion (row spinor)
+template <class R>
+__device__ __forceinline__ void vbar_in(const double (&p)[4], double m, sp<R> (&vb)[2]) {
+  sp<double> v[2];
+  v_out<double>(p, m, v);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    vb[h].c[0] = cast<R>(conjg(v[h].c[2]));
+    vb[h].c[1] = cast<R>(conjg(v[h].c[3]));
+    vb[h].c[2] = cast<R>(conjg(v[h].c[0]));
+    vb[h].c[3] = cast<R>(conjg(v[h].c[1]));
+  }
+}
+
+// Transverse polarisation eps(k, lambda) = (-lambda e1 - i e2)/sqrt(2),
+// e1 = (0, cos t cos f, cos t sin f, -sin t), e2 = (0, -sin f, cos f, 0);
+// index 0: lambda = +1, 1: lambda = -1; conjugated for an outgoing gluon.
+template <class R>
+__device__ __forceinline__ void polvec(const double (&k)[4], bool outgoing, cv<R> (&e)[2]) {
+  const double pt = sqrt(k[1] * k[1] + k[2] * k[2]);
+  const double kk = sqrt(pt * pt + k[3] * k[3]);
+  const double ct = k[3] / kk, st = pt / kk;
+  const double cf = pt > 0.0 ? k[1] / pt : 1.0, sf = pt > 0.0 ? k[2] / pt : 0.0;
+  const double r2 = 0.70710678118654752440;
+  const double e1[4] = {0.0, ct * cf, ct * sf, -st};
+  const double e2[4] = {0.0, -sf, cf, 0.0};
+  const double sgn = outgoing ? -1.0 : 1.0;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    e[0].c[m] = {R(-r2 * e1[m]), R(-sgn * r2 * e2[m])};
+    e[1].c[m] = {R(r2 * e1[m]), R(-sgn * r2 * e2[m])};
+  }
+}
+
+}  // namespace rw

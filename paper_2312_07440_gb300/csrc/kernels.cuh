@@ -1,0 +1,212 @@
+// The fused reweighting kernel (Sec. 3.2, steps 3-7, Eqs. 2-3 of
+// arXiv:2312.07440), one launch for a whole event batch and every parameter
+// point:
+//   per event: load the FP64 momenta (structure of arrays, coalesced), |M|^2
+//   under the original parameters, then for each point p: (mass-shell
+//   reshuffle if the top mass changed) |M'_p|^2, r_p = |M'_p|^2/|M|^2 in FP64,
+//   W'_p = r_p W; the cross sections sigma'_p = sum W'_p and sigma = sum W are
+//   accumulated as compensated (TwoSum) pairs per warp and block and reduced
+//   in a fixed order by the last block to finish, so the result is
+//   deterministic for a given launch shape.
+// Events violating |M|^2 != 0 (zero or non-finite) get r = W' = 0, are left
+// out of sigma' and are counted.
+//
+// Threads: a group of 2^LB lanes shares one event; each lane sums its slice
+// of the helicities and the slices are combined by xor shuffles inside the
+// group.  The grid is at most (resident blocks x SMs) and strides over the
+// events.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "helas.cuh"
+
+namespace rw {
+
+constexpr int MAX_POINTS = 256;
+
+struct PointDev {
+  double cscale;  // QCD: (4 pi alpha_s)^n / (spin/colour average x n_ident! x colour denominator)
+  double m_t;     // top mass of this evaluation
+  double e, gL, gR, MZ, WZ;  // electroweak couplings (e+e- -> mu+mu-)
+  int reshuffle;  // 1: move the event onto the m_t mass shell first
+  int pad;
+};
+
+struct RwArgs {
+  const double* mom;  // [N][4][E]
+  const double* w;    // [E]
+  long long E;
+  double* me0;     // [E] or null
+  double* me_pts;  // [P][E] or null
+  double* ratio;   // [P][E] or null
+  double* wnew;    // [P][E] or null
+  double2* block_part;            // [gridDim.x][P+1] scratch
+  double* sigma;                  // [P+1]: sigma'_0..P-1, sigma (original)
+  unsigned int* ticket;           // zero between launches
+  unsigned long long* nbad_count; // zero between launches
+  unsigned long long* nbad_out;
+  int P;
+  int me_only;  // evaluate pt[0] only and write me0 (no reductions)
+  PointDev pt[MAX_POINTS + 1];  // [0] original, [1..P] modified points
+};
+
+// ---- compensated (TwoSum) accumulation -------------------------------------
+__device__ __forceinline__ void two_sum_acc(double& s, double& c, double x, double cx) {
+  const double t = s + x;
+  const double bp = t - s;
+  const double e = (s - (t - bp)) + (x - bp);
+  s = t;
+  c += cx + e;
+}
+
+__device__ __forceinline__ void warp_sum2(double& s, double& c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const double c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    two_sum_acc(s, c, s2, c2);
+  }
+}
+
+// lane 0 of the warp adds the warp total of x into slot (warp, j)
+__device__ __forceinline__ void warp_accumulate(double2* sacc, int warp, int stride, int j, double x) {
+  __syncwarp();
+  double s = x, c = 0.0;
+  warp_sum2(s, c);
+  if ((threadIdx.x & 31) == 0) {
+    double2 v = sacc[warp * stride + j];
+    two_sum_acc(v.x, v.y, s, c);
+    sacc[warp * stride + j] = v;
+  }
+}
+
+// deterministic block reduction of (s, c); result valid in thread 0
+__device__ __forceinline__ void block_sum2(double& s, double& c, double2* scratch) {
+  warp_sum2(s, c);
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) scratch[warp] = make_double2(s, c);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ss = 0.0, cc = 0.0;
+    for (int i = 0; i < nw; ++i) two_sum_acc(ss, cc, scratch[i].x, scratch[i].y);
+    s = ss;
+    c = cc;
+  }
+  __syncthreads();
+}
+
+// |M|^2 for one parameter point; a point with a new top mass first moves the
+// event onto its mass shell (|M'|^2 = 0 when the new masses do not fit).
+template <class Proc, class R, int LB>
+__device__ __forceinline__ double eval_point(const double (&p)[Proc::NEXT][4], const PointDev& pt, int lane,
+                                             unsigned gmask) {
+  double q[Proc::NEXT][4];
+  bool inside = true;
+  if (pt.reshuffle) {
+    inside = Proc::reshuffle(p, pt.m_t, q);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Proc::NEXT; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) q[i][m] = p[i][m];
+  }
+  const double v = Proc::template me<R, LB>(q, pt, lane, gmask);
+  return inside ? v : 0.0;
+}
+
+template <class Proc, class R, int LB>
+__global__ void __launch_bounds__(256, 1) k_reweight(const __grid_constant__ RwArgs a) {
+  constexpr int NEXT = Proc::NEXT;
+  constexpr int LANES = 1 << LB;
+  extern __shared__ double2 sacc[];  // [nwarps][P+1]
+  __shared__ double2 red[32];
+  __shared__ int is_last;
+  const int P = a.P;
+  const int stride = P + 1;
+  const int tid = threadIdx.x;
+  const int nw = blockDim.x >> 5;
+  const int warp = tid >> 5, wl = tid & 31;
+  const int lane = tid & (LANES - 1);
+  const unsigned gmask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << (wl & ~(LANES - 1)));
+  if (!a.me_only)
+    for (int i = tid; i < nw * stride; i += blockDim.x) sacc[i] = make_double2(0.0, 0.0);
+  __syncthreads();
+  const long long gpb = blockDim.x / LANES;
+  const long long ngroups = (long long)gridDim.x * gpb;
+  const long long g0 = (long long)blockIdx.x * gpb + tid / LANES;
+  const long long E = a.E;
+  unsigned long long nbad = 0;
+  for (long long base = 0; base < E; base += ngroups) {
+    const long long ev = base + g0;
+    const bool valid = ev < E;
+    const long long evc = valid ? ev : E - 1;
+    double p[NEXT][4];
+#pragma unroll
+    for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) p[i][m] = __ldg(a.mom + ((long long)(i * 4 + m)) * E + evc);
+    // One call site for every evaluation (original, then each point), so that
+    // identical parameters give bitwise identical |M|^2 and r == 1 exactly.
+    const bool leader = valid && lane == 0;
+    const double w = __ldg(a.w + evc);
+    double me0 = 0.0;
+    bool ok = false;
+    const int nev = a.me_only ? 1 : P + 1;
+#pragma unroll 1
+    for (int j = 0; j < nev; ++j) {
+      const double me = eval_point<Proc, R, LB>(p, a.pt[j], lane, gmask);
+      if (j == 0) {
+        me0 = me;
+        if (a.me_only) {
+          if (leader) a.me0[ev] = me;
+          break;
+        }
+        ok = isfinite(me0) && me0 != 0.0;
+        if (leader && !ok) ++nbad;
+        if (leader && a.me0) a.me0[ev] = me0;
+        warp_accumulate(sacc, warp, stride, P, leader ? w : 0.0);
+        continue;
+      }
+      const double r = ok ? me / me0 : 0.0;
+      const double wn = ok ? r * w : 0.0;
+      if (leader) {
+        const long long o = (long long)(j - 1) * E + ev;
+        if (a.me_pts) a.me_pts[o] = me;
+        if (a.ratio) a.ratio[o] = r;
+        if (a.wnew) a.wnew[o] = wn;
+      }
+      warp_accumulate(sacc, warp, stride, j - 1, leader ? wn : 0.0);
+    }
+  }
+  if (a.me_only) return;
+  __syncthreads();
+  for (int j = tid; j < stride; j += blockDim.x) {
+    double s = 0.0, c = 0.0;
+    for (int wi = 0; wi < nw; ++wi) two_sum_acc(s, c, sacc[wi * stride + j].x, sacc[wi * stride + j].y);
+    a.block_part[(long long)blockIdx.x * stride + j] = make_double2(s, c);
+  }
+  if (nbad) atomicAdd(a.nbad_count, nbad);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int j = 0; j < stride; ++j) {
+    double s = 0.0, c = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+      const double2 v = __ldcg(a.block_part + (long long)b * stride + j);
+      two_sum_acc(s, c, v.x, v.y);
+    }
+    block_sum2(s, c, red);
+    if (tid == 0) a.sigma[j] = s + c;
+  }
+  if (tid == 0) {
+    *a.nbad_out = atomicExch(a.nbad_count, 0ull);
+    *a.ticket = 0u;
+  }
+}
+
+}  // namespace rw

@@ -1,0 +1,28 @@
+// g g -> t tbar + n g kernel variants (gg_ttg, fp32).
+#include "../../include/rwgt.h"
+#include "gen_qcd_gg_ttg.cuh"
+#include "kernels.cuh"
+#include "procs.cuh"
+#include "registry.h"
+
+namespace rw {
+namespace {
+struct Tag {
+  static constexpr int NG = gg_ttg::NG;
+  static constexpr int NEXT = gg_ttg::NEXT;
+  template <class R, int LB>
+  __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
+    return gg_ttg::hel_sum<R, LB>(X, K, lane);
+  }
+};
+using P = QcdProc<Tag>;
+}  // namespace
+
+void register_gg_ttg_fp32(std::vector<KernelEntry>& t) {
+  t.push_back({RW_GG_TTG, RW_FP32, 0, (const void*)&k_reweight<P, float, 0>});
+  t.push_back({RW_GG_TTG, RW_FP32, 1, (const void*)&k_reweight<P, float, 1>});
+  t.push_back({RW_GG_TTG, RW_FP32, 2, (const void*)&k_reweight<P, float, 2>});
+  t.push_back({RW_GG_TTG, RW_FP32, 3, (const void*)&k_reweight<P, float, 3>});
+}
+
+}  // namespace rw

@@ -1,0 +1,33 @@
+// g g -> t tbar + n g kernel variants (gg_ttg, fp64).
+#include "../../include/rwgt.h"
+#include "gen_qcd_gg_ttg.cuh"
+#include "kernels.cuh"
+#include "procs.cuh"
+#include "registry.h"
+
+namespace rw {
+namespace {
+struct Tag {
+  static constexpr int NG = gg_ttg::NG;
+  static constexpr int NEXT = gg_ttg::NEXT;
+  template <class R, int LB>
+  __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
+    return gg_ttg::hel_sum<R, LB>(X, K, lane);
+  }
+};
+using P = QcdProc<Tag>;
+}  // namespace
+
+void register_gg_ttg_fp64(std::vector<KernelEntry>& t) {
+  t.push_back({RW_GG_TTG, RW_FP64, 0, (const void*)&k_reweight<P, double, 0>});
+  t.push_back({RW_GG_TTG, RW_FP64, 1, (const void*)&k_reweight<P, double, 1>});
+  t.push_back({RW_GG_TTG, RW_FP64, 2, (const void*)&k_reweight<P, double, 2>});
+  t.push_back({RW_GG_TTG, RW_FP64, 3, (const void*)&k_reweight<P, double, 3>});
+}
+
+void static_gg_ttg(ProcStatic& s) {
+  s = {gg_ttg::NEXT, gg_ttg::NHEL, gg_ttg::K, gg_ttg::NDIAG, gg_ttg::CDEN, gg_ttg::IDENT, gg_ttg::NG,
+       gg_ttg::FLOPS_HEL_SUM, gg_ttg::NEXT};
+}
+
+}  // namespace rw

@@ -1,0 +1,25 @@
+// g g -> t tbar + n g kernel variants (gg_ttgg, fp32).
+#include "../../include/rwgt.h"
+#include "gen_qcd_gg_ttgg.cuh"
+#include "kernels.cuh"
+#include "procs.cuh"
+#include "registry.h"
+
+namespace rw {
+namespace {
+struct Tag {
+  static constexpr int NG = gg_ttgg::NG;
+  static constexpr int NEXT = gg_ttgg::NEXT;
+  template <class R, int LB>
+  __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
+    return gg_ttgg::hel_sum<R, LB>(X, K, lane);
+  }
+};
+using P = QcdProc<Tag>;
+}  // namespace
+
+void register_gg_ttgg_fp32(std::vector<KernelEntry>& t) {
+  t.push_back({RW_GG_TTGG, RW_FP32, 2, (const void*)&k_reweight<P, float, 2>});
+}
+
+}  // namespace rw

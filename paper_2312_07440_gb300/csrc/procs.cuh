@@ -1,0 +1,103 @@
+// Process adapters for the fused kernel: |M|^2 of one event for one
+// parameter point, helicity slices combined across the 2^LB lanes of a group.
+#pragma once
+#include "helas.cuh"
+#include "kernels.cuh"
+#include "qcd.cuh"
+
+namespace rw {
+
+// g g -> t tbar + n g.  Tag provides NG, NEXT and hel_sum<R, LB>().
+template <class Tag>
+struct QcdProc {
+  static constexpr int NG = Tag::NG;
+  static constexpr int NEXT = Tag::NEXT;
+
+  // Out of line: every evaluation runs the same instructions, so identical
+  // inputs give bitwise identical |M|^2 (r == 1 exactly for unchanged
+  // parameters), and the kernel keeps one copy of the amplitude code.
+  template <class R, int LB>
+  __device__ __noinline__ static double me(const double (&p)[NEXT][4], const PointDev& pt, int lane, unsigned gmask) {
+    QcdExt<R, NG> X;
+    QcdKin<R, NG> Kn;
+    qcd_setup<R, NG, NEXT>(p, pt.m_t, X, Kn);
+    double s = double(Tag::template hel_sum<R, LB>(X, Kn, lane));
+#pragma unroll
+    for (int o = 1; o < (1 << LB); o <<= 1) s += __shfl_xor_sync(gmask, s, o);
+    return s * pt.cscale;
+  }
+  __device__ __forceinline__ static bool reshuffle(const double (&p)[NEXT][4], double mt, double (&q)[NEXT][4]) {
+    return reshuffle_tops<NEXT>(p, mt, q);
+  }
+};
+
+// e-(p0) e+(p1) -> mu-(p2) mu+(p3) through s-channel photon and Z (unitary
+// gauge, fixed width), massless leptons:
+//   M = e^2 (jo.ji)/s + [zo.zi - (k.zo)(k.zi)/MZ^2] / (s - MZ^2 + i MZ WZ)
+// with ji = vbar(p1) gamma^mu u(p0), zi = vbar(p1) gamma^mu (gL PL + gR PR) u(p0)
+// and jo, zo the same for ubar(p2) ... v(p3); |M|^2 averaged over the 4
+// initial helicity states.
+struct EeMumu {
+  static constexpr int NEXT = 4;
+  static constexpr int NHEL = 16;
+
+  template <class R, int LB>
+  __device__ __noinline__ static double me(const double (&p)[NEXT][4], const PointDev& pt, int lane,
+                                           unsigned gmask) {
+    sp<R> u0[2], vb1[2], ub2[2], v3[2];
+    u_in<R>(p[0], 0.0, u0);
+    vbar_in<R>(p[1], 0.0, vb1);
+    ubar_out<R>(p[2], 0.0, ub2);
+    v_out<R>(p[3], 0.0, v3);
+    R k[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) k[m] = R(p[0][m] + p[1][m]);
+    const double sd = 2.0 * dot4(p[0], p[1]);
+    const R e2s = R(pt.e * pt.e / sd);
+    // 1/(s - MZ^2 + i MZ WZ)
+    const double dr = sd - pt.MZ * pt.MZ, di = pt.MZ * pt.WZ, dn = dr * dr + di * di;
+    const cx<R> dz = {R(dr / dn), R(-di / dn)};
+    const R imz2 = R(1.0 / (pt.MZ * pt.MZ));
+    const R gL = R(pt.gL), gR = R(pt.gR);
+    R acc = R(0);
+    constexpr int NLOC = NHEL >> LB;
+#pragma unroll 1
+    for (int hh = 0; hh < NLOC; ++hh) {
+      const int h = (lane << (4 - LB)) | hh;  // bits: 3 -> p0, 2 -> p1, 1 -> p2, 0 -> p3
+      const sp<R>& u = u0[(h >> 3) & 1];
+      const sp<R>& vb = vb1[(h >> 2) & 1];
+      const sp<R>& ub = ub2[(h >> 1) & 1];
+      const sp<R>& v = v3[h & 1];
+      const sp<R> uL = {{u.c[0], u.c[1], {R(0), R(0)}, {R(0), R(0)}}};
+      const sp<R> uR = {{{R(0), R(0)}, {R(0), R(0)}, u.c[2], u.c[3]}};
+      const sp<R> vL = {{v.c[0], v.c[1], {R(0), R(0)}, {R(0), R(0)}}};
+      const sp<R> vR = {{{R(0), R(0)}, {R(0), R(0)}, v.c[2], v.c[3]}};
+      const cv<R> jiL = fcur(vb, uL), jiR = fcur(vb, uR);
+      const cv<R> joL = fcur(ub, vL), joR = fcur(ub, vR);
+      cv<R> ji, jo, zi, zo;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        ji.c[m] = jiL.c[m] + jiR.c[m];
+        jo.c[m] = joL.c[m] + joR.c[m];
+        zi.c[m] = gL * jiL.c[m] + gR * jiR.c[m];
+        zo.c[m] = gL * joL.c[m] + gR * joR.c[m];
+      }
+      const cx<R> zz = dot(zo, zi) - imz2 * (dotr(k, zo) * dotr(k, zi));
+      const cx<R> M = e2s * dot(jo, ji) + zz * dz;
+      acc += M.r * M.r + M.i * M.i;
+    }
+    double s = double(acc);
+#pragma unroll
+    for (int o = 1; o < (1 << LB); o <<= 1) s += __shfl_xor_sync(gmask, s, o);
+    return 0.25 * s;
+  }
+  __device__ __forceinline__ static bool reshuffle(const double (&p)[NEXT][4], double, double (&q)[NEXT][4]) {
+#pragma unroll
+    for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) q[i][m] = p[i][m];
+    return true;
+  }
+};
+
+}  // namespace rw

@@ -1,0 +1,138 @@
+// Per-event set-up for g g -> t tbar + n g: external wavefunctions of both
+// helicities and the propagator invariants, formed in FP64 from the FP64
+// momenta and then cast to the working precision R (so that FP32 mode never
+// forms p^2 - m^2 by cancellation in single precision).
+#pragma once
+#include "helas.cuh"
+
+namespace rw {
+
+template <class R, int NG>
+struct QcdExt {
+  cv<R> eps[NG][2];  // gluon polarisations (conjugated for outgoing gluons)
+  sp<R> ub[2];       // top: ubar(p3, lambda)
+  sp<R> v[2];        // antitop: v(p4, lambda)
+};
+
+template <class R, int NG>
+struct QcdKin {
+  R P[1 << NG][4];   // summed incoming momentum of each gluon subset
+  R cg[1 << NG];     // -1/K^2  (3-gluon vertex + gluon propagator)
+  R c4[1 << NG];     // +1/K^2  (4-gluon vertex + gluon propagator)
+  R qc[1 << NG][4];  // c (K - p4), c = -1/((K - p4)^2 - m^2)  (top propagator)
+  R mc[1 << NG];     // c m
+};
+
+// particle index of gluon g on the top line: 0, 1 incoming, then 4, 5, ...
+__host__ __device__ constexpr int gluon_particle(int g) { return g < 2 ? g : g + 2; }
+
+__device__ __forceinline__ double dot4(const double (&a)[4], const double (&b)[4]) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+
+template <class R, int NG, int NEXT>
+__device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, QcdExt<R, NG>& X,
+                                          QcdKin<R, NG>& Kn) {
+  static_assert(NEXT == NG + 2, "t tbar + NG gluons");
+  double k[NG][4];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const int ip = gluon_particle(g);
+    const double s = ip < 2 ? 1.0 : -1.0;
+#pragma unroll
+    for (int m4 = 0; m4 < 4; ++m4) k[g][m4] = s * p[ip][m4];
+    polvec<R>(p[ip], ip >= 2, X.eps[g]);
+  }
+  ubar_out<R>(p[2], m, X.ub);
+  v_out<R>(p[3], m, X.v);
+  // pairwise k_i.k_j (the gluons are massless: k_i^2 = 0 exactly)
+  double d[NG][NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i)
+#pragma unroll
+    for (int j = i + 1; j < NG; ++j) d[i][j] = dot4(k[i], k[j]);
+  constexpr int FULL = (1 << NG) - 1;
+#pragma unroll
+  for (int msk = 1; msk <= FULL; ++msk) {
+    double P[4] = {0.0, 0.0, 0.0, 0.0};
+    double K2 = 0.0;
+    int cnt = 0;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      if (!((msk >> i) & 1)) continue;
+      ++cnt;
+#pragma unroll
+      for (int m4 = 0; m4 < 4; ++m4) P[m4] += k[i][m4];
+#pragma unroll
+      for (int j = i + 1; j < NG; ++j)
+        if ((msk >> j) & 1) K2 += 2.0 * d[i][j];
+    }
+#pragma unroll
+    for (int m4 = 0; m4 < 4; ++m4) Kn.P[msk][m4] = R(P[m4]);
+    if (cnt >= 2) {
+      const double inv = 1.0 / K2;
+      Kn.cg[msk] = R(-inv);
+      Kn.c4[msk] = R(inv);
+    } else {
+      Kn.cg[msk] = R(0);
+      Kn.c4[msk] = R(0);
+    }
+    if (msk != FULL) {
+      // (K - p4)^2 - m^2 = K^2 - 2 K.p4  (p4^2 = m^2)
+      const double den = K2 - 2.0 * dot4(P, p[3]);
+      const double c = -1.0 / den;
+#pragma unroll
+      for (int m4 = 0; m4 < 4; ++m4) Kn.qc[msk][m4] = R(c * (P[m4] - p[3][m4]));
+      Kn.mc[msk] = R(c * m);
+    } else {
+#pragma unroll
+      for (int m4 = 0; m4 < 4; ++m4) Kn.qc[msk][m4] = R(0);
+      Kn.mc[msk] = R(0);
+    }
+  }
+}
+
+// Move the outgoing particles (2..NEXT-1) onto the mass shells m_t (tops),
+// 0 (gluons) at fixed partonic energy: p_i -> xi p_i (3-momenta) with
+// sum_i sqrt(m_i^2 + xi^2 |p_i|^2) = sum_i E_i, Newton's method from xi = 1.
+// Returns false when the new masses do not fit (sum m_i >= E).
+template <int NEXT>
+__device__ __forceinline__ bool reshuffle_tops(const double (&p)[NEXT][4], double mt, double (&q)[NEXT][4]) {
+  double etot = 0.0, p2[NEXT];
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+    etot += p[i][0];
+    p2[i] = p[i][1] * p[i][1] + p[i][2] * p[i][2] + p[i][3] * p[i][3];
+  }
+#pragma unroll
+  for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+    for (int m4 = 0; m4 < 4; ++m4) q[i][m4] = p[i][m4];
+  if (!(2.0 * mt < etot)) return false;
+  const double mt2 = mt * mt;
+  double xi = 1.0;
+  for (int it = 0; it < 100; ++it) {
+    double f = -etot, df = 0.0;
+#pragma unroll
+    for (int i = 2; i < NEXT; ++i) {
+      const double m2 = i < 4 ? mt2 : 0.0;
+      const double e = sqrt(m2 + xi * xi * p2[i]);
+      f += e;
+      df += xi * p2[i] / e;
+    }
+    double step = f / df;
+    if (xi - step <= 0.0) step = 0.5 * xi;
+    xi -= step;
+    if (fabs(step) <= 1e-15 * xi) break;
+  }
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+    const double m2 = i < 4 ? mt2 : 0.0;
+#pragma unroll
+    for (int m4 = 1; m4 < 4; ++m4) q[i][m4] = xi * p[i][m4];
+    q[i][0] = sqrt(m2 + xi * xi * p2[i]);
+  }
+  return true;
+}
+
+}  // namespace rw

@@ -1,0 +1,31 @@
+// Internal: table of compiled kernel variants, filled by the per-process
+// translation units (proc_*.cu) and looked up by the C ABI (rw_abi.cu).
+#pragma once
+#include <vector>
+
+namespace rw {
+
+struct KernelEntry {
+  int process;       // RW_* process id
+  int mode;          // RW_FP64 / RW_FP32
+  int lane_bits;     // helicity slices per event = 2^lane_bits
+  const void* func;  // __global__ k_reweight<...>(RwArgs)
+};
+
+struct ProcStatic {
+  int n_external, n_helicities, n_colour_flows, n_diagrams, colour_den, n_ident, n_gluons;
+  long long flops_hel_sum;
+  int max_lane_bits;  // helicity loop levels that can be mapped to lanes
+};
+
+void register_ee_mumu(std::vector<KernelEntry>& t, ProcStatic& s);
+#define RW_DECLARE_QCD(name)                              \
+  void register_##name##_fp64(std::vector<KernelEntry>& t); \
+  void register_##name##_fp32(std::vector<KernelEntry>& t); \
+  void static_##name(ProcStatic& s);
+RW_DECLARE_QCD(gg_tt)
+RW_DECLARE_QCD(gg_ttg)
+RW_DECLARE_QCD(gg_ttgg)
+#undef RW_DECLARE_QCD
+
+}  // namespace rw

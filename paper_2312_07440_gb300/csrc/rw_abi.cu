@@ -1,0 +1,487 @@
+// C ABI of librwgt.so (declared in include/rwgt.h): context, argument
+// validation, parameter derivation and kernel launches.  Every step of the
+// per-event path runs in the kernels of proc_*.cu; this file only prepares
+// the per-point constants (O(1) per parameter point) and launches.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/rwgt.h"
+#include "kernels.cuh"
+#include "registry.h"
+
+using rw::KernelEntry;
+using rw::PointDev;
+using rw::ProcStatic;
+using rw::RwArgs;
+
+namespace {
+
+constexpr int GRID_CAP = 8192;
+constexpr int NPROC = 4;
+
+struct Registry {
+  std::vector<KernelEntry> kernels;
+  ProcStatic st[NPROC];
+  Registry() {
+    rw::register_ee_mumu(kernels, st[RW_EE_MUMU]);
+    rw::register_gg_tt_fp64(kernels);
+    rw::register_gg_tt_fp32(kernels);
+    rw::static_gg_tt(st[RW_GG_TT]);
+    rw::register_gg_ttg_fp64(kernels);
+    rw::register_gg_ttg_fp32(kernels);
+    rw::static_gg_ttg(st[RW_GG_TTG]);
+    rw::register_gg_ttgg_fp64(kernels);
+    rw::register_gg_ttgg_fp32(kernels);
+    rw::static_gg_ttgg(st[RW_GG_TTGG]);
+  }
+  const KernelEntry* find(int process, int mode, int lb) const {
+    for (const auto& k : kernels)
+      if (k.process == process && k.mode == mode && k.lane_bits == lb) return &k;
+    return nullptr;
+  }
+};
+
+const Registry& registry() {
+  static Registry r;
+  return r;
+}
+
+// default lanes per event (2^bits) per process and mode, before tuning
+int default_lane_bits(int process, int mode) {
+  switch (process) {
+    case RW_EE_MUMU: return 2;
+    case RW_GG_TT: return mode == RW_FP64 ? 0 : 1;
+    case RW_GG_TTG: return 1;
+    case RW_GG_TTGG: return 2;
+  }
+  return 0;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct rw_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  int process = -1, mode = -1;
+  bool have_p0 = false;
+  rw_params p0{};
+  std::vector<rw_params> pts;
+  const double* mom = nullptr;
+  const double* w = nullptr;
+  int64_t E = 0;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int lane_bits = -1, block = 0;
+  std::string err;
+  double* h_stage = nullptr;  // pinned [RW_MAX_POINTS + 2]
+  std::map<std::tuple<const void*, int, size_t>, int> occ;
+};
+
+namespace {
+
+int fail(rw_ctx* c, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(rw_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+int cuda_fail(rw_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, RW_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+bool finite_params(const rw_params& p) {
+  const double v[8] = {p.alpha_s, p.m_t, p.w_t, p.yt_scale, p.alpha_em_inv, p.G_F, p.m_Z, p.w_Z};
+  for (double x : v)
+    if (!isfinite(x)) return false;
+  return true;
+}
+
+int check_params(rw_ctx* c, const rw_params& p) {
+  if (!finite_params(p)) return fail(c, RW_ERR_PARAM, "parameters must be finite");
+  if (c->process == RW_EE_MUMU) {
+    if (!(p.alpha_em_inv > 0 && p.G_F > 0 && p.m_Z > 0 && p.w_Z >= 0))
+      return fail(c, RW_ERR_PARAM, "need alpha_em_inv > 0, G_F > 0, m_Z > 0, w_Z >= 0");
+    const double a = 1.0 / p.alpha_em_inv;
+    const double disc = 0.25 * pow(p.m_Z, 4) - M_PI * a * p.m_Z * p.m_Z / (sqrt(2.0) * p.G_F);
+    if (!(disc >= 0)) return fail(c, RW_ERR_PARAM, "no real M_W for these (alpha, G_F, M_Z)");
+  } else {
+    if (!(p.alpha_s > 0)) return fail(c, RW_ERR_PARAM, "alpha_s must be > 0");
+    if (!(p.m_t > 0)) return fail(c, RW_ERR_PARAM, "m_t must be > 0");
+    if (p.w_t != 0.0) return fail(c, RW_ERR_PARAM, "w_t must be 0 (all top propagators are off shell)");
+  }
+  return RW_OK;
+}
+
+// per-evaluation constants (derived couplings), computed once per point
+PointDev make_point(const rw_ctx* c, const rw_params& p, bool reshuffle) {
+  PointDev d{};
+  const ProcStatic& s = registry().st[c->process];
+  d.m_t = p.m_t;
+  d.reshuffle = reshuffle ? 1 : 0;
+  if (c->process == RW_EE_MUMU) {
+    const double alpha = 1.0 / p.alpha_em_inv, MZ = p.m_Z;
+    const double MW2 = 0.5 * MZ * MZ + sqrt(0.25 * MZ * MZ * MZ * MZ - M_PI * alpha * MZ * MZ / (sqrt(2.0) * p.G_F));
+    const double sw2 = 1.0 - MW2 / (MZ * MZ), sw = sqrt(sw2), cw = sqrt(1.0 - sw2);
+    d.e = sqrt(4.0 * M_PI * alpha);
+    // lepton: T3 = -1/2, Q = -1
+    d.gL = d.e * (-0.5 + sw2) / (sw * cw);
+    d.gR = d.e * sw2 / (sw * cw);
+    d.MZ = MZ;
+    d.WZ = p.w_Z;
+    d.cscale = 1.0;
+  } else {
+    double ident_fact = 1.0;
+    for (int i = 2; i <= s.n_ident; ++i) ident_fact *= i;
+    const double g2 = 4.0 * M_PI * p.alpha_s;
+    double gpow = 1.0;
+    for (int i = 0; i < s.n_gluons; ++i) gpow *= g2;
+    d.cscale = gpow / (4.0 * 64.0 * ident_fact * s.colour_den);
+  }
+  return d;
+}
+
+size_t ws_core_bytes(int P) { return 256 + align256(8 * (size_t)(P + 2)) + (size_t)GRID_CAP * (P + 1) * 16; }
+
+int check_dev_ptr(rw_ctx* c, const void* p, const char* name) {
+  if (!p) return fail(c, RW_ERR_NULL, "%s is NULL", name);
+  if (reinterpret_cast<uintptr_t>(p) % 8) return fail(c, RW_ERR_ALIGN, "%s not 8-byte aligned", name);
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(c, e, name);
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(c, RW_ERR_ARG, "%s is not device memory", name);
+  if (at.type == cudaMemoryTypeDevice && at.device != c->device)
+    return fail(c, RW_ERR_ARG, "%s lives on device %d, context on %d", name, at.device, c->device);
+  return RW_OK;
+}
+
+int ready(rw_ctx* c, bool need_events) {
+  if (!c) return RW_ERR_NULL;
+  if (c->process < 0) return fail(c, RW_ERR_STATE, "no process set");
+  if (!c->have_p0) return fail(c, RW_ERR_STATE, "no original parameters set");
+  if (need_events && !c->mom) return fail(c, RW_ERR_STATE, "no events loaded");
+  return RW_OK;
+}
+
+// launch the fused kernel; `points` empty => single evaluation mode
+int launch(rw_ctx* c, RwArgs& a) {
+  const int lb = c->lane_bits >= 0 ? c->lane_bits : default_lane_bits(c->process, c->mode);
+  const KernelEntry* k = registry().find(c->process, c->mode, lb);
+  if (!k) return fail(c, RW_ERR_MODE, "no kernel for process %d mode %d lane_bits %d", c->process, c->mode, lb);
+  const int block = c->block > 0 ? c->block : 128;
+  const int lanes = 1 << lb;
+  const size_t smem = (size_t)(block / 32) * (a.P + 1) * sizeof(double2);
+  auto key = std::make_tuple(k->func, block, smem);
+  auto it = c->occ.find(key);
+  int per_sm;
+  if (it == c->occ.end()) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, block, smem);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) per_sm = 1;
+    c->occ[key] = per_sm;
+  } else {
+    per_sm = it->second;
+  }
+  const long long need = (a.E * lanes + block - 1) / block;
+  const int grid = (int)std::max(1LL, std::min<long long>({(long long)GRID_CAP, (long long)per_sm * c->sm_count, need}));
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchKernel(k->func, dim3(grid), dim3(block), args, smem, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+  return RW_OK;
+}
+
+void fill_ws(rw_ctx* c, RwArgs& a, int P) {
+  char* b = c->ws;
+  a.ticket = reinterpret_cast<unsigned int*>(b);
+  a.nbad_count = reinterpret_cast<unsigned long long*>(b + 8);
+  a.sigma = reinterpret_cast<double*>(b + 64);
+  a.nbad_out = reinterpret_cast<unsigned long long*>(b + 64 + 8 * (size_t)(P + 1));
+  a.block_part = reinterpret_cast<double2*>(b + 256 + align256(8 * (size_t)(P + 2)));
+}
+
+}  // namespace
+
+extern "C" {
+
+int rw_create(rw_ctx** out, int device, void* stream) {
+  if (!out) return RW_ERR_NULL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return RW_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return RW_ERR_ARG;
+  DeviceGuard g(device);
+  if (!g.ok) return RW_ERR_CUDA;
+  rw_ctx* c = new rw_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMallocHost(&c->h_stage, sizeof(double) * (RW_MAX_POINTS + 4)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return RW_ERR_CUDA;
+  }
+  (void)registry();
+  *out = c;
+  return RW_OK;
+}
+
+int rw_destroy(rw_ctx* c) {
+  if (!c) return RW_ERR_NULL;
+  DeviceGuard g(c->device);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  delete c;
+  return RW_OK;
+}
+
+const char* rw_last_error(const rw_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int rw_process_info_get(int process, rw_process_info* out) {
+  if (!out) return RW_ERR_NULL;
+  if (process < 0 || process >= NPROC) return RW_ERR_ARG;
+  const ProcStatic& s = registry().st[process];
+  out->n_external = s.n_external;
+  out->n_helicities = s.n_helicities;
+  out->n_colour_flows = s.n_colour_flows;
+  out->n_diagrams = s.n_diagrams;
+  out->colour_den = s.colour_den;
+  out->flops_hel_sum = s.flops_hel_sum;
+  return RW_OK;
+}
+
+int rw_set_process(rw_ctx* c, int process, int mode) {
+  if (!c) return RW_ERR_NULL;
+  if (process < 0 || process >= NPROC) return fail(c, RW_ERR_ARG, "unknown process %d", process);
+  if (mode != RW_FP64 && mode != RW_FP32) return fail(c, RW_ERR_MODE, "unknown mode %d", mode);
+  bool any = false;
+  for (const auto& k : registry().kernels) any |= k.process == process && k.mode == mode;
+  if (!any) return fail(c, RW_ERR_MODE, "process %d has no kernels in mode %d", process, mode);
+  c->process = process;
+  c->mode = mode;
+  c->have_p0 = false;
+  c->pts.clear();
+  c->mom = nullptr;
+  c->w = nullptr;
+  c->E = 0;
+  return RW_OK;
+}
+
+int rw_set_params(rw_ctx* c, const rw_params* p) {
+  if (!c) return RW_ERR_NULL;
+  if (!p) return fail(c, RW_ERR_NULL, "params is NULL");
+  if (c->process < 0) return fail(c, RW_ERR_STATE, "set the process first");
+  int rc = check_params(c, *p);
+  if (rc) return rc;
+  c->p0 = *p;
+  c->have_p0 = true;
+  return RW_OK;
+}
+
+int rw_set_reweight_points(rw_ctx* c, const rw_params* pts, int P) {
+  if (!c) return RW_ERR_NULL;
+  if (!pts) return fail(c, RW_ERR_NULL, "points is NULL");
+  if (c->process < 0) return fail(c, RW_ERR_STATE, "set the process first");
+  if (P < 1 || P > RW_MAX_POINTS) return fail(c, RW_ERR_ARG, "need 1 <= P <= %d, got %d", RW_MAX_POINTS, P);
+  for (int j = 0; j < P; ++j) {
+    int rc = check_params(c, pts[j]);
+    if (rc) return fail(c, rc, "point %d: %s", j, c->err.c_str());
+  }
+  if (c->mom && ws_core_bytes(P) > c->ws_bytes)
+    return fail(c, RW_ERR_WORKSPACE, "attached workspace too small for %d points", P);
+  c->pts.assign(pts, pts + P);
+  return RW_OK;
+}
+
+int rw_set_tuning(rw_ctx* c, int lane_bits, int block) {
+  if (!c) return RW_ERR_NULL;
+  if (block != 0 && (block < 32 || block > 256 || block % 32))
+    return fail(c, RW_ERR_ARG, "block must be a multiple of 32 in [32, 256]");
+  if (lane_bits >= 0 && c->process >= 0) {
+    if (!registry().find(c->process, c->mode, lane_bits))
+      return fail(c, RW_ERR_MODE, "lane_bits %d not compiled for this process/mode", lane_bits);
+    if ((1 << lane_bits) > (block ? block : 128)) return fail(c, RW_ERR_ARG, "more lanes than threads");
+  }
+  c->lane_bits = lane_bits;
+  c->block = block;
+  return RW_OK;
+}
+
+size_t rw_workspace_bytes(const rw_ctx* c, int64_t) {
+  if (!c) return 0;
+  return ws_core_bytes(std::max<int>(1, (int)c->pts.size()));
+}
+
+int rw_load_events(rw_ctx* c, const double* d_mom, const double* d_w, int64_t E, void* d_ws, size_t ws_bytes) {
+  if (!c) return RW_ERR_NULL;
+  if (c->process < 0) return fail(c, RW_ERR_STATE, "set the process first");
+  if (E <= 0) return fail(c, RW_ERR_ARG, "n_events must be > 0, got %lld", (long long)E);
+  if (E > (int64_t(1) << 40)) return fail(c, RW_ERR_ARG, "n_events too large");
+  DeviceGuard g(c->device);
+  int rc;
+  if ((rc = check_dev_ptr(c, d_mom, "momenta"))) return rc;
+  if ((rc = check_dev_ptr(c, d_w, "weights"))) return rc;
+  if ((rc = check_dev_ptr(c, d_ws, "workspace"))) return rc;
+  if (reinterpret_cast<uintptr_t>(d_ws) % 16) return fail(c, RW_ERR_ALIGN, "workspace not 16-byte aligned");
+  if (ws_bytes < rw_workspace_bytes(c, E))
+    return fail(c, RW_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, rw_workspace_bytes(c, E));
+  cudaError_t e = cudaMemsetAsync(d_ws, 0, 256, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+  c->mom = d_mom;
+  c->w = d_w;
+  c->E = E;
+  c->ws = static_cast<char*>(d_ws);
+  c->ws_bytes = ws_bytes;
+  return RW_OK;
+}
+
+int rw_eval_me(rw_ctx* c, int point, double* d_me) {
+  int rc = ready(c, true);
+  if (rc) return rc;
+  if (point < -1 || point >= (int)c->pts.size()) return fail(c, RW_ERR_ARG, "point %d out of range", point);
+  DeviceGuard g(c->device);
+  if ((rc = check_dev_ptr(c, d_me, "me_out"))) return rc;
+  RwArgs a{};
+  a.mom = c->mom;
+  a.w = c->w;
+  a.E = c->E;
+  a.me0 = d_me;
+  a.P = 0;
+  a.me_only = 1;
+  if (point < 0) {
+    a.pt[0] = make_point(c, c->p0, false);
+  } else {
+    const bool moved = c->process != RW_EE_MUMU && c->pts[point].m_t != c->p0.m_t;
+    a.pt[0] = make_point(c, c->pts[point], moved);
+  }
+  fill_ws(c, a, 0);
+  return launch(c, a);
+}
+
+int rw_reweight_async(rw_ctx* c, double* d_wnew, double* d_ratio, double* d_me0, double* d_me_pts) {
+  int rc = ready(c, true);
+  if (rc) return rc;
+  if (c->pts.empty()) return fail(c, RW_ERR_STATE, "no reweight points set");
+  DeviceGuard g(c->device);
+  if (d_wnew && (rc = check_dev_ptr(c, d_wnew, "wnew"))) return rc;
+  if (d_ratio && (rc = check_dev_ptr(c, d_ratio, "ratio"))) return rc;
+  if (d_me0 && (rc = check_dev_ptr(c, d_me0, "me0"))) return rc;
+  if (d_me_pts && (rc = check_dev_ptr(c, d_me_pts, "me_pts"))) return rc;
+  const int P = (int)c->pts.size();
+  if (ws_core_bytes(P) > c->ws_bytes) return fail(c, RW_ERR_WORKSPACE, "workspace too small for %d points", P);
+  RwArgs a{};
+  a.mom = c->mom;
+  a.w = c->w;
+  a.E = c->E;
+  a.me0 = d_me0;
+  a.me_pts = d_me_pts;
+  a.ratio = d_ratio;
+  a.wnew = d_wnew;
+  a.P = P;
+  a.me_only = 0;
+  a.pt[0] = make_point(c, c->p0, false);
+  for (int j = 0; j < P; ++j) {
+    const bool moved = c->process != RW_EE_MUMU && c->pts[j].m_t != c->p0.m_t;
+    a.pt[1 + j] = make_point(c, c->pts[j], moved);
+  }
+  fill_ws(c, a, P);
+  return launch(c, a);
+}
+
+int rw_get_results(rw_ctx* c, double* h_sigma, double* h_sigma_orig, int64_t* h_n_bad) {
+  int rc = ready(c, true);
+  if (rc) return rc;
+  if (c->pts.empty()) return fail(c, RW_ERR_STATE, "no reweight points set");
+  DeviceGuard g(c->device);
+  const int P = (int)c->pts.size();
+  cudaError_t e = cudaMemcpyAsync(c->h_stage, c->ws + 64, 8 * (size_t)(P + 2), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  if (h_sigma) memcpy(h_sigma, c->h_stage, 8 * (size_t)P);
+  if (h_sigma_orig) *h_sigma_orig = c->h_stage[P];
+  unsigned long long nb;
+  memcpy(&nb, c->h_stage + P + 1, 8);
+  if (h_n_bad) *h_n_bad = (int64_t)nb;
+  return nb ? RW_WARN_BAD_EVENTS : RW_OK;
+}
+
+int rw_reweight(rw_ctx* c, double* d_wnew, double* d_ratio, double* h_sigma, double* h_sigma_orig,
+                int64_t* h_n_bad) {
+  int rc = rw_reweight_async(c, d_wnew, d_ratio, nullptr, nullptr);
+  if (rc < 0) return rc;
+  return rw_get_results(c, h_sigma, h_sigma_orig, h_n_bad);
+}
+
+size_t rw_workspace_bytes_host(const rw_ctx* c, int64_t E) {
+  if (!c || c->process < 0 || E <= 0) return 0;
+  const int N = registry().st[c->process].n_external;
+  const size_t P = std::max<size_t>(1, c->pts.size());
+  return ws_core_bytes((int)P) + align256(8 * 4 * (size_t)N * E) + align256(8 * (size_t)E) + align256(8 * P * E);
+}
+
+int rw_reweight_host(rw_ctx* c, const double* h_mom, const double* h_w, int64_t E, double* h_wnew, double* h_sigma,
+                     double* h_sigma_orig, int64_t* h_n_bad, void* d_ws, size_t ws_bytes) {
+  if (!c) return RW_ERR_NULL;
+  if (!h_mom || !h_w) return fail(c, RW_ERR_NULL, "host momenta/weights are NULL");
+  if (c->process < 0 || !c->have_p0 || c->pts.empty()) return fail(c, RW_ERR_STATE, "process/params/points unset");
+  if (E <= 0) return fail(c, RW_ERR_ARG, "n_events must be > 0");
+  if (ws_bytes < rw_workspace_bytes_host(c, E)) return fail(c, RW_ERR_WORKSPACE, "workspace too small");
+  DeviceGuard g(c->device);
+  const int N = registry().st[c->process].n_external;
+  const int P = (int)c->pts.size();
+  char* base = static_cast<char*>(d_ws);
+  const size_t core = ws_core_bytes(P);
+  double* d_mom = reinterpret_cast<double*>(base + core);
+  double* d_w = reinterpret_cast<double*>(base + core + align256(8 * 4 * (size_t)N * E));
+  double* d_wnew = reinterpret_cast<double*>(reinterpret_cast<char*>(d_w) + align256(8 * (size_t)E));
+  cudaError_t e = cudaMemcpyAsync(d_mom, h_mom, 8 * 4 * (size_t)N * E, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, h_w, 8 * (size_t)E, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  int rc = rw_load_events(c, d_mom, d_w, E, d_ws, ws_bytes);
+  if (rc) return rc;
+  rc = rw_reweight_async(c, h_wnew ? d_wnew : nullptr, nullptr, nullptr, nullptr);
+  if (rc < 0) return rc;
+  if (h_wnew) {
+    e = cudaMemcpyAsync(h_wnew, d_wnew, 8 * (size_t)P * E, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  }
+  return rw_get_results(c, h_sigma, h_sigma_orig, h_n_bad);
+}
+
+}  // extern "C"

@@ -1,0 +1,364 @@
+"""Build-time generator of the per-process amplitude code for g g -> t tbar + n g.
+
+The paper's amplitudes are generated per process by a meta-program that
+emits HELAS-style call chains (Sec. 3.1); this is the library's own, much
+smaller generator for the processes it ships.  For n gluons on the top line it
+
+  * counts the tree-level Feynman diagrams (3, 16, 123 for n = 2, 3, 4) from
+    the 3-gluon, 4-gluon and quark-gluon vertices;
+  * derives the colour matrix C_{sigma tau} = sum_colours
+    (t^sigma)^*_{ij} (t^tau)_{ij} of the colour-ordered basis
+    (t^{a_sigma1} ... t^{a_sigman})_{ij} exactly, by Fierz reduction of
+    SU(N) traces in rational arithmetic at N = 3;
+  * emits a CUDA device function that evaluates every colour-ordered
+    amplitude as chains of vertex and propagator calls -- off-shell gluon
+    currents (3- and 4-gluon vertices), off-shell top currents (quark-gluon
+    vertex + top propagator) and their contraction -- sharing every
+    sub-current between the n! orderings (the sum over all Feynman diagrams,
+    organised so that no diagram's chain is recomputed), with the helicity
+    sum written as nested loops over the external helicities and every
+    current computed at the outermost loop level on which it depends;
+  * counts the floating-point operations of the emitted code.
+
+Couplings are stripped (g = 1): every partial amplitude carries exactly g^n,
+restored as (4 pi alpha_s)^n on |M|^2.
+
+Run ``python -m paper_2312_07440_gb300.gen.qcd_gen`` to regenerate
+``csrc/gen_qcd_*.cuh`` (the generated headers are committed).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+import os
+from fractions import Fraction
+
+# ---------------------------------------------------------------------------
+# colour algebra: Fierz reduction of traces of SU(N) generators
+# ---------------------------------------------------------------------------
+NC = 3
+
+
+def _reduce(coef, traces):
+    """Fully contract a product of traces of generator words.
+
+    traces: tuple of tuples of adjoint labels; each label occurs exactly twice
+    over the whole product.  Uses, with T = t^a summed over a,
+      Tr(X t^a Y t^a) = 1/2 Tr(X) Tr(Y) - 1/(2N) Tr(X Y)
+      Tr(X t^a) Tr(Y t^a) = 1/2 Tr(X Y) - 1/(2N) Tr(X) Tr(Y)
+    and Tr(1) = N.  Returns an exact Fraction.
+    """
+    # find a label
+    for ti, tr in enumerate(traces):
+        if tr:
+            lab = tr[0]
+            break
+    else:
+        return coef * Fraction(NC) ** len(traces)
+    pos = [(ti, k) for ti, tr in enumerate(traces) for k, x in enumerate(tr) if x == lab]
+    assert len(pos) == 2
+    (t1, k1), (t2, k2) = pos
+    rest = [tr for ti, tr in enumerate(traces) if ti not in (t1, t2)]
+    half = Fraction(1, 2)
+    inv2n = Fraction(1, 2 * NC)
+    if t1 == t2:
+        tr = traces[t1]
+        # rotate so that the first occurrence is at position 0: Tr(t^a Y t^a X)
+        rot = tr[k1:] + tr[:k1]
+        j = rot.index(lab, 1)
+        Y, X = rot[1:j], rot[j + 1:]
+        return (_reduce(coef * half, tuple(rest) + (X, Y)) - _reduce(coef * inv2n, tuple(rest) + (X + Y,)))
+    a, b = traces[t1], traces[t2]
+    X = a[k1 + 1:] + a[:k1]  # Tr(t^a X) with X cyclically after a
+    Y = b[k2 + 1:] + b[:k2]
+    return (_reduce(coef * half, tuple(rest) + (X + Y,)) - _reduce(coef * inv2n, tuple(rest) + (X, Y)))
+
+
+def orderings(n):
+    return list(itertools.permutations(range(n)))
+
+
+def colour_matrix(n):
+    """C[s][t] = Tr(t^{sigma_n} ... t^{sigma_1} t^{tau_1} ... t^{tau_n}) summed
+    over the adjoint labels, as exact Fractions (lexicographic orderings)."""
+    perms = orderings(n)
+    C = []
+    for s in perms:
+        row = []
+        for t in perms:
+            word = tuple(reversed(s)) + tuple(t)
+            row.append(_reduce(Fraction(1), (word,)))
+        C.append(row)
+    return C
+
+
+def colour_matrix_int(n):
+    """(integer matrix, common denominator) with C = Cint / den."""
+    C = colour_matrix(n)
+    den = 1
+    for row in C:
+        for x in row:
+            den = den * x.denominator // math.gcd(den, x.denominator)
+    return [[int(x * den) for x in row] for row in C], den
+
+
+# ---------------------------------------------------------------------------
+# diagram counting (unordered, colour-dressed Feynman graphs)
+# ---------------------------------------------------------------------------
+def _set_partitions(items, k):
+    """Unordered partitions of the tuple ``items`` into k nonempty blocks."""
+    items = list(items)
+    if k == 1:
+        yield (tuple(items),)
+        return
+    first, rest = items[0], items[1:]
+    # block containing `first`
+    for r in range(0, len(rest) + 1):
+        for others in itertools.combinations(rest, r):
+            block = (first,) + others
+            remaining = tuple(x for x in rest if x not in others)
+            if len(remaining) < k - 1:
+                continue
+            for sub in _set_partitions(remaining, k - 1):
+                yield (block,) + sub
+
+
+def diagram_count(n):
+    """Number of tree diagrams for t tbar + n gluons (3g, 4g, qqg vertices)."""
+    from functools import lru_cache
+
+    @lru_cache(None)
+    def dg(S):
+        if len(S) == 1:
+            return 1
+        tot = 0
+        for a, b in _set_partitions(S, 2):
+            tot += dg(a) * dg(b)
+        if len(S) >= 3:
+            for a, b, c in _set_partitions(S, 3):
+                tot += dg(a) * dg(b) * dg(c)
+        return tot
+
+    @lru_cache(None)
+    def df(S):
+        if not S:
+            return 1
+        tot = 0
+        for r in range(1, len(S) + 1):
+            for sub in itertools.combinations(S, r):
+                rest = tuple(x for x in S if x not in sub)
+                tot += dg(sub) * df(rest)
+        return tot
+
+    return df(tuple(range(n)))
+
+
+# ---------------------------------------------------------------------------
+# code emission
+# ---------------------------------------------------------------------------
+# floating-point operations of the device primitives in helas.cuh (real
+# operations; an FMA counts 2).  Kept in step with helas.cuh by hand.
+FLOPS = {
+    "vvv": 156,      # 3-gluon vertex with folded propagator factor
+    "vvvv_acc": 193, # 4-gluon vertex accumulated
+    "slash": 64,     # Jslash psi
+    "sp_add": 8,     # spinor accumulate
+    "fprop": 58,     # c (qslash + m) chi
+    "fcur": 72,      # ubar gamma^mu psi
+    "dot": 30,       # complex Minkowski product
+    "cadd": 2,
+}
+
+
+def seq_name(prefix, seq):
+    return prefix + "_".join(str(x) for x in seq) if seq else prefix + "E"
+
+
+def mask(seq):
+    m = 0
+    for x in seq:
+        m |= 1 << x
+    return m
+
+
+class Emitter:
+    def __init__(self, n):
+        self.n = n
+        self.flops_per_level = [0] * (n + 2)  # flops emitted at each loop level
+
+    def count(self, level, key, times=1):
+        self.flops_per_level[level] += FLOPS[key] * times
+
+
+def emit_process(name, n, outgoing_gluons, n_identical):
+    """Emit the helicity-summed, couplings-stripped colour sum for t tbar + n g.
+
+    Loop levels 0..n-1: gluon helicities; level n: antitop; level n+1: top.
+    The returned device function sums over the helicities of one lane; the
+    outermost LB levels take their helicity bits from the lane index.
+    """
+    em = Emitter(n)
+    perms = orderings(n)
+    K = len(perms)
+    Cint, den = colour_matrix_int(n)
+    lines = []
+    w = lines.append
+    w(f"// ---- generated by gen/qcd_gen.py: {name} (g g -> t tbar + {n - 2} g), do not edit ----")
+    w(f"// {diagram_count(n)} Feynman diagrams, {K} colour orderings, {2 ** (n + 2)} helicities.")
+    w(f"// colour matrix C = Cint / {den}")
+    w("#pragma once")
+    w('#include "qcd.cuh"')
+    w("")
+    w(f"namespace rw {{ namespace {name} {{")
+    w(f"constexpr int NG = {n};")
+    w(f"constexpr int NEXT = {n + 2};")
+    w(f"constexpr int K = {K};")
+    w(f"constexpr int NHEL = {2 ** (n + 2)};")
+    w(f"constexpr int NDIAG = {diagram_count(n)};")
+    w(f"constexpr int CDEN = {den};")
+    w(f"constexpr int IDENT = {n_identical};  // identical outgoing gluons (1/IDENT!)")
+    w(f"constexpr unsigned OUTGOING_GLUONS = {sum(1 << g for g in outgoing_gluons)}u;  // bit g: gluon g outgoing")
+    flat = ", ".join(str(x) for row in Cint for x in row)
+    w(f"__host__ __device__ constexpr int cint(int i, int j) {{ constexpr int c[K * K] = {{{flat}}}; return c[i * K + j]; }}")
+    w(f"constexpr int ORDER[K][NG] = {{{', '.join('{' + ', '.join(map(str, p)) + '}' for p in perms)}}};")
+    w("")
+    w("// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1.")
+    w("template <class R, int LB>")
+    w("__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {")
+    w("  R acc = R(0);")
+    ind = "  "
+
+    # all sequences of distinct gluons, by length
+    seqs = {L: list(itertools.permutations(range(n), L)) for L in range(1, n + 1)}
+    canon = {}  # J name for reversed sequences
+    nlev = n + 2
+
+    def open_level(L, hvar, sel):
+        nonlocal ind
+        bit = f"((lane >> (LB - 1 - {L})) & 1)"
+        w(f"{ind}#pragma unroll 1")
+        w(f"{ind}for (int i{L} = 0; i{L} < (LB > {L} ? 1 : 2); ++i{L}) {{")
+        ind += "  "
+        w(f"{ind}const int {hvar} = LB > {L} ? {bit} : i{L};")
+        w(f"{ind}{sel}")
+
+    # gluon levels
+    for g in range(n):
+        open_level(g, f"h{g}", f"const cv<R> E{g} = h{g} ? X.eps[{g}][1] : X.eps[{g}][0];")
+        for L in range(2, n + 1):
+            for sq in seqs[L]:
+                if max(sq) != g:
+                    continue
+                nm = seq_name("J", sq)
+                rv = tuple(reversed(sq))
+                if rv in canon:
+                    # reflection identity J(reversed) = (-1)^{L+1} J
+                    src = canon[rv]
+                    w(f"{ind}const cv<R> {nm} = {'neg(' + src + ')' if L % 2 == 0 else src};")
+                    continue
+                canon[sq] = nm
+                m = mask(sq)
+
+                def jn(s):
+                    return f"E{s[0]}" if len(s) == 1 else seq_name("J", s)
+                terms = []
+                for c in range(1, L):
+                    a, b = sq[:c], sq[c:]
+                    terms.append(f"vvv({jn(a)}, Kn.P[{mask(a)}], {jn(b)}, Kn.P[{mask(b)}], Kn.cg[{m}])")
+                    em.count(g, "vvv")
+                w(f"{ind}cv<R> {nm} = {terms[0]};")
+                for t in terms[1:]:
+                    w(f"{ind}addto({nm}, {t});")
+                    em.count(g, "cadd", 8)
+                for c in range(1, L):
+                    for d in range(c + 1, L):
+                        a, b, cc = sq[:c], sq[c:d], sq[d:]
+                        w(f"{ind}vvvv_acc({nm}, {jn(a)}, {jn(b)}, {jn(cc)}, Kn.c4[{m}]);")
+                        em.count(g, "vvvv_acc")
+    # antitop level: fermion currents psi(rho), rho proper (len 1..n-1)
+    open_level(n, f"h{n}", f"const sp<R> S_E = h{n} ? X.v[1] : X.v[0];")
+
+    def jn(s):
+        return f"E{s[0]}" if len(s) == 1 else seq_name("J", s)
+    for L in range(1, n):
+        for rho in seqs[L]:
+            nm = seq_name("S_", rho)
+            terms = []
+            for c in range(1, L + 1):
+                a, b = rho[:c], rho[c:]
+                terms.append(f"slash({jn(a)}, {seq_name('S_', b)})")
+                em.count(n, "slash")
+            w(f"{ind}sp<R> t{nm} = {terms[0]};")
+            for t in terms[1:]:
+                w(f"{ind}spadd(t{nm}, {t});")
+                em.count(n, "sp_add")
+            w(f"{ind}const sp<R> {nm} = fprop(Kn.qc[{mask(rho)}], Kn.mc[{mask(rho)}], t{nm});")
+            em.count(n, "fprop")
+    # top level: fermion currents F(rho) = ubar gamma psi(rho), amplitudes, colour sum
+    open_level(n + 1, f"h{n + 1}", f"const sp<R> UB = h{n + 1} ? X.ub[1] : X.ub[0];")
+    w(f"{ind}const cv<R> F_E = fcur(UB, S_E);")
+    em.count(n + 1, "fcur")
+    for L in range(1, n):
+        for rho in seqs[L]:
+            nm = seq_name("S_", rho)
+            w(f"{ind}const cv<R> F{nm[1:]} = fcur(UB, {nm});")
+            em.count(n + 1, "fcur")
+    for k, sg in enumerate(perms):
+        terms = []
+        for c in range(1, n + 1):
+            a, b = sg[:c], sg[c:]
+            fn = "F_E" if not b else "F" + seq_name("S_", b)[1:]
+            terms.append(f"dot({jn(a)}, {fn})")
+            em.count(n + 1, "dot")
+        w(f"{ind}const cx<R> A{k} = {' + '.join(terms)};")
+        em.count(n + 1, "cadd", len(terms) - 1)
+    # colour sum with the symmetric integer matrix: sum_i Re(A_i^* (C_ii/2 A_i + sum_{j>i} C_ij A_j)) * 2
+    w(f"{ind}R cs = R(0);")
+    for i in range(K):
+        tr, ti = f"R({Cint[i][i]}) * R(0.5) * A{i}.r", f"R({Cint[i][i]}) * R(0.5) * A{i}.i"
+        parts_r, parts_i = [tr], [ti]
+        for j in range(i + 1, K):
+            if Cint[i][j] == 0:
+                continue
+            parts_r.append(f"R({Cint[i][j]}) * A{j}.r")
+            parts_i.append(f"R({Cint[i][j]}) * A{j}.i")
+        w(f"{ind}{{ const R zr = {' + '.join(parts_r)}; const R zi = {' + '.join(parts_i)};")
+        w(f"{ind}  cs += A{i}.r * zr + A{i}.i * zi; }}")
+        em.flops_per_level[n + 1] += 4 * len(parts_r) + 4
+    w(f"{ind}acc += R(2) * cs;")
+    for L in range(nlev - 1, -1, -1):
+        ind = ind[:-2]
+        w(f"{ind}}}")
+    w("  return acc;")
+    w("}")
+    w("")
+    # flops per event for the full helicity sum (one lane doing all helicities)
+    total = 0
+    for L in range(nlev):
+        total += em.flops_per_level[L] * (2 ** (L + 1))
+    w(f"// floating-point operations of one full helicity sum (all levels, all loop trips)")
+    w(f"constexpr long FLOPS_HEL_SUM = {total};")
+    w("}}  // namespace")
+    return "\n".join(lines) + "\n", total
+
+
+PROCESSES = {
+    # name: (gluons on the top line, outgoing gluon indices, identical outgoing gluons)
+    "gg_tt": (2, (), 1),
+    "gg_ttg": (3, (2,), 1),
+    "gg_ttgg": (4, (2, 3), 2),
+}
+
+
+def main():
+    here = os.path.dirname(os.path.abspath(__file__))
+    out_dir = os.path.join(os.path.dirname(here), "csrc")
+    for name, (n, outg, ident) in PROCESSES.items():
+        src, fl = emit_process(name, n, outg, ident)
+        with open(os.path.join(out_dir, f"gen_qcd_{name}.cuh"), "w") as f:
+            f.write(src)
+        print(name, "diagrams", diagram_count(n), "flops/hel-sum", fl)
+
+
+if __name__ == "__main__":
+    main()

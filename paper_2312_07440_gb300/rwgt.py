@@ -1,0 +1,222 @@
+"""Thin Python binding of librwgt.so (include/rwgt.h): argument marshalling only.
+
+Every step of the reweighting path runs in the library's CUDA kernels; this
+module converts Python/torch arguments to the C ABI's plain pointers and
+sizes.  There is no CPU fallback: if the library is missing or fails to load,
+``load()`` raises.  torch is used for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "librwgt.so")
+
+RW_OK = 0
+RW_WARN_BAD_EVENTS = 1
+ERRORS = {-1: "RW_ERR_NULL", -2: "RW_ERR_ARG", -3: "RW_ERR_MODE", -4: "RW_ERR_PARAM", -5: "RW_ERR_CUDA",
+          -6: "RW_ERR_STATE", -7: "RW_ERR_ALIGN", -8: "RW_ERR_WORKSPACE"}
+PROCESS = {"ee_mumu": 0, "gg_tt": 1, "gg_ttg": 2, "gg_ttgg": 3}
+MODE = {"fp64": 0, "fp32": 1}
+MAX_POINTS = 256
+PARAM_FIELDS = ("alpha_s", "m_t", "w_t", "yt_scale", "alpha_em_inv", "G_F", "m_Z", "w_Z")
+
+
+class RwParams(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in PARAM_FIELDS]
+
+
+class RwProcessInfo(ctypes.Structure):
+    _fields_ = [("n_external", ctypes.c_int), ("n_helicities", ctypes.c_int), ("n_colour_flows", ctypes.c_int),
+                ("n_diagrams", ctypes.c_int), ("colour_den", ctypes.c_int), ("flops_hel_sum", ctypes.c_longlong)]
+
+
+class RwError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load librwgt.so (built by build.py / __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i, d, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "rw_create": ([ctypes.POINTER(P), i, P], i),
+        "rw_destroy": ([P], i),
+        "rw_last_error": ([P], ctypes.c_char_p),
+        "rw_process_info_get": ([i, ctypes.POINTER(RwProcessInfo)], i),
+        "rw_set_process": ([P, i, i], i),
+        "rw_set_params": ([P, ctypes.POINTER(RwParams)], i),
+        "rw_set_reweight_points": ([P, P, i], i),
+        "rw_set_tuning": ([P, i, i], i),
+        "rw_workspace_bytes": ([P, i64], sz),
+        "rw_load_events": ([P, P, P, i64, P, sz], i),
+        "rw_eval_me": ([P, i, P], i),
+        "rw_reweight_async": ([P, P, P, P, P], i),
+        "rw_get_results": ([P, P, P, P], i),
+        "rw_reweight": ([P, P, P, P, P, P], i),
+        "rw_workspace_bytes_host": ([P, i64], sz),
+        "rw_reweight_host": ([P, P, P, i64, P, P, P, P, P, sz], i),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def process_info(process: str) -> RwProcessInfo:
+    info = RwProcessInfo()
+    rc = load().rw_process_info_get(PROCESS[process], ctypes.byref(info))
+    if rc:
+        raise RwError(rc, "rw_process_info_get")
+    return info
+
+
+def params_struct(vec) -> RwParams:
+    v = np.asarray(vec, dtype=np.float64).reshape(8)
+    return RwParams(*[float(x) for x in v])
+
+
+class Context:
+    """One rw_ctx: process, precision mode, parameter points, attached events."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.h = None
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.rw_create(ctypes.byref(h), int(device), stream)
+        if rc:
+            raise RwError(rc, "rw_create failed")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.rw_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def last_error(self) -> str:
+        return self.lib.rw_last_error(self.h).decode()
+
+    def _check(self, rc, what):
+        if rc < 0:
+            raise RwError(rc, f"{what}: {self.last_error()}")
+        return rc
+
+    def set_process(self, process: str, mode: str = "fp64"):
+        return self._check(self.lib.rw_set_process(self.h, PROCESS[process], MODE[mode]), "rw_set_process")
+
+    def set_params(self, vec):
+        p = params_struct(vec)
+        return self._check(self.lib.rw_set_params(self.h, ctypes.byref(p)), "rw_set_params")
+
+    def set_reweight_points(self, pts):
+        arr = np.ascontiguousarray(np.atleast_2d(pts), dtype=np.float64)
+        return self._check(self.lib.rw_set_reweight_points(self.h, arr.ctypes.data, arr.shape[0]),
+                           "rw_set_reweight_points")
+
+    def set_tuning(self, lane_bits: int = -1, block: int = 0):
+        return self._check(self.lib.rw_set_tuning(self.h, int(lane_bits), int(block)), "rw_set_tuning")
+
+    def workspace_bytes(self, n_events: int) -> int:
+        return int(self.lib.rw_workspace_bytes(self.h, int(n_events)))
+
+    def workspace_bytes_host(self, n_events: int) -> int:
+        return int(self.lib.rw_workspace_bytes_host(self.h, int(n_events)))
+
+    def load_events(self, mom, w, n_events: int, workspace, workspace_bytes: int):
+        return self._check(self.lib.rw_load_events(self.h, _ptr(mom), _ptr(w), int(n_events), _ptr(workspace),
+                                                   int(workspace_bytes)), "rw_load_events")
+
+    def eval_me(self, point: int, out):
+        return self._check(self.lib.rw_eval_me(self.h, int(point), _ptr(out)), "rw_eval_me")
+
+    def reweight_async(self, wnew=None, ratio=None, me0=None, me_pts=None):
+        return self._check(self.lib.rw_reweight_async(self.h, _ptr(wnew), _ptr(ratio), _ptr(me0), _ptr(me_pts)),
+                           "rw_reweight_async")
+
+    def get_results(self, n_points: int):
+        sig = np.zeros(n_points)
+        so = ctypes.c_double()
+        nb = ctypes.c_int64()
+        rc = self._check(self.lib.rw_get_results(self.h, sig.ctypes.data, ctypes.byref(so), ctypes.byref(nb)),
+                         "rw_get_results")
+        return sig, so.value, nb.value, rc
+
+    def reweight(self, n_points: int, wnew=None, ratio=None):
+        sig = np.zeros(n_points)
+        so = ctypes.c_double()
+        nb = ctypes.c_int64()
+        rc = self._check(self.lib.rw_reweight(self.h, _ptr(wnew), _ptr(ratio), sig.ctypes.data, ctypes.byref(so),
+                                              ctypes.byref(nb)), "rw_reweight")
+        return sig, so.value, nb.value, rc
+
+    def reweight_host(self, h_mom, h_w, n_events: int, h_wnew, n_points: int, workspace, workspace_bytes: int):
+        sig = np.zeros(n_points)
+        so = ctypes.c_double()
+        nb = ctypes.c_int64()
+        rc = self._check(self.lib.rw_reweight_host(self.h, _ptr(h_mom), _ptr(h_w), int(n_events), _ptr(h_wnew),
+                                                   sig.ctypes.data, ctypes.byref(so), ctypes.byref(nb),
+                                                   _ptr(workspace), int(workspace_bytes)), "rw_reweight_host")
+        return sig, so.value, nb.value, rc
+
+
+def reweight(process: str, mode: str, mom, w, p0, points, *, lane_bits: int = -1, block: int = 0,
+             want_me: bool = True, device=None):
+    """Convenience: reweight a device batch (torch float64 tensors mom[N][4][E],
+    w[E]) for P points; returns a dict of torch tensors and the sums."""
+    import torch
+    dev = mom.device if device is None else device
+    E = mom.shape[-1]
+    pts = np.atleast_2d(np.asarray(points, dtype=np.float64))
+    P = pts.shape[0]
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    with Context(dev.index or 0, stream) as c:
+        c.set_process(process, mode)
+        c.set_params(p0)
+        c.set_reweight_points(pts)
+        c.set_tuning(lane_bits, block)
+        nb = c.workspace_bytes(E)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        c.load_events(mom, w, E, ws, nb)
+        out = {"wnew": torch.empty((P, E), dtype=torch.float64, device=dev),
+               "ratio": torch.empty((P, E), dtype=torch.float64, device=dev)}
+        if want_me:
+            out["me0"] = torch.empty(E, dtype=torch.float64, device=dev)
+            out["me"] = torch.empty((P, E), dtype=torch.float64, device=dev)
+        c.reweight_async(out["wnew"], out["ratio"], out.get("me0"), out.get("me"))
+        sig, so, nbad, rc = c.get_results(P)
+        out.update(sigma=sig, sigma_orig=so, n_bad=nbad, status=rc)
+        return out

@@ -1,0 +1,274 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (per event, relative): 1e-12 in FP64 mode, 1e-5 in FP32 mode, on
+|M|^2, |M'|^2, r and W'.  Cross sections: the GPU sigma' must equal the
+exactly rounded sum of the GPU's own W' to 2 ulp (compensated summation), and
+agree with the oracle's exact sum to the per-event tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_07440_gb300 import events as ev
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2312_07440_gb300 import rwgt  # noqa: E402
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+DEV = torch.device("cuda", 0)
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    den = np.maximum(np.abs(b), 1e-300)
+    return np.where((a == b), 0.0, np.abs(a - b) / den)
+
+
+_ORACLE_CACHE = {}
+
+
+def oracle_run(proc, wl_name, n, pts, start=0):
+    key = (proc, wl_name, n, start, pts.tobytes())
+    if key not in _ORACLE_CACHE:
+        mom, w = ev.generate(ev.WORKLOADS[wl_name], n, start=start)
+        _ORACLE_CACHE[key] = (mom, w, oracle.reweight(proc, ev.param_vector(), pts, mom, w))
+    return _ORACLE_CACHE[key]
+
+
+def run_gpu(proc, mode, mom, w, pts, lane_bits=-1, block=0):
+    out = rwgt.reweight(proc, mode, to_dev(mom), to_dev(w), ev.param_vector(), pts, lane_bits=lane_bits,
+                        block=block)
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+
+
+def check_against_oracle(g, o, mode):
+    tol = TOL[mode]
+    assert rel(g["me0"], o["me0"]).max() < tol
+    assert rel(g["me"], o["me"]).max() < tol
+    assert rel(g["ratio"], o["ratio"]).max() < tol
+    assert rel(g["wnew"], o["wnew"]).max() < tol
+    for j in range(len(g["sigma"])):
+        exact_gpu = math.fsum(g["wnew"][j])
+        assert abs(g["sigma"][j] - exact_gpu) <= 2 * np.spacing(exact_gpu)
+        assert abs(g["sigma"][j] / o["sigma"][j] - 1) < tol
+    assert abs(g["sigma_orig"] - o["sigma_orig"]) <= 2 * np.spacing(o["sigma_orig"])
+    assert g["n_bad"] == o["n_bad"]
+
+
+# --------------------------------------------------------------------------
+# g g -> t tbar (the 1M-event workload's process), every launch variant
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+@pytest.mark.parametrize("lane_bits", [0, 1, 2, 3, 4])
+def test_gg_tt_parity(mode, lane_bits):
+    pts = ev.reweight_points("gg_tt_1m")
+    mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 5003, pts)  # several blocks + a ragged tail
+    g = run_gpu("gg_tt", mode, mom, w, pts, lane_bits=lane_bits)
+    check_against_oracle(g, o, mode)
+
+
+@pytest.mark.parametrize("block", [32, 64, 256])
+def test_gg_tt_block_sizes(block):
+    pts = ev.reweight_points("gg_tt_1m")
+    mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 5003, pts)
+    g = run_gpu("gg_tt", "fp64", mom, w, pts, block=block)
+    check_against_oracle(g, o, "fp64")
+
+
+def test_gg_tt_several_points_and_alpha_s_scaling():
+    pts = np.stack([ev.param_vector(alpha_s=0.120), ev.param_vector(m_t=175.0), ev.param_vector(),
+                    ev.param_vector(m_t=175.0, alpha_s=0.120), ev.param_vector(m_t=160.0)])
+    mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 777, pts)
+    g = run_gpu("gg_tt", "fp64", mom, w, pts)
+    check_against_oracle(g, o, "fp64")
+    assert np.abs(g["ratio"][0] / (0.120 / 0.118) ** 2 - 1).max() < 1e-14   # P9
+    assert np.all(g["ratio"][2] == 1.0) and np.all(g["wnew"][2] == w)       # P8 (bitwise)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_ee_mumu_parity_full_sample(mode):
+    pts = ev.reweight_points("ee_mumu_4k")
+    mom, w, o = oracle_run("ee_mumu", "ee_mumu_4k", 4096, pts)
+    for lb in ([0, 2, 4] if mode == "fp64" else [0]):
+        g = run_gpu("ee_mumu", mode, mom, w, pts, lane_bits=lb)
+        check_against_oracle(g, o, mode)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+@pytest.mark.parametrize("lane_bits", [0, 1, 2, 3])
+def test_gg_ttg_parity(mode, lane_bits):
+    pts = ev.reweight_points("gg_ttg_4m", "mt")[::21]  # kappa = 0.8, 0.933, 1.067, 1.2 (m_t = kappa 173)
+    mom, w, o = oracle_run("gg_ttg", "gg_ttg_4m", 611, pts)
+    g = run_gpu("gg_ttg", mode, mom, w, pts, lane_bits=lane_bits)
+    check_against_oracle(g, o, mode)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_gg_ttgg_parity(mode):
+    pts = ev.reweight_points("gg_ttgg_1m", "mt")
+    mom, w, o = oracle_run("gg_ttgg", "gg_ttgg_1m", 197, pts)
+    g = run_gpu("gg_ttgg", mode, mom, w, pts, lane_bits=2)
+    check_against_oracle(g, o, mode)
+
+
+def test_yukawa_axis_gives_unit_ratio():
+    pts = ev.reweight_points("gg_ttg_4m")[:8]
+    mom, w = ev.generate(ev.WORKLOADS["gg_ttg_4m"], 300)
+    g = run_gpu("gg_ttg", "fp64", mom, w, pts)
+    assert np.all(g["ratio"] == 1.0)
+
+
+# --------------------------------------------------------------------------
+# edge cases and error behaviour
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 129])
+def test_tiny_batches(n):
+    pts = ev.reweight_points("gg_tt_1m")
+    mom, w, o = oracle_run("gg_tt", "gg_tt_1m", n, pts)
+    g = run_gpu("gg_tt", "fp64", mom, w, pts)
+    check_against_oracle(g, o, "fp64")
+
+
+def test_bad_events_are_counted_and_excluded():
+    pts = ev.reweight_points("gg_tt_1m")
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 500)
+    mom[:, :, 17] = 0.0      # |M|^2 = NaN
+    mom[:, :, 400] = np.nan
+    o = oracle.reweight("gg_tt", ev.param_vector(), pts, mom, w)
+    g = run_gpu("gg_tt", "fp64", mom, w, pts)
+    assert g["status"] == rwgt.RW_WARN_BAD_EVENTS and g["n_bad"] == 2 == o["n_bad"]
+    for k in (17, 400):
+        assert g["ratio"][0, k] == 0.0 and g["wnew"][0, k] == 0.0
+    ok = np.ones(500, bool)
+    ok[[17, 400]] = False
+    assert rel(g["wnew"][0, ok], o["wnew"][0, ok]).max() < 1e-12
+    assert abs(g["sigma"][0] / o["sigma"][0] - 1) < 1e-12
+
+
+def test_mass_that_does_not_fit_gives_zero_weight():
+    pts = ev.param_vector(m_t=700.0)[None]
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 400)
+    o = oracle.reweight("gg_tt", ev.param_vector(), pts, mom, w)
+    g = run_gpu("gg_tt", "fp64", mom, w, pts)
+    out = (mom[0, 0] + mom[1, 0]) <= 1400.0
+    assert out.any() and np.all(g["wnew"][0, out] == 0.0) and np.all(o["wnew"][0, out] == 0.0)
+    assert rel(g["wnew"][0], o["wnew"][0]).max() < 1e-12
+
+
+def test_deterministic_results():
+    pts = ev.reweight_points("gg_tt_1m")
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 20000)
+    a = run_gpu("gg_tt", "fp64", mom, w, pts)
+    b = run_gpu("gg_tt", "fp64", mom, w, pts)
+    assert np.array_equal(a["wnew"], b["wnew"]) and np.array_equal(a["sigma"], b["sigma"])
+
+
+def test_eval_me_matches_fused_path():
+    pts = ev.reweight_points("gg_tt_1m")
+    mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 1000, pts)
+    dm, dw = to_dev(mom), to_dev(w)
+    stream = torch.cuda.current_stream().cuda_stream
+    with rwgt.Context(0, stream) as c:
+        c.set_process("gg_tt", "fp64")
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(pts)
+        nb = c.workspace_bytes(1000)
+        ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+        c.load_events(dm, dw, 1000, ws, nb)
+        me0 = torch.empty(1000, dtype=torch.float64, device=DEV)
+        me1 = torch.empty(1000, dtype=torch.float64, device=DEV)
+        c.eval_me(-1, me0)
+        c.eval_me(0, me1)
+        torch.cuda.synchronize()
+    assert rel(me0.cpu().numpy(), o["me0"]).max() < 1e-12
+    assert rel(me1.cpu().numpy(), o["me"][0]).max() < 1e-12
+
+
+def test_host_entry_point_matches_device_path():
+    pts = ev.reweight_points("gg_tt_1m")
+    mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 3001, pts)
+    with rwgt.Context(0, torch.cuda.current_stream().cuda_stream) as c:
+        c.set_process("gg_tt", "fp64")
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(pts)
+        nb = c.workspace_bytes_host(3001)
+        ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+        hw = np.empty((1, 3001))
+        sig, so, nbad, rc = c.reweight_host(np.ascontiguousarray(mom), np.ascontiguousarray(w), 3001, hw, 1, ws, nb)
+    assert rc == 0 and nbad == 0
+    assert rel(hw, o["wnew"]).max() < 1e-12
+    assert abs(sig[0] - math.fsum(hw[0])) <= 2 * np.spacing(sig[0])
+
+
+def test_argument_errors():
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 64)
+    dm, dw = to_dev(mom), to_dev(w)
+    with rwgt.Context(0, torch.cuda.current_stream().cuda_stream) as c:
+        with pytest.raises(rwgt.RwError) as e:
+            c.load_events(dm, dw, 64, None, 0)
+        assert e.value.code == -6  # no process yet
+        c.set_process("gg_tt", "fp64")
+        for bad in (dict(w_t=1.5), dict(alpha_s=-0.1), dict(m_t=float("nan"))):
+            with pytest.raises(rwgt.RwError) as e:
+                c.set_params(ev.param_vector(**bad))
+            assert e.value.code == -4
+        c.set_params(ev.param_vector())
+        with pytest.raises(rwgt.RwError) as e:
+            c.set_reweight_points(np.zeros((0, 8)))
+        assert e.value.code == -2
+        with pytest.raises(rwgt.RwError) as e:
+            c.set_reweight_points(np.tile(ev.param_vector(), (300, 1)))
+        assert e.value.code == -2
+        c.set_reweight_points(ev.reweight_points("gg_tt_1m"))
+        nb = c.workspace_bytes(64)
+        ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+        with pytest.raises(rwgt.RwError) as e:
+            c.load_events(dm, dw, 0, ws, nb)
+        assert e.value.code == -2
+        with pytest.raises(rwgt.RwError) as e:
+            c.load_events(dm, dw, 64, ws, nb - 1)
+        assert e.value.code == -8
+        with pytest.raises(rwgt.RwError) as e:
+            c.load_events(dm.data_ptr() + 4, dw, 64, ws, nb)
+        assert e.value.code == -7
+        with pytest.raises(rwgt.RwError) as e:
+            c.load_events(np.ascontiguousarray(mom), dw, 64, ws, nb)  # host pointer
+        assert e.value.code in (-2, -5)
+        with pytest.raises(rwgt.RwError) as e:
+            c.reweight_async()
+        assert e.value.code == -6  # no events
+        with pytest.raises(rwgt.RwError) as e:
+            c.set_tuning(7, 0)
+        assert e.value.code == -3
+
+
+# --------------------------------------------------------------------------
+# full size, in the benchmark's launch configuration: sampled events
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_gg_tt_full_size_sampled(mode):
+    wl = ev.WORKLOADS["gg_tt_1m"]
+    pts = ev.reweight_points("gg_tt_1m")
+    mom, w = ev.generate(wl)
+    g = run_gpu("gg_tt", mode, mom, w, pts)
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([rng.integers(0, wl.n_events, 1500), np.argsort(g["me0"])[:50],
+                                    np.argsort(g["me0"])[-50:], [0, wl.n_events - 1]]))
+    o = oracle.reweight("gg_tt", ev.param_vector(), pts, np.ascontiguousarray(mom[:, :, idx]), w[idx])
+    tol = TOL[mode]
+    assert rel(g["me0"][idx], o["me0"]).max() < tol
+    assert rel(g["wnew"][0, idx], o["wnew"][0]).max() < tol
+    exact = math.fsum(g["wnew"][0])
+    assert abs(g["sigma"][0] - exact) <= 2 * np.spacing(exact)
+    assert g["n_bad"] == 0
