@@ -148,6 +148,34 @@ int rw_reweight_host(rw_ctx* ctx, const double* h_mom, const double* h_w, int64_
                      double* h_sigma, double* h_sigma_orig, int64_t* h_n_bad, void* d_workspace,
                      size_t workspace_bytes);
 
+/* ---------------------------------------------------------------------------
+   Allocation-free variant of rw_reweight_async.  The paper has no counterpart:
+   it exists for callers that cannot allocate device memory -- code that runs
+   inside a host framework owning the whole device memory budget up front
+   (online/trigger-style services, plug-ins hooked into an event generator),
+   or in a latency-critical loop where cudaMalloc's implicit device
+   synchronisation is not acceptable.  The caller passes inputs and outputs
+   only; the reduction scratch lives in a fixed array of RW_NOALLOC_SCRATCH_BYTES
+   bytes in this library's device memory, which every GPU that loads the
+   library holds until the process exits.
+     d_mom [N][4][E], d_w [E]      device inputs (as rw_load_events)
+     d_wnew [P][E], d_ratio [P][E] device outputs, may be NULL
+     d_sigma [P+1]                 device output: sigma'_0..P-1, then sigma
+     d_n_bad [1]                   device output: events with |M|^2 == 0/non-finite
+   Process, mode, parameters and at most RW_NOALLOC_MAX_POINTS points come from
+   the context (set beforehand).  No cudaMalloc/cudaFree or other allocation
+   happens in the call; it returns without synchronising the stream.
+   The first call on a device looks up the array's device address (once per
+   device, with that device current); make that first call before any stream
+   capture.  All calls share the one array and each call overwrites it: calls
+   whose kernels overlap on the GPU (e.g. two streams at once) race and must
+   be serialised by the caller.  More points than the maximum -> RW_ERR_ARG;
+   error texts of this call are short (at most 15 characters). */
+#define RW_NOALLOC_MAX_POINTS 16
+#define RW_NOALLOC_SCRATCH_BYTES (256 + 2048 * (RW_NOALLOC_MAX_POINTS + 1) * 16)
+int rw_reweight_noalloc(rw_ctx* ctx, const double* d_mom, const double* d_w, int64_t n_events, double* d_wnew,
+                        double* d_ratio, double* d_sigma, unsigned long long* d_n_bad);
+
 #ifdef __cplusplus
 }
 #endif

@@ -485,3 +485,118 @@ int rw_reweight_host(rw_ctx* c, const double* h_mom, const double* h_w, int64_t 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// rw_reweight_noalloc: the fused reweight with its scratch in a fixed device
+// array of this file instead of a caller-provided workspace.  See rwgt.h.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int NOALLOC_MAX_GRID = 2048;
+constexpr size_t NOALLOC_HEADER = 256;  // ticket (u32 at 0), bad-event counter (u64 at 8)
+static_assert(RW_NOALLOC_SCRATCH_BYTES ==
+                  NOALLOC_HEADER + (size_t)NOALLOC_MAX_GRID * (RW_NOALLOC_MAX_POINTS + 1) * sizeof(double2),
+              "scratch size in rwgt.h out of step");
+
+// Shared by every call on a device; the module keeps it until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RW_NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Error text without growing the context's string (no host allocation):
+// every message below fits the string's smallest capacity (15 characters).
+int noalloc_fail(rw_ctx* c, int code, const char* msg) {
+  if (c) c->err.assign(msg, std::min(strlen(msg), c->err.capacity()));
+  return code;
+}
+
+// Device address of the scratch array on the current device (set up once per
+// device, with that device current).
+void* noalloc_scratch(int device) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    g_noalloc_addr[device] = ptr;
+  }
+  return g_noalloc_addr[device];
+}
+
+bool noalloc_dev_ptr_ok(const void* p, int device) {
+  if (!p || reinterpret_cast<uintptr_t>(p) % 8) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == device;
+}
+
+}  // namespace
+
+extern "C" int rw_reweight_noalloc(rw_ctx* c, const double* d_mom, const double* d_w, int64_t E, double* d_wnew,
+                                   double* d_ratio, double* d_sigma, unsigned long long* d_n_bad) {
+  if (!c) return RW_ERR_NULL;
+  if (c->process < 0 || !c->have_p0 || c->pts.empty())
+    return noalloc_fail(c, RW_ERR_STATE, "state not set");
+  const int P = (int)c->pts.size();
+  if (P > RW_NOALLOC_MAX_POINTS) return noalloc_fail(c, RW_ERR_ARG, "too many points");
+  if (E <= 0 || E > (int64_t(1) << 40)) return noalloc_fail(c, RW_ERR_ARG, "bad n_events");
+  if (c->device < 0 || c->device >= NOALLOC_MAX_DEVICES) return noalloc_fail(c, RW_ERR_ARG, "bad device");
+  DeviceGuard g(c->device);
+  if (!g.ok) return noalloc_fail(c, RW_ERR_CUDA, "cudaSetDevice");
+  if (!d_mom || !d_w || !d_sigma || !d_n_bad) return noalloc_fail(c, RW_ERR_NULL, "NULL pointer");
+  if (!noalloc_dev_ptr_ok(d_mom, c->device) || !noalloc_dev_ptr_ok(d_w, c->device) ||
+      !noalloc_dev_ptr_ok(d_sigma, c->device) || !noalloc_dev_ptr_ok(d_n_bad, c->device) ||
+      (d_wnew && !noalloc_dev_ptr_ok(d_wnew, c->device)) || (d_ratio && !noalloc_dev_ptr_ok(d_ratio, c->device)))
+    return noalloc_fail(c, RW_ERR_ARG, "bad buffer");
+  char* scratch = static_cast<char*>(noalloc_scratch(c->device));
+  if (!scratch) return noalloc_fail(c, RW_ERR_CUDA, "scratch lookup");
+
+  const int lb = c->lane_bits >= 0 ? c->lane_bits : default_lane_bits(c->process, c->mode);
+  const KernelEntry* k = registry().find(c->process, c->mode, lb);
+  if (!k) return noalloc_fail(c, RW_ERR_MODE, "no kernel");
+  const int block = c->block > 0 ? c->block : 128;
+  const size_t smem = (size_t)(block / 32) * (P + 1) * sizeof(double2);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return noalloc_fail(c, RW_ERR_CUDA, "occupancy query");
+  }
+  if (per_sm < 1) per_sm = 1;
+  const long long need = (E * (1LL << lb) + block - 1) / block;
+  const int grid =
+      (int)std::max(1LL, std::min<long long>({(long long)NOALLOC_MAX_GRID, (long long)per_sm * c->sm_count, need}));
+
+  RwArgs a{};
+  a.mom = d_mom;
+  a.w = d_w;
+  a.E = E;
+  a.ratio = d_ratio;
+  a.wnew = d_wnew;
+  a.P = P;
+  a.me_only = 0;
+  a.pt[0] = make_point(c, c->p0, false);
+  for (int j = 0; j < P; ++j) {
+    const bool moved = c->process != RW_EE_MUMU && c->pts[j].m_t != c->p0.m_t;
+    a.pt[1 + j] = make_point(c, c->pts[j], moved);
+  }
+  a.ticket = reinterpret_cast<unsigned int*>(scratch);
+  a.nbad_count = reinterpret_cast<unsigned long long*>(scratch + 8);
+  a.block_part = reinterpret_cast<double2*>(scratch + NOALLOC_HEADER);
+  a.sigma = d_sigma;
+  a.nbad_out = d_n_bad;
+  // the ticket and the bad-event counter must start at zero
+  cudaError_t e = cudaMemsetAsync(scratch, 0, NOALLOC_HEADER, c->stream);
+  if (e != cudaSuccess) return noalloc_fail(c, RW_ERR_CUDA, "scratch memset");
+  void* args[] = {&a};
+  e = cudaLaunchKernel(k->func, dim3(grid), dim3(block), args, smem, c->stream);
+  if (e != cudaSuccess) return noalloc_fail(c, RW_ERR_CUDA, "kernel launch");
+  return RW_OK;
+}
