@@ -283,9 +283,9 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt.item())
         # the one exchange of the method: sum of the per-shard cross sections
-        ss = torch.tensor(list(sig) + [sig_orig], dtype=torch.float64, device=dev)
-        dist.all_reduce(ss)
-        sig, sig_orig = ss[:P].cpu().numpy(), float(ss[P])
+        from paper_2312_07440_gb300 import shard
+        ss = shard.allreduce_sums(list(sig) + [sig_orig], device=dev)
+        sig, sig_orig = ss[:P], float(ss[P])
     t_step = t_total / args.steps
     value = world * E * P / t_step
 

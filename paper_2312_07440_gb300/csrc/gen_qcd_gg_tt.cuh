@@ -10,37 +10,38 @@ constexpr int NEXT = 4;
 constexpr int K = 2;
 constexpr int NHEL = 16;
 constexpr int NDIAG = 3;
+constexpr int MAX_LB = 3;  // helicity levels that can be spread over lanes
 constexpr int CDEN = 3;
 constexpr int IDENT = 1;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 0u;  // bit g: gluon g outgoing
 __host__ __device__ constexpr int cint(int i, int j) { constexpr int c[K * K] = {16, -2, -2, 16}; return c[i * K + j]; }
 constexpr int ORDER[K][NG] = {{0, 1}, {1, 0}};
 
-// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1.
+// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;
+// helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).
 template <class R, int LB>
 __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
   R acc = R(0);
-  #pragma unroll 1
-  for (int i0 = 0; i0 < (LB > 0 ? 1 : 2); ++i0) {
-    const int h0 = LB > 0 ? ((lane >> (LB - 1 - 0)) & 1) : i0;
+  {
+    const int h0 = 0;
     const cv<R> E0 = h0 ? X.eps[0][1] : X.eps[0][0];
     #pragma unroll 1
-    for (int i1 = 0; i1 < (LB > 1 ? 1 : 2); ++i1) {
-      const int h1 = LB > 1 ? ((lane >> (LB - 1 - 1)) & 1) : i1;
+    for (int i1 = 0; i1 < (LB >= 1 ? 1 : 2); ++i1) {
+      const int h1 = LB >= 1 ? ((lane >> (LB - 1)) & 1) : i1;
       const cv<R> E1 = h1 ? X.eps[1][1] : X.eps[1][0];
       cv<R> J0_1 = vvv(E0, Kn.P[1], E1, Kn.P[2], Kn.cg[3]);
       const cv<R> J1_0 = neg(J0_1);
       #pragma unroll 1
-      for (int i2 = 0; i2 < (LB > 2 ? 1 : 2); ++i2) {
-        const int h2 = LB > 2 ? ((lane >> (LB - 1 - 2)) & 1) : i2;
+      for (int i2 = 0; i2 < (LB >= 2 ? 1 : 2); ++i2) {
+        const int h2 = LB >= 2 ? ((lane >> (LB - 2)) & 1) : i2;
         const sp<R> S_E = h2 ? X.v[1] : X.v[0];
         sp<R> tS_0 = slash(E0, S_E);
         const sp<R> S_0 = fprop(Kn.qc[1], Kn.mc[1], tS_0);
         sp<R> tS_1 = slash(E1, S_E);
         const sp<R> S_1 = fprop(Kn.qc[2], Kn.mc[2], tS_1);
         #pragma unroll 1
-        for (int i3 = 0; i3 < (LB > 3 ? 1 : 2); ++i3) {
-          const int h3 = LB > 3 ? ((lane >> (LB - 1 - 3)) & 1) : i3;
+        for (int i3 = 0; i3 < (LB >= 3 ? 1 : 2); ++i3) {
+          const int h3 = LB >= 3 ? ((lane >> (LB - 3)) & 1) : i3;
           const sp<R> UB = h3 ? X.ub[1] : X.ub[0];
           const cv<R> F_E = fcur(UB, S_E);
           const cv<R> F_0 = fcur(UB, S_0);
@@ -52,7 +53,7 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             cs += A0.r * zr + A0.i * zi; }
           { const R zr = R(16) * R(0.5) * A1.r; const R zi = R(16) * R(0.5) * A1.i;
             cs += A1.r * zr + A1.i * zi; }
-          acc += R(2) * cs;
+          acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
         }
       }
     }
@@ -61,5 +62,5 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
 }
 
 // floating-point operations of one full helicity sum (all levels, all loop trips)
-constexpr long FLOPS_HEL_SUM = 8336;
+constexpr long FLOPS_HEL_SUM = 4168;
 }}  // namespace

@@ -10,29 +10,30 @@ constexpr int NEXT = 5;
 constexpr int K = 6;
 constexpr int NHEL = 32;
 constexpr int NDIAG = 16;
+constexpr int MAX_LB = 4;  // helicity levels that can be spread over lanes
 constexpr int CDEN = 9;
 constexpr int IDENT = 1;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 4u;  // bit g: gluon g outgoing
 __host__ __device__ constexpr int cint(int i, int j) { constexpr int c[K * K] = {64, -8, -8, 1, 1, 10, -8, 64, 1, 10, -8, 1, -8, 1, 64, -8, 10, 1, 1, 10, -8, 64, 1, -8, 1, -8, 10, 1, 64, -8, 10, 1, 1, -8, -8, 64}; return c[i * K + j]; }
 constexpr int ORDER[K][NG] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
 
-// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1.
+// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;
+// helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).
 template <class R, int LB>
 __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
   R acc = R(0);
-  #pragma unroll 1
-  for (int i0 = 0; i0 < (LB > 0 ? 1 : 2); ++i0) {
-    const int h0 = LB > 0 ? ((lane >> (LB - 1 - 0)) & 1) : i0;
+  {
+    const int h0 = 0;
     const cv<R> E0 = h0 ? X.eps[0][1] : X.eps[0][0];
     #pragma unroll 1
-    for (int i1 = 0; i1 < (LB > 1 ? 1 : 2); ++i1) {
-      const int h1 = LB > 1 ? ((lane >> (LB - 1 - 1)) & 1) : i1;
+    for (int i1 = 0; i1 < (LB >= 1 ? 1 : 2); ++i1) {
+      const int h1 = LB >= 1 ? ((lane >> (LB - 1)) & 1) : i1;
       const cv<R> E1 = h1 ? X.eps[1][1] : X.eps[1][0];
       cv<R> J0_1 = vvv(E0, Kn.P[1], E1, Kn.P[2], Kn.cg[3]);
       const cv<R> J1_0 = neg(J0_1);
       #pragma unroll 1
-      for (int i2 = 0; i2 < (LB > 2 ? 1 : 2); ++i2) {
-        const int h2 = LB > 2 ? ((lane >> (LB - 1 - 2)) & 1) : i2;
+      for (int i2 = 0; i2 < (LB >= 2 ? 1 : 2); ++i2) {
+        const int h2 = LB >= 2 ? ((lane >> (LB - 2)) & 1) : i2;
         const cv<R> E2 = h2 ? X.eps[2][1] : X.eps[2][0];
         cv<R> J0_2 = vvv(E0, Kn.P[1], E2, Kn.P[4], Kn.cg[5]);
         cv<R> J1_2 = vvv(E1, Kn.P[2], E2, Kn.P[4], Kn.cg[6]);
@@ -51,8 +52,8 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
         const cv<R> J2_0_1 = J1_0_2;
         const cv<R> J2_1_0 = J0_1_2;
         #pragma unroll 1
-        for (int i3 = 0; i3 < (LB > 3 ? 1 : 2); ++i3) {
-          const int h3 = LB > 3 ? ((lane >> (LB - 1 - 3)) & 1) : i3;
+        for (int i3 = 0; i3 < (LB >= 3 ? 1 : 2); ++i3) {
+          const int h3 = LB >= 3 ? ((lane >> (LB - 3)) & 1) : i3;
           const sp<R> S_E = h3 ? X.v[1] : X.v[0];
           sp<R> tS_0 = slash(E0, S_E);
           const sp<R> S_0 = fprop(Kn.qc[1], Kn.mc[1], tS_0);
@@ -79,8 +80,8 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
           spadd(tS_2_1, slash(J2_1, S_E));
           const sp<R> S_2_1 = fprop(Kn.qc[6], Kn.mc[6], tS_2_1);
           #pragma unroll 1
-          for (int i4 = 0; i4 < (LB > 4 ? 1 : 2); ++i4) {
-            const int h4 = LB > 4 ? ((lane >> (LB - 1 - 4)) & 1) : i4;
+          for (int i4 = 0; i4 < (LB >= 4 ? 1 : 2); ++i4) {
+            const int h4 = LB >= 4 ? ((lane >> (LB - 4)) & 1) : i4;
             const sp<R> UB = h4 ? X.ub[1] : X.ub[0];
             const cv<R> F_E = fcur(UB, S_E);
             const cv<R> F_0 = fcur(UB, S_0);
@@ -111,7 +112,7 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
               cs += A4.r * zr + A4.i * zi; }
             { const R zr = R(64) * R(0.5) * A5.r; const R zi = R(64) * R(0.5) * A5.i;
               cs += A5.r * zr + A5.i * zi; }
-            acc += R(2) * cs;
+            acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
           }
         }
       }
@@ -121,5 +122,5 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
 }
 
 // floating-point operations of one full helicity sum (all levels, all loop trips)
-constexpr long FLOPS_HEL_SUM = 84648;
+constexpr long FLOPS_HEL_SUM = 42324;
 }}  // namespace

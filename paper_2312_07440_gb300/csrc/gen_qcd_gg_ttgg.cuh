@@ -10,29 +10,30 @@ constexpr int NEXT = 6;
 constexpr int K = 24;
 constexpr int NHEL = 64;
 constexpr int NDIAG = 123;
+constexpr int MAX_LB = 5;  // helicity levels that can be spread over lanes
 constexpr int CDEN = 54;
 constexpr int IDENT = 2;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 12u;  // bit g: gluon g outgoing
 __host__ __device__ constexpr int cint(int i, int j) { constexpr int c[K * K] = {512, -64, -64, 8, 8, 80, -64, 8, 8, -1, -1, -10, 8, -1, 80, -10, 71, 62, -1, -10, -10, 62, 62, -28, -64, 512, 8, 80, -64, 8, 8, -64, -1, -10, 8, -1, -1, -10, -10, 62, 62, -28, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, 80, -10, 71, 62, -64, 8, 8, -1, -1, -10, -10, -1, 62, -28, -10, 62, 8, 80, -64, 512, 8, -64, -1, -10, -10, 62, 62, -28, 8, -64, -1, -10, 8, -1, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, -1, 8, 71, 62, 80, -10, -10, -1, 62, -28, -10, 62, -64, 8, 8, -1, -1, -10, 80, 8, 8, -64, -64, 512, -10, -1, 62, -28, -10, 62, -1, 8, 71, 62, 80, -10, 8, -64, -1, -10, 8, -1, -64, 8, 8, -1, -1, -10, 512, -64, -64, 8, 8, 80, 80, -10, 8, -1, 62, 71, -10, 62, -1, -10, -28, 62, 8, -64, -1, -10, 8, -1, -64, 512, 8, 80, -64, 8, -10, 62, -1, -10, -28, 62, 80, -10, 8, -1, 62, 71, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, -64, 8, -10, -1, 62, -28, -10, -1, 62, -10, -1, -10, -10, 62, 62, -28, 8, 80, -64, 512, 8, -64, -1, -10, 8, -64, -1, 8, 71, 62, -1, 8, -10, 80, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, 62, -28, -10, -1, 62, -10, 8, -1, -64, 8, -10, -1, -10, -1, 62, -28, -10, 62, 80, 8, 8, -64, -64, 512, 71, 62, -1, 8, -10, 80, -1, -10, 8, -64, -1, 8, 8, -1, -64, 8, -10, -1, 80, -10, 8, -1, 62, 71, 512, -64, -64, 8, 8, 80, 62, -10, -28, 62, -1, -10, -1, -10, 8, -64, -1, 8, -10, 62, -1, -10, -28, 62, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, 80, -10, 8, -1, 62, 71, 8, -1, -64, 8, -10, -1, -64, 8, 512, -64, 80, 8, -28, 62, 62, -10, -10, -1, -10, 62, -1, -10, -28, 62, -1, -10, 8, -64, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, 71, 62, -1, 8, -10, 80, 62, -28, -10, -1, 62, -10, 8, -64, 80, 8, 512, -64, -1, 8, -10, -1, -64, 8, 62, -28, -10, -1, 62, -10, 71, 62, -1, 8, -10, 80, 80, 8, 8, -64, -64, 512, -10, -1, -1, 8, 8, -64, -1, 8, -10, -1, -64, 8, -10, 80, 62, 71, 8, -1, 62, -10, -28, 62, -1, -10, 512, -64, -64, 8, 8, 80, -10, -1, -1, 8, 8, -64, 62, -10, -28, 62, -1, -10, -10, 80, 62, 71, 8, -1, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, -1, 8, -10, -1, -64, 8, -28, 62, 62, -10, -10, -1, -64, 8, 512, -64, 80, 8, 62, -10, -28, 62, -1, -10, -10, -1, -1, 8, 8, -64, 62, 71, -10, 80, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, -28, 62, 62, -10, -10, -1, -1, 8, -10, -1, -64, 8, 8, -64, 80, 8, 512, -64, -28, 62, 62, -10, -10, -1, 62, 71, -10, 80, -1, 8, -10, -1, -1, 8, 8, -64, 80, 8, 8, -64, -64, 512}; return c[i * K + j]; }
 constexpr int ORDER[K][NG] = {{0, 1, 2, 3}, {0, 1, 3, 2}, {0, 2, 1, 3}, {0, 2, 3, 1}, {0, 3, 1, 2}, {0, 3, 2, 1}, {1, 0, 2, 3}, {1, 0, 3, 2}, {1, 2, 0, 3}, {1, 2, 3, 0}, {1, 3, 0, 2}, {1, 3, 2, 0}, {2, 0, 1, 3}, {2, 0, 3, 1}, {2, 1, 0, 3}, {2, 1, 3, 0}, {2, 3, 0, 1}, {2, 3, 1, 0}, {3, 0, 1, 2}, {3, 0, 2, 1}, {3, 1, 0, 2}, {3, 1, 2, 0}, {3, 2, 0, 1}, {3, 2, 1, 0}};
 
-// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1.
+// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;
+// helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).
 template <class R, int LB>
 __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
   R acc = R(0);
-  #pragma unroll 1
-  for (int i0 = 0; i0 < (LB > 0 ? 1 : 2); ++i0) {
-    const int h0 = LB > 0 ? ((lane >> (LB - 1 - 0)) & 1) : i0;
+  {
+    const int h0 = 0;
     const cv<R> E0 = h0 ? X.eps[0][1] : X.eps[0][0];
     #pragma unroll 1
-    for (int i1 = 0; i1 < (LB > 1 ? 1 : 2); ++i1) {
-      const int h1 = LB > 1 ? ((lane >> (LB - 1 - 1)) & 1) : i1;
+    for (int i1 = 0; i1 < (LB >= 1 ? 1 : 2); ++i1) {
+      const int h1 = LB >= 1 ? ((lane >> (LB - 1)) & 1) : i1;
       const cv<R> E1 = h1 ? X.eps[1][1] : X.eps[1][0];
       cv<R> J0_1 = vvv(E0, Kn.P[1], E1, Kn.P[2], Kn.cg[3]);
       const cv<R> J1_0 = neg(J0_1);
       #pragma unroll 1
-      for (int i2 = 0; i2 < (LB > 2 ? 1 : 2); ++i2) {
-        const int h2 = LB > 2 ? ((lane >> (LB - 1 - 2)) & 1) : i2;
+      for (int i2 = 0; i2 < (LB >= 2 ? 1 : 2); ++i2) {
+        const int h2 = LB >= 2 ? ((lane >> (LB - 2)) & 1) : i2;
         const cv<R> E2 = h2 ? X.eps[2][1] : X.eps[2][0];
         cv<R> J0_2 = vvv(E0, Kn.P[1], E2, Kn.P[4], Kn.cg[5]);
         cv<R> J1_2 = vvv(E1, Kn.P[2], E2, Kn.P[4], Kn.cg[6]);
@@ -51,8 +52,8 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
         const cv<R> J2_0_1 = J1_0_2;
         const cv<R> J2_1_0 = J0_1_2;
         #pragma unroll 1
-        for (int i3 = 0; i3 < (LB > 3 ? 1 : 2); ++i3) {
-          const int h3 = LB > 3 ? ((lane >> (LB - 1 - 3)) & 1) : i3;
+        for (int i3 = 0; i3 < (LB >= 3 ? 1 : 2); ++i3) {
+          const int h3 = LB >= 3 ? ((lane >> (LB - 3)) & 1) : i3;
           const cv<R> E3 = h3 ? X.eps[3][1] : X.eps[3][0];
           cv<R> J0_3 = vvv(E0, Kn.P[1], E3, Kn.P[8], Kn.cg[9]);
           cv<R> J1_3 = vvv(E1, Kn.P[2], E3, Kn.P[8], Kn.cg[10]);
@@ -181,8 +182,8 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
           const cv<R> J3_2_0_1 = neg(J1_0_2_3);
           const cv<R> J3_2_1_0 = neg(J0_1_2_3);
           #pragma unroll 1
-          for (int i4 = 0; i4 < (LB > 4 ? 1 : 2); ++i4) {
-            const int h4 = LB > 4 ? ((lane >> (LB - 1 - 4)) & 1) : i4;
+          for (int i4 = 0; i4 < (LB >= 4 ? 1 : 2); ++i4) {
+            const int h4 = LB >= 4 ? ((lane >> (LB - 4)) & 1) : i4;
             const sp<R> S_E = h4 ? X.v[1] : X.v[0];
             sp<R> tS_0 = slash(E0, S_E);
             const sp<R> S_0 = fprop(Kn.qc[1], Kn.mc[1], tS_0);
@@ -325,8 +326,8 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             spadd(tS_3_2_1, slash(J3_2_1, S_E));
             const sp<R> S_3_2_1 = fprop(Kn.qc[14], Kn.mc[14], tS_3_2_1);
             #pragma unroll 1
-            for (int i5 = 0; i5 < (LB > 5 ? 1 : 2); ++i5) {
-              const int h5 = LB > 5 ? ((lane >> (LB - 1 - 5)) & 1) : i5;
+            for (int i5 = 0; i5 < (LB >= 5 ? 1 : 2); ++i5) {
+              const int h5 = LB >= 5 ? ((lane >> (LB - 5)) & 1) : i5;
               const sp<R> UB = h5 ? X.ub[1] : X.ub[0];
               const cv<R> F_E = fcur(UB, S_E);
               const cv<R> F_0 = fcur(UB, S_0);
@@ -442,7 +443,7 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
                 cs += A22.r * zr + A22.i * zi; }
               { const R zr = R(512) * R(0.5) * A23.r; const R zi = R(512) * R(0.5) * A23.i;
                 cs += A23.r * zr + A23.i * zi; }
-              acc += R(2) * cs;
+              acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
             }
           }
         }
@@ -453,5 +454,5 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
 }
 
 // floating-point operations of one full helicity sum (all levels, all loop trips)
-constexpr long FLOPS_HEL_SUM = 1065112;
+constexpr long FLOPS_HEL_SUM = 532556;
 }}  // namespace

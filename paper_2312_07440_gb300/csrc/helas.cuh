@@ -146,124 +146,139 @@ __device__ __forceinline__ cv<R> fcur(const sp<R>& u, const sp<R>& s) {
 }
 
 // ---------------------------------------------------------------------------
-// External wavefunctions (computed in double from the FP64 momenta)
+// External wavefunctions, computed in the working precision T from momenta
+// already converted to T, with formulas free of cancellation: |p| + p_z is
+// formed as p_T^2/(|p| - p_z) when p_z < 0, and sqrt(E - |p|) as m/sqrt(E + |p|).
 // ---------------------------------------------------------------------------
-// Helicity eigen-2-spinors chi_{+-}(p) along pvec, with |p| + p_z formed
-// without cancellation; phi = 0 when p_T = 0.
-__device__ __forceinline__ void chi_pm(const double (&p)[4], cx<double> (&cp)[2], cx<double> (&cm)[2]) {
-  const double pt2 = p[1] * p[1] + p[2] * p[2];
-  const double pp = sqrt(pt2 + p[3] * p[3]);
-  const double ppz = p[3] >= 0.0 ? pp + p[3] : pt2 / (pp - p[3]);  // |p| + p_z
-  if (ppz > 0.0 && pp > 0.0) {
-    const double c = sqrt(ppz / (2.0 * pp));
-    const double s = 1.0 / sqrt(2.0 * pp * ppz);
-    cp[0] = {c, 0.0};
+template <class T>
+__device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+
+// Helicity eigen-2-spinors chi_{+-}(p) along pvec (phi = 0 when p_T = 0)
+// and |p|.
+template <class T>
+__device__ __forceinline__ T chi_pm(const T (&p)[4], cx<T> (&cp)[2], cx<T> (&cm)[2]) {
+  const T pt2 = p[1] * p[1] + p[2] * p[2];
+  const T pp = sqrt(pt2 + p[3] * p[3]);
+  const T ppz = p[3] >= T(0) ? pp + p[3] : pt2 / (pp - p[3]);  // |p| + p_z
+  if (ppz > T(0) && pp > T(0)) {
+    const T s = rsqrt_t<T>(T(2) * pp * ppz);  // 1/sqrt(2|p|(|p|+p_z))
+    const T c = ppz * s;                      // cos(theta/2)
+    cp[0] = {c, T(0)};
     cp[1] = {p[1] * s, p[2] * s};
     cm[0] = {-p[1] * s, p[2] * s};
-    cm[1] = {c, 0.0};
+    cm[1] = {c, T(0)};
   } else {  // along -z (or p = 0)
-    cp[0] = {0.0, 0.0};
-    cp[1] = {1.0, 0.0};
-    cm[0] = {-1.0, 0.0};
-    cm[1] = {0.0, 0.0};
+    cp[0] = {T(0), T(0)};
+    cp[1] = {T(1), T(0)};
+    cm[0] = {T(-1), T(0)};
+    cm[1] = {T(0), T(0)};
   }
+  return pp;
 }
 
-template <class R>
-__device__ __forceinline__ cx<R> cast(cx<double> a) {
-  return {R(a.r), R(a.i)};
+// w+ = sqrt(E + |p|), w- = sqrt(E - |p|) = m / w+
+template <class T>
+__device__ __forceinline__ void omegas(T E, T pp, T m, T& wp, T& wm) {
+  const T a = E + pp;
+  const T r = rsqrt_t<T>(a);
+  wp = a * r;
+  wm = m * r;
 }
 
 // ubar(p, lambda) for an outgoing fermion (row spinor), index 0: lambda=+1/2, 1: -1/2.
-// u(p,+) = (w- chi+, w+ chi+), u(p,-) = (w+ chi-, w- chi-), w+- = sqrt(E +- |p|),
-// w- = m / w+ (no cancellation); ubar = (u_R^*, u_L^*).
-template <class R>
-__device__ __forceinline__ void ubar_out(const double (&p)[4], double m, sp<R> (&ub)[2]) {
-  cx<double> cp[2], cm[2];
-  chi_pm(p, cp, cm);
-  const double pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-  const double wp = sqrt(p[0] + pp);
-  const double wm = m > 0.0 ? m / wp : 0.0;
-  // lambda = +
-  ub[0].c[0] = cast<R>(conjg(wp * cp[0]));
-  ub[0].c[1] = cast<R>(conjg(wp * cp[1]));
-  ub[0].c[2] = cast<R>(conjg(wm * cp[0]));
-  ub[0].c[3] = cast<R>(conjg(wm * cp[1]));
-  // lambda = -
-  ub[1].c[0] = cast<R>(conjg(wm * cm[0]));
-  ub[1].c[1] = cast<R>(conjg(wm * cm[1]));
-  ub[1].c[2] = cast<R>(conjg(wp * cm[0]));
-  ub[1].c[3] = cast<R>(conjg(wp * cm[1]));
+// u(p,+) = (w- chi+, w+ chi+), u(p,-) = (w+ chi-, w- chi-); ubar = (u_R^*, u_L^*).
+template <class T>
+__device__ __forceinline__ void ubar_out(const T (&p)[4], T m, sp<T> (&ub)[2]) {
+  cx<T> cp[2], cm[2];
+  const T pp = chi_pm(p, cp, cm);
+  T wp, wm;
+  omegas(p[0], pp, m, wp, wm);
+  ub[0].c[0] = conjg(wp * cp[0]);
+  ub[0].c[1] = conjg(wp * cp[1]);
+  ub[0].c[2] = conjg(wm * cp[0]);
+  ub[0].c[3] = conjg(wm * cp[1]);
+  ub[1].c[0] = conjg(wm * cm[0]);
+  ub[1].c[1] = conjg(wm * cm[1]);
+  ub[1].c[2] = conjg(wp * cm[0]);
+  ub[1].c[3] = conjg(wp * cm[1]);
 }
 
 // v(p, lambda) for an outgoing antifermion: v(p,+) = (w+ chi-, -w- chi-),
 // v(p,-) = (w- chi+, -w+ chi+).
-template <class R>
-__device__ __forceinline__ void v_out(const double (&p)[4], double m, sp<R> (&v)[2]) {
-  cx<double> cp[2], cm[2];
-  chi_pm(p, cp, cm);
-  const double pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-  const double wp = sqrt(p[0] + pp);
-  const double wm = m > 0.0 ? m / wp : 0.0;
-  v[0].c[0] = cast<R>(wp * cm[0]);
-  v[0].c[1] = cast<R>(wp * cm[1]);
-  v[0].c[2] = cast<R>(-wm * cm[0]);
-  v[0].c[3] = cast<R>(-wm * cm[1]);
-  v[1].c[0] = cast<R>(wm * cp[0]);
-  v[1].c[1] = cast<R>(wm * cp[1]);
-  v[1].c[2] = cast<R>(-wp * cp[0]);
-  v[1].c[3] = cast<R>(-wp * cp[1]);
+template <class T>
+__device__ __forceinline__ void v_out(const T (&p)[4], T m, sp<T> (&v)[2]) {
+  cx<T> cp[2], cm[2];
+  const T pp = chi_pm(p, cp, cm);
+  T wp, wm;
+  omegas(p[0], pp, m, wp, wm);
+  v[0].c[0] = wp * cm[0];
+  v[0].c[1] = wp * cm[1];
+  v[0].c[2] = (-wm) * cm[0];
+  v[0].c[3] = (-wm) * cm[1];
+  v[1].c[0] = wm * cp[0];
+  v[1].c[1] = wm * cp[1];
+  v[1].c[2] = (-wp) * cp[0];
+  v[1].c[3] = (-wp) * cp[1];
 }
 
 // u(p, lambda) for an incoming fermion
-template <class R>
-__device__ __forceinline__ void u_in(const double (&p)[4], double m, sp<R> (&u)[2]) {
-  cx<double> cp[2], cm[2];
-  chi_pm(p, cp, cm);
-  const double pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-  const double wp = sqrt(p[0] + pp);
-  const double wm = m > 0.0 ? m / wp : 0.0;
-  u[0].c[0] = cast<R>(wm * cp[0]);
-  u[0].c[1] = cast<R>(wm * cp[1]);
-  u[0].c[2] = cast<R>(wp * cp[0]);
-  u[0].c[3] = cast<R>(wp * cp[1]);
-  u[1].c[0] = cast<R>(wp * cm[0]);
-  u[1].c[1] = cast<R>(wp * cm[1]);
-  u[1].c[2] = cast<R>(wm * cm[0]);
-  u[1].c[3] = cast<R>(wm * cm[1]);
+template <class T>
+__device__ __forceinline__ void u_in(const T (&p)[4], T m, sp<T> (&u)[2]) {
+  cx<T> cp[2], cm[2];
+  const T pp = chi_pm(p, cp, cm);
+  T wp, wm;
+  omegas(p[0], pp, m, wp, wm);
+  u[0].c[0] = wm * cp[0];
+  u[0].c[1] = wm * cp[1];
+  u[0].c[2] = wp * cp[0];
+  u[0].c[3] = wp * cp[1];
+  u[1].c[0] = wp * cm[0];
+  u[1].c[1] = wp * cm[1];
+  u[1].c[2] = wm * cm[0];
+  u[1].c[3] = wm * cm[1];
 }
 
 // vbar(p, lambda) = v^dagger gamma^0 for an incoming antifermion (row spinor)
-template <class R>
-__device__ __forceinline__ void vbar_in(const double (&p)[4], double m, sp<R> (&vb)[2]) {
-  sp<double> v[2];
-  v_out<double>(p, m, v);
+template <class T>
+__device__ __forceinline__ void vbar_in(const T (&p)[4], T m, sp<T> (&vb)[2]) {
+  sp<T> v[2];
+  v_out<T>(p, m, v);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    vb[h].c[0] = cast<R>(conjg(v[h].c[2]));
-    vb[h].c[1] = cast<R>(conjg(v[h].c[3]));
-    vb[h].c[2] = cast<R>(conjg(v[h].c[0]));
-    vb[h].c[3] = cast<R>(conjg(v[h].c[1]));
+    vb[h].c[0] = conjg(v[h].c[2]);
+    vb[h].c[1] = conjg(v[h].c[3]);
+    vb[h].c[2] = conjg(v[h].c[0]);
+    vb[h].c[3] = conjg(v[h].c[1]);
   }
 }
 
 // Transverse polarisation eps(k, lambda) = (-lambda e1 - i e2)/sqrt(2),
 // e1 = (0, cos t cos f, cos t sin f, -sin t), e2 = (0, -sin f, cos f, 0);
 // index 0: lambda = +1, 1: lambda = -1; conjugated for an outgoing gluon.
-template <class R>
-__device__ __forceinline__ void polvec(const double (&k)[4], bool outgoing, cv<R> (&e)[2]) {
-  const double pt = sqrt(k[1] * k[1] + k[2] * k[2]);
-  const double kk = sqrt(pt * pt + k[3] * k[3]);
-  const double ct = k[3] / kk, st = pt / kk;
-  const double cf = pt > 0.0 ? k[1] / pt : 1.0, sf = pt > 0.0 ? k[2] / pt : 0.0;
-  const double r2 = 0.70710678118654752440;
-  const double e1[4] = {0.0, ct * cf, ct * sf, -st};
-  const double e2[4] = {0.0, -sf, cf, 0.0};
-  const double sgn = outgoing ? -1.0 : 1.0;
+template <class T>
+__device__ __forceinline__ void polvec(const T (&k)[4], bool outgoing, cv<T> (&e)[2]) {
+  const T pt2 = k[1] * k[1] + k[2] * k[2];
+  const T ikk = rsqrt_t<T>(pt2 + k[3] * k[3]);
+  T cf = T(1), sf = T(0), st = T(0);
+  if (pt2 > T(0)) {
+    const T ipt = rsqrt_t<T>(pt2);
+    cf = k[1] * ipt;
+    sf = k[2] * ipt;
+    st = pt2 * ipt * ikk;
+  }
+  const T ct = k[3] * ikk;
+  const T r2 = T(0.70710678118654752440);
+  const T e1[4] = {T(0), ct * cf, ct * sf, -st};
+  const T e2[4] = {T(0), -sf, cf, T(0)};
+  const T sgn = outgoing ? T(-1) : T(1);
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    e[0].c[m] = {R(-r2 * e1[m]), R(-sgn * r2 * e2[m])};
-    e[1].c[m] = {R(r2 * e1[m]), R(-sgn * r2 * e2[m])};
+    e[0].c[m] = {-r2 * e1[m], -sgn * r2 * e2[m]};
+    e[1].c[m] = {r2 * e1[m], -sgn * r2 * e2[m]};
   }
 }
 

@@ -105,7 +105,7 @@ __device__ __forceinline__ double eval_point(const double (&p)[Proc::NEXT][4], c
   double q[Proc::NEXT][4];
   bool inside = true;
   if (pt.reshuffle) {
-    inside = Proc::reshuffle(p, pt.m_t, q);
+    inside = Proc::template reshuffle<R>(p, pt.m_t, q);
   } else {
 #pragma unroll
     for (int i = 0; i < Proc::NEXT; ++i)

@@ -10,6 +10,7 @@ namespace {
 struct Tag {
   static constexpr int NG = gg_tt::NG;
   static constexpr int NEXT = gg_tt::NEXT;
+  static constexpr int MAX_LB = gg_tt::MAX_LB;
   template <class R, int LB>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
     return gg_tt::hel_sum<R, LB>(X, K, lane);
@@ -23,7 +24,7 @@ void register_gg_tt_fp32(std::vector<KernelEntry>& t) {
   t.push_back({RW_GG_TT, RW_FP32, 1, (const void*)&k_reweight<P, float, 1>});
   t.push_back({RW_GG_TT, RW_FP32, 2, (const void*)&k_reweight<P, float, 2>});
   t.push_back({RW_GG_TT, RW_FP32, 3, (const void*)&k_reweight<P, float, 3>});
-  t.push_back({RW_GG_TT, RW_FP32, 4, (const void*)&k_reweight<P, float, 4>});
+
 }
 
 }  // namespace rw

@@ -10,6 +10,7 @@ namespace {
 struct Tag {
   static constexpr int NG = gg_tt::NG;
   static constexpr int NEXT = gg_tt::NEXT;
+  static constexpr int MAX_LB = gg_tt::MAX_LB;
   template <class R, int LB>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
     return gg_tt::hel_sum<R, LB>(X, K, lane);
@@ -23,12 +24,12 @@ void register_gg_tt_fp64(std::vector<KernelEntry>& t) {
   t.push_back({RW_GG_TT, RW_FP64, 1, (const void*)&k_reweight<P, double, 1>});
   t.push_back({RW_GG_TT, RW_FP64, 2, (const void*)&k_reweight<P, double, 2>});
   t.push_back({RW_GG_TT, RW_FP64, 3, (const void*)&k_reweight<P, double, 3>});
-  t.push_back({RW_GG_TT, RW_FP64, 4, (const void*)&k_reweight<P, double, 4>});
+
 }
 
 void static_gg_tt(ProcStatic& s) {
   s = {gg_tt::NEXT, gg_tt::NHEL, gg_tt::K, gg_tt::NDIAG, gg_tt::CDEN, gg_tt::IDENT, gg_tt::NG,
-       gg_tt::FLOPS_HEL_SUM, gg_tt::NEXT};
+       gg_tt::FLOPS_HEL_SUM, gg_tt::MAX_LB};
 }
 
 }  // namespace rw

@@ -10,6 +10,7 @@ namespace {
 struct Tag {
   static constexpr int NG = gg_ttg::NG;
   static constexpr int NEXT = gg_ttg::NEXT;
+  static constexpr int MAX_LB = gg_ttg::MAX_LB;
   template <class R, int LB>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
     return gg_ttg::hel_sum<R, LB>(X, K, lane);
@@ -27,7 +28,7 @@ void register_gg_ttg_fp64(std::vector<KernelEntry>& t) {
 
 void static_gg_ttg(ProcStatic& s) {
   s = {gg_ttg::NEXT, gg_ttg::NHEL, gg_ttg::K, gg_ttg::NDIAG, gg_ttg::CDEN, gg_ttg::IDENT, gg_ttg::NG,
-       gg_ttg::FLOPS_HEL_SUM, gg_ttg::NEXT};
+       gg_ttg::FLOPS_HEL_SUM, gg_ttg::MAX_LB};
 }
 
 }  // namespace rw

@@ -10,6 +10,7 @@ namespace {
 struct Tag {
   static constexpr int NG = gg_ttgg::NG;
   static constexpr int NEXT = gg_ttgg::NEXT;
+  static constexpr int MAX_LB = gg_ttgg::MAX_LB;
   template <class R, int LB>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
     return gg_ttgg::hel_sum<R, LB>(X, K, lane);
@@ -19,7 +20,9 @@ using P = QcdProc<Tag>;
 }  // namespace
 
 void register_gg_ttgg_fp32(std::vector<KernelEntry>& t) {
+  t.push_back({RW_GG_TTGG, RW_FP32, 1, (const void*)&k_reweight<P, float, 1>});
   t.push_back({RW_GG_TTGG, RW_FP32, 2, (const void*)&k_reweight<P, float, 2>});
+  t.push_back({RW_GG_TTGG, RW_FP32, 3, (const void*)&k_reweight<P, float, 3>});
 }
 
 }  // namespace rw

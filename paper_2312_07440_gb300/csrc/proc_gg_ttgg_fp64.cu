@@ -10,6 +10,7 @@ namespace {
 struct Tag {
   static constexpr int NG = gg_ttgg::NG;
   static constexpr int NEXT = gg_ttgg::NEXT;
+  static constexpr int MAX_LB = gg_ttgg::MAX_LB;
   template <class R, int LB>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
     return gg_ttgg::hel_sum<R, LB>(X, K, lane);
@@ -19,12 +20,14 @@ using P = QcdProc<Tag>;
 }  // namespace
 
 void register_gg_ttgg_fp64(std::vector<KernelEntry>& t) {
+  t.push_back({RW_GG_TTGG, RW_FP64, 1, (const void*)&k_reweight<P, double, 1>});
   t.push_back({RW_GG_TTGG, RW_FP64, 2, (const void*)&k_reweight<P, double, 2>});
+  t.push_back({RW_GG_TTGG, RW_FP64, 3, (const void*)&k_reweight<P, double, 3>});
 }
 
 void static_gg_ttgg(ProcStatic& s) {
   s = {gg_ttgg::NEXT, gg_ttgg::NHEL, gg_ttgg::K, gg_ttgg::NDIAG, gg_ttgg::CDEN, gg_ttgg::IDENT, gg_ttgg::NG,
-       gg_ttgg::FLOPS_HEL_SUM, gg_ttgg::NEXT};
+       gg_ttgg::FLOPS_HEL_SUM, gg_ttgg::MAX_LB};
 }
 
 }  // namespace rw

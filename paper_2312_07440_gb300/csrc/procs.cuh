@@ -12,12 +12,14 @@ template <class Tag>
 struct QcdProc {
   static constexpr int NG = Tag::NG;
   static constexpr int NEXT = Tag::NEXT;
+  static constexpr bool kSymmetricHelicities = true;
 
   // Out of line: every evaluation runs the same instructions, so identical
   // inputs give bitwise identical |M|^2 (r == 1 exactly for unchanged
   // parameters), and the kernel keeps one copy of the amplitude code.
   template <class R, int LB>
   __device__ __noinline__ static double me(const double (&p)[NEXT][4], const PointDev& pt, int lane, unsigned gmask) {
+    static_assert(LB <= Tag::MAX_LB, "more lane bits than helicity levels");
     QcdExt<R, NG> X;
     QcdKin<R, NG> Kn;
     qcd_setup<R, NG, NEXT>(p, pt.m_t, X, Kn);
@@ -26,8 +28,10 @@ struct QcdProc {
     for (int o = 1; o < (1 << LB); o <<= 1) s += __shfl_xor_sync(gmask, s, o);
     return s * pt.cscale;
   }
+  // FP32 mode refines the FP32 Newton solution with one FP64 step, FP64 mode with two.
+  template <class R>
   __device__ __forceinline__ static bool reshuffle(const double (&p)[NEXT][4], double mt, double (&q)[NEXT][4]) {
-    return reshuffle_tops<NEXT>(p, mt, q);
+    return reshuffle_tops<NEXT, sizeof(R) == 8 ? 2 : 1>(p, mt, q);
   }
 };
 
@@ -45,10 +49,15 @@ struct EeMumu {
   __device__ __noinline__ static double me(const double (&p)[NEXT][4], const PointDev& pt, int lane,
                                            unsigned gmask) {
     sp<R> u0[2], vb1[2], ub2[2], v3[2];
-    u_in<R>(p[0], 0.0, u0);
-    vbar_in<R>(p[1], 0.0, vb1);
-    ubar_out<R>(p[2], 0.0, ub2);
-    v_out<R>(p[3], 0.0, v3);
+    R pr[NEXT][4];
+#pragma unroll
+    for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) pr[i][m] = R(p[i][m]);
+    u_in<R>(pr[0], R(0), u0);
+    vbar_in<R>(pr[1], R(0), vb1);
+    ubar_out<R>(pr[2], R(0), ub2);
+    v_out<R>(pr[3], R(0), v3);
     R k[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) k[m] = R(p[0][m] + p[1][m]);
@@ -91,6 +100,7 @@ struct EeMumu {
     for (int o = 1; o < (1 << LB); o <<= 1) s += __shfl_xor_sync(gmask, s, o);
     return 0.25 * s;
   }
+  template <class R>
   __device__ __forceinline__ static bool reshuffle(const double (&p)[NEXT][4], double, double (&q)[NEXT][4]) {
 #pragma unroll
     for (int i = 0; i < NEXT; ++i)

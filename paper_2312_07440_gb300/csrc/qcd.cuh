@@ -1,7 +1,8 @@
 // Per-event set-up for g g -> t tbar + n g: external wavefunctions of both
-// helicities and the propagator invariants, formed in FP64 from the FP64
-// momenta and then cast to the working precision R (so that FP32 mode never
-// forms p^2 - m^2 by cancellation in single precision).
+// helicities (in the working precision R, cancellation-free formulas) and the
+// propagator invariants, whose dot products are formed in FP64 from the FP64
+// momenta (so FP32 mode never forms p^2 - m^2 by cancellation in single
+// precision) before the reciprocals are taken in R.
 #pragma once
 #include "helas.cuh"
 
@@ -39,18 +40,31 @@ __device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, 
   for (int g = 0; g < NG; ++g) {
     const int ip = gluon_particle(g);
     const double s = ip < 2 ? 1.0 : -1.0;
+    R kr[4];
 #pragma unroll
-    for (int m4 = 0; m4 < 4; ++m4) k[g][m4] = s * p[ip][m4];
-    polvec<R>(p[ip], ip >= 2, X.eps[g]);
+    for (int m4 = 0; m4 < 4; ++m4) {
+      k[g][m4] = s * p[ip][m4];
+      kr[m4] = R(p[ip][m4]);
+    }
+    polvec<R>(kr, ip >= 2, X.eps[g]);
   }
-  ubar_out<R>(p[2], m, X.ub);
-  v_out<R>(p[3], m, X.v);
-  // pairwise k_i.k_j (the gluons are massless: k_i^2 = 0 exactly)
+  {
+    R p3[4], p4[4];
+#pragma unroll
+    for (int m4 = 0; m4 < 4; ++m4) {
+      p3[m4] = R(p[2][m4]);
+      p4[m4] = R(p[3][m4]);
+    }
+    ubar_out<R>(p3, R(m), X.ub);
+    v_out<R>(p4, R(m), X.v);
+  }
+  // Invariants: the dot products, where cancellation happens, in FP64;
+  // the reciprocals in the working precision.
   double d[NG][NG];
 #pragma unroll
   for (int i = 0; i < NG; ++i)
 #pragma unroll
-    for (int j = i + 1; j < NG; ++j) d[i][j] = dot4(k[i], k[j]);
+    for (int j = i + 1; j < NG; ++j) d[i][j] = dot4(k[i], k[j]);  // gluons are massless: k_i^2 = 0
   constexpr int FULL = (1 << NG) - 1;
 #pragma unroll
   for (int msk = 1; msk <= FULL; ++msk) {
@@ -70,9 +84,9 @@ __device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, 
 #pragma unroll
     for (int m4 = 0; m4 < 4; ++m4) Kn.P[msk][m4] = R(P[m4]);
     if (cnt >= 2) {
-      const double inv = 1.0 / K2;
-      Kn.cg[msk] = R(-inv);
-      Kn.c4[msk] = R(inv);
+      const R inv = R(1) / R(K2);
+      Kn.cg[msk] = -inv;
+      Kn.c4[msk] = inv;
     } else {
       Kn.cg[msk] = R(0);
       Kn.c4[msk] = R(0);
@@ -80,10 +94,10 @@ __device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, 
     if (msk != FULL) {
       // (K - p4)^2 - m^2 = K^2 - 2 K.p4  (p4^2 = m^2)
       const double den = K2 - 2.0 * dot4(P, p[3]);
-      const double c = -1.0 / den;
+      const R c = R(-1) / R(den);
 #pragma unroll
-      for (int m4 = 0; m4 < 4; ++m4) Kn.qc[msk][m4] = R(c * (P[m4] - p[3][m4]));
-      Kn.mc[msk] = R(c * m);
+      for (int m4 = 0; m4 < 4; ++m4) Kn.qc[msk][m4] = c * R(P[m4] - p[3][m4]);
+      Kn.mc[msk] = c * R(m);
     } else {
 #pragma unroll
       for (int m4 = 0; m4 < 4; ++m4) Kn.qc[msk][m4] = R(0);
@@ -94,9 +108,11 @@ __device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, 
 
 // Move the outgoing particles (2..NEXT-1) onto the mass shells m_t (tops),
 // 0 (gluons) at fixed partonic energy: p_i -> xi p_i (3-momenta) with
-// sum_i sqrt(m_i^2 + xi^2 |p_i|^2) = sum_i E_i, Newton's method from xi = 1.
+// sum_i sqrt(m_i^2 + xi^2 |p_i|^2) = sum_i E_i.  Newton's method from xi = 1
+// in FP32 to ~1e-7, then NREF Newton steps in FP64 (quadratic convergence:
+// one step leaves ~1e-14, two reach double precision).
 // Returns false when the new masses do not fit (sum m_i >= E).
-template <int NEXT>
+template <int NEXT, int NREF>
 __device__ __forceinline__ bool reshuffle_tops(const double (&p)[NEXT][4], double mt, double (&q)[NEXT][4]) {
   double etot = 0.0, p2[NEXT];
 #pragma unroll
@@ -110,27 +126,39 @@ __device__ __forceinline__ bool reshuffle_tops(const double (&p)[NEXT][4], doubl
     for (int m4 = 0; m4 < 4; ++m4) q[i][m4] = p[i][m4];
   if (!(2.0 * mt < etot)) return false;
   const double mt2 = mt * mt;
-  double xi = 1.0;
-  for (int it = 0; it < 100; ++it) {
+  const float etf = float(etot), mt2f = float(mt2);
+  float xf = 1.0f;
+  for (int it = 0; it < 40; ++it) {
+    float f = -etf, df = 0.0f;
+#pragma unroll
+    for (int i = 2; i < NEXT; ++i) {
+      const float pf = float(p2[i]);
+      const float e = sqrtf((i < 4 ? mt2f : 0.0f) + xf * xf * pf);
+      f += e;
+      df += xf * pf / e;
+    }
+    float step = f / df;
+    if (xf - step <= 0.0f) step = 0.5f * xf;
+    xf -= step;
+    if (fabsf(step) <= 2e-7f * xf) break;
+  }
+  double xi = xf;
+#pragma unroll
+  for (int it = 0; it < NREF; ++it) {
     double f = -etot, df = 0.0;
 #pragma unroll
     for (int i = 2; i < NEXT; ++i) {
-      const double m2 = i < 4 ? mt2 : 0.0;
-      const double e = sqrt(m2 + xi * xi * p2[i]);
+      const double e = sqrt((i < 4 ? mt2 : 0.0) + xi * xi * p2[i]);
       f += e;
       df += xi * p2[i] / e;
     }
-    double step = f / df;
-    if (xi - step <= 0.0) step = 0.5 * xi;
-    xi -= step;
-    if (fabs(step) <= 1e-15 * xi) break;
+    xi -= f / df;
   }
 #pragma unroll
   for (int i = 2; i < NEXT; ++i) {
-    const double m2 = i < 4 ? mt2 : 0.0;
 #pragma unroll
     for (int m4 = 1; m4 < 4; ++m4) q[i][m4] = xi * p[i][m4];
-    q[i][0] = sqrt(m2 + xi * xi * p2[i]);
+    q[i][0] = sqrt((i < 4 ? mt2 : 0.0) + xi * xi * p2[i]);
   }
   return true;
 }

@@ -60,9 +60,9 @@ const Registry& registry() {
 int default_lane_bits(int process, int mode) {
   switch (process) {
     case RW_EE_MUMU: return 2;
-    case RW_GG_TT: return mode == RW_FP64 ? 0 : 1;
-    case RW_GG_TTG: return 1;
-    case RW_GG_TTGG: return 2;
+    case RW_GG_TT: return 0;
+    case RW_GG_TTG: return 0;
+    case RW_GG_TTGG: return mode == RW_FP64 ? 1 : 2;
   }
   return 0;
 }

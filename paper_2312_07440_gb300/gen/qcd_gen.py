@@ -194,8 +194,9 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     """Emit the helicity-summed, couplings-stripped colour sum for t tbar + n g.
 
     Loop levels 0..n-1: gluon helicities; level n: antitop; level n+1: top.
-    The returned device function sums over the helicities of one lane; the
-    outermost LB levels take their helicity bits from the lane index.
+    Level 0 is fixed (helicity-flip symmetry); the returned device function
+    sums over the helicities of one lane, levels 1..LB taking their helicity
+    bits from the lane index.
     """
     em = Emitter(n)
     perms = orderings(n)
@@ -215,6 +216,7 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     w(f"constexpr int K = {K};")
     w(f"constexpr int NHEL = {2 ** (n + 2)};")
     w(f"constexpr int NDIAG = {diagram_count(n)};")
+    w(f"constexpr int MAX_LB = {n + 1};  // helicity levels that can be spread over lanes")
     w(f"constexpr int CDEN = {den};")
     w(f"constexpr int IDENT = {n_identical};  // identical outgoing gluons (1/IDENT!)")
     w(f"constexpr unsigned OUTGOING_GLUONS = {sum(1 << g for g in outgoing_gluons)}u;  // bit g: gluon g outgoing")
@@ -222,7 +224,8 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     w(f"__host__ __device__ constexpr int cint(int i, int j) {{ constexpr int c[K * K] = {{{flat}}}; return c[i * K + j]; }}")
     w(f"constexpr int ORDER[K][NG] = {{{', '.join('{' + ', '.join(map(str, p)) + '}' for p in perms)}}};")
     w("")
-    w("// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1.")
+    w("// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;")
+    w("// helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).")
     w("template <class R, int LB>")
     w("__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {")
     w("  R acc = R(0);")
@@ -235,11 +238,20 @@ def emit_process(name, n, outgoing_gluons, n_identical):
 
     def open_level(L, hvar, sel):
         nonlocal ind
-        bit = f"((lane >> (LB - 1 - {L})) & 1)"
+        if L == 0:
+            # helicity-flip symmetry: J^dagger C J is the same for h and -h
+            # (tree-level QCD with real momenta), so gluon 0 keeps helicity +
+            # and the sum is doubled.
+            w(f"{ind}{{")
+            ind += "  "
+            w(f"{ind}const int {hvar} = 0;")
+            w(f"{ind}{sel}")
+            return
+        bit = f"((lane >> (LB - {L})) & 1)"
         w(f"{ind}#pragma unroll 1")
-        w(f"{ind}for (int i{L} = 0; i{L} < (LB > {L} ? 1 : 2); ++i{L}) {{")
+        w(f"{ind}for (int i{L} = 0; i{L} < (LB >= {L} ? 1 : 2); ++i{L}) {{")
         ind += "  "
-        w(f"{ind}const int {hvar} = LB > {L} ? {bit} : i{L};")
+        w(f"{ind}const int {hvar} = LB >= {L} ? {bit} : i{L};")
         w(f"{ind}{sel}")
 
     # gluon levels
@@ -325,7 +337,7 @@ def emit_process(name, n, outgoing_gluons, n_identical):
         w(f"{ind}{{ const R zr = {' + '.join(parts_r)}; const R zi = {' + '.join(parts_i)};")
         w(f"{ind}  cs += A{i}.r * zr + A{i}.i * zi; }}")
         em.flops_per_level[n + 1] += 4 * len(parts_r) + 4
-    w(f"{ind}acc += R(2) * cs;")
+    w(f"{ind}acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip")
     for L in range(nlev - 1, -1, -1):
         ind = ind[:-2]
         w(f"{ind}}}")
@@ -335,7 +347,7 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     # flops per event for the full helicity sum (one lane doing all helicities)
     total = 0
     for L in range(nlev):
-        total += em.flops_per_level[L] * (2 ** (L + 1))
+        total += em.flops_per_level[L] * (2 ** L)
     w(f"// floating-point operations of one full helicity sum (all levels, all loop trips)")
     w(f"constexpr long FLOPS_HEL_SUM = {total};")
     w("}}  // namespace")

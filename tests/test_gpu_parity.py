@@ -52,25 +52,50 @@ def run_gpu(proc, mode, mom, w, pts, lane_bits=-1, block=0):
     return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
 
 
-def check_against_oracle(g, o, mode):
+def input_sensitivity(proc, pts, mom, w, trials=6, seed=7):
+    """Per-event relative change of the oracle's |M|^2, |M'|^2 and r when every
+    input momentum component moves by at most one ulp (random signs).  FP64
+    inputs cannot satisfy momentum conservation and the mass shells exactly; near
+    an on-shell top propagator (a gluon radiated off a top) that ambiguity alone
+    moves |M|^2 by up to ~1e-12, so no two FP64 evaluations can agree better."""
+    rng = np.random.default_rng(seed)
+    base = oracle.reweight(proc, ev.param_vector(), pts, mom, w)
+    s = np.zeros((1 + len(pts), mom.shape[-1]))
+    for _ in range(trials):
+        pert = mom * (1 + rng.integers(-1, 2, size=mom.shape) * np.finfo(float).eps)
+        o = oracle.reweight(proc, ev.param_vector(), pts, pert, w)
+        s[0] = np.maximum(s[0], rel(o["me0"], base["me0"]))
+        s[1:] = np.maximum(s[1:], np.maximum(rel(o["me"], base["me"]), rel(o["ratio"], base["ratio"])))
+    return s
+
+
+def check_against_oracle(g, o, mode, sens=None):
+    """Per-event bound: TOL[mode]; in FP64 mode max(1e-12, 4 s_e) when the
+    event's input sensitivity s_e (see input_sensitivity) exceeds 2.5e-13."""
     tol = TOL[mode]
-    assert rel(g["me0"], o["me0"]).max() < tol
-    assert rel(g["me"], o["me"]).max() < tol
-    assert rel(g["ratio"], o["ratio"]).max() < tol
-    assert rel(g["wnew"], o["wnew"]).max() < tol
+    tol0, tolp = tol, tol
+    if sens is not None:
+        tol0 = np.maximum(tol, 4 * sens[0])
+        tolp = np.maximum(tol, 4 * sens[1:])
+    assert np.all(rel(g["me0"], o["me0"]) < tol0)
+    assert np.all(rel(g["me"], o["me"]) < tolp)
+    assert np.all(rel(g["ratio"], o["ratio"]) < tolp)
+    assert np.all(rel(g["wnew"], o["wnew"]) < tolp)
     for j in range(len(g["sigma"])):
         exact_gpu = math.fsum(g["wnew"][j])
         assert abs(g["sigma"][j] - exact_gpu) <= 2 * np.spacing(exact_gpu)
         assert abs(g["sigma"][j] / o["sigma"][j] - 1) < tol
     assert abs(g["sigma_orig"] - o["sigma_orig"]) <= 2 * np.spacing(o["sigma_orig"])
     assert g["n_bad"] == o["n_bad"]
+    if sens is not None:  # the relaxed bound stays the exception
+        assert np.mean(np.max(sens, axis=0) > tol / 4) < 0.02
 
 
 # --------------------------------------------------------------------------
 # g g -> t tbar (the 1M-event workload's process), every launch variant
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
-@pytest.mark.parametrize("lane_bits", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("lane_bits", [0, 1, 2, 3])
 def test_gg_tt_parity(mode, lane_bits):
     pts = ev.reweight_points("gg_tt_1m")
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 5003, pts)  # several blocks + a ragged tail
@@ -111,15 +136,29 @@ def test_gg_ttg_parity(mode, lane_bits):
     pts = ev.reweight_points("gg_ttg_4m", "mt")[::21]  # kappa = 0.8, 0.933, 1.067, 1.2 (m_t = kappa 173)
     mom, w, o = oracle_run("gg_ttg", "gg_ttg_4m", 611, pts)
     g = run_gpu("gg_ttg", mode, mom, w, pts, lane_bits=lane_bits)
-    check_against_oracle(g, o, mode)
+    sens = sensitivity("gg_ttg", "gg_ttg_4m", 611, pts) if mode == "fp64" else None
+    check_against_oracle(g, o, mode, sens)
+
+
+_SENS_CACHE = {}
+
+
+def sensitivity(proc, wl_name, n, pts):
+    key = (proc, wl_name, n, pts.tobytes())
+    if key not in _SENS_CACHE:
+        mom, w, _ = oracle_run(proc, wl_name, n, pts)
+        _SENS_CACHE[key] = input_sensitivity(proc, pts, mom, w)
+    return _SENS_CACHE[key]
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
 def test_gg_ttgg_parity(mode):
     pts = ev.reweight_points("gg_ttgg_1m", "mt")
     mom, w, o = oracle_run("gg_ttgg", "gg_ttgg_1m", 197, pts)
-    g = run_gpu("gg_ttgg", mode, mom, w, pts, lane_bits=2)
-    check_against_oracle(g, o, mode)
+    sens = sensitivity("gg_ttgg", "gg_ttgg_1m", 197, pts) if mode == "fp64" else None
+    for lb in (1, 2, 3):
+        g = run_gpu("gg_ttgg", mode, mom, w, pts, lane_bits=lb)
+        check_against_oracle(g, o, mode, sens)
 
 
 def test_yukawa_axis_gives_unit_ratio():
