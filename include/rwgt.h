@@ -68,8 +68,11 @@ extern "C" {
 
 /* precision modes of the amplitude arithmetic; momenta, propagator
    invariants, r, W' and sigma are FP64 in every mode */
-#define RW_FP64 0
-#define RW_FP32 1
+#define RW_FP64 0       /* FP64 amplitudes and colour sum */
+#define RW_FP32 1       /* FP32 amplitudes and colour sum */
+#define RW_MIXED_FP16 2 /* FP32 amplitudes, colour sum on the tensor cores in FP16 (power-of-two
+                           scaled rows) with FP32 accumulation; QCD processes; blocks <= 128 */
+#define RW_MIXED_BF16 3 /* as RW_MIXED_FP16 with BF16 operands */
 
 #define RW_MAX_POINTS 256
 
@@ -113,6 +116,19 @@ int rw_set_reweight_points(rw_ctx* ctx, const rw_params* pts, int P);
 /* Launch shape: lanes per event = 2^lane_bits (-1 = default), threads per
    block (multiple of 32, <= 256; 0 = default). */
 int rw_set_tuning(rw_ctx* ctx, int lane_bits, int block);
+
+/* The launch shape in use (after rw_set_tuning or rw_autotune). */
+int rw_get_tuning(const rw_ctx* ctx, int* lane_bits, int* block);
+/* Autotuner: times every compiled lanes-per-event variant x block size in
+   {64, 128, 256} on the first min(E, max_events) attached events (CUDA events
+   on the context's stream, median of 3 launches after one warm-up), keeps the
+   fastest with rw_set_tuning and returns its time per launch in *ms (may be
+   NULL).  Events must be loaded.  cache_path (may be NULL): a JSON-lines file of
+   {"key": "<gpu>|<process>|<mode>|P<points>|E<2^k>", "lane_bits", "block", "ms"};
+   a matching entry is used without timing, a new result is appended.
+   Synchronises the stream; results are unchanged by the choice (every variant
+   computes the same sums; the sigma reduction order follows the grid). */
+int rw_autotune(rw_ctx* ctx, int64_t max_events, const char* cache_path, double* ms);
 
 /* Device workspace needed for E events with the current points (bytes). */
 size_t rw_workspace_bytes(const rw_ctx* ctx, int64_t n_events);

@@ -2,6 +2,7 @@
 // 3 Feynman diagrams, 2 colour orderings, 16 helicities.
 // colour matrix C = Cint / 3
 #pragma once
+#include "colour_mma.cuh"
 #include "qcd.cuh"
 
 namespace rw { namespace gg_tt {
@@ -16,11 +17,15 @@ constexpr int IDENT = 1;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 0u;  // bit g: gluon g outgoing
 __host__ __device__ constexpr int cint(int i, int j) { constexpr int c[K * K] = {16, -2, -2, 16}; return c[i * K + j]; }
 constexpr int ORDER[K][NG] = {{0, 1}, {1, 0}};
+static __device__ const short CI[K * K] = {16, -2, -2, 16};  // row-major C_int for the tensor-core sum
 
 // Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;
 // helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).
-template <class R, int LB>
+// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float).
+template <class R, int LB, int CM = CM_FMA>
 __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
+  static_assert(CM == CM_FMA || sizeof(R) == 4, "tensor-core colour sum takes FP32 amplitudes");
+  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI);
   R acc = R(0);
   {
     const int h0 = 0;
@@ -48,12 +53,17 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
           const cv<R> F_1 = fcur(UB, S_1);
           const cx<R> A0 = dot(E0, F_1) + dot(J0_1, F_E);
           const cx<R> A1 = dot(E1, F_0) + dot(J1_0, F_E);
-          R cs = R(0);
-          { const R zr = R(16) * R(0.5) * A0.r + R(-2) * A1.r; const R zi = R(16) * R(0.5) * A0.i + R(-2) * A1.i;
-            cs += A0.r * zr + A0.i * zi; }
-          { const R zr = R(16) * R(0.5) * A1.r; const R zi = R(16) * R(0.5) * A1.i;
-            cs += A1.r * zr + A1.i * zi; }
-          acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
+          if constexpr (CM != CM_FMA) {
+            const cx<float> Aa[K] = {A0, A1};
+            acc += R(2) * cmma.sum(Aa);  // x2 helicity flip
+          } else {
+            R cs = R(0);
+            { const R zr = R(16) * R(0.5) * A0.r + R(-2) * A1.r; const R zi = R(16) * R(0.5) * A0.i + R(-2) * A1.i;
+              cs += A0.r * zr + A0.i * zi; }
+            { const R zr = R(16) * R(0.5) * A1.r; const R zi = R(16) * R(0.5) * A1.i;
+              cs += A1.r * zr + A1.i * zi; }
+            acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
+          }
         }
       }
     }

@@ -2,6 +2,7 @@
 // 16 Feynman diagrams, 6 colour orderings, 32 helicities.
 // colour matrix C = Cint / 9
 #pragma once
+#include "colour_mma.cuh"
 #include "qcd.cuh"
 
 namespace rw { namespace gg_ttg {
@@ -16,11 +17,15 @@ constexpr int IDENT = 1;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 4u;  // bit g: gluon g outgoing
 __host__ __device__ constexpr int cint(int i, int j) { constexpr int c[K * K] = {64, -8, -8, 1, 1, 10, -8, 64, 1, 10, -8, 1, -8, 1, 64, -8, 10, 1, 1, 10, -8, 64, 1, -8, 1, -8, 10, 1, 64, -8, 10, 1, 1, -8, -8, 64}; return c[i * K + j]; }
 constexpr int ORDER[K][NG] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+static __device__ const short CI[K * K] = {64, -8, -8, 1, 1, 10, -8, 64, 1, 10, -8, 1, -8, 1, 64, -8, 10, 1, 1, 10, -8, 64, 1, -8, 1, -8, 10, 1, 64, -8, 10, 1, 1, -8, -8, 64};  // row-major C_int for the tensor-core sum
 
 // Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;
 // helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).
-template <class R, int LB>
+// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float).
+template <class R, int LB, int CM = CM_FMA>
 __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
+  static_assert(CM == CM_FMA || sizeof(R) == 4, "tensor-core colour sum takes FP32 amplitudes");
+  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI);
   R acc = R(0);
   {
     const int h0 = 0;
@@ -99,20 +104,25 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             const cx<R> A3 = dot(E1, F_2_0) + dot(J1_2, F_0) + dot(J1_2_0, F_E);
             const cx<R> A4 = dot(E2, F_0_1) + dot(J2_0, F_1) + dot(J2_0_1, F_E);
             const cx<R> A5 = dot(E2, F_1_0) + dot(J2_1, F_0) + dot(J2_1_0, F_E);
-            R cs = R(0);
-            { const R zr = R(64) * R(0.5) * A0.r + R(-8) * A1.r + R(-8) * A2.r + R(1) * A3.r + R(1) * A4.r + R(10) * A5.r; const R zi = R(64) * R(0.5) * A0.i + R(-8) * A1.i + R(-8) * A2.i + R(1) * A3.i + R(1) * A4.i + R(10) * A5.i;
-              cs += A0.r * zr + A0.i * zi; }
-            { const R zr = R(64) * R(0.5) * A1.r + R(1) * A2.r + R(10) * A3.r + R(-8) * A4.r + R(1) * A5.r; const R zi = R(64) * R(0.5) * A1.i + R(1) * A2.i + R(10) * A3.i + R(-8) * A4.i + R(1) * A5.i;
-              cs += A1.r * zr + A1.i * zi; }
-            { const R zr = R(64) * R(0.5) * A2.r + R(-8) * A3.r + R(10) * A4.r + R(1) * A5.r; const R zi = R(64) * R(0.5) * A2.i + R(-8) * A3.i + R(10) * A4.i + R(1) * A5.i;
-              cs += A2.r * zr + A2.i * zi; }
-            { const R zr = R(64) * R(0.5) * A3.r + R(1) * A4.r + R(-8) * A5.r; const R zi = R(64) * R(0.5) * A3.i + R(1) * A4.i + R(-8) * A5.i;
-              cs += A3.r * zr + A3.i * zi; }
-            { const R zr = R(64) * R(0.5) * A4.r + R(-8) * A5.r; const R zi = R(64) * R(0.5) * A4.i + R(-8) * A5.i;
-              cs += A4.r * zr + A4.i * zi; }
-            { const R zr = R(64) * R(0.5) * A5.r; const R zi = R(64) * R(0.5) * A5.i;
-              cs += A5.r * zr + A5.i * zi; }
-            acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
+            if constexpr (CM != CM_FMA) {
+              const cx<float> Aa[K] = {A0, A1, A2, A3, A4, A5};
+              acc += R(2) * cmma.sum(Aa);  // x2 helicity flip
+            } else {
+              R cs = R(0);
+              { const R zr = R(64) * R(0.5) * A0.r + R(-8) * A1.r + R(-8) * A2.r + R(1) * A3.r + R(1) * A4.r + R(10) * A5.r; const R zi = R(64) * R(0.5) * A0.i + R(-8) * A1.i + R(-8) * A2.i + R(1) * A3.i + R(1) * A4.i + R(10) * A5.i;
+                cs += A0.r * zr + A0.i * zi; }
+              { const R zr = R(64) * R(0.5) * A1.r + R(1) * A2.r + R(10) * A3.r + R(-8) * A4.r + R(1) * A5.r; const R zi = R(64) * R(0.5) * A1.i + R(1) * A2.i + R(10) * A3.i + R(-8) * A4.i + R(1) * A5.i;
+                cs += A1.r * zr + A1.i * zi; }
+              { const R zr = R(64) * R(0.5) * A2.r + R(-8) * A3.r + R(10) * A4.r + R(1) * A5.r; const R zi = R(64) * R(0.5) * A2.i + R(-8) * A3.i + R(10) * A4.i + R(1) * A5.i;
+                cs += A2.r * zr + A2.i * zi; }
+              { const R zr = R(64) * R(0.5) * A3.r + R(1) * A4.r + R(-8) * A5.r; const R zi = R(64) * R(0.5) * A3.i + R(1) * A4.i + R(-8) * A5.i;
+                cs += A3.r * zr + A3.i * zi; }
+              { const R zr = R(64) * R(0.5) * A4.r + R(-8) * A5.r; const R zi = R(64) * R(0.5) * A4.i + R(-8) * A5.i;
+                cs += A4.r * zr + A4.i * zi; }
+              { const R zr = R(64) * R(0.5) * A5.r; const R zi = R(64) * R(0.5) * A5.i;
+                cs += A5.r * zr + A5.i * zi; }
+              acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
+            }
           }
         }
       }

@@ -2,6 +2,7 @@
 // 123 Feynman diagrams, 24 colour orderings, 64 helicities.
 // colour matrix C = Cint / 54
 #pragma once
+#include "colour_mma.cuh"
 #include "qcd.cuh"
 
 namespace rw { namespace gg_ttgg {
@@ -16,11 +17,15 @@ constexpr int IDENT = 2;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 12u;  // bit g: gluon g outgoing
 __host__ __device__ constexpr int cint(int i, int j) { constexpr int c[K * K] = {512, -64, -64, 8, 8, 80, -64, 8, 8, -1, -1, -10, 8, -1, 80, -10, 71, 62, -1, -10, -10, 62, 62, -28, -64, 512, 8, 80, -64, 8, 8, -64, -1, -10, 8, -1, -1, -10, -10, 62, 62, -28, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, 80, -10, 71, 62, -64, 8, 8, -1, -1, -10, -10, -1, 62, -28, -10, 62, 8, 80, -64, 512, 8, -64, -1, -10, -10, 62, 62, -28, 8, -64, -1, -10, 8, -1, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, -1, 8, 71, 62, 80, -10, -10, -1, 62, -28, -10, 62, -64, 8, 8, -1, -1, -10, 80, 8, 8, -64, -64, 512, -10, -1, 62, -28, -10, 62, -1, 8, 71, 62, 80, -10, 8, -64, -1, -10, 8, -1, -64, 8, 8, -1, -1, -10, 512, -64, -64, 8, 8, 80, 80, -10, 8, -1, 62, 71, -10, 62, -1, -10, -28, 62, 8, -64, -1, -10, 8, -1, -64, 512, 8, 80, -64, 8, -10, 62, -1, -10, -28, 62, 80, -10, 8, -1, 62, 71, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, -64, 8, -10, -1, 62, -28, -10, -1, 62, -10, -1, -10, -10, 62, 62, -28, 8, 80, -64, 512, 8, -64, -1, -10, 8, -64, -1, 8, 71, 62, -1, 8, -10, 80, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, 62, -28, -10, -1, 62, -10, 8, -1, -64, 8, -10, -1, -10, -1, 62, -28, -10, 62, 80, 8, 8, -64, -64, 512, 71, 62, -1, 8, -10, 80, -1, -10, 8, -64, -1, 8, 8, -1, -64, 8, -10, -1, 80, -10, 8, -1, 62, 71, 512, -64, -64, 8, 8, 80, 62, -10, -28, 62, -1, -10, -1, -10, 8, -64, -1, 8, -10, 62, -1, -10, -28, 62, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, 80, -10, 8, -1, 62, 71, 8, -1, -64, 8, -10, -1, -64, 8, 512, -64, 80, 8, -28, 62, 62, -10, -10, -1, -10, 62, -1, -10, -28, 62, -1, -10, 8, -64, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, 71, 62, -1, 8, -10, 80, 62, -28, -10, -1, 62, -10, 8, -64, 80, 8, 512, -64, -1, 8, -10, -1, -64, 8, 62, -28, -10, -1, 62, -10, 71, 62, -1, 8, -10, 80, 80, 8, 8, -64, -64, 512, -10, -1, -1, 8, 8, -64, -1, 8, -10, -1, -64, 8, -10, 80, 62, 71, 8, -1, 62, -10, -28, 62, -1, -10, 512, -64, -64, 8, 8, 80, -10, -1, -1, 8, 8, -64, 62, -10, -28, 62, -1, -10, -10, 80, 62, 71, 8, -1, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, -1, 8, -10, -1, -64, 8, -28, 62, 62, -10, -10, -1, -64, 8, 512, -64, 80, 8, 62, -10, -28, 62, -1, -10, -10, -1, -1, 8, 8, -64, 62, 71, -10, 80, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, -28, 62, 62, -10, -10, -1, -1, 8, -10, -1, -64, 8, 8, -64, 80, 8, 512, -64, -28, 62, 62, -10, -10, -1, 62, 71, -10, 80, -1, 8, -10, -1, -1, 8, 8, -64, 80, 8, 8, -64, -64, 512}; return c[i * K + j]; }
 constexpr int ORDER[K][NG] = {{0, 1, 2, 3}, {0, 1, 3, 2}, {0, 2, 1, 3}, {0, 2, 3, 1}, {0, 3, 1, 2}, {0, 3, 2, 1}, {1, 0, 2, 3}, {1, 0, 3, 2}, {1, 2, 0, 3}, {1, 2, 3, 0}, {1, 3, 0, 2}, {1, 3, 2, 0}, {2, 0, 1, 3}, {2, 0, 3, 1}, {2, 1, 0, 3}, {2, 1, 3, 0}, {2, 3, 0, 1}, {2, 3, 1, 0}, {3, 0, 1, 2}, {3, 0, 2, 1}, {3, 1, 0, 2}, {3, 1, 2, 0}, {3, 2, 0, 1}, {3, 2, 1, 0}};
+static __device__ const short CI[K * K] = {512, -64, -64, 8, 8, 80, -64, 8, 8, -1, -1, -10, 8, -1, 80, -10, 71, 62, -1, -10, -10, 62, 62, -28, -64, 512, 8, 80, -64, 8, 8, -64, -1, -10, 8, -1, -1, -10, -10, 62, 62, -28, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, 80, -10, 71, 62, -64, 8, 8, -1, -1, -10, -10, -1, 62, -28, -10, 62, 8, 80, -64, 512, 8, -64, -1, -10, -10, 62, 62, -28, 8, -64, -1, -10, 8, -1, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, -1, 8, 71, 62, 80, -10, -10, -1, 62, -28, -10, 62, -64, 8, 8, -1, -1, -10, 80, 8, 8, -64, -64, 512, -10, -1, 62, -28, -10, 62, -1, 8, 71, 62, 80, -10, 8, -64, -1, -10, 8, -1, -64, 8, 8, -1, -1, -10, 512, -64, -64, 8, 8, 80, 80, -10, 8, -1, 62, 71, -10, 62, -1, -10, -28, 62, 8, -64, -1, -10, 8, -1, -64, 512, 8, 80, -64, 8, -10, 62, -1, -10, -28, 62, 80, -10, 8, -1, 62, 71, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, -64, 8, -10, -1, 62, -28, -10, -1, 62, -10, -1, -10, -10, 62, 62, -28, 8, 80, -64, 512, 8, -64, -1, -10, 8, -64, -1, 8, 71, 62, -1, 8, -10, 80, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, 62, -28, -10, -1, 62, -10, 8, -1, -64, 8, -10, -1, -10, -1, 62, -28, -10, 62, 80, 8, 8, -64, -64, 512, 71, 62, -1, 8, -10, 80, -1, -10, 8, -64, -1, 8, 8, -1, -64, 8, -10, -1, 80, -10, 8, -1, 62, 71, 512, -64, -64, 8, 8, 80, 62, -10, -28, 62, -1, -10, -1, -10, 8, -64, -1, 8, -10, 62, -1, -10, -28, 62, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, 80, -10, 8, -1, 62, 71, 8, -1, -64, 8, -10, -1, -64, 8, 512, -64, 80, 8, -28, 62, 62, -10, -10, -1, -10, 62, -1, -10, -28, 62, -1, -10, 8, -64, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, 71, 62, -1, 8, -10, 80, 62, -28, -10, -1, 62, -10, 8, -64, 80, 8, 512, -64, -1, 8, -10, -1, -64, 8, 62, -28, -10, -1, 62, -10, 71, 62, -1, 8, -10, 80, 80, 8, 8, -64, -64, 512, -10, -1, -1, 8, 8, -64, -1, 8, -10, -1, -64, 8, -10, 80, 62, 71, 8, -1, 62, -10, -28, 62, -1, -10, 512, -64, -64, 8, 8, 80, -10, -1, -1, 8, 8, -64, 62, -10, -28, 62, -1, -10, -10, 80, 62, 71, 8, -1, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, -1, 8, -10, -1, -64, 8, -28, 62, 62, -10, -10, -1, -64, 8, 512, -64, 80, 8, 62, -10, -28, 62, -1, -10, -10, -1, -1, 8, 8, -64, 62, 71, -10, 80, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, -28, 62, 62, -10, -10, -1, -1, 8, -10, -1, -64, 8, 8, -64, 80, 8, 512, -64, -28, 62, 62, -10, -10, -1, 62, 71, -10, 80, -1, 8, -10, -1, -1, 8, 8, -64, 80, 8, 8, -64, -64, 512};  // row-major C_int for the tensor-core sum
 
 // Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;
 // helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).
-template <class R, int LB>
+// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float).
+template <class R, int LB, int CM = CM_FMA>
 __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
+  static_assert(CM == CM_FMA || sizeof(R) == 4, "tensor-core colour sum takes FP32 amplitudes");
+  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI);
   R acc = R(0);
   {
     const int h0 = 0;
@@ -394,56 +399,61 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
               const cx<R> A21 = dot(E3, F_1_2_0) + dot(J3_1, F_2_0) + dot(J3_1_2, F_0) + dot(J3_1_2_0, F_E);
               const cx<R> A22 = dot(E3, F_2_0_1) + dot(J3_2, F_0_1) + dot(J3_2_0, F_1) + dot(J3_2_0_1, F_E);
               const cx<R> A23 = dot(E3, F_2_1_0) + dot(J3_2, F_1_0) + dot(J3_2_1, F_0) + dot(J3_2_1_0, F_E);
-              R cs = R(0);
-              { const R zr = R(512) * R(0.5) * A0.r + R(-64) * A1.r + R(-64) * A2.r + R(8) * A3.r + R(8) * A4.r + R(80) * A5.r + R(-64) * A6.r + R(8) * A7.r + R(8) * A8.r + R(-1) * A9.r + R(-1) * A10.r + R(-10) * A11.r + R(8) * A12.r + R(-1) * A13.r + R(80) * A14.r + R(-10) * A15.r + R(71) * A16.r + R(62) * A17.r + R(-1) * A18.r + R(-10) * A19.r + R(-10) * A20.r + R(62) * A21.r + R(62) * A22.r + R(-28) * A23.r; const R zi = R(512) * R(0.5) * A0.i + R(-64) * A1.i + R(-64) * A2.i + R(8) * A3.i + R(8) * A4.i + R(80) * A5.i + R(-64) * A6.i + R(8) * A7.i + R(8) * A8.i + R(-1) * A9.i + R(-1) * A10.i + R(-10) * A11.i + R(8) * A12.i + R(-1) * A13.i + R(80) * A14.i + R(-10) * A15.i + R(71) * A16.i + R(62) * A17.i + R(-1) * A18.i + R(-10) * A19.i + R(-10) * A20.i + R(62) * A21.i + R(62) * A22.i + R(-28) * A23.i;
-                cs += A0.r * zr + A0.i * zi; }
-              { const R zr = R(512) * R(0.5) * A1.r + R(8) * A2.r + R(80) * A3.r + R(-64) * A4.r + R(8) * A5.r + R(8) * A6.r + R(-64) * A7.r + R(-1) * A8.r + R(-10) * A9.r + R(8) * A10.r + R(-1) * A11.r + R(-1) * A12.r + R(-10) * A13.r + R(-10) * A14.r + R(62) * A15.r + R(62) * A16.r + R(-28) * A17.r + R(8) * A18.r + R(-1) * A19.r + R(80) * A20.r + R(-10) * A21.r + R(71) * A22.r + R(62) * A23.r; const R zi = R(512) * R(0.5) * A1.i + R(8) * A2.i + R(80) * A3.i + R(-64) * A4.i + R(8) * A5.i + R(8) * A6.i + R(-64) * A7.i + R(-1) * A8.i + R(-10) * A9.i + R(8) * A10.i + R(-1) * A11.i + R(-1) * A12.i + R(-10) * A13.i + R(-10) * A14.i + R(62) * A15.i + R(62) * A16.i + R(-28) * A17.i + R(8) * A18.i + R(-1) * A19.i + R(80) * A20.i + R(-10) * A21.i + R(71) * A22.i + R(62) * A23.i;
-                cs += A1.r * zr + A1.i * zi; }
-              { const R zr = R(512) * R(0.5) * A2.r + R(-64) * A3.r + R(80) * A4.r + R(8) * A5.r + R(8) * A6.r + R(-1) * A7.r + R(80) * A8.r + R(-10) * A9.r + R(71) * A10.r + R(62) * A11.r + R(-64) * A12.r + R(8) * A13.r + R(8) * A14.r + R(-1) * A15.r + R(-1) * A16.r + R(-10) * A17.r + R(-10) * A18.r + R(-1) * A19.r + R(62) * A20.r + R(-28) * A21.r + R(-10) * A22.r + R(62) * A23.r; const R zi = R(512) * R(0.5) * A2.i + R(-64) * A3.i + R(80) * A4.i + R(8) * A5.i + R(8) * A6.i + R(-1) * A7.i + R(80) * A8.i + R(-10) * A9.i + R(71) * A10.i + R(62) * A11.i + R(-64) * A12.i + R(8) * A13.i + R(8) * A14.i + R(-1) * A15.i + R(-1) * A16.i + R(-10) * A17.i + R(-10) * A18.i + R(-1) * A19.i + R(62) * A20.i + R(-28) * A21.i + R(-10) * A22.i + R(62) * A23.i;
-                cs += A2.r * zr + A2.i * zi; }
-              { const R zr = R(512) * R(0.5) * A3.r + R(8) * A4.r + R(-64) * A5.r + R(-1) * A6.r + R(-10) * A7.r + R(-10) * A8.r + R(62) * A9.r + R(62) * A10.r + R(-28) * A11.r + R(8) * A12.r + R(-64) * A13.r + R(-1) * A14.r + R(-10) * A15.r + R(8) * A16.r + R(-1) * A17.r + R(-1) * A18.r + R(8) * A19.r + R(71) * A20.r + R(62) * A21.r + R(80) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A3.i + R(8) * A4.i + R(-64) * A5.i + R(-1) * A6.i + R(-10) * A7.i + R(-10) * A8.i + R(62) * A9.i + R(62) * A10.i + R(-28) * A11.i + R(8) * A12.i + R(-64) * A13.i + R(-1) * A14.i + R(-10) * A15.i + R(8) * A16.i + R(-1) * A17.i + R(-1) * A18.i + R(8) * A19.i + R(71) * A20.i + R(62) * A21.i + R(80) * A22.i + R(-10) * A23.i;
-                cs += A3.r * zr + A3.i * zi; }
-              { const R zr = R(512) * R(0.5) * A4.r + R(-64) * A5.r + R(-1) * A6.r + R(8) * A7.r + R(71) * A8.r + R(62) * A9.r + R(80) * A10.r + R(-10) * A11.r + R(-10) * A12.r + R(-1) * A13.r + R(62) * A14.r + R(-28) * A15.r + R(-10) * A16.r + R(62) * A17.r + R(-64) * A18.r + R(8) * A19.r + R(8) * A20.r + R(-1) * A21.r + R(-1) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A4.i + R(-64) * A5.i + R(-1) * A6.i + R(8) * A7.i + R(71) * A8.i + R(62) * A9.i + R(80) * A10.i + R(-10) * A11.i + R(-10) * A12.i + R(-1) * A13.i + R(62) * A14.i + R(-28) * A15.i + R(-10) * A16.i + R(62) * A17.i + R(-64) * A18.i + R(8) * A19.i + R(8) * A20.i + R(-1) * A21.i + R(-1) * A22.i + R(-10) * A23.i;
-                cs += A4.r * zr + A4.i * zi; }
-              { const R zr = R(512) * R(0.5) * A5.r + R(-10) * A6.r + R(-1) * A7.r + R(62) * A8.r + R(-28) * A9.r + R(-10) * A10.r + R(62) * A11.r + R(-1) * A12.r + R(8) * A13.r + R(71) * A14.r + R(62) * A15.r + R(80) * A16.r + R(-10) * A17.r + R(8) * A18.r + R(-64) * A19.r + R(-1) * A20.r + R(-10) * A21.r + R(8) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A5.i + R(-10) * A6.i + R(-1) * A7.i + R(62) * A8.i + R(-28) * A9.i + R(-10) * A10.i + R(62) * A11.i + R(-1) * A12.i + R(8) * A13.i + R(71) * A14.i + R(62) * A15.i + R(80) * A16.i + R(-10) * A17.i + R(8) * A18.i + R(-64) * A19.i + R(-1) * A20.i + R(-10) * A21.i + R(8) * A22.i + R(-1) * A23.i;
-                cs += A5.r * zr + A5.i * zi; }
-              { const R zr = R(512) * R(0.5) * A6.r + R(-64) * A7.r + R(-64) * A8.r + R(8) * A9.r + R(8) * A10.r + R(80) * A11.r + R(80) * A12.r + R(-10) * A13.r + R(8) * A14.r + R(-1) * A15.r + R(62) * A16.r + R(71) * A17.r + R(-10) * A18.r + R(62) * A19.r + R(-1) * A20.r + R(-10) * A21.r + R(-28) * A22.r + R(62) * A23.r; const R zi = R(512) * R(0.5) * A6.i + R(-64) * A7.i + R(-64) * A8.i + R(8) * A9.i + R(8) * A10.i + R(80) * A11.i + R(80) * A12.i + R(-10) * A13.i + R(8) * A14.i + R(-1) * A15.i + R(62) * A16.i + R(71) * A17.i + R(-10) * A18.i + R(62) * A19.i + R(-1) * A20.i + R(-10) * A21.i + R(-28) * A22.i + R(62) * A23.i;
-                cs += A6.r * zr + A6.i * zi; }
-              { const R zr = R(512) * R(0.5) * A7.r + R(8) * A8.r + R(80) * A9.r + R(-64) * A10.r + R(8) * A11.r + R(-10) * A12.r + R(62) * A13.r + R(-1) * A14.r + R(-10) * A15.r + R(-28) * A16.r + R(62) * A17.r + R(80) * A18.r + R(-10) * A19.r + R(8) * A20.r + R(-1) * A21.r + R(62) * A22.r + R(71) * A23.r; const R zi = R(512) * R(0.5) * A7.i + R(8) * A8.i + R(80) * A9.i + R(-64) * A10.i + R(8) * A11.i + R(-10) * A12.i + R(62) * A13.i + R(-1) * A14.i + R(-10) * A15.i + R(-28) * A16.i + R(62) * A17.i + R(80) * A18.i + R(-10) * A19.i + R(8) * A20.i + R(-1) * A21.i + R(62) * A22.i + R(71) * A23.i;
-                cs += A7.r * zr + A7.i * zi; }
-              { const R zr = R(512) * R(0.5) * A8.r + R(-64) * A9.r + R(80) * A10.r + R(8) * A11.r + R(8) * A12.r + R(-1) * A13.r + R(-64) * A14.r + R(8) * A15.r + R(-10) * A16.r + R(-1) * A17.r + R(62) * A18.r + R(-28) * A19.r + R(-10) * A20.r + R(-1) * A21.r + R(62) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A8.i + R(-64) * A9.i + R(80) * A10.i + R(8) * A11.i + R(8) * A12.i + R(-1) * A13.i + R(-64) * A14.i + R(8) * A15.i + R(-10) * A16.i + R(-1) * A17.i + R(62) * A18.i + R(-28) * A19.i + R(-10) * A20.i + R(-1) * A21.i + R(62) * A22.i + R(-10) * A23.i;
-                cs += A8.r * zr + A8.i * zi; }
-              { const R zr = R(512) * R(0.5) * A9.r + R(8) * A10.r + R(-64) * A11.r + R(-1) * A12.r + R(-10) * A13.r + R(8) * A14.r + R(-64) * A15.r + R(-1) * A16.r + R(8) * A17.r + R(71) * A18.r + R(62) * A19.r + R(-1) * A20.r + R(8) * A21.r + R(-10) * A22.r + R(80) * A23.r; const R zi = R(512) * R(0.5) * A9.i + R(8) * A10.i + R(-64) * A11.i + R(-1) * A12.i + R(-10) * A13.i + R(8) * A14.i + R(-64) * A15.i + R(-1) * A16.i + R(8) * A17.i + R(71) * A18.i + R(62) * A19.i + R(-1) * A20.i + R(8) * A21.i + R(-10) * A22.i + R(80) * A23.i;
-                cs += A9.r * zr + A9.i * zi; }
-              { const R zr = R(512) * R(0.5) * A10.r + R(-64) * A11.r + R(62) * A12.r + R(-28) * A13.r + R(-10) * A14.r + R(-1) * A15.r + R(62) * A16.r + R(-10) * A17.r + R(8) * A18.r + R(-1) * A19.r + R(-64) * A20.r + R(8) * A21.r + R(-10) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A10.i + R(-64) * A11.i + R(62) * A12.i + R(-28) * A13.i + R(-10) * A14.i + R(-1) * A15.i + R(62) * A16.i + R(-10) * A17.i + R(8) * A18.i + R(-1) * A19.i + R(-64) * A20.i + R(8) * A21.i + R(-10) * A22.i + R(-1) * A23.i;
-                cs += A10.r * zr + A10.i * zi; }
-              { const R zr = R(512) * R(0.5) * A11.r + R(71) * A12.r + R(62) * A13.r + R(-1) * A14.r + R(8) * A15.r + R(-10) * A16.r + R(80) * A17.r + R(-1) * A18.r + R(-10) * A19.r + R(8) * A20.r + R(-64) * A21.r + R(-1) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A11.i + R(71) * A12.i + R(62) * A13.i + R(-1) * A14.i + R(8) * A15.i + R(-10) * A16.i + R(80) * A17.i + R(-1) * A18.i + R(-10) * A19.i + R(8) * A20.i + R(-64) * A21.i + R(-1) * A22.i + R(8) * A23.i;
-                cs += A11.r * zr + A11.i * zi; }
-              { const R zr = R(512) * R(0.5) * A12.r + R(-64) * A13.r + R(-64) * A14.r + R(8) * A15.r + R(8) * A16.r + R(80) * A17.r + R(62) * A18.r + R(-10) * A19.r + R(-28) * A20.r + R(62) * A21.r + R(-1) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A12.i + R(-64) * A13.i + R(-64) * A14.i + R(8) * A15.i + R(8) * A16.i + R(80) * A17.i + R(62) * A18.i + R(-10) * A19.i + R(-28) * A20.i + R(62) * A21.i + R(-1) * A22.i + R(-10) * A23.i;
-                cs += A12.r * zr + A12.i * zi; }
-              { const R zr = R(512) * R(0.5) * A13.r + R(8) * A14.r + R(80) * A15.r + R(-64) * A16.r + R(8) * A17.r + R(-10) * A18.r + R(80) * A19.r + R(62) * A20.r + R(71) * A21.r + R(8) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A13.i + R(8) * A14.i + R(80) * A15.i + R(-64) * A16.i + R(8) * A17.i + R(-10) * A18.i + R(80) * A19.i + R(62) * A20.i + R(71) * A21.i + R(8) * A22.i + R(-1) * A23.i;
-                cs += A13.r * zr + A13.i * zi; }
-              { const R zr = R(512) * R(0.5) * A14.r + R(-64) * A15.r + R(80) * A16.r + R(8) * A17.r + R(-28) * A18.r + R(62) * A19.r + R(62) * A20.r + R(-10) * A21.r + R(-10) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A14.i + R(-64) * A15.i + R(80) * A16.i + R(8) * A17.i + R(-28) * A18.i + R(62) * A19.i + R(62) * A20.i + R(-10) * A21.i + R(-10) * A22.i + R(-1) * A23.i;
-                cs += A14.r * zr + A14.i * zi; }
-              { const R zr = R(512) * R(0.5) * A15.r + R(8) * A16.r + R(-64) * A17.r + R(62) * A18.r + R(71) * A19.r + R(-10) * A20.r + R(80) * A21.r + R(-1) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A15.i + R(8) * A16.i + R(-64) * A17.i + R(62) * A18.i + R(71) * A19.i + R(-10) * A20.i + R(80) * A21.i + R(-1) * A22.i + R(8) * A23.i;
-                cs += A15.r * zr + A15.i * zi; }
-              { const R zr = R(512) * R(0.5) * A16.r + R(-64) * A17.r + R(-1) * A18.r + R(8) * A19.r + R(-10) * A20.r + R(-1) * A21.r + R(-64) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A16.i + R(-64) * A17.i + R(-1) * A18.i + R(8) * A19.i + R(-10) * A20.i + R(-1) * A21.i + R(-64) * A22.i + R(8) * A23.i;
-                cs += A16.r * zr + A16.i * zi; }
-              { const R zr = R(512) * R(0.5) * A17.r + R(-10) * A18.r + R(-1) * A19.r + R(-1) * A20.r + R(8) * A21.r + R(8) * A22.r + R(-64) * A23.r; const R zi = R(512) * R(0.5) * A17.i + R(-10) * A18.i + R(-1) * A19.i + R(-1) * A20.i + R(8) * A21.i + R(8) * A22.i + R(-64) * A23.i;
-                cs += A17.r * zr + A17.i * zi; }
-              { const R zr = R(512) * R(0.5) * A18.r + R(-64) * A19.r + R(-64) * A20.r + R(8) * A21.r + R(8) * A22.r + R(80) * A23.r; const R zi = R(512) * R(0.5) * A18.i + R(-64) * A19.i + R(-64) * A20.i + R(8) * A21.i + R(8) * A22.i + R(80) * A23.i;
-                cs += A18.r * zr + A18.i * zi; }
-              { const R zr = R(512) * R(0.5) * A19.r + R(8) * A20.r + R(80) * A21.r + R(-64) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A19.i + R(8) * A20.i + R(80) * A21.i + R(-64) * A22.i + R(8) * A23.i;
-                cs += A19.r * zr + A19.i * zi; }
-              { const R zr = R(512) * R(0.5) * A20.r + R(-64) * A21.r + R(80) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A20.i + R(-64) * A21.i + R(80) * A22.i + R(8) * A23.i;
-                cs += A20.r * zr + A20.i * zi; }
-              { const R zr = R(512) * R(0.5) * A21.r + R(8) * A22.r + R(-64) * A23.r; const R zi = R(512) * R(0.5) * A21.i + R(8) * A22.i + R(-64) * A23.i;
-                cs += A21.r * zr + A21.i * zi; }
-              { const R zr = R(512) * R(0.5) * A22.r + R(-64) * A23.r; const R zi = R(512) * R(0.5) * A22.i + R(-64) * A23.i;
-                cs += A22.r * zr + A22.i * zi; }
-              { const R zr = R(512) * R(0.5) * A23.r; const R zi = R(512) * R(0.5) * A23.i;
-                cs += A23.r * zr + A23.i * zi; }
-              acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
+              if constexpr (CM != CM_FMA) {
+                const cx<float> Aa[K] = {A0, A1, A2, A3, A4, A5, A6, A7, A8, A9, A10, A11, A12, A13, A14, A15, A16, A17, A18, A19, A20, A21, A22, A23};
+                acc += R(2) * cmma.sum(Aa);  // x2 helicity flip
+              } else {
+                R cs = R(0);
+                { const R zr = R(512) * R(0.5) * A0.r + R(-64) * A1.r + R(-64) * A2.r + R(8) * A3.r + R(8) * A4.r + R(80) * A5.r + R(-64) * A6.r + R(8) * A7.r + R(8) * A8.r + R(-1) * A9.r + R(-1) * A10.r + R(-10) * A11.r + R(8) * A12.r + R(-1) * A13.r + R(80) * A14.r + R(-10) * A15.r + R(71) * A16.r + R(62) * A17.r + R(-1) * A18.r + R(-10) * A19.r + R(-10) * A20.r + R(62) * A21.r + R(62) * A22.r + R(-28) * A23.r; const R zi = R(512) * R(0.5) * A0.i + R(-64) * A1.i + R(-64) * A2.i + R(8) * A3.i + R(8) * A4.i + R(80) * A5.i + R(-64) * A6.i + R(8) * A7.i + R(8) * A8.i + R(-1) * A9.i + R(-1) * A10.i + R(-10) * A11.i + R(8) * A12.i + R(-1) * A13.i + R(80) * A14.i + R(-10) * A15.i + R(71) * A16.i + R(62) * A17.i + R(-1) * A18.i + R(-10) * A19.i + R(-10) * A20.i + R(62) * A21.i + R(62) * A22.i + R(-28) * A23.i;
+                  cs += A0.r * zr + A0.i * zi; }
+                { const R zr = R(512) * R(0.5) * A1.r + R(8) * A2.r + R(80) * A3.r + R(-64) * A4.r + R(8) * A5.r + R(8) * A6.r + R(-64) * A7.r + R(-1) * A8.r + R(-10) * A9.r + R(8) * A10.r + R(-1) * A11.r + R(-1) * A12.r + R(-10) * A13.r + R(-10) * A14.r + R(62) * A15.r + R(62) * A16.r + R(-28) * A17.r + R(8) * A18.r + R(-1) * A19.r + R(80) * A20.r + R(-10) * A21.r + R(71) * A22.r + R(62) * A23.r; const R zi = R(512) * R(0.5) * A1.i + R(8) * A2.i + R(80) * A3.i + R(-64) * A4.i + R(8) * A5.i + R(8) * A6.i + R(-64) * A7.i + R(-1) * A8.i + R(-10) * A9.i + R(8) * A10.i + R(-1) * A11.i + R(-1) * A12.i + R(-10) * A13.i + R(-10) * A14.i + R(62) * A15.i + R(62) * A16.i + R(-28) * A17.i + R(8) * A18.i + R(-1) * A19.i + R(80) * A20.i + R(-10) * A21.i + R(71) * A22.i + R(62) * A23.i;
+                  cs += A1.r * zr + A1.i * zi; }
+                { const R zr = R(512) * R(0.5) * A2.r + R(-64) * A3.r + R(80) * A4.r + R(8) * A5.r + R(8) * A6.r + R(-1) * A7.r + R(80) * A8.r + R(-10) * A9.r + R(71) * A10.r + R(62) * A11.r + R(-64) * A12.r + R(8) * A13.r + R(8) * A14.r + R(-1) * A15.r + R(-1) * A16.r + R(-10) * A17.r + R(-10) * A18.r + R(-1) * A19.r + R(62) * A20.r + R(-28) * A21.r + R(-10) * A22.r + R(62) * A23.r; const R zi = R(512) * R(0.5) * A2.i + R(-64) * A3.i + R(80) * A4.i + R(8) * A5.i + R(8) * A6.i + R(-1) * A7.i + R(80) * A8.i + R(-10) * A9.i + R(71) * A10.i + R(62) * A11.i + R(-64) * A12.i + R(8) * A13.i + R(8) * A14.i + R(-1) * A15.i + R(-1) * A16.i + R(-10) * A17.i + R(-10) * A18.i + R(-1) * A19.i + R(62) * A20.i + R(-28) * A21.i + R(-10) * A22.i + R(62) * A23.i;
+                  cs += A2.r * zr + A2.i * zi; }
+                { const R zr = R(512) * R(0.5) * A3.r + R(8) * A4.r + R(-64) * A5.r + R(-1) * A6.r + R(-10) * A7.r + R(-10) * A8.r + R(62) * A9.r + R(62) * A10.r + R(-28) * A11.r + R(8) * A12.r + R(-64) * A13.r + R(-1) * A14.r + R(-10) * A15.r + R(8) * A16.r + R(-1) * A17.r + R(-1) * A18.r + R(8) * A19.r + R(71) * A20.r + R(62) * A21.r + R(80) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A3.i + R(8) * A4.i + R(-64) * A5.i + R(-1) * A6.i + R(-10) * A7.i + R(-10) * A8.i + R(62) * A9.i + R(62) * A10.i + R(-28) * A11.i + R(8) * A12.i + R(-64) * A13.i + R(-1) * A14.i + R(-10) * A15.i + R(8) * A16.i + R(-1) * A17.i + R(-1) * A18.i + R(8) * A19.i + R(71) * A20.i + R(62) * A21.i + R(80) * A22.i + R(-10) * A23.i;
+                  cs += A3.r * zr + A3.i * zi; }
+                { const R zr = R(512) * R(0.5) * A4.r + R(-64) * A5.r + R(-1) * A6.r + R(8) * A7.r + R(71) * A8.r + R(62) * A9.r + R(80) * A10.r + R(-10) * A11.r + R(-10) * A12.r + R(-1) * A13.r + R(62) * A14.r + R(-28) * A15.r + R(-10) * A16.r + R(62) * A17.r + R(-64) * A18.r + R(8) * A19.r + R(8) * A20.r + R(-1) * A21.r + R(-1) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A4.i + R(-64) * A5.i + R(-1) * A6.i + R(8) * A7.i + R(71) * A8.i + R(62) * A9.i + R(80) * A10.i + R(-10) * A11.i + R(-10) * A12.i + R(-1) * A13.i + R(62) * A14.i + R(-28) * A15.i + R(-10) * A16.i + R(62) * A17.i + R(-64) * A18.i + R(8) * A19.i + R(8) * A20.i + R(-1) * A21.i + R(-1) * A22.i + R(-10) * A23.i;
+                  cs += A4.r * zr + A4.i * zi; }
+                { const R zr = R(512) * R(0.5) * A5.r + R(-10) * A6.r + R(-1) * A7.r + R(62) * A8.r + R(-28) * A9.r + R(-10) * A10.r + R(62) * A11.r + R(-1) * A12.r + R(8) * A13.r + R(71) * A14.r + R(62) * A15.r + R(80) * A16.r + R(-10) * A17.r + R(8) * A18.r + R(-64) * A19.r + R(-1) * A20.r + R(-10) * A21.r + R(8) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A5.i + R(-10) * A6.i + R(-1) * A7.i + R(62) * A8.i + R(-28) * A9.i + R(-10) * A10.i + R(62) * A11.i + R(-1) * A12.i + R(8) * A13.i + R(71) * A14.i + R(62) * A15.i + R(80) * A16.i + R(-10) * A17.i + R(8) * A18.i + R(-64) * A19.i + R(-1) * A20.i + R(-10) * A21.i + R(8) * A22.i + R(-1) * A23.i;
+                  cs += A5.r * zr + A5.i * zi; }
+                { const R zr = R(512) * R(0.5) * A6.r + R(-64) * A7.r + R(-64) * A8.r + R(8) * A9.r + R(8) * A10.r + R(80) * A11.r + R(80) * A12.r + R(-10) * A13.r + R(8) * A14.r + R(-1) * A15.r + R(62) * A16.r + R(71) * A17.r + R(-10) * A18.r + R(62) * A19.r + R(-1) * A20.r + R(-10) * A21.r + R(-28) * A22.r + R(62) * A23.r; const R zi = R(512) * R(0.5) * A6.i + R(-64) * A7.i + R(-64) * A8.i + R(8) * A9.i + R(8) * A10.i + R(80) * A11.i + R(80) * A12.i + R(-10) * A13.i + R(8) * A14.i + R(-1) * A15.i + R(62) * A16.i + R(71) * A17.i + R(-10) * A18.i + R(62) * A19.i + R(-1) * A20.i + R(-10) * A21.i + R(-28) * A22.i + R(62) * A23.i;
+                  cs += A6.r * zr + A6.i * zi; }
+                { const R zr = R(512) * R(0.5) * A7.r + R(8) * A8.r + R(80) * A9.r + R(-64) * A10.r + R(8) * A11.r + R(-10) * A12.r + R(62) * A13.r + R(-1) * A14.r + R(-10) * A15.r + R(-28) * A16.r + R(62) * A17.r + R(80) * A18.r + R(-10) * A19.r + R(8) * A20.r + R(-1) * A21.r + R(62) * A22.r + R(71) * A23.r; const R zi = R(512) * R(0.5) * A7.i + R(8) * A8.i + R(80) * A9.i + R(-64) * A10.i + R(8) * A11.i + R(-10) * A12.i + R(62) * A13.i + R(-1) * A14.i + R(-10) * A15.i + R(-28) * A16.i + R(62) * A17.i + R(80) * A18.i + R(-10) * A19.i + R(8) * A20.i + R(-1) * A21.i + R(62) * A22.i + R(71) * A23.i;
+                  cs += A7.r * zr + A7.i * zi; }
+                { const R zr = R(512) * R(0.5) * A8.r + R(-64) * A9.r + R(80) * A10.r + R(8) * A11.r + R(8) * A12.r + R(-1) * A13.r + R(-64) * A14.r + R(8) * A15.r + R(-10) * A16.r + R(-1) * A17.r + R(62) * A18.r + R(-28) * A19.r + R(-10) * A20.r + R(-1) * A21.r + R(62) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A8.i + R(-64) * A9.i + R(80) * A10.i + R(8) * A11.i + R(8) * A12.i + R(-1) * A13.i + R(-64) * A14.i + R(8) * A15.i + R(-10) * A16.i + R(-1) * A17.i + R(62) * A18.i + R(-28) * A19.i + R(-10) * A20.i + R(-1) * A21.i + R(62) * A22.i + R(-10) * A23.i;
+                  cs += A8.r * zr + A8.i * zi; }
+                { const R zr = R(512) * R(0.5) * A9.r + R(8) * A10.r + R(-64) * A11.r + R(-1) * A12.r + R(-10) * A13.r + R(8) * A14.r + R(-64) * A15.r + R(-1) * A16.r + R(8) * A17.r + R(71) * A18.r + R(62) * A19.r + R(-1) * A20.r + R(8) * A21.r + R(-10) * A22.r + R(80) * A23.r; const R zi = R(512) * R(0.5) * A9.i + R(8) * A10.i + R(-64) * A11.i + R(-1) * A12.i + R(-10) * A13.i + R(8) * A14.i + R(-64) * A15.i + R(-1) * A16.i + R(8) * A17.i + R(71) * A18.i + R(62) * A19.i + R(-1) * A20.i + R(8) * A21.i + R(-10) * A22.i + R(80) * A23.i;
+                  cs += A9.r * zr + A9.i * zi; }
+                { const R zr = R(512) * R(0.5) * A10.r + R(-64) * A11.r + R(62) * A12.r + R(-28) * A13.r + R(-10) * A14.r + R(-1) * A15.r + R(62) * A16.r + R(-10) * A17.r + R(8) * A18.r + R(-1) * A19.r + R(-64) * A20.r + R(8) * A21.r + R(-10) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A10.i + R(-64) * A11.i + R(62) * A12.i + R(-28) * A13.i + R(-10) * A14.i + R(-1) * A15.i + R(62) * A16.i + R(-10) * A17.i + R(8) * A18.i + R(-1) * A19.i + R(-64) * A20.i + R(8) * A21.i + R(-10) * A22.i + R(-1) * A23.i;
+                  cs += A10.r * zr + A10.i * zi; }
+                { const R zr = R(512) * R(0.5) * A11.r + R(71) * A12.r + R(62) * A13.r + R(-1) * A14.r + R(8) * A15.r + R(-10) * A16.r + R(80) * A17.r + R(-1) * A18.r + R(-10) * A19.r + R(8) * A20.r + R(-64) * A21.r + R(-1) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A11.i + R(71) * A12.i + R(62) * A13.i + R(-1) * A14.i + R(8) * A15.i + R(-10) * A16.i + R(80) * A17.i + R(-1) * A18.i + R(-10) * A19.i + R(8) * A20.i + R(-64) * A21.i + R(-1) * A22.i + R(8) * A23.i;
+                  cs += A11.r * zr + A11.i * zi; }
+                { const R zr = R(512) * R(0.5) * A12.r + R(-64) * A13.r + R(-64) * A14.r + R(8) * A15.r + R(8) * A16.r + R(80) * A17.r + R(62) * A18.r + R(-10) * A19.r + R(-28) * A20.r + R(62) * A21.r + R(-1) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A12.i + R(-64) * A13.i + R(-64) * A14.i + R(8) * A15.i + R(8) * A16.i + R(80) * A17.i + R(62) * A18.i + R(-10) * A19.i + R(-28) * A20.i + R(62) * A21.i + R(-1) * A22.i + R(-10) * A23.i;
+                  cs += A12.r * zr + A12.i * zi; }
+                { const R zr = R(512) * R(0.5) * A13.r + R(8) * A14.r + R(80) * A15.r + R(-64) * A16.r + R(8) * A17.r + R(-10) * A18.r + R(80) * A19.r + R(62) * A20.r + R(71) * A21.r + R(8) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A13.i + R(8) * A14.i + R(80) * A15.i + R(-64) * A16.i + R(8) * A17.i + R(-10) * A18.i + R(80) * A19.i + R(62) * A20.i + R(71) * A21.i + R(8) * A22.i + R(-1) * A23.i;
+                  cs += A13.r * zr + A13.i * zi; }
+                { const R zr = R(512) * R(0.5) * A14.r + R(-64) * A15.r + R(80) * A16.r + R(8) * A17.r + R(-28) * A18.r + R(62) * A19.r + R(62) * A20.r + R(-10) * A21.r + R(-10) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A14.i + R(-64) * A15.i + R(80) * A16.i + R(8) * A17.i + R(-28) * A18.i + R(62) * A19.i + R(62) * A20.i + R(-10) * A21.i + R(-10) * A22.i + R(-1) * A23.i;
+                  cs += A14.r * zr + A14.i * zi; }
+                { const R zr = R(512) * R(0.5) * A15.r + R(8) * A16.r + R(-64) * A17.r + R(62) * A18.r + R(71) * A19.r + R(-10) * A20.r + R(80) * A21.r + R(-1) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A15.i + R(8) * A16.i + R(-64) * A17.i + R(62) * A18.i + R(71) * A19.i + R(-10) * A20.i + R(80) * A21.i + R(-1) * A22.i + R(8) * A23.i;
+                  cs += A15.r * zr + A15.i * zi; }
+                { const R zr = R(512) * R(0.5) * A16.r + R(-64) * A17.r + R(-1) * A18.r + R(8) * A19.r + R(-10) * A20.r + R(-1) * A21.r + R(-64) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A16.i + R(-64) * A17.i + R(-1) * A18.i + R(8) * A19.i + R(-10) * A20.i + R(-1) * A21.i + R(-64) * A22.i + R(8) * A23.i;
+                  cs += A16.r * zr + A16.i * zi; }
+                { const R zr = R(512) * R(0.5) * A17.r + R(-10) * A18.r + R(-1) * A19.r + R(-1) * A20.r + R(8) * A21.r + R(8) * A22.r + R(-64) * A23.r; const R zi = R(512) * R(0.5) * A17.i + R(-10) * A18.i + R(-1) * A19.i + R(-1) * A20.i + R(8) * A21.i + R(8) * A22.i + R(-64) * A23.i;
+                  cs += A17.r * zr + A17.i * zi; }
+                { const R zr = R(512) * R(0.5) * A18.r + R(-64) * A19.r + R(-64) * A20.r + R(8) * A21.r + R(8) * A22.r + R(80) * A23.r; const R zi = R(512) * R(0.5) * A18.i + R(-64) * A19.i + R(-64) * A20.i + R(8) * A21.i + R(8) * A22.i + R(80) * A23.i;
+                  cs += A18.r * zr + A18.i * zi; }
+                { const R zr = R(512) * R(0.5) * A19.r + R(8) * A20.r + R(80) * A21.r + R(-64) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A19.i + R(8) * A20.i + R(80) * A21.i + R(-64) * A22.i + R(8) * A23.i;
+                  cs += A19.r * zr + A19.i * zi; }
+                { const R zr = R(512) * R(0.5) * A20.r + R(-64) * A21.r + R(80) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A20.i + R(-64) * A21.i + R(80) * A22.i + R(8) * A23.i;
+                  cs += A20.r * zr + A20.i * zi; }
+                { const R zr = R(512) * R(0.5) * A21.r + R(8) * A22.r + R(-64) * A23.r; const R zi = R(512) * R(0.5) * A21.i + R(8) * A22.i + R(-64) * A23.i;
+                  cs += A21.r * zr + A21.i * zi; }
+                { const R zr = R(512) * R(0.5) * A22.r + R(-64) * A23.r; const R zi = R(512) * R(0.5) * A22.i + R(-64) * A23.i;
+                  cs += A22.r * zr + A22.i * zi; }
+                { const R zr = R(512) * R(0.5) * A23.r; const R zi = R(512) * R(0.5) * A23.i;
+                  cs += A23.r * zr + A23.i * zi; }
+                acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
+              }
             }
           }
         }

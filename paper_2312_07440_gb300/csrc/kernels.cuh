@@ -34,9 +34,10 @@ struct PointDev {
 };
 
 struct RwArgs {
-  const double* mom;  // [N][4][E]
+  const double* mom;  // [N][4][ld]
   const double* w;    // [E]
   long long E;
+  long long ld;       // row stride of mom (>= E)
   double* me0;     // [E] or null
   double* me_pts;  // [P][E] or null
   double* ratio;   // [P][E] or null
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(256, 1) k_reweight(const __grid_constant__ RwA
 #pragma unroll
     for (int i = 0; i < NEXT; ++i)
 #pragma unroll
-      for (int m = 0; m < 4; ++m) p[i][m] = __ldg(a.mom + ((long long)(i * 4 + m)) * E + evc);
+      for (int m = 0; m < 4; ++m) p[i][m] = __ldg(a.mom + ((long long)(i * 4 + m)) * a.ld + evc);
     // One call site for every evaluation (original, then each point), so that
     // identical parameters give bitwise identical |M|^2 and r == 1 exactly.
     const bool leader = valid && lane == 0;

@@ -1,0 +1,31 @@
+// g g -> t tbar + n g kernel variants (gg_tt, mixed precision: FP32 amplitudes,
+// FP16/BF16 tensor-core colour sum with FP32 accumulation).
+#include "../../include/rwgt.h"
+#include "gen_qcd_gg_tt.cuh"
+#include "kernels.cuh"
+#include "procs.cuh"
+#include "registry.h"
+
+namespace rw {
+namespace {
+struct Tag {
+  static constexpr int NG = gg_tt::NG;
+  static constexpr int NEXT = gg_tt::NEXT;
+  static constexpr int MAX_LB = gg_tt::MAX_LB;
+  template <class R, int LB, int CM>
+  __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
+    return gg_tt::hel_sum<R, LB, CM>(X, K, lane);
+  }
+};
+using P16 = QcdProc<Tag, CM_FP16>;
+using PB16 = QcdProc<Tag, CM_BF16>;
+}  // namespace
+
+void register_gg_tt_mixed(std::vector<KernelEntry>& t) {
+  t.push_back({RW_GG_TT, RW_MIXED_FP16, 0, (const void*)&k_reweight<P16, float, 0>, 128});
+  t.push_back({RW_GG_TT, RW_MIXED_BF16, 0, (const void*)&k_reweight<PB16, float, 0>, 128});
+  t.push_back({RW_GG_TT, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1>, 128});
+  t.push_back({RW_GG_TT, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1>, 128});
+}
+
+}  // namespace rw

@@ -7,8 +7,9 @@
 
 namespace rw {
 
-// g g -> t tbar + n g.  Tag provides NG, NEXT and hel_sum<R, LB>().
-template <class Tag>
+// g g -> t tbar + n g.  Tag provides NG, NEXT, MAX_LB and hel_sum<R, LB, CM>();
+// CM selects the colour sum (FMA, or tensor cores in FP16/BF16).
+template <class Tag, int CM = 0>
 struct QcdProc {
   static constexpr int NG = Tag::NG;
   static constexpr int NEXT = Tag::NEXT;
@@ -23,7 +24,7 @@ struct QcdProc {
     QcdExt<R, NG> X;
     QcdKin<R, NG> Kn;
     qcd_setup<R, NG, NEXT>(p, pt.m_t, X, Kn);
-    double s = double(Tag::template hel_sum<R, LB>(X, Kn, lane));
+    double s = double(Tag::template hel_sum<R, LB, CM>(X, Kn, lane));
 #pragma unroll
     for (int o = 1; o < (1 << LB); o <<= 1) s += __shfl_xor_sync(gmask, s, o);
     return s * pt.cscale;

@@ -10,6 +10,7 @@ struct KernelEntry {
   int mode;          // RW_FP64 / RW_FP32
   int lane_bits;     // helicity slices per event = 2^lane_bits
   const void* func;  // __global__ k_reweight<...>(RwArgs)
+  int max_block = 256;  // threads per block the variant supports
 };
 
 struct ProcStatic {
@@ -22,7 +23,8 @@ void register_ee_mumu(std::vector<KernelEntry>& t, ProcStatic& s);
 #define RW_DECLARE_QCD(name)                              \
   void register_##name##_fp64(std::vector<KernelEntry>& t); \
   void register_##name##_fp32(std::vector<KernelEntry>& t); \
-  void static_##name(ProcStatic& s);
+  void static_##name(ProcStatic& s);                          \
+  void register_##name##_mixed(std::vector<KernelEntry>& t);
 RW_DECLARE_QCD(gg_tt)
 RW_DECLARE_QCD(gg_ttg)
 RW_DECLARE_QCD(gg_ttgg)

@@ -34,6 +34,9 @@ struct Registry {
   ProcStatic st[NPROC];
   Registry() {
     rw::register_ee_mumu(kernels, st[RW_EE_MUMU]);
+    rw::register_gg_tt_mixed(kernels);
+    rw::register_gg_ttg_mixed(kernels);
+    rw::register_gg_ttgg_mixed(kernels);
     rw::register_gg_tt_fp64(kernels);
     rw::register_gg_tt_fp32(kernels);
     rw::static_gg_tt(st[RW_GG_TT]);
@@ -94,6 +97,7 @@ struct rw_ctx {
   const double* mom = nullptr;
   const double* w = nullptr;
   int64_t E = 0;
+  int64_t ld = 0;  // row stride of the momenta (the E of rw_load_events)
   char* ws = nullptr;
   size_t ws_bytes = 0;
   int lane_bits = -1, block = 0;
@@ -202,6 +206,7 @@ int launch(rw_ctx* c, RwArgs& a) {
   const KernelEntry* k = registry().find(c->process, c->mode, lb);
   if (!k) return fail(c, RW_ERR_MODE, "no kernel for process %d mode %d lane_bits %d", c->process, c->mode, lb);
   const int block = c->block > 0 ? c->block : 128;
+  if (block > k->max_block) return fail(c, RW_ERR_ARG, "block %d above this variant's %d", block, k->max_block);
   const int lanes = 1 << lb;
   const size_t smem = (size_t)(block / 32) * (a.P + 1) * sizeof(double2);
   auto key = std::make_tuple(k->func, block, smem);
@@ -288,7 +293,7 @@ int rw_process_info_get(int process, rw_process_info* out) {
 int rw_set_process(rw_ctx* c, int process, int mode) {
   if (!c) return RW_ERR_NULL;
   if (process < 0 || process >= NPROC) return fail(c, RW_ERR_ARG, "unknown process %d", process);
-  if (mode != RW_FP64 && mode != RW_FP32) return fail(c, RW_ERR_MODE, "unknown mode %d", mode);
+  if (mode < RW_FP64 || mode > RW_MIXED_BF16) return fail(c, RW_ERR_MODE, "unknown mode %d", mode);
   bool any = false;
   for (const auto& k : registry().kernels) any |= k.process == process && k.mode == mode;
   if (!any) return fail(c, RW_ERR_MODE, "process %d has no kernels in mode %d", process, mode);
@@ -333,12 +338,107 @@ int rw_set_tuning(rw_ctx* c, int lane_bits, int block) {
   if (block != 0 && (block < 32 || block > 256 || block % 32))
     return fail(c, RW_ERR_ARG, "block must be a multiple of 32 in [32, 256]");
   if (lane_bits >= 0 && c->process >= 0) {
-    if (!registry().find(c->process, c->mode, lane_bits))
-      return fail(c, RW_ERR_MODE, "lane_bits %d not compiled for this process/mode", lane_bits);
+    const KernelEntry* k = registry().find(c->process, c->mode, lane_bits);
+    if (!k) return fail(c, RW_ERR_MODE, "lane_bits %d not compiled for this process/mode", lane_bits);
+    if (block > k->max_block) return fail(c, RW_ERR_ARG, "block above this variant's %d", k->max_block);
     if ((1 << lane_bits) > (block ? block : 128)) return fail(c, RW_ERR_ARG, "more lanes than threads");
   }
   c->lane_bits = lane_bits;
   c->block = block;
+  return RW_OK;
+}
+
+int rw_get_tuning(const rw_ctx* c, int* lane_bits, int* block) {
+  if (!c || !lane_bits || !block) return RW_ERR_NULL;
+  if (c->process < 0) return RW_ERR_STATE;
+  *lane_bits = c->lane_bits >= 0 ? c->lane_bits : default_lane_bits(c->process, c->mode);
+  *block = c->block > 0 ? c->block : 128;
+  return RW_OK;
+}
+
+int rw_autotune(rw_ctx* c, int64_t max_events, const char* cache_path, double* ms_out) {
+  int rc = ready(c, true);
+  if (rc) return rc;
+  if (c->pts.empty()) return fail(c, RW_ERR_STATE, "no reweight points set");
+  if (max_events <= 0) return fail(c, RW_ERR_ARG, "max_events must be > 0");
+  DeviceGuard g(c->device);
+  const int P = (int)c->pts.size();
+  const int64_t E = std::min<int64_t>(c->E, max_events);
+  int ebits = 0;
+  while ((int64_t(1) << (ebits + 1)) <= E) ++ebits;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return fail(c, RW_ERR_CUDA, "device properties");
+  char key[512];
+  snprintf(key, sizeof key, "%s|%d|%d|P%d|E%d", prop.name, c->process, c->mode, P, ebits);
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[1024];
+      while (fgets(line, sizeof line, f)) {
+        char k[512];
+        int lb, bl;
+        double ms;
+        if (sscanf(line, "{\"key\": \"%511[^\"]\", \"lane_bits\": %d, \"block\": %d, \"ms\": %lf}", k, &lb, &bl, &ms) ==
+                4 &&
+            strcmp(k, key) == 0 && registry().find(c->process, c->mode, lb)) {
+          fclose(f);
+          c->lane_bits = lb;
+          c->block = bl;
+          if (ms_out) *ms_out = ms;
+          return RW_OK;
+        }
+      }
+      fclose(f);
+    }
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(c, RW_ERR_CUDA, "cudaEventCreate");
+  const int64_t E_saved = c->E;
+  const int lb_saved = c->lane_bits, bl_saved = c->block;
+  c->E = E;
+  double best = 1e300;
+  int best_lb = -1, best_bl = 0;
+  static const int blocks[] = {64, 128, 256};
+  for (const auto& k : registry().kernels) {
+    if (k.process != c->process || k.mode != c->mode) continue;
+    for (int bl : blocks) {
+      if ((1 << k.lane_bits) > bl || bl > k.max_block) continue;
+      c->lane_bits = k.lane_bits;
+      c->block = bl;
+      float t[3];
+      bool ok = true;
+      for (int it = -1; it < 3 && ok; ++it) {
+        cudaEventRecord(e0, c->stream);
+        ok = rw_reweight_async(c, nullptr, nullptr, nullptr, nullptr) == RW_OK;
+        cudaEventRecord(e1, c->stream);
+        if (ok && cudaEventSynchronize(e1) == cudaSuccess && it >= 0) cudaEventElapsedTime(&t[it], e0, e1);
+      }
+      if (!ok) continue;
+      std::sort(t, t + 3);
+      if (t[1] < best) {
+        best = t[1];
+        best_lb = k.lane_bits;
+        best_bl = bl;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->E = E_saved;
+  if (best_lb < 0) {
+    c->lane_bits = lb_saved;
+    c->block = bl_saved;
+    return fail(c, RW_ERR_CUDA, "no variant ran: %s", c->err.c_str());
+  }
+  c->lane_bits = best_lb;
+  c->block = best_bl;
+  if (ms_out) *ms_out = best;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "a")) {
+      fprintf(f, "{\"key\": \"%s\", \"lane_bits\": %d, \"block\": %d, \"ms\": %.6f}\n", key, best_lb, best_bl, best);
+      fclose(f);
+    }
+  }
   return RW_OK;
 }
 
@@ -365,6 +465,7 @@ int rw_load_events(rw_ctx* c, const double* d_mom, const double* d_w, int64_t E,
   c->mom = d_mom;
   c->w = d_w;
   c->E = E;
+  c->ld = E;
   c->ws = static_cast<char*>(d_ws);
   c->ws_bytes = ws_bytes;
   return RW_OK;
@@ -380,6 +481,7 @@ int rw_eval_me(rw_ctx* c, int point, double* d_me) {
   a.mom = c->mom;
   a.w = c->w;
   a.E = c->E;
+  a.ld = c->ld;
   a.me0 = d_me;
   a.P = 0;
   a.me_only = 1;
@@ -408,6 +510,7 @@ int rw_reweight_async(rw_ctx* c, double* d_wnew, double* d_ratio, double* d_me0,
   a.mom = c->mom;
   a.w = c->w;
   a.E = c->E;
+  a.ld = c->ld;
   a.me0 = d_me0;
   a.me_pts = d_me_pts;
   a.ratio = d_ratio;
@@ -563,6 +666,7 @@ extern "C" int rw_reweight_noalloc(rw_ctx* c, const double* d_mom, const double*
   const KernelEntry* k = registry().find(c->process, c->mode, lb);
   if (!k) return noalloc_fail(c, RW_ERR_MODE, "no kernel");
   const int block = c->block > 0 ? c->block : 128;
+  if (block > k->max_block) return noalloc_fail(c, RW_ERR_ARG, "block too large");
   const size_t smem = (size_t)(block / 32) * (P + 1) * sizeof(double2);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, block, smem) != cudaSuccess) {
@@ -578,6 +682,7 @@ extern "C" int rw_reweight_noalloc(rw_ctx* c, const double* d_mom, const double*
   a.mom = d_mom;
   a.w = d_w;
   a.E = E;
+  a.ld = E;
   a.ratio = d_ratio;
   a.wnew = d_wnew;
   a.P = P;

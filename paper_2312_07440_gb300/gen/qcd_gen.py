@@ -208,6 +208,7 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     w(f"// {diagram_count(n)} Feynman diagrams, {K} colour orderings, {2 ** (n + 2)} helicities.")
     w(f"// colour matrix C = Cint / {den}")
     w("#pragma once")
+    w('#include "colour_mma.cuh"')
     w('#include "qcd.cuh"')
     w("")
     w(f"namespace rw {{ namespace {name} {{")
@@ -223,11 +224,15 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     flat = ", ".join(str(x) for row in Cint for x in row)
     w(f"__host__ __device__ constexpr int cint(int i, int j) {{ constexpr int c[K * K] = {{{flat}}}; return c[i * K + j]; }}")
     w(f"constexpr int ORDER[K][NG] = {{{', '.join('{' + ', '.join(map(str, p)) + '}' for p in perms)}}};")
+    w(f"static __device__ const short CI[K * K] = {{{flat}}};  // row-major C_int for the tensor-core sum")
     w("")
     w("// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;")
     w("// helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).")
-    w("template <class R, int LB>")
+    w("// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float).")
+    w("template <class R, int LB, int CM = CM_FMA>")
     w("__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {")
+    w("  static_assert(CM == CM_FMA || sizeof(R) == 4, \"tensor-core colour sum takes FP32 amplitudes\");")
+    w("  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI);")
     w("  R acc = R(0);")
     ind = "  "
 
@@ -324,6 +329,11 @@ def emit_process(name, n, outgoing_gluons, n_identical):
             em.count(n + 1, "dot")
         w(f"{ind}const cx<R> A{k} = {' + '.join(terms)};")
         em.count(n + 1, "cadd", len(terms) - 1)
+    w(f"{ind}if constexpr (CM != CM_FMA) {{")
+    w(f"{ind}  const cx<float> Aa[K] = {{{', '.join(f'A{k}' for k in range(K))}}};")
+    w(f"{ind}  acc += R(2) * cmma.sum(Aa);  // x2 helicity flip")
+    w(f"{ind}}} else {{")
+    ind += "  "
     # colour sum with the symmetric integer matrix: sum_i Re(A_i^* (C_ii/2 A_i + sum_{j>i} C_ij A_j)) * 2
     w(f"{ind}R cs = R(0);")
     for i in range(K):
@@ -338,6 +348,8 @@ def emit_process(name, n, outgoing_gluons, n_identical):
         w(f"{ind}  cs += A{i}.r * zr + A{i}.i * zi; }}")
         em.flops_per_level[n + 1] += 4 * len(parts_r) + 4
     w(f"{ind}acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip")
+    ind = ind[:-2]
+    w(f"{ind}}}")
     for L in range(nlev - 1, -1, -1):
         ind = ind[:-2]
         w(f"{ind}}}")

@@ -20,7 +20,7 @@ RW_WARN_BAD_EVENTS = 1
 ERRORS = {-1: "RW_ERR_NULL", -2: "RW_ERR_ARG", -3: "RW_ERR_MODE", -4: "RW_ERR_PARAM", -5: "RW_ERR_CUDA",
           -6: "RW_ERR_STATE", -7: "RW_ERR_ALIGN", -8: "RW_ERR_WORKSPACE"}
 PROCESS = {"ee_mumu": 0, "gg_tt": 1, "gg_ttg": 2, "gg_ttgg": 3}
-MODE = {"fp64": 0, "fp32": 1}
+MODE = {"fp64": 0, "fp32": 1, "mixed_fp16": 2, "mixed_bf16": 3}
 MAX_POINTS = 256
 PARAM_FIELDS = ("alpha_s", "m_t", "w_t", "yt_scale", "alpha_em_inv", "G_F", "m_Z", "w_Z")
 
@@ -69,6 +69,8 @@ def load():
         "rw_reweight": ([P, P, P, P, P, P], i),
         "rw_workspace_bytes_host": ([P, i64], sz),
         "rw_reweight_host": ([P, P, P, i64, P, P, P, P, P, sz], i),
+        "rw_get_tuning": ([P, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+        "rw_autotune": ([P, i64, ctypes.c_char_p, ctypes.POINTER(d)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -149,6 +151,18 @@ class Context:
 
     def set_tuning(self, lane_bits: int = -1, block: int = 0):
         return self._check(self.lib.rw_set_tuning(self.h, int(lane_bits), int(block)), "rw_set_tuning")
+
+    def get_tuning(self):
+        lb, bl = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.rw_get_tuning(self.h, ctypes.byref(lb), ctypes.byref(bl)), "rw_get_tuning")
+        return lb.value, bl.value
+
+    def autotune(self, max_events: int = 1 << 18, cache_path: str | None = None) -> float:
+        """Time every compiled launch shape on the attached events; keep the fastest."""
+        ms = ctypes.c_double()
+        self._check(self.lib.rw_autotune(self.h, int(max_events), cache_path.encode() if cache_path else None,
+                                         ctypes.byref(ms)), "rw_autotune")
+        return ms.value
 
     def workspace_bytes(self, n_events: int) -> int:
         return int(self.lib.rw_workspace_bytes(self.h, int(n_events)))

@@ -311,3 +311,78 @@ def test_gg_tt_full_size_sampled(mode):
     exact = math.fsum(g["wnew"][0])
     assert abs(g["sigma"][0] - exact) <= 2 * np.spacing(exact)
     assert g["n_bad"] == 0
+
+
+# --------------------------------------------------------------------------
+# autotuner
+# --------------------------------------------------------------------------
+def test_autotune_keeps_parity_and_uses_its_cache(tmp_path):
+    pts = ev.reweight_points("gg_tt_1m")
+    mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 5003, pts)
+    dm, dw = to_dev(mom), to_dev(w)
+    cache = str(tmp_path / "tune.jsonl")
+    chosen = []
+    for _ in range(2):
+        with rwgt.Context(0, torch.cuda.current_stream().cuda_stream) as c:
+            c.set_process("gg_tt", "fp64")
+            c.set_params(ev.param_vector())
+            c.set_reweight_points(pts)
+            nb = c.workspace_bytes(5003)
+            ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+            c.load_events(dm, dw, 5003, ws, nb)
+            ms = c.autotune(max_events=1000, cache_path=cache)  # a sub-range of a longer batch
+            assert ms > 0
+            lb, bl = c.get_tuning()
+            assert 0 <= lb <= 3 and bl in (64, 128, 256)
+            chosen.append((lb, bl))
+            wnew = torch.empty((1, 5003), dtype=torch.float64, device=DEV)
+            c.reweight_async(wnew)
+            sig, so, nbad, rc = c.get_results(1)
+            assert rel(wnew.cpu().numpy(), o["wnew"]).max() < 1e-12
+            assert abs(sig[0] / o["sigma"][0] - 1) < 1e-12
+    assert chosen[0] == chosen[1]
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and '"lane_bits"' in lines[0]
+
+
+# --------------------------------------------------------------------------
+# mixed precision: FP32 amplitudes, tensor-core colour sum in FP16 / BF16
+# --------------------------------------------------------------------------
+def mixed_bound(mode, n_gluons):
+    """Rounding J to p significant bits changes J^dagger C J by at most
+    2 u sqrt(kappa(C)) relative (u = 2^-p, kappa the colour matrix's condition
+    number), plus the FP32 amplitude error (1e-5)."""
+    C, _ = oracle.colour_matrix(n_gluons)
+    ev_ = np.linalg.eigvalsh(C)
+    u = 2.0 ** -11 if mode == "mixed_fp16" else 2.0 ** -8
+    return 2 * u * math.sqrt(ev_.max() / ev_.min()) + 1e-5
+
+
+@pytest.mark.parametrize("mode", ["mixed_fp16", "mixed_bf16"])
+@pytest.mark.parametrize("proc,wl,n,lbs,pts", [
+    ("gg_tt", "gg_tt_1m", 5003, (0, 1), ev.reweight_points("gg_tt_1m")),
+    ("gg_ttg", "gg_ttg_4m", 611, (0, 1, 2), ev.reweight_points("gg_ttg_4m", "mt")[::21]),
+    ("gg_ttgg", "gg_ttgg_1m", 197, (1, 2, 3), ev.reweight_points("gg_ttgg_1m", "mt")),
+])
+def test_mixed_precision_colour_sum(mode, proc, wl, n, lbs, pts):
+    mom, w, o = oracle_run(proc, wl, n, pts)
+    b = mixed_bound(mode, ev.N_EXTERNAL[proc] - 2)
+    for lb in lbs:
+        g = run_gpu(proc, mode, mom, w, pts, lane_bits=lb)
+        assert rel(g["me0"], o["me0"]).max() < b
+        assert rel(g["me"], o["me"]).max() < b
+        assert rel(g["ratio"], o["ratio"]).max() < 2 * b
+        for j in range(len(g["sigma"])):
+            exact_gpu = math.fsum(g["wnew"][j])
+            assert abs(g["sigma"][j] - exact_gpu) <= 2 * np.spacing(exact_gpu)
+            assert abs(g["sigma"][j] / o["sigma"][j] - 1) < 2 * b
+        # the rounding is not systematic: the mean error is far below the bound
+        assert rel(g["me0"], o["me0"]).mean() < b / 4
+
+
+def test_mixed_modes_reject_large_blocks():
+    with rwgt.Context(0) as c:
+        c.set_process("gg_ttg", "mixed_fp16")
+        with pytest.raises(rwgt.RwError) as e:
+            c.set_tuning(0, 256)
+        assert e.value.code == -2
