@@ -64,6 +64,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="learned-surrogate run on g g -> t tbar g g: train on exact labels, then time "
+                         "surrogate inference with exact fallback against the exact kernel")
+    ap.add_argument("--train-events", type=int, default=1 << 20)
+    ap.add_argument("--train-steps", type=int, default=16000)
+    ap.add_argument("--infer-events", type=int, default=1 << 22)
     return ap.parse_args()
 
 
@@ -382,10 +388,136 @@ def run_e2e(ctx, torch, dev, mom_h, w_h, E, P, N, world, args):
             "d2h_bytes_per_step": int(8 * (P * E + P + 2)), "ms_per_step": 1e3 * t, "steps": steps}
 
 
+def run_surrogate(args):
+    """Learned surrogate (g g -> t tbar g g, m_t = kappa 173 GeV): exact FP32
+    labels log r on a 16-point kappa grid in [0.8, 1.2] for --train-events
+    events, MLP (24 momentum components + kappa + 15 invariants -> 4 x 256 SiLU
+    -> (mu, s)) trained by the library's kernels, error threshold calibrated on
+    held-out events for a 0.1 % violation rate of |d log r| <= 1e-3, then
+    --infer-events unseen events at kappa = 0.9, 1.1, 1.2 reweighted by the
+    surrogate with exact fallback; the exact FP32 path on the same events and
+    points is the comparison and the judge of every accepted event."""
+    import torch
+    from paper_2312_07440_gb300 import rwgt
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    wl = ev.WORKLOADS["gg_ttgg_1m"]
+    kg = np.linspace(0.8, 1.2, 16)
+    grid = np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in kg])
+    n_in, hidden, layers, batch, p_scale, k_scale = 40, 256, 4, 16384, 2000.0, 0.2
+
+    def attach(c, mom, w, pts, mode="fp32"):
+        E = mom.shape[-1]
+        dm, dw = torch.from_numpy(mom).to(dev), torch.from_numpy(w).to(dev)
+        c.set_process("gg_ttgg", mode)
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(pts)
+        nb = c.workspace_bytes(E)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        c.load_events(dm, dw, E, ws, nb)
+        return dm, dw, ws
+
+    def labelled(mom, w, pts):
+        E, P = mom.shape[-1], pts.shape[0]
+        with rwgt.Context(0, st) as c:
+            keep = attach(c, mom, w, pts)
+            ratio = torch.empty((P, E), dtype=torch.float64, device=dev)
+            c.reweight_async(None, ratio)
+            x = torch.empty((P * E, n_in), dtype=torch.float32, device=dev)
+            y = torch.empty(P * E, dtype=torch.float32, device=dev)
+            rwgt.surrogate_features(c, n_in, p_scale, k_scale, ratio, x, y)
+            torch.cuda.synchronize()
+            del keep
+        return x, y
+
+    t0 = time.perf_counter()
+    mom_tr, w_tr = ev.generate(wl, args.train_events)
+    mom_ca, w_ca = ev.generate(wl, 16384, start=args.train_events)
+    x_tr, y_tr = labelled(mom_tr, w_tr, grid)
+    x_ca, y_ca = labelled(mom_ca, w_ca, grid)
+    t_labels = time.perf_counter() - t0
+    tau = float(y_tr.std())
+    m = rwgt.Mlp(0, st, n_in, hidden, layers, batch, seed=2024)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for frac, lr in ((0.4, 1e-3), (0.3, 3e-4), (0.2, 1e-4), (0.1, 3e-5)):
+        m.train(x_tr, y_tr, batch, int(frac * args.train_steps), lr, tau, 0.05, seed=31)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    out = torch.empty((x_ca.shape[0], 2), dtype=torch.float32, device=dev)
+    m.forward(x_ca, out)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    dk = np.repeat(kg - 1.0, 16384)
+    mu, s_err, yl = dk * o[:, 0], o[:, 1] + np.log(np.abs(dk)), dk * y_ca.cpu().numpy()
+    order = np.argsort(s_err)
+    bad = np.cumsum(np.abs(mu - yl)[order] > 1e-3)
+    okk = np.nonzero(bad <= 1e-3 * np.arange(1, len(order) + 1))[0]
+    s_max = float(s_err[order][okk[-1]]) if okk.size else -1e30
+    del x_tr, y_tr
+    # inference: surrogate + exact fallback vs exact, same events and points
+    pts = np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in (0.9, 1.1, 1.2)])
+    P = pts.shape[0]
+    mom_te, w_te = ev.generate(wl, args.infer_events, start=args.train_events + 16384)
+    E = mom_te.shape[-1]
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    with rwgt.Context(0, st) as c:
+        keep = attach(c, mom_te, w_te, pts)
+        c.autotune(max_events=1 << 16)
+        w_ex = torch.empty((P, E), dtype=torch.float64, device=dev)
+        t_ex = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            c.reweight_async(w_ex)
+            sig_ex, _, _, _ = c.get_results(P)
+            if i >= args.warmup:
+                t_ex.append(time.perf_counter() - t1)
+        sb = c.surrogate_workspace_bytes(n_in)
+        sws = torch.empty(sb, dtype=torch.uint8, device=dev)
+        w_su = torch.empty((P, E), dtype=torch.float64, device=dev)
+        flag = torch.empty((P, E), dtype=torch.uint8, device=dev)
+        t_su = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            sig_su, nfb = rwgt.surrogate_reweight(c, m, p_scale, k_scale, s_max, w_su, flag, P, sws, sb)
+            if i >= args.warmup:
+                t_su.append(time.perf_counter() - t1)
+        del keep
+    fl = flag.cpu().numpy().astype(bool)
+    a, b = w_su.cpu().numpy(), w_ex.cpu().numpy()
+    err = np.abs(np.log(a[~fl] / b[~fl])) if (~fl).any() else np.zeros(0)
+    t_ex_s, t_su_s = statistics.median(t_ex), statistics.median(t_su)
+    line = {
+        "metric": METRIC, "value": E * P / t_su_s, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_su_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 MLP (fp32 first/last layers) + f32 exact fallback", "data": "synthetic",
+        "config": {"workload": "surrogate gg_ttgg", "infer_events": E, "points_kappa": [0.9, 1.1, 1.2],
+                   "train_events": args.train_events, "train_labels": int(args.train_events * 16),
+                   "train_steps": args.train_steps, "batch": batch, "mlp": f"{n_in}->{layers}x{hidden} SiLU->2",
+                   "error_bound": "|d log r| <= 1e-3, calibrated for 0.1 % violations on 16384 held-out events"},
+        "surrogate": {"exact_value": E * P / t_ex_s, "gain_vs_exact": t_ex_s / t_su_s,
+                      "fallback_fraction": float(fl.mean()), "accepted_violation_rate":
+                          float(np.mean(err > 1e-3)) if err.size else 0.0,
+                      "accepted_err_max": float(err.max()) if err.size else 0.0,
+                      "sigma_rel_diff": [float(x / y - 1) for x, y in zip(sig_su, sig_ex)],
+                      "label_seconds": t_labels, "train_seconds": t_train, "s_max": s_max},
+        "timing": "wall clock per step incl. host sync (both paths), L2 flushed before each step",
+    }
+    print(json.dumps(line), flush=True)
+    m.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.surrogate:
+        run_surrogate(args)
     else:
         run_ours(args)
 

@@ -165,6 +165,62 @@ int rw_reweight_host(rw_ctx* ctx, const double* h_mom, const double* h_w, int64_
                      size_t workspace_bytes);
 
 /* ---------------------------------------------------------------------------
+   Learned surrogate for log r (spec extension; the paper has none).
+   An MLP n_in -> [hidden, SiLU] x n_layers -> 2 predicts mu = log r and
+   s = log of its own error for a feature vector built from an event and a
+   parameter point; BF16 weights/activations, FP32 accumulation on the tensor
+   cores, FP32 master weights and Adam.  The object owns its device memory
+   (parameters, optimiser state, activations for max_batch rows).
+   Parameter vector layout: for each linear layer l = 0..n_layers,
+   W_l [in_l][out_l] row-major then b_l [out_l]. */
+typedef struct rw_mlp rw_mlp;
+int rw_mlp_create(rw_mlp** m, int device, void* cuda_stream, int n_in, int hidden, int n_layers, int max_batch,
+                  uint64_t seed);
+int rw_mlp_destroy(rw_mlp* m);
+const char* rw_mlp_last_error(const rw_mlp* m);
+int64_t rw_mlp_n_params(const rw_mlp* m);
+/* shape and stream the model was created with (pointers may be NULL) */
+int rw_mlp_info(const rw_mlp* m, int* n_in, int* hidden, int* n_layers, void** cuda_stream);
+/* checkpoint / resume: FP32 parameters, Adam moments (may be NULL) and step */
+int rw_mlp_get_state(rw_mlp* m, float* h_params, float* h_m1, float* h_m2, int64_t* h_step);
+int rw_mlp_set_state(rw_mlp* m, const float* h_params, const float* h_m1, const float* h_m2, int64_t step);
+/* out [n][2] = (mu, s) for features x [n][n_in] (device, FP32) */
+int rw_mlp_forward(rw_mlp* m, const float* d_x, int64_t n, float* d_out);
+/* loss and its gradient at the current parameters for n <= max_batch rows
+   (no update): loss = mean ((y-mu)/tau)^2 + lam (r^2 e^{-2s}/2 + s), r = y - mu
+   held constant in the second term; h_grad [n_params] may be NULL. Synchronises. */
+int rw_mlp_gradient(rw_mlp* m, const float* d_x, const float* d_y, int64_t n, float tau, float lam, float* h_grad,
+                    float* h_loss);
+/* n_steps Adam steps on minibatches of `batch` rows drawn with a counter-based
+   generator from (seed, step) out of x [n][n_in], y [n]; asynchronous. */
+int rw_mlp_train(rw_mlp* m, const float* d_x, const float* d_y, int64_t n, int batch, int64_t n_steps, float lr,
+                 float tau, float lam, uint64_t seed);
+
+/* Surrogate features of the attached events for every point p, row p*E + e:
+   x = (p_i^mu / p_scale for all N particles after the rotation about the beam
+   axis that puts the top's p_T along +x, (kappa_p - 1)/k_scale, then -- when
+   n_in leaves room for them -- the N(N-1)/2 pairwise invariants
+   2 p_i.p_j / s-hat, zero padding) [n_in],
+   kappa_p = m_t(point p) / m_t(original); and, when d_ratio [P][E] is not NULL,
+   labels y [P*E] = log r / (kappa_p - 1) (0 where r <= 0 or kappa_p = 1): the
+   network's mu predicts log r per unit shift and s the log of its error in
+   log r per unit shift.  Device buffers. */
+int rw_surrogate_features(rw_ctx* ctx, int n_in, double p_scale, double k_scale, const double* d_ratio, float* d_x,
+                          float* d_y);
+/* Surrogate reweighting of the attached events for every point (Sec. 3.2
+   steps 5-7 with the MLP in place of |M'|^2/|M|^2): r = exp((kappa-1) mu);
+   events whose predicted log error of log r, s + log|kappa - 1|, exceeds s_max
+   fall back to the exact fused kernel; W'[P][E],
+   optional fallback flags [P][E] (1 = exact), sigma'_p (h_sigma [P]) and the
+   fallback counts (h_n_fallback [P]).  The model must be created on the
+   context's stream with the width n_in used here.  Device workspace of
+   rw_surrogate_workspace_bytes(ctx, n_in); synchronises. */
+size_t rw_surrogate_workspace_bytes(const rw_ctx* ctx, int n_in);
+int rw_surrogate_reweight(rw_ctx* ctx, rw_mlp* m, double p_scale, double k_scale, double s_max, double* d_wnew,
+                          unsigned char* d_fallback, double* h_sigma, int64_t* h_n_fallback, void* d_workspace,
+                          size_t workspace_bytes);
+
+/* ---------------------------------------------------------------------------
    Allocation-free variant of rw_reweight_async.  The paper has no counterpart:
    it exists for callers that cannot allocate device memory -- code that runs
    inside a host framework owning the whole device memory budget up front

@@ -1,0 +1,625 @@
+// Learned surrogate for log r = log(|M'|^2/|M|^2): a multilayer perceptron
+// n_in -> [hidden, SiLU] x n_layers -> 2 (mu = predicted log r, s = predicted
+// log of its error).  Hidden layers: BF16 weights and activations, FP32
+// accumulation on the tensor cores (mma.sync m16n8k16); the first layer (from
+// the unrounded FP32 features) and the output layer run in FP32 (about 4 % of
+// the flops); FP32 master weights with Adam.  Every step
+// of training and inference runs in the kernels of this file:
+//   k_gemm<EPI>    C = A B with strided (optionally transposed) BF16 operands,
+//                  fused epilogues: bias + SiLU (forward), bias (output layer),
+//                  x SiLU'(z) (backward data), FP32 store (weight gradients)
+//   k_colsum       bias gradients
+//   k_loss         MSE on mu + Gaussian NLL on s with the residual detached
+//   k_adam         Adam on FP32 master weights, BF16 copies for the GEMMs
+//   k_gather_rows  minibatch gather
+// The C ABI (rw_mlp_*) is declared in include/rwgt.h.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/rwgt.h"
+
+namespace {
+
+using bf16 = unsigned short;
+
+__device__ __forceinline__ float bf2f(bf16 x) { return __bfloat162float(__ushort_as_bfloat16(x)); }
+__device__ __forceinline__ bf16 f2bf(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
+
+enum Epi { EPI_FWD_SILU = 0, EPI_FWD_LINEAR = 1, EPI_BWD_DATA = 2, EPI_WGRAD = 3 };
+
+struct GemmArgs {
+  const bf16* A;  // element (m, k) at A[m * sam + k * sak]
+  const bf16* B;  // element (k, n) at B[k * sbk + n * sbn]
+  long long sam, sak, sbk, sbn;
+  int M, N, K;
+  const float* bias;  // [N] (forward epilogues)
+  float* Zf;          // FWD_SILU: pre-activation out [M][N]; BWD_DATA: pre-activation in [M][N]
+  bf16* H;            // FWD_SILU: activation out; BWD_DATA: dZ out  [M][N] bf16
+  float* C;           // FWD_LINEAR / WGRAD: FP32 out [M][N]
+};
+
+constexpr int BM = 64, BN = 64, BK = 32, LDA = BK + 8;
+
+// 128 threads, 2 x 2 warps, each warp 32 x 32 (2 m16 tiles x 4 n8 tiles).
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
+  __shared__ __align__(16) bf16 As[BM * LDA];  // [m][k]
+  __shared__ __align__(16) bf16 Bs[BN * LDA];  // [n][k]
+  const int tid = threadIdx.x, warp = tid >> 5, l = tid & 31;
+  const int gr = l >> 2, gc = l & 3;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    // cooperative tile loads (bounds -> zero); consecutive threads walk the
+    // operand's contiguous dimension
+    const bool a_k_fast = g.sak == 1, b_k_fast = g.sbk == 1;
+#pragma unroll 4
+    for (int i = tid; i < BM * BK; i += 128) {
+      const int mm = a_k_fast ? i / BK : i % BM, kk = a_k_fast ? i % BK : i / BM;
+      const int m = m0 + mm, k = k0 + kk;
+      As[mm * LDA + kk] = (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : (bf16)0;
+    }
+#pragma unroll 4
+    for (int i = tid; i < BN * BK; i += 128) {
+      const int nn = b_k_fast ? i / BK : i % BN, kk = b_k_fast ? i % BK : i / BN;
+      const int n = n0 + nn, k = k0 + kk;
+      Bs[nn * LDA + kk] = (n < g.N && k < g.K) ? g.B[k * g.sbk + n * g.sbn] : (bf16)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      unsigned af[2][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r0 = wm + i * 16 + gr;
+        af[i][0] = *reinterpret_cast<const unsigned*>(&As[r0 * LDA + kk + 2 * gc]);
+        af[i][1] = *reinterpret_cast<const unsigned*>(&As[(r0 + 8) * LDA + kk + 2 * gc]);
+        af[i][2] = *reinterpret_cast<const unsigned*>(&As[r0 * LDA + kk + 8 + 2 * gc]);
+        af[i][3] = *reinterpret_cast<const unsigned*>(&As[(r0 + 8) * LDA + kk + 8 + 2 * gc]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c0 = wn + j * 8 + gr;
+        bfr[j][0] = *reinterpret_cast<const unsigned*>(&Bs[c0 * LDA + kk + 2 * gc]);
+        bfr[j][1] = *reinterpret_cast<const unsigned*>(&Bs[c0 * LDA + kk + 8 + 2 * gc]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
+    }
+    __syncthreads();
+  }
+  // epilogue: acc[i][j] = rows (wm+16i+gr, +8), cols (wn+8j+2gc, +1)
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int m = m0 + wm + i * 16 + gr + (q >= 2 ? 8 : 0);
+        const int n = n0 + wn + j * 8 + 2 * gc + (q & 1);
+        if (m >= g.M || n >= g.N) continue;
+        const long long o = (long long)m * g.N + n;
+        const float v = acc[i][j][q];
+        if constexpr (EPI == EPI_FWD_SILU) {
+          const float z = v + g.bias[n];
+          g.Zf[o] = z;
+          g.H[o] = f2bf(z * sigmoidf_(z));
+        } else if constexpr (EPI == EPI_FWD_LINEAR) {
+          g.C[o] = v + g.bias[n];
+        } else if constexpr (EPI == EPI_BWD_DATA) {
+          const float z = g.Zf[o];
+          const float s = sigmoidf_(z);
+          g.H[o] = f2bf(v * s * (1.0f + z * (1.0f - s)));
+        } else {
+          g.C[o] = v;
+        }
+      }
+}
+
+// First layer in FP32 (the inputs are never rounded): Z = X W + b,
+// H = bf16(SiLU(Z)); one thread per (row, unit), W [nin][N] FP32.
+__global__ void k_dense_in(const float* __restrict__ X, int B, int nin, const float* __restrict__ W,
+                           const float* __restrict__ b, int N, float* __restrict__ Z, bf16* __restrict__ H) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)B * N) return;
+  const int r = (int)(t / N), n = (int)(t % N);
+  float z = b[n];
+  for (int k = 0; k < nin; ++k) z = fmaf(X[(long long)r * nin + k], W[(long long)k * N + n], z);
+  Z[t] = z;
+  H[t] = f2bf(z * sigmoidf_(z));
+}
+
+// Output layer in FP32 from the last pre-activation: out = SiLU(Z) W + b,
+// W [K][2]; one warp per row.
+__global__ void k_dense_out(const float* __restrict__ Z, int B, int K, const float* __restrict__ W,
+                            const float* __restrict__ b, float* __restrict__ out) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), l = threadIdx.x & 31;
+  if (r >= B) return;
+  float a0 = 0.0f, a1 = 0.0f;
+  for (int k = l; k < K; k += 32) {
+    const float z = Z[(long long)r * K + k];
+    const float h = z * sigmoidf_(z);
+    a0 = fmaf(h, W[2 * k], a0);
+    a1 = fmaf(h, W[2 * k + 1], a1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+  }
+  if (l == 0) {
+    out[2 * r] = a0 + b[0];
+    out[2 * r + 1] = a1 + b[1];
+  }
+}
+
+// Backward through the output layer: dZ[r][k] = (sum_o dOut[r][o] W[k][o]) SiLU'(Z[r][k])
+__global__ void k_dense_out_bwd(const float* __restrict__ dout, const float* __restrict__ Z, int B, int K,
+                                const float* __restrict__ W, bf16* __restrict__ dZ) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)B * K) return;
+  const int r = (int)(t / K), k = (int)(t % K);
+  const float z = Z[t], s = sigmoidf_(z);
+  const float dh = dout[2 * r] * W[2 * k] + dout[2 * r + 1] * W[2 * k + 1];
+  dZ[t] = f2bf(dh * s * (1.0f + z * (1.0f - s)));
+}
+
+// db[n] = sum_m dZ[m][n]   (one thread per column, fixed order)
+__global__ void k_colsum(const bf16* __restrict__ dZ, int M, int N, float* __restrict__ out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.0f;
+  for (int m = 0; m < M; ++m) s += bf2f(dZ[(long long)m * N + n]);
+  out[n] = s;
+}
+
+// db[n] = sum_m D[m][n] for an FP32 matrix
+__global__ void k_colsum_f32(const float* __restrict__ D, int M, int N, float* __restrict__ out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.0f;
+  for (int m = 0; m < M; ++m) s += D[(long long)m * N + n];
+  out[n] = s;
+}
+
+// Loss per sample (mean over the batch): ((y - mu)/tau)^2 + lam (r^2 e^{-2s}/2 + s),
+// r = y - mu treated as a constant in the second term.  Writes dOut [B][2]
+// (FP32 and BF16) and the per-sample loss.
+__global__ void k_loss(const float* __restrict__ out, const float* __restrict__ y, int B, float inv_tau2, float lam,
+                       float* __restrict__ dout_f, bf16* __restrict__ dout_b, float* __restrict__ loss) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const float mu = out[2 * b], s = fminf(fmaxf(out[2 * b + 1], -16.0f), 4.0f);
+  const float r = y[b] - mu;
+  const float e2 = __expf(-2.0f * s);
+  const float dmu = -2.0f * r * inv_tau2 / B;
+  const float ds = lam * (1.0f - r * r * e2) / B;
+  dout_f[2 * b] = dmu;
+  dout_f[2 * b + 1] = ds;
+  dout_b[2 * b] = f2bf(dmu);
+  dout_b[2 * b + 1] = f2bf(ds);
+  loss[b] = r * r * inv_tau2 + lam * (0.5f * r * r * e2 + s);
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m1,
+                       float* __restrict__ m2, bf16* __restrict__ pb, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = gr[i];
+  const float a = b1 * m1[i] + (1.0f - b1) * g;
+  const float v = b2 * m2[i] + (1.0f - b2) * g * g;
+  m1[i] = a;
+  m2[i] = v;
+  const float q = p[i] - lr * (a / c1) / (sqrtf(v / c2) + eps);
+  p[i] = q;
+  pb[i] = f2bf(q);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ x, bf16* __restrict__ y, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = f2bf(x[i]);
+}
+
+// rows idx[b] of X [*][nin] (FP32) -> Xf [B][nin] (FP32) and Xb (BF16), y[idx[b]] -> yb[b]
+__global__ void k_gather_rows(const float* __restrict__ X, const float* __restrict__ y, const int64_t* __restrict__ idx,
+                              int B, int nin, float* __restrict__ Xf, bf16* __restrict__ Xb, float* __restrict__ yb) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)B * nin) return;
+  const int b = (int)(t / nin), j = (int)(t % nin);
+  const int64_t r = idx[b];
+  const float v = X[r * nin + j];
+  Xf[t] = v;
+  Xb[t] = f2bf(v);
+  if (j == 0 && y) yb[b] = y[r];
+}
+
+// minibatch indices: a counter-based hash (splitmix64) of (seed, step, b)
+__global__ void k_batch_indices(uint64_t seed, uint64_t step, int B, int64_t n, int64_t* __restrict__ idx) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (step * 0x100000001ull + (uint64_t)b + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  idx[b] = (int64_t)(z % (uint64_t)n);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the model object
+// ---------------------------------------------------------------------------
+struct rw_mlp {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n_in = 0, hidden = 0, n_layers = 0, max_batch = 0;
+  int n_out = 2;
+  std::vector<int> din, dout;           // per linear layer
+  std::vector<long long> w_off, b_off;  // offsets in the parameter vector
+  long long n_params = 0;
+  float *p = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;  // FP32 [n_params]
+  bf16* pb = nullptr;                                              // BF16 copy
+  long long step = 0;
+  // activations for one batch
+  bf16* X = nullptr;                  // [max_batch][n_in] (BF16 copy, weight gradients)
+  float* Xf = nullptr;                // [max_batch][n_in] FP32 (training minibatch)
+  std::vector<bf16*> H;               // per hidden layer [max_batch][hidden]
+  std::vector<float*> Z;              // pre-activations
+  float* out = nullptr;               // [max_batch][2]
+  float* dout_f = nullptr;
+  bf16* dout_b = nullptr;
+  bf16 *dA = nullptr, *dB = nullptr;  // dZ ping-pong [max_batch][hidden]
+  float* loss = nullptr;              // [max_batch]
+  float* yb = nullptr;
+  int64_t* idx = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int mlp_fail(rw_mlp* m, int code, const char* msg) {
+  if (m) m->err = msg;
+  return code;
+}
+
+int launch_gemm(rw_mlp* m, int epi, GemmArgs a) {
+  dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM);
+  switch (epi) {
+    case EPI_FWD_SILU: k_gemm<EPI_FWD_SILU><<<grid, 128, 0, m->stream>>>(a); break;
+    case EPI_FWD_LINEAR: k_gemm<EPI_FWD_LINEAR><<<grid, 128, 0, m->stream>>>(a); break;
+    case EPI_BWD_DATA: k_gemm<EPI_BWD_DATA><<<grid, 128, 0, m->stream>>>(a); break;
+    default: k_gemm<EPI_WGRAD><<<grid, 128, 0, m->stream>>>(a); break;
+  }
+  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "gemm launch");
+}
+
+// Forward for B <= max_batch rows of FP32 features xf (device); output in
+// m->out.  First and last layers in FP32, hidden layers BF16 on the tensor cores.
+int forward_batch(rw_mlp* m, const float* xf, int B) {
+  const int L = m->n_layers;
+  k_dense_in<<<(unsigned)(((long long)B * m->hidden + 255) / 256), 256, 0, m->stream>>>(
+      xf, B, m->n_in, m->p + m->w_off[0], m->p + m->b_off[0], m->hidden, m->Z[0], m->H[0]);
+  for (int l = 1; l < L; ++l) {
+    GemmArgs a{};
+    a.A = m->H[l - 1];
+    a.sam = m->hidden;
+    a.sak = 1;
+    a.B = m->pb + m->w_off[l];
+    a.sbk = m->dout[l];
+    a.sbn = 1;
+    a.M = B;
+    a.N = m->dout[l];
+    a.K = m->din[l];
+    a.bias = m->p + m->b_off[l];
+    a.Zf = m->Z[l];
+    a.H = m->H[l];
+    int rc = launch_gemm(m, EPI_FWD_SILU, a);
+    if (rc) return rc;
+  }
+  k_dense_out<<<(B + 7) / 8, 256, 0, m->stream>>>(m->Z[L - 1], B, m->hidden, m->p + m->w_off[L], m->p + m->b_off[L],
+                                                 m->out);
+  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "forward launch");
+}
+
+// Backward: gradients of the loss (m->dout_f set, m->X holds the BF16
+// inputs) into m->g.  Weight gradients on the tensor cores (BF16 operands,
+// FP32 accumulation); the output layer's backward in FP32.
+int backward_batch(rw_mlp* m, int B) {
+  const int L = m->n_layers;
+  int rc;
+  // output layer: dW = H_{L-1}^T dOut, db = colsum(dOut), dZ_{L-1}
+  {
+    GemmArgs w{};
+    w.A = m->H[L - 1];
+    w.sam = 1;
+    w.sak = m->hidden;
+    w.B = m->dout_b;
+    w.sbk = m->n_out;
+    w.sbn = 1;
+    w.M = m->hidden;
+    w.N = m->n_out;
+    w.K = B;
+    w.C = m->g + m->w_off[L];
+    if ((rc = launch_gemm(m, EPI_WGRAD, w))) return rc;
+    k_colsum_f32<<<1, 128, 0, m->stream>>>(m->dout_f, B, m->n_out, m->g + m->b_off[L]);
+    k_dense_out_bwd<<<(unsigned)(((long long)B * m->hidden + 255) / 256), 256, 0, m->stream>>>(
+        m->dout_f, m->Z[L - 1], B, m->hidden, m->p + m->w_off[L], m->dA);
+  }
+  bf16* bufs[2] = {m->dA, m->dB};
+  int cur = 0;  // dZ of layer l lives in bufs[cur]
+  for (int l = L - 1; l >= 0; --l) {
+    const bf16* dZ = bufs[cur];
+    const bf16* Hin = l == 0 ? m->X : m->H[l - 1];
+    const int nin = m->din[l];
+    GemmArgs w{};
+    w.A = Hin;
+    w.sam = 1;
+    w.sak = nin;
+    w.B = dZ;
+    w.sbk = m->hidden;
+    w.sbn = 1;
+    w.M = nin;
+    w.N = m->hidden;
+    w.K = B;
+    w.C = m->g + m->w_off[l];
+    if ((rc = launch_gemm(m, EPI_WGRAD, w))) return rc;
+    k_colsum<<<(m->hidden + 127) / 128, 128, 0, m->stream>>>(dZ, B, m->hidden, m->g + m->b_off[l]);
+    if (l == 0) break;
+    GemmArgs d{};
+    d.A = dZ;
+    d.sam = m->hidden;
+    d.sak = 1;
+    d.B = m->pb + m->w_off[l];  // (k = out unit, n = in unit) -> W[n][k]
+    d.sbk = 1;
+    d.sbn = m->dout[l];
+    d.M = B;
+    d.N = nin;
+    d.K = m->hidden;
+    d.Zf = m->Z[l - 1];
+    d.H = bufs[cur ^ 1];
+    if ((rc = launch_gemm(m, EPI_BWD_DATA, d))) return rc;
+    cur ^= 1;
+  }
+  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "backward launch");
+}
+
+template <class T>
+bool dalloc(T** p, size_t n) {
+  return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T)) == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rw_mlp_create(rw_mlp** out, int device, void* stream, int n_in, int hidden, int n_layers, int max_batch,
+                  uint64_t seed) {
+  if (!out) return RW_ERR_NULL;
+  *out = nullptr;
+  if (n_in < 1 || n_in % 8 || hidden < 8 || hidden % 8 || n_layers < 1 || n_layers > 16 || max_batch < 1 ||
+      max_batch > (1 << 24))
+    return RW_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return RW_ERR_CUDA;
+  rw_mlp* m = new rw_mlp();
+  m->device = device;
+  m->stream = static_cast<cudaStream_t>(stream);
+  m->n_in = n_in;
+  m->hidden = hidden;
+  m->n_layers = n_layers;
+  m->max_batch = max_batch;
+  long long off = 0;
+  for (int l = 0; l <= n_layers; ++l) {
+    const int a = l == 0 ? n_in : hidden, b = l == n_layers ? m->n_out : hidden;
+    m->din.push_back(a);
+    m->dout.push_back(b);
+    m->w_off.push_back(off);
+    off += (long long)a * b;
+    m->b_off.push_back(off);
+    off += b;
+  }
+  m->n_params = off;
+  // deterministic initialisation: uniform(-sqrt(6/fan_in), +) (SiLU gain ~ ReLU), zero biases,
+  // output layer scaled by 0.1; splitmix64 stream from the seed
+  std::vector<float> hp(off, 0.0f);
+  uint64_t st = seed;
+  auto rnd = [&st]() {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  for (int l = 0; l <= n_layers; ++l) {
+    const double lim = sqrt(6.0 / m->din[l]) * (l == n_layers ? 0.1 : 1.0);
+    for (long long i = 0; i < (long long)m->din[l] * m->dout[l]; ++i)
+      hp[m->w_off[l] + i] = (float)((2.0 * rnd() - 1.0) * lim);
+  }
+  bool ok = dalloc(&m->p, off) && dalloc(&m->g, off) && dalloc(&m->m1, off) && dalloc(&m->m2, off) &&
+            dalloc(&m->pb, off) && dalloc(&m->X, (size_t)max_batch * n_in) &&
+            dalloc(&m->Xf, (size_t)max_batch * n_in) &&
+            dalloc(&m->out, (size_t)max_batch * 2) && dalloc(&m->dout_f, (size_t)max_batch * 2) &&
+            dalloc(&m->dout_b, (size_t)max_batch * 2) && dalloc(&m->dA, (size_t)max_batch * hidden) &&
+            dalloc(&m->dB, (size_t)max_batch * hidden) && dalloc(&m->loss, (size_t)max_batch) &&
+            dalloc(&m->yb, (size_t)max_batch) && dalloc(&m->idx, (size_t)max_batch);
+  for (int l = 0; ok && l < n_layers; ++l) {
+    bf16* h = nullptr;
+    float* z = nullptr;
+    ok = dalloc(&h, (size_t)max_batch * hidden) && dalloc(&z, (size_t)max_batch * hidden);
+    m->H.push_back(h);
+    m->Z.push_back(z);
+  }
+  if (ok) ok = cudaMemcpy(m->p, hp.data(), off * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemset(m->m1, 0, off * sizeof(float)) == cudaSuccess &&
+               cudaMemset(m->m2, 0, off * sizeof(float)) == cudaSuccess;
+  if (ok) {
+    k_to_bf16<<<(unsigned)((off + 255) / 256), 256>>>(m->p, m->pb, off);
+    ok = cudaDeviceSynchronize() == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    rw_mlp_destroy(m);
+    return RW_ERR_CUDA;
+  }
+  *out = m;
+  return RW_OK;
+}
+
+int rw_mlp_destroy(rw_mlp* m) {
+  if (!m) return RW_ERR_NULL;
+  cudaSetDevice(m->device);
+  for (void* q : {(void*)m->p, (void*)m->g, (void*)m->m1, (void*)m->m2, (void*)m->pb, (void*)m->X, (void*)m->Xf,
+                  (void*)m->out,
+                  (void*)m->dout_f, (void*)m->dout_b, (void*)m->dA, (void*)m->dB, (void*)m->loss, (void*)m->yb,
+                  (void*)m->idx})
+    if (q) cudaFree(q);
+  for (auto* h : m->H) cudaFree(h);
+  for (auto* z : m->Z) cudaFree(z);
+  delete m;
+  return RW_OK;
+}
+
+const char* rw_mlp_last_error(const rw_mlp* m) { return m ? m->err.c_str() : "null model"; }
+
+int64_t rw_mlp_n_params(const rw_mlp* m) { return m ? m->n_params : -1; }
+
+int rw_mlp_info(const rw_mlp* m, int* n_in, int* hidden, int* n_layers, void** stream) {
+  if (!m) return RW_ERR_NULL;
+  if (n_in) *n_in = m->n_in;
+  if (hidden) *hidden = m->hidden;
+  if (n_layers) *n_layers = m->n_layers;
+  if (stream) *stream = static_cast<void*>(m->stream);
+  return RW_OK;
+}
+
+int rw_mlp_get_state(rw_mlp* m, float* h_params, float* h_m1, float* h_m2, int64_t* h_step) {
+  if (!m) return RW_ERR_NULL;
+  cudaSetDevice(m->device);
+  const size_t nb = m->n_params * sizeof(float);
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return mlp_fail(m, RW_ERR_CUDA, "sync");
+  if ((h_params && cudaMemcpy(h_params, m->p, nb, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (h_m1 && cudaMemcpy(h_m1, m->m1, nb, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (h_m2 && cudaMemcpy(h_m2, m->m2, nb, cudaMemcpyDeviceToHost) != cudaSuccess))
+    return mlp_fail(m, RW_ERR_CUDA, "copy");
+  if (h_step) *h_step = m->step;
+  return RW_OK;
+}
+
+int rw_mlp_set_state(rw_mlp* m, const float* h_params, const float* h_m1, const float* h_m2, int64_t step) {
+  if (!m || !h_params) return RW_ERR_NULL;
+  cudaSetDevice(m->device);
+  const size_t nb = m->n_params * sizeof(float);
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return mlp_fail(m, RW_ERR_CUDA, "sync");
+  bool ok = cudaMemcpy(m->p, h_params, nb, cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && (h_m1 ? cudaMemcpy(m->m1, h_m1, nb, cudaMemcpyHostToDevice) : cudaMemset(m->m1, 0, nb)) == cudaSuccess;
+  ok = ok && (h_m2 ? cudaMemcpy(m->m2, h_m2, nb, cudaMemcpyHostToDevice) : cudaMemset(m->m2, 0, nb)) == cudaSuccess;
+  if (!ok) return mlp_fail(m, RW_ERR_CUDA, "copy");
+  k_to_bf16<<<(unsigned)((m->n_params + 255) / 256), 256, 0, m->stream>>>(m->p, m->pb, m->n_params);
+  m->step = step < 0 ? 0 : step;
+  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "launch");
+}
+
+// out [n][2] = MLP(x [n][n_in] FP32), processed in chunks of max_batch rows
+int rw_mlp_forward(rw_mlp* m, const float* d_x, int64_t n, float* d_out) {
+  if (!m) return RW_ERR_NULL;
+  if (!d_x || !d_out) return mlp_fail(m, RW_ERR_NULL, "NULL buffer");
+  if (n <= 0) return mlp_fail(m, RW_ERR_ARG, "n must be > 0");
+  cudaSetDevice(m->device);
+  for (int64_t s = 0; s < n; s += m->max_batch) {
+    const int B = (int)std::min<int64_t>(m->max_batch, n - s);
+    int rc = forward_batch(m, d_x + s * m->n_in, B);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(d_out + 2 * s, m->out, (size_t)B * 2 * sizeof(float), cudaMemcpyDeviceToDevice,
+                        m->stream) != cudaSuccess)
+      return mlp_fail(m, RW_ERR_CUDA, "copy out");
+  }
+  return RW_OK;
+}
+
+// Loss gradient at the current parameters for the first n <= max_batch rows
+// (no update): h_grad [n_params] (may be NULL), *h_loss the mean loss.
+int rw_mlp_gradient(rw_mlp* m, const float* d_x, const float* d_y, int64_t n, float tau, float lam, float* h_grad,
+                    float* h_loss) {
+  if (!m) return RW_ERR_NULL;
+  if (!d_x || !d_y) return mlp_fail(m, RW_ERR_NULL, "NULL buffer");
+  if (n <= 0 || n > m->max_batch) return mlp_fail(m, RW_ERR_ARG, "n must be in [1, max_batch]");
+  cudaSetDevice(m->device);
+  const int B = (int)n;
+  k_to_bf16<<<(unsigned)(((long long)B * m->n_in + 255) / 256), 256, 0, m->stream>>>(d_x, m->X,
+                                                                                    (long long)B * m->n_in);
+  int rc = forward_batch(m, d_x, B);
+  if (rc) return rc;
+  k_loss<<<(B + 127) / 128, 128, 0, m->stream>>>(m->out, d_y, B, 1.0f / (tau * tau), lam, m->dout_f, m->dout_b,
+                                                 m->loss);
+  rc = backward_batch(m, B);
+  if (rc) return rc;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return mlp_fail(m, RW_ERR_CUDA, "sync");
+  if (h_grad && cudaMemcpy(h_grad, m->g, m->n_params * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return mlp_fail(m, RW_ERR_CUDA, "copy");
+  if (h_loss) {
+    std::vector<float> lb(B);
+    if (cudaMemcpy(lb.data(), m->loss, B * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return mlp_fail(m, RW_ERR_CUDA, "copy");
+    double s = 0;
+    for (float v : lb) s += v;
+    *h_loss = (float)(s / B);
+  }
+  return RW_OK;
+}
+
+// Adam training: n_steps minibatches of `batch` rows drawn (counter-based,
+// with replacement) from x [n][n_in], y [n]; asynchronous on the model's
+// stream.  Resumable: the draw depends on (seed, step counter).
+int rw_mlp_train(rw_mlp* m, const float* d_x, const float* d_y, int64_t n, int batch, int64_t n_steps, float lr,
+                 float tau, float lam, uint64_t seed) {
+  if (!m) return RW_ERR_NULL;
+  if (!d_x || !d_y) return mlp_fail(m, RW_ERR_NULL, "NULL buffer");
+  if (n <= 0 || batch <= 0 || batch > m->max_batch || n_steps < 0) return mlp_fail(m, RW_ERR_ARG, "bad sizes");
+  cudaSetDevice(m->device);
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int64_t it = 0; it < n_steps; ++it) {
+    const uint64_t step = (uint64_t)m->step;
+    k_batch_indices<<<(batch + 127) / 128, 128, 0, m->stream>>>(seed, step, batch, n, m->idx);
+    k_gather_rows<<<(unsigned)(((long long)batch * m->n_in + 255) / 256), 256, 0, m->stream>>>(
+        d_x, d_y, m->idx, batch, m->n_in, m->Xf, m->X, m->yb);
+    int rc = forward_batch(m, m->Xf, batch);
+    if (rc) return rc;
+    k_loss<<<(batch + 127) / 128, 128, 0, m->stream>>>(m->out, m->yb, batch, 1.0f / (tau * tau), lam, m->dout_f,
+                                                       m->dout_b, m->loss);
+    rc = backward_batch(m, batch);
+    if (rc) return rc;
+    m->step += 1;
+    const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
+    k_adam<<<(unsigned)((m->n_params + 255) / 256), 256, 0, m->stream>>>(m->p, m->g, m->m1, m->m2, m->pb,
+                                                                         m->n_params, lr, b1, b2, eps, c1, c2);
+  }
+  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "train launch");
+}
+
+}  // extern "C"

@@ -705,3 +705,280 @@ extern "C" int rw_reweight_noalloc(rw_ctx* c, const double* d_mom, const double*
   if (e != cudaSuccess) return noalloc_fail(c, RW_ERR_CUDA, "kernel launch");
   return RW_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Surrogate: features/labels, decision, exact fallback, sigma
+// ---------------------------------------------------------------------------
+namespace {
+
+struct KappaList {
+  float k[RW_MAX_POINTS];
+};
+
+// Features x[(p*E + e)][0..n_in): the event's momenta / p_scale after the
+// azimuthal rotation about the beam that puts the top's p_T along +x (|M|^2 is
+// invariant under it), then (kappa_p - 1)/k_scale, zero padding.  Label
+// y = log r / (kappa_p - 1): the network learns the log ratio per unit shift,
+// so r = 1 at kappa = 1 holds exactly (y = 0 when kappa_p = 1 or r <= 0).
+__global__ void k_features(const double* __restrict__ mom, long long ld, long long E, int N, int P, KappaList kap,
+                           int n_in, double inv_ps, double inv_ks, const double* __restrict__ ratio,
+                           float* __restrict__ x, float* __restrict__ y) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)P * E) return;
+  const int p = (int)(t / E);
+  const long long e = t % E;
+  const double tx = mom[(long long)(2 * 4 + 1) * ld + e], ty = mom[(long long)(2 * 4 + 2) * ld + e];
+  const double pt = sqrt(tx * tx + ty * ty);
+  const double c = pt > 0.0 ? tx / pt : 1.0, s = pt > 0.0 ? ty / pt : 0.0;
+  float* xr = x + t * n_in;
+  int j = 0;
+  for (int i = 0; i < N && j + 4 <= n_in; ++i, j += 4) {
+    const double px = mom[(long long)(i * 4 + 1) * ld + e], py = mom[(long long)(i * 4 + 2) * ld + e];
+    xr[j] = (float)(mom[(long long)(i * 4) * ld + e] * inv_ps);
+    xr[j + 1] = (float)((c * px + s * py) * inv_ps);
+    xr[j + 2] = (float)((-s * px + c * py) * inv_ps);
+    xr[j + 3] = (float)(mom[(long long)(i * 4 + 3) * ld + e] * inv_ps);
+  }
+  const double dk = (double)kap.k[p] - 1.0;
+  if (j < n_in) xr[j++] = (float)(dk * inv_ks);
+  // with room for them, the pairwise invariants 2 p_i.p_j / s-hat (i < j)
+  if (n_in - j >= N * (N - 1) / 2) {
+    double q[8][4];
+    for (int i = 0; i < N && i < 8; ++i)
+      for (int m = 0; m < 4; ++m) q[i][m] = mom[(long long)(i * 4 + m) * ld + e];
+    const double sh = (q[0][0] + q[1][0]) * (q[0][0] + q[1][0]) - (q[0][1] + q[1][1]) * (q[0][1] + q[1][1]) -
+                      (q[0][2] + q[1][2]) * (q[0][2] + q[1][2]) - (q[0][3] + q[1][3]) * (q[0][3] + q[1][3]);
+    const double ish = sh > 0.0 ? 2.0 / sh : 0.0;
+    for (int a = 0; a < N && a < 8; ++a)
+      for (int b2 = a + 1; b2 < N && b2 < 8; ++b2)
+        xr[j++] = (float)((q[a][0] * q[b2][0] - q[a][1] * q[b2][1] - q[a][2] * q[b2][2] - q[a][3] * q[b2][3]) * ish);
+  }
+  for (; j < n_in; ++j) xr[j] = 0.0f;
+  if (ratio && y) {
+    const double r = ratio[t];
+    y[t] = (r > 0.0 && fabs(dk) > 1e-12) ? (float)(log(r) / dk) : 0.0f;
+  }
+}
+
+// Accept W' = exp((kappa-1) mu) W where s + log|kappa-1| <= s_max (the
+// network's predicted log error of log r), else list the event for the exact
+// path; kappa = 1 gives W' = W exactly.
+__global__ void k_decide(const float* __restrict__ out, const double* __restrict__ w, long long E, int P,
+                         KappaList kap, float s_max, double* __restrict__ wnew, unsigned char* __restrict__ flag,
+                         unsigned long long* __restrict__ count, long long* __restrict__ list) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)P * E) return;
+  const int p = (int)(t / E);
+  const long long e = t % E;
+  const double dk = (double)kap.k[p] - 1.0;
+  const float mu = out[2 * t], s = out[2 * t + 1];
+  bool accept;
+  double lr = 0.0;
+  if (fabs(dk) <= 1e-12) {
+    accept = true;
+  } else {
+    lr = dk * (double)mu;
+    accept = isfinite(mu) && isfinite(s) && (double)s + log(fabs(dk)) <= (double)s_max;
+  }
+  if (flag) flag[t] = accept ? 0 : 1;
+  if (accept) {
+    wnew[t] = exp(lr) * w[e];
+  } else {
+    const unsigned long long i = atomicAdd(count + p, 1ull);
+    list[(long long)p * E + (long long)i] = e;
+  }
+}
+
+__global__ void k_gather_events(const double* __restrict__ mom, long long ld, const double* __restrict__ w, int N,
+                                 const long long* __restrict__ list, long long n, double* __restrict__ mom_g,
+                                 double* __restrict__ w_g) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long e = list[i];
+  for (int r = 0; r < 4 * N; ++r) mom_g[(long long)r * n + i] = mom[(long long)r * ld + e];
+  w_g[i] = w[e];
+}
+
+__global__ void k_scatter(const double* __restrict__ v, const long long* __restrict__ list, long long n,
+                          double* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[list[i]] = v[i];
+}
+
+__device__ __forceinline__ void ts_acc(double& s, double& c, double x, double cx) {
+  const double t = s + x, bp = t - s;
+  c += cx + ((s - (t - bp)) + (x - bp));
+  s = t;
+}
+
+// compensated sum of x[0..n): per-block partials (fixed grid), then one block
+__global__ void k_sum_partials(const double* __restrict__ x, long long n, double2* __restrict__ part) {
+  __shared__ double2 sh[256];
+  double s = 0.0, c = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    ts_acc(s, c, x[i], 0.0);
+  sh[threadIdx.x] = make_double2(s, c);
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      double2 a = sh[threadIdx.x];
+      const double2 b = sh[threadIdx.x + o];
+      ts_acc(a.x, a.y, b.x, b.y);
+      sh[threadIdx.x] = a;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+__global__ void k_sum_final(const double2* __restrict__ part, int nb, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0, c = 0.0;
+  for (int b = 0; b < nb; ++b) ts_acc(s, c, part[b].x, part[b].y);
+  *out = s + c;
+}
+
+constexpr int SUM_BLOCKS = 512;
+
+struct SurrogateLayout {
+  size_t core, x, out, counts, list, mom_g, w_g, wn_g, part, sig, total;
+};
+
+SurrogateLayout surrogate_layout(const rw_ctx* c, int n_in) {
+  SurrogateLayout L{};
+  const size_t P = c->pts.size(), E = (size_t)c->E, N = registry().st[c->process].n_external;
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {
+    const size_t at = o;
+    o += align256(bytes);
+    return at;
+  };
+  L.core = take(ws_core_bytes(1));
+  L.x = take(4 * P * E * n_in);
+  L.out = take(4 * P * E * 2);
+  L.counts = take(8 * P);
+  L.list = take(8 * P * E);
+  L.mom_g = take(8 * 4 * N * E);
+  L.w_g = take(8 * E);
+  L.wn_g = take(8 * E);
+  L.part = take(16 * SUM_BLOCKS);
+  L.sig = take(8 * P);
+  L.total = o;
+  return L;
+}
+
+KappaList kappas(const rw_ctx* c) {
+  KappaList k{};
+  for (size_t j = 0; j < c->pts.size(); ++j) k.k[j] = (float)(c->pts[j].m_t / c->p0.m_t);
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rw_surrogate_features(rw_ctx* c, int n_in, double p_scale, double k_scale, const double* d_ratio, float* d_x,
+                          float* d_y) {
+  int rc = ready(c, true);
+  if (rc) return rc;
+  if (c->pts.empty()) return fail(c, RW_ERR_STATE, "no points set");
+  if (!d_x) return fail(c, RW_ERR_NULL, "x is NULL");
+  if (n_in < 1 || !(p_scale > 0) || !(k_scale > 0)) return fail(c, RW_ERR_ARG, "bad feature parameters");
+  DeviceGuard g(c->device);
+  const int P = (int)c->pts.size(), N = registry().st[c->process].n_external;
+  const long long tot = (long long)P * c->E;
+  k_features<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->mom, c->ld, c->E, N, P, kappas(c), n_in,
+                                                                   1.0 / p_scale, 1.0 / k_scale, d_ratio, d_x, d_y);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? RW_OK : cuda_fail(c, e, "features launch");
+}
+
+size_t rw_surrogate_workspace_bytes(const rw_ctx* c, int n_in) {
+  if (!c || c->process < 0 || !c->mom || c->pts.empty() || n_in < 1) return 0;
+  return surrogate_layout(c, n_in).total;
+}
+
+int rw_surrogate_reweight(rw_ctx* c, rw_mlp* m, double p_scale, double k_scale, double s_max, double* d_wnew,
+                          unsigned char* d_fallback, double* h_sigma, int64_t* h_n_fallback, void* d_ws,
+                          size_t ws_bytes) {
+  int rc = ready(c, true);
+  if (rc) return rc;
+  if (!m || !d_wnew || !d_ws) return fail(c, RW_ERR_NULL, "model, W' and workspace are required");
+  if (c->pts.empty()) return fail(c, RW_ERR_STATE, "no points set");
+  DeviceGuard g(c->device);
+  int nin = 0, hidden = 0, layers = 0;
+  void* mstream = nullptr;
+  if (rw_mlp_info(m, &nin, &hidden, &layers, &mstream) != RW_OK) return fail(c, RW_ERR_ARG, "bad model");
+  if (mstream != static_cast<void*>(c->stream))
+    return fail(c, RW_ERR_ARG, "the model must be created on the context's stream");
+  const SurrogateLayout L = surrogate_layout(c, nin);
+  if (ws_bytes < L.total) return fail(c, RW_ERR_WORKSPACE, "workspace %zu < %zu", ws_bytes, L.total);
+  char* b = static_cast<char*>(d_ws);
+  float* x = reinterpret_cast<float*>(b + L.x);
+  float* out = reinterpret_cast<float*>(b + L.out);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(b + L.counts);
+  long long* list = reinterpret_cast<long long*>(b + L.list);
+  double* mom_g = reinterpret_cast<double*>(b + L.mom_g);
+  double* w_g = reinterpret_cast<double*>(b + L.w_g);
+  double* wn_g = reinterpret_cast<double*>(b + L.wn_g);
+  double2* part = reinterpret_cast<double2*>(b + L.part);
+  double* sig = reinterpret_cast<double*>(b + L.sig);
+  const int P = (int)c->pts.size(), N = registry().st[c->process].n_external;
+  const long long E = c->E, tot = (long long)P * E;
+  // 1. features, 2. MLP
+  if ((rc = rw_surrogate_features(c, nin, p_scale, k_scale, nullptr, x, nullptr))) return rc;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, 8 * (size_t)P, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+  if ((rc = rw_mlp_forward(m, x, tot, out))) return fail(c, rc, "mlp forward: %s", rw_mlp_last_error(m));
+  // 3. decision
+  k_decide<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(out, c->w, E, P, kappas(c), (float)s_max, d_wnew,
+                                                                 d_fallback, cnt, list);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "decide launch");
+  if ((e = cudaMemcpyAsync(c->h_stage, cnt, 8 * (size_t)P, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "fallback counts");
+  std::vector<unsigned long long> counts(P);
+  memcpy(counts.data(), c->h_stage, 8 * (size_t)P);
+  // 4. exact path for the listed events, point by point
+  const double* mom_saved = c->mom;
+  const double* w_saved = c->w;
+  const int64_t ld_saved = c->ld;
+  for (int p = 0; p < P; ++p) {
+    const long long n = (long long)counts[p];
+    if (h_n_fallback) h_n_fallback[p] = n;
+    if (n == 0) continue;
+    const long long* lp = list + (long long)p * E;
+    k_gather_events<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(mom_saved, ld_saved, w_saved, N, lp, n,
+                                                                         mom_g, w_g);
+    RwArgs a{};
+    a.mom = mom_g;
+    a.w = w_g;
+    a.E = n;
+    a.ld = n;
+    a.wnew = wn_g;
+    a.P = 1;
+    a.pt[0] = make_point(c, c->p0, false);
+    a.pt[1] = make_point(c, c->pts[p], c->process != RW_EE_MUMU && c->pts[p].m_t != c->p0.m_t);
+    char* core = b + L.core;
+    a.ticket = reinterpret_cast<unsigned int*>(core);
+    a.nbad_count = reinterpret_cast<unsigned long long*>(core + 8);
+    a.sigma = reinterpret_cast<double*>(core + 64);
+    a.nbad_out = reinterpret_cast<unsigned long long*>(core + 64 + 16);
+    a.block_part = reinterpret_cast<double2*>(core + 256 + align256(8 * 3));
+    if ((e = cudaMemsetAsync(core, 0, 256, c->stream)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    if ((rc = launch(c, a))) return rc;
+    k_scatter<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(wn_g, lp, n, d_wnew + (long long)p * E);
+  }
+  // 5. sigma'_p
+  for (int p = 0; p < P; ++p) {
+    k_sum_partials<<<SUM_BLOCKS, 256, 0, c->stream>>>(d_wnew + (long long)p * E, E, part);
+    k_sum_final<<<1, 32, 0, c->stream>>>(part, SUM_BLOCKS, sig + p);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "sum launch");
+  if ((e = cudaMemcpyAsync(c->h_stage, sig, 8 * (size_t)P, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "sigma copy");
+  if (h_sigma) memcpy(h_sigma, c->h_stage, 8 * (size_t)P);
+  return RW_OK;
+}
+
+}  // extern "C"

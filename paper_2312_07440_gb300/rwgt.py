@@ -70,6 +70,19 @@ def load():
         "rw_workspace_bytes_host": ([P, i64], sz),
         "rw_reweight_host": ([P, P, P, i64, P, P, P, P, P, sz], i),
         "rw_get_tuning": ([P, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+        "rw_mlp_create": ([ctypes.POINTER(P), i, P, i, i, i, i, ctypes.c_uint64], i),
+        "rw_mlp_destroy": ([P], i),
+        "rw_mlp_last_error": ([P], ctypes.c_char_p),
+        "rw_mlp_n_params": ([P], i64),
+        "rw_mlp_info": ([P, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(P)], i),
+        "rw_mlp_get_state": ([P, P, P, P, ctypes.POINTER(i64)], i),
+        "rw_mlp_set_state": ([P, P, P, P, i64], i),
+        "rw_mlp_forward": ([P, P, i64, P], i),
+        "rw_mlp_gradient": ([P, P, P, i64, ctypes.c_float, ctypes.c_float, P, ctypes.POINTER(ctypes.c_float)], i),
+        "rw_mlp_train": ([P, P, P, i64, i, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_uint64], i),
+        "rw_surrogate_features": ([P, i, d, d, P, P, P], i),
+        "rw_surrogate_workspace_bytes": ([P, i], sz),
+        "rw_surrogate_reweight": ([P, P, d, d, d, P, P, P, P, P, sz], i),
         "rw_autotune": ([P, i64, ctypes.c_char_p, ctypes.POINTER(d)], i),
     }
     for name, (args, res) in sig.items():
@@ -167,6 +180,9 @@ class Context:
     def workspace_bytes(self, n_events: int) -> int:
         return int(self.lib.rw_workspace_bytes(self.h, int(n_events)))
 
+    def surrogate_workspace_bytes(self, n_in: int = 32) -> int:
+        return int(self.lib.rw_surrogate_workspace_bytes(self.h, int(n_in)))
+
     def workspace_bytes_host(self, n_events: int) -> int:
         return int(self.lib.rw_workspace_bytes_host(self.h, int(n_events)))
 
@@ -205,6 +221,84 @@ class Context:
                                                    sig.ctypes.data, ctypes.byref(so), ctypes.byref(nb),
                                                    _ptr(workspace), int(workspace_bytes)), "rw_reweight_host")
         return sig, so.value, nb.value, rc
+
+
+class Mlp:
+    """rw_mlp: the surrogate network (n_in -> hidden x n_layers SiLU -> (mu, s))."""
+
+    def __init__(self, device: int = 0, stream=None, n_in: int = 32, hidden: int = 256, n_layers: int = 4,
+                 max_batch: int = 16384, seed: int = 1):
+        self.h = None
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.rw_mlp_create(ctypes.byref(h), int(device), stream, n_in, hidden, n_layers, max_batch, seed)
+        if rc:
+            raise RwError(rc, "rw_mlp_create failed")
+        self.h = h
+        self.n_in, self.hidden, self.n_layers, self.max_batch = n_in, hidden, n_layers, max_batch
+        self.n_params = int(self.lib.rw_mlp_n_params(h))
+
+    def close(self):
+        if self.h:
+            self.lib.rw_mlp_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc, what):
+        if rc < 0:
+            raise RwError(rc, f"{what}: {self.lib.rw_mlp_last_error(self.h).decode()}")
+        return rc
+
+    def get_state(self):
+        p = np.empty(self.n_params, np.float32)
+        m1 = np.empty_like(p)
+        m2 = np.empty_like(p)
+        st = ctypes.c_int64()
+        self._check(self.lib.rw_mlp_get_state(self.h, p.ctypes.data, m1.ctypes.data, m2.ctypes.data,
+                                              ctypes.byref(st)), "rw_mlp_get_state")
+        return {"params": p, "m1": m1, "m2": m2, "step": st.value}
+
+    def set_state(self, params, m1=None, m2=None, step=0):
+        p = np.ascontiguousarray(params, np.float32)
+        a = np.ascontiguousarray(m1, np.float32) if m1 is not None else None
+        b = np.ascontiguousarray(m2, np.float32) if m2 is not None else None
+        self._check(self.lib.rw_mlp_set_state(self.h, p.ctypes.data, _ptr(a), _ptr(b), int(step)),
+                    "rw_mlp_set_state")
+
+    def forward(self, x, out):
+        self._check(self.lib.rw_mlp_forward(self.h, _ptr(x), int(x.shape[0]), _ptr(out)), "rw_mlp_forward")
+
+    def gradient(self, x, y, tau: float, lam: float):
+        g = np.empty(self.n_params, np.float32)
+        loss = ctypes.c_float()
+        self._check(self.lib.rw_mlp_gradient(self.h, _ptr(x), _ptr(y), int(x.shape[0]), tau, lam, g.ctypes.data,
+                                             ctypes.byref(loss)), "rw_mlp_gradient")
+        return loss.value, g
+
+    def train(self, x, y, batch: int, n_steps: int, lr: float, tau: float, lam: float, seed: int = 7):
+        self._check(self.lib.rw_mlp_train(self.h, _ptr(x), _ptr(y), int(x.shape[0]), int(batch), int(n_steps), lr,
+                                          tau, lam, int(seed)), "rw_mlp_train")
+
+
+def surrogate_features(ctx: "Context", n_in, p_scale, k_scale, ratio, x, y):
+    return ctx._check(ctx.lib.rw_surrogate_features(ctx.h, int(n_in), float(p_scale), float(k_scale), _ptr(ratio),
+                                                    _ptr(x), _ptr(y)), "rw_surrogate_features")
+
+
+def surrogate_reweight(ctx: "Context", mlp: Mlp, p_scale, k_scale, s_max, wnew, fallback, n_points, ws, ws_bytes):
+    sig = np.zeros(n_points)
+    nf = np.zeros(n_points, np.int64)
+    ctx._check(ctx.lib.rw_surrogate_reweight(ctx.h, mlp.h, float(p_scale), float(k_scale), float(s_max), _ptr(wnew),
+                                             _ptr(fallback), sig.ctypes.data, nf.ctypes.data, _ptr(ws),
+                                             int(ws_bytes)), "rw_surrogate_reweight")
+    return sig, nf
 
 
 def reweight(process: str, mode: str, mom, w, p0, points, *, lane_bits: int = -1, block: int = 0,
