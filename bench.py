@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--workload", default="gg_tt_1m", choices=list(ev.WORKLOADS))
     ap.add_argument("--variant", default="default", help="point set variant (gg_ttg/gg_ttgg: default|mt)")
     ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32", "mixed_fp16", "mixed_bf16"])
+    ap.add_argument("--events", type=int, default=0, help="override the workload's event count (profiling runs)")
     ap.add_argument("--lane-bits", type=int, default=-1)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -240,6 +241,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = ev.WORKLOADS[args.workload]
+    if args.events > 0:
+        import dataclasses
+        wl = dataclasses.replace(wl, n_events=args.events)
     pts = ev.reweight_points(args.workload, args.variant)
     P = pts.shape[0]
     E = wl.n_events

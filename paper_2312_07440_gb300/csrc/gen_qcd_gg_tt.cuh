@@ -44,15 +44,16 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
         const sp<R> S_0 = fprop(Kn.qc[1], Kn.mc[1], tS_0);
         sp<R> tS_1 = slash(E1, S_E);
         const sp<R> S_1 = fprop(Kn.qc[2], Kn.mc[2], tS_1);
+        sp<R> X0 = slash(E0, S_1);
+        spadd(X0, slash(J0_1, S_E));
+        sp<R> X1 = slash(E1, S_0);
+        spadd(X1, slash(J1_0, S_E));
         #pragma unroll 1
         for (int i3 = 0; i3 < (LB >= 3 ? 1 : 2); ++i3) {
           const int h3 = LB >= 3 ? ((lane >> (LB - 3)) & 1) : i3;
           const sp<R> UB = h3 ? X.ub[1] : X.ub[0];
-          const cv<R> F_E = fcur(UB, S_E);
-          const cv<R> F_0 = fcur(UB, S_0);
-          const cv<R> F_1 = fcur(UB, S_1);
-          const cx<R> A0 = dot(E0, F_1) + dot(J0_1, F_E);
-          const cx<R> A1 = dot(E1, F_0) + dot(J1_0, F_E);
+          const cx<R> A0 = rowcol(UB, X0);
+          const cx<R> A1 = rowcol(UB, X1);
           if constexpr (CM != CM_FMA) {
             const cx<float> Aa[K] = {A0, A1};
             acc += R(2) * cmma.sum(Aa);  // x2 helicity flip
@@ -72,5 +73,5 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
 }
 
 // floating-point operations of one full helicity sum (all levels, all loop trips)
-constexpr long FLOPS_HEL_SUM = 4168;
+constexpr long FLOPS_HEL_SUM = 3016;
 }}  // namespace

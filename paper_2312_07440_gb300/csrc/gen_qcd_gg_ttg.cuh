@@ -84,26 +84,34 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
           sp<R> tS_2_1 = slash(E2, S_1);
           spadd(tS_2_1, slash(J2_1, S_E));
           const sp<R> S_2_1 = fprop(Kn.qc[6], Kn.mc[6], tS_2_1);
+          sp<R> X0 = slash(E0, S_1_2);
+          spadd(X0, slash(J0_1, S_2));
+          spadd(X0, slash(J0_1_2, S_E));
+          sp<R> X1 = slash(E0, S_2_1);
+          spadd(X1, slash(J0_2, S_1));
+          spadd(X1, slash(J0_2_1, S_E));
+          sp<R> X2 = slash(E1, S_0_2);
+          spadd(X2, slash(J1_0, S_2));
+          spadd(X2, slash(J1_0_2, S_E));
+          sp<R> X3 = slash(E1, S_2_0);
+          spadd(X3, slash(J1_2, S_0));
+          spadd(X3, slash(J1_2_0, S_E));
+          sp<R> X4 = slash(E2, S_0_1);
+          spadd(X4, slash(J2_0, S_1));
+          spadd(X4, slash(J2_0_1, S_E));
+          sp<R> X5 = slash(E2, S_1_0);
+          spadd(X5, slash(J2_1, S_0));
+          spadd(X5, slash(J2_1_0, S_E));
           #pragma unroll 1
           for (int i4 = 0; i4 < (LB >= 4 ? 1 : 2); ++i4) {
             const int h4 = LB >= 4 ? ((lane >> (LB - 4)) & 1) : i4;
             const sp<R> UB = h4 ? X.ub[1] : X.ub[0];
-            const cv<R> F_E = fcur(UB, S_E);
-            const cv<R> F_0 = fcur(UB, S_0);
-            const cv<R> F_1 = fcur(UB, S_1);
-            const cv<R> F_2 = fcur(UB, S_2);
-            const cv<R> F_0_1 = fcur(UB, S_0_1);
-            const cv<R> F_0_2 = fcur(UB, S_0_2);
-            const cv<R> F_1_0 = fcur(UB, S_1_0);
-            const cv<R> F_1_2 = fcur(UB, S_1_2);
-            const cv<R> F_2_0 = fcur(UB, S_2_0);
-            const cv<R> F_2_1 = fcur(UB, S_2_1);
-            const cx<R> A0 = dot(E0, F_1_2) + dot(J0_1, F_2) + dot(J0_1_2, F_E);
-            const cx<R> A1 = dot(E0, F_2_1) + dot(J0_2, F_1) + dot(J0_2_1, F_E);
-            const cx<R> A2 = dot(E1, F_0_2) + dot(J1_0, F_2) + dot(J1_0_2, F_E);
-            const cx<R> A3 = dot(E1, F_2_0) + dot(J1_2, F_0) + dot(J1_2_0, F_E);
-            const cx<R> A4 = dot(E2, F_0_1) + dot(J2_0, F_1) + dot(J2_0_1, F_E);
-            const cx<R> A5 = dot(E2, F_1_0) + dot(J2_1, F_0) + dot(J2_1_0, F_E);
+            const cx<R> A0 = rowcol(UB, X0);
+            const cx<R> A1 = rowcol(UB, X1);
+            const cx<R> A2 = rowcol(UB, X2);
+            const cx<R> A3 = rowcol(UB, X3);
+            const cx<R> A4 = rowcol(UB, X4);
+            const cx<R> A5 = rowcol(UB, X5);
             if constexpr (CM != CM_FMA) {
               const cx<float> Aa[K] = {A0, A1, A2, A3, A4, A5};
               acc += R(2) * cmma.sum(Aa);  // x2 helicity flip
@@ -132,5 +140,5 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
 }
 
 // floating-point operations of one full helicity sum (all levels, all loop trips)
-constexpr long FLOPS_HEL_SUM = 42324;
+constexpr long FLOPS_HEL_SUM = 34644;
 }}  // namespace

@@ -330,75 +330,130 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             spadd(tS_3_2_1, slash(J3_2, S_1));
             spadd(tS_3_2_1, slash(J3_2_1, S_E));
             const sp<R> S_3_2_1 = fprop(Kn.qc[14], Kn.mc[14], tS_3_2_1);
+            sp<R> X0 = slash(E0, S_1_2_3);
+            spadd(X0, slash(J0_1, S_2_3));
+            spadd(X0, slash(J0_1_2, S_3));
+            spadd(X0, slash(J0_1_2_3, S_E));
+            sp<R> X1 = slash(E0, S_1_3_2);
+            spadd(X1, slash(J0_1, S_3_2));
+            spadd(X1, slash(J0_1_3, S_2));
+            spadd(X1, slash(J0_1_3_2, S_E));
+            sp<R> X2 = slash(E0, S_2_1_3);
+            spadd(X2, slash(J0_2, S_1_3));
+            spadd(X2, slash(J0_2_1, S_3));
+            spadd(X2, slash(J0_2_1_3, S_E));
+            sp<R> X3 = slash(E0, S_2_3_1);
+            spadd(X3, slash(J0_2, S_3_1));
+            spadd(X3, slash(J0_2_3, S_1));
+            spadd(X3, slash(J0_2_3_1, S_E));
+            sp<R> X4 = slash(E0, S_3_1_2);
+            spadd(X4, slash(J0_3, S_1_2));
+            spadd(X4, slash(J0_3_1, S_2));
+            spadd(X4, slash(J0_3_1_2, S_E));
+            sp<R> X5 = slash(E0, S_3_2_1);
+            spadd(X5, slash(J0_3, S_2_1));
+            spadd(X5, slash(J0_3_2, S_1));
+            spadd(X5, slash(J0_3_2_1, S_E));
+            sp<R> X6 = slash(E1, S_0_2_3);
+            spadd(X6, slash(J1_0, S_2_3));
+            spadd(X6, slash(J1_0_2, S_3));
+            spadd(X6, slash(J1_0_2_3, S_E));
+            sp<R> X7 = slash(E1, S_0_3_2);
+            spadd(X7, slash(J1_0, S_3_2));
+            spadd(X7, slash(J1_0_3, S_2));
+            spadd(X7, slash(J1_0_3_2, S_E));
+            sp<R> X8 = slash(E1, S_2_0_3);
+            spadd(X8, slash(J1_2, S_0_3));
+            spadd(X8, slash(J1_2_0, S_3));
+            spadd(X8, slash(J1_2_0_3, S_E));
+            sp<R> X9 = slash(E1, S_2_3_0);
+            spadd(X9, slash(J1_2, S_3_0));
+            spadd(X9, slash(J1_2_3, S_0));
+            spadd(X9, slash(J1_2_3_0, S_E));
+            sp<R> X10 = slash(E1, S_3_0_2);
+            spadd(X10, slash(J1_3, S_0_2));
+            spadd(X10, slash(J1_3_0, S_2));
+            spadd(X10, slash(J1_3_0_2, S_E));
+            sp<R> X11 = slash(E1, S_3_2_0);
+            spadd(X11, slash(J1_3, S_2_0));
+            spadd(X11, slash(J1_3_2, S_0));
+            spadd(X11, slash(J1_3_2_0, S_E));
+            sp<R> X12 = slash(E2, S_0_1_3);
+            spadd(X12, slash(J2_0, S_1_3));
+            spadd(X12, slash(J2_0_1, S_3));
+            spadd(X12, slash(J2_0_1_3, S_E));
+            sp<R> X13 = slash(E2, S_0_3_1);
+            spadd(X13, slash(J2_0, S_3_1));
+            spadd(X13, slash(J2_0_3, S_1));
+            spadd(X13, slash(J2_0_3_1, S_E));
+            sp<R> X14 = slash(E2, S_1_0_3);
+            spadd(X14, slash(J2_1, S_0_3));
+            spadd(X14, slash(J2_1_0, S_3));
+            spadd(X14, slash(J2_1_0_3, S_E));
+            sp<R> X15 = slash(E2, S_1_3_0);
+            spadd(X15, slash(J2_1, S_3_0));
+            spadd(X15, slash(J2_1_3, S_0));
+            spadd(X15, slash(J2_1_3_0, S_E));
+            sp<R> X16 = slash(E2, S_3_0_1);
+            spadd(X16, slash(J2_3, S_0_1));
+            spadd(X16, slash(J2_3_0, S_1));
+            spadd(X16, slash(J2_3_0_1, S_E));
+            sp<R> X17 = slash(E2, S_3_1_0);
+            spadd(X17, slash(J2_3, S_1_0));
+            spadd(X17, slash(J2_3_1, S_0));
+            spadd(X17, slash(J2_3_1_0, S_E));
+            sp<R> X18 = slash(E3, S_0_1_2);
+            spadd(X18, slash(J3_0, S_1_2));
+            spadd(X18, slash(J3_0_1, S_2));
+            spadd(X18, slash(J3_0_1_2, S_E));
+            sp<R> X19 = slash(E3, S_0_2_1);
+            spadd(X19, slash(J3_0, S_2_1));
+            spadd(X19, slash(J3_0_2, S_1));
+            spadd(X19, slash(J3_0_2_1, S_E));
+            sp<R> X20 = slash(E3, S_1_0_2);
+            spadd(X20, slash(J3_1, S_0_2));
+            spadd(X20, slash(J3_1_0, S_2));
+            spadd(X20, slash(J3_1_0_2, S_E));
+            sp<R> X21 = slash(E3, S_1_2_0);
+            spadd(X21, slash(J3_1, S_2_0));
+            spadd(X21, slash(J3_1_2, S_0));
+            spadd(X21, slash(J3_1_2_0, S_E));
+            sp<R> X22 = slash(E3, S_2_0_1);
+            spadd(X22, slash(J3_2, S_0_1));
+            spadd(X22, slash(J3_2_0, S_1));
+            spadd(X22, slash(J3_2_0_1, S_E));
+            sp<R> X23 = slash(E3, S_2_1_0);
+            spadd(X23, slash(J3_2, S_1_0));
+            spadd(X23, slash(J3_2_1, S_0));
+            spadd(X23, slash(J3_2_1_0, S_E));
             #pragma unroll 1
             for (int i5 = 0; i5 < (LB >= 5 ? 1 : 2); ++i5) {
               const int h5 = LB >= 5 ? ((lane >> (LB - 5)) & 1) : i5;
               const sp<R> UB = h5 ? X.ub[1] : X.ub[0];
-              const cv<R> F_E = fcur(UB, S_E);
-              const cv<R> F_0 = fcur(UB, S_0);
-              const cv<R> F_1 = fcur(UB, S_1);
-              const cv<R> F_2 = fcur(UB, S_2);
-              const cv<R> F_3 = fcur(UB, S_3);
-              const cv<R> F_0_1 = fcur(UB, S_0_1);
-              const cv<R> F_0_2 = fcur(UB, S_0_2);
-              const cv<R> F_0_3 = fcur(UB, S_0_3);
-              const cv<R> F_1_0 = fcur(UB, S_1_0);
-              const cv<R> F_1_2 = fcur(UB, S_1_2);
-              const cv<R> F_1_3 = fcur(UB, S_1_3);
-              const cv<R> F_2_0 = fcur(UB, S_2_0);
-              const cv<R> F_2_1 = fcur(UB, S_2_1);
-              const cv<R> F_2_3 = fcur(UB, S_2_3);
-              const cv<R> F_3_0 = fcur(UB, S_3_0);
-              const cv<R> F_3_1 = fcur(UB, S_3_1);
-              const cv<R> F_3_2 = fcur(UB, S_3_2);
-              const cv<R> F_0_1_2 = fcur(UB, S_0_1_2);
-              const cv<R> F_0_1_3 = fcur(UB, S_0_1_3);
-              const cv<R> F_0_2_1 = fcur(UB, S_0_2_1);
-              const cv<R> F_0_2_3 = fcur(UB, S_0_2_3);
-              const cv<R> F_0_3_1 = fcur(UB, S_0_3_1);
-              const cv<R> F_0_3_2 = fcur(UB, S_0_3_2);
-              const cv<R> F_1_0_2 = fcur(UB, S_1_0_2);
-              const cv<R> F_1_0_3 = fcur(UB, S_1_0_3);
-              const cv<R> F_1_2_0 = fcur(UB, S_1_2_0);
-              const cv<R> F_1_2_3 = fcur(UB, S_1_2_3);
-              const cv<R> F_1_3_0 = fcur(UB, S_1_3_0);
-              const cv<R> F_1_3_2 = fcur(UB, S_1_3_2);
-              const cv<R> F_2_0_1 = fcur(UB, S_2_0_1);
-              const cv<R> F_2_0_3 = fcur(UB, S_2_0_3);
-              const cv<R> F_2_1_0 = fcur(UB, S_2_1_0);
-              const cv<R> F_2_1_3 = fcur(UB, S_2_1_3);
-              const cv<R> F_2_3_0 = fcur(UB, S_2_3_0);
-              const cv<R> F_2_3_1 = fcur(UB, S_2_3_1);
-              const cv<R> F_3_0_1 = fcur(UB, S_3_0_1);
-              const cv<R> F_3_0_2 = fcur(UB, S_3_0_2);
-              const cv<R> F_3_1_0 = fcur(UB, S_3_1_0);
-              const cv<R> F_3_1_2 = fcur(UB, S_3_1_2);
-              const cv<R> F_3_2_0 = fcur(UB, S_3_2_0);
-              const cv<R> F_3_2_1 = fcur(UB, S_3_2_1);
-              const cx<R> A0 = dot(E0, F_1_2_3) + dot(J0_1, F_2_3) + dot(J0_1_2, F_3) + dot(J0_1_2_3, F_E);
-              const cx<R> A1 = dot(E0, F_1_3_2) + dot(J0_1, F_3_2) + dot(J0_1_3, F_2) + dot(J0_1_3_2, F_E);
-              const cx<R> A2 = dot(E0, F_2_1_3) + dot(J0_2, F_1_3) + dot(J0_2_1, F_3) + dot(J0_2_1_3, F_E);
-              const cx<R> A3 = dot(E0, F_2_3_1) + dot(J0_2, F_3_1) + dot(J0_2_3, F_1) + dot(J0_2_3_1, F_E);
-              const cx<R> A4 = dot(E0, F_3_1_2) + dot(J0_3, F_1_2) + dot(J0_3_1, F_2) + dot(J0_3_1_2, F_E);
-              const cx<R> A5 = dot(E0, F_3_2_1) + dot(J0_3, F_2_1) + dot(J0_3_2, F_1) + dot(J0_3_2_1, F_E);
-              const cx<R> A6 = dot(E1, F_0_2_3) + dot(J1_0, F_2_3) + dot(J1_0_2, F_3) + dot(J1_0_2_3, F_E);
-              const cx<R> A7 = dot(E1, F_0_3_2) + dot(J1_0, F_3_2) + dot(J1_0_3, F_2) + dot(J1_0_3_2, F_E);
-              const cx<R> A8 = dot(E1, F_2_0_3) + dot(J1_2, F_0_3) + dot(J1_2_0, F_3) + dot(J1_2_0_3, F_E);
-              const cx<R> A9 = dot(E1, F_2_3_0) + dot(J1_2, F_3_0) + dot(J1_2_3, F_0) + dot(J1_2_3_0, F_E);
-              const cx<R> A10 = dot(E1, F_3_0_2) + dot(J1_3, F_0_2) + dot(J1_3_0, F_2) + dot(J1_3_0_2, F_E);
-              const cx<R> A11 = dot(E1, F_3_2_0) + dot(J1_3, F_2_0) + dot(J1_3_2, F_0) + dot(J1_3_2_0, F_E);
-              const cx<R> A12 = dot(E2, F_0_1_3) + dot(J2_0, F_1_3) + dot(J2_0_1, F_3) + dot(J2_0_1_3, F_E);
-              const cx<R> A13 = dot(E2, F_0_3_1) + dot(J2_0, F_3_1) + dot(J2_0_3, F_1) + dot(J2_0_3_1, F_E);
-              const cx<R> A14 = dot(E2, F_1_0_3) + dot(J2_1, F_0_3) + dot(J2_1_0, F_3) + dot(J2_1_0_3, F_E);
-              const cx<R> A15 = dot(E2, F_1_3_0) + dot(J2_1, F_3_0) + dot(J2_1_3, F_0) + dot(J2_1_3_0, F_E);
-              const cx<R> A16 = dot(E2, F_3_0_1) + dot(J2_3, F_0_1) + dot(J2_3_0, F_1) + dot(J2_3_0_1, F_E);
-              const cx<R> A17 = dot(E2, F_3_1_0) + dot(J2_3, F_1_0) + dot(J2_3_1, F_0) + dot(J2_3_1_0, F_E);
-              const cx<R> A18 = dot(E3, F_0_1_2) + dot(J3_0, F_1_2) + dot(J3_0_1, F_2) + dot(J3_0_1_2, F_E);
-              const cx<R> A19 = dot(E3, F_0_2_1) + dot(J3_0, F_2_1) + dot(J3_0_2, F_1) + dot(J3_0_2_1, F_E);
-              const cx<R> A20 = dot(E3, F_1_0_2) + dot(J3_1, F_0_2) + dot(J3_1_0, F_2) + dot(J3_1_0_2, F_E);
-              const cx<R> A21 = dot(E3, F_1_2_0) + dot(J3_1, F_2_0) + dot(J3_1_2, F_0) + dot(J3_1_2_0, F_E);
-              const cx<R> A22 = dot(E3, F_2_0_1) + dot(J3_2, F_0_1) + dot(J3_2_0, F_1) + dot(J3_2_0_1, F_E);
-              const cx<R> A23 = dot(E3, F_2_1_0) + dot(J3_2, F_1_0) + dot(J3_2_1, F_0) + dot(J3_2_1_0, F_E);
+              const cx<R> A0 = rowcol(UB, X0);
+              const cx<R> A1 = rowcol(UB, X1);
+              const cx<R> A2 = rowcol(UB, X2);
+              const cx<R> A3 = rowcol(UB, X3);
+              const cx<R> A4 = rowcol(UB, X4);
+              const cx<R> A5 = rowcol(UB, X5);
+              const cx<R> A6 = rowcol(UB, X6);
+              const cx<R> A7 = rowcol(UB, X7);
+              const cx<R> A8 = rowcol(UB, X8);
+              const cx<R> A9 = rowcol(UB, X9);
+              const cx<R> A10 = rowcol(UB, X10);
+              const cx<R> A11 = rowcol(UB, X11);
+              const cx<R> A12 = rowcol(UB, X12);
+              const cx<R> A13 = rowcol(UB, X13);
+              const cx<R> A14 = rowcol(UB, X14);
+              const cx<R> A15 = rowcol(UB, X15);
+              const cx<R> A16 = rowcol(UB, X16);
+              const cx<R> A17 = rowcol(UB, X17);
+              const cx<R> A18 = rowcol(UB, X18);
+              const cx<R> A19 = rowcol(UB, X19);
+              const cx<R> A20 = rowcol(UB, X20);
+              const cx<R> A21 = rowcol(UB, X21);
+              const cx<R> A22 = rowcol(UB, X22);
+              const cx<R> A23 = rowcol(UB, X23);
               if constexpr (CM != CM_FMA) {
                 const cx<float> Aa[K] = {A0, A1, A2, A3, A4, A5, A6, A7, A8, A9, A10, A11, A12, A13, A14, A15, A16, A17, A18, A19, A20, A21, A22, A23};
                 acc += R(2) * cmma.sum(Aa);  // x2 helicity flip
@@ -464,5 +519,5 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
 }
 
 // floating-point operations of one full helicity sum (all levels, all loop trips)
-constexpr long FLOPS_HEL_SUM = 532556;
+constexpr long FLOPS_HEL_SUM = 471884;
 }}  // namespace

@@ -145,6 +145,12 @@ __device__ __forceinline__ cv<R> fcur(const sp<R>& u, const sp<R>& s) {
   return o;
 }
 
+// ubar . X: a row spinor times a column spinor                           (30 flops)
+template <class R>
+__device__ __forceinline__ cx<R> rowcol(const sp<R>& u, const sp<R>& x) {
+  return u.c[0] * x.c[0] + u.c[1] * x.c[1] + u.c[2] * x.c[2] + u.c[3] * x.c[3];
+}
+
 // ---------------------------------------------------------------------------
 // External wavefunctions, computed in the working precision T from momenta
 // already converted to T, with formulas free of cancellation: |p| + p_z is

@@ -13,7 +13,8 @@ smaller generator for the processes it ships.  For n gluons on the top line it
   * emits a CUDA device function that evaluates every colour-ordered
     amplitude as chains of vertex and propagator calls -- off-shell gluon
     currents (3- and 4-gluon vertices), off-shell top currents (quark-gluon
-    vertex + top propagator) and their contraction -- sharing every
+    vertex + top propagator), the amputated spinor of each ordering closed by
+    the top's ubar in the innermost helicity loop -- sharing every
     sub-current between the n! orderings (the sum over all Feynman diagrams,
     organised so that no diagram's chain is recomputed), with the helicity
     sum written as nested loops over the external helicities and every
@@ -166,6 +167,7 @@ FLOPS = {
     "fprop": 58,     # c (qslash + m) chi
     "fcur": 72,      # ubar gamma^mu psi
     "dot": 30,       # complex Minkowski product
+    "rowcol": 30,    # ubar . X (row times column spinor)
     "cadd": 2,
 }
 
@@ -311,24 +313,24 @@ def emit_process(name, n, outgoing_gluons, n_identical):
                 em.count(n, "sp_add")
             w(f"{ind}const sp<R> {nm} = fprop(Kn.qc[{mask(rho)}], Kn.mc[{mask(rho)}], t{nm});")
             em.count(n, "fprop")
-    # top level: fermion currents F(rho) = ubar gamma psi(rho), amplitudes, colour sum
-    open_level(n + 1, f"h{n + 1}", f"const sp<R> UB = h{n + 1} ? X.ub[1] : X.ub[0];")
-    w(f"{ind}const cv<R> F_E = fcur(UB, S_E);")
-    em.count(n + 1, "fcur")
-    for L in range(1, n):
-        for rho in seqs[L]:
-            nm = seq_name("S_", rho)
-            w(f"{ind}const cv<R> F{nm[1:]} = fcur(UB, {nm});")
-            em.count(n + 1, "fcur")
+    # still at the antitop level: the amputated spinors of every ordering,
+    # X(sigma) = sum_c Jslash(sigma[..c]) psi(sigma[c+1..]), so that the top
+    # level only closes them with ubar
     for k, sg in enumerate(perms):
         terms = []
         for c in range(1, n + 1):
             a, b = sg[:c], sg[c:]
-            fn = "F_E" if not b else "F" + seq_name("S_", b)[1:]
-            terms.append(f"dot({jn(a)}, {fn})")
-            em.count(n + 1, "dot")
-        w(f"{ind}const cx<R> A{k} = {' + '.join(terms)};")
-        em.count(n + 1, "cadd", len(terms) - 1)
+            terms.append(f"slash({jn(a)}, {seq_name('S_', b)})")
+            em.count(n, "slash")
+        w(f"{ind}sp<R> X{k} = {terms[0]};")
+        for t in terms[1:]:
+            w(f"{ind}spadd(X{k}, {t});")
+            em.count(n, "sp_add")
+    # top level: A(sigma) = ubar X(sigma), colour sum
+    open_level(n + 1, f"h{n + 1}", f"const sp<R> UB = h{n + 1} ? X.ub[1] : X.ub[0];")
+    for k in range(K):
+        w(f"{ind}const cx<R> A{k} = rowcol(UB, X{k});")
+        em.count(n + 1, "rowcol")
     w(f"{ind}if constexpr (CM != CM_FMA) {{")
     w(f"{ind}  const cx<float> Aa[K] = {{{', '.join(f'A{k}' for k in range(K))}}};")
     w(f"{ind}  acc += R(2) * cmma.sum(Aa);  // x2 helicity flip")
