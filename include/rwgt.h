@@ -165,6 +165,21 @@ int rw_reweight_host(rw_ctx* ctx, const double* h_mom, const double* h_w, int64_
                      size_t workspace_bytes);
 
 /* ---------------------------------------------------------------------------
+   CUDA-graph batching: record rw_reweight_async / rw_eval_me calls of any
+   number of contexts (processes, modes, point sets) that queue on one stream
+   between rw_graph_begin and rw_graph_end, then replay them all with one
+   rw_graph_launch.  Each replay recomputes every recorded reweight from the
+   events and outputs bound at capture time (the kernels reset their own
+   counters, so replays are independent).  Do not call functions that
+   synchronise (rw_get_results, rw_autotune, ...) while capturing, and run
+   rw_autotune (if used) before capturing. */
+typedef struct rw_graph rw_graph;
+int rw_graph_begin(void* cuda_stream);
+int rw_graph_end(void* cuda_stream, rw_graph** graph);
+int rw_graph_launch(rw_graph* graph, void* cuda_stream);
+int rw_graph_destroy(rw_graph* graph);
+
+/* ---------------------------------------------------------------------------
    Learned surrogate for log r (spec extension; the paper has none).
    An MLP n_in -> [hidden, SiLU] x n_layers -> 2 predicts mu = log r and
    s = log of its own error for a feature vector built from an event and a

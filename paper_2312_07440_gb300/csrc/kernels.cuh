@@ -139,6 +139,14 @@ __global__ void __launch_bounds__(256, 1) k_reweight(const __grid_constant__ RwA
   const long long g0 = (long long)blockIdx.x * gpb + tid / LANES;
   const long long E = a.E;
   unsigned long long nbad = 0;
+  // Up to FEW points: per-thread compensated accumulators for the cross
+  // sections (slot P = sigma of the original weights), reduced once at the end;
+  // more points: a warp reduction per event into shared memory.
+  constexpr int FEW = 3;
+  const bool few = P <= FEW;
+  double rs[FEW + 1], rc[FEW + 1];
+#pragma unroll
+  for (int q = 0; q <= FEW; ++q) rs[q] = rc[q] = 0.0;
   for (long long base = 0; base < E; base += ngroups) {
     const long long ev = base + g0;
     const bool valid = ev < E;
@@ -167,7 +175,15 @@ __global__ void __launch_bounds__(256, 1) k_reweight(const __grid_constant__ RwA
         ok = isfinite(me0) && me0 != 0.0;
         if (leader && !ok) ++nbad;
         if (leader && a.me0) a.me0[ev] = me0;
-        warp_accumulate(sacc, warp, stride, P, leader ? w : 0.0);
+        if (few) {
+          if (leader) {
+#pragma unroll
+            for (int q = 0; q <= FEW; ++q)
+              if (q == P) two_sum_acc(rs[q], rc[q], w, 0.0);
+          }
+        } else {
+          warp_accumulate(sacc, warp, stride, P, leader ? w : 0.0);
+        }
         continue;
       }
       const double r = ok ? me / me0 : 0.0;
@@ -178,10 +194,28 @@ __global__ void __launch_bounds__(256, 1) k_reweight(const __grid_constant__ RwA
         if (a.ratio) a.ratio[o] = r;
         if (a.wnew) a.wnew[o] = wn;
       }
-      warp_accumulate(sacc, warp, stride, j - 1, leader ? wn : 0.0);
+      if (few) {
+        if (leader) {
+#pragma unroll
+          for (int q = 0; q < FEW; ++q)
+            if (q == j - 1) two_sum_acc(rs[q], rc[q], wn, 0.0);
+        }
+      } else {
+        warp_accumulate(sacc, warp, stride, j - 1, leader ? wn : 0.0);
+      }
     }
   }
   if (a.me_only) return;
+  if (few) {  // one warp reduction per slot for the whole launch
+#pragma unroll
+    for (int q = 0; q <= FEW; ++q) {
+      if (q > P) break;
+      double s = rs[q], c = rc[q];
+      __syncwarp();
+      warp_sum2(s, c);
+      if (wl == 0) sacc[warp * stride + q] = make_double2(s, c);
+    }
+  }
   __syncthreads();
   for (int j = tid; j < stride; j += blockDim.x) {
     double s = 0.0, c = 0.0;

@@ -982,3 +982,58 @@ int rw_surrogate_reweight(rw_ctx* c, rw_mlp* m, double p_scale, double k_scale, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// CUDA-graph batching
+// ---------------------------------------------------------------------------
+struct rw_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+int rw_graph_begin(void* stream) {
+  const cudaError_t e = cudaStreamBeginCapture(static_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return RW_ERR_CUDA;
+  }
+  return RW_OK;
+}
+
+int rw_graph_end(void* stream, rw_graph** out) {
+  if (!out) return RW_ERR_NULL;
+  *out = nullptr;
+  rw_graph* g = new rw_graph();
+  cudaError_t e = cudaStreamEndCapture(static_cast<cudaStream_t>(stream), &g->graph);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return RW_ERR_CUDA;
+  }
+  *out = g;
+  return RW_OK;
+}
+
+int rw_graph_launch(rw_graph* g, void* stream) {
+  if (!g) return RW_ERR_NULL;
+  const cudaError_t e = cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return RW_ERR_CUDA;
+  }
+  return RW_OK;
+}
+
+int rw_graph_destroy(rw_graph* g) {
+  if (!g) return RW_ERR_NULL;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return RW_OK;
+}
+
+}  // extern "C"

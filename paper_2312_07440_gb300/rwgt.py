@@ -83,6 +83,10 @@ def load():
         "rw_surrogate_features": ([P, i, d, d, P, P, P], i),
         "rw_surrogate_workspace_bytes": ([P, i], sz),
         "rw_surrogate_reweight": ([P, P, d, d, d, P, P, P, P, P, sz], i),
+        "rw_graph_begin": ([P], i),
+        "rw_graph_end": ([P, ctypes.POINTER(P)], i),
+        "rw_graph_launch": ([P, P], i),
+        "rw_graph_destroy": ([P], i),
         "rw_autotune": ([P, i64, ctypes.c_char_p, ctypes.POINTER(d)], i),
     }
     for name, (args, res) in sig.items():
@@ -285,6 +289,39 @@ class Mlp:
     def train(self, x, y, batch: int, n_steps: int, lr: float, tau: float, lam: float, seed: int = 7):
         self._check(self.lib.rw_mlp_train(self.h, _ptr(x), _ptr(y), int(x.shape[0]), int(batch), int(n_steps), lr,
                                           tau, lam, int(seed)), "rw_mlp_train")
+
+
+class Graph:
+    """Record rw_* calls queued on `stream` between begin() and end(); replay with launch()."""
+
+    def __init__(self, stream):
+        self.lib = load()
+        self.stream = stream
+        self.h = None
+
+    def begin(self):
+        rc = self.lib.rw_graph_begin(self.stream)
+        if rc:
+            raise RwError(rc, "rw_graph_begin")
+
+    def end(self):
+        h = ctypes.c_void_p()
+        rc = self.lib.rw_graph_end(self.stream, ctypes.byref(h))
+        if rc:
+            raise RwError(rc, "rw_graph_end")
+        self.h = h
+
+    def launch(self):
+        rc = self.lib.rw_graph_launch(self.h, self.stream)
+        if rc:
+            raise RwError(rc, "rw_graph_launch")
+
+    def close(self):
+        if self.h:
+            self.lib.rw_graph_destroy(self.h)
+            self.h = None
+
+    __del__ = close
 
 
 def surrogate_features(ctx: "Context", n_in, p_scale, k_scale, ratio, x, y):

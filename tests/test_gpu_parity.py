@@ -386,3 +386,48 @@ def test_mixed_modes_reject_large_blocks():
         with pytest.raises(rwgt.RwError) as e:
             c.set_tuning(0, 256)
         assert e.value.code == -2
+
+
+# --------------------------------------------------------------------------
+# CUDA-graph batching: several processes and point sets in one replay
+# --------------------------------------------------------------------------
+def test_graph_batches_processes_and_replays():
+    side = torch.cuda.Stream(DEV)
+    jobs = [("gg_tt", "fp64", "gg_tt_1m", 3001, ev.reweight_points("gg_tt_1m")),
+            ("ee_mumu", "fp64", "ee_mumu_4k", 4096, ev.reweight_points("ee_mumu_4k")),
+            ("gg_ttg", "fp32", "gg_ttg_4m", 500, ev.reweight_points("gg_ttg_4m", "mt")[::9])]
+    ctxs, outs, refs, keep = [], [], [], []
+    for proc, mode, wl, n, pts in jobs:
+        mom, w, o = oracle_run(proc, wl, n, pts)
+        dm, dw = to_dev(mom), to_dev(w)
+        c = rwgt.Context(0, side.cuda_stream)
+        c.set_process(proc, mode)
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(pts)
+        nb = c.workspace_bytes(n)
+        ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+        c.load_events(dm, dw, n, ws, nb)
+        out = torch.full((pts.shape[0], n), -1.0, dtype=torch.float64, device=DEV)
+        ctxs.append(c)
+        outs.append(out)
+        refs.append((o, mode))
+        keep += [dm, dw, ws]
+    torch.cuda.synchronize()
+    g = rwgt.Graph(side.cuda_stream)
+    g.begin()
+    for c, out in zip(ctxs, outs):
+        c.reweight_async(out)
+    g.end()
+    for rep in range(2):
+        for out in outs:
+            out.fill_(-1.0)
+        torch.cuda.synchronize()
+        g.launch()
+        side.synchronize()
+        for c, out, (o, mode), job in zip(ctxs, outs, refs, jobs):
+            assert rel(out.cpu().numpy(), o["wnew"]).max() < TOL[mode]
+            sig, so, nbad, _ = c.get_results(job[4].shape[0])
+            assert np.abs(sig / o["sigma"] - 1).max() < TOL[mode]
+    g.close()
+    for c in ctxs:
+        c.close()
