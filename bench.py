@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP32 variant of the default FP64 run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
@@ -313,6 +314,11 @@ def run_ours(args):
         acc = accuracy_sample(wl, pts, mom_h, w_h, wnew, args.mode)
 
     # end to end through the host entry point (rank 0 of each node does it on its own GPU)
+    # the same workload in FP32 mode (same events, same points), device-resident
+    variants = None
+    if rank == 0 and world == 1 and args.mode == "fp64" and not args.no_variants:
+        variants = {"fp32": run_variant(torch, dev, stream, wl, pts, mom, w, mom_h, w_h, "fp32", args, flush)}
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(ctx, torch, dev, mom_h, w_h, E, P, N, world, args)
@@ -343,7 +349,7 @@ def run_ours(args):
             "config": dict(config_dict(args, wl, P), tuning={"lane_bits": lane_bits, "block": block,
                                                               "source": tuning_source}),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clocks, "accuracy_vs_oracle": acc,
+            "clocks": clocks, "accuracy_vs_oracle": acc, "variants": variants,
             "sigma": [float(x) for x in sig], "sigma_orig": sig_orig, "n_bad": int(nbad),
             "step_ms_min_median_max": [1e3 * min(per_step), 1e3 * statistics.median(per_step),
                                        1e3 * max(per_step)],
@@ -352,6 +358,44 @@ def run_ours(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_variant(torch, dev, stream, wl, pts, mom, w, mom_h, w_h, mode, args, flush):
+    """Device-resident timing of the same step in another precision mode."""
+    from paper_2312_07440_gb300 import rwgt
+    E, P = wl.n_events, pts.shape[0]
+    c = rwgt.Context(dev.index or 0, stream.cuda_stream)
+    c.set_process(wl.process, mode)
+    c.set_params(ev.param_vector())
+    c.set_reweight_points(pts)
+    nb = c.workspace_bytes(E)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    c.load_events(mom, w, E, ws, nb)
+    c.autotune(max_events=min(E, 1 << 18))
+    lb, bl = c.get_tuning()
+    wn = torch.empty((P, E), dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        c.reweight_async(wn)
+    ts = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        c.reweight_async(wn)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    c.close()
+    t = sum(ts) / len(ts)
+    from paper_2312_07440_gb300 import rwgt as _r
+    info = _r.process_info(wl.process)
+    fl = (1 + P) * info.flops_hel_sum * E / t / 1e12
+    return {"value": E * P / t, "unit": UNIT, "ms_per_step": 1e3 * t, "dtype": "f32",
+            "tuning": {"lane_bits": lb, "block": bl},
+            "roofline": {"bound": "alu", "achieved": fl, "peak": ALU_PEAK_TFLOPS[mode], "unit": "TFLOP/s",
+                         "frac": fl / ALU_PEAK_TFLOPS[mode]},
+            "accuracy_vs_oracle": accuracy_sample(wl, pts, mom_h, w_h, wn, mode)}
 
 
 def accuracy_sample(wl, pts, mom_h, w_h, wnew, mode, n=2000):
