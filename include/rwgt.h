@@ -263,6 +263,21 @@ int rw_surrogate_reweight(rw_ctx* ctx, rw_mlp* m, double p_scale, double k_scale
 int rw_reweight_noalloc(rw_ctx* ctx, const double* d_mom, const double* d_w, int64_t n_events, double* d_wnew,
                         double* d_ratio, double* d_sigma, unsigned long long* d_n_bad);
 
+/* ---------------------------------------------------------------------------
+   Input conversion of the FP32 modes, exposed for verification.  The paper has
+   no counterpart.  In RW_FP32 / RW_MIXED_* the g g -> t tbar (+g) kernels split
+   every FP64 momentum component x into two floats, hi = the float nearest to x
+   (ties to even) and lo = x - hi rounded to float, using integer operations
+   (the kinematic invariants and the reshuffle are then done in double-float
+   arithmetic on the FP32 pipe).  This call runs that split on n device doubles:
+     d_x [n]  device input;   d_hi [n], d_lo [n]  device outputs (float)
+   Zero and |x| < 2^-126 give +-0 (lo 0); |x| >= 2^128 gives +-inf; NaN stays
+   NaN; lo is 0 for |x| < 2^-74.  Asynchronous on `stream` (a cudaStream_t,
+   NULL = legacy default stream); n < 0 -> RW_ERR_ARG, a NULL pointer with
+   n > 0 -> RW_ERR_NULL, a failed launch -> RW_ERR_CUDA (there is no context,
+   so no message). */
+int rw_split_double(const double* d_x, int64_t n, float* d_hi, float* d_lo, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
 #include "helas.cuh"
 
 namespace rw {
@@ -100,10 +101,15 @@ __device__ __forceinline__ void block_sum2(double& s, double& c, double2* scratc
 
 // |M|^2 for one parameter point; a point with a new top mass first moves the
 // event onto its mass shell (|M'|^2 = 0 when the new masses do not fit).
+// FP64 input momenta to the process's momentum type: FP64 as is, or the
+// double-float split done with integer operations (no FP64-pipe conversion).
+__device__ __forceinline__ void load_mom(double& dst, double x) { dst = x; }
+__device__ __forceinline__ void load_mom(df& dst, double x) { dst = df_from_double(x); }
+
 template <class Proc, class R, int LB>
-__device__ __forceinline__ double eval_point(const double (&p)[Proc::NEXT][4], const PointDev& pt, int lane,
-                                             unsigned gmask) {
-  double q[Proc::NEXT][4];
+__device__ __forceinline__ double eval_point(const typename Proc::template mom_t<R> (&p)[Proc::NEXT][4],
+                                             const PointDev& pt, int lane, unsigned gmask) {
+  typename Proc::template mom_t<R> q[Proc::NEXT][4];
   bool inside = true;
   if (pt.reshuffle) {
     inside = Proc::template reshuffle<R>(p, pt.m_t, q);
@@ -117,8 +123,11 @@ __device__ __forceinline__ double eval_point(const double (&p)[Proc::NEXT][4], c
   return inside ? v : 0.0;
 }
 
-template <class Proc, class R, int LB>
-__global__ void __launch_bounds__(256, 1) k_reweight(const __grid_constant__ RwArgs a) {
+// MINB: resident blocks of 256 threads per SM the register allocation must
+// allow (1: up to 255 registers; 2: 128, for small processes whose FP32
+// kernels are latency-bound at 8 warps per SM).
+template <class Proc, class R, int LB, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB) k_reweight(const __grid_constant__ RwArgs a) {
   constexpr int NEXT = Proc::NEXT;
   constexpr int LANES = 1 << LB;
   extern __shared__ double2 sacc[];  // [nwarps][P+1]
@@ -151,11 +160,11 @@ __global__ void __launch_bounds__(256, 1) k_reweight(const __grid_constant__ RwA
     const long long ev = base + g0;
     const bool valid = ev < E;
     const long long evc = valid ? ev : E - 1;
-    double p[NEXT][4];
+    typename Proc::template mom_t<R> p[NEXT][4];
 #pragma unroll
     for (int i = 0; i < NEXT; ++i)
 #pragma unroll
-      for (int m = 0; m < 4; ++m) p[i][m] = __ldg(a.mom + ((long long)(i * 4 + m)) * a.ld + evc);
+      for (int m = 0; m < 4; ++m) load_mom(p[i][m], __ldg(a.mom + ((long long)(i * 4 + m)) * a.ld + evc));
     // One call site for every evaluation (original, then each point), so that
     // identical parameters give bitwise identical |M|^2 and r == 1 exactly.
     const bool leader = valid && lane == 0;

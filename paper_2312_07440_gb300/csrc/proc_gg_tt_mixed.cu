@@ -22,10 +22,10 @@ using PB16 = QcdProc<Tag, CM_BF16>;
 }  // namespace
 
 void register_gg_tt_mixed(std::vector<KernelEntry>& t) {
-  t.push_back({RW_GG_TT, RW_MIXED_FP16, 0, (const void*)&k_reweight<P16, float, 0>, 128});
-  t.push_back({RW_GG_TT, RW_MIXED_BF16, 0, (const void*)&k_reweight<PB16, float, 0>, 128});
-  t.push_back({RW_GG_TT, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1>, 128});
-  t.push_back({RW_GG_TT, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1>, 128});
+  t.push_back({RW_GG_TT, RW_MIXED_FP16, 0, (const void*)&k_reweight<P16, float, 0, 2>, 128});
+  t.push_back({RW_GG_TT, RW_MIXED_BF16, 0, (const void*)&k_reweight<PB16, float, 0, 2>, 128});
+  t.push_back({RW_GG_TT, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1, 2>, 128});
+  t.push_back({RW_GG_TT, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1, 2>, 128});
 }
 
 }  // namespace rw

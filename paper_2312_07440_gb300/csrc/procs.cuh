@@ -1,6 +1,8 @@
 // Process adapters for the fused kernel: |M|^2 of one event for one
 // parameter point, helicity slices combined across the 2^LB lanes of a group.
 #pragma once
+#include <type_traits>
+
 #include "helas.cuh"
 #include "kernels.cuh"
 #include "qcd.cuh"
@@ -18,8 +20,13 @@ struct QcdProc {
   // Out of line: every evaluation runs the same instructions, so identical
   // inputs give bitwise identical |M|^2 (r == 1 exactly for unchanged
   // parameters), and the kernel keeps one copy of the amplitude code.
+  // Momenta: FP64 in FP64 mode, double-float in the FP32 modes (dfloat.cuh).
+  template <class R>
+  using mom_t = typename std::conditional<sizeof(R) == 8, double, df>::type;
+
   template <class R, int LB>
-  __device__ __noinline__ static double me(const double (&p)[NEXT][4], const PointDev& pt, int lane, unsigned gmask) {
+  __device__ __noinline__ static double me(const mom_t<R> (&p)[NEXT][4], const PointDev& pt, int lane,
+                                           unsigned gmask) {
     static_assert(LB <= Tag::MAX_LB, "more lane bits than helicity levels");
     QcdExt<R, NG> X;
     QcdKin<R, NG> Kn;
@@ -29,10 +36,14 @@ struct QcdProc {
     for (int o = 1; o < (1 << LB); o <<= 1) s += __shfl_xor_sync(gmask, s, o);
     return s * pt.cscale;
   }
-  // FP32 mode refines the FP32 Newton solution with one FP64 step, FP64 mode with two.
+  // FP64 mode refines the FP32 Newton solution with two FP64 steps, the FP32
+  // modes with one double-float step.
   template <class R>
-  __device__ __forceinline__ static bool reshuffle(const double (&p)[NEXT][4], double mt, double (&q)[NEXT][4]) {
-    return reshuffle_tops<NEXT, sizeof(R) == 8 ? 2 : 1>(p, mt, q);
+  __device__ __forceinline__ static bool reshuffle(const mom_t<R> (&p)[NEXT][4], double mt, mom_t<R> (&q)[NEXT][4]) {
+    if constexpr (sizeof(R) == 8)
+      return reshuffle_tops<NEXT, 2>(p, mt, q);
+    else
+      return reshuffle_tops<NEXT>(p, mt, q);
   }
 };
 
@@ -45,6 +56,10 @@ struct QcdProc {
 struct EeMumu {
   static constexpr int NEXT = 4;
   static constexpr int NHEL = 16;
+  // FP64 momenta in every mode (a 4-particle process with no reshuffle: its
+  // few FP64 invariants per event are not a bottleneck)
+  template <class R>
+  using mom_t = double;
 
   template <class R, int LB>
   __device__ __noinline__ static double me(const double (&p)[NEXT][4], const PointDev& pt, int lane,

@@ -1,9 +1,11 @@
 // Per-event set-up for g g -> t tbar + n g: external wavefunctions of both
 // helicities (in the working precision R, cancellation-free formulas) and the
-// propagator invariants, whose dot products are formed in FP64 from the FP64
-// momenta (so FP32 mode never forms p^2 - m^2 by cancellation in single
-// precision) before the reciprocals are taken in R.
+// propagator invariants, whose dot products are formed at ~double precision
+// -- FP64 in FP64 mode, double-float (dfloat.cuh) in the FP32 modes -- so
+// that FP32 mode never forms p^2 - m^2 by cancellation in single precision,
+// before the reciprocals are taken in R.
 #pragma once
+#include "dfloat.cuh"
 #include "helas.cuh"
 
 namespace rw {
@@ -175,6 +177,149 @@ __device__ __forceinline__ bool reshuffle_tops(const double (&p)[NEXT][4], doubl
   for (int i = 2; i < NEXT; ++i) {
 #pragma unroll
     for (int m4 = 1; m4 < 4; ++m4) q[i][m4] = xi * p[i][m4];
+    q[i][0] = e[i];
+  }
+  return true;
+}
+
+// FP32 modes: the same set-up from double-float momenta (the split of the
+// FP64 inputs); invariants in double-float, everything else in float.
+template <class R, int NG, int NEXT>
+__device__ __forceinline__ void qcd_setup(const df (&p)[NEXT][4], double m, QcdExt<R, NG>& X, QcdKin<R, NG>& Kn) {
+  static_assert(NEXT == NG + 2, "t tbar + NG gluons");
+  static_assert(sizeof(R) == 4, "double-float set-up feeds FP32 amplitudes");
+  df k[NG][4];
+  R kw[NG][4];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const int ip = gluon_particle(g);
+    R kr[4];
+#pragma unroll
+    for (int m4 = 0; m4 < 4; ++m4) {
+      k[g][m4] = ip < 2 ? p[ip][m4] : df_neg(p[ip][m4]);
+      kr[m4] = p[ip][m4].hi;
+      kw[g][m4] = ip < 2 ? kr[m4] : -kr[m4];
+    }
+    polvec<R>(kr, ip >= 2, X.eps[g]);
+  }
+  {
+    R p3[4], p4[4];
+#pragma unroll
+    for (int m4 = 0; m4 < 4; ++m4) {
+      p3[m4] = p[2][m4].hi;
+      p4[m4] = p[3][m4].hi;
+    }
+    ubar_out<R>(p3, R(m), X.ub);
+    v_out<R>(p4, R(m), X.v);
+  }
+  df d[NG][NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i)
+#pragma unroll
+    for (int j = i + 1; j < NG; ++j) d[i][j] = df_scale(df_dot4(k[i], k[j]), 2.0f);  // 2 k_i.k_j
+  constexpr int FULL = (1 << NG) - 1;
+#pragma unroll
+  for (int msk = 1; msk <= FULL; ++msk) {
+    df P[4];
+    df K2 = {0.0f, 0.0f};
+    bool first = true;
+    int cnt = 0;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      if (!((msk >> i) & 1)) continue;
+      ++cnt;
+#pragma unroll
+      for (int m4 = 0; m4 < 4; ++m4) P[m4] = first ? k[i][m4] : df_add(P[m4], k[i][m4]);
+      first = false;
+#pragma unroll
+      for (int j = i + 1; j < NG; ++j)
+        if ((msk >> j) & 1) K2 = df_add(K2, d[i][j]);
+    }
+#pragma unroll
+    for (int m4 = 0; m4 < 4; ++m4) {
+      R v = R(0);
+#pragma unroll
+      for (int i = 0; i < NG; ++i)
+        if ((msk >> i) & 1) v += kw[i][m4];
+      Kn.P[msk][m4] = v;
+    }
+    if (cnt >= 2) {
+      const R inv = R(1) / K2.hi;
+      Kn.cg[msk] = -inv;
+      Kn.c4[msk] = inv;
+    } else {
+      Kn.cg[msk] = R(0);
+      Kn.c4[msk] = R(0);
+    }
+    if (msk != FULL) {
+      // (K - p4)^2 - m^2 = K^2 - 2 K.p4  (p4^2 = m^2)
+      const df den = df_sub(K2, df_scale(df_dot4(P, p[3]), 2.0f));
+      const R c = R(-1) / den.hi;
+#pragma unroll
+      for (int m4 = 0; m4 < 4; ++m4) Kn.qc[msk][m4] = c * df_sub(P[m4], p[3][m4]).hi;
+      Kn.mc[msk] = c * R(m);
+    } else {
+#pragma unroll
+      for (int m4 = 0; m4 < 4; ++m4) Kn.qc[msk][m4] = R(0);
+      Kn.mc[msk] = R(0);
+    }
+  }
+}
+
+// FP32 modes: the reshuffle on double-float momenta.  The FP32 Newton
+// iteration as above, then one Newton step in double-float (from ~1e-7 to
+// the double-float precision), energies updated to first order as above, so
+// that the moved momenta are on their mass shells to ~1e-14 relative.
+template <int NEXT>
+__device__ __forceinline__ bool reshuffle_tops(const df (&p)[NEXT][4], double mt, df (&q)[NEXT][4]) {
+  df etot = {0.0f, 0.0f}, p2[NEXT];
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+    etot = i == 2 ? p[i][0] : df_add(etot, p[i][0]);
+    p2[i] = df_norm3(p[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+    for (int m4 = 0; m4 < 4; ++m4) q[i][m4] = p[i][m4];
+  const df mtd = df_from_double(mt);
+  if (!(df_sub(etot, df_scale(mtd, 2.0f)).hi > 0.0f)) return false;
+  const df mt2 = df_mul(mtd, mtd);
+  const float etf = etot.hi, mt2f = mt2.hi;
+  float xf = 1.0f;
+  for (int it = 0; it < 40; ++it) {
+    float f = -etf, dfx = 0.0f;
+#pragma unroll
+    for (int i = 2; i < NEXT; ++i) {
+      const float pf = p2[i].hi;
+      const float e = sqrtf((i < 4 ? mt2f : 0.0f) + xf * xf * pf);
+      f += e;
+      dfx += xf * pf / e;
+    }
+    float step = f / dfx;
+    if (xf - step <= 0.0f) step = 0.5f * xf;
+    xf -= step;
+    if (fabsf(step) <= 2e-7f * xf) break;
+  }
+  const df xi2 = df_two_prod(xf, xf);
+  df e[NEXT];
+  df f = df_neg(etot);
+  float dfx = 0.0f;
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+    const df a = df_mul(xi2, p2[i]);
+    e[i] = df_sqrt(i < 4 ? df_add(mt2, a) : a);
+    f = df_add(f, e[i]);
+    dfx += xf * p2[i].hi / e[i].hi;
+  }
+  const float corr = -f.hi / dfx;
+  const df xn = df_fast_two_sum(xf, corr);
+#pragma unroll
+  for (int i = 2; i < NEXT; ++i) {
+    // e' = e + (xn^2 - xi^2) |p|^2 / (2 e), exact to O(corr^2)
+    e[i] = df_add_f(e[i], corr * (2.0f * xf + corr) * p2[i].hi / (2.0f * e[i].hi));
+#pragma unroll
+    for (int m4 = 1; m4 < 4; ++m4) q[i][m4] = df_mul(xn, p[i][m4]);
     q[i][0] = e[i];
   }
   return true;

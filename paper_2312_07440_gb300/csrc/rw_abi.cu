@@ -1037,3 +1037,26 @@ int rw_graph_destroy(rw_graph* g) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// rw_split_double: the FP32 modes' FP64 -> double-float input split, run on
+// an array (verification of df_from_double against the IEEE conversion).
+namespace {
+__global__ void k_split_double(const double* __restrict__ x, long long n, float* __restrict__ hi,
+                               float* __restrict__ lo) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const rw::df v = rw::df_from_double(x[i]);
+    hi[i] = v.hi;
+    lo[i] = v.lo;
+  }
+}
+}  // namespace
+
+extern "C" int rw_split_double(const double* d_x, int64_t n, float* d_hi, float* d_lo, void* stream) {
+  if (n < 0) return RW_ERR_ARG;
+  if (n > 0 && (!d_x || !d_hi || !d_lo)) return RW_ERR_NULL;
+  if (n == 0) return RW_OK;
+  const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+  k_split_double<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(d_x, n, d_hi, d_lo);
+  return cudaGetLastError() == cudaSuccess ? RW_OK : RW_ERR_CUDA;
+}

@@ -88,6 +88,7 @@ def load():
         "rw_graph_launch": ([P, P], i),
         "rw_graph_destroy": ([P], i),
         "rw_autotune": ([P, i64, ctypes.c_char_p, ctypes.POINTER(d)], i),
+        "rw_split_double": ([P, i64, P, P, P], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -106,6 +107,17 @@ def _ptr(x):
     if isinstance(x, np.ndarray):
         return x.ctypes.data
     return x.data_ptr()
+
+
+def split_double(d_x, d_hi, d_lo, stream=None):
+    """rw_split_double: the FP32 modes' FP64 -> (hi, lo) float split of the
+    device array d_x into d_hi, d_lo (same length), asynchronous on stream."""
+    n = int(d_x.numel())
+    if d_hi.numel() != n or d_lo.numel() != n:
+        raise ValueError("d_hi and d_lo must have the length of d_x")
+    rc = load().rw_split_double(_ptr(d_x), n, _ptr(d_hi), _ptr(d_lo), stream)
+    if rc:
+        raise RwError(rc, "rw_split_double")
 
 
 def process_info(process: str) -> RwProcessInfo:
