@@ -27,8 +27,8 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
-PROCESS_ID = {"ee_mumu": 0, "gg_tt": 1, "gg_ttg": 2, "gg_ttgg": 3}
-N_EXTERNAL = {"ee_mumu": 4, "gg_tt": 4, "gg_ttg": 5, "gg_ttgg": 6}
+PROCESS_ID = {"ee_mumu": 0, "gg_tt": 1, "gg_ttg": 2, "gg_ttgg": 3, "ee_5a": 4}
+N_EXTERNAL = {"ee_mumu": 4, "gg_tt": 4, "gg_ttg": 5, "gg_ttgg": 6, "ee_5a": 7}
 PARAM_FIELDS = ("alpha_s", "m_t", "w_t", "yt_scale", "alpha_em_inv", "G_F", "m_Z", "w_Z")
 
 _lib = None
@@ -80,6 +80,8 @@ def _load():
     lib.oracle_me_traces.restype = d
     lib.oracle_full_colour_amp.argtypes = [i, P, d, d, P, P, P]
     lib.oracle_full_colour_amp.restype = i
+    lib.oracle_ee_photons.argtypes = [i, P, P, i, P, P, P]
+    lib.oracle_ee_photons.restype = d
     lib.oracle_init()
     _lib = lib
     return lib
@@ -231,3 +233,19 @@ def full_colour_amp(process: str, p_aos, m: float, alpha_s: float, ext, adj) -> 
     M = np.empty(9, dtype=np.complex128)
     lib.oracle_full_colour_amp(PROCESS_ID[process], _ptr(p), m, alpha_s, _ptr(ext), _ptr(adj), _ptr(M))
     return M.reshape(3, 3)
+
+
+def ee_photons(n: int, par, p_aos, basis: int = 0, hel=None, eps=None):
+    """e- e+ -> n photons for one event p_aos[n+2][4]: (|M|^2 spin-averaged
+    with 1/4 and 1/n!, helicity amplitude for hel[n+2] in ``basis`` or None).
+    ``eps`` (complex [n][4], used as given) replaces the photon polarisations
+    of the amplitude (gauge tests)."""
+    lib = _load()
+    par = np.ascontiguousarray(par, dtype=np.float64)
+    p = np.ascontiguousarray(p_aos, dtype=np.float64).reshape(n + 2, 4)
+    amp = np.zeros(1, dtype=np.complex128)
+    h = None if hel is None else np.ascontiguousarray(hel, dtype=np.int32)
+    ep = None if eps is None else np.ascontiguousarray(eps, dtype=np.complex128).reshape(n, 4)
+    me2 = lib.oracle_ee_photons(n, _ptr(par), _ptr(p), basis, _ptr(h) if h is not None else None,
+                                _ptr(amp) if h is not None else None, _ptr(ep) if ep is not None else None)
+    return me2, (complex(amp[0]) if h is not None else None)

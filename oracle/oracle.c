@@ -31,13 +31,19 @@
  *     brute force from the 8 Gell-Mann matrices;
  *   - e+ e- -> mu+ mu- from explicit photon and Z currents, Z propagator in
  *     unitary gauge with a fixed width;
+ *   - e+ e- -> n photons (pure QED, massless electrons) as the sum over the
+ *     n! orders in which the photons attach to the electron line, one 4x4
+ *     matrix chain per order (the n! Feynman diagrams written out);
  *   - two further independent evaluations used only as pins: spin sums by
  *     traces with (pslash + m) projectors, and full-colour amplitudes from the
  *     colour-dressed (f^{abc}, t^a) Feynman rules.
  *
  * Readings where the paper is silent (it prints no amplitude formulas):
  *   - |M|^2 normalisation: 1/4 spin average, 1/64 colour average for g g,
- *     1/n! for n identical outgoing gluons;
+ *     1/n! for n identical outgoing gluons or photons;
+ *   - e+ e- -> 5 photons: massless electrons, coupling e = sqrt(4 pi alpha)
+ *     with alpha = 1/alpha_em_inv (the "electroweak coupling" the paper's
+ *     benchmark varies);
  *   - EW inputs (alpha, G_F, M_Z) with M_W, s_W derived per parameter set;
  *   - top width 0 in every top propagator (all are off shell);
  *   - a top-mass change moves the event onto the new mass shell by a common
@@ -62,9 +68,11 @@ typedef double complex cx;
 #define OR_GG_TT 1
 #define OR_GG_TTG 2
 #define OR_GG_TTGG 3
+#define OR_EE_5A 4  /* e- e+ -> 5 photons (the paper's own process, Table 1) */
 #define MAXG 4      /* max gluons on the quark line */
 #define MAXK 24     /* 4! colour orderings */
-#define MAXN 6      /* max external particles */
+#define MAXN 7      /* max external particles */
+#define MAXA 5      /* max photons on the electron line */
 
 /* model parameters, same field order as the product's rw_params */
 typedef struct {
@@ -513,10 +521,12 @@ static int n_external(int process) {
     case OR_GG_TT: return 4;
     case OR_GG_TTG: return 5;
     case OR_GG_TTGG: return 6;
+    case OR_EE_5A: return 7;
     }
     return -1;
 }
-static int n_gluons(int process) { return process == OR_EE_MUMU ? 0 : n_external(process) - 2; }
+static int is_qcd(int process) { return process >= OR_GG_TT && process <= OR_GG_TTGG; }
+static int n_gluons(int process) { return is_qcd(process) ? n_external(process) - 2 : 0; }
 
 /* gluon g of the quark line -> particle index: g0 = 0, g1 = 1, g2.. = 4.. */
 static int gluon_particle(int g) { return g < 2 ? g : g + 2; }
@@ -645,8 +655,74 @@ static double me_gg_tt_ng(int process, double p[][4], const or_params *par) {
     return sum / (4.0 * 64.0 * factorial(n - 2));
 }
 
+/*
+ * e-(p0) e+(p1) -> photons k_1..k_n (particles 2..n+1), massless electrons,
+ * pure QED.  For one helicity configuration (basis as in spinor_u/polvec;
+ * hel[0] e-, hel[1] e+, hel[2..] photons):
+ *   A = e^n sum_{orders s} vbar(p1) eps*_{s_n}slash S(q_{n-1}) ...
+ *       eps*_{s_2}slash S(q_1) eps*_{s_1}slash u(p0),
+ *   q_j = p0 - k_{s_1} - ... - k_{s_j},  S(q) = qslash / q^2,
+ * the n! tree diagrams with the photons attached to the electron line in
+ * every order (common factors of i and the vertex sign dropped: every
+ * diagram carries the same ones).
+ */
+static cx amp_ee_photons(int n, double p[][4], int basis, const int *hel, double e, const cx *eps_in) {
+    cx u[4], v[4], vb[4], E[MAXA][4][4];
+    spinor_u(p[0], 0.0, basis, hel[0], u);
+    spinor_v(p[1], 0.0, basis, hel[1], v);
+    dirac_bar(v, vb);
+    for (int i = 0; i < n; i++) {
+        cx eps[4];
+        if (eps_in) { /* explicit (already conjugated) polarisation vectors */
+            memcpy(eps, eps_in + 4 * i, sizeof(eps));
+        } else {
+            polvec(p[2 + i], basis, hel[2 + i], eps);
+            for (int mu = 0; mu < 4; mu++) eps[mu] = conj(eps[mu]);
+        }
+        slash(eps, E[i]);
+    }
+    int order[MAXA];
+    for (int i = 0; i < n; i++) order[i] = i;
+    cx A = 0;
+    do {
+        cx psi[4], t[4];
+        double q[4];
+        memcpy(psi, u, sizeof(psi));
+        memcpy(q, p[0], sizeof(q));
+        for (int j = 0; j < n; j++) {
+            matvec(E[order[j]], psi, t);
+            if (j == n - 1) {
+                memcpy(psi, t, sizeof(psi));
+                break;
+            }
+            for (int mu = 0; mu < 4; mu++) q[mu] -= p[2 + order[j]][mu];
+            cx Q[4][4];
+            rslash(q, Q);
+            matvec(Q, t, psi);
+            double q2 = rdot(q, q);
+            for (int a = 0; a < 4; a++) psi[a] /= q2;
+        }
+        A += rowcol(vb, psi);
+    } while (next_perm(order, n));
+    return pow(e, n) * A;
+}
+
+/* spin-averaged |M|^2 of e- e+ -> n photons (1/4, 1/n!) */
+static double me_ee_photons(int n, double p[][4], const or_params *par) {
+    double e = sqrt(4.0 * M_PI / par->alpha_em_inv);
+    double sum = 0;
+    int hel[MAXA + 2];
+    for (int h = 0; h < (1 << (n + 2)); h++) {
+        for (int i = 0; i < n + 2; i++) hel[i] = (h >> i) & 1;
+        cx A = amp_ee_photons(n, p, 0, hel, e, NULL);
+        sum += creal(A * conj(A));
+    }
+    return sum / (4.0 * factorial(n));
+}
+
 static double me_event(int process, double p[][4], const or_params *par) {
     if (process == OR_EE_MUMU) return me_ee_mumu(p, par);
+    if (process == OR_EE_5A) return me_ee_photons(5, p, par);
     return me_gg_tt_ng(process, p, par);
 }
 
@@ -690,7 +766,7 @@ static int reshuffle(int N, const double *mnew, double pin[][4], double pout[][4
 static void new_masses(int process, const or_params *par, double *m) {
     int N = n_external(process);
     for (int i = 0; i < N; i++) m[i] = 0;
-    if (process != OR_EE_MUMU) m[2] = m[3] = par->m_t;
+    if (is_qcd(process)) m[2] = m[3] = par->m_t;
 }
 
 static void load_event(int N, long E, const double *mom, long e, double p[][4]) {
@@ -770,7 +846,7 @@ int oracle_reweight(int process, const double *par0, int P, const double *pars, 
         if (me0) me0[e] = m0;
         for (int j = 0; j < P; j++) {
             double m1;
-            if (process != OR_EE_MUMU && pt[j].m_t != p0->m_t) {
+            if (is_qcd(process) && pt[j].m_t != p0->m_t) {
                 double mn[MAXN];
                 new_masses(process, &pt[j], mn);
                 m1 = reshuffle(N, mn, p, q) ? 0.0 : me_event(process, q, &pt[j]);
@@ -820,7 +896,7 @@ void oracle_dirac(cx *g, cx *g5) {
  * (row), antitop -> v.  basis 0: z-spin / linear, 1: helicity.  hel[i] in {0,1}.
  */
 int oracle_external(int process, const double *p, double m, int basis, const int *hel, cx *ext) {
-    if (process == OR_EE_MUMU || n_external(process) < 0) return -1;
+    if (!is_qcd(process)) return -1;
     init_all();
     int N = n_external(process);
     double pp[MAXN][4];
@@ -854,7 +930,7 @@ void oracle_polvec(const double *k, int basis, int s, cx *out) { polvec(k, basis
 
 /* all partial amplitudes A[K] for explicit external wavefunctions ext[N][4] */
 int oracle_partial_amps(int process, const double *p, double m, double alpha_s, const cx *ext, cx *A) {
-    if (process == OR_EE_MUMU || n_external(process) < 0) return -1;
+    if (!is_qcd(process)) return -1;
     init_all();
     int n = n_gluons(process), N = n_external(process);
     double pp[MAXN][4], k[MAXG][4];
@@ -876,7 +952,7 @@ int oracle_partial_amps(int process, const double *p, double m, double alpha_s, 
 double oracle_me_traces(int process, const double *par, const double *p_aos) {
     init_all();
     int N = n_external(process);
-    if (N < 0) return NAN;
+    if (N < 0 || process == OR_EE_5A) return NAN;
     const or_params *pp = (const or_params *)par;
     double p[MAXN][4];
     memcpy(p, p_aos, sizeof(double) * 4 * N);
@@ -978,7 +1054,7 @@ double oracle_me_traces(int process, const double *par, const double *p_aos) {
  */
 int oracle_full_colour_amp(int process, const double *p_aos, double m, double alpha_s, const cx *ext, const int *adj,
                            cx *Mout) {
-    if (process == OR_EE_MUMU || n_external(process) < 0) return -1;
+    if (!is_qcd(process)) return -1;
     init_all();
     int n = n_gluons(process), N = n_external(process);
     double p[MAXN][4], k[MAXG][4];
@@ -1118,4 +1194,22 @@ int oracle_full_colour_amp(int process, const double *p_aos, double m, double al
         }
     }
     return 0;
+}
+
+/*
+ * e- e+ -> n photons (n = 1..5) for one event (AoS p[n+2][4]): the helicity
+ * amplitude for hel[n+2] in `basis` (0: z-spin / linear, 1: helicity) into
+ * *amp -- with the photon polarisations eps_in[n][4] (used as given, i.e.
+ * already conjugated) instead when eps_in is not NULL -- and the
+ * spin-averaged |M|^2 (1/4, 1/n!) as the return value.
+ */
+double oracle_ee_photons(int n, const double *par, const double *p_aos, int basis, const int *hel, cx *amp,
+                         const cx *eps_in) {
+    if (n < 1 || n > MAXA) return NAN;
+    init_all();
+    double p[MAXN][4];
+    memcpy(p, p_aos, sizeof(double) * 4 * (n + 2));
+    const or_params *pp = (const or_params *)par;
+    if (amp && hel) *amp = amp_ee_photons(n, p, basis, hel, sqrt(4.0 * M_PI / pp->alpha_em_inv), eps_in);
+    return me_ee_photons(n, p, pp);
 }

@@ -163,18 +163,20 @@ M_TOP = 173.0
 class Workload:
     """A synthetic event sample: process, sizes, kinematic ranges and cuts."""
     name: str
-    process: str          # 'ee_mumu' | 'gg_tt' | 'gg_ttg' | 'gg_ttgg'
+    process: str          # 'ee_mumu' | 'gg_tt' | 'gg_ttg' | 'gg_ttgg' | 'ee_5a'
     n_events: int
     sqrt_s: tuple         # (lo, hi); lo == hi for a fixed energy
     final_masses: tuple   # masses of the outgoing particles, in order
-    pt_min: float = 0.0   # applied to the outgoing gluons
-    dr_min: float = 0.0   # applied to outgoing gluon pairs
+    pt_min: float = 0.0   # applied to the outgoing gluons / photons
+    dr_min: float = 0.0   # applied to outgoing gluon / photon pairs
     seed: int = 231207440
+    eta_max: float = 0.0  # |pseudorapidity| bound on the same particles (0: none)
 
 
-N_EXTERNAL = {"ee_mumu": 4, "gg_tt": 4, "gg_ttg": 5, "gg_ttgg": 6}
-# index of the first outgoing gluon (gluons follow t, tbar)
-_FIRST_FINAL_GLUON = {"ee_mumu": None, "gg_tt": None, "gg_ttg": 4, "gg_ttgg": 4}
+N_EXTERNAL = {"ee_mumu": 4, "gg_tt": 4, "gg_ttg": 5, "gg_ttgg": 6, "ee_5a": 7}
+# index of the first outgoing particle the cuts apply to (gluons follow t,
+# tbar; the five photons of e- e+ -> 5 photons are particles 2..6)
+_FIRST_FINAL_GLUON = {"ee_mumu": None, "gg_tt": None, "gg_ttg": 4, "gg_ttgg": 4, "ee_5a": 2}
 
 # The five sample definitions (events, energies, cuts) the library is
 # benchmarked and tested on; seeds are 231207440 + index.
@@ -185,6 +187,11 @@ WORKLOADS = {
                           seed=231207440 + 2),
     "gg_ttgg_1m": Workload("gg_ttgg_1m", "gg_ttgg", 1 << 20, (600.0, 4000.0), (M_TOP, M_TOP, 0.0, 0.0),
                            pt_min=20.0, dr_min=0.4, seed=231207440 + 3),
+    # the paper's own benchmark process (Table 1), e- e+ -> 5 photons; photon
+    # cuts p_T > 10 GeV, |eta| < 2.5, Delta R > 0.4 (the usual generator-level
+    # photon cuts), sqrt(s) = 500 GeV
+    "ee_5a_1m": Workload("ee_5a_1m", "ee_5a", 1 << 20, (500.0, 500.0), (0.0,) * 5, pt_min=10.0, dr_min=0.4,
+                         seed=231207440 + 5, eta_max=2.5),
 }
 
 
@@ -198,6 +205,11 @@ def _cuts_pass(p, wl):
     if wl.pt_min > 0:
         for i in gl:
             ok &= pt[i] > wl.pt_min
+    if wl.eta_max > 0:
+        for i in gl:
+            pa = np.sqrt(p[i, 1] ** 2 + p[i, 2] ** 2 + p[i, 3] ** 2)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                ok &= np.abs(0.5 * np.log((pa + p[i, 3]) / (pa - p[i, 3]))) < wl.eta_max
     if wl.dr_min > 0 and len(gl) > 1:
         for a in range(len(gl)):
             for b in range(a + 1, len(gl)):
@@ -313,11 +325,19 @@ def reweight_points(workload_name: str, variant: str = "default"):
                 Yukawa (absent from these tree amplitudes, so r = 1), 'mt'
                 scales m_t = kappa * 173 GeV instead.
     gg_ttgg_1m: one point kappa = 1.2, same two variants.
+    ee_5a_1m:   8 points with a random electroweak coupling each (the paper's
+                benchmark, Table 1): alpha' = alpha (0.5 + u), u ~ U[0, 1)
+                from the sample's Philox stream 2.
     """
     if workload_name == "ee_mumu_4k":
         return param_vector(m_Z=92.0, w_Z=2.6)[None]
     if workload_name == "gg_tt_1m":
         return param_vector(m_t=175.0, alpha_s=0.120)[None]
+    if workload_name == "ee_5a_1m":
+        wl = WORKLOADS[workload_name]
+        u = _uniforms(wl.seed, np.arange(8, dtype=np.uint64), 0, 1, stream=2)[0]
+        inv0 = SM_PARAMS["alpha_em_inv"]
+        return np.stack([param_vector(alpha_em_inv=inv0 / (0.5 + x)) for x in u])
     if workload_name in ("gg_ttg_4m", "gg_ttgg_1m"):
         ks = [0.8 + 0.4 * i / 63 for i in range(64)] if workload_name == "gg_ttg_4m" else [1.2]
         if variant == "mt":

@@ -32,17 +32,23 @@ def test_rambo_kinematics_and_cuts(name):
         assert np.allclose(m2[i], m * m, atol=1e-8 * mom[i, 0].max() ** 2)
     rs = mom[0, 0] + mom[1, 0]
     assert rs.min() >= wl.sqrt_s[0] - 1e-9 and rs.max() <= wl.sqrt_s[1] + 1e-9
-    if wl.pt_min:
-        for i in range(4, N):
-            assert np.hypot(mom[i, 1], mom[i, 2]).min() > wl.pt_min
-    if wl.dr_min:
-        p5, p6 = mom[4], mom[5]
+    first = 2 if wl.process == "ee_5a" else 4  # cut particles: photons / outgoing gluons
 
-        def eta(p):
-            a = np.sqrt(p[1] ** 2 + p[2] ** 2 + p[3] ** 2)
-            return 0.5 * np.log((a + p[3]) / (a - p[3]))
-        dphi = np.angle(np.exp(1j * (np.arctan2(p5[2], p5[1]) - np.arctan2(p6[2], p6[1]))))
-        assert np.sqrt((eta(p5) - eta(p6)) ** 2 + dphi ** 2).min() > wl.dr_min
+    def eta(p):
+        a = np.sqrt(p[1] ** 2 + p[2] ** 2 + p[3] ** 2)
+        return 0.5 * np.log((a + p[3]) / (a - p[3]))
+    if wl.pt_min:
+        for i in range(first, N):
+            assert np.hypot(mom[i, 1], mom[i, 2]).min() > wl.pt_min
+    if wl.eta_max:
+        for i in range(first, N):
+            assert np.abs(eta(mom[i])).max() < wl.eta_max
+    if wl.dr_min:
+        for i in range(first, N):
+            for j in range(i + 1, N):
+                pa, pb = mom[i], mom[j]
+                dphi = np.angle(np.exp(1j * (np.arctan2(pa[2], pa[1]) - np.arctan2(pb[2], pb[1]))))
+                assert np.sqrt((eta(pa) - eta(pb)) ** 2 + dphi ** 2).min() > wl.dr_min
     # lognormal weights: log w ~ N(0, 1)
     lw = np.log(w)
     assert abs(lw.mean()) < 0.1 and abs(lw.std() - 1) < 0.1
