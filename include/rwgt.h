@@ -65,6 +65,8 @@ extern "C" {
 #define RW_GG_TT 1     /* g g -> t tbar, 3 diagrams, 2 colour orderings */
 #define RW_GG_TTG 2    /* g g -> t tbar g, 16 diagrams, 6 orderings */
 #define RW_GG_TTGG 3   /* g g -> t tbar g g, 123 diagrams, 24 orderings */
+#define RW_EE_5A 4     /* e- e+ -> 5 photons (the paper's benchmark process, Table 1): pure QED,
+                          massless electrons, 120 diagrams, 128 helicities; FP64 and FP32 modes */
 
 /* precision modes of the amplitude arithmetic; momenta, propagator
    invariants, r, W' and sigma are FP64 in every mode */
@@ -80,7 +82,8 @@ extern "C" {
    (w_t must be 0: every top propagator here is off shell; yt_scale, the top
    Yukawa scale, enters no tree diagram of these processes).  e+e- -> mu+mu-
    uses alpha_em_inv = 1/alpha, G_F [GeV^-2], m_Z, w_Z [GeV]; M_W and s_W are
-   derived: M_W^2 = M_Z^2/2 + sqrt(M_Z^4/4 - pi alpha M_Z^2/(sqrt2 G_F)). */
+   derived: M_W^2 = M_Z^2/2 + sqrt(M_Z^4/4 - pi alpha M_Z^2/(sqrt2 G_F)).
+   e+e- -> 5 photons uses alpha_em_inv only (e = sqrt(4 pi / alpha_em_inv)). */
 typedef struct rw_params {
   double alpha_s, m_t, w_t, yt_scale;
   double alpha_em_inv, G_F, m_Z, w_Z;

@@ -6,6 +6,7 @@
 #include "helas.cuh"
 #include "kernels.cuh"
 #include "qcd.cuh"
+#include "qed.cuh"
 
 namespace rw {
 
@@ -44,6 +45,38 @@ struct QcdProc {
       return reshuffle_tops<NEXT, 2>(p, mt, q);
     else
       return reshuffle_tops<NEXT>(p, mt, q);
+  }
+};
+
+// e-(p0) e+(p1) -> n photons (massless QED).  Tag provides NA, NEXT, MAX_LB
+// and hel_sum<R, LB>() (generated by gen/qed_gen.py); |M|^2 = cscale * sum,
+// cscale = e^(2n) / (4 n!).  Nothing moves with the parameters (no reshuffle).
+template <class Tag>
+struct QedProc {
+  static constexpr int NA = Tag::NA;
+  static constexpr int NEXT = Tag::NEXT;
+  template <class R>
+  using mom_t = typename std::conditional<sizeof(R) == 8, double, df>::type;
+
+  template <class R, int LB>
+  __device__ __noinline__ static double me(const mom_t<R> (&p)[NEXT][4], const PointDev& pt, int lane,
+                                           unsigned gmask) {
+    static_assert(LB <= Tag::MAX_LB, "more lane bits than helicity levels");
+    QedExt<R, NA> X;
+    QedKin<R, NA> Kn;
+    qed_setup<R, NA, NEXT>(p, X, Kn);
+    double s = double(Tag::template hel_sum<R, LB>(X, Kn, lane));
+#pragma unroll
+    for (int o = 1; o < (1 << LB); o <<= 1) s += __shfl_xor_sync(gmask, s, o);
+    return s * pt.cscale;
+  }
+  template <class R>
+  __device__ __forceinline__ static bool reshuffle(const mom_t<R> (&p)[NEXT][4], double, mom_t<R> (&q)[NEXT][4]) {
+#pragma unroll
+    for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) q[i][m] = p[i][m];
+    return true;
   }
 };
 

@@ -20,6 +20,9 @@ struct ProcStatic {
 };
 
 void register_ee_mumu(std::vector<KernelEntry>& t, ProcStatic& s);
+void register_ee_5a_fp64(std::vector<KernelEntry>& t);
+void register_ee_5a_fp32(std::vector<KernelEntry>& t);
+void static_ee_5a(ProcStatic& s);
 #define RW_DECLARE_QCD(name)                              \
   void register_##name##_fp64(std::vector<KernelEntry>& t); \
   void register_##name##_fp32(std::vector<KernelEntry>& t); \

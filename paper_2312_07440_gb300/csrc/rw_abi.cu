@@ -27,7 +27,7 @@ using rw::RwArgs;
 namespace {
 
 constexpr int GRID_CAP = 8192;
-constexpr int NPROC = 4;
+constexpr int NPROC = 5;
 
 struct Registry {
   std::vector<KernelEntry> kernels;
@@ -46,6 +46,9 @@ struct Registry {
     rw::register_gg_ttgg_fp64(kernels);
     rw::register_gg_ttgg_fp32(kernels);
     rw::static_gg_ttgg(st[RW_GG_TTGG]);
+    rw::register_ee_5a_fp64(kernels);
+    rw::register_ee_5a_fp32(kernels);
+    rw::static_ee_5a(st[RW_EE_5A]);
   }
   const KernelEntry* find(int process, int mode, int lb) const {
     for (const auto& k : kernels)
@@ -66,6 +69,7 @@ int default_lane_bits(int process, int mode) {
     case RW_GG_TT: return 0;
     case RW_GG_TTG: return 0;
     case RW_GG_TTGG: return mode == RW_FP64 ? 1 : 2;
+    case RW_EE_5A: return 0;
   }
   return 0;
 }
@@ -132,7 +136,9 @@ bool finite_params(const rw_params& p) {
 
 int check_params(rw_ctx* c, const rw_params& p) {
   if (!finite_params(p)) return fail(c, RW_ERR_PARAM, "parameters must be finite");
-  if (c->process == RW_EE_MUMU) {
+  if (c->process == RW_EE_5A) {
+    if (!(p.alpha_em_inv > 0)) return fail(c, RW_ERR_PARAM, "alpha_em_inv must be > 0");
+  } else if (c->process == RW_EE_MUMU) {
     if (!(p.alpha_em_inv > 0 && p.G_F > 0 && p.m_Z > 0 && p.w_Z >= 0))
       return fail(c, RW_ERR_PARAM, "need alpha_em_inv > 0, G_F > 0, m_Z > 0, w_Z >= 0");
     const double a = 1.0 / p.alpha_em_inv;
@@ -144,6 +150,13 @@ int check_params(rw_ctx* c, const rw_params& p) {
     if (p.w_t != 0.0) return fail(c, RW_ERR_PARAM, "w_t must be 0 (all top propagators are off shell)");
   }
   return RW_OK;
+}
+
+bool moves_possible(const rw_ctx* c) { return c->process >= RW_GG_TT && c->process <= RW_GG_TTGG; }
+
+// a top-mass change moves the event onto the new mass shell (QCD processes)
+bool moves_event(const rw_ctx* c, const rw_params& pt) {
+  return c->process >= RW_GG_TT && c->process <= RW_GG_TTGG && pt.m_t != c->p0.m_t;
 }
 
 // per-evaluation constants (derived couplings), computed once per point
@@ -163,6 +176,15 @@ PointDev make_point(const rw_ctx* c, const rw_params& p, bool reshuffle) {
     d.MZ = MZ;
     d.WZ = p.w_Z;
     d.cscale = 1.0;
+  } else if (c->process == RW_EE_5A) {
+    // e^(2n) / (4 n!): couplings stripped from the amplitude, spin average, identical photons
+    const double e2 = 4.0 * M_PI / p.alpha_em_inv;
+    double epow = 1.0, nfact = 1.0;
+    for (int i = 1; i <= s.n_ident; ++i) {
+      epow *= e2;
+      nfact *= i;
+    }
+    d.cscale = epow / (4.0 * nfact);
   } else {
     double ident_fact = 1.0;
     for (int i = 2; i <= s.n_ident; ++i) ident_fact *= i;
@@ -488,7 +510,7 @@ int rw_eval_me(rw_ctx* c, int point, double* d_me) {
   if (point < 0) {
     a.pt[0] = make_point(c, c->p0, false);
   } else {
-    const bool moved = c->process != RW_EE_MUMU && c->pts[point].m_t != c->p0.m_t;
+    const bool moved = moves_event(c, c->pts[point]);
     a.pt[0] = make_point(c, c->pts[point], moved);
   }
   fill_ws(c, a, 0);
@@ -519,7 +541,7 @@ int rw_reweight_async(rw_ctx* c, double* d_wnew, double* d_ratio, double* d_me0,
   a.me_only = 0;
   a.pt[0] = make_point(c, c->p0, false);
   for (int j = 0; j < P; ++j) {
-    const bool moved = c->process != RW_EE_MUMU && c->pts[j].m_t != c->p0.m_t;
+    const bool moved = moves_event(c, c->pts[j]);
     a.pt[1 + j] = make_point(c, c->pts[j], moved);
   }
   fill_ws(c, a, P);
@@ -689,7 +711,7 @@ extern "C" int rw_reweight_noalloc(rw_ctx* c, const double* d_mom, const double*
   a.me_only = 0;
   a.pt[0] = make_point(c, c->p0, false);
   for (int j = 0; j < P; ++j) {
-    const bool moved = c->process != RW_EE_MUMU && c->pts[j].m_t != c->p0.m_t;
+    const bool moved = moves_event(c, c->pts[j]);
     a.pt[1 + j] = make_point(c, c->pts[j], moved);
   }
   a.ticket = reinterpret_cast<unsigned int*>(scratch);
@@ -880,6 +902,7 @@ int rw_surrogate_features(rw_ctx* c, int n_in, double p_scale, double k_scale, c
                           float* d_y) {
   int rc = ready(c, true);
   if (rc) return rc;
+  if (!moves_possible(c)) return fail(c, RW_ERR_MODE, "the surrogate covers the top-mass axis of the QCD processes");
   if (c->pts.empty()) return fail(c, RW_ERR_STATE, "no points set");
   if (!d_x) return fail(c, RW_ERR_NULL, "x is NULL");
   if (n_in < 1 || !(p_scale > 0) || !(k_scale > 0)) return fail(c, RW_ERR_ARG, "bad feature parameters");
@@ -902,6 +925,7 @@ int rw_surrogate_reweight(rw_ctx* c, rw_mlp* m, double p_scale, double k_scale, 
                           size_t ws_bytes) {
   int rc = ready(c, true);
   if (rc) return rc;
+  if (!moves_possible(c)) return fail(c, RW_ERR_MODE, "the surrogate covers the top-mass axis of the QCD processes");
   if (!m || !d_wnew || !d_ws) return fail(c, RW_ERR_NULL, "model, W' and workspace are required");
   if (c->pts.empty()) return fail(c, RW_ERR_STATE, "no points set");
   DeviceGuard g(c->device);
@@ -957,7 +981,7 @@ int rw_surrogate_reweight(rw_ctx* c, rw_mlp* m, double p_scale, double k_scale, 
     a.wnew = wn_g;
     a.P = 1;
     a.pt[0] = make_point(c, c->p0, false);
-    a.pt[1] = make_point(c, c->pts[p], c->process != RW_EE_MUMU && c->pts[p].m_t != c->p0.m_t);
+    a.pt[1] = make_point(c, c->pts[p], moves_event(c, c->pts[p]));
     char* core = b + L.core;
     a.ticket = reinterpret_cast<unsigned int*>(core);
     a.nbad_count = reinterpret_cast<unsigned long long*>(core + 8);

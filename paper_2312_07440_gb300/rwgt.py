@@ -19,7 +19,7 @@ RW_OK = 0
 RW_WARN_BAD_EVENTS = 1
 ERRORS = {-1: "RW_ERR_NULL", -2: "RW_ERR_ARG", -3: "RW_ERR_MODE", -4: "RW_ERR_PARAM", -5: "RW_ERR_CUDA",
           -6: "RW_ERR_STATE", -7: "RW_ERR_ALIGN", -8: "RW_ERR_WORKSPACE"}
-PROCESS = {"ee_mumu": 0, "gg_tt": 1, "gg_ttg": 2, "gg_ttgg": 3}
+PROCESS = {"ee_mumu": 0, "gg_tt": 1, "gg_ttg": 2, "gg_ttgg": 3, "ee_5a": 4}
 MODE = {"fp64": 0, "fp32": 1, "mixed_fp16": 2, "mixed_bf16": 3}
 MAX_POINTS = 256
 PARAM_FIELDS = ("alpha_s", "m_t", "w_t", "yt_scale", "alpha_em_inv", "G_F", "m_Z", "w_Z")

@@ -161,6 +161,36 @@ def test_gg_ttgg_parity(mode):
         check_against_oracle(g, o, mode, sens)
 
 
+# --------------------------------------------------------------------------
+# e- e+ -> 5 photons (the paper's benchmark process), random coupling points
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+@pytest.mark.parametrize("lane_bits", [0, 1, 2, 3])
+def test_ee_5a_parity(mode, lane_bits):
+    pts = ev.reweight_points("ee_5a_1m")[:3]
+    mom, w, o = oracle_run("ee_5a", "ee_5a_1m", 517, pts)  # several blocks + a ragged tail
+    g = run_gpu("ee_5a", mode, mom, w, pts, lane_bits=lane_bits)
+    sens = sensitivity("ee_5a", "ee_5a_1m", 517, pts) if mode == "fp64" else None
+    check_against_oracle(g, o, mode, sens)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_ee_5a_coupling_only_points(mode):
+    """Unchanged parameters give r == 1 bitwise (P8); a coupling change gives
+    r = (alpha'/alpha)^5 for every event (only e enters)."""
+    pts = np.stack([ev.param_vector(), ev.param_vector(alpha_em_inv=100.0)])
+    mom, w = ev.generate(ev.WORKLOADS["ee_5a_1m"], 300)
+    g = run_gpu("ee_5a", mode, mom, w, pts)
+    assert np.all(g["ratio"][0] == 1.0) and np.all(g["wnew"][0] == w)
+    assert np.abs(g["ratio"][1] / (ev.SM_PARAMS["alpha_em_inv"] / 100.0) ** 5 - 1).max() < 1e-14
+
+
+def test_ee_5a_has_no_mixed_mode():
+    mom, w = ev.generate(ev.WORKLOADS["ee_5a_1m"], 64)
+    with pytest.raises(rwgt.RwError):
+        run_gpu("ee_5a", "mixed_fp16", mom, w, ev.reweight_points("ee_5a_1m"))
+
+
 def test_yukawa_axis_gives_unit_ratio():
     pts = ev.reweight_points("gg_ttg_4m")[:8]
     mom, w = ev.generate(ev.WORKLOADS["gg_ttg_4m"], 300)
