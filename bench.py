@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--train-events", type=int, default=1 << 20)
     ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--infer-events", type=int, default=1 << 22)
+    ap.add_argument("--scan", choices=["events", "points"], default=None,
+                    help="scaling study of the paper's Figs. 2-3: time to reweight n events for one "
+                         "point (events), or 100,000 events for n points (points), through the host entry "
+                         "point and device-resident")
     return ap.parse_args()
 
 
@@ -560,12 +564,93 @@ def run_surrogate(args):
     m.close()
 
 
+def scan_points(wl, n):
+    """n parameter points for a scan: random couplings (e- e+ -> 5 photons),
+    else m_t = kappa 173 GeV with kappa spread over [0.8, 1.2]."""
+    if wl.process == "ee_5a":
+        return ev.coupling_points(n)
+    if wl.process == "ee_mumu":
+        return np.stack([ev.param_vector(m_Z=91.0 + 2.0 * i / max(n - 1, 1)) for i in range(n)])
+    ks = [0.8 + 0.4 * i / max(n - 1, 1) for i in range(n)]
+    return np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in ks])
+
+
+def run_scan(args):
+    """Runtime against the number of events (one point) or of parameter points
+    (100,000 events), as in the paper's Figs. 2 and 3: per configuration the
+    median of 5 host-to-host calls (rw_reweight_host: H2D, reweight, D2H) with
+    min and max, and the device-resident time of the same reweight."""
+    import torch
+    from paper_2312_07440_gb300 import rwgt
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    wl = ev.WORKLOADS[args.workload]
+    if args.scan == "events":
+        grid = [(n, 1) for n in (1, 10, 100, 1000, 10000, 100000, 1000000) if n <= wl.n_events]
+    else:
+        grid = [(100000, p) for p in (1, 2, 4, 8, 16, 32, 64, 128)]
+    nmax = max(n for n, _ in grid)
+    mom_h, w_h = ev.generate(wl, nmax)
+    rows = []
+    for n, P in grid:
+        pts = scan_points(wl, P)
+        m = np.ascontiguousarray(mom_h[:, :, :n])
+        wv = np.ascontiguousarray(w_h[:n])
+        N = m.shape[0]
+        c = rwgt.Context(0, stream.cuda_stream)
+        c.set_process(wl.process, args.mode)
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(pts)
+        if args.lane_bits >= 0 or args.block:
+            c.set_tuning(args.lane_bits, args.block)
+        hm, hw = torch.from_numpy(m).pin_memory(), torch.from_numpy(wv).pin_memory()
+        hwn = torch.empty((P, n), dtype=torch.float64).pin_memory()
+        nb = c.workspace_bytes_host(n)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            c.reweight_host(hm, hw, n, hwn, P, ws, nb)
+        th = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            c.reweight_host(hm, hw, n, hwn, P, ws, nb)
+            th.append(time.perf_counter() - t0)
+        dm, dw = torch.from_numpy(m).to(dev), torch.from_numpy(wv).to(dev)
+        nbd = c.workspace_bytes(n)
+        wsd = torch.empty(nbd, dtype=torch.uint8, device=dev)
+        c.load_events(dm, dw, n, wsd, nbd)
+        wn = torch.empty((P, n), dtype=torch.float64, device=dev)
+        for _ in range(3):
+            c.reweight_async(wn)
+        td = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            c.reweight_async(wn)
+            b.record(stream)
+            torch.cuda.synchronize()
+            td.append(a.elapsed_time(b) * 1e-3)
+        c.close()
+        rows.append({"events": n, "points": P, "e2e_ms_median_min_max": [1e3 * statistics.median(th),
+                                                                        1e3 * min(th), 1e3 * max(th)],
+                     "device_ms_median": 1e3 * statistics.median(td),
+                     "h2d_bytes": int(8 * (4 * N * n + n)), "d2h_bytes": int(8 * (P * n + P + 2))})
+    last = rows[-1]
+    value = last["events"] * last["points"] / (last["e2e_ms_median_min_max"][0] * 1e-3)
+    print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+                      "data": "synthetic", "dtype": {"fp64": "f64", "fp32": "f32"}.get(args.mode, args.mode),
+                      "config": {"workload": wl.name, "process": wl.process, "mode": args.mode,
+                                 "scan": args.scan, "value_from": "largest configuration, end to end"},
+                      "scan": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.surrogate:
         run_surrogate(args)
+    elif args.scan:
+        run_scan(args)
     else:
         run_ours(args)
 

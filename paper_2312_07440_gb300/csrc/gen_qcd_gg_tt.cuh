@@ -45,9 +45,9 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
         sp<R> tS_1 = slash(E1, S_E);
         const sp<R> S_1 = fprop(Kn.qc[2], Kn.mc[2], tS_1);
         sp<R> X0 = slash(E0, S_1);
-        spadd(X0, slash(J0_1, S_E));
+        slash_acc(X0, J0_1, S_E);
         sp<R> X1 = slash(E1, S_0);
-        spadd(X1, slash(J1_0, S_E));
+        slash_acc(X1, J1_0, S_E);
         #pragma unroll 1
         for (int i3 = 0; i3 < (LB >= 3 ? 1 : 2); ++i3) {
           const int h3 = LB >= 3 ? ((lane >> (LB - 3)) & 1) : i3;

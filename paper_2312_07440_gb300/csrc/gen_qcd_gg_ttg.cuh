@@ -45,13 +45,13 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
         const cv<R> J2_0 = neg(J0_2);
         const cv<R> J2_1 = neg(J1_2);
         cv<R> J0_1_2 = vvv(E0, Kn.P[1], J1_2, Kn.P[6], Kn.cg[7]);
-        addto(J0_1_2, vvv(J0_1, Kn.P[3], E2, Kn.P[4], Kn.cg[7]));
+        vvv_acc(J0_1_2, J0_1, Kn.P[3], E2, Kn.P[4], Kn.cg[7]);
         vvvv_acc(J0_1_2, E0, E1, E2, Kn.c4[7]);
         cv<R> J0_2_1 = vvv(E0, Kn.P[1], J2_1, Kn.P[6], Kn.cg[7]);
-        addto(J0_2_1, vvv(J0_2, Kn.P[5], E1, Kn.P[2], Kn.cg[7]));
+        vvv_acc(J0_2_1, J0_2, Kn.P[5], E1, Kn.P[2], Kn.cg[7]);
         vvvv_acc(J0_2_1, E0, E2, E1, Kn.c4[7]);
         cv<R> J1_0_2 = vvv(E1, Kn.P[2], J0_2, Kn.P[5], Kn.cg[7]);
-        addto(J1_0_2, vvv(J1_0, Kn.P[3], E2, Kn.P[4], Kn.cg[7]));
+        vvv_acc(J1_0_2, J1_0, Kn.P[3], E2, Kn.P[4], Kn.cg[7]);
         vvvv_acc(J1_0_2, E1, E0, E2, Kn.c4[7]);
         const cv<R> J1_2_0 = J0_2_1;
         const cv<R> J2_0_1 = J1_0_2;
@@ -67,41 +67,41 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
           sp<R> tS_2 = slash(E2, S_E);
           const sp<R> S_2 = fprop(Kn.qc[4], Kn.mc[4], tS_2);
           sp<R> tS_0_1 = slash(E0, S_1);
-          spadd(tS_0_1, slash(J0_1, S_E));
+          slash_acc(tS_0_1, J0_1, S_E);
           const sp<R> S_0_1 = fprop(Kn.qc[3], Kn.mc[3], tS_0_1);
           sp<R> tS_0_2 = slash(E0, S_2);
-          spadd(tS_0_2, slash(J0_2, S_E));
+          slash_acc(tS_0_2, J0_2, S_E);
           const sp<R> S_0_2 = fprop(Kn.qc[5], Kn.mc[5], tS_0_2);
           sp<R> tS_1_0 = slash(E1, S_0);
-          spadd(tS_1_0, slash(J1_0, S_E));
+          slash_acc(tS_1_0, J1_0, S_E);
           const sp<R> S_1_0 = fprop(Kn.qc[3], Kn.mc[3], tS_1_0);
           sp<R> tS_1_2 = slash(E1, S_2);
-          spadd(tS_1_2, slash(J1_2, S_E));
+          slash_acc(tS_1_2, J1_2, S_E);
           const sp<R> S_1_2 = fprop(Kn.qc[6], Kn.mc[6], tS_1_2);
           sp<R> tS_2_0 = slash(E2, S_0);
-          spadd(tS_2_0, slash(J2_0, S_E));
+          slash_acc(tS_2_0, J2_0, S_E);
           const sp<R> S_2_0 = fprop(Kn.qc[5], Kn.mc[5], tS_2_0);
           sp<R> tS_2_1 = slash(E2, S_1);
-          spadd(tS_2_1, slash(J2_1, S_E));
+          slash_acc(tS_2_1, J2_1, S_E);
           const sp<R> S_2_1 = fprop(Kn.qc[6], Kn.mc[6], tS_2_1);
           sp<R> X0 = slash(E0, S_1_2);
-          spadd(X0, slash(J0_1, S_2));
-          spadd(X0, slash(J0_1_2, S_E));
+          slash_acc(X0, J0_1, S_2);
+          slash_acc(X0, J0_1_2, S_E);
           sp<R> X1 = slash(E0, S_2_1);
-          spadd(X1, slash(J0_2, S_1));
-          spadd(X1, slash(J0_2_1, S_E));
+          slash_acc(X1, J0_2, S_1);
+          slash_acc(X1, J0_2_1, S_E);
           sp<R> X2 = slash(E1, S_0_2);
-          spadd(X2, slash(J1_0, S_2));
-          spadd(X2, slash(J1_0_2, S_E));
+          slash_acc(X2, J1_0, S_2);
+          slash_acc(X2, J1_0_2, S_E);
           sp<R> X3 = slash(E1, S_2_0);
-          spadd(X3, slash(J1_2, S_0));
-          spadd(X3, slash(J1_2_0, S_E));
+          slash_acc(X3, J1_2, S_0);
+          slash_acc(X3, J1_2_0, S_E);
           sp<R> X4 = slash(E2, S_0_1);
-          spadd(X4, slash(J2_0, S_1));
-          spadd(X4, slash(J2_0_1, S_E));
+          slash_acc(X4, J2_0, S_1);
+          slash_acc(X4, J2_0_1, S_E);
           sp<R> X5 = slash(E2, S_1_0);
-          spadd(X5, slash(J2_1, S_0));
-          spadd(X5, slash(J2_1_0, S_E));
+          slash_acc(X5, J2_1, S_0);
+          slash_acc(X5, J2_1_0, S_E);
           #pragma unroll 1
           for (int i4 = 0; i4 < (LB >= 4 ? 1 : 2); ++i4) {
             const int h4 = LB >= 4 ? ((lane >> (LB - 4)) & 1) : i4;

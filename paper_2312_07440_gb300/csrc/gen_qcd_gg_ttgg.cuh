@@ -45,13 +45,13 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
         const cv<R> J2_0 = neg(J0_2);
         const cv<R> J2_1 = neg(J1_2);
         cv<R> J0_1_2 = vvv(E0, Kn.P[1], J1_2, Kn.P[6], Kn.cg[7]);
-        addto(J0_1_2, vvv(J0_1, Kn.P[3], E2, Kn.P[4], Kn.cg[7]));
+        vvv_acc(J0_1_2, J0_1, Kn.P[3], E2, Kn.P[4], Kn.cg[7]);
         vvvv_acc(J0_1_2, E0, E1, E2, Kn.c4[7]);
         cv<R> J0_2_1 = vvv(E0, Kn.P[1], J2_1, Kn.P[6], Kn.cg[7]);
-        addto(J0_2_1, vvv(J0_2, Kn.P[5], E1, Kn.P[2], Kn.cg[7]));
+        vvv_acc(J0_2_1, J0_2, Kn.P[5], E1, Kn.P[2], Kn.cg[7]);
         vvvv_acc(J0_2_1, E0, E2, E1, Kn.c4[7]);
         cv<R> J1_0_2 = vvv(E1, Kn.P[2], J0_2, Kn.P[5], Kn.cg[7]);
-        addto(J1_0_2, vvv(J1_0, Kn.P[3], E2, Kn.P[4], Kn.cg[7]));
+        vvv_acc(J1_0_2, J1_0, Kn.P[3], E2, Kn.P[4], Kn.cg[7]);
         vvvv_acc(J1_0_2, E1, E0, E2, Kn.c4[7]);
         const cv<R> J1_2_0 = J0_2_1;
         const cv<R> J2_0_1 = J1_0_2;
@@ -67,32 +67,32 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
           const cv<R> J3_1 = neg(J1_3);
           const cv<R> J3_2 = neg(J2_3);
           cv<R> J0_1_3 = vvv(E0, Kn.P[1], J1_3, Kn.P[10], Kn.cg[11]);
-          addto(J0_1_3, vvv(J0_1, Kn.P[3], E3, Kn.P[8], Kn.cg[11]));
+          vvv_acc(J0_1_3, J0_1, Kn.P[3], E3, Kn.P[8], Kn.cg[11]);
           vvvv_acc(J0_1_3, E0, E1, E3, Kn.c4[11]);
           cv<R> J0_2_3 = vvv(E0, Kn.P[1], J2_3, Kn.P[12], Kn.cg[13]);
-          addto(J0_2_3, vvv(J0_2, Kn.P[5], E3, Kn.P[8], Kn.cg[13]));
+          vvv_acc(J0_2_3, J0_2, Kn.P[5], E3, Kn.P[8], Kn.cg[13]);
           vvvv_acc(J0_2_3, E0, E2, E3, Kn.c4[13]);
           cv<R> J0_3_1 = vvv(E0, Kn.P[1], J3_1, Kn.P[10], Kn.cg[11]);
-          addto(J0_3_1, vvv(J0_3, Kn.P[9], E1, Kn.P[2], Kn.cg[11]));
+          vvv_acc(J0_3_1, J0_3, Kn.P[9], E1, Kn.P[2], Kn.cg[11]);
           vvvv_acc(J0_3_1, E0, E3, E1, Kn.c4[11]);
           cv<R> J0_3_2 = vvv(E0, Kn.P[1], J3_2, Kn.P[12], Kn.cg[13]);
-          addto(J0_3_2, vvv(J0_3, Kn.P[9], E2, Kn.P[4], Kn.cg[13]));
+          vvv_acc(J0_3_2, J0_3, Kn.P[9], E2, Kn.P[4], Kn.cg[13]);
           vvvv_acc(J0_3_2, E0, E3, E2, Kn.c4[13]);
           cv<R> J1_0_3 = vvv(E1, Kn.P[2], J0_3, Kn.P[9], Kn.cg[11]);
-          addto(J1_0_3, vvv(J1_0, Kn.P[3], E3, Kn.P[8], Kn.cg[11]));
+          vvv_acc(J1_0_3, J1_0, Kn.P[3], E3, Kn.P[8], Kn.cg[11]);
           vvvv_acc(J1_0_3, E1, E0, E3, Kn.c4[11]);
           cv<R> J1_2_3 = vvv(E1, Kn.P[2], J2_3, Kn.P[12], Kn.cg[14]);
-          addto(J1_2_3, vvv(J1_2, Kn.P[6], E3, Kn.P[8], Kn.cg[14]));
+          vvv_acc(J1_2_3, J1_2, Kn.P[6], E3, Kn.P[8], Kn.cg[14]);
           vvvv_acc(J1_2_3, E1, E2, E3, Kn.c4[14]);
           const cv<R> J1_3_0 = J0_3_1;
           cv<R> J1_3_2 = vvv(E1, Kn.P[2], J3_2, Kn.P[12], Kn.cg[14]);
-          addto(J1_3_2, vvv(J1_3, Kn.P[10], E2, Kn.P[4], Kn.cg[14]));
+          vvv_acc(J1_3_2, J1_3, Kn.P[10], E2, Kn.P[4], Kn.cg[14]);
           vvvv_acc(J1_3_2, E1, E3, E2, Kn.c4[14]);
           cv<R> J2_0_3 = vvv(E2, Kn.P[4], J0_3, Kn.P[9], Kn.cg[13]);
-          addto(J2_0_3, vvv(J2_0, Kn.P[5], E3, Kn.P[8], Kn.cg[13]));
+          vvv_acc(J2_0_3, J2_0, Kn.P[5], E3, Kn.P[8], Kn.cg[13]);
           vvvv_acc(J2_0_3, E2, E0, E3, Kn.c4[13]);
           cv<R> J2_1_3 = vvv(E2, Kn.P[4], J1_3, Kn.P[10], Kn.cg[14]);
-          addto(J2_1_3, vvv(J2_1, Kn.P[6], E3, Kn.P[8], Kn.cg[14]));
+          vvv_acc(J2_1_3, J2_1, Kn.P[6], E3, Kn.P[8], Kn.cg[14]);
           vvvv_acc(J2_1_3, E2, E1, E3, Kn.c4[14]);
           const cv<R> J2_3_0 = J0_3_2;
           const cv<R> J2_3_1 = J1_3_2;
@@ -103,77 +103,77 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
           const cv<R> J3_2_0 = J0_2_3;
           const cv<R> J3_2_1 = J1_2_3;
           cv<R> J0_1_2_3 = vvv(E0, Kn.P[1], J1_2_3, Kn.P[14], Kn.cg[15]);
-          addto(J0_1_2_3, vvv(J0_1, Kn.P[3], J2_3, Kn.P[12], Kn.cg[15]));
-          addto(J0_1_2_3, vvv(J0_1_2, Kn.P[7], E3, Kn.P[8], Kn.cg[15]));
+          vvv_acc(J0_1_2_3, J0_1, Kn.P[3], J2_3, Kn.P[12], Kn.cg[15]);
+          vvv_acc(J0_1_2_3, J0_1_2, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J0_1_2_3, E0, E1, J2_3, Kn.c4[15]);
           vvvv_acc(J0_1_2_3, E0, J1_2, E3, Kn.c4[15]);
           vvvv_acc(J0_1_2_3, J0_1, E2, E3, Kn.c4[15]);
           cv<R> J0_1_3_2 = vvv(E0, Kn.P[1], J1_3_2, Kn.P[14], Kn.cg[15]);
-          addto(J0_1_3_2, vvv(J0_1, Kn.P[3], J3_2, Kn.P[12], Kn.cg[15]));
-          addto(J0_1_3_2, vvv(J0_1_3, Kn.P[11], E2, Kn.P[4], Kn.cg[15]));
+          vvv_acc(J0_1_3_2, J0_1, Kn.P[3], J3_2, Kn.P[12], Kn.cg[15]);
+          vvv_acc(J0_1_3_2, J0_1_3, Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
           vvvv_acc(J0_1_3_2, E0, E1, J3_2, Kn.c4[15]);
           vvvv_acc(J0_1_3_2, E0, J1_3, E2, Kn.c4[15]);
           vvvv_acc(J0_1_3_2, J0_1, E3, E2, Kn.c4[15]);
           cv<R> J0_2_1_3 = vvv(E0, Kn.P[1], J2_1_3, Kn.P[14], Kn.cg[15]);
-          addto(J0_2_1_3, vvv(J0_2, Kn.P[5], J1_3, Kn.P[10], Kn.cg[15]));
-          addto(J0_2_1_3, vvv(J0_2_1, Kn.P[7], E3, Kn.P[8], Kn.cg[15]));
+          vvv_acc(J0_2_1_3, J0_2, Kn.P[5], J1_3, Kn.P[10], Kn.cg[15]);
+          vvv_acc(J0_2_1_3, J0_2_1, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J0_2_1_3, E0, E2, J1_3, Kn.c4[15]);
           vvvv_acc(J0_2_1_3, E0, J2_1, E3, Kn.c4[15]);
           vvvv_acc(J0_2_1_3, J0_2, E1, E3, Kn.c4[15]);
           cv<R> J0_2_3_1 = vvv(E0, Kn.P[1], J2_3_1, Kn.P[14], Kn.cg[15]);
-          addto(J0_2_3_1, vvv(J0_2, Kn.P[5], J3_1, Kn.P[10], Kn.cg[15]));
-          addto(J0_2_3_1, vvv(J0_2_3, Kn.P[13], E1, Kn.P[2], Kn.cg[15]));
+          vvv_acc(J0_2_3_1, J0_2, Kn.P[5], J3_1, Kn.P[10], Kn.cg[15]);
+          vvv_acc(J0_2_3_1, J0_2_3, Kn.P[13], E1, Kn.P[2], Kn.cg[15]);
           vvvv_acc(J0_2_3_1, E0, E2, J3_1, Kn.c4[15]);
           vvvv_acc(J0_2_3_1, E0, J2_3, E1, Kn.c4[15]);
           vvvv_acc(J0_2_3_1, J0_2, E3, E1, Kn.c4[15]);
           cv<R> J0_3_1_2 = vvv(E0, Kn.P[1], J3_1_2, Kn.P[14], Kn.cg[15]);
-          addto(J0_3_1_2, vvv(J0_3, Kn.P[9], J1_2, Kn.P[6], Kn.cg[15]));
-          addto(J0_3_1_2, vvv(J0_3_1, Kn.P[11], E2, Kn.P[4], Kn.cg[15]));
+          vvv_acc(J0_3_1_2, J0_3, Kn.P[9], J1_2, Kn.P[6], Kn.cg[15]);
+          vvv_acc(J0_3_1_2, J0_3_1, Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
           vvvv_acc(J0_3_1_2, E0, E3, J1_2, Kn.c4[15]);
           vvvv_acc(J0_3_1_2, E0, J3_1, E2, Kn.c4[15]);
           vvvv_acc(J0_3_1_2, J0_3, E1, E2, Kn.c4[15]);
           cv<R> J0_3_2_1 = vvv(E0, Kn.P[1], J3_2_1, Kn.P[14], Kn.cg[15]);
-          addto(J0_3_2_1, vvv(J0_3, Kn.P[9], J2_1, Kn.P[6], Kn.cg[15]));
-          addto(J0_3_2_1, vvv(J0_3_2, Kn.P[13], E1, Kn.P[2], Kn.cg[15]));
+          vvv_acc(J0_3_2_1, J0_3, Kn.P[9], J2_1, Kn.P[6], Kn.cg[15]);
+          vvv_acc(J0_3_2_1, J0_3_2, Kn.P[13], E1, Kn.P[2], Kn.cg[15]);
           vvvv_acc(J0_3_2_1, E0, E3, J2_1, Kn.c4[15]);
           vvvv_acc(J0_3_2_1, E0, J3_2, E1, Kn.c4[15]);
           vvvv_acc(J0_3_2_1, J0_3, E2, E1, Kn.c4[15]);
           cv<R> J1_0_2_3 = vvv(E1, Kn.P[2], J0_2_3, Kn.P[13], Kn.cg[15]);
-          addto(J1_0_2_3, vvv(J1_0, Kn.P[3], J2_3, Kn.P[12], Kn.cg[15]));
-          addto(J1_0_2_3, vvv(J1_0_2, Kn.P[7], E3, Kn.P[8], Kn.cg[15]));
+          vvv_acc(J1_0_2_3, J1_0, Kn.P[3], J2_3, Kn.P[12], Kn.cg[15]);
+          vvv_acc(J1_0_2_3, J1_0_2, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J1_0_2_3, E1, E0, J2_3, Kn.c4[15]);
           vvvv_acc(J1_0_2_3, E1, J0_2, E3, Kn.c4[15]);
           vvvv_acc(J1_0_2_3, J1_0, E2, E3, Kn.c4[15]);
           cv<R> J1_0_3_2 = vvv(E1, Kn.P[2], J0_3_2, Kn.P[13], Kn.cg[15]);
-          addto(J1_0_3_2, vvv(J1_0, Kn.P[3], J3_2, Kn.P[12], Kn.cg[15]));
-          addto(J1_0_3_2, vvv(J1_0_3, Kn.P[11], E2, Kn.P[4], Kn.cg[15]));
+          vvv_acc(J1_0_3_2, J1_0, Kn.P[3], J3_2, Kn.P[12], Kn.cg[15]);
+          vvv_acc(J1_0_3_2, J1_0_3, Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
           vvvv_acc(J1_0_3_2, E1, E0, J3_2, Kn.c4[15]);
           vvvv_acc(J1_0_3_2, E1, J0_3, E2, Kn.c4[15]);
           vvvv_acc(J1_0_3_2, J1_0, E3, E2, Kn.c4[15]);
           cv<R> J1_2_0_3 = vvv(E1, Kn.P[2], J2_0_3, Kn.P[13], Kn.cg[15]);
-          addto(J1_2_0_3, vvv(J1_2, Kn.P[6], J0_3, Kn.P[9], Kn.cg[15]));
-          addto(J1_2_0_3, vvv(J1_2_0, Kn.P[7], E3, Kn.P[8], Kn.cg[15]));
+          vvv_acc(J1_2_0_3, J1_2, Kn.P[6], J0_3, Kn.P[9], Kn.cg[15]);
+          vvv_acc(J1_2_0_3, J1_2_0, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J1_2_0_3, E1, E2, J0_3, Kn.c4[15]);
           vvvv_acc(J1_2_0_3, E1, J2_0, E3, Kn.c4[15]);
           vvvv_acc(J1_2_0_3, J1_2, E0, E3, Kn.c4[15]);
           const cv<R> J1_2_3_0 = neg(J0_3_2_1);
           cv<R> J1_3_0_2 = vvv(E1, Kn.P[2], J3_0_2, Kn.P[13], Kn.cg[15]);
-          addto(J1_3_0_2, vvv(J1_3, Kn.P[10], J0_2, Kn.P[5], Kn.cg[15]));
-          addto(J1_3_0_2, vvv(J1_3_0, Kn.P[11], E2, Kn.P[4], Kn.cg[15]));
+          vvv_acc(J1_3_0_2, J1_3, Kn.P[10], J0_2, Kn.P[5], Kn.cg[15]);
+          vvv_acc(J1_3_0_2, J1_3_0, Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
           vvvv_acc(J1_3_0_2, E1, E3, J0_2, Kn.c4[15]);
           vvvv_acc(J1_3_0_2, E1, J3_0, E2, Kn.c4[15]);
           vvvv_acc(J1_3_0_2, J1_3, E0, E2, Kn.c4[15]);
           const cv<R> J1_3_2_0 = neg(J0_2_3_1);
           cv<R> J2_0_1_3 = vvv(E2, Kn.P[4], J0_1_3, Kn.P[11], Kn.cg[15]);
-          addto(J2_0_1_3, vvv(J2_0, Kn.P[5], J1_3, Kn.P[10], Kn.cg[15]));
-          addto(J2_0_1_3, vvv(J2_0_1, Kn.P[7], E3, Kn.P[8], Kn.cg[15]));
+          vvv_acc(J2_0_1_3, J2_0, Kn.P[5], J1_3, Kn.P[10], Kn.cg[15]);
+          vvv_acc(J2_0_1_3, J2_0_1, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J2_0_1_3, E2, E0, J1_3, Kn.c4[15]);
           vvvv_acc(J2_0_1_3, E2, J0_1, E3, Kn.c4[15]);
           vvvv_acc(J2_0_1_3, J2_0, E1, E3, Kn.c4[15]);
           const cv<R> J2_0_3_1 = neg(J1_3_0_2);
           cv<R> J2_1_0_3 = vvv(E2, Kn.P[4], J1_0_3, Kn.P[11], Kn.cg[15]);
-          addto(J2_1_0_3, vvv(J2_1, Kn.P[6], J0_3, Kn.P[9], Kn.cg[15]));
-          addto(J2_1_0_3, vvv(J2_1_0, Kn.P[7], E3, Kn.P[8], Kn.cg[15]));
+          vvv_acc(J2_1_0_3, J2_1, Kn.P[6], J0_3, Kn.P[9], Kn.cg[15]);
+          vvv_acc(J2_1_0_3, J2_1_0, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J2_1_0_3, E2, E1, J0_3, Kn.c4[15]);
           vvvv_acc(J2_1_0_3, E2, J1_0, E3, Kn.c4[15]);
           vvvv_acc(J2_1_0_3, J2_1, E0, E3, Kn.c4[15]);
@@ -199,233 +199,233 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             sp<R> tS_3 = slash(E3, S_E);
             const sp<R> S_3 = fprop(Kn.qc[8], Kn.mc[8], tS_3);
             sp<R> tS_0_1 = slash(E0, S_1);
-            spadd(tS_0_1, slash(J0_1, S_E));
+            slash_acc(tS_0_1, J0_1, S_E);
             const sp<R> S_0_1 = fprop(Kn.qc[3], Kn.mc[3], tS_0_1);
             sp<R> tS_0_2 = slash(E0, S_2);
-            spadd(tS_0_2, slash(J0_2, S_E));
+            slash_acc(tS_0_2, J0_2, S_E);
             const sp<R> S_0_2 = fprop(Kn.qc[5], Kn.mc[5], tS_0_2);
             sp<R> tS_0_3 = slash(E0, S_3);
-            spadd(tS_0_3, slash(J0_3, S_E));
+            slash_acc(tS_0_3, J0_3, S_E);
             const sp<R> S_0_3 = fprop(Kn.qc[9], Kn.mc[9], tS_0_3);
             sp<R> tS_1_0 = slash(E1, S_0);
-            spadd(tS_1_0, slash(J1_0, S_E));
+            slash_acc(tS_1_0, J1_0, S_E);
             const sp<R> S_1_0 = fprop(Kn.qc[3], Kn.mc[3], tS_1_0);
             sp<R> tS_1_2 = slash(E1, S_2);
-            spadd(tS_1_2, slash(J1_2, S_E));
+            slash_acc(tS_1_2, J1_2, S_E);
             const sp<R> S_1_2 = fprop(Kn.qc[6], Kn.mc[6], tS_1_2);
             sp<R> tS_1_3 = slash(E1, S_3);
-            spadd(tS_1_3, slash(J1_3, S_E));
+            slash_acc(tS_1_3, J1_3, S_E);
             const sp<R> S_1_3 = fprop(Kn.qc[10], Kn.mc[10], tS_1_3);
             sp<R> tS_2_0 = slash(E2, S_0);
-            spadd(tS_2_0, slash(J2_0, S_E));
+            slash_acc(tS_2_0, J2_0, S_E);
             const sp<R> S_2_0 = fprop(Kn.qc[5], Kn.mc[5], tS_2_0);
             sp<R> tS_2_1 = slash(E2, S_1);
-            spadd(tS_2_1, slash(J2_1, S_E));
+            slash_acc(tS_2_1, J2_1, S_E);
             const sp<R> S_2_1 = fprop(Kn.qc[6], Kn.mc[6], tS_2_1);
             sp<R> tS_2_3 = slash(E2, S_3);
-            spadd(tS_2_3, slash(J2_3, S_E));
+            slash_acc(tS_2_3, J2_3, S_E);
             const sp<R> S_2_3 = fprop(Kn.qc[12], Kn.mc[12], tS_2_3);
             sp<R> tS_3_0 = slash(E3, S_0);
-            spadd(tS_3_0, slash(J3_0, S_E));
+            slash_acc(tS_3_0, J3_0, S_E);
             const sp<R> S_3_0 = fprop(Kn.qc[9], Kn.mc[9], tS_3_0);
             sp<R> tS_3_1 = slash(E3, S_1);
-            spadd(tS_3_1, slash(J3_1, S_E));
+            slash_acc(tS_3_1, J3_1, S_E);
             const sp<R> S_3_1 = fprop(Kn.qc[10], Kn.mc[10], tS_3_1);
             sp<R> tS_3_2 = slash(E3, S_2);
-            spadd(tS_3_2, slash(J3_2, S_E));
+            slash_acc(tS_3_2, J3_2, S_E);
             const sp<R> S_3_2 = fprop(Kn.qc[12], Kn.mc[12], tS_3_2);
             sp<R> tS_0_1_2 = slash(E0, S_1_2);
-            spadd(tS_0_1_2, slash(J0_1, S_2));
-            spadd(tS_0_1_2, slash(J0_1_2, S_E));
+            slash_acc(tS_0_1_2, J0_1, S_2);
+            slash_acc(tS_0_1_2, J0_1_2, S_E);
             const sp<R> S_0_1_2 = fprop(Kn.qc[7], Kn.mc[7], tS_0_1_2);
             sp<R> tS_0_1_3 = slash(E0, S_1_3);
-            spadd(tS_0_1_3, slash(J0_1, S_3));
-            spadd(tS_0_1_3, slash(J0_1_3, S_E));
+            slash_acc(tS_0_1_3, J0_1, S_3);
+            slash_acc(tS_0_1_3, J0_1_3, S_E);
             const sp<R> S_0_1_3 = fprop(Kn.qc[11], Kn.mc[11], tS_0_1_3);
             sp<R> tS_0_2_1 = slash(E0, S_2_1);
-            spadd(tS_0_2_1, slash(J0_2, S_1));
-            spadd(tS_0_2_1, slash(J0_2_1, S_E));
+            slash_acc(tS_0_2_1, J0_2, S_1);
+            slash_acc(tS_0_2_1, J0_2_1, S_E);
             const sp<R> S_0_2_1 = fprop(Kn.qc[7], Kn.mc[7], tS_0_2_1);
             sp<R> tS_0_2_3 = slash(E0, S_2_3);
-            spadd(tS_0_2_3, slash(J0_2, S_3));
-            spadd(tS_0_2_3, slash(J0_2_3, S_E));
+            slash_acc(tS_0_2_3, J0_2, S_3);
+            slash_acc(tS_0_2_3, J0_2_3, S_E);
             const sp<R> S_0_2_3 = fprop(Kn.qc[13], Kn.mc[13], tS_0_2_3);
             sp<R> tS_0_3_1 = slash(E0, S_3_1);
-            spadd(tS_0_3_1, slash(J0_3, S_1));
-            spadd(tS_0_3_1, slash(J0_3_1, S_E));
+            slash_acc(tS_0_3_1, J0_3, S_1);
+            slash_acc(tS_0_3_1, J0_3_1, S_E);
             const sp<R> S_0_3_1 = fprop(Kn.qc[11], Kn.mc[11], tS_0_3_1);
             sp<R> tS_0_3_2 = slash(E0, S_3_2);
-            spadd(tS_0_3_2, slash(J0_3, S_2));
-            spadd(tS_0_3_2, slash(J0_3_2, S_E));
+            slash_acc(tS_0_3_2, J0_3, S_2);
+            slash_acc(tS_0_3_2, J0_3_2, S_E);
             const sp<R> S_0_3_2 = fprop(Kn.qc[13], Kn.mc[13], tS_0_3_2);
             sp<R> tS_1_0_2 = slash(E1, S_0_2);
-            spadd(tS_1_0_2, slash(J1_0, S_2));
-            spadd(tS_1_0_2, slash(J1_0_2, S_E));
+            slash_acc(tS_1_0_2, J1_0, S_2);
+            slash_acc(tS_1_0_2, J1_0_2, S_E);
             const sp<R> S_1_0_2 = fprop(Kn.qc[7], Kn.mc[7], tS_1_0_2);
             sp<R> tS_1_0_3 = slash(E1, S_0_3);
-            spadd(tS_1_0_3, slash(J1_0, S_3));
-            spadd(tS_1_0_3, slash(J1_0_3, S_E));
+            slash_acc(tS_1_0_3, J1_0, S_3);
+            slash_acc(tS_1_0_3, J1_0_3, S_E);
             const sp<R> S_1_0_3 = fprop(Kn.qc[11], Kn.mc[11], tS_1_0_3);
             sp<R> tS_1_2_0 = slash(E1, S_2_0);
-            spadd(tS_1_2_0, slash(J1_2, S_0));
-            spadd(tS_1_2_0, slash(J1_2_0, S_E));
+            slash_acc(tS_1_2_0, J1_2, S_0);
+            slash_acc(tS_1_2_0, J1_2_0, S_E);
             const sp<R> S_1_2_0 = fprop(Kn.qc[7], Kn.mc[7], tS_1_2_0);
             sp<R> tS_1_2_3 = slash(E1, S_2_3);
-            spadd(tS_1_2_3, slash(J1_2, S_3));
-            spadd(tS_1_2_3, slash(J1_2_3, S_E));
+            slash_acc(tS_1_2_3, J1_2, S_3);
+            slash_acc(tS_1_2_3, J1_2_3, S_E);
             const sp<R> S_1_2_3 = fprop(Kn.qc[14], Kn.mc[14], tS_1_2_3);
             sp<R> tS_1_3_0 = slash(E1, S_3_0);
-            spadd(tS_1_3_0, slash(J1_3, S_0));
-            spadd(tS_1_3_0, slash(J1_3_0, S_E));
+            slash_acc(tS_1_3_0, J1_3, S_0);
+            slash_acc(tS_1_3_0, J1_3_0, S_E);
             const sp<R> S_1_3_0 = fprop(Kn.qc[11], Kn.mc[11], tS_1_3_0);
             sp<R> tS_1_3_2 = slash(E1, S_3_2);
-            spadd(tS_1_3_2, slash(J1_3, S_2));
-            spadd(tS_1_3_2, slash(J1_3_2, S_E));
+            slash_acc(tS_1_3_2, J1_3, S_2);
+            slash_acc(tS_1_3_2, J1_3_2, S_E);
             const sp<R> S_1_3_2 = fprop(Kn.qc[14], Kn.mc[14], tS_1_3_2);
             sp<R> tS_2_0_1 = slash(E2, S_0_1);
-            spadd(tS_2_0_1, slash(J2_0, S_1));
-            spadd(tS_2_0_1, slash(J2_0_1, S_E));
+            slash_acc(tS_2_0_1, J2_0, S_1);
+            slash_acc(tS_2_0_1, J2_0_1, S_E);
             const sp<R> S_2_0_1 = fprop(Kn.qc[7], Kn.mc[7], tS_2_0_1);
             sp<R> tS_2_0_3 = slash(E2, S_0_3);
-            spadd(tS_2_0_3, slash(J2_0, S_3));
-            spadd(tS_2_0_3, slash(J2_0_3, S_E));
+            slash_acc(tS_2_0_3, J2_0, S_3);
+            slash_acc(tS_2_0_3, J2_0_3, S_E);
             const sp<R> S_2_0_3 = fprop(Kn.qc[13], Kn.mc[13], tS_2_0_3);
             sp<R> tS_2_1_0 = slash(E2, S_1_0);
-            spadd(tS_2_1_0, slash(J2_1, S_0));
-            spadd(tS_2_1_0, slash(J2_1_0, S_E));
+            slash_acc(tS_2_1_0, J2_1, S_0);
+            slash_acc(tS_2_1_0, J2_1_0, S_E);
             const sp<R> S_2_1_0 = fprop(Kn.qc[7], Kn.mc[7], tS_2_1_0);
             sp<R> tS_2_1_3 = slash(E2, S_1_3);
-            spadd(tS_2_1_3, slash(J2_1, S_3));
-            spadd(tS_2_1_3, slash(J2_1_3, S_E));
+            slash_acc(tS_2_1_3, J2_1, S_3);
+            slash_acc(tS_2_1_3, J2_1_3, S_E);
             const sp<R> S_2_1_3 = fprop(Kn.qc[14], Kn.mc[14], tS_2_1_3);
             sp<R> tS_2_3_0 = slash(E2, S_3_0);
-            spadd(tS_2_3_0, slash(J2_3, S_0));
-            spadd(tS_2_3_0, slash(J2_3_0, S_E));
+            slash_acc(tS_2_3_0, J2_3, S_0);
+            slash_acc(tS_2_3_0, J2_3_0, S_E);
             const sp<R> S_2_3_0 = fprop(Kn.qc[13], Kn.mc[13], tS_2_3_0);
             sp<R> tS_2_3_1 = slash(E2, S_3_1);
-            spadd(tS_2_3_1, slash(J2_3, S_1));
-            spadd(tS_2_3_1, slash(J2_3_1, S_E));
+            slash_acc(tS_2_3_1, J2_3, S_1);
+            slash_acc(tS_2_3_1, J2_3_1, S_E);
             const sp<R> S_2_3_1 = fprop(Kn.qc[14], Kn.mc[14], tS_2_3_1);
             sp<R> tS_3_0_1 = slash(E3, S_0_1);
-            spadd(tS_3_0_1, slash(J3_0, S_1));
-            spadd(tS_3_0_1, slash(J3_0_1, S_E));
+            slash_acc(tS_3_0_1, J3_0, S_1);
+            slash_acc(tS_3_0_1, J3_0_1, S_E);
             const sp<R> S_3_0_1 = fprop(Kn.qc[11], Kn.mc[11], tS_3_0_1);
             sp<R> tS_3_0_2 = slash(E3, S_0_2);
-            spadd(tS_3_0_2, slash(J3_0, S_2));
-            spadd(tS_3_0_2, slash(J3_0_2, S_E));
+            slash_acc(tS_3_0_2, J3_0, S_2);
+            slash_acc(tS_3_0_2, J3_0_2, S_E);
             const sp<R> S_3_0_2 = fprop(Kn.qc[13], Kn.mc[13], tS_3_0_2);
             sp<R> tS_3_1_0 = slash(E3, S_1_0);
-            spadd(tS_3_1_0, slash(J3_1, S_0));
-            spadd(tS_3_1_0, slash(J3_1_0, S_E));
+            slash_acc(tS_3_1_0, J3_1, S_0);
+            slash_acc(tS_3_1_0, J3_1_0, S_E);
             const sp<R> S_3_1_0 = fprop(Kn.qc[11], Kn.mc[11], tS_3_1_0);
             sp<R> tS_3_1_2 = slash(E3, S_1_2);
-            spadd(tS_3_1_2, slash(J3_1, S_2));
-            spadd(tS_3_1_2, slash(J3_1_2, S_E));
+            slash_acc(tS_3_1_2, J3_1, S_2);
+            slash_acc(tS_3_1_2, J3_1_2, S_E);
             const sp<R> S_3_1_2 = fprop(Kn.qc[14], Kn.mc[14], tS_3_1_2);
             sp<R> tS_3_2_0 = slash(E3, S_2_0);
-            spadd(tS_3_2_0, slash(J3_2, S_0));
-            spadd(tS_3_2_0, slash(J3_2_0, S_E));
+            slash_acc(tS_3_2_0, J3_2, S_0);
+            slash_acc(tS_3_2_0, J3_2_0, S_E);
             const sp<R> S_3_2_0 = fprop(Kn.qc[13], Kn.mc[13], tS_3_2_0);
             sp<R> tS_3_2_1 = slash(E3, S_2_1);
-            spadd(tS_3_2_1, slash(J3_2, S_1));
-            spadd(tS_3_2_1, slash(J3_2_1, S_E));
+            slash_acc(tS_3_2_1, J3_2, S_1);
+            slash_acc(tS_3_2_1, J3_2_1, S_E);
             const sp<R> S_3_2_1 = fprop(Kn.qc[14], Kn.mc[14], tS_3_2_1);
             sp<R> X0 = slash(E0, S_1_2_3);
-            spadd(X0, slash(J0_1, S_2_3));
-            spadd(X0, slash(J0_1_2, S_3));
-            spadd(X0, slash(J0_1_2_3, S_E));
+            slash_acc(X0, J0_1, S_2_3);
+            slash_acc(X0, J0_1_2, S_3);
+            slash_acc(X0, J0_1_2_3, S_E);
             sp<R> X1 = slash(E0, S_1_3_2);
-            spadd(X1, slash(J0_1, S_3_2));
-            spadd(X1, slash(J0_1_3, S_2));
-            spadd(X1, slash(J0_1_3_2, S_E));
+            slash_acc(X1, J0_1, S_3_2);
+            slash_acc(X1, J0_1_3, S_2);
+            slash_acc(X1, J0_1_3_2, S_E);
             sp<R> X2 = slash(E0, S_2_1_3);
-            spadd(X2, slash(J0_2, S_1_3));
-            spadd(X2, slash(J0_2_1, S_3));
-            spadd(X2, slash(J0_2_1_3, S_E));
+            slash_acc(X2, J0_2, S_1_3);
+            slash_acc(X2, J0_2_1, S_3);
+            slash_acc(X2, J0_2_1_3, S_E);
             sp<R> X3 = slash(E0, S_2_3_1);
-            spadd(X3, slash(J0_2, S_3_1));
-            spadd(X3, slash(J0_2_3, S_1));
-            spadd(X3, slash(J0_2_3_1, S_E));
+            slash_acc(X3, J0_2, S_3_1);
+            slash_acc(X3, J0_2_3, S_1);
+            slash_acc(X3, J0_2_3_1, S_E);
             sp<R> X4 = slash(E0, S_3_1_2);
-            spadd(X4, slash(J0_3, S_1_2));
-            spadd(X4, slash(J0_3_1, S_2));
-            spadd(X4, slash(J0_3_1_2, S_E));
+            slash_acc(X4, J0_3, S_1_2);
+            slash_acc(X4, J0_3_1, S_2);
+            slash_acc(X4, J0_3_1_2, S_E);
             sp<R> X5 = slash(E0, S_3_2_1);
-            spadd(X5, slash(J0_3, S_2_1));
-            spadd(X5, slash(J0_3_2, S_1));
-            spadd(X5, slash(J0_3_2_1, S_E));
+            slash_acc(X5, J0_3, S_2_1);
+            slash_acc(X5, J0_3_2, S_1);
+            slash_acc(X5, J0_3_2_1, S_E);
             sp<R> X6 = slash(E1, S_0_2_3);
-            spadd(X6, slash(J1_0, S_2_3));
-            spadd(X6, slash(J1_0_2, S_3));
-            spadd(X6, slash(J1_0_2_3, S_E));
+            slash_acc(X6, J1_0, S_2_3);
+            slash_acc(X6, J1_0_2, S_3);
+            slash_acc(X6, J1_0_2_3, S_E);
             sp<R> X7 = slash(E1, S_0_3_2);
-            spadd(X7, slash(J1_0, S_3_2));
-            spadd(X7, slash(J1_0_3, S_2));
-            spadd(X7, slash(J1_0_3_2, S_E));
+            slash_acc(X7, J1_0, S_3_2);
+            slash_acc(X7, J1_0_3, S_2);
+            slash_acc(X7, J1_0_3_2, S_E);
             sp<R> X8 = slash(E1, S_2_0_3);
-            spadd(X8, slash(J1_2, S_0_3));
-            spadd(X8, slash(J1_2_0, S_3));
-            spadd(X8, slash(J1_2_0_3, S_E));
+            slash_acc(X8, J1_2, S_0_3);
+            slash_acc(X8, J1_2_0, S_3);
+            slash_acc(X8, J1_2_0_3, S_E);
             sp<R> X9 = slash(E1, S_2_3_0);
-            spadd(X9, slash(J1_2, S_3_0));
-            spadd(X9, slash(J1_2_3, S_0));
-            spadd(X9, slash(J1_2_3_0, S_E));
+            slash_acc(X9, J1_2, S_3_0);
+            slash_acc(X9, J1_2_3, S_0);
+            slash_acc(X9, J1_2_3_0, S_E);
             sp<R> X10 = slash(E1, S_3_0_2);
-            spadd(X10, slash(J1_3, S_0_2));
-            spadd(X10, slash(J1_3_0, S_2));
-            spadd(X10, slash(J1_3_0_2, S_E));
+            slash_acc(X10, J1_3, S_0_2);
+            slash_acc(X10, J1_3_0, S_2);
+            slash_acc(X10, J1_3_0_2, S_E);
             sp<R> X11 = slash(E1, S_3_2_0);
-            spadd(X11, slash(J1_3, S_2_0));
-            spadd(X11, slash(J1_3_2, S_0));
-            spadd(X11, slash(J1_3_2_0, S_E));
+            slash_acc(X11, J1_3, S_2_0);
+            slash_acc(X11, J1_3_2, S_0);
+            slash_acc(X11, J1_3_2_0, S_E);
             sp<R> X12 = slash(E2, S_0_1_3);
-            spadd(X12, slash(J2_0, S_1_3));
-            spadd(X12, slash(J2_0_1, S_3));
-            spadd(X12, slash(J2_0_1_3, S_E));
+            slash_acc(X12, J2_0, S_1_3);
+            slash_acc(X12, J2_0_1, S_3);
+            slash_acc(X12, J2_0_1_3, S_E);
             sp<R> X13 = slash(E2, S_0_3_1);
-            spadd(X13, slash(J2_0, S_3_1));
-            spadd(X13, slash(J2_0_3, S_1));
-            spadd(X13, slash(J2_0_3_1, S_E));
+            slash_acc(X13, J2_0, S_3_1);
+            slash_acc(X13, J2_0_3, S_1);
+            slash_acc(X13, J2_0_3_1, S_E);
             sp<R> X14 = slash(E2, S_1_0_3);
-            spadd(X14, slash(J2_1, S_0_3));
-            spadd(X14, slash(J2_1_0, S_3));
-            spadd(X14, slash(J2_1_0_3, S_E));
+            slash_acc(X14, J2_1, S_0_3);
+            slash_acc(X14, J2_1_0, S_3);
+            slash_acc(X14, J2_1_0_3, S_E);
             sp<R> X15 = slash(E2, S_1_3_0);
-            spadd(X15, slash(J2_1, S_3_0));
-            spadd(X15, slash(J2_1_3, S_0));
-            spadd(X15, slash(J2_1_3_0, S_E));
+            slash_acc(X15, J2_1, S_3_0);
+            slash_acc(X15, J2_1_3, S_0);
+            slash_acc(X15, J2_1_3_0, S_E);
             sp<R> X16 = slash(E2, S_3_0_1);
-            spadd(X16, slash(J2_3, S_0_1));
-            spadd(X16, slash(J2_3_0, S_1));
-            spadd(X16, slash(J2_3_0_1, S_E));
+            slash_acc(X16, J2_3, S_0_1);
+            slash_acc(X16, J2_3_0, S_1);
+            slash_acc(X16, J2_3_0_1, S_E);
             sp<R> X17 = slash(E2, S_3_1_0);
-            spadd(X17, slash(J2_3, S_1_0));
-            spadd(X17, slash(J2_3_1, S_0));
-            spadd(X17, slash(J2_3_1_0, S_E));
+            slash_acc(X17, J2_3, S_1_0);
+            slash_acc(X17, J2_3_1, S_0);
+            slash_acc(X17, J2_3_1_0, S_E);
             sp<R> X18 = slash(E3, S_0_1_2);
-            spadd(X18, slash(J3_0, S_1_2));
-            spadd(X18, slash(J3_0_1, S_2));
-            spadd(X18, slash(J3_0_1_2, S_E));
+            slash_acc(X18, J3_0, S_1_2);
+            slash_acc(X18, J3_0_1, S_2);
+            slash_acc(X18, J3_0_1_2, S_E);
             sp<R> X19 = slash(E3, S_0_2_1);
-            spadd(X19, slash(J3_0, S_2_1));
-            spadd(X19, slash(J3_0_2, S_1));
-            spadd(X19, slash(J3_0_2_1, S_E));
+            slash_acc(X19, J3_0, S_2_1);
+            slash_acc(X19, J3_0_2, S_1);
+            slash_acc(X19, J3_0_2_1, S_E);
             sp<R> X20 = slash(E3, S_1_0_2);
-            spadd(X20, slash(J3_1, S_0_2));
-            spadd(X20, slash(J3_1_0, S_2));
-            spadd(X20, slash(J3_1_0_2, S_E));
+            slash_acc(X20, J3_1, S_0_2);
+            slash_acc(X20, J3_1_0, S_2);
+            slash_acc(X20, J3_1_0_2, S_E);
             sp<R> X21 = slash(E3, S_1_2_0);
-            spadd(X21, slash(J3_1, S_2_0));
-            spadd(X21, slash(J3_1_2, S_0));
-            spadd(X21, slash(J3_1_2_0, S_E));
+            slash_acc(X21, J3_1, S_2_0);
+            slash_acc(X21, J3_1_2, S_0);
+            slash_acc(X21, J3_1_2_0, S_E);
             sp<R> X22 = slash(E3, S_2_0_1);
-            spadd(X22, slash(J3_2, S_0_1));
-            spadd(X22, slash(J3_2_0, S_1));
-            spadd(X22, slash(J3_2_0_1, S_E));
+            slash_acc(X22, J3_2, S_0_1);
+            slash_acc(X22, J3_2_0, S_1);
+            slash_acc(X22, J3_2_0_1, S_E);
             sp<R> X23 = slash(E3, S_2_1_0);
-            spadd(X23, slash(J3_2, S_1_0));
-            spadd(X23, slash(J3_2_1, S_0));
-            spadd(X23, slash(J3_2_1_0, S_E));
+            slash_acc(X23, J3_2, S_1_0);
+            slash_acc(X23, J3_2_1, S_0);
+            slash_acc(X23, J3_2_1_0, S_E);
             #pragma unroll 1
             for (int i5 = 0; i5 < (LB >= 5 ? 1 : 2); ++i5) {
               const int h5 = LB >= 5 ? ((lane >> (LB - 5)) & 1) : i5;

@@ -45,16 +45,57 @@ __device__ __forceinline__ cx<R> conjg(cx<R> a) { return {a.r, -a.i}; }
 template <class R>
 __device__ __forceinline__ cx<R> times_i(cx<R> a) { return {-a.i, a.r}; }
 
+// ---------------------------------------------------------------------------
+// Fused arithmetic.  Every product-sum below is written as a chain of fused
+// multiply-adds into its accumulator (a*b + c with one rounding), so a
+// complex product costs 2 MUL + 2 FMA and each further product accumulated
+// into a sum 4 FMA, with no separate additions.  On GB300's FP64 pipe every
+// instruction counts; the flop counts quoted are those of the formulas
+// (an FMA is 2 flops), unchanged by the fusion.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R fmadd(R a, R b, R c);
+template <>
+__device__ __forceinline__ double fmadd<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <>
+__device__ __forceinline__ float fmadd<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// a*b
+template <class R>
+__device__ __forceinline__ cx<R> cmul(cx<R> a, cx<R> b) {
+  return {fmadd(a.r, b.r, -(a.i * b.i)), fmadd(a.r, b.i, a.i * b.r)};
+}
+// acc + a*b
+template <class R>
+__device__ __forceinline__ cx<R> cmac(cx<R> a, cx<R> b, cx<R> acc) {
+  return {fmadd(a.r, b.r, fmadd(-a.i, b.i, acc.r)), fmadd(a.r, b.i, fmadd(a.i, b.r, acc.i))};
+}
+// acc - a*b
+template <class R>
+__device__ __forceinline__ cx<R> cmsc(cx<R> a, cx<R> b, cx<R> acc) {
+  return {fmadd(-a.r, b.r, fmadd(a.i, b.i, acc.r)), fmadd(-a.r, b.i, fmadd(-a.i, b.r, acc.i))};
+}
+// acc + s*a, s real
+template <class R>
+__device__ __forceinline__ cx<R> rmac(R s, cx<R> a, cx<R> acc) {
+  return {fmadd(s, a.r, acc.r), fmadd(s, a.i, acc.i)};
+}
+
 // a.b (Minkowski, no conjugation): 30 flops
 template <class R>
 __device__ __forceinline__ cx<R> dot(const cv<R>& a, const cv<R>& b) {
-  return a.c[0] * b.c[0] - a.c[1] * b.c[1] - a.c[2] * b.c[2] - a.c[3] * b.c[3];
+  cx<R> s = cmul(a.c[0], b.c[0]);
+  s = cmsc(a.c[1], b.c[1], s);
+  s = cmsc(a.c[2], b.c[2], s);
+  return cmsc(a.c[3], b.c[3], s);
 }
 // p.a with a real vector p: 14 flops
 template <class R>
 __device__ __forceinline__ cx<R> dotr(const R (&p)[4], const cv<R>& a) {
-  return {p[0] * a.c[0].r - p[1] * a.c[1].r - p[2] * a.c[2].r - p[3] * a.c[3].r,
-          p[0] * a.c[0].i - p[1] * a.c[1].i - p[2] * a.c[2].i - p[3] * a.c[3].i};
+  cx<R> s = {p[0] * a.c[0].r, p[0] * a.c[0].i};
+  s = rmac(-p[1], a.c[1], s);
+  s = rmac(-p[2], a.c[2], s);
+  return rmac(-p[3], a.c[3], s);
 }
 template <class R>
 __device__ __forceinline__ cv<R> neg(const cv<R>& a) {
@@ -74,22 +115,37 @@ __device__ __forceinline__ void spadd(sp<R>& a, const sp<R>& b) {
 // Colour-ordered 3-gluon vertex and the off-shell gluon propagator,
 // c = -1/K^2 (Feynman gauge, g stripped), K = P1 + P2:
 //   out = c [ -J1 (2P1+P2).J2 + (J1.J2)(P1-P2) + J2 (2P2+P1).J1 ]     (156 flops)
-template <class R>
-__device__ __forceinline__ cv<R> vvv(const cv<R>& J1, const R (&P1)[4], const cv<R>& J2, const R (&P2)[4], R c) {
+// vvv returns it, vvv_acc adds it to o (+8 flops).
+template <class R, bool ACC>
+__device__ __forceinline__ void vvv_impl(cv<R>& o, const cv<R>& J1, const R (&P1)[4], const cv<R>& J2,
+                                         const R (&P2)[4], R c) {
   R a[4], b[4], d[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    a[m] = R(2) * P1[m] + P2[m];
-    b[m] = R(2) * P2[m] + P1[m];
+    a[m] = fmadd(R(2), P1[m], P2[m]);
+    b[m] = fmadd(R(2), P2[m], P1[m]);
     d[m] = P1[m] - P2[m];
   }
   const cx<R> s1 = c * dotr(a, J2);
   const cx<R> s2 = c * dotr(b, J1);
   const cx<R> s12 = c * dot(J1, J2);
-  cv<R> o;
 #pragma unroll
-  for (int m = 0; m < 4; ++m) o.c[m] = J2.c[m] * s2 - J1.c[m] * s1 + d[m] * s12;
+  for (int m = 0; m < 4; ++m) {
+    cx<R> t = ACC ? rmac(d[m], s12, o.c[m]) : cx<R>{d[m] * s12.r, d[m] * s12.i};
+    t = cmac(J2.c[m], s2, t);
+    o.c[m] = cmsc(J1.c[m], s1, t);
+  }
+}
+template <class R>
+__device__ __forceinline__ cv<R> vvv(const cv<R>& J1, const R (&P1)[4], const cv<R>& J2, const R (&P2)[4], R c) {
+  cv<R> o;
+  vvv_impl<R, false>(o, J1, P1, J2, P2, c);
   return o;
+}
+template <class R>
+__device__ __forceinline__ void vvv_acc(cv<R>& o, const cv<R>& J1, const R (&P1)[4], const cv<R>& J2,
+                                        const R (&P2)[4], R c) {
+  vvv_impl<R, true>(o, J1, P1, J2, P2, c);
 }
 
 // Colour-ordered 4-gluon vertex with the propagator c = +1/K^2:
@@ -100,34 +156,47 @@ __device__ __forceinline__ void vvvv_acc(cv<R>& o, const cv<R>& J1, const cv<R>&
   const cx<R> t23 = c * dot(J2, J3);
   const cx<R> t12 = c * dot(J1, J2);
 #pragma unroll
-  for (int m = 0; m < 4; ++m) o.c[m] = o.c[m] + J2.c[m] * t13 - J1.c[m] * t23 - J3.c[m] * t12;
+  for (int m = 0; m < 4; ++m) o.c[m] = cmsc(J3.c[m], t12, cmsc(J1.c[m], t23, cmac(J2.c[m], t13, o.c[m])));
 }
 
 // Jslash psi = gamma^mu J_mu psi                                          (64 flops)
-template <class R>
-__device__ __forceinline__ sp<R> slash(const cv<R>& a, const sp<R>& s) {
+// slash returns it, slash_acc adds it to o (+8 flops).
+template <class R, bool ACC>
+__device__ __forceinline__ void slash_impl(sp<R>& o, const cv<R>& a, const sp<R>& s) {
   const cx<R> ap = a.c[0] + a.c[3], am = a.c[0] - a.c[3];
   const cx<R> bp = {a.c[1].r - a.c[2].i, a.c[1].i + a.c[2].r};  // a1 + i a2
   const cx<R> bm = {a.c[1].r + a.c[2].i, a.c[1].i - a.c[2].r};  // a1 - i a2
+  o.c[0] = cmsc(bm, s.c[3], ACC ? cmac(am, s.c[2], o.c[0]) : cmul(am, s.c[2]));
+  o.c[1] = cmsc(bp, s.c[2], ACC ? cmac(ap, s.c[3], o.c[1]) : cmul(ap, s.c[3]));
+  o.c[2] = cmac(bm, s.c[1], ACC ? cmac(ap, s.c[0], o.c[2]) : cmul(ap, s.c[0]));
+  o.c[3] = cmac(am, s.c[1], ACC ? cmac(bp, s.c[0], o.c[3]) : cmul(bp, s.c[0]));
+}
+template <class R>
+__device__ __forceinline__ sp<R> slash(const cv<R>& a, const sp<R>& s) {
   sp<R> o;
-  o.c[0] = am * s.c[2] - bm * s.c[3];
-  o.c[1] = ap * s.c[3] - bp * s.c[2];
-  o.c[2] = ap * s.c[0] + bm * s.c[1];
-  o.c[3] = bp * s.c[0] + am * s.c[1];
+  slash_impl<R, false>(o, a, s);
   return o;
+}
+template <class R>
+__device__ __forceinline__ void slash_acc(sp<R>& o, const cv<R>& a, const sp<R>& s) {
+  slash_impl<R, true>(o, a, s);
 }
 
 // Top propagator applied to a spinor, with the factor folded in:
 //   (qc slash + mc) chi,  qc = c q, mc = c m,  c = -1/(q^2 - m^2)         (58 flops)
+// Each real component is one chain: am s2 - (q1 - i q2) s3 + mc s0, etc.
 template <class R>
 __device__ __forceinline__ sp<R> fprop(const R (&q)[4], R mc, const sp<R>& s) {
-  const R ap = q[0] + q[3], am = q[0] - q[3];
+  const R ap = q[0] + q[3], am = q[0] - q[3], q1 = q[1], q2 = q[2];
   sp<R> o;
-  // (q1 - i q2) s3  and  (q1 + i q2) s2 etc.
-  o.c[0] = am * s.c[2] - cx<R>{q[1] * s.c[3].r + q[2] * s.c[3].i, q[1] * s.c[3].i - q[2] * s.c[3].r} + mc * s.c[0];
-  o.c[1] = ap * s.c[3] - cx<R>{q[1] * s.c[2].r - q[2] * s.c[2].i, q[1] * s.c[2].i + q[2] * s.c[2].r} + mc * s.c[1];
-  o.c[2] = ap * s.c[0] + cx<R>{q[1] * s.c[1].r + q[2] * s.c[1].i, q[1] * s.c[1].i - q[2] * s.c[1].r} + mc * s.c[2];
-  o.c[3] = am * s.c[1] + cx<R>{q[1] * s.c[0].r - q[2] * s.c[0].i, q[1] * s.c[0].i + q[2] * s.c[0].r} + mc * s.c[3];
+  o.c[0] = {fmadd(mc, s.c[0].r, fmadd(-q2, s.c[3].i, fmadd(-q1, s.c[3].r, am * s.c[2].r))),
+            fmadd(mc, s.c[0].i, fmadd(q2, s.c[3].r, fmadd(-q1, s.c[3].i, am * s.c[2].i)))};
+  o.c[1] = {fmadd(mc, s.c[1].r, fmadd(q2, s.c[2].i, fmadd(-q1, s.c[2].r, ap * s.c[3].r))),
+            fmadd(mc, s.c[1].i, fmadd(-q2, s.c[2].r, fmadd(-q1, s.c[2].i, ap * s.c[3].i)))};
+  o.c[2] = {fmadd(mc, s.c[2].r, fmadd(q2, s.c[1].i, fmadd(q1, s.c[1].r, ap * s.c[0].r))),
+            fmadd(mc, s.c[2].i, fmadd(-q2, s.c[1].r, fmadd(q1, s.c[1].i, ap * s.c[0].i)))};
+  o.c[3] = {fmadd(mc, s.c[3].r, fmadd(-q2, s.c[0].i, fmadd(q1, s.c[0].r, am * s.c[1].r))),
+            fmadd(mc, s.c[3].i, fmadd(q2, s.c[0].r, fmadd(q1, s.c[0].i, am * s.c[1].i)))};
   return o;
 }
 
@@ -148,7 +217,7 @@ __device__ __forceinline__ cv<R> fcur(const sp<R>& u, const sp<R>& s) {
 // ubar . X: a row spinor times a column spinor                           (30 flops)
 template <class R>
 __device__ __forceinline__ cx<R> rowcol(const sp<R>& u, const sp<R>& x) {
-  return u.c[0] * x.c[0] + u.c[1] * x.c[1] + u.c[2] * x.c[2] + u.c[3] * x.c[3];
+  return cmac(u.c[3], x.c[3], cmac(u.c[2], x.c[2], cmac(u.c[1], x.c[1], cmul(u.c[0], x.c[0]))));
 }
 
 // ---------------------------------------------------------------------------

@@ -32,16 +32,16 @@ __device__ __forceinline__ ws<R> weyl_form(const cv<R>& a) {
           {a.c[1].r + a.c[2].i, a.c[1].i - a.c[2].r}};
 }
 
-template <class R>
-__device__ __forceinline__ void addto(w2<R>& a, const w2<R>& b) {
-  a.c[0] = a.c[0] + b.c[0];
-  a.c[1] = a.c[1] + b.c[1];
-}
-
 // eps-slash on a right-handed spinor -> left-handed                        (28 flops)
 template <class R>
 __device__ __forceinline__ w2<R> sl_RL(const ws<R>& a, const w2<R>& s) {
-  return {{a.am * s.c[0] - a.bm * s.c[1], a.ap * s.c[1] - a.bp * s.c[0]}};
+  return {{cmsc(a.bm, s.c[1], cmul(a.am, s.c[0])), cmsc(a.bp, s.c[0], cmul(a.ap, s.c[1]))}};
+}
+// o += eps-slash s, fused                                                  (+4 flops)
+template <class R>
+__device__ __forceinline__ void sl_RL_acc(w2<R>& o, const ws<R>& a, const w2<R>& s) {
+  o.c[0] = cmsc(a.bm, s.c[1], cmac(a.am, s.c[0], o.c[0]));
+  o.c[1] = cmsc(a.bp, s.c[0], cmac(a.ap, s.c[1], o.c[1]));
 }
 
 // massless propagator qslash/q^2 on a left-handed spinor -> right-handed;
@@ -49,14 +49,14 @@ __device__ __forceinline__ w2<R> sl_RL(const ws<R>& a, const w2<R>& s) {
 template <class R>
 __device__ __forceinline__ w2<R> pr_LR(const R (&q)[4], const w2<R>& s) {
   const cx<R> s0 = s.c[0], s1 = s.c[1];
-  return {{{q[0] * s0.r + q[2] * s1.r + q[3] * s1.i, q[0] * s0.i + q[2] * s1.i - q[3] * s1.r},
-           {q[2] * s0.r - q[3] * s0.i + q[1] * s1.r, q[2] * s0.i + q[3] * s0.r + q[1] * s1.i}}};
+  return {{{fmadd(q[3], s1.i, fmadd(q[2], s1.r, q[0] * s0.r)), fmadd(-q[3], s1.r, fmadd(q[2], s1.i, q[0] * s0.i))},
+           {fmadd(q[1], s1.r, fmadd(-q[3], s0.i, q[2] * s0.r)), fmadd(q[1], s1.i, fmadd(q[3], s0.r, q[2] * s0.i))}}};
 }
 
 // vbar (left-handed slot, a row) . psi                                     (14 flops)
 template <class R>
 __device__ __forceinline__ cx<R> close_L(const w2<R>& vb, const w2<R>& s) {
-  return vb.c[0] * s.c[0] + vb.c[1] * s.c[1];
+  return cmac(vb.c[1], s.c[1], cmul(vb.c[0], s.c[0]));
 }
 
 template <class R, int NA>

@@ -316,6 +316,16 @@ def param_vector(**overrides):
     return np.array([d[f] for f in PARAM_FIELDS], dtype=np.float64)
 
 
+def coupling_points(n: int):
+    """n points with a random electroweak coupling each, alpha' = alpha (0.5 + u),
+    u ~ U[0, 1) from the e- e+ -> 5 photons sample's Philox stream 2 (point i
+    is the same for every n)."""
+    wl = WORKLOADS["ee_5a_1m"]
+    u = _uniforms(wl.seed, np.arange(n, dtype=np.uint64), 0, 1, stream=2)[0]
+    inv0 = SM_PARAMS["alpha_em_inv"]
+    return np.stack([param_vector(alpha_em_inv=inv0 / (0.5 + x)) for x in u])
+
+
 def reweight_points(workload_name: str, variant: str = "default"):
     """Modified parameter points of each sample, float64[P][8].
 
@@ -334,10 +344,7 @@ def reweight_points(workload_name: str, variant: str = "default"):
     if workload_name == "gg_tt_1m":
         return param_vector(m_t=175.0, alpha_s=0.120)[None]
     if workload_name == "ee_5a_1m":
-        wl = WORKLOADS[workload_name]
-        u = _uniforms(wl.seed, np.arange(8, dtype=np.uint64), 0, 1, stream=2)[0]
-        inv0 = SM_PARAMS["alpha_em_inv"]
-        return np.stack([param_vector(alpha_em_inv=inv0 / (0.5 + x)) for x in u])
+        return coupling_points(8)
     if workload_name in ("gg_ttg_4m", "gg_ttgg_1m"):
         ks = [0.8 + 0.4 * i / 63 for i in range(64)] if workload_name == "gg_ttg_4m" else [1.2]
         if variant == "mt":

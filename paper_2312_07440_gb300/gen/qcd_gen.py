@@ -283,11 +283,11 @@ def emit_process(name, n, outgoing_gluons, n_identical):
                 terms = []
                 for c in range(1, L):
                     a, b = sq[:c], sq[c:]
-                    terms.append(f"vvv({jn(a)}, Kn.P[{mask(a)}], {jn(b)}, Kn.P[{mask(b)}], Kn.cg[{m}])")
+                    terms.append(f"{jn(a)}, Kn.P[{mask(a)}], {jn(b)}, Kn.P[{mask(b)}], Kn.cg[{m}]")
                     em.count(g, "vvv")
-                w(f"{ind}cv<R> {nm} = {terms[0]};")
+                w(f"{ind}cv<R> {nm} = vvv({terms[0]});")
                 for t in terms[1:]:
-                    w(f"{ind}addto({nm}, {t});")
+                    w(f"{ind}vvv_acc({nm}, {t});")  # fused accumulation
                     em.count(g, "cadd", 8)
                 for c in range(1, L):
                     for d in range(c + 1, L):
@@ -305,11 +305,11 @@ def emit_process(name, n, outgoing_gluons, n_identical):
             terms = []
             for c in range(1, L + 1):
                 a, b = rho[:c], rho[c:]
-                terms.append(f"slash({jn(a)}, {seq_name('S_', b)})")
+                terms.append(f"{jn(a)}, {seq_name('S_', b)}")
                 em.count(n, "slash")
-            w(f"{ind}sp<R> t{nm} = {terms[0]};")
+            w(f"{ind}sp<R> t{nm} = slash({terms[0]});")
             for t in terms[1:]:
-                w(f"{ind}spadd(t{nm}, {t});")
+                w(f"{ind}slash_acc(t{nm}, {t});")  # fused accumulation
                 em.count(n, "sp_add")
             w(f"{ind}const sp<R> {nm} = fprop(Kn.qc[{mask(rho)}], Kn.mc[{mask(rho)}], t{nm});")
             em.count(n, "fprop")
@@ -320,11 +320,11 @@ def emit_process(name, n, outgoing_gluons, n_identical):
         terms = []
         for c in range(1, n + 1):
             a, b = sg[:c], sg[c:]
-            terms.append(f"slash({jn(a)}, {seq_name('S_', b)})")
+            terms.append(f"{jn(a)}, {seq_name('S_', b)}")
             em.count(n, "slash")
-        w(f"{ind}sp<R> X{k} = {terms[0]};")
+        w(f"{ind}sp<R> X{k} = slash({terms[0]});")
         for t in terms[1:]:
-            w(f"{ind}spadd(X{k}, {t});")
+            w(f"{ind}slash_acc(X{k}, {t});")
             em.count(n, "sp_add")
     # top level: A(sigma) = ubar X(sigma), colour sum
     open_level(n + 1, f"h{n + 1}", f"const sp<R> UB = h{n + 1} ? X.ub[1] : X.ub[0];")

@@ -85,7 +85,7 @@ def emit_process(name, n):
             w(f"{ind}w2<R> t{m} = sl_RL(E{terms[0]}, {sname(m & ~(1 << terms[0]))});")
             flops_level[L] += FLOPS["sl"]
             for i in terms[1:]:
-                w(f"{ind}addto(t{m}, sl_RL(E{i}, {sname(m & ~(1 << i))}));")
+                w(f"{ind}sl_RL_acc(t{m}, E{i}, {sname(m & ~(1 << i))});")  # fused accumulation
                 flops_level[L] += FLOPS["sl"] + FLOPS["acc"]
             w(f"{ind}const w2<R> {sname(m)} = pr_LR(Kn.q[{m}], t{m});")
             flops_level[L] += FLOPS["pr"]
@@ -94,7 +94,7 @@ def emit_process(name, n):
             w(f"{ind}w2<R> T = sl_RL(E0, {sname(full & ~1)});")
             flops_level[L] += FLOPS["sl"]
             for i in range(1, n):
-                w(f"{ind}addto(T, sl_RL(E{i}, {sname(full & ~(1 << i))}));")
+                w(f"{ind}sl_RL_acc(T, E{i}, {sname(full & ~(1 << i))});")
                 flops_level[L] += FLOPS["sl"] + FLOPS["acc"]
             w(f"{ind}const cx<R> A = close_L(X.vb, T);")
             w(f"{ind}acc += A.r * A.r + A.i * A.i;")
