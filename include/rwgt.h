@@ -161,7 +161,15 @@ int rw_reweight(rw_ctx* ctx, double* d_wnew, double* d_ratio, double* h_sigma, d
    the device workspace, reweights, copies W'[P][E] back to h_wnew (may be
    NULL) and the sums to h_sigma/h_sigma_orig/h_n_bad; synchronises.  The
    device workspace must hold rw_workspace_bytes_host(E) bytes.  Host buffers
-   should be pinned (cudaHostAlloc) for full copy bandwidth. */
+   should be pinned (cudaHostAlloc) for full copy bandwidth.  Large batches are
+   pipelined: chunks of about E/8 events (a multiple of the threads one launch
+   keeps resident) are copied in on a second stream the context creates on
+   first use, and the reweight of chunk k starts as soon as its copy is in,
+   overlapping the copies of the later chunks; W' of chunk k is copied out
+   while chunk k+1 is reweighted.  The sums are carried across chunks in
+   compensated form, in chunk order, so results stay deterministic.  The work starts after what is
+   already queued on the context's stream and the call returns with all of
+   it done. */
 size_t rw_workspace_bytes_host(const rw_ctx* ctx, int64_t n_events);
 int rw_reweight_host(rw_ctx* ctx, const double* h_mom, const double* h_w, int64_t n_events, double* h_wnew,
                      double* h_sigma, double* h_sigma_orig, int64_t* h_n_bad, void* d_workspace,

@@ -48,6 +48,9 @@ struct RwArgs {
   unsigned int* ticket;           // zero between launches
   unsigned long long* nbad_count; // zero between launches
   unsigned long long* nbad_out;
+  double2* sigma_acc;  // [P+1] (sum, compensation) carried across launches, or null
+  long long ldo;       // row stride of the [P][.] outputs (0: E)
+  int accumulate;      // 1: add this launch's sums and bad events to the previous launch's
   int P;
   int me_only;  // evaluate pt[0] only and write me0 (no reductions)
   PointDev pt[MAX_POINTS + 1];  // [0] original, [1..P] modified points
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(256, MINB) k_reweight(const __grid_constant__ 
   const long long ngroups = (long long)gridDim.x * gpb;
   const long long g0 = (long long)blockIdx.x * gpb + tid / LANES;
   const long long E = a.E;
+  const long long ldo = a.ldo ? a.ldo : a.E;
   unsigned long long nbad = 0;
   // Up to FEW points: per-thread compensated accumulators for the cross
   // sections (slot P = sigma of the original weights), reduced once at the end;
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(256, MINB) k_reweight(const __grid_constant__ 
       const double r = ok ? me / me0 : 0.0;
       const double wn = ok ? r * w : 0.0;
       if (leader) {
-        const long long o = (long long)(j - 1) * E + ev;
+        const long long o = (long long)(j - 1) * ldo + ev;
         if (a.me_pts) a.me_pts[o] = me;
         if (a.ratio) a.ratio[o] = r;
         if (a.wnew) a.wnew[o] = wn;
@@ -245,10 +249,20 @@ __global__ void __launch_bounds__(256, MINB) k_reweight(const __grid_constant__ 
       two_sum_acc(s, c, v.x, v.y);
     }
     block_sum2(s, c, red);
-    if (tid == 0) a.sigma[j] = s + c;
+    if (tid == 0) {
+      if (a.sigma_acc) {  // chunked launches: carry (sum, compensation) in launch order
+        double2 t = a.accumulate ? a.sigma_acc[j] : make_double2(0.0, 0.0);
+        two_sum_acc(t.x, t.y, s, c);
+        a.sigma_acc[j] = t;
+        a.sigma[j] = t.x + t.y;
+      } else {
+        a.sigma[j] = s + c;
+      }
+    }
   }
   if (tid == 0) {
-    *a.nbad_out = atomicExch(a.nbad_count, 0ull);
+    const unsigned long long nb = atomicExch(a.nbad_count, 0ull);
+    *a.nbad_out = a.accumulate ? *a.nbad_out + nb : nb;
     *a.ticket = 0u;
   }
 }

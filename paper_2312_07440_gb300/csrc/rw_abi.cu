@@ -108,6 +108,9 @@ struct rw_ctx {
   std::string err;
   double* h_stage = nullptr;  // pinned [RW_MAX_POINTS + 2]
   std::map<std::tuple<const void*, int, size_t>, int> occ;
+  // rw_reweight_host pipeline: copy stream and events, created on first use
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> events;
 };
 
 namespace {
@@ -223,14 +226,21 @@ int ready(rw_ctx* c, bool need_events) {
 }
 
 // launch the fused kernel; `points` empty => single evaluation mode
-int launch(rw_ctx* c, RwArgs& a) {
+// launch shape of the current kernel variant: the entry, threads per block,
+// lanes per event, shared memory and resident blocks per SM for P points
+struct Shape {
+  const KernelEntry* k;
+  int block, lanes, per_sm;
+  size_t smem;
+};
+
+int shape(rw_ctx* c, int P, Shape& sh) {
   const int lb = c->lane_bits >= 0 ? c->lane_bits : default_lane_bits(c->process, c->mode);
   const KernelEntry* k = registry().find(c->process, c->mode, lb);
   if (!k) return fail(c, RW_ERR_MODE, "no kernel for process %d mode %d lane_bits %d", c->process, c->mode, lb);
   const int block = c->block > 0 ? c->block : 128;
   if (block > k->max_block) return fail(c, RW_ERR_ARG, "block %d above this variant's %d", block, k->max_block);
-  const int lanes = 1 << lb;
-  const size_t smem = (size_t)(block / 32) * (a.P + 1) * sizeof(double2);
+  const size_t smem = (size_t)(block / 32) * (P + 1) * sizeof(double2);
   auto key = std::make_tuple(k->func, block, smem);
   auto it = c->occ.find(key);
   int per_sm;
@@ -242,12 +252,46 @@ int launch(rw_ctx* c, RwArgs& a) {
   } else {
     per_sm = it->second;
   }
+  sh = {k, block, 1 << lb, per_sm, smem};
+  return RW_OK;
+}
+
+int launch(rw_ctx* c, RwArgs& a) {
+  Shape sh;
+  int rc = shape(c, a.P, sh);
+  if (rc) return rc;
+  const KernelEntry* k = sh.k;
+  const int block = sh.block, lanes = sh.lanes, per_sm = sh.per_sm;
+  const size_t smem = sh.smem;
   const long long need = (a.E * lanes + block - 1) / block;
   const int grid = (int)std::max(1LL, std::min<long long>({(long long)GRID_CAP, (long long)per_sm * c->sm_count, need}));
   void* args[] = {&a};
   cudaError_t e = cudaLaunchKernel(k->func, dim3(grid), dim3(block), args, smem, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
   return RW_OK;
+}
+
+void fill_ws(rw_ctx* c, RwArgs& a, int P);
+
+// the fused reweight of all attached events and points
+void reweight_args(rw_ctx* c, RwArgs& a, double* d_wnew, double* d_ratio, double* d_me0, double* d_me_pts) {
+  const int P = (int)c->pts.size();
+  a.mom = c->mom;
+  a.w = c->w;
+  a.E = c->E;
+  a.ld = c->ld;
+  a.me0 = d_me0;
+  a.me_pts = d_me_pts;
+  a.ratio = d_ratio;
+  a.wnew = d_wnew;
+  a.P = P;
+  a.me_only = 0;
+  a.pt[0] = make_point(c, c->p0, false);
+  for (int j = 0; j < P; ++j) {
+    const bool moved = moves_event(c, c->pts[j]);
+    a.pt[1 + j] = make_point(c, c->pts[j], moved);
+  }
+  fill_ws(c, a, P);
 }
 
 void fill_ws(rw_ctx* c, RwArgs& a, int P) {
@@ -292,6 +336,11 @@ int rw_create(rw_ctx** out, int device, void* stream) {
 int rw_destroy(rw_ctx* c) {
   if (!c) return RW_ERR_NULL;
   DeviceGuard g(c->device);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   delete c;
   return RW_OK;
@@ -529,22 +578,7 @@ int rw_reweight_async(rw_ctx* c, double* d_wnew, double* d_ratio, double* d_me0,
   const int P = (int)c->pts.size();
   if (ws_core_bytes(P) > c->ws_bytes) return fail(c, RW_ERR_WORKSPACE, "workspace too small for %d points", P);
   RwArgs a{};
-  a.mom = c->mom;
-  a.w = c->w;
-  a.E = c->E;
-  a.ld = c->ld;
-  a.me0 = d_me0;
-  a.me_pts = d_me_pts;
-  a.ratio = d_ratio;
-  a.wnew = d_wnew;
-  a.P = P;
-  a.me_only = 0;
-  a.pt[0] = make_point(c, c->p0, false);
-  for (int j = 0; j < P; ++j) {
-    const bool moved = moves_event(c, c->pts[j]);
-    a.pt[1 + j] = make_point(c, c->pts[j], moved);
-  }
-  fill_ws(c, a, P);
+  reweight_args(c, a, d_wnew, d_ratio, d_me0, d_me_pts);
   return launch(c, a);
 }
 
@@ -577,9 +611,17 @@ size_t rw_workspace_bytes_host(const rw_ctx* c, int64_t E) {
   if (!c || c->process < 0 || E <= 0) return 0;
   const int N = registry().st[c->process].n_external;
   const size_t P = std::max<size_t>(1, c->pts.size());
-  return ws_core_bytes((int)P) + align256(8 * 4 * (size_t)N * E) + align256(8 * (size_t)E) + align256(8 * P * E);
+  return ws_core_bytes((int)P) + align256(16 * (P + 1)) + align256(8 * 4 * (size_t)N * E) +
+         align256(8 * (size_t)E) + align256(8 * P * E);
 }
 
+// The events are processed in chunks whose size is a multiple of the threads
+// one launch keeps resident: the copy stream moves every chunk to the device
+// in order, the kernel of chunk k starts on the context's stream once chunk k
+// is in (while later chunks are still arriving), and W' of chunk k goes back
+// on the copy stream while chunk k+1 is reweighted; the cross sections are
+// carried from launch to launch in (sum, compensation) form, in chunk order
+// (deterministic).
 int rw_reweight_host(rw_ctx* c, const double* h_mom, const double* h_w, int64_t E, double* h_wnew, double* h_sigma,
                      double* h_sigma_orig, int64_t* h_n_bad, void* d_ws, size_t ws_bytes) {
   if (!c) return RW_ERR_NULL;
@@ -592,20 +634,83 @@ int rw_reweight_host(rw_ctx* c, const double* h_mom, const double* h_w, int64_t 
   const int P = (int)c->pts.size();
   char* base = static_cast<char*>(d_ws);
   const size_t core = ws_core_bytes(P);
-  double* d_mom = reinterpret_cast<double*>(base + core);
-  double* d_w = reinterpret_cast<double*>(base + core + align256(8 * 4 * (size_t)N * E));
+  double2* d_sacc = reinterpret_cast<double2*>(base + core);
+  double* d_mom = reinterpret_cast<double*>(base + core + align256(16 * (size_t)(P + 1)));
+  double* d_w = reinterpret_cast<double*>(reinterpret_cast<char*>(d_mom) + align256(8 * 4 * (size_t)N * E));
   double* d_wnew = reinterpret_cast<double*>(reinterpret_cast<char*>(d_w) + align256(8 * (size_t)E));
-  cudaError_t e = cudaMemcpyAsync(d_mom, h_mom, 8 * 4 * (size_t)N * E, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, h_w, 8 * (size_t)E, cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
   int rc = rw_load_events(c, d_mom, d_w, E, d_ws, ws_bytes);
   if (rc) return rc;
-  rc = rw_reweight_async(c, h_wnew ? d_wnew : nullptr, nullptr, nullptr, nullptr);
-  if (rc < 0) return rc;
-  if (h_wnew) {
-    e = cudaMemcpyAsync(h_wnew, d_wnew, 8 * (size_t)P * E, cudaMemcpyDeviceToHost, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  Shape sh;
+  if ((rc = shape(c, P, sh))) return rc;
+  // events one launch keeps resident, and the chunk size: about E/8, rounded
+  // up to it; the first chunk is one resident set only (its copy-in is the
+  // part of the transfer nothing overlaps)
+  const long long resident = std::max(1LL, (long long)sh.per_sm * c->sm_count * sh.block / sh.lanes);
+  const long long chunk = std::max(resident, (((E + 7) / 8 + resident - 1) / resident) * resident);
+  auto chunk_start = [&](int k) { return k == 0 ? 0LL : std::min<long long>(E, resident + (k - 1) * chunk); };
+  const int K = E <= resident ? 1 : 1 + (int)((E - resident + chunk - 1) / chunk);
+  cudaError_t e;
+  if (K == 1) {
+    e = cudaMemcpyAsync(d_mom, h_mom, 8 * 4 * (size_t)N * E, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_w, h_w, 8 * (size_t)E, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+    rc = rw_reweight_async(c, h_wnew ? d_wnew : nullptr, nullptr, nullptr, nullptr);
+    if (rc < 0) return rc;
+    if (h_wnew) {
+      e = cudaMemcpyAsync(h_wnew, d_wnew, 8 * (size_t)P * E, cudaMemcpyDeviceToHost, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+    }
+    return rw_get_results(c, h_sigma, h_sigma_orig, h_n_bad);
   }
+  if (!c->copy_stream && (e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(c, e, "cudaStreamCreateWithFlags");
+  while ((int)c->events.size() < 2 * K + 2) {
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(c, e, "cudaEventCreateWithFlags");
+    c->events.push_back(ev);
+  }
+  cudaStream_t cs = c->copy_stream;
+  // the copies start after the work already queued on the context's stream
+  if ((e = cudaEventRecord(c->events[0], c->stream)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(cs, c->events[0], 0)) != cudaSuccess)
+    return cuda_fail(c, e, "stream ordering");
+  const size_t row = 8 * (size_t)E;
+  // all copies in first (the copy stream is in order: a copy-out queued
+  // between them would hold the next chunk's copy-in behind a kernel)
+  for (int kc = 0; kc < K; ++kc) {
+    const long long e0 = chunk_start(kc), n = chunk_start(kc + 1) - e0;
+    e = cudaMemcpy2DAsync(d_mom + e0, row, h_mom + e0, row, 8 * (size_t)n, 4 * (size_t)N, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_w + e0, h_w + e0, 8 * (size_t)n, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(c->events[2 + 2 * kc], cs);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  }
+  for (int kc = 0; kc < K; ++kc) {
+    const long long e0 = chunk_start(kc), n = chunk_start(kc + 1) - e0;
+    cudaEvent_t ready = c->events[2 + 2 * kc], done = c->events[3 + 2 * kc];
+    if ((e = cudaStreamWaitEvent(c->stream, ready, 0)) != cudaSuccess) return cuda_fail(c, e, "stream ordering");
+    RwArgs a{};
+    reweight_args(c, a, h_wnew ? d_wnew + e0 : nullptr, nullptr, nullptr, nullptr);
+    a.mom = d_mom + e0;
+    a.w = d_w + e0;
+    a.E = n;
+    a.ld = E;
+    a.ldo = E;
+    a.sigma_acc = d_sacc;
+    a.accumulate = kc > 0;
+    if ((rc = launch(c, a))) return rc;
+    if (h_wnew) {
+      e = cudaEventRecord(done, c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, done, 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(h_wnew + e0, row, d_wnew + e0, row, 8 * (size_t)n, (size_t)P, cudaMemcpyDeviceToHost, cs);
+      if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+    }
+  }
+  // the context's stream (and so rw_get_results) waits for the last copies
+  if ((e = cudaEventRecord(c->events[1], cs)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(c->stream, c->events[1], 0)) != cudaSuccess)
+    return cuda_fail(c, e, "stream ordering");
   return rw_get_results(c, h_sigma, h_sigma_orig, h_n_bad);
 }
 

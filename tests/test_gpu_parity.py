@@ -280,6 +280,34 @@ def test_host_entry_point_matches_device_path():
     assert abs(sig[0] - math.fsum(hw[0])) <= 2 * np.spacing(sig[0])
 
 
+def test_host_entry_point_pipelined_chunks():
+    """A batch larger than one launch's resident threads goes through the
+    chunked copy/compute pipeline: W' bit-identical to the device path, the
+    carried sums within 2 ulp of the exact sums, and the same result without
+    the W' copy-out."""
+    E = 300001  # several chunks and a ragged last one
+    pts = np.stack([ev.param_vector(m_t=175.0, alpha_s=0.120), ev.param_vector(m_t=170.0)])
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], E)
+    g = run_gpu("gg_tt", "fp64", mom, w, pts)
+    with rwgt.Context(0, torch.cuda.current_stream().cuda_stream) as c:
+        c.set_process("gg_tt", "fp64")
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(pts)
+        nb = c.workspace_bytes_host(E)
+        ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+        hm, hwt = torch.from_numpy(mom).pin_memory(), torch.from_numpy(w).pin_memory()
+        hw = torch.empty((2, E), dtype=torch.float64).pin_memory()
+        sig, so, nbad, rc = c.reweight_host(hm, hwt, E, hw, 2, ws, nb)
+        sig2, so2, _, _ = c.reweight_host(hm, hwt, E, None, 2, ws, nb)
+    hw = hw.numpy()
+    assert rc == 0 and nbad == 0
+    assert np.array_equal(hw, g["wnew"])
+    for j in range(2):
+        assert abs(sig[j] - math.fsum(hw[j])) <= 2 * np.spacing(sig[j])
+    assert abs(so - math.fsum(w)) <= 2 * np.spacing(so)
+    assert np.array_equal(sig, sig2) and so == so2
+
+
 def test_argument_errors():
     mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 64)
     dm, dw = to_dev(mom), to_dev(w)
