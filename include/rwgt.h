@@ -275,6 +275,33 @@ int rw_reweight_noalloc(rw_ctx* ctx, const double* d_mom, const double* d_w, int
                         double* d_ratio, double* d_sigma, unsigned long long* d_n_bad);
 
 /* ---------------------------------------------------------------------------
+   Interpolation surrogate for many points on one parameter axis (the paper
+   has no counterpart; it is the second surrogate of the library, beside the
+   learned one above).  The points must differ from the original parameters
+   in one field only (m_t, alpha_s, alpha_em_inv, m_Z, ...), the same field
+   for all.  Per event the kernel evaluates |M|^2 exactly at the original
+   point and at n_nodes Chebyshev nodes of the points' range [a, b] of that
+   field (n_nodes in [3, 16]), interpolates y = log(|M'|^2/|M|^2) by the
+   Chebyshev series through the nodes and reads log r for every point off it:
+   1 + n_nodes amplitude evaluations per event instead of 1 + P.  log r is
+   analytic along these axes, so the series coefficients fall off
+   geometrically and |c_{n-1}| + |c_{n-2}| estimates the error; an event whose
+   estimate exceeds tol, or with a node |M|^2 <= 0 or non-finite (e.g. a top
+   mass that does not fit), is recomputed on the exact path for all points
+   (d_fallback[e] = 1).  Events with |M|^2 == 0 or non-finite get W' = 0 and
+   are counted in h_n_bad (RW_WARN_BAD_EVENTS).  Outputs: d_wnew [P][E]
+   (device), d_fallback [E] (device, may be NULL), sigma'_p and sigma as
+   compensated sums of the final W' and W (h_sigma [P], h_sigma_orig), the
+   number of recomputed events.  Works on the attached events; the workspace
+   (rw_interp_workspace_bytes, with events and points set) is separate from
+   rw_load_events'.  Synchronises.  RW_ERR_ARG when the points are not on one
+   axis or n_nodes / tol are out of range; RW_ERR_MODE in the mixed modes. */
+size_t rw_interp_workspace_bytes(const rw_ctx* ctx);
+int rw_reweight_interp(rw_ctx* ctx, int n_nodes, double tol, double* d_wnew, unsigned char* d_fallback,
+                       double* h_sigma, double* h_sigma_orig, int64_t* h_n_fallback, int64_t* h_n_bad,
+                       void* d_workspace, size_t workspace_bytes);
+
+/* ---------------------------------------------------------------------------
    Input conversion of the FP32 modes, exposed for verification.  The paper has
    no counterpart.  In RW_FP32 / RW_MIXED_* the g g -> t tbar (+g) kernels split
    every FP64 momentum component x into two floats, hi = the float nearest to x

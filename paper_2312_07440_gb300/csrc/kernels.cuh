@@ -267,4 +267,109 @@ __global__ void __launch_bounds__(256, MINB) k_reweight(const __grid_constant__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Interpolation surrogate for many points on one parameter axis v (m_t,
+// alpha_s, alpha, M_Z, ...): per event, |M|^2 exactly at the original point
+// and at K Chebyshev nodes v_k = (a+b)/2 + (b-a)/2 x_k, x_k = cos(pi (k+1/2)/K),
+// of the points' range [a, b]; y_k = log(|M(v_k)|^2/|M|^2) is interpolated by
+// p(x) = sum_{i<K} c_i T_i(x), c = cheb . y, and log r at every point read off
+// p.  log r is analytic in v on [a, b] for these processes, so the Chebyshev
+// coefficients decay geometrically and |c_{K-1}| + |c_{K-2}| estimates the
+// interpolation error.  Events whose estimate exceeds tol (or with a
+// non-positive or non-finite node value) are listed for the exact path;
+// events with |M|^2 == 0 or non-finite get W' = 0 and are counted as bad.
+// ---------------------------------------------------------------------------
+constexpr int MAX_NODES = 16;
+
+struct InterpArgs {
+  const double* mom;  // [N][4][ld]
+  const double* w;    // [E]
+  long long E, ld;
+  double* wnew;                 // [P][E]; rows of listed events are left for the exact path
+  unsigned char* flag;          // [E]: 1 listed for the exact path, or null
+  unsigned long long* counts;   // [0] listed events, [1] bad events
+  long long* list;              // [E] listed event indices
+  int P, K;
+  double tol;
+  PointDev pt0;
+  PointDev node[MAX_NODES];
+  double cheb[MAX_NODES][MAX_NODES];  // c_i = sum_k cheb[i][k] y_k; zero for i or k >= K
+  double x[MAX_POINTS];               // the points' abscissae in [-1, 1]
+};
+
+template <class Proc, class R, int LB, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB) k_interp(const __grid_constant__ InterpArgs a) {
+  constexpr int NEXT = Proc::NEXT;
+  constexpr int LANES = 1 << LB;
+  const int tid = threadIdx.x;
+  const int wl = tid & 31;
+  const int lane = tid & (LANES - 1);
+  const unsigned gmask = LANES == 32 ? 0xffffffffu : (((1u << LANES) - 1u) << (wl & ~(LANES - 1)));
+  const long long gpb = blockDim.x / LANES;
+  const long long ngroups = (long long)gridDim.x * gpb;
+  const long long g0 = (long long)blockIdx.x * gpb + tid / LANES;
+  const long long E = a.E;
+  for (long long base = 0; base < E; base += ngroups) {
+    const long long ev = base + g0;
+    const bool valid = ev < E;
+    const long long evc = valid ? ev : E - 1;
+    typename Proc::template mom_t<R> p[NEXT][4];
+#pragma unroll
+    for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) load_mom(p[i][m], __ldg(a.mom + ((long long)(i * 4 + m)) * a.ld + evc));
+    const double me0 = eval_point<Proc, R, LB>(p, a.pt0, lane, gmask);
+    const bool ok = isfinite(me0) && me0 != 0.0;
+    R y[MAX_NODES];
+    bool good = ok;
+#pragma unroll 1
+    for (int k = 0; k < a.K; ++k) {
+      const double t = eval_point<Proc, R, LB>(p, a.node[k], lane, gmask) / me0;
+      good = good && isfinite(t) && t > 0.0;
+      y[k] = good ? R(log(R(t))) : R(0);
+    }
+    if (!valid || lane != 0) continue;
+    if (!ok) {
+      atomicAdd(a.counts + 1, 1ull);
+      if (a.flag) a.flag[ev] = 0;
+      for (int j = 0; j < a.P; ++j) a.wnew[(long long)j * E + ev] = 0.0;
+      continue;
+    }
+    // fixed-size register arrays (cheb is zero beyond K, so the padded
+    // coefficients vanish and the 16-term Clenshaw sum equals the K-term one)
+    R yr[MAX_NODES], c[MAX_NODES];
+#pragma unroll
+    for (int k = 0; k < MAX_NODES; ++k) yr[k] = k < a.K ? y[k] : R(0);
+    double est = 0.0;
+#pragma unroll
+    for (int i = 0; i < MAX_NODES; ++i) {
+      R s = R(0);
+#pragma unroll
+      for (int k = 0; k < MAX_NODES; ++k) s = fmadd(R(a.cheb[i][k]), yr[k], s);
+      c[i] = s;
+      if (i == a.K - 1 || i == a.K - 2) est += fabs((double)s);
+    }
+    if (!(good && est <= a.tol)) {
+      if (a.flag) a.flag[ev] = 1;
+      a.list[atomicAdd(a.counts, 1ull)] = ev;
+      continue;
+    }
+    if (a.flag) a.flag[ev] = 0;
+    const double w = __ldg(a.w + ev);
+    for (int j = 0; j < a.P; ++j) {
+      // Clenshaw: p(x) = sum_i c_i T_i(x)
+      const R x = R(a.x[j]), x2 = R(2) * x;
+      R b1 = R(0), b2 = R(0);
+#pragma unroll
+      for (int i = MAX_NODES - 1; i >= 1; --i) {
+        const R b0 = fmadd(x2, b1, c[i] - b2);
+        b2 = b1;
+        b1 = b0;
+      }
+      const R lr = fmadd(x, b1, c[0] - b2);
+      a.wnew[(long long)j * E + ev] = (double)exp(lr) * w;
+    }
+  }
+}
+
 }  // namespace rw

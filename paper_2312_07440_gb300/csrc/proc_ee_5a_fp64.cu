@@ -21,9 +21,13 @@ using P = QedProc<Tag>;
 
 void register_ee_5a_fp64(std::vector<KernelEntry>& t) {
   t.push_back({RW_EE_5A, RW_FP64, 0, (const void*)&k_reweight<P, double, 0>});
+  t.push_back({RW_EE_5A, RW_FP64, 0, (const void*)&k_interp<P, double, 0>, 256, 1});
   t.push_back({RW_EE_5A, RW_FP64, 1, (const void*)&k_reweight<P, double, 1>});
+  t.push_back({RW_EE_5A, RW_FP64, 1, (const void*)&k_interp<P, double, 1>, 256, 1});
   t.push_back({RW_EE_5A, RW_FP64, 2, (const void*)&k_reweight<P, double, 2>});
+  t.push_back({RW_EE_5A, RW_FP64, 2, (const void*)&k_interp<P, double, 2>, 256, 1});
   t.push_back({RW_EE_5A, RW_FP64, 3, (const void*)&k_reweight<P, double, 3>});
+  t.push_back({RW_EE_5A, RW_FP64, 3, (const void*)&k_interp<P, double, 3>, 256, 1});
 }
 
 void static_ee_5a(ProcStatic& s) {

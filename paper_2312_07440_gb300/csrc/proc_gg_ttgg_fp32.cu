@@ -21,8 +21,11 @@ using P = QcdProc<Tag>;
 
 void register_gg_ttgg_fp32(std::vector<KernelEntry>& t) {
   t.push_back({RW_GG_TTGG, RW_FP32, 1, (const void*)&k_reweight<P, float, 1>});
+  t.push_back({RW_GG_TTGG, RW_FP32, 1, (const void*)&k_interp<P, float, 1>, 256, 1});
   t.push_back({RW_GG_TTGG, RW_FP32, 2, (const void*)&k_reweight<P, float, 2>});
+  t.push_back({RW_GG_TTGG, RW_FP32, 2, (const void*)&k_interp<P, float, 2>, 256, 1});
   t.push_back({RW_GG_TTGG, RW_FP32, 3, (const void*)&k_reweight<P, float, 3>});
+  t.push_back({RW_GG_TTGG, RW_FP32, 3, (const void*)&k_interp<P, float, 3>, 256, 1});
 }
 
 }  // namespace rw

@@ -130,8 +130,9 @@ __device__ __forceinline__ void qed_setup(const double (&p)[NEXT][4], QedExt<R, 
   }
 }
 
-// FP32 modes: the same from double-float momenta (invariants and q in
-// double-float, dfloat.cuh), everything else in float.
+// FP32 modes: the same from double-float momenta, the invariants q^2 in
+// double-float (dfloat.cuh), everything else -- the numerator vector q
+// included, which is never formed by cancellation against itself -- in float.
 template <class R, int NA, int NEXT>
 __device__ __forceinline__ void qed_setup(const df (&p)[NEXT][4], QedExt<R, NA>& X, QedKin<R, NA>& Kn) {
   static_assert(NEXT == NA + 2, "e- e+ + NA photons");
@@ -152,22 +153,23 @@ __device__ __forceinline__ void qed_setup(const df (&p)[NEXT][4], QedExt<R, NA>&
   constexpr int FULL = (1 << NA) - 1;
 #pragma unroll
   for (int msk = 1; msk < FULL; ++msk) {
-    df q[4] = {p[0][0], p[0][1], p[0][2], p[0][3]}, q2 = {0.0f, 0.0f};
+    R q[4] = {pr[0][0], pr[0][1], pr[0][2], pr[0][3]};
+    df q2 = {0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
       if (!((msk >> i) & 1)) continue;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) q[m] = df_sub(q[m], p[2 + i][m]);
+      for (int m = 0; m < 4; ++m) q[m] -= pr[2 + i][m];
       q2 = df_add(q2, d0[i]);
 #pragma unroll
       for (int j = i + 1; j < NA; ++j)
         if ((msk >> j) & 1) q2 = df_add(q2, dk[i][j]);
     }
     const R c = R(1) / q2.hi;
-    Kn.q[msk][0] = c * df_add(q[0], q[3]).hi;
-    Kn.q[msk][1] = c * df_sub(q[0], q[3]).hi;
-    Kn.q[msk][2] = c * q[1].hi;
-    Kn.q[msk][3] = c * q[2].hi;
+    Kn.q[msk][0] = c * (q[0] + q[3]);
+    Kn.q[msk][1] = c * (q[0] - q[3]);
+    Kn.q[msk][2] = c * q[1];
+    Kn.q[msk][3] = c * q[2];
   }
 }
 

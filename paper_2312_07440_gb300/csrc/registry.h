@@ -9,8 +9,9 @@ struct KernelEntry {
   int process;       // RW_* process id
   int mode;          // RW_FP64 / RW_FP32
   int lane_bits;     // helicity slices per event = 2^lane_bits
-  const void* func;  // __global__ k_reweight<...>(RwArgs)
+  const void* func;  // __global__ k_reweight<...>(RwArgs) or k_interp<...>(InterpArgs)
   int max_block = 256;  // threads per block the variant supports
+  int kind = 0;         // 0: k_reweight, 1: k_interp (interpolation surrogate)
 };
 
 struct ProcStatic {

@@ -50,9 +50,9 @@ struct Registry {
     rw::register_ee_5a_fp32(kernels);
     rw::static_ee_5a(st[RW_EE_5A]);
   }
-  const KernelEntry* find(int process, int mode, int lb) const {
+  const KernelEntry* find(int process, int mode, int lb, int kind = 0) const {
     for (const auto& k : kernels)
-      if (k.process == process && k.mode == mode && k.lane_bits == lb) return &k;
+      if (k.process == process && k.mode == mode && k.lane_bits == lb && k.kind == kind) return &k;
     return nullptr;
   }
 };
@@ -366,7 +366,7 @@ int rw_set_process(rw_ctx* c, int process, int mode) {
   if (process < 0 || process >= NPROC) return fail(c, RW_ERR_ARG, "unknown process %d", process);
   if (mode < RW_FP64 || mode > RW_MIXED_BF16) return fail(c, RW_ERR_MODE, "unknown mode %d", mode);
   bool any = false;
-  for (const auto& k : registry().kernels) any |= k.process == process && k.mode == mode;
+  for (const auto& k : registry().kernels) any |= k.process == process && k.mode == mode && k.kind == 0;
   if (!any) return fail(c, RW_ERR_MODE, "process %d has no kernels in mode %d", process, mode);
   c->process = process;
   c->mode = mode;
@@ -471,7 +471,7 @@ int rw_autotune(rw_ctx* c, int64_t max_events, const char* cache_path, double* m
   int best_lb = -1, best_bl = 0;
   static const int blocks[] = {64, 128, 256};
   for (const auto& k : registry().kernels) {
-    if (k.process != c->process || k.mode != c->mode) continue;
+    if (k.process != c->process || k.mode != c->mode || k.kind != 0) continue;
     for (int bl : blocks) {
       if ((1 << k.lane_bits) > bl || bl > k.max_block) continue;
       c->lane_bits = k.lane_bits;
@@ -938,9 +938,14 @@ __device__ __forceinline__ void ts_acc(double& s, double& c, double x, double cx
   s = t;
 }
 
-// compensated sum of x[0..n): per-block partials (fixed grid), then one block
-__global__ void k_sum_partials(const double* __restrict__ x, long long n, double2* __restrict__ part) {
+// Compensated sums of nrows rows of n doubles (row r at rows + r*stride for
+// r < nrows - 1, the last row at `last`): per-(block, row) partials on a
+// fixed grid, then one warp per row, in a fixed order (deterministic).
+__global__ void k_sum_partials(const double* __restrict__ rows, long long stride, int nrows,
+                               const double* __restrict__ last, long long n, double2* __restrict__ part) {
   __shared__ double2 sh[256];
+  const int r = blockIdx.y;
+  const double* x = r < nrows - 1 ? rows + (long long)r * stride : last;
   double s = 0.0, c = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     ts_acc(s, c, x[i], 0.0);
@@ -955,16 +960,28 @@ __global__ void k_sum_partials(const double* __restrict__ x, long long n, double
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) part[(long long)r * gridDim.x + blockIdx.x] = sh[0];
 }
 __global__ void k_sum_final(const double2* __restrict__ part, int nb, double* __restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int r = blockIdx.x, l = threadIdx.x;
   double s = 0.0, c = 0.0;
-  for (int b = 0; b < nb; ++b) ts_acc(s, c, part[b].x, part[b].y);
-  *out = s + c;
+  for (int b = l; b < nb; b += 32) ts_acc(s, c, part[(long long)r * nb + b].x, part[(long long)r * nb + b].y);
+  for (int o = 16; o > 0; o >>= 1) {
+    const double s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    ts_acc(s, c, s2, c2);
+  }
+  if (l == 0) out[r] = s + c;
 }
 
-constexpr int SUM_BLOCKS = 512;
+constexpr int SUM_BLOCKS = 256;
+
+// sigma'_p of the P rows of W' [P][E] and sigma of W, into sig[P + 1]
+cudaError_t row_sums(cudaStream_t st, const double* wnew, long long E, int P, const double* w, double2* part,
+                     double* sig) {
+  k_sum_partials<<<dim3(SUM_BLOCKS, P + 1), 256, 0, st>>>(wnew, E, P + 1, w, E, part);
+  k_sum_final<<<P + 1, 32, 0, st>>>(part, SUM_BLOCKS, sig);
+  return cudaGetLastError();
+}
 
 struct SurrogateLayout {
   size_t core, x, out, counts, list, mom_g, w_g, wn_g, part, sig, total;
@@ -987,8 +1004,8 @@ SurrogateLayout surrogate_layout(const rw_ctx* c, int n_in) {
   L.mom_g = take(8 * 4 * N * E);
   L.w_g = take(8 * E);
   L.wn_g = take(8 * E);
-  L.part = take(16 * SUM_BLOCKS);
-  L.sig = take(8 * P);
+  L.part = take(16 * SUM_BLOCKS * (P + 1));
+  L.sig = take(8 * (P + 1));
   L.total = o;
   return L;
 }
@@ -1097,12 +1114,8 @@ int rw_surrogate_reweight(rw_ctx* c, rw_mlp* m, double p_scale, double k_scale, 
     if ((rc = launch(c, a))) return rc;
     k_scatter<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(wn_g, lp, n, d_wnew + (long long)p * E);
   }
-  // 5. sigma'_p
-  for (int p = 0; p < P; ++p) {
-    k_sum_partials<<<SUM_BLOCKS, 256, 0, c->stream>>>(d_wnew + (long long)p * E, E, part);
-    k_sum_final<<<1, 32, 0, c->stream>>>(part, SUM_BLOCKS, sig + p);
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "sum launch");
+  // 5. sigma'_p (and sigma of W in the last slot)
+  if ((e = row_sums(c->stream, d_wnew, E, P, c->w, part, sig)) != cudaSuccess) return cuda_fail(c, e, "sum launch");
   if ((e = cudaMemcpyAsync(c->h_stage, sig, 8 * (size_t)P, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "sigma copy");
@@ -1189,3 +1202,188 @@ extern "C" int rw_split_double(const double* d_x, int64_t n, float* d_hi, float*
   k_split_double<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(d_x, n, d_hi, d_lo);
   return cudaGetLastError() == cudaSuccess ? RW_OK : RW_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// rw_reweight_interp: Chebyshev interpolation of log r along one parameter
+// axis (k_interp in kernels.cuh), exact fallback for the listed events.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct InterpLayout {
+  size_t core, counts, list, mom_g, w_g, wn_g, part, sig, total;
+};
+
+InterpLayout interp_layout(const rw_ctx* c) {
+  InterpLayout L{};
+  const size_t P = std::max<size_t>(1, c->pts.size()), E = (size_t)c->E, N = registry().st[c->process].n_external;
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {
+    const size_t at = o;
+    o += align256(bytes);
+    return at;
+  };
+  L.core = take(ws_core_bytes((int)P));
+  L.counts = take(16);
+  L.list = take(8 * E);
+  L.mom_g = take(8 * 4 * N * E);
+  L.w_g = take(8 * E);
+  L.wn_g = take(8 * P * E);
+  L.part = take(16 * SUM_BLOCKS * (P + 1));
+  L.sig = take(8 * (P + 1));
+  L.total = o;
+  return L;
+}
+
+// the one parameter field in which every point differs from the original
+// parameters (the others equal), or -1
+int interp_axis(const rw_ctx* c) {
+  auto field = [](const rw_params& p, int f) {
+    const double v[8] = {p.alpha_s, p.m_t, p.w_t, p.yt_scale, p.alpha_em_inv, p.G_F, p.m_Z, p.w_Z};
+    return v[f];
+  };
+  int axis = -1;
+  for (const rw_params& q : c->pts)
+    for (int f = 0; f < 8; ++f) {
+      if (field(q, f) == field(c->p0, f)) continue;
+      if (axis >= 0 && axis != f) return -1;
+      axis = f;
+    }
+  return axis;
+}
+
+rw_params with_axis(rw_params p, int axis, double v) {
+  double* f[8] = {&p.alpha_s, &p.m_t, &p.w_t, &p.yt_scale, &p.alpha_em_inv, &p.G_F, &p.m_Z, &p.w_Z};
+  *f[axis] = v;
+  return p;
+}
+
+__global__ void k_scatter_rows(const double* __restrict__ v, const long long* __restrict__ list, long long n, int P,
+                               long long E, double* __restrict__ dst) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)P * n) return;
+  const long long j = t / n, i = t % n;
+  dst[j * E + list[i]] = v[j * n + i];
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rw_interp_workspace_bytes(const rw_ctx* c) {
+  if (!c || c->process < 0 || !c->mom || c->pts.empty()) return 0;
+  return interp_layout(c).total;
+}
+
+int rw_reweight_interp(rw_ctx* c, int n_nodes, double tol, double* d_wnew, unsigned char* d_fallback,
+                       double* h_sigma, double* h_sigma_orig, int64_t* h_n_fallback, int64_t* h_n_bad, void* d_ws,
+                       size_t ws_bytes) {
+  int rc = ready(c, true);
+  if (rc) return rc;
+  if (c->pts.empty()) return fail(c, RW_ERR_STATE, "no points set");
+  if (!d_wnew || !d_ws) return fail(c, RW_ERR_NULL, "W' and workspace are required");
+  if (n_nodes < 3 || n_nodes > rw::MAX_NODES) return fail(c, RW_ERR_ARG, "n_nodes must be in [3, %d]", rw::MAX_NODES);
+  if (!(tol > 0)) return fail(c, RW_ERR_ARG, "tol must be > 0");
+  const InterpLayout L = interp_layout(c);
+  if (ws_bytes < L.total) return fail(c, RW_ERR_WORKSPACE, "workspace %zu < %zu", ws_bytes, L.total);
+  const int axis = interp_axis(c);
+  if (axis < 0) return fail(c, RW_ERR_ARG, "the points must differ from the original parameters in one field only");
+  const int lb = c->lane_bits >= 0 ? c->lane_bits : default_lane_bits(c->process, c->mode);
+  const KernelEntry* k = registry().find(c->process, c->mode, lb, 1);
+  if (!k) return fail(c, RW_ERR_MODE, "no interpolation kernel for process %d mode %d lane_bits %d", c->process,
+                      c->mode, lb);
+  DeviceGuard g(c->device);
+  const int P = (int)c->pts.size(), N = registry().st[c->process].n_external, K = n_nodes;
+  const long long E = c->E;
+  auto field = [axis](const rw_params& p) {
+    const double v[8] = {p.alpha_s, p.m_t, p.w_t, p.yt_scale, p.alpha_em_inv, p.G_F, p.m_Z, p.w_Z};
+    return v[axis];
+  };
+  double lo = field(c->pts[0]), hi = lo;
+  for (const rw_params& q : c->pts) {
+    lo = std::min(lo, field(q));
+    hi = std::max(hi, field(q));
+  }
+  if (!(hi > lo)) {  // one distinct value: a tiny interval around it
+    lo -= 1e-6 * fabs(lo) + 1e-12;
+    hi += 1e-6 * fabs(hi) + 1e-12;
+  }
+  rw::InterpArgs ia{};
+  ia.mom = c->mom;
+  ia.w = c->w;
+  ia.E = E;
+  ia.ld = c->ld;
+  ia.wnew = d_wnew;
+  ia.flag = d_fallback;
+  char* b = static_cast<char*>(d_ws);
+  ia.counts = reinterpret_cast<unsigned long long*>(b + L.counts);
+  ia.list = reinterpret_cast<long long*>(b + L.list);
+  ia.P = P;
+  ia.K = K;
+  ia.tol = tol;
+  ia.pt0 = make_point(c, c->p0, false);
+  for (int kk = 0; kk < K; ++kk) {
+    const double xk = cos(M_PI * (kk + 0.5) / K);
+    const rw_params q = with_axis(c->p0, axis, 0.5 * (lo + hi) + 0.5 * (hi - lo) * xk);
+    ia.node[kk] = make_point(c, q, moves_event(c, q));
+    for (int i = 0; i < K; ++i) ia.cheb[i][kk] = (i == 0 ? 1.0 : 2.0) / K * cos(i * M_PI * (kk + 0.5) / K);
+  }
+  for (int j = 0; j < P; ++j) ia.x[j] = (2.0 * field(c->pts[j]) - (lo + hi)) / (hi - lo);
+  cudaError_t e = cudaMemsetAsync(ia.counts, 0, 16, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+  {
+    Shape sh;
+    if ((rc = shape(c, 0, sh))) return rc;
+    int per_sm = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, sh.block, 0)) != cudaSuccess)
+      return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    const long long need = (E * (1 << lb) + sh.block - 1) / sh.block;
+    const int grid = (int)std::max(1LL, std::min<long long>({(long long)GRID_CAP,
+                                                              (long long)std::max(1, per_sm) * c->sm_count, need}));
+    void* args[] = {&ia};
+    if ((e = cudaLaunchKernel(k->func, dim3(grid), dim3(sh.block), args, 0, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "interpolation kernel launch");
+  }
+  if ((e = cudaMemcpyAsync(c->h_stage, ia.counts, 16, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "fallback count");
+  unsigned long long cnt[2];
+  memcpy(cnt, c->h_stage, 16);
+  const long long n = (long long)cnt[0];
+  if (h_n_fallback) *h_n_fallback = n;
+  if (h_n_bad) *h_n_bad = (int64_t)cnt[1];
+  double* mom_g = reinterpret_cast<double*>(b + L.mom_g);
+  double* w_g = reinterpret_cast<double*>(b + L.w_g);
+  double* wn_g = reinterpret_cast<double*>(b + L.wn_g);
+  if (n > 0) {  // the exact path for the listed events, all points in one launch
+    k_gather_events<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->mom, c->ld, c->w, N, ia.list, n, mom_g,
+                                                                         w_g);
+    RwArgs a{};
+    reweight_args(c, a, wn_g, nullptr, nullptr, nullptr);
+    a.mom = mom_g;
+    a.w = w_g;
+    a.E = n;
+    a.ld = n;
+    char* core = b + L.core;
+    a.ticket = reinterpret_cast<unsigned int*>(core);
+    a.nbad_count = reinterpret_cast<unsigned long long*>(core + 8);
+    a.sigma = reinterpret_cast<double*>(core + 64);
+    a.nbad_out = reinterpret_cast<unsigned long long*>(core + 64 + 8 * (size_t)(P + 1));
+    a.block_part = reinterpret_cast<double2*>(core + 256 + align256(8 * (size_t)(P + 2)));
+    if ((e = cudaMemsetAsync(core, 0, 256, c->stream)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    if ((rc = launch(c, a))) return rc;
+    k_scatter_rows<<<(unsigned)((P * n + 255) / 256), 256, 0, c->stream>>>(wn_g, ia.list, n, P, E, d_wnew);
+  }
+  // cross sections: deterministic compensated sums of the final W' rows and of W
+  double2* part = reinterpret_cast<double2*>(b + L.part);
+  double* sig = reinterpret_cast<double*>(b + L.sig);
+  if ((e = row_sums(c->stream, d_wnew, E, P, c->w, part, sig)) != cudaSuccess) return cuda_fail(c, e, "sums");
+  std::vector<double> hs(P + 1);
+  if ((e = cudaMemcpyAsync(hs.data(), sig, 8 * (size_t)(P + 1), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "sums");
+  if (h_sigma) memcpy(h_sigma, hs.data(), 8 * (size_t)P);
+  if (h_sigma_orig) *h_sigma_orig = hs[P];
+  return cnt[1] ? RW_WARN_BAD_EVENTS : RW_OK;
+}
+
+}  // extern "C"

@@ -89,6 +89,8 @@ def load():
         "rw_graph_destroy": ([P], i),
         "rw_autotune": ([P, i64, ctypes.c_char_p, ctypes.POINTER(d)], i),
         "rw_split_double": ([P, i64, P, P, P], i),
+        "rw_interp_workspace_bytes": ([P], sz),
+        "rw_reweight_interp": ([P, i, d, P, P, P, P, P, P, P, sz], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -237,6 +239,26 @@ class Context:
                                                    sig.ctypes.data, ctypes.byref(so), ctypes.byref(nb),
                                                    _ptr(workspace), int(workspace_bytes)), "rw_reweight_host")
         return sig, so.value, nb.value, rc
+
+
+def reweight_interp(ctx, n_nodes, tol, d_wnew, d_fallback=None):
+    """rw_reweight_interp on a Context with events and points attached:
+    returns dict(sigma[P], sigma_orig, n_fallback, n_bad, status); W' and the
+    fallback flags go to the given device tensors."""
+    lib = ctx.lib
+    nb = int(lib.rw_interp_workspace_bytes(ctx.h))
+    import torch
+    ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=d_wnew.device)
+    P = d_wnew.shape[0]
+    sig = np.zeros(P)
+    so = ctypes.c_double()
+    nfb = ctypes.c_int64()
+    nbad = ctypes.c_int64()
+    rc = ctx._check(lib.rw_reweight_interp(ctx.h, int(n_nodes), float(tol), _ptr(d_wnew), _ptr(d_fallback),
+                                           sig.ctypes.data, ctypes.byref(so), ctypes.byref(nfb), ctypes.byref(nbad),
+                                           _ptr(ws), nb), "rw_reweight_interp")
+    return {"sigma": sig, "sigma_orig": so.value, "n_fallback": int(nfb.value), "n_bad": int(nbad.value),
+            "status": rc}
 
 
 class Mlp:
