@@ -302,6 +302,32 @@ int rw_reweight_interp(rw_ctx* ctx, int n_nodes, double tol, double* d_wnew, uns
                        void* d_workspace, size_t workspace_bytes);
 
 /* ---------------------------------------------------------------------------
+   Les Houches Event files (Sec. 3.2 step 2, "parse events", and step 8,
+   "return new weights"; the format of hep-ph/0609017, per-event weight
+   blocks as in its version 3.0).  Host-side, no GPU needed.
+   rw_lhe_open loads the file and indexes its <event> blocks (RW_ERR_ARG when
+   the file cannot be read or an <event> is not closed; no handle then).
+   rw_lhe_read parses events [first, first+n) with n_threads threads into
+   h_mom [N][4][ld] (E, px, py, pz; the process's particle order, matched by
+   PDG code among the incoming (status -1) and outgoing (status +1) lines in
+   file order, other lines skipped) and h_w [n] (XWGTUP), boosting each event
+   along the beam axis into the partonic centre-of-mass frame the kernels
+   assume.  RW_ERR_ARG with the event index in rw_lhe_last_error when an event
+   does not match the process or a number does not parse.
+   rw_lhe_write writes the file again to `path` with, for every event k, the
+   lines <wgt id='ids[j]'> h_wnew[j*ld + k] </wgt> (j < P, 11 significant digits) inside its
+   <rwgt> block (created before </event> when absent); everything else is
+   copied byte for byte.  ids must not contain ' < > &. */
+typedef struct rw_lhe rw_lhe;
+int rw_lhe_open(rw_lhe** out, const char* path);
+int rw_lhe_close(rw_lhe* lhe);
+const char* rw_lhe_last_error(const rw_lhe* lhe);
+int64_t rw_lhe_n_events(const rw_lhe* lhe);
+int rw_lhe_read(rw_lhe* lhe, int process, int64_t first, int64_t n, double* h_mom, int64_t ld, double* h_w,
+                int n_threads);
+int rw_lhe_write(rw_lhe* lhe, const char* path, const double* h_wnew, int P, int64_t ld, const char* const* ids);
+
+/* ---------------------------------------------------------------------------
    Input conversion of the FP32 modes, exposed for verification.  The paper has
    no counterpart.  In RW_FP32 / RW_MIXED_* the g g -> t tbar (+g) kernels split
    every FP64 momentum component x into two floats, hi = the float nearest to x

@@ -1,0 +1,310 @@
+// Les Houches Event files (hep-ph/0609017; version 3.0 adds per-event weight
+// blocks): the "parse events" and "return new weights" steps of the
+// reweighting procedure (Sec. 3.2, steps 2 and 8), host-side.
+//
+// Reading: the file is loaded once and its <event> blocks indexed; events are
+// parsed in parallel (std::thread, contiguous ranges) with locale-independent
+// number conversion (std::from_chars).  Each event's first line is
+//   NUP IDPRUP XWGTUP SCALUP AQEDUP AQCDUP
+// followed by NUP particle lines
+//   IDUP ISTUP MOTHUP1 MOTHUP2 ICOLUP1 ICOLUP2 PX PY PZ E M VTIMUP SPINUP.
+// Incoming (ISTUP = -1) and outgoing (ISTUP = +1) particles are matched, in
+// file order, to the library's particle order of the process by PDG code;
+// intermediate lines (ISTUP = 2, ...) are skipped.  The momenta are boosted
+// along the beam axis into the partonic centre-of-mass frame (the frame the
+// kernels and the mass-shell reshuffle assume; |M|^2 itself is invariant) and
+// stored as [N][4][ld] (E, px, py, pz); XWGTUP is the weight.
+//
+// Writing: the original text, with each event's new weights added as
+//   <wgt id='ID'> value </wgt>
+// lines inside its <rwgt> block (created before </event> when absent).
+#include <algorithm>
+#include <charconv>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/rwgt.h"
+
+struct rw_lhe {
+  std::string text;
+  std::vector<size_t> body, end;  // per event: first byte after "<event...>", position of "</event>"
+  std::string err;
+};
+
+namespace {
+
+int lhe_fail(rw_lhe* h, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int lhe_fail(rw_lhe* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return code;
+}
+
+// particle order of each process in the kernels (PDG codes)
+bool process_codes(int process, std::vector<int>& codes) {
+  switch (process) {
+    case RW_EE_MUMU: codes = {11, -11, 13, -13}; return true;
+    case RW_GG_TT: codes = {21, 21, 6, -6}; return true;
+    case RW_GG_TTG: codes = {21, 21, 6, -6, 21}; return true;
+    case RW_GG_TTGG: codes = {21, 21, 6, -6, 21, 21}; return true;
+    case RW_EE_5A: codes = {11, -11, 22, 22, 22, 22, 22}; return true;
+  }
+  return false;
+}
+
+struct Cursor {
+  const char* p;
+  const char* e;
+  void skip_ws() {
+    while (p < e && (*p == ' ' || *p == '\t' || *p == '\r' || *p == '\n')) ++p;
+  }
+  bool num(double& v) {
+    skip_ws();
+    if (p < e && *p == '+') ++p;
+    auto r = std::from_chars(p, e, v);
+    if (r.ec != std::errc()) return false;
+    p = r.ptr;
+    return true;
+  }
+  bool num(long long& v) {
+    skip_ws();
+    if (p < e && *p == '+') ++p;
+    auto r = std::from_chars(p, e, v);
+    if (r.ec != std::errc()) return false;
+    p = r.ptr;
+    return true;
+  }
+};
+
+struct Particle {
+  long long id, status;
+  double px, py, pz, e;
+};
+
+// parse event k into out[N][4] (E, px, py, pz) and its weight; 0 or an error index
+int parse_event(const rw_lhe* h, size_t k, const std::vector<int>& codes, double (*out)[4], double& w,
+                std::string& why) {
+  Cursor c{h->text.data() + h->body[k], h->text.data() + h->end[k]};
+  double d;
+  long long nup, idprup;
+  if (!c.num(nup) || !c.num(idprup) || !c.num(w) || !c.num(d) || !c.num(d) || !c.num(d)) {
+    why = "bad event header line";
+    return 1;
+  }
+  if (nup < 1 || nup > 64) {
+    why = "NUP out of range";
+    return 1;
+  }
+  Particle ps[64];
+  for (long long i = 0; i < nup; ++i) {
+    long long m1, m2, c1, c2;
+    double mass, vt, sp;
+    Particle& q = ps[i];
+    if (!c.num(q.id) || !c.num(q.status) || !c.num(m1) || !c.num(m2) || !c.num(c1) || !c.num(c2) || !c.num(q.px) ||
+        !c.num(q.py) || !c.num(q.pz) || !c.num(q.e) || !c.num(mass) || !c.num(vt) || !c.num(sp)) {
+      why = "bad particle line";
+      return 1;
+    }
+  }
+  const int N = (int)codes.size();
+  bool used[64] = {};
+  for (int s = 0; s < N; ++s) {
+    const long long want_status = s < 2 ? -1 : 1;
+    int found = -1;
+    for (long long i = 0; i < nup && found < 0; ++i)
+      if (!used[i] && ps[i].status == want_status && ps[i].id == codes[s]) found = (int)i;
+    if (found < 0) {
+      why = "particles do not match the process";
+      return 1;
+    }
+    used[found] = true;
+    out[s][0] = ps[found].e;
+    out[s][1] = ps[found].px;
+    out[s][2] = ps[found].py;
+    out[s][3] = ps[found].pz;
+  }
+  for (long long i = 0; i < nup; ++i)
+    if (!used[i] && (ps[i].status == -1 || ps[i].status == 1)) {
+      why = "extra external particles for the process";
+      return 1;
+    }
+  // boost along z into the centre-of-mass frame of the two incoming partons
+  const double et = out[0][0] + out[1][0], pzt = out[0][3] + out[1][3];
+  if (!(et > 0.0) || !(std::fabs(pzt) < et)) {
+    why = "unphysical incoming momenta";
+    return 1;
+  }
+  if (pzt != 0.0) {
+    const double b = pzt / et, g = 1.0 / std::sqrt((1.0 - b) * (1.0 + b));
+    for (int s = 0; s < N; ++s) {
+      const double e0 = out[s][0], z0 = out[s][3];
+      out[s][0] = g * (e0 - b * z0);
+      out[s][3] = g * (z0 - b * e0);
+    }
+  }
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rw_lhe_open(rw_lhe** out, const char* path) {
+  if (!out || !path) return RW_ERR_NULL;
+  *out = nullptr;
+  rw_lhe* h = new rw_lhe();
+  FILE* f = fopen(path, "rb");
+  if (!f) {
+    delete h;
+    return RW_ERR_ARG;
+  }
+  fseek(f, 0, SEEK_END);
+  const long sz = ftell(f);
+  fseek(f, 0, SEEK_SET);
+  h->text.resize(sz > 0 ? (size_t)sz : 0);
+  const size_t got = sz > 0 ? fread(&h->text[0], 1, (size_t)sz, f) : 0;
+  fclose(f);
+  if (sz < 0 || got != (size_t)sz) {
+    delete h;
+    return RW_ERR_ARG;
+  }
+  // index the <event> blocks
+  size_t pos = 0;
+  const std::string& t = h->text;
+  while ((pos = t.find("<event", pos)) != std::string::npos) {
+    const char nx = pos + 6 < t.size() ? t[pos + 6] : '\0';
+    if (nx != '>' && nx != ' ' && nx != '\t' && nx != '\n' && nx != '\r') {  // e.g. <eventgroup>
+      pos += 6;
+      continue;
+    }
+    const size_t gt = t.find('>', pos);
+    const size_t close = gt == std::string::npos ? gt : t.find("</event>", gt);
+    if (close == std::string::npos) {
+      delete h;
+      return RW_ERR_ARG;
+    }
+    h->body.push_back(gt + 1);
+    h->end.push_back(close);
+    pos = close + 8;
+  }
+  *out = h;
+  return RW_OK;
+}
+
+int rw_lhe_close(rw_lhe* h) {
+  if (!h) return RW_ERR_NULL;
+  delete h;
+  return RW_OK;
+}
+
+const char* rw_lhe_last_error(const rw_lhe* h) { return h ? h->err.c_str() : "null handle"; }
+
+int64_t rw_lhe_n_events(const rw_lhe* h) { return h ? (int64_t)h->body.size() : -1; }
+
+int rw_lhe_read(rw_lhe* h, int process, int64_t first, int64_t n, double* h_mom, int64_t ld, double* h_w,
+                int n_threads) {
+  if (!h) return RW_ERR_NULL;
+  std::vector<int> codes;
+  if (!process_codes(process, codes)) return lhe_fail(h, RW_ERR_ARG, "unknown process %d", process);
+  if (!h_mom || !h_w) return lhe_fail(h, RW_ERR_NULL, "momenta/weights are NULL");
+  if (first < 0 || n < 0 || first + n > (int64_t)h->body.size() || ld < n)
+    return lhe_fail(h, RW_ERR_ARG, "range [%lld, %lld) / ld %lld outside the %zu events", (long long)first,
+                    (long long)(first + n), (long long)ld, h->body.size());
+  const int N = (int)codes.size();
+  const int T = std::max(1, std::min<int>(n_threads > 0 ? n_threads : 1, (int)std::max<int64_t>(1, n / 1024)));
+  std::vector<long long> bad(T, -1);
+  std::vector<std::string> why(T);
+  auto work = [&](int t) {
+    const int64_t a = n * t / T, b = n * (t + 1) / T;
+    double p[16][4];
+    for (int64_t i = a; i < b; ++i) {
+      double w;
+      if (parse_event(h, (size_t)(first + i), codes, p, w, why[t])) {
+        bad[t] = first + i;
+        return;
+      }
+      for (int s = 0; s < N; ++s)
+        for (int m = 0; m < 4; ++m) h_mom[((int64_t)s * 4 + m) * ld + i] = p[s][m];
+      h_w[i] = w;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < T; ++t) pool.emplace_back(work, t);
+  work(0);
+  for (auto& th : pool) th.join();
+  for (int t = 0; t < T; ++t)
+    if (bad[t] >= 0) return lhe_fail(h, RW_ERR_ARG, "event %lld: %s", bad[t], why[t].c_str());
+  return RW_OK;
+}
+
+int rw_lhe_write(rw_lhe* h, const char* path, const double* h_wnew, int P, int64_t ld, const char* const* ids) {
+  if (!h) return RW_ERR_NULL;
+  if (!path || !h_wnew || !ids) return lhe_fail(h, RW_ERR_NULL, "path, weights and ids are required");
+  const int64_t E = (int64_t)h->body.size();
+  if (P < 1 || ld < E) return lhe_fail(h, RW_ERR_ARG, "need P >= 1 and ld >= %lld", (long long)E);
+  for (int j = 0; j < P; ++j) {
+    if (!ids[j] || !*ids[j]) return lhe_fail(h, RW_ERR_ARG, "id %d is empty", j);
+    for (const char* q = ids[j]; *q; ++q)
+      if (*q == '\'' || *q == '<' || *q == '>' || *q == '&') return lhe_fail(h, RW_ERR_ARG, "id %d: bad character", j);
+  }
+  const std::string& t = h->text;
+  // per event: where the weight lines go and whether an <rwgt> block exists
+  std::vector<size_t> cut(E);
+  std::vector<char> has(E);
+  for (int64_t k = 0; k < E; ++k) {
+    const size_t rb = t.find("<rwgt>", h->body[k]);
+    has[k] = rb != std::string::npos && rb < h->end[k];
+    cut[k] = has[k] ? t.find("</rwgt>", rb) : h->end[k];
+    if (cut[k] == std::string::npos || cut[k] > h->end[k])
+      return lhe_fail(h, RW_ERR_ARG, "event %lld: unclosed <rwgt>", (long long)k);
+  }
+  // the inserted text of every event, formatted in parallel (std::to_chars,
+  // scientific, 10 digits after the point), written in order
+  const int T = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), (int)(E / 4096) + 1));
+  std::vector<std::string> ins(E);
+  auto fmt = [&](int th) {
+    char num[64];
+    for (int64_t k = E * th / T; k < E * (th + 1) / T; ++k) {
+      std::string& o = ins[k];
+      if (!has[k]) o += "<rwgt>\n";
+      for (int j = 0; j < P; ++j) {
+        auto r = std::to_chars(num, num + sizeof num, h_wnew[(int64_t)j * ld + k], std::chars_format::scientific, 10);
+        o += "<wgt id='";
+        o += ids[j];
+        o += "'> ";
+        o.append(num, r.ptr);
+        o += " </wgt>\n";
+      }
+      if (!has[k]) o += "</rwgt>\n";
+    }
+  };
+  {
+    std::vector<std::thread> pool;
+    for (int th = 1; th < T; ++th) pool.emplace_back(fmt, th);
+    fmt(0);
+    for (auto& x : pool) x.join();
+  }
+  FILE* f = fopen(path, "wb");
+  if (!f) return lhe_fail(h, RW_ERR_ARG, "cannot open %s", path);
+  size_t at = 0;
+  bool ok = true;
+  for (int64_t k = 0; k < E && ok; ++k) {
+    ok = fwrite(t.data() + at, 1, cut[k] - at, f) == cut[k] - at &&
+         fwrite(ins[k].data(), 1, ins[k].size(), f) == ins[k].size();
+    at = cut[k];
+  }
+  if (ok) ok = fwrite(t.data() + at, 1, t.size() - at, f) == t.size() - at;
+  if (fclose(f) != 0) ok = false;
+  return ok ? RW_OK : lhe_fail(h, RW_ERR_ARG, "write to %s failed", path);
+}
+
+}  // extern "C"

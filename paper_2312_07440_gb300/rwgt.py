@@ -90,6 +90,12 @@ def load():
         "rw_autotune": ([P, i64, ctypes.c_char_p, ctypes.POINTER(d)], i),
         "rw_split_double": ([P, i64, P, P, P], i),
         "rw_interp_workspace_bytes": ([P], sz),
+        "rw_lhe_open": ([ctypes.POINTER(P), ctypes.c_char_p], i),
+        "rw_lhe_close": ([P], i),
+        "rw_lhe_last_error": ([P], ctypes.c_char_p),
+        "rw_lhe_n_events": ([P], i64),
+        "rw_lhe_read": ([P, i, i64, i64, P, i64, P, i], i),
+        "rw_lhe_write": ([P, ctypes.c_char_p, P, i, i64, P], i),
         "rw_reweight_interp": ([P, i, d, P, P, P, P, P, P, P, sz], i),
     }
     for name, (args, res) in sig.items():
@@ -259,6 +265,56 @@ def reweight_interp(ctx, n_nodes, tol, d_wnew, d_fallback=None):
                                            _ptr(ws), nb), "rw_reweight_interp")
     return {"sigma": sig, "sigma_orig": so.value, "n_fallback": int(nfb.value), "n_bad": int(nbad.value),
             "status": rc}
+
+
+class Lhe:
+    """A Les Houches Event file: read events into the library's layout, write
+    it back with new weights (rw_lhe_*; host only, no GPU needed)."""
+
+    def __init__(self, path):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        rc = self.lib.rw_lhe_open(ctypes.byref(h), os.fsencode(path))
+        if rc:
+            raise RwError(rc, f"rw_lhe_open: cannot read {path}")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.rw_lhe_close(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __len__(self):
+        return int(self.lib.rw_lhe_n_events(self.h))
+
+    def _check(self, rc, what):
+        if rc < 0:
+            raise RwError(rc, f"{what}: {self.lib.rw_lhe_last_error(self.h).decode()}")
+        return rc
+
+    def read(self, process: str, first: int = 0, n=None, threads: int = 8):
+        """(mom [N][4][n] float64, w [n]) for events [first, first + n)."""
+        n = len(self) - first if n is None else int(n)
+        N = process_info(process).n_external
+        mom = np.empty((N, 4, n))
+        w = np.empty(n)
+        self._check(self.lib.rw_lhe_read(self.h, PROCESS[process], int(first), n, mom.ctypes.data, n,
+                                         w.ctypes.data, int(threads)), "rw_lhe_read")
+        return mom, w
+
+    def write(self, path, wnew, ids):
+        """Write the file to ``path`` with wnew[P][E] (E = all events) added as
+        <wgt id=...> lines of each event's <rwgt> block."""
+        wnew = np.ascontiguousarray(wnew, dtype=np.float64)
+        P, ld = wnew.shape
+        arr = (ctypes.c_char_p * P)(*[str(x).encode() for x in ids])
+        self._check(self.lib.rw_lhe_write(self.h, os.fsencode(path), wnew.ctypes.data, P, ld, arr), "rw_lhe_write")
 
 
 class Mlp:

@@ -1,0 +1,129 @@
+"""Les Houches Event files through the library's reader and writer (host
+only): round trip of momenta and weights from a lab-frame file with shuffled
+particle order, intermediate lines and existing weight blocks; the weights
+written back; error reporting."""
+import math
+import re
+
+import numpy as np
+import pytest
+
+from paper_2312_07440_gb300 import events as ev
+
+rwgt = pytest.importorskip("paper_2312_07440_gb300.rwgt")
+try:
+    rwgt.load()
+except (RuntimeError, OSError) as e:  # the library is built by __graft_entry__.build()
+    pytest.skip(f"library not built: {e}", allow_module_level=True)
+
+PDG = {"gg_tt": [21, 21, 6, -6], "gg_ttg": [21, 21, 6, -6, 21], "ee_5a": [11, -11, 22, 22, 22, 22, 22]}
+
+
+def boost_z(p, beta):
+    g = 1.0 / math.sqrt(1.0 - beta * beta)
+    q = p.copy()
+    q[..., 0] = g * (p[..., 0] + beta * p[..., 3])
+    q[..., 3] = g * (p[..., 3] + beta * p[..., 0])
+    return q
+
+
+def write_lhe(path, process, mom, w, beta=0.3, extra=True):
+    """A minimal LHE 3.0 file: lab frame (boost beta along z), outgoing
+    particles before incoming ones and antiparticles first, an intermediate
+    resonance line, a comment and, every third event, an existing <rwgt>."""
+    codes = PDG[process]
+    N, _, E = mom.shape
+    out = ['<LesHouchesEvents version="3.0">', "<header>", "<!-- synthetic -->", "</header>", "<init>",
+           "2212 2212 6.5e3 6.5e3 0 0 0 0 3 1", "1.0 0.1 1.0 1", "</init>"]
+    order = list(range(2, N))[::-1] + [1, 0]
+    # identical particles keep their relative order (the reader matches in file order)
+    order = sorted(order, key=lambda i: (codes[i], i)) if process != "gg_tt" else [3, 2, 0, 1]
+    for e in range(E):
+        p = boost_z(mom[:, :, e], beta)
+        lines = [f"{N + (1 if extra else 0)} 1 {float(w[e])!r} 91.1880000e+00 7.546771e-03 1.180000e-01"]
+        if extra:
+            lines.append(" 23 2 1 2 0 0 0.0 0.0 0.0 91.1876 91.1876 0. 0.")
+        for i in order:
+            st = -1 if i < 2 else 1
+            px, py, pz, en = (float(p[i, m]) for m in (1, 2, 3, 0))
+            lines.append(f" {codes[i]} {st} 0 0 0 0 {px!r} {py!r} {pz!r} {en!r} 0.0 0. 9.")
+        if extra:
+            lines.append("# a comment line")
+        if extra and e % 3 == 0:
+            lines += ["<rwgt>", "<wgt id='old'> 1.0 </wgt>", "</rwgt>"]
+        out += ["<event>"] + lines + ["</event>"]
+    out.append("</LesHouchesEvents>")
+    with open(path, "w") as f:
+        f.write("\n".join(out) + "\n")
+
+
+@pytest.mark.parametrize("process,wl", [("gg_ttg", "gg_ttg_4m"), ("ee_5a", "ee_5a_1m"), ("gg_tt", "gg_tt_1m")])
+def test_read_round_trip(tmp_path, process, wl):
+    mom, w = ev.generate(ev.WORKLOADS[wl], 2500)
+    path = tmp_path / "in.lhe"
+    write_lhe(path, process, mom, w)
+    with rwgt.Lhe(path) as f:
+        assert len(f) == 2500
+        m1, w1 = f.read(process, threads=1)
+        m4, w4 = f.read(process, threads=4)
+        m_part, w_part = f.read(process, first=100, n=50)
+    assert np.array_equal(m1, m4) and np.array_equal(w1, w4)
+    assert np.array_equal(w1, w)  # the weight text is exact
+    # back in the centre-of-mass frame: the boost there and back costs a few ulp
+    scale = mom[0, 0][None, None, :]
+    assert np.abs(m1 - mom).max() <= 1e-13 * scale.max()
+    assert np.array_equal(m_part, m1[:, :, 100:150]) and np.array_equal(w_part, w1[100:150])
+
+
+def test_write_new_weights(tmp_path):
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 300)
+    src, dst = tmp_path / "in.lhe", tmp_path / "out.lhe"
+    write_lhe(src, "gg_tt", mom, w)
+    rng = np.random.default_rng(4)
+    wnew = rng.lognormal(size=(3, 300))
+    with rwgt.Lhe(src) as f:
+        f.write(dst, wnew, ["mt175", "as120", "both"])
+    text = dst.read_text()
+    # every event carries its three new weights, in order, after any old ones
+    blocks = re.findall(r"<event>(.*?)</event>", text, re.S)
+    assert len(blocks) == 300
+    for k, b in enumerate(blocks):
+        vals = re.findall(r"<wgt id='(\w+)'> (\S+) </wgt>", b)
+        names = [n for n, _ in vals if n != "old"]
+        assert names == ["mt175", "as120", "both"]
+        got = [float(v) for n, v in vals if n != "old"]
+        assert np.allclose(got, wnew[:, k], rtol=1e-10, atol=0)
+        assert b.count("<rwgt>") == 1
+    # removing the added lines (and the blocks created for them) gives the input back
+    stripped = re.sub(r"<wgt id='(mt175|as120|both)'> \S+ </wgt>\n", "", text)
+    stripped = stripped.replace("<rwgt>\n</rwgt>\n", "")
+    assert stripped == src.read_text()
+    # and the written file reads back to the same events
+    with rwgt.Lhe(dst) as g:
+        m2, w2 = g.read("gg_tt")
+    with rwgt.Lhe(src) as f:
+        m1, w1 = f.read("gg_tt")
+    assert np.array_equal(m1, m2) and np.array_equal(w1, w2)
+
+
+def test_errors(tmp_path):
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 10)
+    path = tmp_path / "in.lhe"
+    write_lhe(path, "gg_tt", mom, w)
+    with pytest.raises(rwgt.RwError):
+        rwgt.Lhe(tmp_path / "missing.lhe")
+    with rwgt.Lhe(path) as f:
+        with pytest.raises(rwgt.RwError, match="event 0"):
+            f.read("ee_5a")
+        with pytest.raises(rwgt.RwError):
+            f.read("gg_tt", first=5, n=6)
+        with pytest.raises(rwgt.RwError):
+            f.write(tmp_path / "o.lhe", np.ones((1, 10)), ["bad'id"])
+    bad = path.read_text().replace(f"{float(w[3])!r}", "bad-number", 1)
+    (tmp_path / "bad.lhe").write_text(bad)
+    with rwgt.Lhe(tmp_path / "bad.lhe") as f:
+        with pytest.raises(rwgt.RwError, match="event 3"):
+            f.read("gg_tt", threads=1)
+    (tmp_path / "open.lhe").write_text("<LesHouchesEvents>\n<event>\n1 1 1.0 0 0 0\n")
+    with pytest.raises(rwgt.RwError):
+        rwgt.Lhe(tmp_path / "open.lhe")
