@@ -11,7 +11,7 @@ constexpr int NEXT = 4;
 constexpr int K = 2;
 constexpr int NHEL = 16;
 constexpr int NDIAG = 3;
-constexpr int MAX_LB = 3;  // helicity levels that can be spread over lanes
+constexpr int MAX_LB = 2;  // helicity levels that can be spread over lanes
 constexpr int CDEN = 3;
 constexpr int IDENT = 1;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 0u;  // bit g: gluon g outgoing
@@ -42,29 +42,29 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
         const sp<R> S_E = h2 ? X.v[1] : X.v[0];
         sp<R> tS_0 = slash(E0, S_E);
         const sp<R> S_0 = fprop(Kn.qc[1], Kn.mc[1], tS_0);
+        sp<R> X1 = slash(E1, S_0);
+        slash_acc(X1, J1_0, S_E);
+        const cx<R> A1_0 = rowcol(X.ub[0], X1), A1_1 = rowcol(X.ub[1], X1);
         sp<R> tS_1 = slash(E1, S_E);
         const sp<R> S_1 = fprop(Kn.qc[2], Kn.mc[2], tS_1);
         sp<R> X0 = slash(E0, S_1);
         slash_acc(X0, J0_1, S_E);
-        sp<R> X1 = slash(E1, S_0);
-        slash_acc(X1, J1_0, S_E);
-        #pragma unroll 1
-        for (int i3 = 0; i3 < (LB >= 3 ? 1 : 2); ++i3) {
-          const int h3 = LB >= 3 ? ((lane >> (LB - 3)) & 1) : i3;
-          const sp<R> UB = h3 ? X.ub[1] : X.ub[0];
-          const cx<R> A0 = rowcol(UB, X0);
-          const cx<R> A1 = rowcol(UB, X1);
-          if constexpr (CM != CM_FMA) {
-            const cx<float> Aa[K] = {A0, A1};
-            acc += R(2) * cmma.sum(Aa);  // x2 helicity flip
-          } else {
-            R cs = R(0);
-            { const R zr = R(16) * R(0.5) * A0.r + R(-2) * A1.r; const R zi = R(16) * R(0.5) * A0.i + R(-2) * A1.i;
-              cs += A0.r * zr + A0.i * zi; }
-            { const R zr = R(16) * R(0.5) * A1.r; const R zi = R(16) * R(0.5) * A1.i;
-              cs += A1.r * zr + A1.i * zi; }
-            acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
-          }
+        const cx<R> A0_0 = rowcol(X.ub[0], X0), A0_1 = rowcol(X.ub[1], X0);
+        if constexpr (CM != CM_FMA) {
+          const cx<float> Aa0[K] = {A0_0, A1_0};
+          const cx<float> Aa1[K] = {A0_1, A1_1};
+          acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip
+        } else {
+          R cs = R(0);
+          { const R zr = R(16) * R(0.5) * A0_0.r + R(-2) * A1_0.r; const R zi = R(16) * R(0.5) * A0_0.i + R(-2) * A1_0.i;
+            cs += A0_0.r * zr + A0_0.i * zi; }
+          { const R zr = R(16) * R(0.5) * A1_0.r; const R zi = R(16) * R(0.5) * A1_0.i;
+            cs += A1_0.r * zr + A1_0.i * zi; }
+          { const R zr = R(16) * R(0.5) * A0_1.r + R(-2) * A1_1.r; const R zi = R(16) * R(0.5) * A0_1.i + R(-2) * A1_1.i;
+            cs += A0_1.r * zr + A0_1.i * zi; }
+          { const R zr = R(16) * R(0.5) * A1_1.r; const R zi = R(16) * R(0.5) * A1_1.i;
+            cs += A1_1.r * zr + A1_1.i * zi; }
+          acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
         }
       }
     }

@@ -11,7 +11,7 @@ constexpr int NEXT = 5;
 constexpr int K = 6;
 constexpr int NHEL = 32;
 constexpr int NDIAG = 16;
-constexpr int MAX_LB = 4;  // helicity levels that can be spread over lanes
+constexpr int MAX_LB = 3;  // helicity levels that can be spread over lanes
 constexpr int CDEN = 9;
 constexpr int IDENT = 1;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 4u;  // bit g: gluon g outgoing
@@ -62,75 +62,83 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
           const sp<R> S_E = h3 ? X.v[1] : X.v[0];
           sp<R> tS_0 = slash(E0, S_E);
           const sp<R> S_0 = fprop(Kn.qc[1], Kn.mc[1], tS_0);
-          sp<R> tS_1 = slash(E1, S_E);
-          const sp<R> S_1 = fprop(Kn.qc[2], Kn.mc[2], tS_1);
-          sp<R> tS_2 = slash(E2, S_E);
-          const sp<R> S_2 = fprop(Kn.qc[4], Kn.mc[4], tS_2);
-          sp<R> tS_0_1 = slash(E0, S_1);
-          slash_acc(tS_0_1, J0_1, S_E);
-          const sp<R> S_0_1 = fprop(Kn.qc[3], Kn.mc[3], tS_0_1);
-          sp<R> tS_0_2 = slash(E0, S_2);
-          slash_acc(tS_0_2, J0_2, S_E);
-          const sp<R> S_0_2 = fprop(Kn.qc[5], Kn.mc[5], tS_0_2);
           sp<R> tS_1_0 = slash(E1, S_0);
           slash_acc(tS_1_0, J1_0, S_E);
           const sp<R> S_1_0 = fprop(Kn.qc[3], Kn.mc[3], tS_1_0);
-          sp<R> tS_1_2 = slash(E1, S_2);
-          slash_acc(tS_1_2, J1_2, S_E);
-          const sp<R> S_1_2 = fprop(Kn.qc[6], Kn.mc[6], tS_1_2);
-          sp<R> tS_2_0 = slash(E2, S_0);
-          slash_acc(tS_2_0, J2_0, S_E);
-          const sp<R> S_2_0 = fprop(Kn.qc[5], Kn.mc[5], tS_2_0);
-          sp<R> tS_2_1 = slash(E2, S_1);
-          slash_acc(tS_2_1, J2_1, S_E);
-          const sp<R> S_2_1 = fprop(Kn.qc[6], Kn.mc[6], tS_2_1);
-          sp<R> X0 = slash(E0, S_1_2);
-          slash_acc(X0, J0_1, S_2);
-          slash_acc(X0, J0_1_2, S_E);
-          sp<R> X1 = slash(E0, S_2_1);
-          slash_acc(X1, J0_2, S_1);
-          slash_acc(X1, J0_2_1, S_E);
-          sp<R> X2 = slash(E1, S_0_2);
-          slash_acc(X2, J1_0, S_2);
-          slash_acc(X2, J1_0_2, S_E);
-          sp<R> X3 = slash(E1, S_2_0);
-          slash_acc(X3, J1_2, S_0);
-          slash_acc(X3, J1_2_0, S_E);
-          sp<R> X4 = slash(E2, S_0_1);
-          slash_acc(X4, J2_0, S_1);
-          slash_acc(X4, J2_0_1, S_E);
           sp<R> X5 = slash(E2, S_1_0);
           slash_acc(X5, J2_1, S_0);
           slash_acc(X5, J2_1_0, S_E);
-          #pragma unroll 1
-          for (int i4 = 0; i4 < (LB >= 4 ? 1 : 2); ++i4) {
-            const int h4 = LB >= 4 ? ((lane >> (LB - 4)) & 1) : i4;
-            const sp<R> UB = h4 ? X.ub[1] : X.ub[0];
-            const cx<R> A0 = rowcol(UB, X0);
-            const cx<R> A1 = rowcol(UB, X1);
-            const cx<R> A2 = rowcol(UB, X2);
-            const cx<R> A3 = rowcol(UB, X3);
-            const cx<R> A4 = rowcol(UB, X4);
-            const cx<R> A5 = rowcol(UB, X5);
-            if constexpr (CM != CM_FMA) {
-              const cx<float> Aa[K] = {A0, A1, A2, A3, A4, A5};
-              acc += R(2) * cmma.sum(Aa);  // x2 helicity flip
-            } else {
-              R cs = R(0);
-              { const R zr = R(64) * R(0.5) * A0.r + R(-8) * A1.r + R(-8) * A2.r + R(1) * A3.r + R(1) * A4.r + R(10) * A5.r; const R zi = R(64) * R(0.5) * A0.i + R(-8) * A1.i + R(-8) * A2.i + R(1) * A3.i + R(1) * A4.i + R(10) * A5.i;
-                cs += A0.r * zr + A0.i * zi; }
-              { const R zr = R(64) * R(0.5) * A1.r + R(1) * A2.r + R(10) * A3.r + R(-8) * A4.r + R(1) * A5.r; const R zi = R(64) * R(0.5) * A1.i + R(1) * A2.i + R(10) * A3.i + R(-8) * A4.i + R(1) * A5.i;
-                cs += A1.r * zr + A1.i * zi; }
-              { const R zr = R(64) * R(0.5) * A2.r + R(-8) * A3.r + R(10) * A4.r + R(1) * A5.r; const R zi = R(64) * R(0.5) * A2.i + R(-8) * A3.i + R(10) * A4.i + R(1) * A5.i;
-                cs += A2.r * zr + A2.i * zi; }
-              { const R zr = R(64) * R(0.5) * A3.r + R(1) * A4.r + R(-8) * A5.r; const R zi = R(64) * R(0.5) * A3.i + R(1) * A4.i + R(-8) * A5.i;
-                cs += A3.r * zr + A3.i * zi; }
-              { const R zr = R(64) * R(0.5) * A4.r + R(-8) * A5.r; const R zi = R(64) * R(0.5) * A4.i + R(-8) * A5.i;
-                cs += A4.r * zr + A4.i * zi; }
-              { const R zr = R(64) * R(0.5) * A5.r; const R zi = R(64) * R(0.5) * A5.i;
-                cs += A5.r * zr + A5.i * zi; }
-              acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
-            }
+          const cx<R> A5_0 = rowcol(X.ub[0], X5), A5_1 = rowcol(X.ub[1], X5);
+          sp<R> tS_2_0 = slash(E2, S_0);
+          slash_acc(tS_2_0, J2_0, S_E);
+          const sp<R> S_2_0 = fprop(Kn.qc[5], Kn.mc[5], tS_2_0);
+          sp<R> X3 = slash(E1, S_2_0);
+          slash_acc(X3, J1_2, S_0);
+          slash_acc(X3, J1_2_0, S_E);
+          const cx<R> A3_0 = rowcol(X.ub[0], X3), A3_1 = rowcol(X.ub[1], X3);
+          sp<R> tS_1 = slash(E1, S_E);
+          const sp<R> S_1 = fprop(Kn.qc[2], Kn.mc[2], tS_1);
+          sp<R> tS_0_1 = slash(E0, S_1);
+          slash_acc(tS_0_1, J0_1, S_E);
+          const sp<R> S_0_1 = fprop(Kn.qc[3], Kn.mc[3], tS_0_1);
+          sp<R> X4 = slash(E2, S_0_1);
+          slash_acc(X4, J2_0, S_1);
+          slash_acc(X4, J2_0_1, S_E);
+          const cx<R> A4_0 = rowcol(X.ub[0], X4), A4_1 = rowcol(X.ub[1], X4);
+          sp<R> tS_2_1 = slash(E2, S_1);
+          slash_acc(tS_2_1, J2_1, S_E);
+          const sp<R> S_2_1 = fprop(Kn.qc[6], Kn.mc[6], tS_2_1);
+          sp<R> X1 = slash(E0, S_2_1);
+          slash_acc(X1, J0_2, S_1);
+          slash_acc(X1, J0_2_1, S_E);
+          const cx<R> A1_0 = rowcol(X.ub[0], X1), A1_1 = rowcol(X.ub[1], X1);
+          sp<R> tS_2 = slash(E2, S_E);
+          const sp<R> S_2 = fprop(Kn.qc[4], Kn.mc[4], tS_2);
+          sp<R> tS_0_2 = slash(E0, S_2);
+          slash_acc(tS_0_2, J0_2, S_E);
+          const sp<R> S_0_2 = fprop(Kn.qc[5], Kn.mc[5], tS_0_2);
+          sp<R> X2 = slash(E1, S_0_2);
+          slash_acc(X2, J1_0, S_2);
+          slash_acc(X2, J1_0_2, S_E);
+          const cx<R> A2_0 = rowcol(X.ub[0], X2), A2_1 = rowcol(X.ub[1], X2);
+          sp<R> tS_1_2 = slash(E1, S_2);
+          slash_acc(tS_1_2, J1_2, S_E);
+          const sp<R> S_1_2 = fprop(Kn.qc[6], Kn.mc[6], tS_1_2);
+          sp<R> X0 = slash(E0, S_1_2);
+          slash_acc(X0, J0_1, S_2);
+          slash_acc(X0, J0_1_2, S_E);
+          const cx<R> A0_0 = rowcol(X.ub[0], X0), A0_1 = rowcol(X.ub[1], X0);
+          if constexpr (CM != CM_FMA) {
+            const cx<float> Aa0[K] = {A0_0, A1_0, A2_0, A3_0, A4_0, A5_0};
+            const cx<float> Aa1[K] = {A0_1, A1_1, A2_1, A3_1, A4_1, A5_1};
+            acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip
+          } else {
+            R cs = R(0);
+            { const R zr = R(64) * R(0.5) * A0_0.r + R(-8) * A1_0.r + R(-8) * A2_0.r + R(1) * A3_0.r + R(1) * A4_0.r + R(10) * A5_0.r; const R zi = R(64) * R(0.5) * A0_0.i + R(-8) * A1_0.i + R(-8) * A2_0.i + R(1) * A3_0.i + R(1) * A4_0.i + R(10) * A5_0.i;
+              cs += A0_0.r * zr + A0_0.i * zi; }
+            { const R zr = R(64) * R(0.5) * A1_0.r + R(1) * A2_0.r + R(10) * A3_0.r + R(-8) * A4_0.r + R(1) * A5_0.r; const R zi = R(64) * R(0.5) * A1_0.i + R(1) * A2_0.i + R(10) * A3_0.i + R(-8) * A4_0.i + R(1) * A5_0.i;
+              cs += A1_0.r * zr + A1_0.i * zi; }
+            { const R zr = R(64) * R(0.5) * A2_0.r + R(-8) * A3_0.r + R(10) * A4_0.r + R(1) * A5_0.r; const R zi = R(64) * R(0.5) * A2_0.i + R(-8) * A3_0.i + R(10) * A4_0.i + R(1) * A5_0.i;
+              cs += A2_0.r * zr + A2_0.i * zi; }
+            { const R zr = R(64) * R(0.5) * A3_0.r + R(1) * A4_0.r + R(-8) * A5_0.r; const R zi = R(64) * R(0.5) * A3_0.i + R(1) * A4_0.i + R(-8) * A5_0.i;
+              cs += A3_0.r * zr + A3_0.i * zi; }
+            { const R zr = R(64) * R(0.5) * A4_0.r + R(-8) * A5_0.r; const R zi = R(64) * R(0.5) * A4_0.i + R(-8) * A5_0.i;
+              cs += A4_0.r * zr + A4_0.i * zi; }
+            { const R zr = R(64) * R(0.5) * A5_0.r; const R zi = R(64) * R(0.5) * A5_0.i;
+              cs += A5_0.r * zr + A5_0.i * zi; }
+            { const R zr = R(64) * R(0.5) * A0_1.r + R(-8) * A1_1.r + R(-8) * A2_1.r + R(1) * A3_1.r + R(1) * A4_1.r + R(10) * A5_1.r; const R zi = R(64) * R(0.5) * A0_1.i + R(-8) * A1_1.i + R(-8) * A2_1.i + R(1) * A3_1.i + R(1) * A4_1.i + R(10) * A5_1.i;
+              cs += A0_1.r * zr + A0_1.i * zi; }
+            { const R zr = R(64) * R(0.5) * A1_1.r + R(1) * A2_1.r + R(10) * A3_1.r + R(-8) * A4_1.r + R(1) * A5_1.r; const R zi = R(64) * R(0.5) * A1_1.i + R(1) * A2_1.i + R(10) * A3_1.i + R(-8) * A4_1.i + R(1) * A5_1.i;
+              cs += A1_1.r * zr + A1_1.i * zi; }
+            { const R zr = R(64) * R(0.5) * A2_1.r + R(-8) * A3_1.r + R(10) * A4_1.r + R(1) * A5_1.r; const R zi = R(64) * R(0.5) * A2_1.i + R(-8) * A3_1.i + R(10) * A4_1.i + R(1) * A5_1.i;
+              cs += A2_1.r * zr + A2_1.i * zi; }
+            { const R zr = R(64) * R(0.5) * A3_1.r + R(1) * A4_1.r + R(-8) * A5_1.r; const R zi = R(64) * R(0.5) * A3_1.i + R(1) * A4_1.i + R(-8) * A5_1.i;
+              cs += A3_1.r * zr + A3_1.i * zi; }
+            { const R zr = R(64) * R(0.5) * A4_1.r + R(-8) * A5_1.r; const R zi = R(64) * R(0.5) * A4_1.i + R(-8) * A5_1.i;
+              cs += A4_1.r * zr + A4_1.i * zi; }
+            { const R zr = R(64) * R(0.5) * A5_1.r; const R zi = R(64) * R(0.5) * A5_1.i;
+              cs += A5_1.r * zr + A5_1.i * zi; }
+            acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
           }
         }
       }

@@ -11,7 +11,7 @@ constexpr int NEXT = 6;
 constexpr int K = 24;
 constexpr int NHEL = 64;
 constexpr int NDIAG = 123;
-constexpr int MAX_LB = 5;  // helicity levels that can be spread over lanes
+constexpr int MAX_LB = 4;  // helicity levels that can be spread over lanes
 constexpr int CDEN = 54;
 constexpr int IDENT = 2;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 12u;  // bit g: gluon g outgoing
@@ -192,323 +192,367 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             const sp<R> S_E = h4 ? X.v[1] : X.v[0];
             sp<R> tS_0 = slash(E0, S_E);
             const sp<R> S_0 = fprop(Kn.qc[1], Kn.mc[1], tS_0);
-            sp<R> tS_1 = slash(E1, S_E);
-            const sp<R> S_1 = fprop(Kn.qc[2], Kn.mc[2], tS_1);
-            sp<R> tS_2 = slash(E2, S_E);
-            const sp<R> S_2 = fprop(Kn.qc[4], Kn.mc[4], tS_2);
-            sp<R> tS_3 = slash(E3, S_E);
-            const sp<R> S_3 = fprop(Kn.qc[8], Kn.mc[8], tS_3);
-            sp<R> tS_0_1 = slash(E0, S_1);
-            slash_acc(tS_0_1, J0_1, S_E);
-            const sp<R> S_0_1 = fprop(Kn.qc[3], Kn.mc[3], tS_0_1);
-            sp<R> tS_0_2 = slash(E0, S_2);
-            slash_acc(tS_0_2, J0_2, S_E);
-            const sp<R> S_0_2 = fprop(Kn.qc[5], Kn.mc[5], tS_0_2);
-            sp<R> tS_0_3 = slash(E0, S_3);
-            slash_acc(tS_0_3, J0_3, S_E);
-            const sp<R> S_0_3 = fprop(Kn.qc[9], Kn.mc[9], tS_0_3);
             sp<R> tS_1_0 = slash(E1, S_0);
             slash_acc(tS_1_0, J1_0, S_E);
             const sp<R> S_1_0 = fprop(Kn.qc[3], Kn.mc[3], tS_1_0);
-            sp<R> tS_1_2 = slash(E1, S_2);
-            slash_acc(tS_1_2, J1_2, S_E);
-            const sp<R> S_1_2 = fprop(Kn.qc[6], Kn.mc[6], tS_1_2);
-            sp<R> tS_1_3 = slash(E1, S_3);
-            slash_acc(tS_1_3, J1_3, S_E);
-            const sp<R> S_1_3 = fprop(Kn.qc[10], Kn.mc[10], tS_1_3);
-            sp<R> tS_2_0 = slash(E2, S_0);
-            slash_acc(tS_2_0, J2_0, S_E);
-            const sp<R> S_2_0 = fprop(Kn.qc[5], Kn.mc[5], tS_2_0);
-            sp<R> tS_2_1 = slash(E2, S_1);
-            slash_acc(tS_2_1, J2_1, S_E);
-            const sp<R> S_2_1 = fprop(Kn.qc[6], Kn.mc[6], tS_2_1);
-            sp<R> tS_2_3 = slash(E2, S_3);
-            slash_acc(tS_2_3, J2_3, S_E);
-            const sp<R> S_2_3 = fprop(Kn.qc[12], Kn.mc[12], tS_2_3);
-            sp<R> tS_3_0 = slash(E3, S_0);
-            slash_acc(tS_3_0, J3_0, S_E);
-            const sp<R> S_3_0 = fprop(Kn.qc[9], Kn.mc[9], tS_3_0);
-            sp<R> tS_3_1 = slash(E3, S_1);
-            slash_acc(tS_3_1, J3_1, S_E);
-            const sp<R> S_3_1 = fprop(Kn.qc[10], Kn.mc[10], tS_3_1);
-            sp<R> tS_3_2 = slash(E3, S_2);
-            slash_acc(tS_3_2, J3_2, S_E);
-            const sp<R> S_3_2 = fprop(Kn.qc[12], Kn.mc[12], tS_3_2);
-            sp<R> tS_0_1_2 = slash(E0, S_1_2);
-            slash_acc(tS_0_1_2, J0_1, S_2);
-            slash_acc(tS_0_1_2, J0_1_2, S_E);
-            const sp<R> S_0_1_2 = fprop(Kn.qc[7], Kn.mc[7], tS_0_1_2);
-            sp<R> tS_0_1_3 = slash(E0, S_1_3);
-            slash_acc(tS_0_1_3, J0_1, S_3);
-            slash_acc(tS_0_1_3, J0_1_3, S_E);
-            const sp<R> S_0_1_3 = fprop(Kn.qc[11], Kn.mc[11], tS_0_1_3);
-            sp<R> tS_0_2_1 = slash(E0, S_2_1);
-            slash_acc(tS_0_2_1, J0_2, S_1);
-            slash_acc(tS_0_2_1, J0_2_1, S_E);
-            const sp<R> S_0_2_1 = fprop(Kn.qc[7], Kn.mc[7], tS_0_2_1);
-            sp<R> tS_0_2_3 = slash(E0, S_2_3);
-            slash_acc(tS_0_2_3, J0_2, S_3);
-            slash_acc(tS_0_2_3, J0_2_3, S_E);
-            const sp<R> S_0_2_3 = fprop(Kn.qc[13], Kn.mc[13], tS_0_2_3);
-            sp<R> tS_0_3_1 = slash(E0, S_3_1);
-            slash_acc(tS_0_3_1, J0_3, S_1);
-            slash_acc(tS_0_3_1, J0_3_1, S_E);
-            const sp<R> S_0_3_1 = fprop(Kn.qc[11], Kn.mc[11], tS_0_3_1);
-            sp<R> tS_0_3_2 = slash(E0, S_3_2);
-            slash_acc(tS_0_3_2, J0_3, S_2);
-            slash_acc(tS_0_3_2, J0_3_2, S_E);
-            const sp<R> S_0_3_2 = fprop(Kn.qc[13], Kn.mc[13], tS_0_3_2);
-            sp<R> tS_1_0_2 = slash(E1, S_0_2);
-            slash_acc(tS_1_0_2, J1_0, S_2);
-            slash_acc(tS_1_0_2, J1_0_2, S_E);
-            const sp<R> S_1_0_2 = fprop(Kn.qc[7], Kn.mc[7], tS_1_0_2);
-            sp<R> tS_1_0_3 = slash(E1, S_0_3);
-            slash_acc(tS_1_0_3, J1_0, S_3);
-            slash_acc(tS_1_0_3, J1_0_3, S_E);
-            const sp<R> S_1_0_3 = fprop(Kn.qc[11], Kn.mc[11], tS_1_0_3);
-            sp<R> tS_1_2_0 = slash(E1, S_2_0);
-            slash_acc(tS_1_2_0, J1_2, S_0);
-            slash_acc(tS_1_2_0, J1_2_0, S_E);
-            const sp<R> S_1_2_0 = fprop(Kn.qc[7], Kn.mc[7], tS_1_2_0);
-            sp<R> tS_1_2_3 = slash(E1, S_2_3);
-            slash_acc(tS_1_2_3, J1_2, S_3);
-            slash_acc(tS_1_2_3, J1_2_3, S_E);
-            const sp<R> S_1_2_3 = fprop(Kn.qc[14], Kn.mc[14], tS_1_2_3);
-            sp<R> tS_1_3_0 = slash(E1, S_3_0);
-            slash_acc(tS_1_3_0, J1_3, S_0);
-            slash_acc(tS_1_3_0, J1_3_0, S_E);
-            const sp<R> S_1_3_0 = fprop(Kn.qc[11], Kn.mc[11], tS_1_3_0);
-            sp<R> tS_1_3_2 = slash(E1, S_3_2);
-            slash_acc(tS_1_3_2, J1_3, S_2);
-            slash_acc(tS_1_3_2, J1_3_2, S_E);
-            const sp<R> S_1_3_2 = fprop(Kn.qc[14], Kn.mc[14], tS_1_3_2);
-            sp<R> tS_2_0_1 = slash(E2, S_0_1);
-            slash_acc(tS_2_0_1, J2_0, S_1);
-            slash_acc(tS_2_0_1, J2_0_1, S_E);
-            const sp<R> S_2_0_1 = fprop(Kn.qc[7], Kn.mc[7], tS_2_0_1);
-            sp<R> tS_2_0_3 = slash(E2, S_0_3);
-            slash_acc(tS_2_0_3, J2_0, S_3);
-            slash_acc(tS_2_0_3, J2_0_3, S_E);
-            const sp<R> S_2_0_3 = fprop(Kn.qc[13], Kn.mc[13], tS_2_0_3);
             sp<R> tS_2_1_0 = slash(E2, S_1_0);
             slash_acc(tS_2_1_0, J2_1, S_0);
             slash_acc(tS_2_1_0, J2_1_0, S_E);
             const sp<R> S_2_1_0 = fprop(Kn.qc[7], Kn.mc[7], tS_2_1_0);
-            sp<R> tS_2_1_3 = slash(E2, S_1_3);
-            slash_acc(tS_2_1_3, J2_1, S_3);
-            slash_acc(tS_2_1_3, J2_1_3, S_E);
-            const sp<R> S_2_1_3 = fprop(Kn.qc[14], Kn.mc[14], tS_2_1_3);
-            sp<R> tS_2_3_0 = slash(E2, S_3_0);
-            slash_acc(tS_2_3_0, J2_3, S_0);
-            slash_acc(tS_2_3_0, J2_3_0, S_E);
-            const sp<R> S_2_3_0 = fprop(Kn.qc[13], Kn.mc[13], tS_2_3_0);
-            sp<R> tS_2_3_1 = slash(E2, S_3_1);
-            slash_acc(tS_2_3_1, J2_3, S_1);
-            slash_acc(tS_2_3_1, J2_3_1, S_E);
-            const sp<R> S_2_3_1 = fprop(Kn.qc[14], Kn.mc[14], tS_2_3_1);
-            sp<R> tS_3_0_1 = slash(E3, S_0_1);
-            slash_acc(tS_3_0_1, J3_0, S_1);
-            slash_acc(tS_3_0_1, J3_0_1, S_E);
-            const sp<R> S_3_0_1 = fprop(Kn.qc[11], Kn.mc[11], tS_3_0_1);
-            sp<R> tS_3_0_2 = slash(E3, S_0_2);
-            slash_acc(tS_3_0_2, J3_0, S_2);
-            slash_acc(tS_3_0_2, J3_0_2, S_E);
-            const sp<R> S_3_0_2 = fprop(Kn.qc[13], Kn.mc[13], tS_3_0_2);
-            sp<R> tS_3_1_0 = slash(E3, S_1_0);
-            slash_acc(tS_3_1_0, J3_1, S_0);
-            slash_acc(tS_3_1_0, J3_1_0, S_E);
-            const sp<R> S_3_1_0 = fprop(Kn.qc[11], Kn.mc[11], tS_3_1_0);
-            sp<R> tS_3_1_2 = slash(E3, S_1_2);
-            slash_acc(tS_3_1_2, J3_1, S_2);
-            slash_acc(tS_3_1_2, J3_1_2, S_E);
-            const sp<R> S_3_1_2 = fprop(Kn.qc[14], Kn.mc[14], tS_3_1_2);
-            sp<R> tS_3_2_0 = slash(E3, S_2_0);
-            slash_acc(tS_3_2_0, J3_2, S_0);
-            slash_acc(tS_3_2_0, J3_2_0, S_E);
-            const sp<R> S_3_2_0 = fprop(Kn.qc[13], Kn.mc[13], tS_3_2_0);
-            sp<R> tS_3_2_1 = slash(E3, S_2_1);
-            slash_acc(tS_3_2_1, J3_2, S_1);
-            slash_acc(tS_3_2_1, J3_2_1, S_E);
-            const sp<R> S_3_2_1 = fprop(Kn.qc[14], Kn.mc[14], tS_3_2_1);
-            sp<R> X0 = slash(E0, S_1_2_3);
-            slash_acc(X0, J0_1, S_2_3);
-            slash_acc(X0, J0_1_2, S_3);
-            slash_acc(X0, J0_1_2_3, S_E);
-            sp<R> X1 = slash(E0, S_1_3_2);
-            slash_acc(X1, J0_1, S_3_2);
-            slash_acc(X1, J0_1_3, S_2);
-            slash_acc(X1, J0_1_3_2, S_E);
-            sp<R> X2 = slash(E0, S_2_1_3);
-            slash_acc(X2, J0_2, S_1_3);
-            slash_acc(X2, J0_2_1, S_3);
-            slash_acc(X2, J0_2_1_3, S_E);
-            sp<R> X3 = slash(E0, S_2_3_1);
-            slash_acc(X3, J0_2, S_3_1);
-            slash_acc(X3, J0_2_3, S_1);
-            slash_acc(X3, J0_2_3_1, S_E);
-            sp<R> X4 = slash(E0, S_3_1_2);
-            slash_acc(X4, J0_3, S_1_2);
-            slash_acc(X4, J0_3_1, S_2);
-            slash_acc(X4, J0_3_1_2, S_E);
-            sp<R> X5 = slash(E0, S_3_2_1);
-            slash_acc(X5, J0_3, S_2_1);
-            slash_acc(X5, J0_3_2, S_1);
-            slash_acc(X5, J0_3_2_1, S_E);
-            sp<R> X6 = slash(E1, S_0_2_3);
-            slash_acc(X6, J1_0, S_2_3);
-            slash_acc(X6, J1_0_2, S_3);
-            slash_acc(X6, J1_0_2_3, S_E);
-            sp<R> X7 = slash(E1, S_0_3_2);
-            slash_acc(X7, J1_0, S_3_2);
-            slash_acc(X7, J1_0_3, S_2);
-            slash_acc(X7, J1_0_3_2, S_E);
-            sp<R> X8 = slash(E1, S_2_0_3);
-            slash_acc(X8, J1_2, S_0_3);
-            slash_acc(X8, J1_2_0, S_3);
-            slash_acc(X8, J1_2_0_3, S_E);
-            sp<R> X9 = slash(E1, S_2_3_0);
-            slash_acc(X9, J1_2, S_3_0);
-            slash_acc(X9, J1_2_3, S_0);
-            slash_acc(X9, J1_2_3_0, S_E);
-            sp<R> X10 = slash(E1, S_3_0_2);
-            slash_acc(X10, J1_3, S_0_2);
-            slash_acc(X10, J1_3_0, S_2);
-            slash_acc(X10, J1_3_0_2, S_E);
-            sp<R> X11 = slash(E1, S_3_2_0);
-            slash_acc(X11, J1_3, S_2_0);
-            slash_acc(X11, J1_3_2, S_0);
-            slash_acc(X11, J1_3_2_0, S_E);
-            sp<R> X12 = slash(E2, S_0_1_3);
-            slash_acc(X12, J2_0, S_1_3);
-            slash_acc(X12, J2_0_1, S_3);
-            slash_acc(X12, J2_0_1_3, S_E);
-            sp<R> X13 = slash(E2, S_0_3_1);
-            slash_acc(X13, J2_0, S_3_1);
-            slash_acc(X13, J2_0_3, S_1);
-            slash_acc(X13, J2_0_3_1, S_E);
-            sp<R> X14 = slash(E2, S_1_0_3);
-            slash_acc(X14, J2_1, S_0_3);
-            slash_acc(X14, J2_1_0, S_3);
-            slash_acc(X14, J2_1_0_3, S_E);
-            sp<R> X15 = slash(E2, S_1_3_0);
-            slash_acc(X15, J2_1, S_3_0);
-            slash_acc(X15, J2_1_3, S_0);
-            slash_acc(X15, J2_1_3_0, S_E);
-            sp<R> X16 = slash(E2, S_3_0_1);
-            slash_acc(X16, J2_3, S_0_1);
-            slash_acc(X16, J2_3_0, S_1);
-            slash_acc(X16, J2_3_0_1, S_E);
-            sp<R> X17 = slash(E2, S_3_1_0);
-            slash_acc(X17, J2_3, S_1_0);
-            slash_acc(X17, J2_3_1, S_0);
-            slash_acc(X17, J2_3_1_0, S_E);
-            sp<R> X18 = slash(E3, S_0_1_2);
-            slash_acc(X18, J3_0, S_1_2);
-            slash_acc(X18, J3_0_1, S_2);
-            slash_acc(X18, J3_0_1_2, S_E);
-            sp<R> X19 = slash(E3, S_0_2_1);
-            slash_acc(X19, J3_0, S_2_1);
-            slash_acc(X19, J3_0_2, S_1);
-            slash_acc(X19, J3_0_2_1, S_E);
-            sp<R> X20 = slash(E3, S_1_0_2);
-            slash_acc(X20, J3_1, S_0_2);
-            slash_acc(X20, J3_1_0, S_2);
-            slash_acc(X20, J3_1_0_2, S_E);
-            sp<R> X21 = slash(E3, S_1_2_0);
-            slash_acc(X21, J3_1, S_2_0);
-            slash_acc(X21, J3_1_2, S_0);
-            slash_acc(X21, J3_1_2_0, S_E);
-            sp<R> X22 = slash(E3, S_2_0_1);
-            slash_acc(X22, J3_2, S_0_1);
-            slash_acc(X22, J3_2_0, S_1);
-            slash_acc(X22, J3_2_0_1, S_E);
             sp<R> X23 = slash(E3, S_2_1_0);
             slash_acc(X23, J3_2, S_1_0);
             slash_acc(X23, J3_2_1, S_0);
             slash_acc(X23, J3_2_1_0, S_E);
-            #pragma unroll 1
-            for (int i5 = 0; i5 < (LB >= 5 ? 1 : 2); ++i5) {
-              const int h5 = LB >= 5 ? ((lane >> (LB - 5)) & 1) : i5;
-              const sp<R> UB = h5 ? X.ub[1] : X.ub[0];
-              const cx<R> A0 = rowcol(UB, X0);
-              const cx<R> A1 = rowcol(UB, X1);
-              const cx<R> A2 = rowcol(UB, X2);
-              const cx<R> A3 = rowcol(UB, X3);
-              const cx<R> A4 = rowcol(UB, X4);
-              const cx<R> A5 = rowcol(UB, X5);
-              const cx<R> A6 = rowcol(UB, X6);
-              const cx<R> A7 = rowcol(UB, X7);
-              const cx<R> A8 = rowcol(UB, X8);
-              const cx<R> A9 = rowcol(UB, X9);
-              const cx<R> A10 = rowcol(UB, X10);
-              const cx<R> A11 = rowcol(UB, X11);
-              const cx<R> A12 = rowcol(UB, X12);
-              const cx<R> A13 = rowcol(UB, X13);
-              const cx<R> A14 = rowcol(UB, X14);
-              const cx<R> A15 = rowcol(UB, X15);
-              const cx<R> A16 = rowcol(UB, X16);
-              const cx<R> A17 = rowcol(UB, X17);
-              const cx<R> A18 = rowcol(UB, X18);
-              const cx<R> A19 = rowcol(UB, X19);
-              const cx<R> A20 = rowcol(UB, X20);
-              const cx<R> A21 = rowcol(UB, X21);
-              const cx<R> A22 = rowcol(UB, X22);
-              const cx<R> A23 = rowcol(UB, X23);
-              if constexpr (CM != CM_FMA) {
-                const cx<float> Aa[K] = {A0, A1, A2, A3, A4, A5, A6, A7, A8, A9, A10, A11, A12, A13, A14, A15, A16, A17, A18, A19, A20, A21, A22, A23};
-                acc += R(2) * cmma.sum(Aa);  // x2 helicity flip
-              } else {
-                R cs = R(0);
-                { const R zr = R(512) * R(0.5) * A0.r + R(-64) * A1.r + R(-64) * A2.r + R(8) * A3.r + R(8) * A4.r + R(80) * A5.r + R(-64) * A6.r + R(8) * A7.r + R(8) * A8.r + R(-1) * A9.r + R(-1) * A10.r + R(-10) * A11.r + R(8) * A12.r + R(-1) * A13.r + R(80) * A14.r + R(-10) * A15.r + R(71) * A16.r + R(62) * A17.r + R(-1) * A18.r + R(-10) * A19.r + R(-10) * A20.r + R(62) * A21.r + R(62) * A22.r + R(-28) * A23.r; const R zi = R(512) * R(0.5) * A0.i + R(-64) * A1.i + R(-64) * A2.i + R(8) * A3.i + R(8) * A4.i + R(80) * A5.i + R(-64) * A6.i + R(8) * A7.i + R(8) * A8.i + R(-1) * A9.i + R(-1) * A10.i + R(-10) * A11.i + R(8) * A12.i + R(-1) * A13.i + R(80) * A14.i + R(-10) * A15.i + R(71) * A16.i + R(62) * A17.i + R(-1) * A18.i + R(-10) * A19.i + R(-10) * A20.i + R(62) * A21.i + R(62) * A22.i + R(-28) * A23.i;
-                  cs += A0.r * zr + A0.i * zi; }
-                { const R zr = R(512) * R(0.5) * A1.r + R(8) * A2.r + R(80) * A3.r + R(-64) * A4.r + R(8) * A5.r + R(8) * A6.r + R(-64) * A7.r + R(-1) * A8.r + R(-10) * A9.r + R(8) * A10.r + R(-1) * A11.r + R(-1) * A12.r + R(-10) * A13.r + R(-10) * A14.r + R(62) * A15.r + R(62) * A16.r + R(-28) * A17.r + R(8) * A18.r + R(-1) * A19.r + R(80) * A20.r + R(-10) * A21.r + R(71) * A22.r + R(62) * A23.r; const R zi = R(512) * R(0.5) * A1.i + R(8) * A2.i + R(80) * A3.i + R(-64) * A4.i + R(8) * A5.i + R(8) * A6.i + R(-64) * A7.i + R(-1) * A8.i + R(-10) * A9.i + R(8) * A10.i + R(-1) * A11.i + R(-1) * A12.i + R(-10) * A13.i + R(-10) * A14.i + R(62) * A15.i + R(62) * A16.i + R(-28) * A17.i + R(8) * A18.i + R(-1) * A19.i + R(80) * A20.i + R(-10) * A21.i + R(71) * A22.i + R(62) * A23.i;
-                  cs += A1.r * zr + A1.i * zi; }
-                { const R zr = R(512) * R(0.5) * A2.r + R(-64) * A3.r + R(80) * A4.r + R(8) * A5.r + R(8) * A6.r + R(-1) * A7.r + R(80) * A8.r + R(-10) * A9.r + R(71) * A10.r + R(62) * A11.r + R(-64) * A12.r + R(8) * A13.r + R(8) * A14.r + R(-1) * A15.r + R(-1) * A16.r + R(-10) * A17.r + R(-10) * A18.r + R(-1) * A19.r + R(62) * A20.r + R(-28) * A21.r + R(-10) * A22.r + R(62) * A23.r; const R zi = R(512) * R(0.5) * A2.i + R(-64) * A3.i + R(80) * A4.i + R(8) * A5.i + R(8) * A6.i + R(-1) * A7.i + R(80) * A8.i + R(-10) * A9.i + R(71) * A10.i + R(62) * A11.i + R(-64) * A12.i + R(8) * A13.i + R(8) * A14.i + R(-1) * A15.i + R(-1) * A16.i + R(-10) * A17.i + R(-10) * A18.i + R(-1) * A19.i + R(62) * A20.i + R(-28) * A21.i + R(-10) * A22.i + R(62) * A23.i;
-                  cs += A2.r * zr + A2.i * zi; }
-                { const R zr = R(512) * R(0.5) * A3.r + R(8) * A4.r + R(-64) * A5.r + R(-1) * A6.r + R(-10) * A7.r + R(-10) * A8.r + R(62) * A9.r + R(62) * A10.r + R(-28) * A11.r + R(8) * A12.r + R(-64) * A13.r + R(-1) * A14.r + R(-10) * A15.r + R(8) * A16.r + R(-1) * A17.r + R(-1) * A18.r + R(8) * A19.r + R(71) * A20.r + R(62) * A21.r + R(80) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A3.i + R(8) * A4.i + R(-64) * A5.i + R(-1) * A6.i + R(-10) * A7.i + R(-10) * A8.i + R(62) * A9.i + R(62) * A10.i + R(-28) * A11.i + R(8) * A12.i + R(-64) * A13.i + R(-1) * A14.i + R(-10) * A15.i + R(8) * A16.i + R(-1) * A17.i + R(-1) * A18.i + R(8) * A19.i + R(71) * A20.i + R(62) * A21.i + R(80) * A22.i + R(-10) * A23.i;
-                  cs += A3.r * zr + A3.i * zi; }
-                { const R zr = R(512) * R(0.5) * A4.r + R(-64) * A5.r + R(-1) * A6.r + R(8) * A7.r + R(71) * A8.r + R(62) * A9.r + R(80) * A10.r + R(-10) * A11.r + R(-10) * A12.r + R(-1) * A13.r + R(62) * A14.r + R(-28) * A15.r + R(-10) * A16.r + R(62) * A17.r + R(-64) * A18.r + R(8) * A19.r + R(8) * A20.r + R(-1) * A21.r + R(-1) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A4.i + R(-64) * A5.i + R(-1) * A6.i + R(8) * A7.i + R(71) * A8.i + R(62) * A9.i + R(80) * A10.i + R(-10) * A11.i + R(-10) * A12.i + R(-1) * A13.i + R(62) * A14.i + R(-28) * A15.i + R(-10) * A16.i + R(62) * A17.i + R(-64) * A18.i + R(8) * A19.i + R(8) * A20.i + R(-1) * A21.i + R(-1) * A22.i + R(-10) * A23.i;
-                  cs += A4.r * zr + A4.i * zi; }
-                { const R zr = R(512) * R(0.5) * A5.r + R(-10) * A6.r + R(-1) * A7.r + R(62) * A8.r + R(-28) * A9.r + R(-10) * A10.r + R(62) * A11.r + R(-1) * A12.r + R(8) * A13.r + R(71) * A14.r + R(62) * A15.r + R(80) * A16.r + R(-10) * A17.r + R(8) * A18.r + R(-64) * A19.r + R(-1) * A20.r + R(-10) * A21.r + R(8) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A5.i + R(-10) * A6.i + R(-1) * A7.i + R(62) * A8.i + R(-28) * A9.i + R(-10) * A10.i + R(62) * A11.i + R(-1) * A12.i + R(8) * A13.i + R(71) * A14.i + R(62) * A15.i + R(80) * A16.i + R(-10) * A17.i + R(8) * A18.i + R(-64) * A19.i + R(-1) * A20.i + R(-10) * A21.i + R(8) * A22.i + R(-1) * A23.i;
-                  cs += A5.r * zr + A5.i * zi; }
-                { const R zr = R(512) * R(0.5) * A6.r + R(-64) * A7.r + R(-64) * A8.r + R(8) * A9.r + R(8) * A10.r + R(80) * A11.r + R(80) * A12.r + R(-10) * A13.r + R(8) * A14.r + R(-1) * A15.r + R(62) * A16.r + R(71) * A17.r + R(-10) * A18.r + R(62) * A19.r + R(-1) * A20.r + R(-10) * A21.r + R(-28) * A22.r + R(62) * A23.r; const R zi = R(512) * R(0.5) * A6.i + R(-64) * A7.i + R(-64) * A8.i + R(8) * A9.i + R(8) * A10.i + R(80) * A11.i + R(80) * A12.i + R(-10) * A13.i + R(8) * A14.i + R(-1) * A15.i + R(62) * A16.i + R(71) * A17.i + R(-10) * A18.i + R(62) * A19.i + R(-1) * A20.i + R(-10) * A21.i + R(-28) * A22.i + R(62) * A23.i;
-                  cs += A6.r * zr + A6.i * zi; }
-                { const R zr = R(512) * R(0.5) * A7.r + R(8) * A8.r + R(80) * A9.r + R(-64) * A10.r + R(8) * A11.r + R(-10) * A12.r + R(62) * A13.r + R(-1) * A14.r + R(-10) * A15.r + R(-28) * A16.r + R(62) * A17.r + R(80) * A18.r + R(-10) * A19.r + R(8) * A20.r + R(-1) * A21.r + R(62) * A22.r + R(71) * A23.r; const R zi = R(512) * R(0.5) * A7.i + R(8) * A8.i + R(80) * A9.i + R(-64) * A10.i + R(8) * A11.i + R(-10) * A12.i + R(62) * A13.i + R(-1) * A14.i + R(-10) * A15.i + R(-28) * A16.i + R(62) * A17.i + R(80) * A18.i + R(-10) * A19.i + R(8) * A20.i + R(-1) * A21.i + R(62) * A22.i + R(71) * A23.i;
-                  cs += A7.r * zr + A7.i * zi; }
-                { const R zr = R(512) * R(0.5) * A8.r + R(-64) * A9.r + R(80) * A10.r + R(8) * A11.r + R(8) * A12.r + R(-1) * A13.r + R(-64) * A14.r + R(8) * A15.r + R(-10) * A16.r + R(-1) * A17.r + R(62) * A18.r + R(-28) * A19.r + R(-10) * A20.r + R(-1) * A21.r + R(62) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A8.i + R(-64) * A9.i + R(80) * A10.i + R(8) * A11.i + R(8) * A12.i + R(-1) * A13.i + R(-64) * A14.i + R(8) * A15.i + R(-10) * A16.i + R(-1) * A17.i + R(62) * A18.i + R(-28) * A19.i + R(-10) * A20.i + R(-1) * A21.i + R(62) * A22.i + R(-10) * A23.i;
-                  cs += A8.r * zr + A8.i * zi; }
-                { const R zr = R(512) * R(0.5) * A9.r + R(8) * A10.r + R(-64) * A11.r + R(-1) * A12.r + R(-10) * A13.r + R(8) * A14.r + R(-64) * A15.r + R(-1) * A16.r + R(8) * A17.r + R(71) * A18.r + R(62) * A19.r + R(-1) * A20.r + R(8) * A21.r + R(-10) * A22.r + R(80) * A23.r; const R zi = R(512) * R(0.5) * A9.i + R(8) * A10.i + R(-64) * A11.i + R(-1) * A12.i + R(-10) * A13.i + R(8) * A14.i + R(-64) * A15.i + R(-1) * A16.i + R(8) * A17.i + R(71) * A18.i + R(62) * A19.i + R(-1) * A20.i + R(8) * A21.i + R(-10) * A22.i + R(80) * A23.i;
-                  cs += A9.r * zr + A9.i * zi; }
-                { const R zr = R(512) * R(0.5) * A10.r + R(-64) * A11.r + R(62) * A12.r + R(-28) * A13.r + R(-10) * A14.r + R(-1) * A15.r + R(62) * A16.r + R(-10) * A17.r + R(8) * A18.r + R(-1) * A19.r + R(-64) * A20.r + R(8) * A21.r + R(-10) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A10.i + R(-64) * A11.i + R(62) * A12.i + R(-28) * A13.i + R(-10) * A14.i + R(-1) * A15.i + R(62) * A16.i + R(-10) * A17.i + R(8) * A18.i + R(-1) * A19.i + R(-64) * A20.i + R(8) * A21.i + R(-10) * A22.i + R(-1) * A23.i;
-                  cs += A10.r * zr + A10.i * zi; }
-                { const R zr = R(512) * R(0.5) * A11.r + R(71) * A12.r + R(62) * A13.r + R(-1) * A14.r + R(8) * A15.r + R(-10) * A16.r + R(80) * A17.r + R(-1) * A18.r + R(-10) * A19.r + R(8) * A20.r + R(-64) * A21.r + R(-1) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A11.i + R(71) * A12.i + R(62) * A13.i + R(-1) * A14.i + R(8) * A15.i + R(-10) * A16.i + R(80) * A17.i + R(-1) * A18.i + R(-10) * A19.i + R(8) * A20.i + R(-64) * A21.i + R(-1) * A22.i + R(8) * A23.i;
-                  cs += A11.r * zr + A11.i * zi; }
-                { const R zr = R(512) * R(0.5) * A12.r + R(-64) * A13.r + R(-64) * A14.r + R(8) * A15.r + R(8) * A16.r + R(80) * A17.r + R(62) * A18.r + R(-10) * A19.r + R(-28) * A20.r + R(62) * A21.r + R(-1) * A22.r + R(-10) * A23.r; const R zi = R(512) * R(0.5) * A12.i + R(-64) * A13.i + R(-64) * A14.i + R(8) * A15.i + R(8) * A16.i + R(80) * A17.i + R(62) * A18.i + R(-10) * A19.i + R(-28) * A20.i + R(62) * A21.i + R(-1) * A22.i + R(-10) * A23.i;
-                  cs += A12.r * zr + A12.i * zi; }
-                { const R zr = R(512) * R(0.5) * A13.r + R(8) * A14.r + R(80) * A15.r + R(-64) * A16.r + R(8) * A17.r + R(-10) * A18.r + R(80) * A19.r + R(62) * A20.r + R(71) * A21.r + R(8) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A13.i + R(8) * A14.i + R(80) * A15.i + R(-64) * A16.i + R(8) * A17.i + R(-10) * A18.i + R(80) * A19.i + R(62) * A20.i + R(71) * A21.i + R(8) * A22.i + R(-1) * A23.i;
-                  cs += A13.r * zr + A13.i * zi; }
-                { const R zr = R(512) * R(0.5) * A14.r + R(-64) * A15.r + R(80) * A16.r + R(8) * A17.r + R(-28) * A18.r + R(62) * A19.r + R(62) * A20.r + R(-10) * A21.r + R(-10) * A22.r + R(-1) * A23.r; const R zi = R(512) * R(0.5) * A14.i + R(-64) * A15.i + R(80) * A16.i + R(8) * A17.i + R(-28) * A18.i + R(62) * A19.i + R(62) * A20.i + R(-10) * A21.i + R(-10) * A22.i + R(-1) * A23.i;
-                  cs += A14.r * zr + A14.i * zi; }
-                { const R zr = R(512) * R(0.5) * A15.r + R(8) * A16.r + R(-64) * A17.r + R(62) * A18.r + R(71) * A19.r + R(-10) * A20.r + R(80) * A21.r + R(-1) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A15.i + R(8) * A16.i + R(-64) * A17.i + R(62) * A18.i + R(71) * A19.i + R(-10) * A20.i + R(80) * A21.i + R(-1) * A22.i + R(8) * A23.i;
-                  cs += A15.r * zr + A15.i * zi; }
-                { const R zr = R(512) * R(0.5) * A16.r + R(-64) * A17.r + R(-1) * A18.r + R(8) * A19.r + R(-10) * A20.r + R(-1) * A21.r + R(-64) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A16.i + R(-64) * A17.i + R(-1) * A18.i + R(8) * A19.i + R(-10) * A20.i + R(-1) * A21.i + R(-64) * A22.i + R(8) * A23.i;
-                  cs += A16.r * zr + A16.i * zi; }
-                { const R zr = R(512) * R(0.5) * A17.r + R(-10) * A18.r + R(-1) * A19.r + R(-1) * A20.r + R(8) * A21.r + R(8) * A22.r + R(-64) * A23.r; const R zi = R(512) * R(0.5) * A17.i + R(-10) * A18.i + R(-1) * A19.i + R(-1) * A20.i + R(8) * A21.i + R(8) * A22.i + R(-64) * A23.i;
-                  cs += A17.r * zr + A17.i * zi; }
-                { const R zr = R(512) * R(0.5) * A18.r + R(-64) * A19.r + R(-64) * A20.r + R(8) * A21.r + R(8) * A22.r + R(80) * A23.r; const R zi = R(512) * R(0.5) * A18.i + R(-64) * A19.i + R(-64) * A20.i + R(8) * A21.i + R(8) * A22.i + R(80) * A23.i;
-                  cs += A18.r * zr + A18.i * zi; }
-                { const R zr = R(512) * R(0.5) * A19.r + R(8) * A20.r + R(80) * A21.r + R(-64) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A19.i + R(8) * A20.i + R(80) * A21.i + R(-64) * A22.i + R(8) * A23.i;
-                  cs += A19.r * zr + A19.i * zi; }
-                { const R zr = R(512) * R(0.5) * A20.r + R(-64) * A21.r + R(80) * A22.r + R(8) * A23.r; const R zi = R(512) * R(0.5) * A20.i + R(-64) * A21.i + R(80) * A22.i + R(8) * A23.i;
-                  cs += A20.r * zr + A20.i * zi; }
-                { const R zr = R(512) * R(0.5) * A21.r + R(8) * A22.r + R(-64) * A23.r; const R zi = R(512) * R(0.5) * A21.i + R(8) * A22.i + R(-64) * A23.i;
-                  cs += A21.r * zr + A21.i * zi; }
-                { const R zr = R(512) * R(0.5) * A22.r + R(-64) * A23.r; const R zi = R(512) * R(0.5) * A22.i + R(-64) * A23.i;
-                  cs += A22.r * zr + A22.i * zi; }
-                { const R zr = R(512) * R(0.5) * A23.r; const R zi = R(512) * R(0.5) * A23.i;
-                  cs += A23.r * zr + A23.i * zi; }
-                acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
-              }
+            const cx<R> A23_0 = rowcol(X.ub[0], X23), A23_1 = rowcol(X.ub[1], X23);
+            sp<R> tS_3_1_0 = slash(E3, S_1_0);
+            slash_acc(tS_3_1_0, J3_1, S_0);
+            slash_acc(tS_3_1_0, J3_1_0, S_E);
+            const sp<R> S_3_1_0 = fprop(Kn.qc[11], Kn.mc[11], tS_3_1_0);
+            sp<R> X17 = slash(E2, S_3_1_0);
+            slash_acc(X17, J2_3, S_1_0);
+            slash_acc(X17, J2_3_1, S_0);
+            slash_acc(X17, J2_3_1_0, S_E);
+            const cx<R> A17_0 = rowcol(X.ub[0], X17), A17_1 = rowcol(X.ub[1], X17);
+            sp<R> tS_2_0 = slash(E2, S_0);
+            slash_acc(tS_2_0, J2_0, S_E);
+            const sp<R> S_2_0 = fprop(Kn.qc[5], Kn.mc[5], tS_2_0);
+            sp<R> tS_1_2_0 = slash(E1, S_2_0);
+            slash_acc(tS_1_2_0, J1_2, S_0);
+            slash_acc(tS_1_2_0, J1_2_0, S_E);
+            const sp<R> S_1_2_0 = fprop(Kn.qc[7], Kn.mc[7], tS_1_2_0);
+            sp<R> X21 = slash(E3, S_1_2_0);
+            slash_acc(X21, J3_1, S_2_0);
+            slash_acc(X21, J3_1_2, S_0);
+            slash_acc(X21, J3_1_2_0, S_E);
+            const cx<R> A21_0 = rowcol(X.ub[0], X21), A21_1 = rowcol(X.ub[1], X21);
+            sp<R> tS_3_2_0 = slash(E3, S_2_0);
+            slash_acc(tS_3_2_0, J3_2, S_0);
+            slash_acc(tS_3_2_0, J3_2_0, S_E);
+            const sp<R> S_3_2_0 = fprop(Kn.qc[13], Kn.mc[13], tS_3_2_0);
+            sp<R> X11 = slash(E1, S_3_2_0);
+            slash_acc(X11, J1_3, S_2_0);
+            slash_acc(X11, J1_3_2, S_0);
+            slash_acc(X11, J1_3_2_0, S_E);
+            const cx<R> A11_0 = rowcol(X.ub[0], X11), A11_1 = rowcol(X.ub[1], X11);
+            sp<R> tS_3_0 = slash(E3, S_0);
+            slash_acc(tS_3_0, J3_0, S_E);
+            const sp<R> S_3_0 = fprop(Kn.qc[9], Kn.mc[9], tS_3_0);
+            sp<R> tS_1_3_0 = slash(E1, S_3_0);
+            slash_acc(tS_1_3_0, J1_3, S_0);
+            slash_acc(tS_1_3_0, J1_3_0, S_E);
+            const sp<R> S_1_3_0 = fprop(Kn.qc[11], Kn.mc[11], tS_1_3_0);
+            sp<R> X15 = slash(E2, S_1_3_0);
+            slash_acc(X15, J2_1, S_3_0);
+            slash_acc(X15, J2_1_3, S_0);
+            slash_acc(X15, J2_1_3_0, S_E);
+            const cx<R> A15_0 = rowcol(X.ub[0], X15), A15_1 = rowcol(X.ub[1], X15);
+            sp<R> tS_2_3_0 = slash(E2, S_3_0);
+            slash_acc(tS_2_3_0, J2_3, S_0);
+            slash_acc(tS_2_3_0, J2_3_0, S_E);
+            const sp<R> S_2_3_0 = fprop(Kn.qc[13], Kn.mc[13], tS_2_3_0);
+            sp<R> X9 = slash(E1, S_2_3_0);
+            slash_acc(X9, J1_2, S_3_0);
+            slash_acc(X9, J1_2_3, S_0);
+            slash_acc(X9, J1_2_3_0, S_E);
+            const cx<R> A9_0 = rowcol(X.ub[0], X9), A9_1 = rowcol(X.ub[1], X9);
+            sp<R> tS_1 = slash(E1, S_E);
+            const sp<R> S_1 = fprop(Kn.qc[2], Kn.mc[2], tS_1);
+            sp<R> tS_0_1 = slash(E0, S_1);
+            slash_acc(tS_0_1, J0_1, S_E);
+            const sp<R> S_0_1 = fprop(Kn.qc[3], Kn.mc[3], tS_0_1);
+            sp<R> tS_2_0_1 = slash(E2, S_0_1);
+            slash_acc(tS_2_0_1, J2_0, S_1);
+            slash_acc(tS_2_0_1, J2_0_1, S_E);
+            const sp<R> S_2_0_1 = fprop(Kn.qc[7], Kn.mc[7], tS_2_0_1);
+            sp<R> X22 = slash(E3, S_2_0_1);
+            slash_acc(X22, J3_2, S_0_1);
+            slash_acc(X22, J3_2_0, S_1);
+            slash_acc(X22, J3_2_0_1, S_E);
+            const cx<R> A22_0 = rowcol(X.ub[0], X22), A22_1 = rowcol(X.ub[1], X22);
+            sp<R> tS_3_0_1 = slash(E3, S_0_1);
+            slash_acc(tS_3_0_1, J3_0, S_1);
+            slash_acc(tS_3_0_1, J3_0_1, S_E);
+            const sp<R> S_3_0_1 = fprop(Kn.qc[11], Kn.mc[11], tS_3_0_1);
+            sp<R> X16 = slash(E2, S_3_0_1);
+            slash_acc(X16, J2_3, S_0_1);
+            slash_acc(X16, J2_3_0, S_1);
+            slash_acc(X16, J2_3_0_1, S_E);
+            const cx<R> A16_0 = rowcol(X.ub[0], X16), A16_1 = rowcol(X.ub[1], X16);
+            sp<R> tS_2_1 = slash(E2, S_1);
+            slash_acc(tS_2_1, J2_1, S_E);
+            const sp<R> S_2_1 = fprop(Kn.qc[6], Kn.mc[6], tS_2_1);
+            sp<R> tS_0_2_1 = slash(E0, S_2_1);
+            slash_acc(tS_0_2_1, J0_2, S_1);
+            slash_acc(tS_0_2_1, J0_2_1, S_E);
+            const sp<R> S_0_2_1 = fprop(Kn.qc[7], Kn.mc[7], tS_0_2_1);
+            sp<R> X19 = slash(E3, S_0_2_1);
+            slash_acc(X19, J3_0, S_2_1);
+            slash_acc(X19, J3_0_2, S_1);
+            slash_acc(X19, J3_0_2_1, S_E);
+            const cx<R> A19_0 = rowcol(X.ub[0], X19), A19_1 = rowcol(X.ub[1], X19);
+            sp<R> tS_3_2_1 = slash(E3, S_2_1);
+            slash_acc(tS_3_2_1, J3_2, S_1);
+            slash_acc(tS_3_2_1, J3_2_1, S_E);
+            const sp<R> S_3_2_1 = fprop(Kn.qc[14], Kn.mc[14], tS_3_2_1);
+            sp<R> X5 = slash(E0, S_3_2_1);
+            slash_acc(X5, J0_3, S_2_1);
+            slash_acc(X5, J0_3_2, S_1);
+            slash_acc(X5, J0_3_2_1, S_E);
+            const cx<R> A5_0 = rowcol(X.ub[0], X5), A5_1 = rowcol(X.ub[1], X5);
+            sp<R> tS_3_1 = slash(E3, S_1);
+            slash_acc(tS_3_1, J3_1, S_E);
+            const sp<R> S_3_1 = fprop(Kn.qc[10], Kn.mc[10], tS_3_1);
+            sp<R> tS_0_3_1 = slash(E0, S_3_1);
+            slash_acc(tS_0_3_1, J0_3, S_1);
+            slash_acc(tS_0_3_1, J0_3_1, S_E);
+            const sp<R> S_0_3_1 = fprop(Kn.qc[11], Kn.mc[11], tS_0_3_1);
+            sp<R> X13 = slash(E2, S_0_3_1);
+            slash_acc(X13, J2_0, S_3_1);
+            slash_acc(X13, J2_0_3, S_1);
+            slash_acc(X13, J2_0_3_1, S_E);
+            const cx<R> A13_0 = rowcol(X.ub[0], X13), A13_1 = rowcol(X.ub[1], X13);
+            sp<R> tS_2_3_1 = slash(E2, S_3_1);
+            slash_acc(tS_2_3_1, J2_3, S_1);
+            slash_acc(tS_2_3_1, J2_3_1, S_E);
+            const sp<R> S_2_3_1 = fprop(Kn.qc[14], Kn.mc[14], tS_2_3_1);
+            sp<R> X3 = slash(E0, S_2_3_1);
+            slash_acc(X3, J0_2, S_3_1);
+            slash_acc(X3, J0_2_3, S_1);
+            slash_acc(X3, J0_2_3_1, S_E);
+            const cx<R> A3_0 = rowcol(X.ub[0], X3), A3_1 = rowcol(X.ub[1], X3);
+            sp<R> tS_2 = slash(E2, S_E);
+            const sp<R> S_2 = fprop(Kn.qc[4], Kn.mc[4], tS_2);
+            sp<R> tS_0_2 = slash(E0, S_2);
+            slash_acc(tS_0_2, J0_2, S_E);
+            const sp<R> S_0_2 = fprop(Kn.qc[5], Kn.mc[5], tS_0_2);
+            sp<R> tS_1_0_2 = slash(E1, S_0_2);
+            slash_acc(tS_1_0_2, J1_0, S_2);
+            slash_acc(tS_1_0_2, J1_0_2, S_E);
+            const sp<R> S_1_0_2 = fprop(Kn.qc[7], Kn.mc[7], tS_1_0_2);
+            sp<R> X20 = slash(E3, S_1_0_2);
+            slash_acc(X20, J3_1, S_0_2);
+            slash_acc(X20, J3_1_0, S_2);
+            slash_acc(X20, J3_1_0_2, S_E);
+            const cx<R> A20_0 = rowcol(X.ub[0], X20), A20_1 = rowcol(X.ub[1], X20);
+            sp<R> tS_3_0_2 = slash(E3, S_0_2);
+            slash_acc(tS_3_0_2, J3_0, S_2);
+            slash_acc(tS_3_0_2, J3_0_2, S_E);
+            const sp<R> S_3_0_2 = fprop(Kn.qc[13], Kn.mc[13], tS_3_0_2);
+            sp<R> X10 = slash(E1, S_3_0_2);
+            slash_acc(X10, J1_3, S_0_2);
+            slash_acc(X10, J1_3_0, S_2);
+            slash_acc(X10, J1_3_0_2, S_E);
+            const cx<R> A10_0 = rowcol(X.ub[0], X10), A10_1 = rowcol(X.ub[1], X10);
+            sp<R> tS_1_2 = slash(E1, S_2);
+            slash_acc(tS_1_2, J1_2, S_E);
+            const sp<R> S_1_2 = fprop(Kn.qc[6], Kn.mc[6], tS_1_2);
+            sp<R> tS_0_1_2 = slash(E0, S_1_2);
+            slash_acc(tS_0_1_2, J0_1, S_2);
+            slash_acc(tS_0_1_2, J0_1_2, S_E);
+            const sp<R> S_0_1_2 = fprop(Kn.qc[7], Kn.mc[7], tS_0_1_2);
+            sp<R> X18 = slash(E3, S_0_1_2);
+            slash_acc(X18, J3_0, S_1_2);
+            slash_acc(X18, J3_0_1, S_2);
+            slash_acc(X18, J3_0_1_2, S_E);
+            const cx<R> A18_0 = rowcol(X.ub[0], X18), A18_1 = rowcol(X.ub[1], X18);
+            sp<R> tS_3_1_2 = slash(E3, S_1_2);
+            slash_acc(tS_3_1_2, J3_1, S_2);
+            slash_acc(tS_3_1_2, J3_1_2, S_E);
+            const sp<R> S_3_1_2 = fprop(Kn.qc[14], Kn.mc[14], tS_3_1_2);
+            sp<R> X4 = slash(E0, S_3_1_2);
+            slash_acc(X4, J0_3, S_1_2);
+            slash_acc(X4, J0_3_1, S_2);
+            slash_acc(X4, J0_3_1_2, S_E);
+            const cx<R> A4_0 = rowcol(X.ub[0], X4), A4_1 = rowcol(X.ub[1], X4);
+            sp<R> tS_3_2 = slash(E3, S_2);
+            slash_acc(tS_3_2, J3_2, S_E);
+            const sp<R> S_3_2 = fprop(Kn.qc[12], Kn.mc[12], tS_3_2);
+            sp<R> tS_0_3_2 = slash(E0, S_3_2);
+            slash_acc(tS_0_3_2, J0_3, S_2);
+            slash_acc(tS_0_3_2, J0_3_2, S_E);
+            const sp<R> S_0_3_2 = fprop(Kn.qc[13], Kn.mc[13], tS_0_3_2);
+            sp<R> X7 = slash(E1, S_0_3_2);
+            slash_acc(X7, J1_0, S_3_2);
+            slash_acc(X7, J1_0_3, S_2);
+            slash_acc(X7, J1_0_3_2, S_E);
+            const cx<R> A7_0 = rowcol(X.ub[0], X7), A7_1 = rowcol(X.ub[1], X7);
+            sp<R> tS_1_3_2 = slash(E1, S_3_2);
+            slash_acc(tS_1_3_2, J1_3, S_2);
+            slash_acc(tS_1_3_2, J1_3_2, S_E);
+            const sp<R> S_1_3_2 = fprop(Kn.qc[14], Kn.mc[14], tS_1_3_2);
+            sp<R> X1 = slash(E0, S_1_3_2);
+            slash_acc(X1, J0_1, S_3_2);
+            slash_acc(X1, J0_1_3, S_2);
+            slash_acc(X1, J0_1_3_2, S_E);
+            const cx<R> A1_0 = rowcol(X.ub[0], X1), A1_1 = rowcol(X.ub[1], X1);
+            sp<R> tS_3 = slash(E3, S_E);
+            const sp<R> S_3 = fprop(Kn.qc[8], Kn.mc[8], tS_3);
+            sp<R> tS_0_3 = slash(E0, S_3);
+            slash_acc(tS_0_3, J0_3, S_E);
+            const sp<R> S_0_3 = fprop(Kn.qc[9], Kn.mc[9], tS_0_3);
+            sp<R> tS_1_0_3 = slash(E1, S_0_3);
+            slash_acc(tS_1_0_3, J1_0, S_3);
+            slash_acc(tS_1_0_3, J1_0_3, S_E);
+            const sp<R> S_1_0_3 = fprop(Kn.qc[11], Kn.mc[11], tS_1_0_3);
+            sp<R> X14 = slash(E2, S_1_0_3);
+            slash_acc(X14, J2_1, S_0_3);
+            slash_acc(X14, J2_1_0, S_3);
+            slash_acc(X14, J2_1_0_3, S_E);
+            const cx<R> A14_0 = rowcol(X.ub[0], X14), A14_1 = rowcol(X.ub[1], X14);
+            sp<R> tS_2_0_3 = slash(E2, S_0_3);
+            slash_acc(tS_2_0_3, J2_0, S_3);
+            slash_acc(tS_2_0_3, J2_0_3, S_E);
+            const sp<R> S_2_0_3 = fprop(Kn.qc[13], Kn.mc[13], tS_2_0_3);
+            sp<R> X8 = slash(E1, S_2_0_3);
+            slash_acc(X8, J1_2, S_0_3);
+            slash_acc(X8, J1_2_0, S_3);
+            slash_acc(X8, J1_2_0_3, S_E);
+            const cx<R> A8_0 = rowcol(X.ub[0], X8), A8_1 = rowcol(X.ub[1], X8);
+            sp<R> tS_1_3 = slash(E1, S_3);
+            slash_acc(tS_1_3, J1_3, S_E);
+            const sp<R> S_1_3 = fprop(Kn.qc[10], Kn.mc[10], tS_1_3);
+            sp<R> tS_0_1_3 = slash(E0, S_1_3);
+            slash_acc(tS_0_1_3, J0_1, S_3);
+            slash_acc(tS_0_1_3, J0_1_3, S_E);
+            const sp<R> S_0_1_3 = fprop(Kn.qc[11], Kn.mc[11], tS_0_1_3);
+            sp<R> X12 = slash(E2, S_0_1_3);
+            slash_acc(X12, J2_0, S_1_3);
+            slash_acc(X12, J2_0_1, S_3);
+            slash_acc(X12, J2_0_1_3, S_E);
+            const cx<R> A12_0 = rowcol(X.ub[0], X12), A12_1 = rowcol(X.ub[1], X12);
+            sp<R> tS_2_1_3 = slash(E2, S_1_3);
+            slash_acc(tS_2_1_3, J2_1, S_3);
+            slash_acc(tS_2_1_3, J2_1_3, S_E);
+            const sp<R> S_2_1_3 = fprop(Kn.qc[14], Kn.mc[14], tS_2_1_3);
+            sp<R> X2 = slash(E0, S_2_1_3);
+            slash_acc(X2, J0_2, S_1_3);
+            slash_acc(X2, J0_2_1, S_3);
+            slash_acc(X2, J0_2_1_3, S_E);
+            const cx<R> A2_0 = rowcol(X.ub[0], X2), A2_1 = rowcol(X.ub[1], X2);
+            sp<R> tS_2_3 = slash(E2, S_3);
+            slash_acc(tS_2_3, J2_3, S_E);
+            const sp<R> S_2_3 = fprop(Kn.qc[12], Kn.mc[12], tS_2_3);
+            sp<R> tS_0_2_3 = slash(E0, S_2_3);
+            slash_acc(tS_0_2_3, J0_2, S_3);
+            slash_acc(tS_0_2_3, J0_2_3, S_E);
+            const sp<R> S_0_2_3 = fprop(Kn.qc[13], Kn.mc[13], tS_0_2_3);
+            sp<R> X6 = slash(E1, S_0_2_3);
+            slash_acc(X6, J1_0, S_2_3);
+            slash_acc(X6, J1_0_2, S_3);
+            slash_acc(X6, J1_0_2_3, S_E);
+            const cx<R> A6_0 = rowcol(X.ub[0], X6), A6_1 = rowcol(X.ub[1], X6);
+            sp<R> tS_1_2_3 = slash(E1, S_2_3);
+            slash_acc(tS_1_2_3, J1_2, S_3);
+            slash_acc(tS_1_2_3, J1_2_3, S_E);
+            const sp<R> S_1_2_3 = fprop(Kn.qc[14], Kn.mc[14], tS_1_2_3);
+            sp<R> X0 = slash(E0, S_1_2_3);
+            slash_acc(X0, J0_1, S_2_3);
+            slash_acc(X0, J0_1_2, S_3);
+            slash_acc(X0, J0_1_2_3, S_E);
+            const cx<R> A0_0 = rowcol(X.ub[0], X0), A0_1 = rowcol(X.ub[1], X0);
+            if constexpr (CM != CM_FMA) {
+              const cx<float> Aa0[K] = {A0_0, A1_0, A2_0, A3_0, A4_0, A5_0, A6_0, A7_0, A8_0, A9_0, A10_0, A11_0, A12_0, A13_0, A14_0, A15_0, A16_0, A17_0, A18_0, A19_0, A20_0, A21_0, A22_0, A23_0};
+              const cx<float> Aa1[K] = {A0_1, A1_1, A2_1, A3_1, A4_1, A5_1, A6_1, A7_1, A8_1, A9_1, A10_1, A11_1, A12_1, A13_1, A14_1, A15_1, A16_1, A17_1, A18_1, A19_1, A20_1, A21_1, A22_1, A23_1};
+              acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip
+            } else {
+              R cs = R(0);
+              { const R zr = R(512) * R(0.5) * A0_0.r + R(-64) * A1_0.r + R(-64) * A2_0.r + R(8) * A3_0.r + R(8) * A4_0.r + R(80) * A5_0.r + R(-64) * A6_0.r + R(8) * A7_0.r + R(8) * A8_0.r + R(-1) * A9_0.r + R(-1) * A10_0.r + R(-10) * A11_0.r + R(8) * A12_0.r + R(-1) * A13_0.r + R(80) * A14_0.r + R(-10) * A15_0.r + R(71) * A16_0.r + R(62) * A17_0.r + R(-1) * A18_0.r + R(-10) * A19_0.r + R(-10) * A20_0.r + R(62) * A21_0.r + R(62) * A22_0.r + R(-28) * A23_0.r; const R zi = R(512) * R(0.5) * A0_0.i + R(-64) * A1_0.i + R(-64) * A2_0.i + R(8) * A3_0.i + R(8) * A4_0.i + R(80) * A5_0.i + R(-64) * A6_0.i + R(8) * A7_0.i + R(8) * A8_0.i + R(-1) * A9_0.i + R(-1) * A10_0.i + R(-10) * A11_0.i + R(8) * A12_0.i + R(-1) * A13_0.i + R(80) * A14_0.i + R(-10) * A15_0.i + R(71) * A16_0.i + R(62) * A17_0.i + R(-1) * A18_0.i + R(-10) * A19_0.i + R(-10) * A20_0.i + R(62) * A21_0.i + R(62) * A22_0.i + R(-28) * A23_0.i;
+                cs += A0_0.r * zr + A0_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A1_0.r + R(8) * A2_0.r + R(80) * A3_0.r + R(-64) * A4_0.r + R(8) * A5_0.r + R(8) * A6_0.r + R(-64) * A7_0.r + R(-1) * A8_0.r + R(-10) * A9_0.r + R(8) * A10_0.r + R(-1) * A11_0.r + R(-1) * A12_0.r + R(-10) * A13_0.r + R(-10) * A14_0.r + R(62) * A15_0.r + R(62) * A16_0.r + R(-28) * A17_0.r + R(8) * A18_0.r + R(-1) * A19_0.r + R(80) * A20_0.r + R(-10) * A21_0.r + R(71) * A22_0.r + R(62) * A23_0.r; const R zi = R(512) * R(0.5) * A1_0.i + R(8) * A2_0.i + R(80) * A3_0.i + R(-64) * A4_0.i + R(8) * A5_0.i + R(8) * A6_0.i + R(-64) * A7_0.i + R(-1) * A8_0.i + R(-10) * A9_0.i + R(8) * A10_0.i + R(-1) * A11_0.i + R(-1) * A12_0.i + R(-10) * A13_0.i + R(-10) * A14_0.i + R(62) * A15_0.i + R(62) * A16_0.i + R(-28) * A17_0.i + R(8) * A18_0.i + R(-1) * A19_0.i + R(80) * A20_0.i + R(-10) * A21_0.i + R(71) * A22_0.i + R(62) * A23_0.i;
+                cs += A1_0.r * zr + A1_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A2_0.r + R(-64) * A3_0.r + R(80) * A4_0.r + R(8) * A5_0.r + R(8) * A6_0.r + R(-1) * A7_0.r + R(80) * A8_0.r + R(-10) * A9_0.r + R(71) * A10_0.r + R(62) * A11_0.r + R(-64) * A12_0.r + R(8) * A13_0.r + R(8) * A14_0.r + R(-1) * A15_0.r + R(-1) * A16_0.r + R(-10) * A17_0.r + R(-10) * A18_0.r + R(-1) * A19_0.r + R(62) * A20_0.r + R(-28) * A21_0.r + R(-10) * A22_0.r + R(62) * A23_0.r; const R zi = R(512) * R(0.5) * A2_0.i + R(-64) * A3_0.i + R(80) * A4_0.i + R(8) * A5_0.i + R(8) * A6_0.i + R(-1) * A7_0.i + R(80) * A8_0.i + R(-10) * A9_0.i + R(71) * A10_0.i + R(62) * A11_0.i + R(-64) * A12_0.i + R(8) * A13_0.i + R(8) * A14_0.i + R(-1) * A15_0.i + R(-1) * A16_0.i + R(-10) * A17_0.i + R(-10) * A18_0.i + R(-1) * A19_0.i + R(62) * A20_0.i + R(-28) * A21_0.i + R(-10) * A22_0.i + R(62) * A23_0.i;
+                cs += A2_0.r * zr + A2_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A3_0.r + R(8) * A4_0.r + R(-64) * A5_0.r + R(-1) * A6_0.r + R(-10) * A7_0.r + R(-10) * A8_0.r + R(62) * A9_0.r + R(62) * A10_0.r + R(-28) * A11_0.r + R(8) * A12_0.r + R(-64) * A13_0.r + R(-1) * A14_0.r + R(-10) * A15_0.r + R(8) * A16_0.r + R(-1) * A17_0.r + R(-1) * A18_0.r + R(8) * A19_0.r + R(71) * A20_0.r + R(62) * A21_0.r + R(80) * A22_0.r + R(-10) * A23_0.r; const R zi = R(512) * R(0.5) * A3_0.i + R(8) * A4_0.i + R(-64) * A5_0.i + R(-1) * A6_0.i + R(-10) * A7_0.i + R(-10) * A8_0.i + R(62) * A9_0.i + R(62) * A10_0.i + R(-28) * A11_0.i + R(8) * A12_0.i + R(-64) * A13_0.i + R(-1) * A14_0.i + R(-10) * A15_0.i + R(8) * A16_0.i + R(-1) * A17_0.i + R(-1) * A18_0.i + R(8) * A19_0.i + R(71) * A20_0.i + R(62) * A21_0.i + R(80) * A22_0.i + R(-10) * A23_0.i;
+                cs += A3_0.r * zr + A3_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A4_0.r + R(-64) * A5_0.r + R(-1) * A6_0.r + R(8) * A7_0.r + R(71) * A8_0.r + R(62) * A9_0.r + R(80) * A10_0.r + R(-10) * A11_0.r + R(-10) * A12_0.r + R(-1) * A13_0.r + R(62) * A14_0.r + R(-28) * A15_0.r + R(-10) * A16_0.r + R(62) * A17_0.r + R(-64) * A18_0.r + R(8) * A19_0.r + R(8) * A20_0.r + R(-1) * A21_0.r + R(-1) * A22_0.r + R(-10) * A23_0.r; const R zi = R(512) * R(0.5) * A4_0.i + R(-64) * A5_0.i + R(-1) * A6_0.i + R(8) * A7_0.i + R(71) * A8_0.i + R(62) * A9_0.i + R(80) * A10_0.i + R(-10) * A11_0.i + R(-10) * A12_0.i + R(-1) * A13_0.i + R(62) * A14_0.i + R(-28) * A15_0.i + R(-10) * A16_0.i + R(62) * A17_0.i + R(-64) * A18_0.i + R(8) * A19_0.i + R(8) * A20_0.i + R(-1) * A21_0.i + R(-1) * A22_0.i + R(-10) * A23_0.i;
+                cs += A4_0.r * zr + A4_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A5_0.r + R(-10) * A6_0.r + R(-1) * A7_0.r + R(62) * A8_0.r + R(-28) * A9_0.r + R(-10) * A10_0.r + R(62) * A11_0.r + R(-1) * A12_0.r + R(8) * A13_0.r + R(71) * A14_0.r + R(62) * A15_0.r + R(80) * A16_0.r + R(-10) * A17_0.r + R(8) * A18_0.r + R(-64) * A19_0.r + R(-1) * A20_0.r + R(-10) * A21_0.r + R(8) * A22_0.r + R(-1) * A23_0.r; const R zi = R(512) * R(0.5) * A5_0.i + R(-10) * A6_0.i + R(-1) * A7_0.i + R(62) * A8_0.i + R(-28) * A9_0.i + R(-10) * A10_0.i + R(62) * A11_0.i + R(-1) * A12_0.i + R(8) * A13_0.i + R(71) * A14_0.i + R(62) * A15_0.i + R(80) * A16_0.i + R(-10) * A17_0.i + R(8) * A18_0.i + R(-64) * A19_0.i + R(-1) * A20_0.i + R(-10) * A21_0.i + R(8) * A22_0.i + R(-1) * A23_0.i;
+                cs += A5_0.r * zr + A5_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A6_0.r + R(-64) * A7_0.r + R(-64) * A8_0.r + R(8) * A9_0.r + R(8) * A10_0.r + R(80) * A11_0.r + R(80) * A12_0.r + R(-10) * A13_0.r + R(8) * A14_0.r + R(-1) * A15_0.r + R(62) * A16_0.r + R(71) * A17_0.r + R(-10) * A18_0.r + R(62) * A19_0.r + R(-1) * A20_0.r + R(-10) * A21_0.r + R(-28) * A22_0.r + R(62) * A23_0.r; const R zi = R(512) * R(0.5) * A6_0.i + R(-64) * A7_0.i + R(-64) * A8_0.i + R(8) * A9_0.i + R(8) * A10_0.i + R(80) * A11_0.i + R(80) * A12_0.i + R(-10) * A13_0.i + R(8) * A14_0.i + R(-1) * A15_0.i + R(62) * A16_0.i + R(71) * A17_0.i + R(-10) * A18_0.i + R(62) * A19_0.i + R(-1) * A20_0.i + R(-10) * A21_0.i + R(-28) * A22_0.i + R(62) * A23_0.i;
+                cs += A6_0.r * zr + A6_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A7_0.r + R(8) * A8_0.r + R(80) * A9_0.r + R(-64) * A10_0.r + R(8) * A11_0.r + R(-10) * A12_0.r + R(62) * A13_0.r + R(-1) * A14_0.r + R(-10) * A15_0.r + R(-28) * A16_0.r + R(62) * A17_0.r + R(80) * A18_0.r + R(-10) * A19_0.r + R(8) * A20_0.r + R(-1) * A21_0.r + R(62) * A22_0.r + R(71) * A23_0.r; const R zi = R(512) * R(0.5) * A7_0.i + R(8) * A8_0.i + R(80) * A9_0.i + R(-64) * A10_0.i + R(8) * A11_0.i + R(-10) * A12_0.i + R(62) * A13_0.i + R(-1) * A14_0.i + R(-10) * A15_0.i + R(-28) * A16_0.i + R(62) * A17_0.i + R(80) * A18_0.i + R(-10) * A19_0.i + R(8) * A20_0.i + R(-1) * A21_0.i + R(62) * A22_0.i + R(71) * A23_0.i;
+                cs += A7_0.r * zr + A7_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A8_0.r + R(-64) * A9_0.r + R(80) * A10_0.r + R(8) * A11_0.r + R(8) * A12_0.r + R(-1) * A13_0.r + R(-64) * A14_0.r + R(8) * A15_0.r + R(-10) * A16_0.r + R(-1) * A17_0.r + R(62) * A18_0.r + R(-28) * A19_0.r + R(-10) * A20_0.r + R(-1) * A21_0.r + R(62) * A22_0.r + R(-10) * A23_0.r; const R zi = R(512) * R(0.5) * A8_0.i + R(-64) * A9_0.i + R(80) * A10_0.i + R(8) * A11_0.i + R(8) * A12_0.i + R(-1) * A13_0.i + R(-64) * A14_0.i + R(8) * A15_0.i + R(-10) * A16_0.i + R(-1) * A17_0.i + R(62) * A18_0.i + R(-28) * A19_0.i + R(-10) * A20_0.i + R(-1) * A21_0.i + R(62) * A22_0.i + R(-10) * A23_0.i;
+                cs += A8_0.r * zr + A8_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A9_0.r + R(8) * A10_0.r + R(-64) * A11_0.r + R(-1) * A12_0.r + R(-10) * A13_0.r + R(8) * A14_0.r + R(-64) * A15_0.r + R(-1) * A16_0.r + R(8) * A17_0.r + R(71) * A18_0.r + R(62) * A19_0.r + R(-1) * A20_0.r + R(8) * A21_0.r + R(-10) * A22_0.r + R(80) * A23_0.r; const R zi = R(512) * R(0.5) * A9_0.i + R(8) * A10_0.i + R(-64) * A11_0.i + R(-1) * A12_0.i + R(-10) * A13_0.i + R(8) * A14_0.i + R(-64) * A15_0.i + R(-1) * A16_0.i + R(8) * A17_0.i + R(71) * A18_0.i + R(62) * A19_0.i + R(-1) * A20_0.i + R(8) * A21_0.i + R(-10) * A22_0.i + R(80) * A23_0.i;
+                cs += A9_0.r * zr + A9_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A10_0.r + R(-64) * A11_0.r + R(62) * A12_0.r + R(-28) * A13_0.r + R(-10) * A14_0.r + R(-1) * A15_0.r + R(62) * A16_0.r + R(-10) * A17_0.r + R(8) * A18_0.r + R(-1) * A19_0.r + R(-64) * A20_0.r + R(8) * A21_0.r + R(-10) * A22_0.r + R(-1) * A23_0.r; const R zi = R(512) * R(0.5) * A10_0.i + R(-64) * A11_0.i + R(62) * A12_0.i + R(-28) * A13_0.i + R(-10) * A14_0.i + R(-1) * A15_0.i + R(62) * A16_0.i + R(-10) * A17_0.i + R(8) * A18_0.i + R(-1) * A19_0.i + R(-64) * A20_0.i + R(8) * A21_0.i + R(-10) * A22_0.i + R(-1) * A23_0.i;
+                cs += A10_0.r * zr + A10_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A11_0.r + R(71) * A12_0.r + R(62) * A13_0.r + R(-1) * A14_0.r + R(8) * A15_0.r + R(-10) * A16_0.r + R(80) * A17_0.r + R(-1) * A18_0.r + R(-10) * A19_0.r + R(8) * A20_0.r + R(-64) * A21_0.r + R(-1) * A22_0.r + R(8) * A23_0.r; const R zi = R(512) * R(0.5) * A11_0.i + R(71) * A12_0.i + R(62) * A13_0.i + R(-1) * A14_0.i + R(8) * A15_0.i + R(-10) * A16_0.i + R(80) * A17_0.i + R(-1) * A18_0.i + R(-10) * A19_0.i + R(8) * A20_0.i + R(-64) * A21_0.i + R(-1) * A22_0.i + R(8) * A23_0.i;
+                cs += A11_0.r * zr + A11_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A12_0.r + R(-64) * A13_0.r + R(-64) * A14_0.r + R(8) * A15_0.r + R(8) * A16_0.r + R(80) * A17_0.r + R(62) * A18_0.r + R(-10) * A19_0.r + R(-28) * A20_0.r + R(62) * A21_0.r + R(-1) * A22_0.r + R(-10) * A23_0.r; const R zi = R(512) * R(0.5) * A12_0.i + R(-64) * A13_0.i + R(-64) * A14_0.i + R(8) * A15_0.i + R(8) * A16_0.i + R(80) * A17_0.i + R(62) * A18_0.i + R(-10) * A19_0.i + R(-28) * A20_0.i + R(62) * A21_0.i + R(-1) * A22_0.i + R(-10) * A23_0.i;
+                cs += A12_0.r * zr + A12_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A13_0.r + R(8) * A14_0.r + R(80) * A15_0.r + R(-64) * A16_0.r + R(8) * A17_0.r + R(-10) * A18_0.r + R(80) * A19_0.r + R(62) * A20_0.r + R(71) * A21_0.r + R(8) * A22_0.r + R(-1) * A23_0.r; const R zi = R(512) * R(0.5) * A13_0.i + R(8) * A14_0.i + R(80) * A15_0.i + R(-64) * A16_0.i + R(8) * A17_0.i + R(-10) * A18_0.i + R(80) * A19_0.i + R(62) * A20_0.i + R(71) * A21_0.i + R(8) * A22_0.i + R(-1) * A23_0.i;
+                cs += A13_0.r * zr + A13_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A14_0.r + R(-64) * A15_0.r + R(80) * A16_0.r + R(8) * A17_0.r + R(-28) * A18_0.r + R(62) * A19_0.r + R(62) * A20_0.r + R(-10) * A21_0.r + R(-10) * A22_0.r + R(-1) * A23_0.r; const R zi = R(512) * R(0.5) * A14_0.i + R(-64) * A15_0.i + R(80) * A16_0.i + R(8) * A17_0.i + R(-28) * A18_0.i + R(62) * A19_0.i + R(62) * A20_0.i + R(-10) * A21_0.i + R(-10) * A22_0.i + R(-1) * A23_0.i;
+                cs += A14_0.r * zr + A14_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A15_0.r + R(8) * A16_0.r + R(-64) * A17_0.r + R(62) * A18_0.r + R(71) * A19_0.r + R(-10) * A20_0.r + R(80) * A21_0.r + R(-1) * A22_0.r + R(8) * A23_0.r; const R zi = R(512) * R(0.5) * A15_0.i + R(8) * A16_0.i + R(-64) * A17_0.i + R(62) * A18_0.i + R(71) * A19_0.i + R(-10) * A20_0.i + R(80) * A21_0.i + R(-1) * A22_0.i + R(8) * A23_0.i;
+                cs += A15_0.r * zr + A15_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A16_0.r + R(-64) * A17_0.r + R(-1) * A18_0.r + R(8) * A19_0.r + R(-10) * A20_0.r + R(-1) * A21_0.r + R(-64) * A22_0.r + R(8) * A23_0.r; const R zi = R(512) * R(0.5) * A16_0.i + R(-64) * A17_0.i + R(-1) * A18_0.i + R(8) * A19_0.i + R(-10) * A20_0.i + R(-1) * A21_0.i + R(-64) * A22_0.i + R(8) * A23_0.i;
+                cs += A16_0.r * zr + A16_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A17_0.r + R(-10) * A18_0.r + R(-1) * A19_0.r + R(-1) * A20_0.r + R(8) * A21_0.r + R(8) * A22_0.r + R(-64) * A23_0.r; const R zi = R(512) * R(0.5) * A17_0.i + R(-10) * A18_0.i + R(-1) * A19_0.i + R(-1) * A20_0.i + R(8) * A21_0.i + R(8) * A22_0.i + R(-64) * A23_0.i;
+                cs += A17_0.r * zr + A17_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A18_0.r + R(-64) * A19_0.r + R(-64) * A20_0.r + R(8) * A21_0.r + R(8) * A22_0.r + R(80) * A23_0.r; const R zi = R(512) * R(0.5) * A18_0.i + R(-64) * A19_0.i + R(-64) * A20_0.i + R(8) * A21_0.i + R(8) * A22_0.i + R(80) * A23_0.i;
+                cs += A18_0.r * zr + A18_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A19_0.r + R(8) * A20_0.r + R(80) * A21_0.r + R(-64) * A22_0.r + R(8) * A23_0.r; const R zi = R(512) * R(0.5) * A19_0.i + R(8) * A20_0.i + R(80) * A21_0.i + R(-64) * A22_0.i + R(8) * A23_0.i;
+                cs += A19_0.r * zr + A19_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A20_0.r + R(-64) * A21_0.r + R(80) * A22_0.r + R(8) * A23_0.r; const R zi = R(512) * R(0.5) * A20_0.i + R(-64) * A21_0.i + R(80) * A22_0.i + R(8) * A23_0.i;
+                cs += A20_0.r * zr + A20_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A21_0.r + R(8) * A22_0.r + R(-64) * A23_0.r; const R zi = R(512) * R(0.5) * A21_0.i + R(8) * A22_0.i + R(-64) * A23_0.i;
+                cs += A21_0.r * zr + A21_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A22_0.r + R(-64) * A23_0.r; const R zi = R(512) * R(0.5) * A22_0.i + R(-64) * A23_0.i;
+                cs += A22_0.r * zr + A22_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A23_0.r; const R zi = R(512) * R(0.5) * A23_0.i;
+                cs += A23_0.r * zr + A23_0.i * zi; }
+              { const R zr = R(512) * R(0.5) * A0_1.r + R(-64) * A1_1.r + R(-64) * A2_1.r + R(8) * A3_1.r + R(8) * A4_1.r + R(80) * A5_1.r + R(-64) * A6_1.r + R(8) * A7_1.r + R(8) * A8_1.r + R(-1) * A9_1.r + R(-1) * A10_1.r + R(-10) * A11_1.r + R(8) * A12_1.r + R(-1) * A13_1.r + R(80) * A14_1.r + R(-10) * A15_1.r + R(71) * A16_1.r + R(62) * A17_1.r + R(-1) * A18_1.r + R(-10) * A19_1.r + R(-10) * A20_1.r + R(62) * A21_1.r + R(62) * A22_1.r + R(-28) * A23_1.r; const R zi = R(512) * R(0.5) * A0_1.i + R(-64) * A1_1.i + R(-64) * A2_1.i + R(8) * A3_1.i + R(8) * A4_1.i + R(80) * A5_1.i + R(-64) * A6_1.i + R(8) * A7_1.i + R(8) * A8_1.i + R(-1) * A9_1.i + R(-1) * A10_1.i + R(-10) * A11_1.i + R(8) * A12_1.i + R(-1) * A13_1.i + R(80) * A14_1.i + R(-10) * A15_1.i + R(71) * A16_1.i + R(62) * A17_1.i + R(-1) * A18_1.i + R(-10) * A19_1.i + R(-10) * A20_1.i + R(62) * A21_1.i + R(62) * A22_1.i + R(-28) * A23_1.i;
+                cs += A0_1.r * zr + A0_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A1_1.r + R(8) * A2_1.r + R(80) * A3_1.r + R(-64) * A4_1.r + R(8) * A5_1.r + R(8) * A6_1.r + R(-64) * A7_1.r + R(-1) * A8_1.r + R(-10) * A9_1.r + R(8) * A10_1.r + R(-1) * A11_1.r + R(-1) * A12_1.r + R(-10) * A13_1.r + R(-10) * A14_1.r + R(62) * A15_1.r + R(62) * A16_1.r + R(-28) * A17_1.r + R(8) * A18_1.r + R(-1) * A19_1.r + R(80) * A20_1.r + R(-10) * A21_1.r + R(71) * A22_1.r + R(62) * A23_1.r; const R zi = R(512) * R(0.5) * A1_1.i + R(8) * A2_1.i + R(80) * A3_1.i + R(-64) * A4_1.i + R(8) * A5_1.i + R(8) * A6_1.i + R(-64) * A7_1.i + R(-1) * A8_1.i + R(-10) * A9_1.i + R(8) * A10_1.i + R(-1) * A11_1.i + R(-1) * A12_1.i + R(-10) * A13_1.i + R(-10) * A14_1.i + R(62) * A15_1.i + R(62) * A16_1.i + R(-28) * A17_1.i + R(8) * A18_1.i + R(-1) * A19_1.i + R(80) * A20_1.i + R(-10) * A21_1.i + R(71) * A22_1.i + R(62) * A23_1.i;
+                cs += A1_1.r * zr + A1_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A2_1.r + R(-64) * A3_1.r + R(80) * A4_1.r + R(8) * A5_1.r + R(8) * A6_1.r + R(-1) * A7_1.r + R(80) * A8_1.r + R(-10) * A9_1.r + R(71) * A10_1.r + R(62) * A11_1.r + R(-64) * A12_1.r + R(8) * A13_1.r + R(8) * A14_1.r + R(-1) * A15_1.r + R(-1) * A16_1.r + R(-10) * A17_1.r + R(-10) * A18_1.r + R(-1) * A19_1.r + R(62) * A20_1.r + R(-28) * A21_1.r + R(-10) * A22_1.r + R(62) * A23_1.r; const R zi = R(512) * R(0.5) * A2_1.i + R(-64) * A3_1.i + R(80) * A4_1.i + R(8) * A5_1.i + R(8) * A6_1.i + R(-1) * A7_1.i + R(80) * A8_1.i + R(-10) * A9_1.i + R(71) * A10_1.i + R(62) * A11_1.i + R(-64) * A12_1.i + R(8) * A13_1.i + R(8) * A14_1.i + R(-1) * A15_1.i + R(-1) * A16_1.i + R(-10) * A17_1.i + R(-10) * A18_1.i + R(-1) * A19_1.i + R(62) * A20_1.i + R(-28) * A21_1.i + R(-10) * A22_1.i + R(62) * A23_1.i;
+                cs += A2_1.r * zr + A2_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A3_1.r + R(8) * A4_1.r + R(-64) * A5_1.r + R(-1) * A6_1.r + R(-10) * A7_1.r + R(-10) * A8_1.r + R(62) * A9_1.r + R(62) * A10_1.r + R(-28) * A11_1.r + R(8) * A12_1.r + R(-64) * A13_1.r + R(-1) * A14_1.r + R(-10) * A15_1.r + R(8) * A16_1.r + R(-1) * A17_1.r + R(-1) * A18_1.r + R(8) * A19_1.r + R(71) * A20_1.r + R(62) * A21_1.r + R(80) * A22_1.r + R(-10) * A23_1.r; const R zi = R(512) * R(0.5) * A3_1.i + R(8) * A4_1.i + R(-64) * A5_1.i + R(-1) * A6_1.i + R(-10) * A7_1.i + R(-10) * A8_1.i + R(62) * A9_1.i + R(62) * A10_1.i + R(-28) * A11_1.i + R(8) * A12_1.i + R(-64) * A13_1.i + R(-1) * A14_1.i + R(-10) * A15_1.i + R(8) * A16_1.i + R(-1) * A17_1.i + R(-1) * A18_1.i + R(8) * A19_1.i + R(71) * A20_1.i + R(62) * A21_1.i + R(80) * A22_1.i + R(-10) * A23_1.i;
+                cs += A3_1.r * zr + A3_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A4_1.r + R(-64) * A5_1.r + R(-1) * A6_1.r + R(8) * A7_1.r + R(71) * A8_1.r + R(62) * A9_1.r + R(80) * A10_1.r + R(-10) * A11_1.r + R(-10) * A12_1.r + R(-1) * A13_1.r + R(62) * A14_1.r + R(-28) * A15_1.r + R(-10) * A16_1.r + R(62) * A17_1.r + R(-64) * A18_1.r + R(8) * A19_1.r + R(8) * A20_1.r + R(-1) * A21_1.r + R(-1) * A22_1.r + R(-10) * A23_1.r; const R zi = R(512) * R(0.5) * A4_1.i + R(-64) * A5_1.i + R(-1) * A6_1.i + R(8) * A7_1.i + R(71) * A8_1.i + R(62) * A9_1.i + R(80) * A10_1.i + R(-10) * A11_1.i + R(-10) * A12_1.i + R(-1) * A13_1.i + R(62) * A14_1.i + R(-28) * A15_1.i + R(-10) * A16_1.i + R(62) * A17_1.i + R(-64) * A18_1.i + R(8) * A19_1.i + R(8) * A20_1.i + R(-1) * A21_1.i + R(-1) * A22_1.i + R(-10) * A23_1.i;
+                cs += A4_1.r * zr + A4_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A5_1.r + R(-10) * A6_1.r + R(-1) * A7_1.r + R(62) * A8_1.r + R(-28) * A9_1.r + R(-10) * A10_1.r + R(62) * A11_1.r + R(-1) * A12_1.r + R(8) * A13_1.r + R(71) * A14_1.r + R(62) * A15_1.r + R(80) * A16_1.r + R(-10) * A17_1.r + R(8) * A18_1.r + R(-64) * A19_1.r + R(-1) * A20_1.r + R(-10) * A21_1.r + R(8) * A22_1.r + R(-1) * A23_1.r; const R zi = R(512) * R(0.5) * A5_1.i + R(-10) * A6_1.i + R(-1) * A7_1.i + R(62) * A8_1.i + R(-28) * A9_1.i + R(-10) * A10_1.i + R(62) * A11_1.i + R(-1) * A12_1.i + R(8) * A13_1.i + R(71) * A14_1.i + R(62) * A15_1.i + R(80) * A16_1.i + R(-10) * A17_1.i + R(8) * A18_1.i + R(-64) * A19_1.i + R(-1) * A20_1.i + R(-10) * A21_1.i + R(8) * A22_1.i + R(-1) * A23_1.i;
+                cs += A5_1.r * zr + A5_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A6_1.r + R(-64) * A7_1.r + R(-64) * A8_1.r + R(8) * A9_1.r + R(8) * A10_1.r + R(80) * A11_1.r + R(80) * A12_1.r + R(-10) * A13_1.r + R(8) * A14_1.r + R(-1) * A15_1.r + R(62) * A16_1.r + R(71) * A17_1.r + R(-10) * A18_1.r + R(62) * A19_1.r + R(-1) * A20_1.r + R(-10) * A21_1.r + R(-28) * A22_1.r + R(62) * A23_1.r; const R zi = R(512) * R(0.5) * A6_1.i + R(-64) * A7_1.i + R(-64) * A8_1.i + R(8) * A9_1.i + R(8) * A10_1.i + R(80) * A11_1.i + R(80) * A12_1.i + R(-10) * A13_1.i + R(8) * A14_1.i + R(-1) * A15_1.i + R(62) * A16_1.i + R(71) * A17_1.i + R(-10) * A18_1.i + R(62) * A19_1.i + R(-1) * A20_1.i + R(-10) * A21_1.i + R(-28) * A22_1.i + R(62) * A23_1.i;
+                cs += A6_1.r * zr + A6_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A7_1.r + R(8) * A8_1.r + R(80) * A9_1.r + R(-64) * A10_1.r + R(8) * A11_1.r + R(-10) * A12_1.r + R(62) * A13_1.r + R(-1) * A14_1.r + R(-10) * A15_1.r + R(-28) * A16_1.r + R(62) * A17_1.r + R(80) * A18_1.r + R(-10) * A19_1.r + R(8) * A20_1.r + R(-1) * A21_1.r + R(62) * A22_1.r + R(71) * A23_1.r; const R zi = R(512) * R(0.5) * A7_1.i + R(8) * A8_1.i + R(80) * A9_1.i + R(-64) * A10_1.i + R(8) * A11_1.i + R(-10) * A12_1.i + R(62) * A13_1.i + R(-1) * A14_1.i + R(-10) * A15_1.i + R(-28) * A16_1.i + R(62) * A17_1.i + R(80) * A18_1.i + R(-10) * A19_1.i + R(8) * A20_1.i + R(-1) * A21_1.i + R(62) * A22_1.i + R(71) * A23_1.i;
+                cs += A7_1.r * zr + A7_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A8_1.r + R(-64) * A9_1.r + R(80) * A10_1.r + R(8) * A11_1.r + R(8) * A12_1.r + R(-1) * A13_1.r + R(-64) * A14_1.r + R(8) * A15_1.r + R(-10) * A16_1.r + R(-1) * A17_1.r + R(62) * A18_1.r + R(-28) * A19_1.r + R(-10) * A20_1.r + R(-1) * A21_1.r + R(62) * A22_1.r + R(-10) * A23_1.r; const R zi = R(512) * R(0.5) * A8_1.i + R(-64) * A9_1.i + R(80) * A10_1.i + R(8) * A11_1.i + R(8) * A12_1.i + R(-1) * A13_1.i + R(-64) * A14_1.i + R(8) * A15_1.i + R(-10) * A16_1.i + R(-1) * A17_1.i + R(62) * A18_1.i + R(-28) * A19_1.i + R(-10) * A20_1.i + R(-1) * A21_1.i + R(62) * A22_1.i + R(-10) * A23_1.i;
+                cs += A8_1.r * zr + A8_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A9_1.r + R(8) * A10_1.r + R(-64) * A11_1.r + R(-1) * A12_1.r + R(-10) * A13_1.r + R(8) * A14_1.r + R(-64) * A15_1.r + R(-1) * A16_1.r + R(8) * A17_1.r + R(71) * A18_1.r + R(62) * A19_1.r + R(-1) * A20_1.r + R(8) * A21_1.r + R(-10) * A22_1.r + R(80) * A23_1.r; const R zi = R(512) * R(0.5) * A9_1.i + R(8) * A10_1.i + R(-64) * A11_1.i + R(-1) * A12_1.i + R(-10) * A13_1.i + R(8) * A14_1.i + R(-64) * A15_1.i + R(-1) * A16_1.i + R(8) * A17_1.i + R(71) * A18_1.i + R(62) * A19_1.i + R(-1) * A20_1.i + R(8) * A21_1.i + R(-10) * A22_1.i + R(80) * A23_1.i;
+                cs += A9_1.r * zr + A9_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A10_1.r + R(-64) * A11_1.r + R(62) * A12_1.r + R(-28) * A13_1.r + R(-10) * A14_1.r + R(-1) * A15_1.r + R(62) * A16_1.r + R(-10) * A17_1.r + R(8) * A18_1.r + R(-1) * A19_1.r + R(-64) * A20_1.r + R(8) * A21_1.r + R(-10) * A22_1.r + R(-1) * A23_1.r; const R zi = R(512) * R(0.5) * A10_1.i + R(-64) * A11_1.i + R(62) * A12_1.i + R(-28) * A13_1.i + R(-10) * A14_1.i + R(-1) * A15_1.i + R(62) * A16_1.i + R(-10) * A17_1.i + R(8) * A18_1.i + R(-1) * A19_1.i + R(-64) * A20_1.i + R(8) * A21_1.i + R(-10) * A22_1.i + R(-1) * A23_1.i;
+                cs += A10_1.r * zr + A10_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A11_1.r + R(71) * A12_1.r + R(62) * A13_1.r + R(-1) * A14_1.r + R(8) * A15_1.r + R(-10) * A16_1.r + R(80) * A17_1.r + R(-1) * A18_1.r + R(-10) * A19_1.r + R(8) * A20_1.r + R(-64) * A21_1.r + R(-1) * A22_1.r + R(8) * A23_1.r; const R zi = R(512) * R(0.5) * A11_1.i + R(71) * A12_1.i + R(62) * A13_1.i + R(-1) * A14_1.i + R(8) * A15_1.i + R(-10) * A16_1.i + R(80) * A17_1.i + R(-1) * A18_1.i + R(-10) * A19_1.i + R(8) * A20_1.i + R(-64) * A21_1.i + R(-1) * A22_1.i + R(8) * A23_1.i;
+                cs += A11_1.r * zr + A11_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A12_1.r + R(-64) * A13_1.r + R(-64) * A14_1.r + R(8) * A15_1.r + R(8) * A16_1.r + R(80) * A17_1.r + R(62) * A18_1.r + R(-10) * A19_1.r + R(-28) * A20_1.r + R(62) * A21_1.r + R(-1) * A22_1.r + R(-10) * A23_1.r; const R zi = R(512) * R(0.5) * A12_1.i + R(-64) * A13_1.i + R(-64) * A14_1.i + R(8) * A15_1.i + R(8) * A16_1.i + R(80) * A17_1.i + R(62) * A18_1.i + R(-10) * A19_1.i + R(-28) * A20_1.i + R(62) * A21_1.i + R(-1) * A22_1.i + R(-10) * A23_1.i;
+                cs += A12_1.r * zr + A12_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A13_1.r + R(8) * A14_1.r + R(80) * A15_1.r + R(-64) * A16_1.r + R(8) * A17_1.r + R(-10) * A18_1.r + R(80) * A19_1.r + R(62) * A20_1.r + R(71) * A21_1.r + R(8) * A22_1.r + R(-1) * A23_1.r; const R zi = R(512) * R(0.5) * A13_1.i + R(8) * A14_1.i + R(80) * A15_1.i + R(-64) * A16_1.i + R(8) * A17_1.i + R(-10) * A18_1.i + R(80) * A19_1.i + R(62) * A20_1.i + R(71) * A21_1.i + R(8) * A22_1.i + R(-1) * A23_1.i;
+                cs += A13_1.r * zr + A13_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A14_1.r + R(-64) * A15_1.r + R(80) * A16_1.r + R(8) * A17_1.r + R(-28) * A18_1.r + R(62) * A19_1.r + R(62) * A20_1.r + R(-10) * A21_1.r + R(-10) * A22_1.r + R(-1) * A23_1.r; const R zi = R(512) * R(0.5) * A14_1.i + R(-64) * A15_1.i + R(80) * A16_1.i + R(8) * A17_1.i + R(-28) * A18_1.i + R(62) * A19_1.i + R(62) * A20_1.i + R(-10) * A21_1.i + R(-10) * A22_1.i + R(-1) * A23_1.i;
+                cs += A14_1.r * zr + A14_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A15_1.r + R(8) * A16_1.r + R(-64) * A17_1.r + R(62) * A18_1.r + R(71) * A19_1.r + R(-10) * A20_1.r + R(80) * A21_1.r + R(-1) * A22_1.r + R(8) * A23_1.r; const R zi = R(512) * R(0.5) * A15_1.i + R(8) * A16_1.i + R(-64) * A17_1.i + R(62) * A18_1.i + R(71) * A19_1.i + R(-10) * A20_1.i + R(80) * A21_1.i + R(-1) * A22_1.i + R(8) * A23_1.i;
+                cs += A15_1.r * zr + A15_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A16_1.r + R(-64) * A17_1.r + R(-1) * A18_1.r + R(8) * A19_1.r + R(-10) * A20_1.r + R(-1) * A21_1.r + R(-64) * A22_1.r + R(8) * A23_1.r; const R zi = R(512) * R(0.5) * A16_1.i + R(-64) * A17_1.i + R(-1) * A18_1.i + R(8) * A19_1.i + R(-10) * A20_1.i + R(-1) * A21_1.i + R(-64) * A22_1.i + R(8) * A23_1.i;
+                cs += A16_1.r * zr + A16_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A17_1.r + R(-10) * A18_1.r + R(-1) * A19_1.r + R(-1) * A20_1.r + R(8) * A21_1.r + R(8) * A22_1.r + R(-64) * A23_1.r; const R zi = R(512) * R(0.5) * A17_1.i + R(-10) * A18_1.i + R(-1) * A19_1.i + R(-1) * A20_1.i + R(8) * A21_1.i + R(8) * A22_1.i + R(-64) * A23_1.i;
+                cs += A17_1.r * zr + A17_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A18_1.r + R(-64) * A19_1.r + R(-64) * A20_1.r + R(8) * A21_1.r + R(8) * A22_1.r + R(80) * A23_1.r; const R zi = R(512) * R(0.5) * A18_1.i + R(-64) * A19_1.i + R(-64) * A20_1.i + R(8) * A21_1.i + R(8) * A22_1.i + R(80) * A23_1.i;
+                cs += A18_1.r * zr + A18_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A19_1.r + R(8) * A20_1.r + R(80) * A21_1.r + R(-64) * A22_1.r + R(8) * A23_1.r; const R zi = R(512) * R(0.5) * A19_1.i + R(8) * A20_1.i + R(80) * A21_1.i + R(-64) * A22_1.i + R(8) * A23_1.i;
+                cs += A19_1.r * zr + A19_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A20_1.r + R(-64) * A21_1.r + R(80) * A22_1.r + R(8) * A23_1.r; const R zi = R(512) * R(0.5) * A20_1.i + R(-64) * A21_1.i + R(80) * A22_1.i + R(8) * A23_1.i;
+                cs += A20_1.r * zr + A20_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A21_1.r + R(8) * A22_1.r + R(-64) * A23_1.r; const R zi = R(512) * R(0.5) * A21_1.i + R(8) * A22_1.i + R(-64) * A23_1.i;
+                cs += A21_1.r * zr + A21_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A22_1.r + R(-64) * A23_1.r; const R zi = R(512) * R(0.5) * A22_1.i + R(-64) * A23_1.i;
+                cs += A22_1.r * zr + A22_1.i * zi; }
+              { const R zr = R(512) * R(0.5) * A23_1.r; const R zi = R(512) * R(0.5) * A23_1.i;
+                cs += A23_1.r * zr + A23_1.i * zi; }
+              acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip
             }
           }
         }

@@ -26,8 +26,6 @@ void register_gg_tt_fp32(std::vector<KernelEntry>& t) {
   t.push_back({RW_GG_TT, RW_FP32, 1, (const void*)&k_interp<P, float, 1, 2>, 256, 1});
   t.push_back({RW_GG_TT, RW_FP32, 2, (const void*)&k_reweight<P, float, 2, 2>});
   t.push_back({RW_GG_TT, RW_FP32, 2, (const void*)&k_interp<P, float, 2, 2>, 256, 1});
-  t.push_back({RW_GG_TT, RW_FP32, 3, (const void*)&k_reweight<P, float, 3, 2>});
-  t.push_back({RW_GG_TT, RW_FP32, 3, (const void*)&k_interp<P, float, 3, 2>, 256, 1});
 
 }
 

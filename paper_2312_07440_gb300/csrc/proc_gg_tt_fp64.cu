@@ -26,8 +26,6 @@ void register_gg_tt_fp64(std::vector<KernelEntry>& t) {
   t.push_back({RW_GG_TT, RW_FP64, 1, (const void*)&k_interp<P, double, 1>, 256, 1});
   t.push_back({RW_GG_TT, RW_FP64, 2, (const void*)&k_reweight<P, double, 2>});
   t.push_back({RW_GG_TT, RW_FP64, 2, (const void*)&k_interp<P, double, 2>, 256, 1});
-  t.push_back({RW_GG_TT, RW_FP64, 3, (const void*)&k_reweight<P, double, 3>});
-  t.push_back({RW_GG_TT, RW_FP64, 3, (const void*)&k_interp<P, double, 3>, 256, 1});
 
 }
 

@@ -13,8 +13,9 @@ smaller generator for the processes it ships.  For n gluons on the top line it
   * emits a CUDA device function that evaluates every colour-ordered
     amplitude as chains of vertex and propagator calls -- off-shell gluon
     currents (3- and 4-gluon vertices), off-shell top currents (quark-gluon
-    vertex + top propagator), the amputated spinor of each ordering closed by
-    the top's ubar in the innermost helicity loop -- sharing every
+    vertex + top propagator) emitted depth-first over the orderings'
+    suffixes, the amputated spinor of each ordering closed at once with the
+    top's ubar of both helicities -- sharing every
     sub-current between the n! orderings (the sum over all Feynman diagrams,
     organised so that no diagram's chain is recomputed), with the helicity
     sum written as nested loops over the external helicities and every
@@ -195,7 +196,8 @@ class Emitter:
 def emit_process(name, n, outgoing_gluons, n_identical):
     """Emit the helicity-summed, couplings-stripped colour sum for t tbar + n g.
 
-    Loop levels 0..n-1: gluon helicities; level n: antitop; level n+1: top.
+    Loop levels 0..n-1: gluon helicities; level n: antitop (the top helicity is
+    summed inside it: both amplitudes of every ordering are formed at once).
     Level 0 is fixed (helicity-flip symmetry); the returned device function
     sums over the helicities of one lane, levels 1..LB taking their helicity
     bits from the lane index.
@@ -219,7 +221,7 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     w(f"constexpr int K = {K};")
     w(f"constexpr int NHEL = {2 ** (n + 2)};")
     w(f"constexpr int NDIAG = {diagram_count(n)};")
-    w(f"constexpr int MAX_LB = {n + 1};  // helicity levels that can be spread over lanes")
+    w(f"constexpr int MAX_LB = {n};  // helicity levels that can be spread over lanes")
     w(f"constexpr int CDEN = {den};")
     w(f"constexpr int IDENT = {n_identical};  // identical outgoing gluons (1/IDENT!)")
     w(f"constexpr unsigned OUTGOING_GLUONS = {sum(1 << g for g in outgoing_gluons)}u;  // bit g: gluon g outgoing")
@@ -241,7 +243,7 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     # all sequences of distinct gluons, by length
     seqs = {L: list(itertools.permutations(range(n), L)) for L in range(1, n + 1)}
     canon = {}  # J name for reversed sequences
-    nlev = n + 2
+    nlev = n + 1
 
     def open_level(L, hvar, sel):
         nonlocal ind
@@ -294,16 +296,41 @@ def emit_process(name, n, outgoing_gluons, n_identical):
                         a, b, cc = sq[:c], sq[c:d], sq[d:]
                         w(f"{ind}vvvv_acc({nm}, {jn(a)}, {jn(b)}, {jn(cc)}, Kn.c4[{m}]);")
                         em.count(g, "vvvv_acc")
-    # antitop level: fermion currents psi(rho), rho proper (len 1..n-1)
+    # antitop level: the fermion currents psi(rho) = S_rho (rho a proper
+    # sequence of gluons attached from the antitop end), the amputated spinor
+    # X(sigma) = sum_c Jslash(sigma[..c]) psi(sigma[c+1..]) of every ordering and
+    # its amplitudes A(sigma, h_t) = ubar(h_t) X(sigma) for both top helicities
+    # (the top level is folded in: X dies as soon as it is closed).  The
+    # spinors are emitted depth-first over the suffix tree -- S(d), S(c d),
+    # S(b c d), then X(a b c d) -- so only the current path of spinors is live
+    # at any time.
     open_level(n, f"h{n}", f"const sp<R> S_E = h{n} ? X.v[1] : X.v[0];")
 
     def jn(s):
         return f"E{s[0]}" if len(s) == 1 else seq_name("J", s)
-    for L in range(1, n):
-        for rho in seqs[L]:
+
+    def visit(suffix):
+        rest = [g for g in range(n) if g not in suffix]
+        if len(rest) == 1:
+            sg = (rest[0],) + suffix
+            k = perms.index(sg)
+            terms = []
+            for c in range(1, n + 1):
+                a, b = sg[:c], sg[c:]
+                terms.append(f"{jn(a)}, {seq_name('S_', b)}")
+                em.count(n, "slash")
+            w(f"{ind}sp<R> X{k} = slash({terms[0]});")
+            for t in terms[1:]:
+                w(f"{ind}slash_acc(X{k}, {t});")
+                em.count(n, "sp_add")
+            w(f"{ind}const cx<R> A{k}_0 = rowcol(X.ub[0], X{k}), A{k}_1 = rowcol(X.ub[1], X{k});")
+            em.count(n, "rowcol", 2)
+            return
+        for b0 in rest:
+            rho = (b0,) + suffix
             nm = seq_name("S_", rho)
             terms = []
-            for c in range(1, L + 1):
+            for c in range(1, len(rho) + 1):
                 a, b = rho[:c], rho[c:]
                 terms.append(f"{jn(a)}, {seq_name('S_', b)}")
                 em.count(n, "slash")
@@ -313,42 +340,29 @@ def emit_process(name, n, outgoing_gluons, n_identical):
                 em.count(n, "sp_add")
             w(f"{ind}const sp<R> {nm} = fprop(Kn.qc[{mask(rho)}], Kn.mc[{mask(rho)}], t{nm});")
             em.count(n, "fprop")
-    # still at the antitop level: the amputated spinors of every ordering,
-    # X(sigma) = sum_c Jslash(sigma[..c]) psi(sigma[c+1..]), so that the top
-    # level only closes them with ubar
-    for k, sg in enumerate(perms):
-        terms = []
-        for c in range(1, n + 1):
-            a, b = sg[:c], sg[c:]
-            terms.append(f"{jn(a)}, {seq_name('S_', b)}")
-            em.count(n, "slash")
-        w(f"{ind}sp<R> X{k} = slash({terms[0]});")
-        for t in terms[1:]:
-            w(f"{ind}slash_acc(X{k}, {t});")
-            em.count(n, "sp_add")
-    # top level: A(sigma) = ubar X(sigma), colour sum
-    open_level(n + 1, f"h{n + 1}", f"const sp<R> UB = h{n + 1} ? X.ub[1] : X.ub[0];")
-    for k in range(K):
-        w(f"{ind}const cx<R> A{k} = rowcol(UB, X{k});")
-        em.count(n + 1, "rowcol")
+            visit(rho)
+    visit(())
+    # colour sums of both top helicities
     w(f"{ind}if constexpr (CM != CM_FMA) {{")
-    w(f"{ind}  const cx<float> Aa[K] = {{{', '.join(f'A{k}' for k in range(K))}}};")
-    w(f"{ind}  acc += R(2) * cmma.sum(Aa);  // x2 helicity flip")
+    for h in (0, 1):
+        w(f"{ind}  const cx<float> Aa{h}[K] = {{{', '.join(f'A{k}_{h}' for k in range(K))}}};")
+    w(f"{ind}  acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip")
     w(f"{ind}}} else {{")
     ind += "  "
     # colour sum with the symmetric integer matrix: sum_i Re(A_i^* (C_ii/2 A_i + sum_{j>i} C_ij A_j)) * 2
     w(f"{ind}R cs = R(0);")
-    for i in range(K):
-        tr, ti = f"R({Cint[i][i]}) * R(0.5) * A{i}.r", f"R({Cint[i][i]}) * R(0.5) * A{i}.i"
-        parts_r, parts_i = [tr], [ti]
-        for j in range(i + 1, K):
-            if Cint[i][j] == 0:
-                continue
-            parts_r.append(f"R({Cint[i][j]}) * A{j}.r")
-            parts_i.append(f"R({Cint[i][j]}) * A{j}.i")
-        w(f"{ind}{{ const R zr = {' + '.join(parts_r)}; const R zi = {' + '.join(parts_i)};")
-        w(f"{ind}  cs += A{i}.r * zr + A{i}.i * zi; }}")
-        em.flops_per_level[n + 1] += 4 * len(parts_r) + 4
+    for h in (0, 1):
+        for i in range(K):
+            tr, ti = f"R({Cint[i][i]}) * R(0.5) * A{i}_{h}.r", f"R({Cint[i][i]}) * R(0.5) * A{i}_{h}.i"
+            parts_r, parts_i = [tr], [ti]
+            for j in range(i + 1, K):
+                if Cint[i][j] == 0:
+                    continue
+                parts_r.append(f"R({Cint[i][j]}) * A{j}_{h}.r")
+                parts_i.append(f"R({Cint[i][j]}) * A{j}_{h}.i")
+            w(f"{ind}{{ const R zr = {' + '.join(parts_r)}; const R zi = {' + '.join(parts_i)};")
+            w(f"{ind}  cs += A{i}_{h}.r * zr + A{i}_{h}.i * zi; }}")
+            em.flops_per_level[n] += 4 * len(parts_r) + 4
     w(f"{ind}acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip")
     ind = ind[:-2]
     w(f"{ind}}}")
