@@ -12,6 +12,7 @@ constexpr int K = 2;
 constexpr int NHEL = 16;
 constexpr int NDIAG = 3;
 constexpr int MAX_LB = 2;  // helicity levels that can be spread over lanes
+constexpr int NJS = 0;  // currents of 3+ gluons, one JStore slot each
 constexpr int CDEN = 3;
 constexpr int IDENT = 1;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 0u;  // bit g: gluon g outgoing
@@ -22,10 +23,11 @@ static __device__ const short CI[K * K] = {16, -2, -2, 16};  // row-major C_int 
 // Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;
 // helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).
 // CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float).
-template <class R, int LB, int CM = CM_FMA>
+template <class R, int LB, int CM = CM_FMA, bool JS = false>
 __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
   static_assert(CM == CM_FMA || sizeof(R) == 4, "tensor-core colour sum takes FP32 amplitudes");
   const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI);
+  JStore<R, NJS, JS> js;
   R acc = R(0);
   {
     const int h0 = 0;

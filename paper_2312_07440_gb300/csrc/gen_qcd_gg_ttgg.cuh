@@ -12,6 +12,7 @@ constexpr int K = 24;
 constexpr int NHEL = 64;
 constexpr int NDIAG = 123;
 constexpr int MAX_LB = 4;  // helicity levels that can be spread over lanes
+constexpr int NJS = 24;  // currents of 3+ gluons, one JStore slot each
 constexpr int CDEN = 54;
 constexpr int IDENT = 2;  // identical outgoing gluons (1/IDENT!)
 constexpr unsigned OUTGOING_GLUONS = 12u;  // bit g: gluon g outgoing
@@ -22,10 +23,11 @@ static __device__ const short CI[K * K] = {512, -64, -64, 8, 8, 80, -64, 8, 8, -
 // Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;
 // helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).
 // CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float).
-template <class R, int LB, int CM = CM_FMA>
+template <class R, int LB, int CM = CM_FMA, bool JS = false>
 __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
   static_assert(CM == CM_FMA || sizeof(R) == 4, "tensor-core colour sum takes FP32 amplitudes");
   const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI);
+  JStore<R, NJS, JS> js;
   R acc = R(0);
   {
     const int h0 = 0;
@@ -47,15 +49,15 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
         cv<R> J0_1_2 = vvv(E0, Kn.P[1], J1_2, Kn.P[6], Kn.cg[7]);
         vvv_acc(J0_1_2, J0_1, Kn.P[3], E2, Kn.P[4], Kn.cg[7]);
         vvvv_acc(J0_1_2, E0, E1, E2, Kn.c4[7]);
+        js.put(0, J0_1_2);
         cv<R> J0_2_1 = vvv(E0, Kn.P[1], J2_1, Kn.P[6], Kn.cg[7]);
         vvv_acc(J0_2_1, J0_2, Kn.P[5], E1, Kn.P[2], Kn.cg[7]);
         vvvv_acc(J0_2_1, E0, E2, E1, Kn.c4[7]);
+        js.put(1, J0_2_1);
         cv<R> J1_0_2 = vvv(E1, Kn.P[2], J0_2, Kn.P[5], Kn.cg[7]);
         vvv_acc(J1_0_2, J1_0, Kn.P[3], E2, Kn.P[4], Kn.cg[7]);
         vvvv_acc(J1_0_2, E1, E0, E2, Kn.c4[7]);
-        const cv<R> J1_2_0 = J0_2_1;
-        const cv<R> J2_0_1 = J1_0_2;
-        const cv<R> J2_1_0 = J0_1_2;
+        js.put(2, J1_0_2);
         #pragma unroll 1
         for (int i3 = 0; i3 < (LB >= 3 ? 1 : 2); ++i3) {
           const int h3 = LB >= 3 ? ((lane >> (LB - 3)) & 1) : i3;
@@ -69,123 +71,123 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
           cv<R> J0_1_3 = vvv(E0, Kn.P[1], J1_3, Kn.P[10], Kn.cg[11]);
           vvv_acc(J0_1_3, J0_1, Kn.P[3], E3, Kn.P[8], Kn.cg[11]);
           vvvv_acc(J0_1_3, E0, E1, E3, Kn.c4[11]);
+          js.put(3, J0_1_3);
           cv<R> J0_2_3 = vvv(E0, Kn.P[1], J2_3, Kn.P[12], Kn.cg[13]);
           vvv_acc(J0_2_3, J0_2, Kn.P[5], E3, Kn.P[8], Kn.cg[13]);
           vvvv_acc(J0_2_3, E0, E2, E3, Kn.c4[13]);
+          js.put(4, J0_2_3);
           cv<R> J0_3_1 = vvv(E0, Kn.P[1], J3_1, Kn.P[10], Kn.cg[11]);
           vvv_acc(J0_3_1, J0_3, Kn.P[9], E1, Kn.P[2], Kn.cg[11]);
           vvvv_acc(J0_3_1, E0, E3, E1, Kn.c4[11]);
+          js.put(5, J0_3_1);
           cv<R> J0_3_2 = vvv(E0, Kn.P[1], J3_2, Kn.P[12], Kn.cg[13]);
           vvv_acc(J0_3_2, J0_3, Kn.P[9], E2, Kn.P[4], Kn.cg[13]);
           vvvv_acc(J0_3_2, E0, E3, E2, Kn.c4[13]);
+          js.put(6, J0_3_2);
           cv<R> J1_0_3 = vvv(E1, Kn.P[2], J0_3, Kn.P[9], Kn.cg[11]);
           vvv_acc(J1_0_3, J1_0, Kn.P[3], E3, Kn.P[8], Kn.cg[11]);
           vvvv_acc(J1_0_3, E1, E0, E3, Kn.c4[11]);
+          js.put(7, J1_0_3);
           cv<R> J1_2_3 = vvv(E1, Kn.P[2], J2_3, Kn.P[12], Kn.cg[14]);
           vvv_acc(J1_2_3, J1_2, Kn.P[6], E3, Kn.P[8], Kn.cg[14]);
           vvvv_acc(J1_2_3, E1, E2, E3, Kn.c4[14]);
-          const cv<R> J1_3_0 = J0_3_1;
+          js.put(8, J1_2_3);
           cv<R> J1_3_2 = vvv(E1, Kn.P[2], J3_2, Kn.P[12], Kn.cg[14]);
           vvv_acc(J1_3_2, J1_3, Kn.P[10], E2, Kn.P[4], Kn.cg[14]);
           vvvv_acc(J1_3_2, E1, E3, E2, Kn.c4[14]);
+          js.put(9, J1_3_2);
           cv<R> J2_0_3 = vvv(E2, Kn.P[4], J0_3, Kn.P[9], Kn.cg[13]);
           vvv_acc(J2_0_3, J2_0, Kn.P[5], E3, Kn.P[8], Kn.cg[13]);
           vvvv_acc(J2_0_3, E2, E0, E3, Kn.c4[13]);
+          js.put(10, J2_0_3);
           cv<R> J2_1_3 = vvv(E2, Kn.P[4], J1_3, Kn.P[10], Kn.cg[14]);
           vvv_acc(J2_1_3, J2_1, Kn.P[6], E3, Kn.P[8], Kn.cg[14]);
           vvvv_acc(J2_1_3, E2, E1, E3, Kn.c4[14]);
-          const cv<R> J2_3_0 = J0_3_2;
-          const cv<R> J2_3_1 = J1_3_2;
-          const cv<R> J3_0_1 = J1_0_3;
-          const cv<R> J3_0_2 = J2_0_3;
-          const cv<R> J3_1_0 = J0_1_3;
-          const cv<R> J3_1_2 = J2_1_3;
-          const cv<R> J3_2_0 = J0_2_3;
-          const cv<R> J3_2_1 = J1_2_3;
-          cv<R> J0_1_2_3 = vvv(E0, Kn.P[1], J1_2_3, Kn.P[14], Kn.cg[15]);
+          js.put(11, J2_1_3);
+          cv<R> J0_1_2_3 = vvv(E0, Kn.P[1], js.get(8), Kn.P[14], Kn.cg[15]);
           vvv_acc(J0_1_2_3, J0_1, Kn.P[3], J2_3, Kn.P[12], Kn.cg[15]);
-          vvv_acc(J0_1_2_3, J0_1_2, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
+          vvv_acc(J0_1_2_3, js.get(0), Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J0_1_2_3, E0, E1, J2_3, Kn.c4[15]);
           vvvv_acc(J0_1_2_3, E0, J1_2, E3, Kn.c4[15]);
           vvvv_acc(J0_1_2_3, J0_1, E2, E3, Kn.c4[15]);
-          cv<R> J0_1_3_2 = vvv(E0, Kn.P[1], J1_3_2, Kn.P[14], Kn.cg[15]);
+          js.put(12, J0_1_2_3);
+          cv<R> J0_1_3_2 = vvv(E0, Kn.P[1], js.get(9), Kn.P[14], Kn.cg[15]);
           vvv_acc(J0_1_3_2, J0_1, Kn.P[3], J3_2, Kn.P[12], Kn.cg[15]);
-          vvv_acc(J0_1_3_2, J0_1_3, Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
+          vvv_acc(J0_1_3_2, js.get(3), Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
           vvvv_acc(J0_1_3_2, E0, E1, J3_2, Kn.c4[15]);
           vvvv_acc(J0_1_3_2, E0, J1_3, E2, Kn.c4[15]);
           vvvv_acc(J0_1_3_2, J0_1, E3, E2, Kn.c4[15]);
-          cv<R> J0_2_1_3 = vvv(E0, Kn.P[1], J2_1_3, Kn.P[14], Kn.cg[15]);
+          js.put(13, J0_1_3_2);
+          cv<R> J0_2_1_3 = vvv(E0, Kn.P[1], js.get(11), Kn.P[14], Kn.cg[15]);
           vvv_acc(J0_2_1_3, J0_2, Kn.P[5], J1_3, Kn.P[10], Kn.cg[15]);
-          vvv_acc(J0_2_1_3, J0_2_1, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
+          vvv_acc(J0_2_1_3, js.get(1), Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J0_2_1_3, E0, E2, J1_3, Kn.c4[15]);
           vvvv_acc(J0_2_1_3, E0, J2_1, E3, Kn.c4[15]);
           vvvv_acc(J0_2_1_3, J0_2, E1, E3, Kn.c4[15]);
-          cv<R> J0_2_3_1 = vvv(E0, Kn.P[1], J2_3_1, Kn.P[14], Kn.cg[15]);
+          js.put(14, J0_2_1_3);
+          cv<R> J0_2_3_1 = vvv(E0, Kn.P[1], js.get(9), Kn.P[14], Kn.cg[15]);
           vvv_acc(J0_2_3_1, J0_2, Kn.P[5], J3_1, Kn.P[10], Kn.cg[15]);
-          vvv_acc(J0_2_3_1, J0_2_3, Kn.P[13], E1, Kn.P[2], Kn.cg[15]);
+          vvv_acc(J0_2_3_1, js.get(4), Kn.P[13], E1, Kn.P[2], Kn.cg[15]);
           vvvv_acc(J0_2_3_1, E0, E2, J3_1, Kn.c4[15]);
           vvvv_acc(J0_2_3_1, E0, J2_3, E1, Kn.c4[15]);
           vvvv_acc(J0_2_3_1, J0_2, E3, E1, Kn.c4[15]);
-          cv<R> J0_3_1_2 = vvv(E0, Kn.P[1], J3_1_2, Kn.P[14], Kn.cg[15]);
+          js.put(15, J0_2_3_1);
+          cv<R> J0_3_1_2 = vvv(E0, Kn.P[1], js.get(11), Kn.P[14], Kn.cg[15]);
           vvv_acc(J0_3_1_2, J0_3, Kn.P[9], J1_2, Kn.P[6], Kn.cg[15]);
-          vvv_acc(J0_3_1_2, J0_3_1, Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
+          vvv_acc(J0_3_1_2, js.get(5), Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
           vvvv_acc(J0_3_1_2, E0, E3, J1_2, Kn.c4[15]);
           vvvv_acc(J0_3_1_2, E0, J3_1, E2, Kn.c4[15]);
           vvvv_acc(J0_3_1_2, J0_3, E1, E2, Kn.c4[15]);
-          cv<R> J0_3_2_1 = vvv(E0, Kn.P[1], J3_2_1, Kn.P[14], Kn.cg[15]);
+          js.put(16, J0_3_1_2);
+          cv<R> J0_3_2_1 = vvv(E0, Kn.P[1], js.get(8), Kn.P[14], Kn.cg[15]);
           vvv_acc(J0_3_2_1, J0_3, Kn.P[9], J2_1, Kn.P[6], Kn.cg[15]);
-          vvv_acc(J0_3_2_1, J0_3_2, Kn.P[13], E1, Kn.P[2], Kn.cg[15]);
+          vvv_acc(J0_3_2_1, js.get(6), Kn.P[13], E1, Kn.P[2], Kn.cg[15]);
           vvvv_acc(J0_3_2_1, E0, E3, J2_1, Kn.c4[15]);
           vvvv_acc(J0_3_2_1, E0, J3_2, E1, Kn.c4[15]);
           vvvv_acc(J0_3_2_1, J0_3, E2, E1, Kn.c4[15]);
-          cv<R> J1_0_2_3 = vvv(E1, Kn.P[2], J0_2_3, Kn.P[13], Kn.cg[15]);
+          js.put(17, J0_3_2_1);
+          cv<R> J1_0_2_3 = vvv(E1, Kn.P[2], js.get(4), Kn.P[13], Kn.cg[15]);
           vvv_acc(J1_0_2_3, J1_0, Kn.P[3], J2_3, Kn.P[12], Kn.cg[15]);
-          vvv_acc(J1_0_2_3, J1_0_2, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
+          vvv_acc(J1_0_2_3, js.get(2), Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J1_0_2_3, E1, E0, J2_3, Kn.c4[15]);
           vvvv_acc(J1_0_2_3, E1, J0_2, E3, Kn.c4[15]);
           vvvv_acc(J1_0_2_3, J1_0, E2, E3, Kn.c4[15]);
-          cv<R> J1_0_3_2 = vvv(E1, Kn.P[2], J0_3_2, Kn.P[13], Kn.cg[15]);
+          js.put(18, J1_0_2_3);
+          cv<R> J1_0_3_2 = vvv(E1, Kn.P[2], js.get(6), Kn.P[13], Kn.cg[15]);
           vvv_acc(J1_0_3_2, J1_0, Kn.P[3], J3_2, Kn.P[12], Kn.cg[15]);
-          vvv_acc(J1_0_3_2, J1_0_3, Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
+          vvv_acc(J1_0_3_2, js.get(7), Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
           vvvv_acc(J1_0_3_2, E1, E0, J3_2, Kn.c4[15]);
           vvvv_acc(J1_0_3_2, E1, J0_3, E2, Kn.c4[15]);
           vvvv_acc(J1_0_3_2, J1_0, E3, E2, Kn.c4[15]);
-          cv<R> J1_2_0_3 = vvv(E1, Kn.P[2], J2_0_3, Kn.P[13], Kn.cg[15]);
+          js.put(19, J1_0_3_2);
+          cv<R> J1_2_0_3 = vvv(E1, Kn.P[2], js.get(10), Kn.P[13], Kn.cg[15]);
           vvv_acc(J1_2_0_3, J1_2, Kn.P[6], J0_3, Kn.P[9], Kn.cg[15]);
-          vvv_acc(J1_2_0_3, J1_2_0, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
+          vvv_acc(J1_2_0_3, js.get(1), Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J1_2_0_3, E1, E2, J0_3, Kn.c4[15]);
           vvvv_acc(J1_2_0_3, E1, J2_0, E3, Kn.c4[15]);
           vvvv_acc(J1_2_0_3, J1_2, E0, E3, Kn.c4[15]);
-          const cv<R> J1_2_3_0 = neg(J0_3_2_1);
-          cv<R> J1_3_0_2 = vvv(E1, Kn.P[2], J3_0_2, Kn.P[13], Kn.cg[15]);
+          js.put(20, J1_2_0_3);
+          cv<R> J1_3_0_2 = vvv(E1, Kn.P[2], js.get(10), Kn.P[13], Kn.cg[15]);
           vvv_acc(J1_3_0_2, J1_3, Kn.P[10], J0_2, Kn.P[5], Kn.cg[15]);
-          vvv_acc(J1_3_0_2, J1_3_0, Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
+          vvv_acc(J1_3_0_2, js.get(5), Kn.P[11], E2, Kn.P[4], Kn.cg[15]);
           vvvv_acc(J1_3_0_2, E1, E3, J0_2, Kn.c4[15]);
           vvvv_acc(J1_3_0_2, E1, J3_0, E2, Kn.c4[15]);
           vvvv_acc(J1_3_0_2, J1_3, E0, E2, Kn.c4[15]);
-          const cv<R> J1_3_2_0 = neg(J0_2_3_1);
-          cv<R> J2_0_1_3 = vvv(E2, Kn.P[4], J0_1_3, Kn.P[11], Kn.cg[15]);
+          js.put(21, J1_3_0_2);
+          cv<R> J2_0_1_3 = vvv(E2, Kn.P[4], js.get(3), Kn.P[11], Kn.cg[15]);
           vvv_acc(J2_0_1_3, J2_0, Kn.P[5], J1_3, Kn.P[10], Kn.cg[15]);
-          vvv_acc(J2_0_1_3, J2_0_1, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
+          vvv_acc(J2_0_1_3, js.get(2), Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J2_0_1_3, E2, E0, J1_3, Kn.c4[15]);
           vvvv_acc(J2_0_1_3, E2, J0_1, E3, Kn.c4[15]);
           vvvv_acc(J2_0_1_3, J2_0, E1, E3, Kn.c4[15]);
-          const cv<R> J2_0_3_1 = neg(J1_3_0_2);
-          cv<R> J2_1_0_3 = vvv(E2, Kn.P[4], J1_0_3, Kn.P[11], Kn.cg[15]);
+          js.put(22, J2_0_1_3);
+          cv<R> J2_1_0_3 = vvv(E2, Kn.P[4], js.get(7), Kn.P[11], Kn.cg[15]);
           vvv_acc(J2_1_0_3, J2_1, Kn.P[6], J0_3, Kn.P[9], Kn.cg[15]);
-          vvv_acc(J2_1_0_3, J2_1_0, Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
+          vvv_acc(J2_1_0_3, js.get(0), Kn.P[7], E3, Kn.P[8], Kn.cg[15]);
           vvvv_acc(J2_1_0_3, E2, E1, J0_3, Kn.c4[15]);
           vvvv_acc(J2_1_0_3, E2, J1_0, E3, Kn.c4[15]);
           vvvv_acc(J2_1_0_3, J2_1, E0, E3, Kn.c4[15]);
-          const cv<R> J2_1_3_0 = neg(J0_3_1_2);
-          const cv<R> J2_3_0_1 = neg(J1_0_3_2);
-          const cv<R> J2_3_1_0 = neg(J0_1_3_2);
-          const cv<R> J3_0_1_2 = neg(J2_1_0_3);
-          const cv<R> J3_0_2_1 = neg(J1_2_0_3);
-          const cv<R> J3_1_0_2 = neg(J2_0_1_3);
-          const cv<R> J3_1_2_0 = neg(J0_2_1_3);
-          const cv<R> J3_2_0_1 = neg(J1_0_2_3);
-          const cv<R> J3_2_1_0 = neg(J0_1_2_3);
+          js.put(23, J2_1_0_3);
           #pragma unroll 1
           for (int i4 = 0; i4 < (LB >= 4 ? 1 : 2); ++i4) {
             const int h4 = LB >= 4 ? ((lane >> (LB - 4)) & 1) : i4;
@@ -197,63 +199,63 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             const sp<R> S_1_0 = fprop(Kn.qc[3], Kn.mc[3], tS_1_0);
             sp<R> tS_2_1_0 = slash(E2, S_1_0);
             slash_acc(tS_2_1_0, J2_1, S_0);
-            slash_acc(tS_2_1_0, J2_1_0, S_E);
+            slash_acc(tS_2_1_0, js.get(0), S_E);
             const sp<R> S_2_1_0 = fprop(Kn.qc[7], Kn.mc[7], tS_2_1_0);
             sp<R> X23 = slash(E3, S_2_1_0);
             slash_acc(X23, J3_2, S_1_0);
-            slash_acc(X23, J3_2_1, S_0);
-            slash_acc(X23, J3_2_1_0, S_E);
+            slash_acc(X23, js.get(8), S_0);
+            slash_acc(X23, neg(js.get(12)), S_E);
             const cx<R> A23_0 = rowcol(X.ub[0], X23), A23_1 = rowcol(X.ub[1], X23);
             sp<R> tS_3_1_0 = slash(E3, S_1_0);
             slash_acc(tS_3_1_0, J3_1, S_0);
-            slash_acc(tS_3_1_0, J3_1_0, S_E);
+            slash_acc(tS_3_1_0, js.get(3), S_E);
             const sp<R> S_3_1_0 = fprop(Kn.qc[11], Kn.mc[11], tS_3_1_0);
             sp<R> X17 = slash(E2, S_3_1_0);
             slash_acc(X17, J2_3, S_1_0);
-            slash_acc(X17, J2_3_1, S_0);
-            slash_acc(X17, J2_3_1_0, S_E);
+            slash_acc(X17, js.get(9), S_0);
+            slash_acc(X17, neg(js.get(13)), S_E);
             const cx<R> A17_0 = rowcol(X.ub[0], X17), A17_1 = rowcol(X.ub[1], X17);
             sp<R> tS_2_0 = slash(E2, S_0);
             slash_acc(tS_2_0, J2_0, S_E);
             const sp<R> S_2_0 = fprop(Kn.qc[5], Kn.mc[5], tS_2_0);
             sp<R> tS_1_2_0 = slash(E1, S_2_0);
             slash_acc(tS_1_2_0, J1_2, S_0);
-            slash_acc(tS_1_2_0, J1_2_0, S_E);
+            slash_acc(tS_1_2_0, js.get(1), S_E);
             const sp<R> S_1_2_0 = fprop(Kn.qc[7], Kn.mc[7], tS_1_2_0);
             sp<R> X21 = slash(E3, S_1_2_0);
             slash_acc(X21, J3_1, S_2_0);
-            slash_acc(X21, J3_1_2, S_0);
-            slash_acc(X21, J3_1_2_0, S_E);
+            slash_acc(X21, js.get(11), S_0);
+            slash_acc(X21, neg(js.get(14)), S_E);
             const cx<R> A21_0 = rowcol(X.ub[0], X21), A21_1 = rowcol(X.ub[1], X21);
             sp<R> tS_3_2_0 = slash(E3, S_2_0);
             slash_acc(tS_3_2_0, J3_2, S_0);
-            slash_acc(tS_3_2_0, J3_2_0, S_E);
+            slash_acc(tS_3_2_0, js.get(4), S_E);
             const sp<R> S_3_2_0 = fprop(Kn.qc[13], Kn.mc[13], tS_3_2_0);
             sp<R> X11 = slash(E1, S_3_2_0);
             slash_acc(X11, J1_3, S_2_0);
-            slash_acc(X11, J1_3_2, S_0);
-            slash_acc(X11, J1_3_2_0, S_E);
+            slash_acc(X11, js.get(9), S_0);
+            slash_acc(X11, neg(js.get(15)), S_E);
             const cx<R> A11_0 = rowcol(X.ub[0], X11), A11_1 = rowcol(X.ub[1], X11);
             sp<R> tS_3_0 = slash(E3, S_0);
             slash_acc(tS_3_0, J3_0, S_E);
             const sp<R> S_3_0 = fprop(Kn.qc[9], Kn.mc[9], tS_3_0);
             sp<R> tS_1_3_0 = slash(E1, S_3_0);
             slash_acc(tS_1_3_0, J1_3, S_0);
-            slash_acc(tS_1_3_0, J1_3_0, S_E);
+            slash_acc(tS_1_3_0, js.get(5), S_E);
             const sp<R> S_1_3_0 = fprop(Kn.qc[11], Kn.mc[11], tS_1_3_0);
             sp<R> X15 = slash(E2, S_1_3_0);
             slash_acc(X15, J2_1, S_3_0);
-            slash_acc(X15, J2_1_3, S_0);
-            slash_acc(X15, J2_1_3_0, S_E);
+            slash_acc(X15, js.get(11), S_0);
+            slash_acc(X15, neg(js.get(16)), S_E);
             const cx<R> A15_0 = rowcol(X.ub[0], X15), A15_1 = rowcol(X.ub[1], X15);
             sp<R> tS_2_3_0 = slash(E2, S_3_0);
             slash_acc(tS_2_3_0, J2_3, S_0);
-            slash_acc(tS_2_3_0, J2_3_0, S_E);
+            slash_acc(tS_2_3_0, js.get(6), S_E);
             const sp<R> S_2_3_0 = fprop(Kn.qc[13], Kn.mc[13], tS_2_3_0);
             sp<R> X9 = slash(E1, S_2_3_0);
             slash_acc(X9, J1_2, S_3_0);
-            slash_acc(X9, J1_2_3, S_0);
-            slash_acc(X9, J1_2_3_0, S_E);
+            slash_acc(X9, js.get(8), S_0);
+            slash_acc(X9, neg(js.get(17)), S_E);
             const cx<R> A9_0 = rowcol(X.ub[0], X9), A9_1 = rowcol(X.ub[1], X9);
             sp<R> tS_1 = slash(E1, S_E);
             const sp<R> S_1 = fprop(Kn.qc[2], Kn.mc[2], tS_1);
@@ -262,63 +264,63 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             const sp<R> S_0_1 = fprop(Kn.qc[3], Kn.mc[3], tS_0_1);
             sp<R> tS_2_0_1 = slash(E2, S_0_1);
             slash_acc(tS_2_0_1, J2_0, S_1);
-            slash_acc(tS_2_0_1, J2_0_1, S_E);
+            slash_acc(tS_2_0_1, js.get(2), S_E);
             const sp<R> S_2_0_1 = fprop(Kn.qc[7], Kn.mc[7], tS_2_0_1);
             sp<R> X22 = slash(E3, S_2_0_1);
             slash_acc(X22, J3_2, S_0_1);
-            slash_acc(X22, J3_2_0, S_1);
-            slash_acc(X22, J3_2_0_1, S_E);
+            slash_acc(X22, js.get(4), S_1);
+            slash_acc(X22, neg(js.get(18)), S_E);
             const cx<R> A22_0 = rowcol(X.ub[0], X22), A22_1 = rowcol(X.ub[1], X22);
             sp<R> tS_3_0_1 = slash(E3, S_0_1);
             slash_acc(tS_3_0_1, J3_0, S_1);
-            slash_acc(tS_3_0_1, J3_0_1, S_E);
+            slash_acc(tS_3_0_1, js.get(7), S_E);
             const sp<R> S_3_0_1 = fprop(Kn.qc[11], Kn.mc[11], tS_3_0_1);
             sp<R> X16 = slash(E2, S_3_0_1);
             slash_acc(X16, J2_3, S_0_1);
-            slash_acc(X16, J2_3_0, S_1);
-            slash_acc(X16, J2_3_0_1, S_E);
+            slash_acc(X16, js.get(6), S_1);
+            slash_acc(X16, neg(js.get(19)), S_E);
             const cx<R> A16_0 = rowcol(X.ub[0], X16), A16_1 = rowcol(X.ub[1], X16);
             sp<R> tS_2_1 = slash(E2, S_1);
             slash_acc(tS_2_1, J2_1, S_E);
             const sp<R> S_2_1 = fprop(Kn.qc[6], Kn.mc[6], tS_2_1);
             sp<R> tS_0_2_1 = slash(E0, S_2_1);
             slash_acc(tS_0_2_1, J0_2, S_1);
-            slash_acc(tS_0_2_1, J0_2_1, S_E);
+            slash_acc(tS_0_2_1, js.get(1), S_E);
             const sp<R> S_0_2_1 = fprop(Kn.qc[7], Kn.mc[7], tS_0_2_1);
             sp<R> X19 = slash(E3, S_0_2_1);
             slash_acc(X19, J3_0, S_2_1);
-            slash_acc(X19, J3_0_2, S_1);
-            slash_acc(X19, J3_0_2_1, S_E);
+            slash_acc(X19, js.get(10), S_1);
+            slash_acc(X19, neg(js.get(20)), S_E);
             const cx<R> A19_0 = rowcol(X.ub[0], X19), A19_1 = rowcol(X.ub[1], X19);
             sp<R> tS_3_2_1 = slash(E3, S_2_1);
             slash_acc(tS_3_2_1, J3_2, S_1);
-            slash_acc(tS_3_2_1, J3_2_1, S_E);
+            slash_acc(tS_3_2_1, js.get(8), S_E);
             const sp<R> S_3_2_1 = fprop(Kn.qc[14], Kn.mc[14], tS_3_2_1);
             sp<R> X5 = slash(E0, S_3_2_1);
             slash_acc(X5, J0_3, S_2_1);
-            slash_acc(X5, J0_3_2, S_1);
-            slash_acc(X5, J0_3_2_1, S_E);
+            slash_acc(X5, js.get(6), S_1);
+            slash_acc(X5, js.get(17), S_E);
             const cx<R> A5_0 = rowcol(X.ub[0], X5), A5_1 = rowcol(X.ub[1], X5);
             sp<R> tS_3_1 = slash(E3, S_1);
             slash_acc(tS_3_1, J3_1, S_E);
             const sp<R> S_3_1 = fprop(Kn.qc[10], Kn.mc[10], tS_3_1);
             sp<R> tS_0_3_1 = slash(E0, S_3_1);
             slash_acc(tS_0_3_1, J0_3, S_1);
-            slash_acc(tS_0_3_1, J0_3_1, S_E);
+            slash_acc(tS_0_3_1, js.get(5), S_E);
             const sp<R> S_0_3_1 = fprop(Kn.qc[11], Kn.mc[11], tS_0_3_1);
             sp<R> X13 = slash(E2, S_0_3_1);
             slash_acc(X13, J2_0, S_3_1);
-            slash_acc(X13, J2_0_3, S_1);
-            slash_acc(X13, J2_0_3_1, S_E);
+            slash_acc(X13, js.get(10), S_1);
+            slash_acc(X13, neg(js.get(21)), S_E);
             const cx<R> A13_0 = rowcol(X.ub[0], X13), A13_1 = rowcol(X.ub[1], X13);
             sp<R> tS_2_3_1 = slash(E2, S_3_1);
             slash_acc(tS_2_3_1, J2_3, S_1);
-            slash_acc(tS_2_3_1, J2_3_1, S_E);
+            slash_acc(tS_2_3_1, js.get(9), S_E);
             const sp<R> S_2_3_1 = fprop(Kn.qc[14], Kn.mc[14], tS_2_3_1);
             sp<R> X3 = slash(E0, S_2_3_1);
             slash_acc(X3, J0_2, S_3_1);
-            slash_acc(X3, J0_2_3, S_1);
-            slash_acc(X3, J0_2_3_1, S_E);
+            slash_acc(X3, js.get(4), S_1);
+            slash_acc(X3, js.get(15), S_E);
             const cx<R> A3_0 = rowcol(X.ub[0], X3), A3_1 = rowcol(X.ub[1], X3);
             sp<R> tS_2 = slash(E2, S_E);
             const sp<R> S_2 = fprop(Kn.qc[4], Kn.mc[4], tS_2);
@@ -327,63 +329,63 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             const sp<R> S_0_2 = fprop(Kn.qc[5], Kn.mc[5], tS_0_2);
             sp<R> tS_1_0_2 = slash(E1, S_0_2);
             slash_acc(tS_1_0_2, J1_0, S_2);
-            slash_acc(tS_1_0_2, J1_0_2, S_E);
+            slash_acc(tS_1_0_2, js.get(2), S_E);
             const sp<R> S_1_0_2 = fprop(Kn.qc[7], Kn.mc[7], tS_1_0_2);
             sp<R> X20 = slash(E3, S_1_0_2);
             slash_acc(X20, J3_1, S_0_2);
-            slash_acc(X20, J3_1_0, S_2);
-            slash_acc(X20, J3_1_0_2, S_E);
+            slash_acc(X20, js.get(3), S_2);
+            slash_acc(X20, neg(js.get(22)), S_E);
             const cx<R> A20_0 = rowcol(X.ub[0], X20), A20_1 = rowcol(X.ub[1], X20);
             sp<R> tS_3_0_2 = slash(E3, S_0_2);
             slash_acc(tS_3_0_2, J3_0, S_2);
-            slash_acc(tS_3_0_2, J3_0_2, S_E);
+            slash_acc(tS_3_0_2, js.get(10), S_E);
             const sp<R> S_3_0_2 = fprop(Kn.qc[13], Kn.mc[13], tS_3_0_2);
             sp<R> X10 = slash(E1, S_3_0_2);
             slash_acc(X10, J1_3, S_0_2);
-            slash_acc(X10, J1_3_0, S_2);
-            slash_acc(X10, J1_3_0_2, S_E);
+            slash_acc(X10, js.get(5), S_2);
+            slash_acc(X10, js.get(21), S_E);
             const cx<R> A10_0 = rowcol(X.ub[0], X10), A10_1 = rowcol(X.ub[1], X10);
             sp<R> tS_1_2 = slash(E1, S_2);
             slash_acc(tS_1_2, J1_2, S_E);
             const sp<R> S_1_2 = fprop(Kn.qc[6], Kn.mc[6], tS_1_2);
             sp<R> tS_0_1_2 = slash(E0, S_1_2);
             slash_acc(tS_0_1_2, J0_1, S_2);
-            slash_acc(tS_0_1_2, J0_1_2, S_E);
+            slash_acc(tS_0_1_2, js.get(0), S_E);
             const sp<R> S_0_1_2 = fprop(Kn.qc[7], Kn.mc[7], tS_0_1_2);
             sp<R> X18 = slash(E3, S_0_1_2);
             slash_acc(X18, J3_0, S_1_2);
-            slash_acc(X18, J3_0_1, S_2);
-            slash_acc(X18, J3_0_1_2, S_E);
+            slash_acc(X18, js.get(7), S_2);
+            slash_acc(X18, neg(js.get(23)), S_E);
             const cx<R> A18_0 = rowcol(X.ub[0], X18), A18_1 = rowcol(X.ub[1], X18);
             sp<R> tS_3_1_2 = slash(E3, S_1_2);
             slash_acc(tS_3_1_2, J3_1, S_2);
-            slash_acc(tS_3_1_2, J3_1_2, S_E);
+            slash_acc(tS_3_1_2, js.get(11), S_E);
             const sp<R> S_3_1_2 = fprop(Kn.qc[14], Kn.mc[14], tS_3_1_2);
             sp<R> X4 = slash(E0, S_3_1_2);
             slash_acc(X4, J0_3, S_1_2);
-            slash_acc(X4, J0_3_1, S_2);
-            slash_acc(X4, J0_3_1_2, S_E);
+            slash_acc(X4, js.get(5), S_2);
+            slash_acc(X4, js.get(16), S_E);
             const cx<R> A4_0 = rowcol(X.ub[0], X4), A4_1 = rowcol(X.ub[1], X4);
             sp<R> tS_3_2 = slash(E3, S_2);
             slash_acc(tS_3_2, J3_2, S_E);
             const sp<R> S_3_2 = fprop(Kn.qc[12], Kn.mc[12], tS_3_2);
             sp<R> tS_0_3_2 = slash(E0, S_3_2);
             slash_acc(tS_0_3_2, J0_3, S_2);
-            slash_acc(tS_0_3_2, J0_3_2, S_E);
+            slash_acc(tS_0_3_2, js.get(6), S_E);
             const sp<R> S_0_3_2 = fprop(Kn.qc[13], Kn.mc[13], tS_0_3_2);
             sp<R> X7 = slash(E1, S_0_3_2);
             slash_acc(X7, J1_0, S_3_2);
-            slash_acc(X7, J1_0_3, S_2);
-            slash_acc(X7, J1_0_3_2, S_E);
+            slash_acc(X7, js.get(7), S_2);
+            slash_acc(X7, js.get(19), S_E);
             const cx<R> A7_0 = rowcol(X.ub[0], X7), A7_1 = rowcol(X.ub[1], X7);
             sp<R> tS_1_3_2 = slash(E1, S_3_2);
             slash_acc(tS_1_3_2, J1_3, S_2);
-            slash_acc(tS_1_3_2, J1_3_2, S_E);
+            slash_acc(tS_1_3_2, js.get(9), S_E);
             const sp<R> S_1_3_2 = fprop(Kn.qc[14], Kn.mc[14], tS_1_3_2);
             sp<R> X1 = slash(E0, S_1_3_2);
             slash_acc(X1, J0_1, S_3_2);
-            slash_acc(X1, J0_1_3, S_2);
-            slash_acc(X1, J0_1_3_2, S_E);
+            slash_acc(X1, js.get(3), S_2);
+            slash_acc(X1, js.get(13), S_E);
             const cx<R> A1_0 = rowcol(X.ub[0], X1), A1_1 = rowcol(X.ub[1], X1);
             sp<R> tS_3 = slash(E3, S_E);
             const sp<R> S_3 = fprop(Kn.qc[8], Kn.mc[8], tS_3);
@@ -392,63 +394,63 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             const sp<R> S_0_3 = fprop(Kn.qc[9], Kn.mc[9], tS_0_3);
             sp<R> tS_1_0_3 = slash(E1, S_0_3);
             slash_acc(tS_1_0_3, J1_0, S_3);
-            slash_acc(tS_1_0_3, J1_0_3, S_E);
+            slash_acc(tS_1_0_3, js.get(7), S_E);
             const sp<R> S_1_0_3 = fprop(Kn.qc[11], Kn.mc[11], tS_1_0_3);
             sp<R> X14 = slash(E2, S_1_0_3);
             slash_acc(X14, J2_1, S_0_3);
-            slash_acc(X14, J2_1_0, S_3);
-            slash_acc(X14, J2_1_0_3, S_E);
+            slash_acc(X14, js.get(0), S_3);
+            slash_acc(X14, js.get(23), S_E);
             const cx<R> A14_0 = rowcol(X.ub[0], X14), A14_1 = rowcol(X.ub[1], X14);
             sp<R> tS_2_0_3 = slash(E2, S_0_3);
             slash_acc(tS_2_0_3, J2_0, S_3);
-            slash_acc(tS_2_0_3, J2_0_3, S_E);
+            slash_acc(tS_2_0_3, js.get(10), S_E);
             const sp<R> S_2_0_3 = fprop(Kn.qc[13], Kn.mc[13], tS_2_0_3);
             sp<R> X8 = slash(E1, S_2_0_3);
             slash_acc(X8, J1_2, S_0_3);
-            slash_acc(X8, J1_2_0, S_3);
-            slash_acc(X8, J1_2_0_3, S_E);
+            slash_acc(X8, js.get(1), S_3);
+            slash_acc(X8, js.get(20), S_E);
             const cx<R> A8_0 = rowcol(X.ub[0], X8), A8_1 = rowcol(X.ub[1], X8);
             sp<R> tS_1_3 = slash(E1, S_3);
             slash_acc(tS_1_3, J1_3, S_E);
             const sp<R> S_1_3 = fprop(Kn.qc[10], Kn.mc[10], tS_1_3);
             sp<R> tS_0_1_3 = slash(E0, S_1_3);
             slash_acc(tS_0_1_3, J0_1, S_3);
-            slash_acc(tS_0_1_3, J0_1_3, S_E);
+            slash_acc(tS_0_1_3, js.get(3), S_E);
             const sp<R> S_0_1_3 = fprop(Kn.qc[11], Kn.mc[11], tS_0_1_3);
             sp<R> X12 = slash(E2, S_0_1_3);
             slash_acc(X12, J2_0, S_1_3);
-            slash_acc(X12, J2_0_1, S_3);
-            slash_acc(X12, J2_0_1_3, S_E);
+            slash_acc(X12, js.get(2), S_3);
+            slash_acc(X12, js.get(22), S_E);
             const cx<R> A12_0 = rowcol(X.ub[0], X12), A12_1 = rowcol(X.ub[1], X12);
             sp<R> tS_2_1_3 = slash(E2, S_1_3);
             slash_acc(tS_2_1_3, J2_1, S_3);
-            slash_acc(tS_2_1_3, J2_1_3, S_E);
+            slash_acc(tS_2_1_3, js.get(11), S_E);
             const sp<R> S_2_1_3 = fprop(Kn.qc[14], Kn.mc[14], tS_2_1_3);
             sp<R> X2 = slash(E0, S_2_1_3);
             slash_acc(X2, J0_2, S_1_3);
-            slash_acc(X2, J0_2_1, S_3);
-            slash_acc(X2, J0_2_1_3, S_E);
+            slash_acc(X2, js.get(1), S_3);
+            slash_acc(X2, js.get(14), S_E);
             const cx<R> A2_0 = rowcol(X.ub[0], X2), A2_1 = rowcol(X.ub[1], X2);
             sp<R> tS_2_3 = slash(E2, S_3);
             slash_acc(tS_2_3, J2_3, S_E);
             const sp<R> S_2_3 = fprop(Kn.qc[12], Kn.mc[12], tS_2_3);
             sp<R> tS_0_2_3 = slash(E0, S_2_3);
             slash_acc(tS_0_2_3, J0_2, S_3);
-            slash_acc(tS_0_2_3, J0_2_3, S_E);
+            slash_acc(tS_0_2_3, js.get(4), S_E);
             const sp<R> S_0_2_3 = fprop(Kn.qc[13], Kn.mc[13], tS_0_2_3);
             sp<R> X6 = slash(E1, S_0_2_3);
             slash_acc(X6, J1_0, S_2_3);
-            slash_acc(X6, J1_0_2, S_3);
-            slash_acc(X6, J1_0_2_3, S_E);
+            slash_acc(X6, js.get(2), S_3);
+            slash_acc(X6, js.get(18), S_E);
             const cx<R> A6_0 = rowcol(X.ub[0], X6), A6_1 = rowcol(X.ub[1], X6);
             sp<R> tS_1_2_3 = slash(E1, S_2_3);
             slash_acc(tS_1_2_3, J1_2, S_3);
-            slash_acc(tS_1_2_3, J1_2_3, S_E);
+            slash_acc(tS_1_2_3, js.get(8), S_E);
             const sp<R> S_1_2_3 = fprop(Kn.qc[14], Kn.mc[14], tS_1_2_3);
             sp<R> X0 = slash(E0, S_1_2_3);
             slash_acc(X0, J0_1, S_2_3);
-            slash_acc(X0, J0_1_2, S_3);
-            slash_acc(X0, J0_1_2_3, S_E);
+            slash_acc(X0, js.get(0), S_3);
+            slash_acc(X0, js.get(12), S_E);
             const cx<R> A0_0 = rowcol(X.ub[0], X0), A0_1 = rowcol(X.ub[1], X0);
             if constexpr (CM != CM_FMA) {
               const cx<float> Aa0[K] = {A0_0, A1_0, A2_0, A3_0, A4_0, A5_0, A6_0, A7_0, A8_0, A9_0, A10_0, A11_0, A12_0, A13_0, A14_0, A15_0, A16_0, A17_0, A18_0, A19_0, A20_0, A21_0, A22_0, A23_0};

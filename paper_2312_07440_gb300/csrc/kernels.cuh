@@ -133,7 +133,10 @@ template <class Proc, class R, int LB, int MINB = 1>
 __global__ void __launch_bounds__(256, MINB) k_reweight(const __grid_constant__ RwArgs a) {
   constexpr int NEXT = Proc::NEXT;
   constexpr int LANES = 1 << LB;
-  extern __shared__ double2 sacc[];  // [nwarps][P+1]
+  // dynamic shared memory: the amplitude code's current store (if any), then
+  // the warp partial sums [nwarps][P+1]
+  extern __shared__ __align__(16) unsigned char rw_dyn_bytes[];
+  double2* sacc = reinterpret_cast<double2*>(rw_dyn_bytes + (size_t)Proc::template jstore_bytes<R>() * blockDim.x);
   __shared__ double2 red[32];
   __shared__ int is_last;
   const int P = a.P;

@@ -12,9 +12,11 @@ struct Tag {
   static constexpr int NG = gg_tt::NG;
   static constexpr int NEXT = gg_tt::NEXT;
   static constexpr int MAX_LB = gg_tt::MAX_LB;
+  static constexpr int NJS = gg_tt::NJS;
+  static constexpr bool JSMEM = false;  // currents of 3+ gluons in shared memory (FP32)
   template <class R, int LB, int CM>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
-    return gg_tt::hel_sum<R, LB, CM>(X, K, lane);
+    return gg_tt::hel_sum<R, LB, CM, JSMEM && sizeof(R) == 4>(X, K, lane);
   }
 };
 using P16 = QcdProc<Tag, CM_FP16>;

@@ -11,9 +11,11 @@ struct Tag {
   static constexpr int NG = gg_ttgg::NG;
   static constexpr int NEXT = gg_ttgg::NEXT;
   static constexpr int MAX_LB = gg_ttgg::MAX_LB;
+  static constexpr int NJS = gg_ttgg::NJS;
+  static constexpr bool JSMEM = false;  // currents of 3+ gluons in shared memory (FP32)
   template <class R, int LB, int CM>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
-    return gg_ttgg::hel_sum<R, LB, CM>(X, K, lane);
+    return gg_ttgg::hel_sum<R, LB, CM, JSMEM && sizeof(R) == 4>(X, K, lane);
   }
 };
 using P = QcdProc<Tag>;

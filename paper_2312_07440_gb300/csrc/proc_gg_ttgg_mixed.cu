@@ -12,9 +12,11 @@ struct Tag {
   static constexpr int NG = gg_ttgg::NG;
   static constexpr int NEXT = gg_ttgg::NEXT;
   static constexpr int MAX_LB = gg_ttgg::MAX_LB;
+  static constexpr int NJS = gg_ttgg::NJS;
+  static constexpr bool JSMEM = true;  // currents of 3+ gluons in shared memory (FP32)
   template <class R, int LB, int CM>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
-    return gg_ttgg::hel_sum<R, LB, CM>(X, K, lane);
+    return gg_ttgg::hel_sum<R, LB, CM, JSMEM && sizeof(R) == 4>(X, K, lane);
   }
 };
 using P16 = QcdProc<Tag, CM_FP16>;
@@ -22,12 +24,14 @@ using PB16 = QcdProc<Tag, CM_BF16>;
 }  // namespace
 
 void register_gg_ttgg_mixed(std::vector<KernelEntry>& t) {
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1>, 128});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1>, 128});
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 2, (const void*)&k_reweight<P16, float, 2>, 128});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 2, (const void*)&k_reweight<PB16, float, 2>, 128});
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 3, (const void*)&k_reweight<P16, float, 3>, 128});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 3, (const void*)&k_reweight<PB16, float, 3>, 128});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1>, 128, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1>, 128, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 2, (const void*)&k_reweight<P16, float, 2>, 128, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 2, (const void*)&k_reweight<PB16, float, 2>, 128, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 3, (const void*)&k_reweight<P16, float, 3>, 128, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 4, (const void*)&k_reweight<P16, float, 4>, 128, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 3, (const void*)&k_reweight<PB16, float, 3>, 128, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 4, (const void*)&k_reweight<PB16, float, 4>, 128, 0, PB16::jstore_bytes<float>()});
 }
 
 }  // namespace rw

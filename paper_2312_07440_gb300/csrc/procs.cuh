@@ -24,6 +24,11 @@ struct QcdProc {
   // Momenta: FP64 in FP64 mode, double-float in the FP32 modes (dfloat.cuh).
   template <class R>
   using mom_t = typename std::conditional<sizeof(R) == 8, double, df>::type;
+  // dynamic shared memory per thread of the amplitude code (the current store)
+  template <class R>
+  static constexpr int jstore_bytes() {
+    return (Tag::JSMEM && sizeof(R) == 4) ? Tag::NJS * 32 : 0;
+  }
 
   template <class R, int LB>
   __device__ __noinline__ static double me(const mom_t<R> (&p)[NEXT][4], const PointDev& pt, int lane,
@@ -57,6 +62,10 @@ struct QedProc {
   static constexpr int NEXT = Tag::NEXT;
   template <class R>
   using mom_t = typename std::conditional<sizeof(R) == 8, double, df>::type;
+  template <class R>
+  static constexpr int jstore_bytes() {
+    return 0;
+  }
 
   template <class R, int LB>
   __device__ __noinline__ static double me(const mom_t<R> (&p)[NEXT][4], const PointDev& pt, int lane,
@@ -93,6 +102,10 @@ struct EeMumu {
   // few FP64 invariants per event are not a bottleneck)
   template <class R>
   using mom_t = double;
+  template <class R>
+  static constexpr int jstore_bytes() {
+    return 0;
+  }
 
   template <class R, int LB>
   __device__ __noinline__ static double me(const double (&p)[NEXT][4], const PointDev& pt, int lane,

@@ -26,6 +26,48 @@ struct QcdKin {
   R mc[1 << NG];     // c m
 };
 
+// Store for the gluon currents of three or more gluons (generated code puts
+// each once and gets it at every use).  Registers: a plain array indexed by
+// constants.  Shared memory (FP32): this thread's slice of the dynamic shared
+// memory, [slot][half][thread] float4 so a warp's accesses are conflict-free;
+// the accesses are volatile, so the compiler neither keeps a stored current
+// in registers nor moves a read above the write of its slot.  The kernel
+// places its own shared data after NS * 32 * blockDim.x bytes.
+template <class R, int NS, bool SMEM>
+struct JStore {
+  cv<R> v[NS > 0 ? NS : 1];
+  __device__ __forceinline__ void put(int s, const cv<R>& x) { v[s] = x; }
+  __device__ __forceinline__ cv<R> get(int s) const { return v[s]; }
+};
+
+template <int NS>
+struct JStore<float, NS, true> {
+  unsigned base, stride;
+  __device__ __forceinline__ JStore() {
+    extern __shared__ float4 rw_dyn_smem[];
+    base = (unsigned)__cvta_generic_to_shared(rw_dyn_smem + threadIdx.x);
+    stride = 16u * blockDim.x;
+  }
+  __device__ __forceinline__ void put(int s, const cv<float>& x) const {
+    const unsigned a = base + 2u * (unsigned)s * stride;
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x.c[0].r), "f"(x.c[0].i), "f"(x.c[1].r),
+                 "f"(x.c[1].i));
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a + stride), "f"(x.c[2].r), "f"(x.c[2].i),
+                 "f"(x.c[3].r), "f"(x.c[3].i));
+  }
+  __device__ __forceinline__ cv<float> get(int s) const {
+    const unsigned a = base + 2u * (unsigned)s * stride;
+    cv<float> x;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(x.c[0].r), "=f"(x.c[0].i), "=f"(x.c[1].r), "=f"(x.c[1].i)
+                 : "r"(a));
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(x.c[2].r), "=f"(x.c[2].i), "=f"(x.c[3].r), "=f"(x.c[3].i)
+                 : "r"(a + stride));
+    return x;
+  }
+};
+
 // particle index of gluon g on the top line: 0, 1 incoming, then 4, 5, ...
 __host__ __device__ constexpr int gluon_particle(int g) { return g < 2 ? g : g + 2; }
 

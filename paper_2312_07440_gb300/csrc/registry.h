@@ -12,6 +12,7 @@ struct KernelEntry {
   const void* func;  // __global__ k_reweight<...>(RwArgs) or k_interp<...>(InterpArgs)
   int max_block = 256;  // threads per block the variant supports
   int kind = 0;         // 0: k_reweight, 1: k_interp (interpolation surrogate)
+  int smem_per_thread = 0;  // dynamic shared memory of the amplitude code (bytes per thread)
 };
 
 struct ProcStatic {

@@ -240,11 +240,15 @@ int shape(rw_ctx* c, int P, Shape& sh) {
   if (!k) return fail(c, RW_ERR_MODE, "no kernel for process %d mode %d lane_bits %d", c->process, c->mode, lb);
   const int block = c->block > 0 ? c->block : 128;
   if (block > k->max_block) return fail(c, RW_ERR_ARG, "block %d above this variant's %d", block, k->max_block);
-  const size_t smem = (size_t)(block / 32) * (P + 1) * sizeof(double2);
+  const size_t smem = (size_t)k->smem_per_thread * block + (size_t)(block / 32) * (P + 1) * sizeof(double2);
   auto key = std::make_tuple(k->func, block, smem);
   auto it = c->occ.find(key);
   int per_sm;
   if (it == c->occ.end()) {
+    if (smem > 48 * 1024) {  // opt in to more than the default 48 KB of dynamic shared memory
+      cudaError_t e = cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
+    }
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, block, smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) per_sm = 1;
@@ -794,7 +798,10 @@ extern "C" int rw_reweight_noalloc(rw_ctx* c, const double* d_mom, const double*
   if (!k) return noalloc_fail(c, RW_ERR_MODE, "no kernel");
   const int block = c->block > 0 ? c->block : 128;
   if (block > k->max_block) return noalloc_fail(c, RW_ERR_ARG, "block too large");
-  const size_t smem = (size_t)(block / 32) * (P + 1) * sizeof(double2);
+  const size_t smem = (size_t)k->smem_per_thread * block + (size_t)(block / 32) * (P + 1) * sizeof(double2);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return noalloc_fail(c, RW_ERR_CUDA, "smem attribute");
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, block, smem) != cudaSuccess) {
     cudaGetLastError();
@@ -1333,14 +1340,18 @@ int rw_reweight_interp(rw_ctx* c, int n_nodes, double tol, double* d_wnew, unsig
   {
     Shape sh;
     if ((rc = shape(c, 0, sh))) return rc;
+    const size_t ismem = (size_t)k->smem_per_thread * sh.block;
+    if (ismem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem)) != cudaSuccess)
+      return cuda_fail(c, e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
     int per_sm = 1;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, sh.block, 0)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, sh.block, ismem)) != cudaSuccess)
       return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     const long long need = (E * (1 << lb) + sh.block - 1) / sh.block;
     const int grid = (int)std::max(1LL, std::min<long long>({(long long)GRID_CAP,
                                                               (long long)std::max(1, per_sm) * c->sm_count, need}));
     void* args[] = {&ia};
-    if ((e = cudaLaunchKernel(k->func, dim3(grid), dim3(sh.block), args, 0, c->stream)) != cudaSuccess)
+    if ((e = cudaLaunchKernel(k->func, dim3(grid), dim3(sh.block), args, ismem, c->stream)) != cudaSuccess)
       return cuda_fail(c, e, "interpolation kernel launch");
   }
   if ((e = cudaMemcpyAsync(c->h_stage, ia.counts, 16, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||

@@ -222,6 +222,8 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     w(f"constexpr int NHEL = {2 ** (n + 2)};")
     w(f"constexpr int NDIAG = {diagram_count(n)};")
     w(f"constexpr int MAX_LB = {n};  // helicity levels that can be spread over lanes")
+    njs = sum(math.perm(n, L) // 2 for L in range(3, n + 1))
+    w(f"constexpr int NJS = {njs};  // currents of 3+ gluons, one JStore slot each")
     w(f"constexpr int CDEN = {den};")
     w(f"constexpr int IDENT = {n_identical};  // identical outgoing gluons (1/IDENT!)")
     w(f"constexpr unsigned OUTGOING_GLUONS = {sum(1 << g for g in outgoing_gluons)}u;  // bit g: gluon g outgoing")
@@ -233,12 +235,23 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     w("// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;")
     w("// helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).")
     w("// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float).")
-    w("template <class R, int LB, int CM = CM_FMA>")
+    w("template <class R, int LB, int CM = CM_FMA, bool JS = false>")
     w("__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {")
     w("  static_assert(CM == CM_FMA || sizeof(R) == 4, \"tensor-core colour sum takes FP32 amplitudes\");")
     w("  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI);")
+    w("  JStore<R, NJS, JS> js;")
     w("  R acc = R(0);")
     ind = "  "
+
+    def jref(sq):
+        """Expression for the current of the gluon sequence sq."""
+        if len(sq) == 1:
+            return f"E{sq[0]}"
+        if sq in slot:
+            return f"js.get({slot[sq]})"
+        if sq in alias:
+            return alias[sq]
+        return seq_name("J", sq)
 
     # all sequences of distinct gluons, by length
     seqs = {L: list(itertools.permutations(range(n), L)) for L in range(1, n + 1)}
@@ -263,7 +276,12 @@ def emit_process(name, n, outgoing_gluons, n_identical):
         w(f"{ind}const int {hvar} = LB >= {L} ? {bit} : i{L};")
         w(f"{ind}{sel}")
 
-    # gluon levels
+    # gluon levels.  Currents of three or more gluons live in a JStore slot
+    # (registers, or this thread's slice of shared memory when JS is set):
+    # they are written once and read back at every use, so the compiler need
+    # not keep all of them in registers through the antitop level.
+    slot = {}    # canonical sequence -> slot
+    alias = {}   # any sequence -> expression
     for g in range(n):
         open_level(g, f"h{g}", f"const cv<R> E{g} = h{g} ? X.eps[{g}][1] : X.eps[{g}][0];")
         for L in range(2, n + 1):
@@ -274,18 +292,19 @@ def emit_process(name, n, outgoing_gluons, n_identical):
                 rv = tuple(reversed(sq))
                 if rv in canon:
                     # reflection identity J(reversed) = (-1)^{L+1} J
-                    src = canon[rv]
-                    w(f"{ind}const cv<R> {nm} = {'neg(' + src + ')' if L % 2 == 0 else src};")
+                    src = jref(rv)
+                    expr = f"neg({src})" if L % 2 == 0 else src
+                    if rv in slot:
+                        alias[sq] = expr
+                    else:
+                        w(f"{ind}const cv<R> {nm} = {expr};")
                     continue
                 canon[sq] = nm
                 m = mask(sq)
-
-                def jn(s):
-                    return f"E{s[0]}" if len(s) == 1 else seq_name("J", s)
                 terms = []
                 for c in range(1, L):
                     a, b = sq[:c], sq[c:]
-                    terms.append(f"{jn(a)}, Kn.P[{mask(a)}], {jn(b)}, Kn.P[{mask(b)}], Kn.cg[{m}]")
+                    terms.append(f"{jref(a)}, Kn.P[{mask(a)}], {jref(b)}, Kn.P[{mask(b)}], Kn.cg[{m}]")
                     em.count(g, "vvv")
                 w(f"{ind}cv<R> {nm} = vvv({terms[0]});")
                 for t in terms[1:]:
@@ -294,8 +313,11 @@ def emit_process(name, n, outgoing_gluons, n_identical):
                 for c in range(1, L):
                     for d in range(c + 1, L):
                         a, b, cc = sq[:c], sq[c:d], sq[d:]
-                        w(f"{ind}vvvv_acc({nm}, {jn(a)}, {jn(b)}, {jn(cc)}, Kn.c4[{m}]);")
+                        w(f"{ind}vvvv_acc({nm}, {jref(a)}, {jref(b)}, {jref(cc)}, Kn.c4[{m}]);")
                         em.count(g, "vvvv_acc")
+                if L >= 3:
+                    slot[sq] = len(slot)
+                    w(f"{ind}js.put({slot[sq]}, {nm});")
     # antitop level: the fermion currents psi(rho) = S_rho (rho a proper
     # sequence of gluons attached from the antitop end), the amputated spinor
     # X(sigma) = sum_c Jslash(sigma[..c]) psi(sigma[c+1..]) of every ordering and
@@ -306,8 +328,7 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     # at any time.
     open_level(n, f"h{n}", f"const sp<R> S_E = h{n} ? X.v[1] : X.v[0];")
 
-    def jn(s):
-        return f"E{s[0]}" if len(s) == 1 else seq_name("J", s)
+    jn = jref
 
     def visit(suffix):
         rest = [g for g in range(n) if g not in suffix]
