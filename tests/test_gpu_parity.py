@@ -280,17 +280,20 @@ def test_host_entry_point_matches_device_path():
     assert abs(sig[0] - math.fsum(hw[0])) <= 2 * np.spacing(sig[0])
 
 
-def test_host_entry_point_pipelined_chunks():
+@pytest.mark.parametrize("proc,wl,mode,E", [
+    ("gg_tt", "gg_tt_1m", "fp64", 300001),   # several chunks and a ragged last one
+    ("gg_ttgg", "gg_ttgg_1m", "fp32", 30001),  # a kernel with its current store in shared memory
+])
+def test_host_entry_point_pipelined_chunks(proc, wl, mode, E):
     """A batch larger than one launch's resident threads goes through the
     chunked copy/compute pipeline: W' bit-identical to the device path, the
     carried sums within 2 ulp of the exact sums, and the same result without
     the W' copy-out."""
-    E = 300001  # several chunks and a ragged last one
     pts = np.stack([ev.param_vector(m_t=175.0, alpha_s=0.120), ev.param_vector(m_t=170.0)])
-    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], E)
-    g = run_gpu("gg_tt", "fp64", mom, w, pts)
+    mom, w = ev.generate(ev.WORKLOADS[wl], E)
+    g = run_gpu(proc, mode, mom, w, pts)
     with rwgt.Context(0, torch.cuda.current_stream().cuda_stream) as c:
-        c.set_process("gg_tt", "fp64")
+        c.set_process(proc, mode)
         c.set_params(ev.param_vector())
         c.set_reweight_points(pts)
         nb = c.workspace_bytes_host(E)

@@ -33,11 +33,13 @@ def noalloc_fn():
     return fn
 
 
-@pytest.mark.parametrize("proc,wl,n,pts", [
-    ("gg_tt", "gg_tt_1m", 5003, ev.reweight_points("gg_tt_1m")),
-    ("gg_ttg", "gg_ttg_4m", 700, ev.reweight_points("gg_ttg_4m", "mt")[::8]),
+@pytest.mark.parametrize("proc,wl,n,pts,mode", [
+    ("gg_tt", "gg_tt_1m", 5003, ev.reweight_points("gg_tt_1m"), "fp64"),
+    ("gg_ttg", "gg_ttg_4m", 700, ev.reweight_points("gg_ttg_4m", "mt")[::8], "fp64"),
+    # a kernel with its current store in dynamic shared memory
+    ("gg_ttgg", "gg_ttgg_1m", 300, ev.reweight_points("gg_ttgg_1m", "mt"), "fp32"),
 ])
-def test_noalloc_matches_workspace_entry_point_twice(proc, wl, n, pts):
+def test_noalloc_matches_workspace_entry_point_twice(proc, wl, n, pts, mode):
     dev = torch.device("cuda", 0)
     mom, w = ev.generate(ev.WORKLOADS[wl], n)
     dm = torch.from_numpy(mom).to(dev)
@@ -46,7 +48,7 @@ def test_noalloc_matches_workspace_entry_point_twice(proc, wl, n, pts):
     stream = torch.cuda.current_stream(dev).cuda_stream
     fn = noalloc_fn()
     with rwgt.Context(0, stream) as c:
-        c.set_process(proc, "fp64")
+        c.set_process(proc, mode)
         c.set_params(ev.param_vector())
         c.set_reweight_points(pts)
         # reference: the workspace-based entry point
