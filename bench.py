@@ -93,13 +93,18 @@ def dist_info():
     return rank, world, local
 
 
-def source_sha():
-    """Hash of the sources the kernels are compiled from (csrc; the host-only
-    event-file I/O in lhe.cu holds no device code and is left out)."""
+def source_sha(process, mode):
+    """Hash of the sources one kernel is compiled from: its translation unit,
+    the launch code and every header except other processes' generated
+    amplitude code (the host-only event-file I/O holds no device code)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2312_07440_gb300", "csrc")
+    tu = f"proc_{process}_{'mixed' if mode.startswith('mixed') else mode}.cu"
+    if not os.path.exists(os.path.join(d, tu)):
+        tu = f"proc_{process}.cu"
     for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".cuh", ".h")) and fn != "lhe.cu":
+        gen = fn.startswith("gen_") and fn.endswith(".cuh")
+        if fn in (tu, "rw_abi.cu") or (fn.endswith((".cuh", ".h")) and (not gen or fn.endswith(f"_{process}.cuh"))):
             with open(os.path.join(d, fn), "rb") as f:
                 h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
@@ -108,7 +113,7 @@ def source_sha():
 def profiled_traffic(workload, mode):
     """DRAM bytes per launch from a committed ncu summary, if it was taken
     on the current kernel sources (profiles/*.md 'traffic:' lines)."""
-    sha = source_sha()
+    sha = source_sha(ev.WORKLOADS[workload].process, mode)
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None

@@ -111,6 +111,18 @@ __device__ __forceinline__ void spadd(sp<R>& a, const sp<R>& b) {
 #pragma unroll
   for (int m = 0; m < 4; ++m) a.c[m] = a.c[m] + b.c[m];
 }
+template <class R>
+__device__ __forceinline__ sp<R> spneg(const sp<R>& a) {
+  sp<R> o;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) o.c[m] = -a.c[m];
+  return o;
+}
+template <class R>
+__device__ __forceinline__ void spsub(sp<R>& a, const sp<R>& b) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) a.c[m] = a.c[m] - b.c[m];
+}
 
 // Colour-ordered 3-gluon vertex and the off-shell gluon propagator,
 // c = -1/K^2 (Feynman gauge, g stripped), K = P1 + P2:
@@ -159,27 +171,44 @@ __device__ __forceinline__ void vvvv_acc(cv<R>& o, const cv<R>& J1, const cv<R>&
   for (int m = 0; m < 4; ++m) o.c[m] = cmsc(J3.c[m], t12, cmsc(J1.c[m], t23, cmac(J2.c[m], t13, o.c[m])));
 }
 
-// Jslash psi = gamma^mu J_mu psi                                          (64 flops)
-// slash returns it, slash_acc adds it to o (+8 flops).
+// A complex vector in Weyl-block form: a0 - a3, a0 + a3, a1 + i a2, a1 - i a2
+// (the entries of the 2x2 blocks of a-slash in the chiral basis)   (8 flops)
+template <class R>
+struct ws {
+  cx<R> am, ap, bp, bm;
+};
+template <class R>
+__device__ __forceinline__ ws<R> weyl_form(const cv<R>& a) {
+  return {a.c[0] - a.c[3], a.c[0] + a.c[3], {a.c[1].r - a.c[2].i, a.c[1].i + a.c[2].r},
+          {a.c[1].r + a.c[2].i, a.c[1].i - a.c[2].r}};
+}
+
+// Jslash psi = gamma^mu J_mu psi: 56 flops from the Weyl-block form, 64 from
+// the vector.  slash returns it, slash_acc adds it to o (+8 flops).
 template <class R, bool ACC>
-__device__ __forceinline__ void slash_impl(sp<R>& o, const cv<R>& a, const sp<R>& s) {
-  const cx<R> ap = a.c[0] + a.c[3], am = a.c[0] - a.c[3];
-  const cx<R> bp = {a.c[1].r - a.c[2].i, a.c[1].i + a.c[2].r};  // a1 + i a2
-  const cx<R> bm = {a.c[1].r + a.c[2].i, a.c[1].i - a.c[2].r};  // a1 - i a2
-  o.c[0] = cmsc(bm, s.c[3], ACC ? cmac(am, s.c[2], o.c[0]) : cmul(am, s.c[2]));
-  o.c[1] = cmsc(bp, s.c[2], ACC ? cmac(ap, s.c[3], o.c[1]) : cmul(ap, s.c[3]));
-  o.c[2] = cmac(bm, s.c[1], ACC ? cmac(ap, s.c[0], o.c[2]) : cmul(ap, s.c[0]));
-  o.c[3] = cmac(am, s.c[1], ACC ? cmac(bp, s.c[0], o.c[3]) : cmul(bp, s.c[0]));
+__device__ __forceinline__ void slash_impl(sp<R>& o, const ws<R>& a, const sp<R>& s) {
+  o.c[0] = cmsc(a.bm, s.c[3], ACC ? cmac(a.am, s.c[2], o.c[0]) : cmul(a.am, s.c[2]));
+  o.c[1] = cmsc(a.bp, s.c[2], ACC ? cmac(a.ap, s.c[3], o.c[1]) : cmul(a.ap, s.c[3]));
+  o.c[2] = cmac(a.bm, s.c[1], ACC ? cmac(a.ap, s.c[0], o.c[2]) : cmul(a.ap, s.c[0]));
+  o.c[3] = cmac(a.am, s.c[1], ACC ? cmac(a.bp, s.c[0], o.c[3]) : cmul(a.bp, s.c[0]));
 }
 template <class R>
-__device__ __forceinline__ sp<R> slash(const cv<R>& a, const sp<R>& s) {
+__device__ __forceinline__ sp<R> slash(const ws<R>& a, const sp<R>& s) {
   sp<R> o;
   slash_impl<R, false>(o, a, s);
   return o;
 }
 template <class R>
-__device__ __forceinline__ void slash_acc(sp<R>& o, const cv<R>& a, const sp<R>& s) {
+__device__ __forceinline__ sp<R> slash(const cv<R>& a, const sp<R>& s) {
+  return slash(weyl_form(a), s);
+}
+template <class R>
+__device__ __forceinline__ void slash_acc(sp<R>& o, const ws<R>& a, const sp<R>& s) {
   slash_impl<R, true>(o, a, s);
+}
+template <class R>
+__device__ __forceinline__ void slash_acc(sp<R>& o, const cv<R>& a, const sp<R>& s) {
+  slash_impl<R, true>(o, weyl_form(a), s);
 }
 
 // Top propagator applied to a spinor, with the factor folded in:

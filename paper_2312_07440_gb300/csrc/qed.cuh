@@ -21,17 +21,6 @@ struct w2 {  // two-component Weyl spinor
   cx<R> c[2];
 };
 
-template <class R>
-struct ws {  // a complex vector in Weyl-block form: a0 - a3, a0 + a3, a1 + i a2, a1 - i a2
-  cx<R> am, ap, bp, bm;
-};
-
-template <class R>
-__device__ __forceinline__ ws<R> weyl_form(const cv<R>& a) {
-  return {a.c[0] - a.c[3], a.c[0] + a.c[3], {a.c[1].r - a.c[2].i, a.c[1].i + a.c[2].r},
-          {a.c[1].r + a.c[2].i, a.c[1].i - a.c[2].r}};
-}
-
 // eps-slash on a right-handed spinor -> left-handed                        (28 flops)
 template <class R>
 __device__ __forceinline__ w2<R> sl_RL(const ws<R>& a, const w2<R>& s) {

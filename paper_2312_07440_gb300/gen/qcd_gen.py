@@ -160,10 +160,15 @@ def diagram_count(n):
 # ---------------------------------------------------------------------------
 # floating-point operations of the device primitives in helas.cuh (real
 # operations; an FMA counts 2).  Kept in step with helas.cuh by hand.
+PAIRS_MAX_K = 6  # colour sums of up to this many orderings by pairs (see emit_process)
+ROW_ACCS = 4     # accumulators per top helicity for the row-wise colour sum
+
 FLOPS = {
     "vvv": 156,      # 3-gluon vertex with folded propagator factor
     "vvvv_acc": 193, # 4-gluon vertex accumulated
-    "slash": 64,     # Jslash psi
+    "slash": 64,     # Jslash psi from the vector J
+    "slash_w": 56,   # Jslash psi from J's Weyl-block form
+    "weyl": 8,       # Weyl-block form of a vector
     "sp_add": 8,     # spinor accumulate
     "fprop": 58,     # c (qslash + m) chi
     "fcur": 72,      # ubar gamma^mu psi
@@ -193,7 +198,7 @@ class Emitter:
         self.flops_per_level[level] += FLOPS[key] * times
 
 
-def emit_process(name, n, outgoing_gluons, n_identical):
+def emit_process(name, n, outgoing_gluons, n_identical, hoist_weyl=True, share_fp32=0):
     """Emit the helicity-summed, couplings-stripped colour sum for t tbar + n g.
 
     Loop levels 0..n-1: gluon helicities; level n: antitop (the top helicity is
@@ -201,6 +206,10 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     Level 0 is fixed (helicity-flip symmetry); the returned device function
     sums over the helicities of one lane, levels 1..LB taking their helicity
     bits from the lane index.
+
+    hoist_weyl: form each polarisation's Weyl-block form once per level trip
+    and both antitop variants of S(0) once per helicity sum (fewer operations,
+    more live registers; it pays where the state is small).
     """
     em = Emitter(n)
     perms = orderings(n)
@@ -241,6 +250,26 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     w("  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI);")
     w("  JStore<R, NJS, JS> js;")
     w("  R acc = R(0);")
+    # Colour sum by FMA.  Up to PAIRS_MAX_K orderings: sum over the pairs
+    # i <= j with C_ij != 0 of c_ij Re(A_i^* A_j) (c_ii = C_ii, c_ij = 2 C_ij),
+    # each product accumulated by two FMAs into one accumulator per distinct
+    # c and top helicity (two independent chains), scaled once after the loops.  Larger K: z = C A row by row, then
+    # Re(A_i^* z_i) into acc (C's symmetric half, coefficients pre-scaled).
+    pairs = K <= PAIRS_MAX_K
+    coef = {}
+    if pairs:
+        for i in range(K):
+            for j in range(i, K):
+                if Cint[i][j]:
+                    c = Cint[i][j] * (1 if i == j else 2)
+                    coef.setdefault(c, len(coef))
+        ccs = [f"cc{k}_{h} = R(0)" for h in (0, 1) for k in range(len(coef))]
+        w(f"  [[maybe_unused]] R {', '.join(ccs)};  // per distinct c_ij and top helicity")
+    else:
+        # rows spread over ROW_ACCS accumulators per top helicity: short FMA
+        # dependency chains
+        czs = [f"cz{h}_{k} = R(0)" for h in (0, 1) for k in range(ROW_ACCS)]
+        w(f"  [[maybe_unused]] R {', '.join(czs)};")
     ind = "  "
 
     def jref(sq):
@@ -281,9 +310,25 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     # they are written once and read back at every use, so the compiler need
     # not keep all of them in registers through the antitop level.
     slot = {}    # canonical sequence -> slot
+    wform = {}   # canonical sequence -> name of its Weyl form
     alias = {}   # any sequence -> expression
     for g in range(n):
         open_level(g, f"h{g}", f"const cv<R> E{g} = h{g} ? X.eps[{g}][1] : X.eps[{g}][0];")
+        if hoist_weyl:
+            w(f"{ind}const ws<R> W{g} = weyl_form(E{g});")
+            em.count(g, "weyl")
+        if g == 0 and hoist_weyl:
+            # S(0) depends on the antitop helicity and on gluon 0's, which is
+            # fixed: both antitop variants are formed here once instead of at
+            # every trip of the inner loops (unless the antitop helicity is a
+            # lane bit, when each lane forms its own below).
+            w(f"{ind}[[maybe_unused]] sp<R> S_0v0, S_0v1;")
+            w(f"{ind}if constexpr (LB < {n}) {{")
+            w(f"{ind}  S_0v0 = fprop(Kn.qc[1], Kn.mc[1], slash(W0, X.v[0]));")
+            w(f"{ind}  S_0v1 = fprop(Kn.qc[1], Kn.mc[1], slash(W0, X.v[1]));")
+            w(f"{ind}}}")
+            em.count(0, "slash_w", 2)
+            em.count(0, "fprop", 2)
         for L in range(2, n + 1):
             for sq in seqs[L]:
                 if max(sq) != g:
@@ -318,6 +363,11 @@ def emit_process(name, n, outgoing_gluons, n_identical):
                 if L >= 3:
                     slot[sq] = len(slot)
                     w(f"{ind}js.put({slot[sq]}, {nm});")
+                elif L == n and hoist_weyl:
+                    # a full-length current is only ever slashed: keep its Weyl form
+                    wform[sq] = f"W{nm}"
+                    w(f"{ind}const ws<R> W{nm} = weyl_form({nm});")
+                    em.count(g, "weyl")
     # antitop level: the fermion currents psi(rho) = S_rho (rho a proper
     # sequence of gluons attached from the antitop end), the amputated spinor
     # X(sigma) = sum_c Jslash(sigma[..c]) psi(sigma[c+1..]) of every ordering and
@@ -328,41 +378,110 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     # at any time.
     open_level(n, f"h{n}", f"const sp<R> S_E = h{n} ? X.v[1] : X.v[0];")
 
-    jn = jref
+    def jn(sq):
+        return f"W{sq[0]}" if len(sq) == 1 and hoist_weyl else jref(sq)
+
+    def slash_kind(sq):
+        return "slash_w" if len(sq) == 1 and hoist_weyl else "slash"
+
+    # Every term Jslash(a) psi(b) with |a| >= 2 occurs twice at this level:
+    # in the node a+b and in rev(a)+b, where J(rev a) = (-1)^{|a|+1} J(a).
+    # The second occurrence reuses the first's spinor Y (one slash instead of
+    # two) in FP64, where a slash costs far more than keeping Y in registers
+    # or L1; in FP32 only when the two uses are at most share_fp32 statements
+    # apart (a distant Y would spill and cost more than the slash it saves).
+    # A node starts from its shared spinors (+-Y, no products) and takes its
+    # single-gluon term last as a fused slash-accumulate.
+    ops = []  # ("line", text) or ("node", target, declaration, [(a, b) terms], single-gluon term)
 
     def visit(suffix):
         rest = [g for g in range(n) if g not in suffix]
         if len(rest) == 1:
             sg = (rest[0],) + suffix
             k = perms.index(sg)
-            terms = []
-            for c in range(1, n + 1):
-                a, b = sg[:c], sg[c:]
-                terms.append(f"{jn(a)}, {seq_name('S_', b)}")
-                em.count(n, "slash")
-            w(f"{ind}sp<R> X{k} = slash({terms[0]});")
-            for t in terms[1:]:
-                w(f"{ind}slash_acc(X{k}, {t});")
-                em.count(n, "sp_add")
-            w(f"{ind}const cx<R> A{k}_0 = rowcol(X.ub[0], X{k}), A{k}_1 = rowcol(X.ub[1], X{k});")
+            ops.append(("node", f"X{k}", f"sp<R> X{k}", [(sg[:c], sg[c:]) for c in range(2, n + 1)], (sg[:1], sg[1:])))
+            ops.append(("line", f"const cx<R> A{k}_0 = rowcol(X.ub[0], X{k}), A{k}_1 = rowcol(X.ub[1], X{k});"))
             em.count(n, "rowcol", 2)
             return
         for b0 in rest:
             rho = (b0,) + suffix
             nm = seq_name("S_", rho)
-            terms = []
-            for c in range(1, len(rho) + 1):
-                a, b = rho[:c], rho[c:]
-                terms.append(f"{jn(a)}, {seq_name('S_', b)}")
-                em.count(n, "slash")
-            w(f"{ind}sp<R> t{nm} = slash({terms[0]});")
-            for t in terms[1:]:
-                w(f"{ind}slash_acc(t{nm}, {t});")  # fused accumulation
-                em.count(n, "sp_add")
-            w(f"{ind}const sp<R> {nm} = fprop(Kn.qc[{mask(rho)}], Kn.mc[{mask(rho)}], t{nm});")
+            if rho == (0,) and hoist_weyl:
+                ops.append(("line", "sp<R> S_0;"))
+                ops.append(("line", f"if constexpr (LB < {n}) S_0 = h{n} ? S_0v1 : S_0v0;"))
+                ops.append(("line", "else S_0 = fprop(Kn.qc[1], Kn.mc[1], slash(W0, S_E));"))
+                visit(rho)
+                continue
+            ops.append(("node", f"t{nm}", f"sp<R> t{nm}", [(rho[:c], rho[c:]) for c in range(2, len(rho) + 1)],
+                        (rho[:1], rho[1:])))
+            ops.append(("line", f"const sp<R> {nm} = fprop(Kn.qc[{mask(rho)}], Kn.mc[{mask(rho)}], t{nm});"))
             em.count(n, "fprop")
             visit(rho)
     visit(())
+
+    def share_key(a, b):
+        ca = a if a in canon else tuple(reversed(a))
+        sgn = 1 if ca == a or len(a) % 2 == 1 else -1
+        return (ca, b), sgn
+
+    uses = {}
+    for i, op in enumerate(ops):
+        if op[0] == "node":
+            for a, b in op[3]:
+                uses.setdefault(share_key(a, b)[0], []).append(i)
+    assert all(len(u) == 2 for u in uses.values())
+    share_gaps = sorted(u[1] - u[0] for u in uses.values())
+    w(f"{ind}constexpr bool SH = sizeof(R) == 8;  // share every repeated slash (FP64)")
+    for i, op in enumerate(ops):
+        if op[0] == "line":
+            w(f"{ind}{op[1]}")
+            continue
+        _, tgt, decl, terms, (a1, b1) = op
+        w1 = f"{jn(a1)}, {seq_name('S_', b1)}"
+        em.count(n, slash_kind(a1))
+        if not terms:
+            w(f"{ind}{decl} = slash({w1});")
+            continue
+        w(f"{ind}{decl};")
+        info = []
+        for t, (a, b) in enumerate(terms):
+            key, sgn = share_key(a, b)
+            first, second = uses[key]
+            yn = "Y" + "_".join(map(str, key[0])) + "__" + seq_name("S_", b)[2:]
+            near = second - first <= share_fp32
+            info.append((a, b, key, sgn, i == first, yn, near))
+            if i == first:
+                w(f"{ind}[[maybe_unused]] sp<R> {yn};  // Jslash({','.join(map(str, key[0]))}) psi({seq_name('S_', b)[2:]})")
+                em.count(n, "slash_w" if key[0] in wform else "slash")
+            if t > 0:
+                em.count(n, "sp_add")
+        em.count(n, "sp_add")  # the single-gluon term, accumulated
+
+        def shared_form(ind2, conds):
+            for t, ((a, b, key, sgn, first, yn, near), cond) in enumerate(zip(info, conds)):
+                sb = seq_name("S_", b)
+                if first:
+                    w(f"{ind2}if constexpr ({cond}) {yn} = slash({wform.get(key[0], jref(key[0]))}, {sb});")
+                if t == 0:
+                    ys = yn if sgn > 0 else f"spneg({yn})"
+                    w(f"{ind2}if constexpr ({cond}) {tgt} = {ys}; else {tgt} = slash({jref(a)}, {sb});")
+                else:
+                    w(f"{ind2}if constexpr ({cond}) {'spadd' if sgn > 0 else 'spsub'}({tgt}, {yn}); "
+                      f"else slash_acc({tgt}, {jref(a)}, {sb});")
+            w(f"{ind2}slash_acc({tgt}, {w1});  // single-gluon term, fused")
+
+        if any(x[6] for x in info):
+            shared_form(ind, ["true" if x[6] else "SH" for x in info])
+        else:
+            # nothing shared in FP32: there the single-gluon term goes first, as
+            # the node's chain starts from the spinor just computed
+            w(f"{ind}if constexpr (SH) {{")
+            shared_form(ind + "  ", ["true"] * len(info))
+            w(f"{ind}}} else {{")
+            w(f"{ind}  {tgt} = slash({w1});")
+            for a, b, *_ in info:
+                w(f"{ind}  slash_acc({tgt}, {jref(a)}, {seq_name('S_', b)});")
+            w(f"{ind}}}")
     # colour sums of both top helicities
     w(f"{ind}if constexpr (CM != CM_FMA) {{")
     for h in (0, 1):
@@ -370,26 +489,44 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     w(f"{ind}  acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip")
     w(f"{ind}}} else {{")
     ind += "  "
-    # colour sum with the symmetric integer matrix: sum_i Re(A_i^* (C_ii/2 A_i + sum_{j>i} C_ij A_j)) * 2
-    w(f"{ind}R cs = R(0);")
-    for h in (0, 1):
-        for i in range(K):
-            tr, ti = f"R({Cint[i][i]}) * R(0.5) * A{i}_{h}.r", f"R({Cint[i][i]}) * R(0.5) * A{i}_{h}.i"
-            parts_r, parts_i = [tr], [ti]
-            for j in range(i + 1, K):
-                if Cint[i][j] == 0:
-                    continue
-                parts_r.append(f"R({Cint[i][j]}) * A{j}_{h}.r")
-                parts_i.append(f"R({Cint[i][j]}) * A{j}_{h}.i")
-            w(f"{ind}{{ const R zr = {' + '.join(parts_r)}; const R zi = {' + '.join(parts_i)};")
-            w(f"{ind}  cs += A{i}_{h}.r * zr + A{i}_{h}.i * zi; }}")
-            em.flops_per_level[n] += 4 * len(parts_r) + 4
-    w(f"{ind}acc += R(4) * cs;  // x2 symmetric colour sum, x2 helicity flip")
+    if pairs:
+        for h in (0, 1):
+            for i in range(K):
+                for j in range(i, K):
+                    if not Cint[i][j]:
+                        continue
+                    k = coef[Cint[i][j] * (1 if i == j else 2)]
+                    a, b = f"A{i}_{h}", f"A{j}_{h}"
+                    w(f"{ind}cc{k}_{h} = fmadd({a}.r, {b}.r, fmadd({a}.i, {b}.i, cc{k}_{h}));")
+                    em.flops_per_level[n] += 4
+    else:
+        # symmetric half, x2 symmetric colour sum, x2 helicity flip folded in:
+        # acc += Re(A_i^* (2 C_ii A_i + 4 sum_{j>i} C_ij A_j))
+        for h in (0, 1):
+            for i in range(K):
+                parts_r, parts_i = [f"R({2 * Cint[i][i]}) * A{i}_{h}.r"], [f"R({2 * Cint[i][i]}) * A{i}_{h}.i"]
+                for j in range(i + 1, K):
+                    if Cint[i][j] == 0:
+                        continue
+                    parts_r.append(f"R({4 * Cint[i][j]}) * A{j}_{h}.r")
+                    parts_i.append(f"R({4 * Cint[i][j]}) * A{j}_{h}.i")
+                w(f"{ind}{{ const R zr = {' + '.join(parts_r)}; const R zi = {' + '.join(parts_i)};")
+                k = f"cz{h}_{i % ROW_ACCS}"
+                w(f"{ind}  {k} = fmadd(A{i}_{h}.r, zr, fmadd(A{i}_{h}.i, zi, {k})); }}")
+                em.flops_per_level[n] += 4 * len(parts_r) + 4
     ind = ind[:-2]
     w(f"{ind}}}")
     for L in range(nlev - 1, -1, -1):
         ind = ind[:-2]
         w(f"{ind}}}")
+    if pairs:
+        combo = " + ".join(f"R({c}) * (cc{k}_0 + cc{k}_1)" for c, k in coef.items())
+        w(f"  if constexpr (CM == CM_FMA) acc = R(2) * ({combo});  // x2 helicity flip")
+        em.flops_per_level[0] += 3 * len(coef) + 1
+    else:
+        combo = " + ".join(f"cz{h}_{k}" for h in (0, 1) for k in range(ROW_ACCS))
+        w(f"  if constexpr (CM == CM_FMA) acc = {combo};")
+        em.flops_per_level[0] += 2 * ROW_ACCS - 1
     w("  return acc;")
     w("}")
     w("")
@@ -400,22 +537,25 @@ def emit_process(name, n, outgoing_gluons, n_identical):
     w(f"// floating-point operations of one full helicity sum (all levels, all loop trips)")
     w(f"constexpr long FLOPS_HEL_SUM = {total};")
     w("}}  // namespace")
+    emit_process.share_gaps = share_gaps
     return "\n".join(lines) + "\n", total
 
 
 PROCESSES = {
-    # name: (gluons on the top line, outgoing gluon indices, identical outgoing gluons)
-    "gg_tt": (2, (), 1),
-    "gg_ttg": (3, (2,), 1),
-    "gg_ttgg": (4, (2, 3), 2),
+    # name: (gluons on the top line, outgoing gluon indices, identical outgoing
+    # gluons, hoist_weyl -- off for n = 4, whose live state already spills,
+    # share_fp32 -- largest distance of a slash shared in FP32)
+    "gg_tt": (2, (), 1, True, 8),
+    "gg_ttg": (3, (2,), 1, True, 16),
+    "gg_ttgg": (4, (2, 3), 2, False, 0),
 }
 
 
 def main():
     here = os.path.dirname(os.path.abspath(__file__))
     out_dir = os.path.join(os.path.dirname(here), "csrc")
-    for name, (n, outg, ident) in PROCESSES.items():
-        src, fl = emit_process(name, n, outg, ident)
+    for name, (n, outg, ident, hw, sh) in PROCESSES.items():
+        src, fl = emit_process(name, n, outg, ident, hw, sh)
         with open(os.path.join(out_dir, f"gen_qcd_{name}.cuh"), "w") as f:
             f.write(src)
         print(name, "diagrams", diagram_count(n), "flops/hel-sum", fl)

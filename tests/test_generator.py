@@ -28,7 +28,7 @@ def test_p7_colour_matrix_matches_oracle(oracle_mod, n):
 
 def test_generated_headers_are_current():
     here = os.path.join(os.path.dirname(qcd_gen.__file__), "..", "csrc")
-    for name, (n, outg, ident) in qcd_gen.PROCESSES.items():
-        src, _ = qcd_gen.emit_process(name, n, outg, ident)
+    for name, spec in qcd_gen.PROCESSES.items():
+        src, _ = qcd_gen.emit_process(name, *spec)
         with open(os.path.join(here, f"gen_qcd_{name}.cuh")) as f:
             assert f.read() == src, f"regenerate gen_qcd_{name}.cuh"
