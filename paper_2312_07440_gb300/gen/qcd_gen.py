@@ -19,7 +19,11 @@ smaller generator for the processes it ships.  For n gluons on the top line it
     sub-current between the n! orderings (the sum over all Feynman diagrams,
     organised so that no diagram's chain is recomputed), with the helicity
     sum written as nested loops over the external helicities and every
-    current computed at the outermost loop level on which it depends;
+    gluon current computed at the outermost loop level on which it depends;
+  * shares, between the two orderings in which it occurs, every slash of a
+    multi-gluon current on a top spinor (reflection identity), hoists the
+    antitop current of the fixed-helicity gluon out of the inner loops, and
+    sums colours in pair form with one FMA accumulator per distinct entry;
   * counts the floating-point operations of the emitted code.
 
 Couplings are stripped (g = 1): every partial amplitude carries exactly g^n,
