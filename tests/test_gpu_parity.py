@@ -209,6 +209,19 @@ def test_tiny_batches(n):
     check_against_oracle(g, o, "fp64")
 
 
+@pytest.mark.parametrize("mode", ["fp64", "fp32"])
+def test_maximum_number_of_points(mode):
+    """256 parameter points in one launch (the most a context takes): m_t and
+    alpha_s on a 16 x 16 grid, a ragged number of events."""
+    mts = np.linspace(165.0, 181.0, 16)
+    als = np.linspace(0.110, 0.126, 16)
+    pts = np.stack([ev.param_vector(m_t=m, alpha_s=a) for m in mts for a in als])
+    assert pts.shape[0] == 256
+    mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 77, pts)
+    g = run_gpu("gg_tt", mode, mom, w, pts)
+    check_against_oracle(g, o, mode)
+
+
 def test_bad_events_are_counted_and_excluded():
     pts = ev.reweight_points("gg_tt_1m")
     mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 500)
