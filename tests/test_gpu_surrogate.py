@@ -182,6 +182,14 @@ def test_surrogate_pipeline_gg_ttgg():
             flag = torch.empty((P, E), dtype=torch.uint8, device=DEV)
             sig, nfb = rwgt.surrogate_reweight(c, m, P_SCALE, K_SCALE, s_max, wnew, flag, P, sws, sb)
             torch.cuda.synchronize()
+        # the network's prediction for every unseen event and point (no labels)
+        x_te, _ = features(mom_te, w_te, pts)
+        o_te = torch.empty((x_te.shape[0], 2), dtype=torch.float32, device=DEV)
+        m.forward(x_te, o_te)
+        torch.cuda.synchronize()
+    k_te = (0.85, 0.95, 1.05, 1.2)  # the inference points' kappa
+    dk = np.repeat(np.asarray(k_te) - 1.0, E)
+    r_net = np.exp(dk * o_te.cpu().numpy()[:, 0].astype(np.float64)).reshape(P, E)
     wn, fl = wnew.cpu().numpy(), flag.cpu().numpy().astype(bool)
     exw = ex["wnew"].cpu().numpy()
     assert np.array_equal(nfb, fl.sum(axis=1))
@@ -197,3 +205,18 @@ def test_surrogate_pipeline_gg_ttgg():
     frac = fl.mean()
     print(f"surrogate: fallback fraction {frac:.3f}, accepted violation rate {viol:.2e}, s_max {s_max:.2f}")
     assert 0.0 <= frac <= 1.0
+    # What the network gains for sigma'.  Exact ratios on a random audit subset
+    # of n events estimate sigma' = sum_e W_e r_e without bias as
+    #   sum_e W_e c_e + (E/n) sum_{e in audit} W_e (r_e - c_e)
+    # for any control c fixed beforehand.  Without the network the best free
+    # control is c = 1 (sigma = sum W is known); with it c = exp(mu).  For equal
+    # statistical error the network needs Var(W (r - 1)) / Var(W (r - r_net))
+    # times fewer exact evaluations.
+    r_ex = ex["ratio"].cpu().numpy()
+    for j in range(P):
+        v_plain = np.var(w_te * (r_ex[j] - 1.0))
+        v_net = np.var(w_te * (r_ex[j] - r_net[j]))
+        gain = v_plain / v_net
+        print(f"kappa {k_te[j]:.2f}: exact evaluations for sigma' at equal error reduced {gain:.0f}x "
+              f"(median |r_net/r - 1| {np.median(np.abs(r_net[j] / r_ex[j] - 1)):.1e})")
+        assert gain > 4.0
