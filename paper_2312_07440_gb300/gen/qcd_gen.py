@@ -108,6 +108,22 @@ def colour_matrix_int(n):
     return [[int(x * den) for x in row] for row in C], den
 
 
+def colour_pairs(Cint):
+    """Pair form of sum_ij Cint_ij Re(A_i^* A_j): [(i, j, c)] over i <= j with
+    Cint_ij != 0, c = Cint_ii on the diagonal and 2 Cint_ij off it."""
+    K = len(Cint)
+    return [(i, j, Cint[i][j] * (1 if i == j else 2)) for i in range(K) for j in range(i, K) if Cint[i][j]]
+
+
+def colour_rows(Cint):
+    """Row form of 2 sum_ij Cint_ij Re(A_i^* A_j) (the factor 2 of the helicity
+    flip folded in): [(i, [(j, coefficient)])], z_i = 2 Cint_ii A_i + 4 sum_{j>i}
+    Cint_ij A_j, and the sum is sum_i Re(A_i^* z_i)."""
+    K = len(Cint)
+    return [(i, [(i, 2 * Cint[i][i])] + [(j, 4 * Cint[i][j]) for j in range(i + 1, K) if Cint[i][j]])
+            for i in range(K)]
+
+
 # ---------------------------------------------------------------------------
 # diagram counting (unordered, colour-dressed Feynman graphs)
 # ---------------------------------------------------------------------------
@@ -262,11 +278,8 @@ def emit_process(name, n, outgoing_gluons, n_identical, hoist_weyl=True, share_f
     pairs = K <= PAIRS_MAX_K
     coef = {}
     if pairs:
-        for i in range(K):
-            for j in range(i, K):
-                if Cint[i][j]:
-                    c = Cint[i][j] * (1 if i == j else 2)
-                    coef.setdefault(c, len(coef))
+        for _, _, c in colour_pairs(Cint):
+            coef.setdefault(c, len(coef))
         ccs = [f"cc{k}_{h} = R(0)" for h in (0, 1) for k in range(len(coef))]
         w(f"  [[maybe_unused]] R {', '.join(ccs)};  // per distinct c_ij and top helicity")
     else:
@@ -495,25 +508,18 @@ def emit_process(name, n, outgoing_gluons, n_identical, hoist_weyl=True, share_f
     ind += "  "
     if pairs:
         for h in (0, 1):
-            for i in range(K):
-                for j in range(i, K):
-                    if not Cint[i][j]:
-                        continue
-                    k = coef[Cint[i][j] * (1 if i == j else 2)]
-                    a, b = f"A{i}_{h}", f"A{j}_{h}"
-                    w(f"{ind}cc{k}_{h} = fmadd({a}.r, {b}.r, fmadd({a}.i, {b}.i, cc{k}_{h}));")
-                    em.flops_per_level[n] += 4
+            for i, j, c in colour_pairs(Cint):
+                k = coef[c]
+                a, b = f"A{i}_{h}", f"A{j}_{h}"
+                w(f"{ind}cc{k}_{h} = fmadd({a}.r, {b}.r, fmadd({a}.i, {b}.i, cc{k}_{h}));")
+                em.flops_per_level[n] += 4
     else:
         # symmetric half, x2 symmetric colour sum, x2 helicity flip folded in:
         # acc += Re(A_i^* (2 C_ii A_i + 4 sum_{j>i} C_ij A_j))
         for h in (0, 1):
-            for i in range(K):
-                parts_r, parts_i = [f"R({2 * Cint[i][i]}) * A{i}_{h}.r"], [f"R({2 * Cint[i][i]}) * A{i}_{h}.i"]
-                for j in range(i + 1, K):
-                    if Cint[i][j] == 0:
-                        continue
-                    parts_r.append(f"R({4 * Cint[i][j]}) * A{j}_{h}.r")
-                    parts_i.append(f"R({4 * Cint[i][j]}) * A{j}_{h}.i")
+            for i, row in colour_rows(Cint):
+                parts_r = [f"R({cf}) * A{j}_{h}.r" for j, cf in row]
+                parts_i = [f"R({cf}) * A{j}_{h}.i" for j, cf in row]
                 w(f"{ind}{{ const R zr = {' + '.join(parts_r)}; const R zi = {' + '.join(parts_i)};")
                 k = f"cz{h}_{i % ROW_ACCS}"
                 w(f"{ind}  {k} = fmadd(A{i}_{h}.r, zr, fmadd(A{i}_{h}.i, zi, {k})); }}")

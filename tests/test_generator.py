@@ -32,3 +32,22 @@ def test_generated_headers_are_current():
         src, _ = qcd_gen.emit_process(name, *spec)
         with open(os.path.join(here, f"gen_qcd_{name}.cuh")) as f:
             assert f.read() == src, f"regenerate gen_qcd_{name}.cuh"
+
+
+def test_colour_sum_forms_equal_the_quadratic_form():
+    """The two FMA forms the generator emits for J^dagger Cint J (pairs with one
+    accumulator per distinct entry; rows z = C A with the helicity-flip factor 2
+    folded in) against the plain quadratic form, for random complex amplitudes."""
+    rng = np.random.default_rng(11)
+    for n in (2, 3, 4):
+        Cint, _ = qcd_gen.colour_matrix_int(n)
+        C = np.array(Cint, dtype=np.float64)
+        K = len(Cint)
+        for _ in range(5):
+            A = rng.normal(size=K) + 1j * rng.normal(size=K)
+            q = float(np.real(np.conj(A) @ C @ A))
+            scale = float(np.abs(A) @ np.abs(C) @ np.abs(A))
+            pairs = sum(c * np.real(np.conj(A[i]) * A[j]) for i, j, c in qcd_gen.colour_pairs(Cint))
+            rows = sum(np.real(np.conj(A[i]) * sum(cf * A[j] for j, cf in row)) for i, row in qcd_gen.colour_rows(Cint))
+            assert abs(pairs - q) <= 1e-12 * scale
+            assert abs(rows - 2 * q) <= 1e-12 * scale
