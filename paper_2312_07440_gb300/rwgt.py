@@ -117,6 +117,25 @@ def _ptr(x):
     return x.data_ptr()
 
 
+def _check_buffer(x, name, min_elems=0, dtype="float64"):
+    """Check a torch tensor or numpy array before its address goes to the
+    library, which takes plain pointers and cannot see their type or size:
+    element type, C-contiguity and at least min_elems elements.  None and raw
+    integer addresses pass unchecked."""
+    if x is None or isinstance(x, int):
+        return
+    if isinstance(x, np.ndarray):
+        kind, contiguous, n = str(x.dtype), bool(x.flags.c_contiguous), int(x.size)
+    else:
+        kind, contiguous, n = str(x.dtype).replace("torch.", ""), bool(x.is_contiguous()), int(x.numel())
+    if kind != dtype:
+        raise ValueError(f"{name}: expected {dtype} elements, got {kind}")
+    if not contiguous:
+        raise ValueError(f"{name}: must be C-contiguous")
+    if n < min_elems:
+        raise ValueError(f"{name}: {n} elements, need at least {min_elems}")
+
+
 def split_double(d_x, d_hi, d_lo, stream=None):
     """rw_split_double: the FP32 modes' FP64 -> (hi, lo) float split of the
     device array d_x into d_hi, d_lo (same length), asynchronous on stream."""
@@ -146,6 +165,9 @@ class Context:
 
     def __init__(self, device: int = 0, stream=None):
         self.h = None
+        self.n_external = 0  # of the process set, for the buffer checks
+        self.n_points = 0
+        self.n_events = 0
         self.lib = load()
         h = ctypes.c_void_p()
         rc = self.lib.rw_create(ctypes.byref(h), int(device), stream)
@@ -175,7 +197,9 @@ class Context:
         return rc
 
     def set_process(self, process: str, mode: str = "fp64"):
-        return self._check(self.lib.rw_set_process(self.h, PROCESS[process], MODE[mode]), "rw_set_process")
+        rc = self._check(self.lib.rw_set_process(self.h, PROCESS[process], MODE[mode]), "rw_set_process")
+        self.n_external = process_info(process).n_external
+        return rc
 
     def set_params(self, vec):
         p = params_struct(vec)
@@ -183,8 +207,10 @@ class Context:
 
     def set_reweight_points(self, pts):
         arr = np.ascontiguousarray(np.atleast_2d(pts), dtype=np.float64)
-        return self._check(self.lib.rw_set_reweight_points(self.h, arr.ctypes.data, arr.shape[0]),
-                           "rw_set_reweight_points")
+        rc = self._check(self.lib.rw_set_reweight_points(self.h, arr.ctypes.data, arr.shape[0]),
+                         "rw_set_reweight_points")
+        self.n_points = arr.shape[0]
+        return rc
 
     def set_tuning(self, lane_bits: int = -1, block: int = 0):
         return self._check(self.lib.rw_set_tuning(self.h, int(lane_bits), int(block)), "rw_set_tuning")
@@ -211,13 +237,22 @@ class Context:
         return int(self.lib.rw_workspace_bytes_host(self.h, int(n_events)))
 
     def load_events(self, mom, w, n_events: int, workspace, workspace_bytes: int):
-        return self._check(self.lib.rw_load_events(self.h, _ptr(mom), _ptr(w), int(n_events), _ptr(workspace),
-                                                   int(workspace_bytes)), "rw_load_events")
+        E = max(int(n_events), 0)
+        _check_buffer(mom, "mom", self.n_external * 4 * E)
+        _check_buffer(w, "w", E)
+        rc = self._check(self.lib.rw_load_events(self.h, _ptr(mom), _ptr(w), int(n_events), _ptr(workspace),
+                                                 int(workspace_bytes)), "rw_load_events")
+        self.n_events = E
+        return rc
 
     def eval_me(self, point: int, out):
         return self._check(self.lib.rw_eval_me(self.h, int(point), _ptr(out)), "rw_eval_me")
 
     def reweight_async(self, wnew=None, ratio=None, me0=None, me_pts=None):
+        PE = self.n_points * self.n_events
+        for x, name, n in ((wnew, "wnew", PE), (ratio, "ratio", PE), (me0, "me0", self.n_events),
+                           (me_pts, "me_pts", PE)):
+            _check_buffer(x, name, n)
         return self._check(self.lib.rw_reweight_async(self.h, _ptr(wnew), _ptr(ratio), _ptr(me0), _ptr(me_pts)),
                            "rw_reweight_async")
 
@@ -238,6 +273,10 @@ class Context:
         return sig, so.value, nb.value, rc
 
     def reweight_host(self, h_mom, h_w, n_events: int, h_wnew, n_points: int, workspace, workspace_bytes: int):
+        E = max(int(n_events), 0)
+        _check_buffer(h_mom, "h_mom", self.n_external * 4 * E)
+        _check_buffer(h_w, "h_w", E)
+        _check_buffer(h_wnew, "h_wnew", int(n_points) * E)
         sig = np.zeros(n_points)
         so = ctypes.c_double()
         nb = ctypes.c_int64()
@@ -313,6 +352,8 @@ class Lhe:
         <wgt id=...> lines of each event's <rwgt> block."""
         wnew = np.ascontiguousarray(wnew, dtype=np.float64)
         P, ld = wnew.shape
+        if len(ids) != P:
+            raise ValueError(f"{len(ids)} weight ids for {P} rows of wnew")
         arr = (ctypes.c_char_p * P)(*[str(x).encode() for x in ids])
         self._check(self.lib.rw_lhe_write(self.h, os.fsencode(path), wnew.ctypes.data, P, ld, arr), "rw_lhe_write")
 

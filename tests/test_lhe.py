@@ -127,3 +127,12 @@ def test_errors(tmp_path):
     (tmp_path / "open.lhe").write_text("<LesHouchesEvents>\n<event>\n1 1 1.0 0 0 0\n")
     with pytest.raises(rwgt.RwError):
         rwgt.Lhe(tmp_path / "open.lhe")
+
+
+def test_write_needs_one_id_per_row(tmp_path):
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 20)
+    path = tmp_path / "in.lhe"
+    write_lhe(path, "gg_tt", mom, w)
+    with rwgt.Lhe(path) as f:
+        with pytest.raises(ValueError):
+            f.write(tmp_path / "o.lhe", np.ones((2, 20)), ["only_one"])
