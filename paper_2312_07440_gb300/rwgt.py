@@ -142,6 +142,9 @@ def split_double(d_x, d_hi, d_lo, stream=None):
     n = int(d_x.numel())
     if d_hi.numel() != n or d_lo.numel() != n:
         raise ValueError("d_hi and d_lo must have the length of d_x")
+    _check_buffer(d_x, "d_x", n)
+    _check_buffer(d_hi, "d_hi", n, "float32")
+    _check_buffer(d_lo, "d_lo", n, "float32")
     rc = load().rw_split_double(_ptr(d_x), n, _ptr(d_hi), _ptr(d_lo), stream)
     if rc:
         raise RwError(rc, "rw_split_double")
@@ -246,6 +249,7 @@ class Context:
         return rc
 
     def eval_me(self, point: int, out):
+        _check_buffer(out, "out", self.n_events)
         return self._check(self.lib.rw_eval_me(self.h, int(point), _ptr(out)), "rw_eval_me")
 
     def reweight_async(self, wnew=None, ratio=None, me0=None, me_pts=None):
@@ -294,8 +298,10 @@ def reweight_interp(ctx, n_nodes, tol, d_wnew, d_fallback=None):
     nb = int(lib.rw_interp_workspace_bytes(ctx.h))
     import torch
     ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=d_wnew.device)
-    P = d_wnew.shape[0]
-    sig = np.zeros(P)
+    P = ctx.n_points
+    _check_buffer(d_wnew, "d_wnew", P * ctx.n_events)
+    _check_buffer(d_fallback, "d_fallback", ctx.n_events, "uint8")
+    sig = np.zeros(max(P, 1))
     so = ctypes.c_double()
     nfb = ctypes.c_int64()
     nbad = ctypes.c_int64()
@@ -408,9 +414,15 @@ class Mlp:
                     "rw_mlp_set_state")
 
     def forward(self, x, out):
+        n = int(x.shape[0])
+        _check_buffer(x, "x", n * self.n_in, "float32")
+        _check_buffer(out, "out", 2 * n, "float32")
         self._check(self.lib.rw_mlp_forward(self.h, _ptr(x), int(x.shape[0]), _ptr(out)), "rw_mlp_forward")
 
     def gradient(self, x, y, tau: float, lam: float):
+        n = int(x.shape[0])
+        _check_buffer(x, "x", n * self.n_in, "float32")
+        _check_buffer(y, "y", n, "float32")
         g = np.empty(self.n_params, np.float32)
         loss = ctypes.c_float()
         self._check(self.lib.rw_mlp_gradient(self.h, _ptr(x), _ptr(y), int(x.shape[0]), tau, lam, g.ctypes.data,
@@ -418,6 +430,9 @@ class Mlp:
         return loss.value, g
 
     def train(self, x, y, batch: int, n_steps: int, lr: float, tau: float, lam: float, seed: int = 7):
+        n = int(x.shape[0])
+        _check_buffer(x, "x", n * self.n_in, "float32")
+        _check_buffer(y, "y", n, "float32")
         self._check(self.lib.rw_mlp_train(self.h, _ptr(x), _ptr(y), int(x.shape[0]), int(batch), int(n_steps), lr,
                                           tau, lam, int(seed)), "rw_mlp_train")
 
@@ -456,13 +471,20 @@ class Graph:
 
 
 def surrogate_features(ctx: "Context", n_in, p_scale, k_scale, ratio, x, y):
+    PE = ctx.n_points * ctx.n_events
+    _check_buffer(ratio, "ratio", PE)
+    _check_buffer(x, "x", PE * int(n_in), "float32")
+    _check_buffer(y, "y", PE, "float32")
     return ctx._check(ctx.lib.rw_surrogate_features(ctx.h, int(n_in), float(p_scale), float(k_scale), _ptr(ratio),
                                                     _ptr(x), _ptr(y)), "rw_surrogate_features")
 
 
 def surrogate_reweight(ctx: "Context", mlp: Mlp, p_scale, k_scale, s_max, wnew, fallback, n_points, ws, ws_bytes):
-    sig = np.zeros(n_points)
-    nf = np.zeros(n_points, np.int64)
+    P = max(int(n_points), ctx.n_points)  # the library writes one sum per attached point
+    _check_buffer(wnew, "wnew", ctx.n_points * ctx.n_events)
+    _check_buffer(fallback, "fallback", ctx.n_points * ctx.n_events, "uint8")
+    sig = np.zeros(P)
+    nf = np.zeros(P, np.int64)
     ctx._check(ctx.lib.rw_surrogate_reweight(ctx.h, mlp.h, float(p_scale), float(k_scale), float(s_max), _ptr(wnew),
                                              _ptr(fallback), sig.ctypes.data, nf.ctypes.data, _ptr(ws),
                                              int(ws_bytes)), "rw_surrogate_reweight")
