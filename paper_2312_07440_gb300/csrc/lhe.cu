@@ -67,11 +67,25 @@ struct Cursor {
   void skip_ws() {
     while (p < e && (*p == ' ' || *p == '\t' || *p == '\r' || *p == '\n')) ++p;
   }
+  // a real number; Fortran's D exponent (1.5D+02) is read as E
   bool num(double& v) {
     skip_ws();
     if (p < e && *p == '+') ++p;
     auto r = std::from_chars(p, e, v);
     if (r.ec != std::errc()) return false;
+    if (r.ptr < e && (*r.ptr == 'D' || *r.ptr == 'd')) {
+      char buf[64];
+      const char* t = r.ptr + 1;
+      while (t < e && ((*t >= '0' && *t <= '9') || ((*t == '+' || *t == '-') && t == r.ptr + 1))) ++t;
+      const size_t n = (size_t)(t - p);
+      if (t == r.ptr + 1 || n >= sizeof buf) return false;
+      std::memcpy(buf, p, n);
+      buf[r.ptr - p] = 'E';
+      const auto r2 = std::from_chars(buf, buf + n, v);
+      if (r2.ec != std::errc() || r2.ptr != buf + n) return false;
+      p = t;
+      return true;
+    }
     p = r.ptr;
     return true;
   }

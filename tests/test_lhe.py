@@ -136,3 +136,31 @@ def test_write_needs_one_id_per_row(tmp_path):
     with rwgt.Lhe(path) as f:
         with pytest.raises(ValueError):
             f.write(tmp_path / "o.lhe", np.ones((2, 20)), ["only_one"])
+
+
+def test_fortran_d_exponents(tmp_path):
+    """Fortran writers may print 1.2345678901D+02: read exactly as the E form."""
+    mom, w = ev.generate(ev.WORKLOADS["gg_ttg_4m"], 40)
+    path_e, path_d = tmp_path / "e.lhe", tmp_path / "d.lhe"
+    write_lhe(path_e, "gg_ttg", mom, w)
+    text = path_e.read_text()
+    # re-print every float of the event blocks in Fortran E/D form
+    head, rest = text.split("<event>", 1)
+
+    def fortran(m):
+        x = float(m.group(0))
+        return f"{x:.15E}"
+
+    body = re.sub(r"-?\d+\.\d+(?:e[+-]?\d+)?", fortran, "<event>" + rest)
+    path_e.write_text(head + body)
+    path_d.write_text(head + body.replace("E+", "D+").replace("E-", "d-"))
+    with rwgt.Lhe(path_e) as f:
+        m_e, w_e = f.read("gg_ttg")
+    with rwgt.Lhe(path_d) as f:
+        m_d, w_d = f.read("gg_ttg")
+    assert np.array_equal(m_e, m_d) and np.array_equal(w_e, w_d)
+    bad = head + body.replace("E+", "D", 1).replace("D", "D ", 1)
+    (tmp_path / "bad.lhe").write_text(bad)
+    with rwgt.Lhe(tmp_path / "bad.lhe") as f:
+        with pytest.raises(rwgt.RwError, match="event 0"):
+            f.read("gg_ttg", threads=1)
