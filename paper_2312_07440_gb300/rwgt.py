@@ -314,20 +314,47 @@ def reweight_interp(ctx, n_nodes, tol, d_wnew, d_fallback=None):
 
 class Lhe:
     """A Les Houches Event file: read events into the library's layout, write
-    it back with new weights (rw_lhe_*; host only, no GPU needed)."""
+    it back with new weights (rw_lhe_*; host only, no GPU needed).  A gzip
+    file (.lhe.gz) is decompressed to a temporary file first, and write() to a
+    path ending in .gz compresses its output."""
 
     def __init__(self, path):
+        self.h = None
+        self._tmp = None
         self.lib = load()
+        src = os.fspath(path)
+        try:
+            with open(src, "rb") as f:
+                gz = f.read(2) == b"\x1f\x8b"
+        except OSError:
+            gz = False  # the library reports the missing or unreadable file
+        if gz:
+            import gzip
+            import shutil
+            import tempfile
+            fd, self._tmp = tempfile.mkstemp(suffix=".lhe")
+            with os.fdopen(fd, "wb") as out, gzip.open(src, "rb") as inp:
+                shutil.copyfileobj(inp, out, 1 << 22)
+            src = self._tmp
         h = ctypes.c_void_p()
-        rc = self.lib.rw_lhe_open(ctypes.byref(h), os.fsencode(path))
+        rc = self.lib.rw_lhe_open(ctypes.byref(h), os.fsencode(src))
         if rc:
+            self._drop_tmp()
             raise RwError(rc, f"rw_lhe_open: cannot read {path}")
         self.h = h
+
+    def _drop_tmp(self):
+        if self._tmp:
+            os.unlink(self._tmp)
+            self._tmp = None
 
     def close(self):
         if self.h:
             self.lib.rw_lhe_close(self.h)
             self.h = None
+        self._drop_tmp()
+
+    __del__ = close
 
     def __enter__(self):
         return self
@@ -361,7 +388,21 @@ class Lhe:
         if len(ids) != P:
             raise ValueError(f"{len(ids)} weight ids for {P} rows of wnew")
         arr = (ctypes.c_char_p * P)(*[str(x).encode() for x in ids])
-        self._check(self.lib.rw_lhe_write(self.h, os.fsencode(path), wnew.ctypes.data, P, ld, arr), "rw_lhe_write")
+        dst = os.fspath(path)
+        if not dst.endswith(".gz"):
+            self._check(self.lib.rw_lhe_write(self.h, os.fsencode(dst), wnew.ctypes.data, P, ld, arr), "rw_lhe_write")
+            return
+        import gzip
+        import shutil
+        import tempfile
+        fd, tmp = tempfile.mkstemp(suffix=".lhe")
+        os.close(fd)
+        try:
+            self._check(self.lib.rw_lhe_write(self.h, os.fsencode(tmp), wnew.ctypes.data, P, ld, arr), "rw_lhe_write")
+            with open(tmp, "rb") as inp, gzip.open(dst, "wb", compresslevel=6) as out:
+                shutil.copyfileobj(inp, out, 1 << 22)
+        finally:
+            os.unlink(tmp)
 
 
 class Mlp:

@@ -3,6 +3,7 @@ only): round trip of momenta and weights from a lab-frame file with shuffled
 particle order, intermediate lines and existing weight blocks; the weights
 written back; error reporting."""
 import math
+import os
 import re
 
 import numpy as np
@@ -164,3 +165,23 @@ def test_fortran_d_exponents(tmp_path):
     with rwgt.Lhe(tmp_path / "bad.lhe") as f:
         with pytest.raises(rwgt.RwError, match="event 0"):
             f.read("gg_ttg", threads=1)
+
+
+def test_gzip_files(tmp_path):
+    """.lhe.gz in and out: the same events and weights as the plain file."""
+    import gzip
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 50)
+    plain, packed = tmp_path / "in.lhe", tmp_path / "in.lhe.gz"
+    write_lhe(plain, "gg_tt", mom, w)
+    packed.write_bytes(gzip.compress(plain.read_bytes()))
+    with rwgt.Lhe(plain) as f:
+        m1, w1 = f.read("gg_tt")
+        wnew = np.vstack([w1 * 1.5])
+        f.write(tmp_path / "out.lhe", wnew, ["x"])
+    with rwgt.Lhe(packed) as f:
+        tmp = f._tmp
+        m2, w2 = f.read("gg_tt")
+        f.write(tmp_path / "out.lhe.gz", wnew, ["x"])
+    assert not os.path.exists(tmp)  # the temporary copy is removed on close
+    assert np.array_equal(m1, m2) and np.array_equal(w1, w2)
+    assert gzip.decompress((tmp_path / "out.lhe.gz").read_bytes()) == (tmp_path / "out.lhe").read_bytes()
