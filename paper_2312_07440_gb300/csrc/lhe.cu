@@ -191,10 +191,25 @@ int rw_lhe_open(rw_lhe** out, const char* path) {
     delete h;
     return RW_ERR_ARG;
   }
-  // index the <event> blocks
-  size_t pos = 0;
+  // index the <event> blocks: after </init> when there is one, skipping XML
+  // comments (a header may mention "<event>" in one); the next comment's
+  // position only moves forward, so the scan stays linear in the file size
   const std::string& t = h->text;
+  const size_t init_end = t.find("</init>");
+  size_t pos = init_end == std::string::npos ? 0 : init_end + 7;
+  size_t cm = t.find("<!--", pos);
   while ((pos = t.find("<event", pos)) != std::string::npos) {
+    if (cm != std::string::npos && cm < pos) {
+      const size_t ce = t.find("-->", cm + 4);
+      if (ce == std::string::npos) break;  // an unterminated comment hides the rest
+      if (ce > pos) {                       // this "<event" is inside the comment
+        pos = ce + 3;
+        cm = t.find("<!--", pos);
+        continue;
+      }
+      cm = t.find("<!--", ce + 3);
+      if (cm != std::string::npos && cm < pos) continue;  // another comment before it: check again
+    }
     const char nx = pos + 6 < t.size() ? t[pos + 6] : '\0';
     if (nx != '>' && nx != ' ' && nx != '\t' && nx != '\n' && nx != '\r') {  // e.g. <eventgroup>
       pos += 6;

@@ -185,3 +185,28 @@ def test_gzip_files(tmp_path):
     assert not os.path.exists(tmp)  # the temporary copy is removed on close
     assert np.array_equal(m1, m2) and np.array_equal(w1, w2)
     assert gzip.decompress((tmp_path / "out.lhe.gz").read_bytes()) == (tmp_path / "out.lhe").read_bytes()
+
+
+def test_event_attributes_extra_tags_and_comments(tmp_path):
+    """<event> attributes, <mgrwt>/<scales> blocks after the particle lines and
+    "<event>" inside header comments leave the events and weights unchanged."""
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 30)
+    plain, fancy = tmp_path / "a.lhe", tmp_path / "b.lhe"
+    write_lhe(plain, "gg_tt", mom, w)
+    t = plain.read_text()
+    t = t.replace("<event>", '<event npLO=" -1 " npNLO=" 1 ">')
+    t = t.replace("</event>", "<mgrwt>\n<rscale> 0 0.1E+03 </rscale>\n</mgrwt>\n"
+                              "<scales pt_clust_1=\"0.1E+03\"></scales>\n</event>")
+    t = t.replace("<header>", "<header>\n<!-- an <event> mentioned in a comment -->\n<!-- and </event> -->")
+    t = t.replace("</init>", "</init>\n<!-- <event> between init and events -->")
+    fancy.write_text(t)
+    with rwgt.Lhe(plain) as f:
+        m1, w1 = f.read("gg_tt")
+    with rwgt.Lhe(fancy) as f:
+        assert len(f) == 30
+        m2, w2 = f.read("gg_tt")
+        f.write(tmp_path / "c.lhe", np.vstack([w2]), ["same"])
+    assert np.array_equal(m1, m2) and np.array_equal(w1, w2)
+    with rwgt.Lhe(tmp_path / "c.lhe") as g:
+        m3, w3 = g.read("gg_tt")
+    assert np.array_equal(m3, m2) and np.array_equal(w3, w2)
