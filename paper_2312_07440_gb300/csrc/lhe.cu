@@ -25,6 +25,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <string_view>
 #include <thread>
 #include <vector>
 
@@ -192,24 +193,22 @@ int rw_lhe_open(rw_lhe** out, const char* path) {
     return RW_ERR_ARG;
   }
   // index the <event> blocks: after </init> when there is one, skipping XML
-  // comments (a header may mention "<event>" in one); the next comment's
-  // position only moves forward, so the scan stays linear in the file size
+  // comments (a file may mention "<event>" in one).  Only the text between the
+  // previous block and the next "<event" is searched for a comment, so the
+  // scan stays linear in the file size.
   const std::string& t = h->text;
+  const std::string_view tv(t);
   const size_t init_end = t.find("</init>");
   size_t pos = init_end == std::string::npos ? 0 : init_end + 7;
-  size_t cm = t.find("<!--", pos);
-  while ((pos = t.find("<event", pos)) != std::string::npos) {
-    if (cm != std::string::npos && cm < pos) {
-      const size_t ce = t.find("-->", cm + 4);
+  for (size_t ev; (ev = t.find("<event", pos)) != std::string::npos;) {
+    const size_t cm = tv.substr(pos, ev - pos).find("<!--");
+    if (cm != std::string_view::npos) {
+      const size_t ce = t.find("-->", pos + cm + 4);
       if (ce == std::string::npos) break;  // an unterminated comment hides the rest
-      if (ce > pos) {                       // this "<event" is inside the comment
-        pos = ce + 3;
-        cm = t.find("<!--", pos);
-        continue;
-      }
-      cm = t.find("<!--", ce + 3);
-      if (cm != std::string::npos && cm < pos) continue;  // another comment before it: check again
+      pos = ce + 3;
+      continue;
     }
+    pos = ev;
     const char nx = pos + 6 < t.size() ? t[pos + 6] : '\0';
     if (nx != '>' && nx != ' ' && nx != '\t' && nx != '\n' && nx != '\r') {  // e.g. <eventgroup>
       pos += 6;
