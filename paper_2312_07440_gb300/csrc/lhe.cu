@@ -288,12 +288,16 @@ int rw_lhe_write(rw_lhe* h, const char* path, const double* h_wnew, int P, int64
   // per event: where the weight lines go and whether an <rwgt> block exists
   std::vector<size_t> cut(E);
   std::vector<char> has(E);
+  // (searched within the event's own block only: linear in the file size)
+  const std::string_view tv(t);
   for (int64_t k = 0; k < E; ++k) {
-    const size_t rb = t.find("<rwgt>", h->body[k]);
-    has[k] = rb != std::string::npos && rb < h->end[k];
-    cut[k] = has[k] ? t.find("</rwgt>", rb) : h->end[k];
-    if (cut[k] == std::string::npos || cut[k] > h->end[k])
+    const std::string_view blk = tv.substr(h->body[k], h->end[k] - h->body[k]);
+    const size_t rb = blk.find("<rwgt>");
+    has[k] = rb != std::string_view::npos;
+    const size_t re = has[k] ? blk.find("</rwgt>", rb) : blk.size();
+    if (re == std::string_view::npos)
       return lhe_fail(h, RW_ERR_ARG, "event %lld: unclosed <rwgt>", (long long)k);
+    cut[k] = h->body[k] + re;
   }
   // the inserted text of every event, formatted in parallel (std::to_chars,
   // scientific, 10 digits after the point), written in order

@@ -210,3 +210,20 @@ def test_event_attributes_extra_tags_and_comments(tmp_path):
     with rwgt.Lhe(tmp_path / "c.lhe") as g:
         m3, w3 = g.read("gg_tt")
     assert np.array_equal(m3, m2) and np.array_equal(w3, w2)
+
+
+def test_write_without_weight_blocks_is_linear(tmp_path):
+    """Events without an <rwgt> block get one; the search for it stays inside
+    each event (it once ran ahead through the rest of the file: quadratic)."""
+    import time
+    E = 20000
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], E)
+    src, dst = tmp_path / "in.lhe", tmp_path / "out.lhe"
+    write_lhe(src, "gg_tt", mom, w, extra=False)
+    with rwgt.Lhe(src) as f:
+        t0 = time.perf_counter()
+        f.write(dst, np.vstack([w * 2.0]), ["twice"])
+        dt = time.perf_counter() - t0
+    assert dt < 2.0  # ~10 ms linear, ~5 s quadratic
+    text = dst.read_text()
+    assert text.count("<rwgt>") == E and text.count("<wgt id='twice'>") == E
