@@ -193,21 +193,33 @@ int rw_lhe_open(rw_lhe** out, const char* path) {
     return RW_ERR_ARG;
   }
   // index the <event> blocks: after </init> when there is one, skipping XML
-  // comments (a file may mention "<event>" in one).  Only the text between the
-  // previous block and the next "<event" is searched for a comment, so the
-  // scan stays linear in the file size.
+  // comments (a file may mention "<event>" or "</event>" in one).  Between
+  // blocks the next "<event" is searched once and only the text before it is
+  // searched for "<!--"; inside a block "</event>" and "<!--" are searched
+  // from the current position on.  Every character is looked at a bounded
+  // number of times, so the scan is linear in the file size.  A comment that
+  // is never closed, or an <event> that is never closed, makes the file
+  // unreadable (RW_ERR_ARG): indexing past it would silently drop events.
   const std::string& t = h->text;
   const std::string_view tv(t);
+  const size_t npos = std::string::npos;
   const size_t init_end = t.find("</init>");
-  size_t pos = init_end == std::string::npos ? 0 : init_end + 7;
-  for (size_t ev; (ev = t.find("<event", pos)) != std::string::npos;) {
-    const size_t cm = tv.substr(pos, ev - pos).find("<!--");
+  size_t pos = init_end == npos ? 0 : init_end + 7;
+  size_t ev = t.find("<event", pos);
+  for (;;) {
+    if (ev != npos && ev < pos) ev = t.find("<event", pos);
+    const size_t lim = ev == npos ? t.size() : ev;
+    const size_t cm = tv.substr(pos, lim - pos).find("<!--");
     if (cm != std::string_view::npos) {
       const size_t ce = t.find("-->", pos + cm + 4);
-      if (ce == std::string::npos) break;  // an unterminated comment hides the rest
+      if (ce == npos) {
+        delete h;
+        return RW_ERR_ARG;
+      }
       pos = ce + 3;
       continue;
     }
+    if (ev == npos) break;
     pos = ev;
     const char nx = pos + 6 < t.size() ? t[pos + 6] : '\0';
     if (nx != '>' && nx != ' ' && nx != '\t' && nx != '\n' && nx != '\r') {  // e.g. <eventgroup>
@@ -215,8 +227,20 @@ int rw_lhe_open(rw_lhe** out, const char* path) {
       continue;
     }
     const size_t gt = t.find('>', pos);
-    const size_t close = gt == std::string::npos ? gt : t.find("</event>", gt);
-    if (close == std::string::npos) {
+    // the block ends at the first "</event>" outside a comment
+    size_t close = npos, ce = npos;
+    for (size_t q = gt == npos ? npos : gt + 1; q != npos;) {
+      if (ce == npos || ce < q) ce = t.find("</event>", q);
+      if (ce == npos) break;
+      const size_t c0 = tv.substr(q, ce - q).find("<!--");
+      if (c0 == std::string_view::npos) {
+        close = ce;
+        break;
+      }
+      const size_t c1 = t.find("-->", q + c0 + 4);
+      q = c1 == npos ? npos : c1 + 3;
+    }
+    if (close == npos) {
       delete h;
       return RW_ERR_ARG;
     }

@@ -338,9 +338,11 @@ class Lhe:
             src = self._tmp
         h = ctypes.c_void_p()
         rc = self.lib.rw_lhe_open(ctypes.byref(h), os.fsencode(src))
+        # the library holds the whole text in memory now: the plain copy of a
+        # compressed file is not needed any more
+        self._drop_tmp()
         if rc:
-            self._drop_tmp()
-            raise RwError(rc, f"rw_lhe_open: cannot read {path}")
+            raise RwError(rc, f"rw_lhe_open: cannot read {path} (or an <event> or XML comment is not closed)")
         self.h = h
 
     def _drop_tmp(self):

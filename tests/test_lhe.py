@@ -179,10 +179,9 @@ def test_gzip_files(tmp_path):
         wnew = np.vstack([w1 * 1.5])
         f.write(tmp_path / "out.lhe", wnew, ["x"])
     with rwgt.Lhe(packed) as f:
-        tmp = f._tmp
+        assert f._tmp is None  # the decompressed copy is gone once the text is in memory
         m2, w2 = f.read("gg_tt")
         f.write(tmp_path / "out.lhe.gz", wnew, ["x"])
-    assert not os.path.exists(tmp)  # the temporary copy is removed on close
     assert np.array_equal(m1, m2) and np.array_equal(w1, w2)
     assert gzip.decompress((tmp_path / "out.lhe.gz").read_bytes()) == (tmp_path / "out.lhe").read_bytes()
 
@@ -227,3 +226,59 @@ def test_write_without_weight_blocks_is_linear(tmp_path):
     assert dt < 2.0  # ~10 ms linear, ~5 s quadratic
     text = dst.read_text()
     assert text.count("<rwgt>") == E and text.count("<wgt id='twice'>") == E
+
+
+def test_unclosed_comment_is_an_error(tmp_path):
+    """A comment that is never closed hides every event after it: the file is
+    rejected instead of being read short."""
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 10)
+    path = tmp_path / "in.lhe"
+    write_lhe(path, "gg_tt", mom, w)
+    t = path.read_text()
+    cut = [m.end() for m in re.finditer("</event>", t)][3]
+    (tmp_path / "oops.lhe").write_text(t[:cut] + "\n<!-- oops\n" + t[cut:])
+    with pytest.raises(rwgt.RwError, match="not closed"):
+        rwgt.Lhe(tmp_path / "oops.lhe")
+
+
+def test_end_tag_inside_a_comment_of_an_event(tmp_path):
+    """'</event>' inside a comment of an event block does not end the block:
+    the event is read whole and the new weights go before the real end tag."""
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 6)
+    plain, tricky = tmp_path / "a.lhe", tmp_path / "b.lhe"
+    write_lhe(plain, "gg_tt", mom, w, extra=False)
+    t = plain.read_text().replace("</event>", "<!-- a </event> in a comment -->\n</event>")
+    tricky.write_text(t)
+    with rwgt.Lhe(plain) as f:
+        m1, w1 = f.read("gg_tt")
+    with rwgt.Lhe(tricky) as f:
+        assert len(f) == 6
+        m2, w2 = f.read("gg_tt")
+        f.write(tmp_path / "c.lhe", np.vstack([2 * w2]), ["twice"])
+    assert np.array_equal(m1, m2) and np.array_equal(w1, w2)
+    out = (tmp_path / "c.lhe").read_text()
+    for blk in re.findall(r"<event>(.*?)\n</event>", out, flags=re.S):
+        assert blk.index("<!-- a </event> in a comment -->") < blk.index("<rwgt>")
+        assert blk.rstrip().endswith("</rwgt>")
+
+
+def test_many_comments_index_in_linear_time(tmp_path):
+    """Many comments between two events, and inside one event, are skipped in
+    one pass (each used to restart the search for the next tag)."""
+    import time
+    mom, w = ev.generate(ev.WORKLOADS["gg_tt_1m"], 4)
+    path = tmp_path / "in.lhe"
+    write_lhe(path, "gg_tt", mom, w, extra=False)
+    t = path.read_text()
+    many = "<!-- c -->\n" * 100000
+    k = t.index("</event>") + len("</event>")
+    t = t[:k] + "\n" + many + t[k:]
+    k = t.rindex("</event>")
+    t = t[:k] + many + t[k:]
+    (tmp_path / "many.lhe").write_text(t)
+    t0 = time.perf_counter()
+    with rwgt.Lhe(tmp_path / "many.lhe") as f:
+        assert len(f) == 4
+        m2, w2 = f.read("gg_tt")
+    assert time.perf_counter() - t0 < 2.0  # ~10 ms linear, minutes quadratic
+    assert np.array_equal(w2, w)
