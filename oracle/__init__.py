@@ -31,20 +31,68 @@ PROCESS_ID = {"ee_mumu": 0, "gg_tt": 1, "gg_ttg": 2, "gg_ttgg": 3, "ee_5a": 4}
 N_EXTERNAL = {"ee_mumu": 4, "gg_tt": 4, "gg_ttg": 5, "gg_ttgg": 6, "ee_5a": 7}
 PARAM_FIELDS = ("alpha_s", "m_t", "w_t", "yt_scale", "alpha_em_inv", "G_F", "m_Z", "w_Z")
 
+_EXT_PATH = os.path.join(_BUILD, "liboracle_ext.so")
+
 _lib = None
+_ext = None
+
+
+def _compile(path, defines, force):
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC):
+        return path
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_BUILD)
+    os.close(fd)
+    cmd = ["gcc", "-O2", "-fopenmp", "-std=c11", "-shared", "-fPIC", *defines, "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, path)
+    return path
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so (atomic replace)."""
+    """Compile oracle.c into _build/liboracle.so (FP64) and
+    _build/liboracle_ext.so (the same formulas in long double: 64-bit
+    significand on x86-64, 113-bit on AArch64), atomic replace."""
     os.makedirs(_BUILD, exist_ok=True)
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
-        return _LIB_PATH
-    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_BUILD)
-    os.close(fd)
-    cmd = ["gcc", "-O2", "-fopenmp", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    _compile(_EXT_PATH, ["-DORACLE_EXTENDED"], force)
+    return _compile(_LIB_PATH, [], force)
+
+
+def _batch_signatures(lib):
+    i, l, P = ctypes.c_int, ctypes.c_long, ctypes.c_void_p
+    lib.oracle_set_threads.argtypes = [i]
+    lib.oracle_set_threads.restype = i
+    lib.oracle_me.argtypes = [i, P, l, P, P]
+    lib.oracle_me.restype = i
+    lib.oracle_reshuffle.argtypes = [i, P, l, P, P, P]
+    lib.oracle_reshuffle.restype = i
+    lib.oracle_reweight.argtypes = [i, P, i, P, l, P, P, P, P, P, P, P]
+    lib.oracle_reweight.restype = i
+
+
+def _load_ext():
+    """The extended-precision build (batch entry points only)."""
+    global _ext
+    if _ext is None:
+        build()
+        lib = ctypes.CDLL(_EXT_PATH)
+        _batch_signatures(lib)
+        lib.oracle_init()
+        _ext = lib
+    return _ext
+
+
+def _pick(precision):
+    if precision == "fp64":
+        return _load()
+    if precision == "extended":
+        return _load_ext()
+    raise ValueError(f"precision must be 'fp64' or 'extended', not {precision!r}")
+
+
+def extended_digits() -> int:
+    """Significand bits of the extended build's long double (64 on x86-64,
+    113 on AArch64)."""
+    return int(np.finfo(np.longdouble).nmant) + 1
 
 
 def _load():
@@ -101,9 +149,10 @@ def set_threads(n: int) -> int:
     return _load().oracle_set_threads(int(n))
 
 
-def me(process: str, par, mom) -> np.ndarray:
-    """|M|^2 per event.  mom: float64 [N][4][E]."""
-    lib = _load()
+def me(process: str, par, mom, precision: str = "fp64") -> np.ndarray:
+    """|M|^2 per event.  mom: float64 [N][4][E].  precision "extended"
+    evaluates the same formulas in long double (result rounded to float64)."""
+    lib = _pick(precision)
     mom = np.ascontiguousarray(mom, dtype=np.float64)
     E = mom.shape[-1]
     out = np.empty(E)
@@ -124,13 +173,15 @@ def reshuffle(process: str, par_new, mom):
     return out, st
 
 
-def reweight(process: str, par0, points, mom, w):
+def reweight(process: str, par0, points, mom, w, precision: str = "fp64"):
     """Eq. 3 for every parameter point and Eq. 2 sums.
 
     Returns dict(me0[E], me[P][E], ratio[P][E], wnew[P][E], sigma[P],
     sigma_orig, n_bad); sigma are exactly rounded sums (math.fsum).
+    precision "extended": the same formulas in long double, every result
+    rounded to float64 once at the end.
     """
-    lib = _load()
+    lib = _pick(precision)
     mom = np.ascontiguousarray(mom, dtype=np.float64)
     w = np.ascontiguousarray(w, dtype=np.float64)
     par0 = np.ascontiguousarray(par0, dtype=np.float64)

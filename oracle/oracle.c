@@ -54,15 +54,28 @@
  * against closed forms, invariances and independent evaluations.
  */
 #define _GNU_SOURCE
-#include <complex.h>
-#include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
 
+/* The arithmetic type.  The default build is FP64.  The same source compiled
+   with -DORACLE_EXTENDED (real = long double: 64-bit significand on x86-64,
+   113-bit IEEE quadruple on AArch64) evaluates the identical formulas with
+   far less rounding; it exports only the batch entry points (oracle_me,
+   oracle_reshuffle, oracle_reweight), whose event data stay float64 at the
+   interface.  <tgmath.h> picks the maths function of the argument's type. */
+#ifdef ORACLE_EXTENDED
+typedef long double real;
+typedef long double complex cx;
+#define OR_PI 3.141592653589793238462643383279502884L
+#else
+typedef double real;
 typedef double complex cx;
+#define OR_PI M_PI
+#endif
 
 #define OR_EE_MUMU 0
 #define OR_GG_TT 1
@@ -76,13 +89,13 @@ typedef double complex cx;
 
 /* model parameters, same field order as the product's rw_params */
 typedef struct {
-    double alpha_s, m_t, w_t, yt_scale, alpha_em_inv, G_F, m_Z, w_Z;
+    real alpha_s, m_t, w_t, yt_scale, alpha_em_inv, G_F, m_Z, w_Z;
 } or_params;
 
 /* ------------------------------------------------------------------------ */
 /* Minkowski space and Dirac algebra                                         */
 /* ------------------------------------------------------------------------ */
-static const double GMETRIC[4] = {1.0, -1.0, -1.0, -1.0};
+static const real GMETRIC[4] = {1.0, -1.0, -1.0, -1.0};
 static cx GAMMA[4][4][4]; /* GAMMA[mu][row][col], upper index mu */
 static cx GAMMA5[4][4];
 static cx IDENT4[4][4];
@@ -128,7 +141,7 @@ static void dirac_init(void) {
 static cx mdot(const cx a[4], const cx b[4]) {
     return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
 }
-static double rdot(const double a[4], const double b[4]) {
+static real rdot(const real a[4], const real b[4]) {
     return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
 }
 
@@ -141,7 +154,7 @@ static void slash(const cx a[4], cx S[4][4]) {
             S[i][j] = s;
         }
 }
-static void rslash(const double a[4], cx S[4][4]) {
+static void rslash(const real a[4], cx S[4][4]) {
     cx c[4] = {a[0], a[1], a[2], a[3]};
     slash(c, S);
 }
@@ -185,30 +198,30 @@ static cx trace4(cx A[4][4]) { return A[0][0] + A[1][1] + A[2][2] + A[3][3]; }
 /* sqrt of the 2x2 positive semi-definite Hermitian matrix
    A = p^0 + sgn * pvec.sigma  (sgn = -1: p.sigma, +1: p.sigmabar),
    sqrt(A) = (A + sqrt(det A) 1)/sqrt(tr A + 2 sqrt(det A)), det A = m^2. */
-static void sqrt_psig(const double p[4], double m, int sgn, cx R[2][2]) {
+static void sqrt_psig(const real p[4], real m, int sgn, cx R[2][2]) {
     cx A[2][2];
     A[0][0] = p[0] + sgn * p[3];
     A[1][1] = p[0] - sgn * p[3];
     A[0][1] = sgn * (p[1] - I * p[2]);
     A[1][0] = sgn * (p[1] + I * p[2]);
-    double sd = fabs(m);
-    double nrm = sqrt(2.0 * p[0] + 2.0 * sd);
+    real sd = fabs(m);
+    real nrm = sqrt(2.0 * p[0] + 2.0 * sd);
     for (int i = 0; i < 2; i++)
         for (int j = 0; j < 2; j++) R[i][j] = (A[i][j] + (i == j ? sd : 0.0)) / nrm;
 }
 
 /* two-component basis spinor: basis 0 -> spin along z (s=0 up, s=1 down);
    basis 1 -> helicity eigenstates along pvec (s=0: +1/2, s=1: -1/2). */
-static void two_spinor(const double p[4], int basis, int s, cx chi[2]) {
+static void two_spinor(const real p[4], int basis, int s, cx chi[2]) {
     if (basis == 0) {
         chi[0] = (s == 0);
         chi[1] = (s == 1);
         return;
     }
-    double pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-    double ct = pp > 0 ? p[3] / pp : 1.0;
-    double c2 = sqrt(fmax(0.0, 0.5 * (1.0 + ct))), s2 = sqrt(fmax(0.0, 0.5 * (1.0 - ct)));
-    double pt = hypot(p[1], p[2]);
+    real pp = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+    real ct = pp > 0 ? p[3] / pp : 1.0;
+    real c2 = sqrt(fmax(0.0, 0.5 * (1.0 + ct))), s2 = sqrt(fmax(0.0, 0.5 * (1.0 - ct)));
+    real pt = hypot(p[1], p[2]);
     cx eph = pt > 0 ? (p[1] + I * p[2]) / pt : 1.0;
     if (s == 0) { /* chi_+ */
         chi[0] = c2;
@@ -219,7 +232,7 @@ static void two_spinor(const double p[4], int basis, int s, cx chi[2]) {
     }
 }
 
-static void spinor_u(const double p[4], double m, int basis, int s, cx u[4]) {
+static void spinor_u(const real p[4], real m, int basis, int s, cx u[4]) {
     cx R[2][2], L[2][2], xi[2];
     two_spinor(p, basis, s, xi);
     sqrt_psig(p, m, -1, L); /* sqrt(p.sigma) */
@@ -231,7 +244,7 @@ static void spinor_u(const double p[4], double m, int basis, int s, cx u[4]) {
 }
 
 /* v: helicity label s=0 (+1/2) uses eta = chi_-, s=1 uses chi_+ */
-static void spinor_v(const double p[4], double m, int basis, int s, cx v[4]) {
+static void spinor_v(const real p[4], real m, int basis, int s, cx v[4]) {
     cx R[2][2], L[2][2], eta[2];
     two_spinor(p, basis, basis == 1 ? 1 - s : s, eta);
     sqrt_psig(p, m, -1, L);
@@ -244,20 +257,20 @@ static void spinor_v(const double p[4], double m, int basis, int s, cx v[4]) {
 
 /* transverse polarisation for momentum k: basis 0 linear (s=0: e1, s=1: e2),
    basis 1 helicity eps(lambda) = (-lambda e1 - i e2)/sqrt2, s=0 -> +1. */
-static void polvec(const double k[4], int basis, int s, cx eps[4]) {
-    double kk = sqrt(k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
-    double ct = kk > 0 ? k[3] / kk : 1.0;
-    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
-    double pt = hypot(k[1], k[2]);
-    double cp = pt > 0 ? k[1] / pt : 1.0, sp = pt > 0 ? k[2] / pt : 0.0;
-    double e1[4] = {0.0, ct * cp, ct * sp, -st};
-    double e2[4] = {0.0, -sp, cp, 0.0};
+static void polvec(const real k[4], int basis, int s, cx eps[4]) {
+    real kk = sqrt(k[1] * k[1] + k[2] * k[2] + k[3] * k[3]);
+    real ct = kk > 0 ? k[3] / kk : 1.0;
+    real st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    real pt = hypot(k[1], k[2]);
+    real cp = pt > 0 ? k[1] / pt : 1.0, sp = pt > 0 ? k[2] / pt : 0.0;
+    real e1[4] = {0.0, ct * cp, ct * sp, -st};
+    real e2[4] = {0.0, -sp, cp, 0.0};
     for (int mu = 0; mu < 4; mu++) {
         if (basis == 0)
             eps[mu] = s == 0 ? e1[mu] : e2[mu];
         else {
-            double lam = s == 0 ? 1.0 : -1.0;
-            eps[mu] = (-lam * e1[mu] - I * e2[mu]) / sqrt(2.0);
+            real lam = s == 0 ? 1.0 : -1.0;
+            eps[mu] = (-lam * e1[mu] - I * e2[mu]) / sqrt((real)2);
         }
     }
 }
@@ -266,8 +279,8 @@ static void polvec(const double k[4], int basis, int s, cx eps[4]) {
 /* SU(3)                                                                     */
 /* ------------------------------------------------------------------------ */
 static cx TGEN[8][3][3]; /* t^a = lambda^a / 2 */
-static double FSTRUCT[8][8][8];
-static double CMAT[MAXG + 1][MAXK][MAXK];
+static real FSTRUCT[8][8][8];
+static real CMAT[MAXG + 1][MAXK][MAXK];
 static int PERM[MAXG + 1][MAXK][MAXG];
 static int NPERM[MAXG + 1];
 static int su3_ready = 0;
@@ -297,7 +310,11 @@ static int next_perm(int *a, int n) {
 
 static void su3_init(void) {
     if (su3_ready) return;
-    static const double s3 = 0.57735026918962576451; /* 1/sqrt(3) */
+#ifdef ORACLE_EXTENDED
+    const real s3 = 1 / sqrt((real)3);
+#else
+    static const real s3 = 0.57735026918962576451; /* 1/sqrt(3) */
+#endif
     cx lam[8][3][3];
     memset(lam, 0, sizeof(lam));
     lam[0][0][1] = 1; lam[0][1][0] = 1;
@@ -335,7 +352,7 @@ static void su3_init(void) {
         } while (next_perm(a, n));
         NPERM[n] = k;
         static cx S[MAXK][3][3];
-        double acc[MAXK][MAXK];
+        real acc[MAXK][MAXK];
         memset(acc, 0, sizeof(acc));
         int ncol = 1;
         for (int i = 0; i < n; i++) ncol *= 8;
@@ -372,7 +389,7 @@ static void init_all(void) {
 /* ------------------------------------------------------------------------ */
 /* 3-gluon: V3(J1,P1;J2,P2)^mu = -J1^mu (2P1+P2).J2 + (J1.J2)(P1-P2)^mu
                                + J2^mu (2P2+P1).J1                           */
-static void vertex3(const cx J1[4], const double P1[4], const cx J2[4], const double P2[4], cx out[4]) {
+static void vertex3(const cx J1[4], const real P1[4], const cx J2[4], const real P2[4], cx out[4]) {
     cx a[4], b[4];
     for (int mu = 0; mu < 4; mu++) {
         a[mu] = 2.0 * P1[mu] + P2[mu];
@@ -394,16 +411,16 @@ static void vertex4(const cx J1[4], const cx J2[4], const cx J3[4], cx out[4]) {
  * eps[g]: its polarisation (already conjugated if outgoing), ubar: top row
  * spinor, v: antitop spinor, p4: antitop momentum.
  */
-static cx amp_ordered(int n, const int *sig, double k[][4], cx eps[][4], const double p4[4], const cx ubar[4],
-                      const cx v[4], double m, double g) {
+static cx amp_ordered(int n, const int *sig, real k[][4], cx eps[][4], const real p4[4], const cx ubar[4],
+                      const cx v[4], real m, real g) {
     cx J[MAXG][MAXG][4];
-    double K[MAXG][MAXG][4];
+    real K[MAXG][MAXG][4];
     cx psi[MAXG + 1][4];
     for (int len = 1; len <= n; len++)
         for (int a = 0; a + len - 1 < n; a++) {
             int b = a + len - 1;
             for (int mu = 0; mu < 4; mu++) {
-                double s = 0;
+                real s = 0;
                 for (int i = a; i <= b; i++) s += k[sig[i]][mu];
                 K[a][b][mu] = s;
             }
@@ -421,12 +438,12 @@ static cx amp_ordered(int n, const int *sig, double k[][4], cx eps[][4], const d
                     vertex4(J[a][c], J[c + 1][d], J[d + 1][b], t);
                     for (int mu = 0; mu < 4; mu++) acc[mu] += g * g * t[mu];
                 }
-            double K2 = rdot(K[a][b], K[a][b]);
+            real K2 = rdot(K[a][b], K[a][b]);
             for (int mu = 0; mu < 4; mu++) J[a][b][mu] = acc[mu] / K2;
         }
     memcpy(psi[n], v, sizeof(cx) * 4);
     for (int a = n - 1; a >= 0; a--) {
-        double q[4];
+        real q[4];
         for (int mu = 0; mu < 4; mu++) q[mu] = K[a][n - 1][mu] - p4[mu];
         cx acc[4] = {0, 0, 0, 0}, t[4], S[4][4];
         for (int c = a; c < n; c++) {
@@ -438,7 +455,7 @@ static cx amp_ordered(int n, const int *sig, double k[][4], cx eps[][4], const d
         rslash(q, P);
         for (int i = 0; i < 4; i++) P[i][i] += m;
         matvec(P, acc, t);
-        double den = rdot(q, q) - m * m;
+        real den = rdot(q, q) - m * m;
         for (int i = 0; i < 4; i++) psi[a][i] = -g * t[i] / den;
     }
     cx A = 0, t[4], S[4][4];
@@ -452,16 +469,16 @@ static cx amp_ordered(int n, const int *sig, double k[][4], cx eps[][4], const d
 
 /* Same recursion with the spinors amputated: Gamma(sigma) is the 4x4 matrix
    with A(sigma) = ubar Gamma(sigma) v (used by the trace evaluation). */
-static void amp_ordered_matrix(int n, const int *sig, double k[][4], cx eps[][4], const double p4[4], double m,
-                               double g, cx Gam[4][4]) {
+static void amp_ordered_matrix(int n, const int *sig, real k[][4], cx eps[][4], const real p4[4], real m,
+                               real g, cx Gam[4][4]) {
     cx J[MAXG][MAXG][4];
-    double K[MAXG][MAXG][4];
+    real K[MAXG][MAXG][4];
     cx Psi[MAXG + 1][4][4];
     for (int len = 1; len <= n; len++)
         for (int a = 0; a + len - 1 < n; a++) {
             int b = a + len - 1;
             for (int mu = 0; mu < 4; mu++) {
-                double s = 0;
+                real s = 0;
                 for (int i = a; i <= b; i++) s += k[sig[i]][mu];
                 K[a][b][mu] = s;
             }
@@ -479,12 +496,12 @@ static void amp_ordered_matrix(int n, const int *sig, double k[][4], cx eps[][4]
                     vertex4(J[a][c], J[c + 1][d], J[d + 1][b], t);
                     for (int mu = 0; mu < 4; mu++) acc[mu] += g * g * t[mu];
                 }
-            double K2 = rdot(K[a][b], K[a][b]);
+            real K2 = rdot(K[a][b], K[a][b]);
             for (int mu = 0; mu < 4; mu++) J[a][b][mu] = acc[mu] / K2;
         }
     memcpy(Psi[n], IDENT4, sizeof(IDENT4));
     for (int a = n - 1; a >= 0; a--) {
-        double q[4];
+        real q[4];
         for (int mu = 0; mu < 4; mu++) q[mu] = K[a][n - 1][mu] - p4[mu];
         cx acc[4][4], S[4][4], T[4][4];
         memset(acc, 0, sizeof(acc));
@@ -498,7 +515,7 @@ static void amp_ordered_matrix(int n, const int *sig, double k[][4], cx eps[][4]
         rslash(q, P);
         for (int i = 0; i < 4; i++) P[i][i] += m;
         mat4_mul(P, acc, T);
-        double den = rdot(q, q) - m * m;
+        real den = rdot(q, q) - m * m;
         for (int i = 0; i < 4; i++)
             for (int j = 0; j < 4; j++) Psi[a][i][j] = -g * T[i][j] / den;
     }
@@ -533,16 +550,16 @@ static int gluon_particle(int g) { return g < 2 ? g : g + 2; }
 static int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
 
 /* electroweak couplings from (alpha^-1, G_F, M_Z) */
-typedef struct { double e, gL, gR, MZ, WZ; } ew_coup;
+typedef struct { real e, gL, gR, MZ, WZ; } ew_coup;
 static ew_coup ew_couplings(const or_params *par) {
     ew_coup c;
-    double alpha = 1.0 / par->alpha_em_inv;
-    double MZ = par->m_Z;
-    double MW2 = 0.5 * MZ * MZ + sqrt(0.25 * MZ * MZ * MZ * MZ - M_PI * alpha * MZ * MZ / (sqrt(2.0) * par->G_F));
-    double sw2 = 1.0 - MW2 / (MZ * MZ);
-    double sw = sqrt(sw2), cw = sqrt(1.0 - sw2);
-    c.e = sqrt(4.0 * M_PI * alpha);
-    double Q = -1.0, T3 = -0.5;
+    real alpha = 1.0 / par->alpha_em_inv;
+    real MZ = par->m_Z;
+    real MW2 = 0.5 * MZ * MZ + sqrt(0.25 * MZ * MZ * MZ * MZ - OR_PI * alpha * MZ * MZ / (sqrt((real)2) * par->G_F));
+    real sw2 = 1.0 - MW2 / (MZ * MZ);
+    real sw = sqrt(sw2), cw = sqrt(1.0 - sw2);
+    c.e = sqrt(4.0 * OR_PI * alpha);
+    real Q = -1.0, T3 = -0.5;
     c.gL = c.e * (T3 - Q * sw2) / (sw * cw);
     c.gR = -c.e * Q * sw2 / (sw * cw);
     c.MZ = MZ;
@@ -572,8 +589,8 @@ static void ew_vertex(const ew_coup *c, int boson, cx G[4][4][4]) {
 }
 
 /* boson propagator numerator/denominator contracted: sum_{mu,nu} a^mu P_{mu nu} b^nu */
-static cx ew_contract(const ew_coup *c, int boson, const cx a[4], const cx b[4], const double kk[4]) {
-    double s = rdot(kk, kk);
+static cx ew_contract(const ew_coup *c, int boson, const cx a[4], const cx b[4], const real kk[4]) {
+    real s = rdot(kk, kk);
     if (boson == 0) return mdot(a, b) / s;
     cx ka = 0, kb = 0;
     cx kc[4] = {kk[0], kk[1], kk[2], kk[3]};
@@ -584,14 +601,14 @@ static cx ew_contract(const ew_coup *c, int boson, const cx a[4], const cx b[4],
 }
 
 /* e-(p0) e+(p1) -> mu-(p2) mu+(p3) */
-static double me_ee_mumu(double p[][4], const or_params *par) {
+static real me_ee_mumu(real p[][4], const or_params *par) {
     ew_coup c = ew_couplings(par);
     cx G[2][4][4][4];
     ew_vertex(&c, 0, G[0]);
     ew_vertex(&c, 1, G[1]);
-    double kk[4];
+    real kk[4];
     for (int mu = 0; mu < 4; mu++) kk[mu] = p[0][mu] + p[1][mu];
-    double sum = 0;
+    real sum = 0;
     for (int h = 0; h < 16; h++) {
         int s0 = h & 1, s1 = (h >> 1) & 1, s2 = (h >> 2) & 1, s3 = (h >> 3) & 1;
         cx u1[4], v2[4], vb2[4], u3[4], ub3[4], v4[4];
@@ -618,22 +635,22 @@ static double me_ee_mumu(double p[][4], const or_params *par) {
 }
 
 /* incoming momenta and default polarisations of the gluons on the quark line */
-static void gluon_kin(int process, double p[][4], double k[][4]) {
+static void gluon_kin(int process, real p[][4], real k[][4]) {
     int n = n_gluons(process);
     for (int g = 0; g < n; g++) {
         int ip = gluon_particle(g);
-        double sgn = ip < 2 ? 1.0 : -1.0;
+        real sgn = ip < 2 ? 1.0 : -1.0;
         for (int mu = 0; mu < 4; mu++) k[g][mu] = sgn * p[ip][mu];
     }
 }
 
-static double me_gg_tt_ng(int process, double p[][4], const or_params *par) {
+static real me_gg_tt_ng(int process, real p[][4], const or_params *par) {
     int n = n_gluons(process), N = n_external(process);
     int K = NPERM[n];
-    double g = sqrt(4.0 * M_PI * par->alpha_s), m = par->m_t;
-    double k[MAXG][4];
+    real g = sqrt(4.0 * OR_PI * par->alpha_s), m = par->m_t;
+    real k[MAXG][4];
     gluon_kin(process, p, k);
-    double sum = 0;
+    real sum = 0;
     for (int h = 0; h < (1 << N); h++) {
         cx eps[MAXG][4], u3[4], ub3[4], v4[4];
         for (int gg = 0; gg < n; gg++) {
@@ -647,7 +664,7 @@ static double me_gg_tt_ng(int process, double p[][4], const or_params *par) {
         spinor_v(p[3], m, 0, (h >> 3) & 1, v4);
         cx A[MAXK];
         for (int s = 0; s < K; s++) A[s] = amp_ordered(n, PERM[n][s], k, eps, p[3], ub3, v4, m, g);
-        double cs = 0;
+        real cs = 0;
         for (int s = 0; s < K; s++)
             for (int t = 0; t < K; t++) cs += CMAT[n][s][t] * creal(conj(A[s]) * A[t]);
         sum += cs;
@@ -666,7 +683,7 @@ static double me_gg_tt_ng(int process, double p[][4], const or_params *par) {
  * every order (common factors of i and the vertex sign dropped: every
  * diagram carries the same ones).
  */
-static cx amp_ee_photons(int n, double p[][4], int basis, const int *hel, double e, const cx *eps_in) {
+static cx amp_ee_photons(int n, real p[][4], int basis, const int *hel, real e, const cx *eps_in) {
     cx u[4], v[4], vb[4], E[MAXA][4][4];
     spinor_u(p[0], 0.0, basis, hel[0], u);
     spinor_v(p[1], 0.0, basis, hel[1], v);
@@ -686,7 +703,7 @@ static cx amp_ee_photons(int n, double p[][4], int basis, const int *hel, double
     cx A = 0;
     do {
         cx psi[4], t[4];
-        double q[4];
+        real q[4];
         memcpy(psi, u, sizeof(psi));
         memcpy(q, p[0], sizeof(q));
         for (int j = 0; j < n; j++) {
@@ -699,7 +716,7 @@ static cx amp_ee_photons(int n, double p[][4], int basis, const int *hel, double
             cx Q[4][4];
             rslash(q, Q);
             matvec(Q, t, psi);
-            double q2 = rdot(q, q);
+            real q2 = rdot(q, q);
             for (int a = 0; a < 4; a++) psi[a] /= q2;
         }
         A += rowcol(vb, psi);
@@ -708,9 +725,9 @@ static cx amp_ee_photons(int n, double p[][4], int basis, const int *hel, double
 }
 
 /* spin-averaged |M|^2 of e- e+ -> n photons (1/4, 1/n!) */
-static double me_ee_photons(int n, double p[][4], const or_params *par) {
-    double e = sqrt(4.0 * M_PI / par->alpha_em_inv);
-    double sum = 0;
+static real me_ee_photons(int n, real p[][4], const or_params *par) {
+    real e = sqrt(4.0 * OR_PI / par->alpha_em_inv);
+    real sum = 0;
     int hel[MAXA + 2];
     for (int h = 0; h < (1 << (n + 2)); h++) {
         for (int i = 0; i < n + 2; i++) hel[i] = (h >> i) & 1;
@@ -720,7 +737,7 @@ static double me_ee_photons(int n, double p[][4], const or_params *par) {
     return sum / (4.0 * factorial(n));
 }
 
-static double me_event(int process, double p[][4], const or_params *par) {
+static real me_event(int process, real p[][4], const or_params *par) {
     if (process == OR_EE_MUMU) return me_ee_mumu(p, par);
     if (process == OR_EE_5A) return me_ee_photons(5, p, par);
     return me_gg_tt_ng(process, p, par);
@@ -733,8 +750,8 @@ static double me_event(int process, double p[][4], const or_params *par) {
    by xi with sum_i sqrt(m_i'^2 + xi^2 |p_i|^2) = sum_i E_i (the partonic
    energy in the centre-of-mass frame).  Returns 0 on success, 1 if the new
    masses do not fit (the event is outside the new phase space). */
-static int reshuffle(int N, const double *mnew, double pin[][4], double pout[][4]) {
-    double etot = 0, msum = 0, p2[MAXN];
+static int reshuffle(int N, const real *mnew, real pin[][4], real pout[][4]) {
+    real etot = 0, msum = 0, p2[MAXN];
     for (int i = 2; i < N; i++) {
         etot += pin[i][0];
         msum += mnew[i];
@@ -743,15 +760,15 @@ static int reshuffle(int N, const double *mnew, double pin[][4], double pout[][4
     for (int i = 0; i < N; i++)
         for (int mu = 0; mu < 4; mu++) pout[i][mu] = pin[i][mu];
     if (!(msum < etot)) return 1;
-    double xi = 1.0;
+    real xi = 1.0;
     for (int it = 0; it < 200; it++) {
-        double f = -etot, df = 0;
+        real f = -etot, df = 0;
         for (int i = 2; i < N; i++) {
-            double e = sqrt(mnew[i] * mnew[i] + xi * xi * p2[i]);
+            real e = sqrt(mnew[i] * mnew[i] + xi * xi * p2[i]);
             f += e;
             df += xi * p2[i] / e;
         }
-        double step = f / df;
+        real step = f / df;
         if (xi - step <= 0) step = 0.5 * xi;
         xi -= step;
         if (fabs(step) <= 1e-15 * xi) break;
@@ -763,15 +780,30 @@ static int reshuffle(int N, const double *mnew, double pin[][4], double pout[][4
     return 0;
 }
 
-static void new_masses(int process, const or_params *par, double *m) {
+static void new_masses(int process, const or_params *par, real *m) {
     int N = n_external(process);
     for (int i = 0; i < N; i++) m[i] = 0;
     if (is_qcd(process)) m[2] = m[3] = par->m_t;
 }
 
-static void load_event(int N, long E, const double *mom, long e, double p[][4]) {
+/* the event data stay float64 at the interface in either build */
+static void load_event(int N, long E, const double *mom, long e, real p[][4]) {
     for (int i = 0; i < N; i++)
         for (int mu = 0; mu < 4; mu++) p[i][mu] = mom[((long)i * 4 + mu) * E + e];
+}
+
+/* parameter vector (alpha_s, m_t, w_t, yt_scale, alpha_em_inv, G_F, m_Z, w_Z) */
+static or_params load_params(const double *v) {
+    or_params q;
+    q.alpha_s = v[0];
+    q.m_t = v[1];
+    q.w_t = v[2];
+    q.yt_scale = v[3];
+    q.alpha_em_inv = v[4];
+    q.G_F = v[5];
+    q.m_Z = v[6];
+    q.w_Z = v[7];
+    return q;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -794,12 +826,12 @@ int oracle_me(int process, const double *par, long E, const double *mom, double 
     if (n_external(process) < 0) return -1;
     init_all();
     int N = n_external(process);
-    const or_params *pp = (const or_params *)par;
+    const or_params pp = load_params(par);
 #pragma omp parallel for schedule(dynamic, 16)
     for (long e = 0; e < E; e++) {
-        double p[MAXN][4];
+        real p[MAXN][4];
         load_event(N, E, mom, e, p);
-        me_out[e] = me_event(process, p, pp);
+        me_out[e] = (double)me_event(process, p, &pp);
     }
     return 0;
 }
@@ -808,15 +840,16 @@ int oracle_me(int process, const double *par, long E, const double *mom, double 
 int oracle_reshuffle(int process, const double *par_new, long E, const double *mom, double *mom_out, int *status) {
     if (n_external(process) < 0) return -1;
     int N = n_external(process);
-    double m[MAXN];
-    new_masses(process, (const or_params *)par_new, m);
+    real m[MAXN];
+    const or_params pn = load_params(par_new);
+    new_masses(process, &pn, m);
 #pragma omp parallel for schedule(static)
     for (long e = 0; e < E; e++) {
-        double p[MAXN][4], q[MAXN][4];
+        real p[MAXN][4], q[MAXN][4];
         load_event(N, E, mom, e, p);
         status[e] = reshuffle(N, m, p, q);
         for (int i = 0; i < N; i++)
-            for (int mu = 0; mu < 4; mu++) mom_out[((long)i * 4 + mu) * E + e] = q[i][mu];
+            for (int mu = 0; mu < 4; mu++) mom_out[((long)i * 4 + mu) * E + e] = (double)q[i][mu];
     }
     return 0;
 }
@@ -833,38 +866,46 @@ int oracle_reweight(int process, const double *par0, int P, const double *pars, 
     if (n_external(process) < 0 || P < 0) return -1;
     init_all();
     int N = n_external(process);
-    const or_params *p0 = (const or_params *)par0;
-    const or_params *pt = (const or_params *)pars;
+    const or_params p0v = load_params(par0);
+    const or_params *p0 = &p0v;
+    or_params *pt = (or_params *)malloc(sizeof(or_params) * (P > 0 ? P : 1));
+    if (!pt) return -1;
+    for (int j = 0; j < P; j++) pt[j] = load_params(pars + 8 * (long)j);
     long bad = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : bad)
     for (long e = 0; e < E; e++) {
-        double p[MAXN][4], q[MAXN][4];
+        real p[MAXN][4], q[MAXN][4];
         load_event(N, E, mom, e, p);
-        double m0 = me_event(process, p, p0);
+        real m0 = me_event(process, p, p0);
         int ok = isfinite(m0) && m0 != 0.0;
         if (!ok) bad++;
-        if (me0) me0[e] = m0;
+        if (me0) me0[e] = (double)m0;
         for (int j = 0; j < P; j++) {
-            double m1;
+            real m1;
             if (is_qcd(process) && pt[j].m_t != p0->m_t) {
-                double mn[MAXN];
+                real mn[MAXN];
                 new_masses(process, &pt[j], mn);
                 m1 = reshuffle(N, mn, p, q) ? 0.0 : me_event(process, q, &pt[j]);
             } else {
                 m1 = me_event(process, p, &pt[j]);
             }
-            double r = ok ? m1 / m0 : 0.0;
-            if (me_pts) me_pts[(long)j * E + e] = m1;
-            if (ratio) ratio[(long)j * E + e] = r;
-            if (wnew) wnew[(long)j * E + e] = ok ? r * w[e] : 0.0;
+            real r = ok ? m1 / m0 : 0.0;
+            if (me_pts) me_pts[(long)j * E + e] = (double)m1;
+            if (ratio) ratio[(long)j * E + e] = (double)r;
+            if (wnew) wnew[(long)j * E + e] = ok ? (double)(r * w[e]) : 0.0;
         }
     }
+    free(pt);
     if (n_bad) *n_bad = bad;
     return 0;
 }
 
+/* Everything below is used by the pin tests only and exists in the FP64
+   build alone. */
+#ifndef ORACLE_EXTENDED
+
 /* colour matrix C[K][K] for n gluons (orderings in lexicographic order) */
-int oracle_colour_matrix(int n, double *C, int *perms) {
+int oracle_colour_matrix(int n, real *C, int *perms) {
     if (n < 1 || n > MAXG) return -1;
     init_all();
     int K = NPERM[n];
@@ -877,7 +918,7 @@ int oracle_colour_matrix(int n, double *C, int *perms) {
 }
 
 /* the generators t^a (8x3x3 complex) and f^{abc} (8x8x8) */
-void oracle_su3(cx *t, double *f) {
+void oracle_su3(cx *t, real *f) {
     init_all();
     if (t) memcpy(t, TGEN, sizeof(TGEN));
     if (f) memcpy(f, FSTRUCT, sizeof(FSTRUCT));
@@ -895,12 +936,12 @@ void oracle_dirac(cx *g, cx *g5) {
  * ext[i][4] complex: gluons -> eps (incoming) or eps^* (outgoing), top -> ubar
  * (row), antitop -> v.  basis 0: z-spin / linear, 1: helicity.  hel[i] in {0,1}.
  */
-int oracle_external(int process, const double *p, double m, int basis, const int *hel, cx *ext) {
+int oracle_external(int process, const real *p, real m, int basis, const int *hel, cx *ext) {
     if (!is_qcd(process)) return -1;
     init_all();
     int N = n_external(process);
-    double pp[MAXN][4];
-    memcpy(pp, p, sizeof(double) * 4 * N);
+    real pp[MAXN][4];
+    memcpy(pp, p, sizeof(real) * 4 * N);
     for (int i = 0; i < N; i++) {
         cx *o = ext + 4 * i;
         if (i == 2) {
@@ -919,26 +960,26 @@ int oracle_external(int process, const double *p, double m, int basis, const int
 }
 
 /* raw spinors for tests: kind 0 = u, 1 = v; basis, s as above */
-void oracle_spinor(int kind, const double *p, double m, int basis, int s, cx *out) {
+void oracle_spinor(int kind, const real *p, real m, int basis, int s, cx *out) {
     init_all();
     if (kind == 0)
         spinor_u(p, m, basis, s, out);
     else
         spinor_v(p, m, basis, s, out);
 }
-void oracle_polvec(const double *k, int basis, int s, cx *out) { polvec(k, basis, s, out); }
+void oracle_polvec(const real *k, int basis, int s, cx *out) { polvec(k, basis, s, out); }
 
 /* all partial amplitudes A[K] for explicit external wavefunctions ext[N][4] */
-int oracle_partial_amps(int process, const double *p, double m, double alpha_s, const cx *ext, cx *A) {
+int oracle_partial_amps(int process, const real *p, real m, real alpha_s, const cx *ext, cx *A) {
     if (!is_qcd(process)) return -1;
     init_all();
     int n = n_gluons(process), N = n_external(process);
-    double pp[MAXN][4], k[MAXG][4];
-    memcpy(pp, p, sizeof(double) * 4 * N);
+    real pp[MAXN][4], k[MAXG][4];
+    memcpy(pp, p, sizeof(real) * 4 * N);
     gluon_kin(process, pp, k);
     cx eps[MAXG][4];
     for (int gg = 0; gg < n; gg++) memcpy(eps[gg], ext + 4 * gluon_particle(gg), sizeof(cx) * 4);
-    double g = sqrt(4.0 * M_PI * alpha_s);
+    real g = sqrt(4.0 * OR_PI * alpha_s);
     for (int s = 0; s < NPERM[n]; s++) A[s] = amp_ordered(n, PERM[n][s], k, eps, pp[3], ext + 8, ext + 12, m, g);
     return NPERM[n];
 }
@@ -949,13 +990,13 @@ int oracle_partial_amps(int process, const double *p, double m, double alpha_s, 
  *    sum_{s,t} C_st Tr[(p3slash + m) Gamma_t (p4slash - m) bar(Gamma_s)];
  *  e+ e- -> mu+ mu-: Tr[p3 G^mu p4 bar(G'^nu)] Tr[p1 G^a p0 bar(G'^b)] P_{mu a} P'^*_{nu b}.
  */
-double oracle_me_traces(int process, const double *par, const double *p_aos) {
+real oracle_me_traces(int process, const real *par, const real *p_aos) {
     init_all();
     int N = n_external(process);
     if (N < 0 || process == OR_EE_5A) return NAN;
     const or_params *pp = (const or_params *)par;
-    double p[MAXN][4];
-    memcpy(p, p_aos, sizeof(double) * 4 * N);
+    real p[MAXN][4];
+    memcpy(p, p_aos, sizeof(real) * 4 * N);
     if (process == OR_EE_MUMU) {
         ew_coup c = ew_couplings(pp);
         cx G[2][4][4][4], Gb[2][4][4][4];
@@ -968,13 +1009,13 @@ double oracle_me_traces(int process, const double *par, const double *p_aos) {
         rslash(p[1], S1);
         rslash(p[2], S2);
         rslash(p[3], S3);
-        double kk[4];
+        real kk[4];
         for (int mu = 0; mu < 4; mu++) kk[mu] = p[0][mu] + p[1][mu];
-        double s = rdot(kk, kk);
+        real s = rdot(kk, kk);
         cx D[2] = {s, s - c.MZ * c.MZ + I * c.MZ * c.WZ};
-        double klow[4];
+        real klow[4];
         for (int mu = 0; mu < 4; mu++) klow[mu] = GMETRIC[mu] * kk[mu];
-        double total = 0;
+        real total = 0;
         for (int V = 0; V < 2; V++)
             for (int W = 0; W < 2; W++) {
                 cx T1[4][4], T2[4][4];
@@ -994,7 +1035,7 @@ double oracle_me_traces(int process, const double *par, const double *p_aos) {
                 cx P[4][4], Q[4][4];
                 for (int mu = 0; mu < 4; mu++)
                     for (int a = 0; a < 4; a++) {
-                        double gm = (mu == a) ? GMETRIC[mu] : 0.0;
+                        real gm = (mu == a) ? GMETRIC[mu] : 0.0;
                         P[mu][a] = (V == 0 ? gm : gm - klow[mu] * klow[a] / (c.MZ * c.MZ)) / D[V];
                         Q[mu][a] = conj((W == 0 ? gm : gm - klow[mu] * klow[a] / (c.MZ * c.MZ)) / D[W]);
                     }
@@ -1009,8 +1050,8 @@ double oracle_me_traces(int process, const double *par, const double *p_aos) {
     }
     int n = n_gluons(process);
     int K = NPERM[n];
-    double g = sqrt(4.0 * M_PI * pp->alpha_s), m = pp->m_t;
-    double k[MAXG][4];
+    real g = sqrt(4.0 * OR_PI * pp->alpha_s), m = pp->m_t;
+    real k[MAXG][4];
     gluon_kin(process, p, k);
     cx P3[4][4], P4[4][4];
     rslash(p[2], P3);
@@ -1019,7 +1060,7 @@ double oracle_me_traces(int process, const double *par, const double *p_aos) {
         P3[i][i] += m;
         P4[i][i] -= m;
     }
-    double total = 0;
+    real total = 0;
     for (int h = 0; h < (1 << n); h++) {
         cx eps[MAXG][4];
         for (int gg = 0; gg < n; gg++) {
@@ -1052,22 +1093,24 @@ double oracle_me_traces(int process, const double *par, const double *p_aos) {
  *   4-gluon vertex       -i g^2 [f^{abe}f^{cde}(g^{mu rho}g^{nu sigma} - g^{mu sigma}g^{nu rho}) + (b<->c perms)]
  *   propagators          -i g_{mu nu}/k^2,  i(qslash + m)/(q^2 - m^2)
  */
-int oracle_full_colour_amp(int process, const double *p_aos, double m, double alpha_s, const cx *ext, const int *adj,
+int oracle_full_colour_amp(int process, const real *p_aos, real m, real alpha_s, const cx *ext, const int *adj,
                            cx *Mout) {
     if (!is_qcd(process)) return -1;
     init_all();
     int n = n_gluons(process), N = n_external(process);
-    double p[MAXN][4], k[MAXG][4];
-    memcpy(p, p_aos, sizeof(double) * 4 * N);
+    real p[MAXN][4], k[MAXG][4];
+    memcpy(p, p_aos, sizeof(real) * 4 * N);
     gluon_kin(process, p, k);
-    double g = sqrt(4.0 * M_PI * alpha_s);
+    real g = sqrt(4.0 * OR_PI * alpha_s);
     int full = (1 << n) - 1;
     static cx J[1 << MAXG][8][4];
-    double KS[1 << MAXG][4];
+    static int nz[1 << MAXG][8]; /* J[S][a] not exactly zero */
+    real KS[1 << MAXG][4];
     memset(J, 0, sizeof(J));
+    memset(nz, 0, sizeof(nz));
     for (int S = 1; S <= full; S++) {
         for (int mu = 0; mu < 4; mu++) {
-            double s = 0;
+            real s = 0;
             for (int i = 0; i < n; i++)
                 if (S >> i & 1) s += k[i][mu];
             KS[S][mu] = s;
@@ -1078,9 +1121,10 @@ int oracle_full_colour_amp(int process, const double *p_aos, double m, double al
         if (pc == 1) {
             int i = __builtin_ctz(S);
             for (int mu = 0; mu < 4; mu++) J[S][adj[i]][mu] = ext[4 * gluon_particle(i) + mu];
+            nz[S][adj[i]] = 1;
             continue;
         }
-        double K2 = rdot(KS[S], KS[S]);
+        real K2 = rdot(KS[S], KS[S]);
         int low = S & -S;
         /* 3-vertex: unordered pairs {S1, S2}, S1 contains the lowest bit */
         for (int S1 = (S - 1) & S; S1 > 0; S1 = (S1 - 1) & S) {
@@ -1089,10 +1133,11 @@ int oracle_full_colour_amp(int process, const double *p_aos, double m, double al
             if (!S2) continue;
             for (int b = 0; b < 8; b++)
                 for (int c = 0; c < 8; c++) {
+                    if (!nz[S1][b] || !nz[S2][c]) continue; /* exact zeros */
                     cx t[4];
                     vertex3(J[S1][b], KS[S1], J[S2][c], KS[S2], t);
                     for (int a = 0; a < 8; a++) {
-                        double f = FSTRUCT[a][b][c];
+                        real f = FSTRUCT[a][b][c];
                         if (f == 0.0) continue;
                         for (int mu = 0; mu < 4; mu++) J[S][a][mu] += (-I / K2) * g * f * t[mu];
                     }
@@ -1111,6 +1156,7 @@ int oracle_full_colour_amp(int process, const double *p_aos, double m, double al
                 for (int b = 0; b < 8; b++)
                     for (int c = 0; c < 8; c++)
                         for (int d = 0; d < 8; d++) {
+                            if (!nz[S1][b] || !nz[S2][c] || !nz[S3][d]) continue; /* exact zeros */
                             const cx *J1 = J[S1][b], *J2 = J[S2][c], *J3 = J[S3][d];
                             cx d12 = mdot(J1, J2), d13 = mdot(J1, J3), d23 = mdot(J2, J3);
                             cx T1[4], T2[4], T3[4];
@@ -1120,7 +1166,7 @@ int oracle_full_colour_amp(int process, const double *p_aos, double m, double al
                                 T3[mu] = J1[mu] * d23 - J2[mu] * d13;
                             }
                             for (int a = 0; a < 8; a++) {
-                                double c1 = 0, c2 = 0, c3 = 0;
+                                real c1 = 0, c2 = 0, c3 = 0;
                                 for (int e = 0; e < 8; e++) {
                                     c1 += FSTRUCT[a][b][e] * FSTRUCT[c][d][e];
                                     c2 += FSTRUCT[a][c][e] * FSTRUCT[b][d][e];
@@ -1133,6 +1179,9 @@ int oracle_full_colour_amp(int process, const double *p_aos, double m, double al
                         }
             }
         }
+        for (int a = 0; a < 8; a++)
+            for (int mu = 0; mu < 4; mu++)
+                if (J[S][a][mu] != 0) nz[S][a] = 1;
     }
     /* fermion line from the antitop end: psi[S][i][j][4] */
     static cx psi[1 << MAXG][3][3][4];
@@ -1141,17 +1190,18 @@ int oracle_full_colour_amp(int process, const double *p_aos, double m, double al
         for (int d = 0; d < 4; d++) psi[0][i][i][d] = ext[12 + d];
     for (int S = 1; S <= full; S++) {
         if (S == full) break;
-        double q[4];
+        real q[4];
         for (int mu = 0; mu < 4; mu++) q[mu] = KS[S][mu] - p[3][mu];
         cx P[4][4];
         rslash(q, P);
         for (int i = 0; i < 4; i++) P[i][i] += m;
-        double den = rdot(q, q) - m * m;
+        real den = rdot(q, q) - m * m;
         cx acc[3][3][4];
         memset(acc, 0, sizeof(acc));
         for (int S1 = S; S1 > 0; S1 = (S1 - 1) & S) {
             int S2 = S ^ S1;
             for (int a = 0; a < 8; a++) {
+                if (!nz[S1][a]) continue; /* exact zeros */
                 cx Sl[4][4];
                 slash(J[S1][a], Sl);
                 for (int i = 0; i < 3; i++)
@@ -1179,6 +1229,7 @@ int oracle_full_colour_amp(int process, const double *p_aos, double m, double al
     for (int S1 = full; S1 > 0; S1 = (S1 - 1) & full) {
         int S2 = full ^ S1;
         for (int a = 0; a < 8; a++) {
+            if (!nz[S1][a]) continue; /* exact zeros */
             cx Sl[4][4];
             slash(J[S1][a], Sl);
             for (int i = 0; i < 3; i++)
@@ -1203,13 +1254,15 @@ int oracle_full_colour_amp(int process, const double *p_aos, double m, double al
  * already conjugated) instead when eps_in is not NULL -- and the
  * spin-averaged |M|^2 (1/4, 1/n!) as the return value.
  */
-double oracle_ee_photons(int n, const double *par, const double *p_aos, int basis, const int *hel, cx *amp,
+real oracle_ee_photons(int n, const real *par, const real *p_aos, int basis, const int *hel, cx *amp,
                          const cx *eps_in) {
     if (n < 1 || n > MAXA) return NAN;
     init_all();
-    double p[MAXN][4];
-    memcpy(p, p_aos, sizeof(double) * 4 * (n + 2));
+    real p[MAXN][4];
+    memcpy(p, p_aos, sizeof(real) * 4 * (n + 2));
     const or_params *pp = (const or_params *)par;
-    if (amp && hel) *amp = amp_ee_photons(n, p, basis, hel, sqrt(4.0 * M_PI / pp->alpha_em_inv), eps_in);
+    if (amp && hel) *amp = amp_ee_photons(n, p, basis, hel, sqrt(4.0 * OR_PI / pp->alpha_em_inv), eps_in);
     return me_ee_photons(n, p, pp);
 }
+
+#endif /* ORACLE_EXTENDED */

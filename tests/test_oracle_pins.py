@@ -352,6 +352,42 @@ def test_full_colour_sum_equals_me(oracle_mod, proc, wl):
     assert abs(tot / me - 1) < 1e-12
 
 
+def _full_colour_spin_sum(args):
+    """sum over the given helicity configurations and every gluon colour of
+    sum_ij |M_ij|^2 from the colour-dressed Feynman rules (worker process)."""
+    import oracle
+    proc, p, hels = args
+    n = oracle.N_EXTERNAL[proc] - 2
+    tot = 0.0
+    for hel in hels:
+        ext = oracle.external(proc, p, 173.0, 0, hel)
+        for adj in itertools.product(range(8), repeat=n):
+            M = oracle.full_colour_amp(proc, p, 173.0, 0.118, ext, adj)
+            tot += float(np.sum(np.abs(M) ** 2))
+    return tot
+
+
+def test_gg_ttgg_identical_gluon_factor(oracle_mod):
+    """g g -> t tbar g g: the two outgoing gluons are identical bosons, so a
+    phase-space integral over both would count every configuration twice;
+    |M|^2 therefore carries 1/2 besides the incoming averages 1/4 (spins) and
+    1/64 (colours).  Checked against the explicit sum over all 64 spin
+    configurations and all 8^4 gluon colour assignments of the colour-dressed
+    Feynman-rule amplitudes (f^abc, t^a, full four-gluon vertex), which uses
+    neither the colour-ordered decomposition nor the colour matrix."""
+    import multiprocessing as mp
+    proc = "gg_ttgg"
+    mom, _ = ev.generate(ev.WORKLOADS["gg_ttgg_1m"], 1)
+    p = mom[:, :, 0].copy()
+    hels = list(itertools.product([0, 1], repeat=6))
+    jobs = [(proc, p, hels[i::16]) for i in range(16)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        tot = math.fsum(pool.map(_full_colour_spin_sum, jobs))
+    spin_avg, colour_avg, identical = 4, 64, 2
+    me = oracle_mod.me(proc, ev.param_vector(), mom)[0]
+    assert abs(tot / (spin_avg * colour_avg * identical) / me - 1) < 1e-12
+
+
 # ---------------------------------------------------------------------------
 # P9 / P8: parameter dependence, reshuffle, Eq. 2/3 bookkeeping
 # ---------------------------------------------------------------------------

@@ -113,10 +113,16 @@ def test_lorentz_and_bose_symmetry(oracle_mod):
     assert np.allclose(oracle_mod.me("ee_5a", PAR, np.ascontiguousarray(mom[perm])), me, rtol=1e-13, atol=0)
 
 
-def test_soft_photon_limit(oracle_mod):
-    """A soft photon k factorises: |M_5|^2 5! -> |M_4|^2 4! e^2 2 p0.p1 /
-    ((p0.k)(p1.k)) (eikonal factor of the two massless beams, summed over
-    the photon's polarisations); the deviation vanishes linearly in |k|."""
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_soft_photon_limit(oracle_mod, n):
+    """A soft photon k factorises the spin-summed squared amplitude:
+    sum |A_n|^2 -> e^2 2 p0.p1 / ((p0.k)(p1.k)) sum |A_(n-1)|^2 (eikonal
+    factor of the two massless beams, summed over the photon's polarisations);
+    the deviation vanishes linearly in |k|.  The oracle's |M|^2 carries 1/n!
+    for n identical photons, so |M_n|^2 n -> |M_(n-1)|^2 x eikonal.  With
+    n = 2 fixed by the textbook cross section (test_two_photons_textbook),
+    the chain n = 3, 4, 5 pins the identical-photon factor 1/5! of the
+    e- e+ -> 5 photon workload."""
     rs = 500.0
 
     def deviation(seed, soft):
@@ -127,15 +133,15 @@ def test_soft_photon_limit(oracle_mod):
         # four hard photons recoiling against k: generated at rest with mass
         # M^2 = (P - k)^2, then boosted to momentum -k
         P = np.array([rs, 0.0, 0.0, 0.0]) - k
-        hard = event(4, seed, rs=math.sqrt(mdot(P, P)))[2:]
+        hard = event(n - 1, seed, rs=math.sqrt(mdot(P, P)))[2:]
         hard = ev.boost(hard[:, :, None], tuple(P[1:] / P[0]))[:, :, 0]
-        beams = event(4, seed)[:2]
-        p5 = np.vstack([beams, hard, k])
-        assert np.abs(p5[0] + p5[1] - p5[2:].sum(axis=0)).max() < 1e-9
-        me5, _ = oracle_mod.ee_photons(5, PAR, p5)
-        me4, _ = oracle_mod.ee_photons(4, PAR, np.vstack([beams, hard]))
-        eik = E2 * 2 * mdot(p5[0], p5[1]) / (mdot(p5[0], k) * mdot(p5[1], k))
-        return me5 * 5 / (me4 * eik) - 1
+        beams = event(n - 1, seed)[:2]
+        pn = np.vstack([beams, hard, k])
+        assert np.abs(pn[0] + pn[1] - pn[2:].sum(axis=0)).max() < 1e-9
+        me_n, _ = oracle_mod.ee_photons(n, PAR, pn)
+        me_m, _ = oracle_mod.ee_photons(n - 1, PAR, np.vstack([beams, hard]))
+        eik = E2 * 2 * mdot(pn[0], pn[1]) / (mdot(pn[0], k) * mdot(pn[1], k))
+        return me_n * n / (me_m * eik) - 1
     for seed in (41, 42, 43):
         d5, d6 = deviation(seed, 1e-5), deviation(seed, 1e-6)
         assert abs(d6) < 1e-4
