@@ -153,6 +153,12 @@ int rw_reweight_async(rw_ctx* ctx, double* d_wnew, double* d_ratio, double* d_me
 /* Copy the last reweight's sigma'_p [P], sigma (original) and bad-event count
    to the host; synchronises the stream.  Returns RW_WARN_BAD_EVENTS if any. */
 int rw_get_results(rw_ctx* ctx, double* h_sigma, double* h_sigma_orig, int64_t* h_n_bad);
+/* The same results as (sum, compensation) pairs before they are added:
+   h_sum[j] + h_comp[j] is sigma'_j for j < P and sigma for j = P (arrays of
+   P+1 doubles, both required).  For merging partial cross sections of event
+   shards (Eq. 2 over all shards) without losing the compensation term.
+   Synchronises the stream.  Returns RW_WARN_BAD_EVENTS if any. */
+int rw_get_result_pairs(rw_ctx* ctx, double* h_sum, double* h_comp, int64_t* h_n_bad);
 /* rw_reweight_async + rw_get_results. */
 int rw_reweight(rw_ctx* ctx, double* d_wnew, double* d_ratio, double* h_sigma, double* h_sigma_orig,
                 int64_t* h_n_bad);
@@ -341,6 +347,19 @@ int rw_lhe_write(rw_lhe* lhe, const char* path, const double* h_wnew, int P, int
    n > 0 -> RW_ERR_NULL, a failed launch -> RW_ERR_CUDA (there is no context,
    so no message). */
 int rw_split_double(const double* d_x, int64_t n, float* d_hi, float* d_lo, void* stream);
+
+/* ---------------------------------------------------------------------------
+   Measured plain-ALU peak of a GPU (the paper has no counterpart): the
+   amplitude kernels are bound by the FP64 pipe in RW_FP64 and by the FP32 FMA
+   pipe in the other modes, so their roofline denominators are these rates.
+   kind 0 = FP64 (DFMA), 1 = FP32 (FFMA): every SM at full occupancy runs
+   eight independent FMA chains per thread, one warm-up launch then the best
+   of three, timed with CUDA events on cuda_stream (a cudaStream_t, NULL = the
+   legacy default stream) of device `device`.  h_tflops: FLOP/s / 1e12
+   (an FMA counts 2); h_ms (may be NULL): the best launch's duration.
+   Synchronises the stream; allocates nothing.  RW_ERR_NULL, RW_ERR_ARG (bad
+   kind) or RW_ERR_CUDA. */
+int rw_alu_peak(int device, void* cuda_stream, int kind, double* h_tflops, double* h_ms);
 
 #ifdef __cplusplus
 }

@@ -49,6 +49,7 @@ struct RwArgs {
   unsigned long long* nbad_count; // zero between launches
   unsigned long long* nbad_out;
   double2* sigma_acc;  // [P+1] (sum, compensation) carried across launches, or null
+  double2* sigma_pair; // [P+1] each result's (sum, compensation) pair, or null
   long long ldo;       // row stride of the [P][.] outputs (0: E)
   int accumulate;      // 1: add this launch's sums and bad events to the previous launch's
   int P;
@@ -258,8 +259,10 @@ __global__ void __launch_bounds__(256, MINB) k_reweight(const __grid_constant__ 
         two_sum_acc(t.x, t.y, s, c);
         a.sigma_acc[j] = t;
         a.sigma[j] = t.x + t.y;
+        if (a.sigma_pair) a.sigma_pair[j] = t;
       } else {
         a.sigma[j] = s + c;
+        if (a.sigma_pair) a.sigma_pair[j] = make_double2(s, c);
       }
     }
   }

@@ -199,7 +199,11 @@ PointDev make_point(const rw_ctx* c, const rw_params& p, bool reshuffle) {
   return d;
 }
 
-size_t ws_core_bytes(int P) { return 256 + align256(8 * (size_t)(P + 2)) + (size_t)GRID_CAP * (P + 1) * 16; }
+// workspace: 256-B header (ticket, bad-event counter; sigma [P+1] and the
+// bad-event count from byte 64), block partials double2 [GRID_CAP][P+1], then
+// the results' (sum, compensation) pairs double2 [P+1]
+size_t ws_pairs_offset(int P) { return 256 + align256(8 * (size_t)(P + 2)) + (size_t)GRID_CAP * (P + 1) * 16; }
+size_t ws_core_bytes(int P) { return ws_pairs_offset(P) + align256(16 * (size_t)(P + 1)); }
 
 int check_dev_ptr(rw_ctx* c, const void* p, const char* name) {
   if (!p) return fail(c, RW_ERR_NULL, "%s is NULL", name);
@@ -305,6 +309,7 @@ void fill_ws(rw_ctx* c, RwArgs& a, int P) {
   a.sigma = reinterpret_cast<double*>(b + 64);
   a.nbad_out = reinterpret_cast<unsigned long long*>(b + 64 + 8 * (size_t)(P + 1));
   a.block_part = reinterpret_cast<double2*>(b + 256 + align256(8 * (size_t)(P + 2)));
+  a.sigma_pair = reinterpret_cast<double2*>(b + ws_pairs_offset(P));
 }
 
 }  // namespace
@@ -600,6 +605,31 @@ int rw_get_results(rw_ctx* c, double* h_sigma, double* h_sigma_orig, int64_t* h_
   if (h_sigma_orig) *h_sigma_orig = c->h_stage[P];
   unsigned long long nb;
   memcpy(&nb, c->h_stage + P + 1, 8);
+  if (h_n_bad) *h_n_bad = (int64_t)nb;
+  return nb ? RW_WARN_BAD_EVENTS : RW_OK;
+}
+
+int rw_get_result_pairs(rw_ctx* c, double* h_sum, double* h_comp, int64_t* h_n_bad) {
+  int rc = ready(c, true);
+  if (rc) return rc;
+  if (c->pts.empty()) return fail(c, RW_ERR_STATE, "no reweight points set");
+  if (!h_sum || !h_comp) return fail(c, RW_ERR_NULL, "h_sum and h_comp are required");
+  DeviceGuard g(c->device);
+  const int P = (int)c->pts.size();
+  std::vector<double2> pairs(P + 1);
+  cudaError_t e = cudaMemcpyAsync(pairs.data(), c->ws + ws_pairs_offset(P), 16 * (size_t)(P + 1),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
+  e = cudaMemcpyAsync(c->h_stage, c->ws + 64 + 8 * (size_t)(P + 1), 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  for (int j = 0; j <= P; ++j) {
+    h_sum[j] = pairs[j].x;
+    h_comp[j] = pairs[j].y;
+  }
+  unsigned long long nb;
+  memcpy(&nb, c->h_stage, 8);
   if (h_n_bad) *h_n_bad = (int64_t)nb;
   return nb ? RW_WARN_BAD_EVENTS : RW_OK;
 }

@@ -66,6 +66,7 @@ def load():
         "rw_eval_me": ([P, i, P], i),
         "rw_reweight_async": ([P, P, P, P, P], i),
         "rw_get_results": ([P, P, P, P], i),
+        "rw_get_result_pairs": ([P, P, P, P], i),
         "rw_reweight": ([P, P, P, P, P, P], i),
         "rw_workspace_bytes_host": ([P, i64], sz),
         "rw_reweight_host": ([P, P, P, i64, P, P, P, P, P, sz], i),
@@ -97,6 +98,7 @@ def load():
         "rw_lhe_read": ([P, i, i64, i64, P, i64, P, i], i),
         "rw_lhe_write": ([P, ctypes.c_char_p, P, i, i64, P], i),
         "rw_reweight_interp": ([P, i, d, P, P, P, P, P, P, P, sz], i),
+        "rw_alu_peak": ([i, P, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -134,6 +136,17 @@ def _check_buffer(x, name, min_elems=0, dtype="float64"):
         raise ValueError(f"{name}: must be C-contiguous")
     if n < min_elems:
         raise ValueError(f"{name}: {n} elements, need at least {min_elems}")
+
+
+def alu_peak(kind, device=0, stream=None):
+    """rw_alu_peak: measured FP64 (kind "fp64") or FP32 ("fp32") FMA throughput
+    of the device in TFLOP/s, and the timed launch's milliseconds."""
+    lib = load()
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib.rw_alu_peak(device, stream, {"fp64": 0, "fp32": 1}[kind], ctypes.byref(t), ctypes.byref(ms))
+    if rc:
+        raise RwError(rc, "rw_alu_peak")
+    return t.value, ms.value
 
 
 def split_double(d_x, d_hi, d_lo, stream=None):
@@ -267,6 +280,16 @@ class Context:
         rc = self._check(self.lib.rw_get_results(self.h, sig.ctypes.data, ctypes.byref(so), ctypes.byref(nb)),
                          "rw_get_results")
         return sig, so.value, nb.value, rc
+
+    def get_result_pairs(self, n_points: int):
+        """(sum[P+1], compensation[P+1], n_bad) of the last reweight; index P
+        is the original sample's sigma."""
+        s = np.zeros(n_points + 1)
+        c = np.zeros(n_points + 1)
+        nb = ctypes.c_int64()
+        self._check(self.lib.rw_get_result_pairs(self.h, s.ctypes.data, c.ctypes.data, ctypes.byref(nb)),
+                    "rw_get_result_pairs")
+        return s, c, nb.value
 
     def reweight(self, n_points: int, wnew=None, ratio=None):
         sig = np.zeros(n_points)

@@ -30,6 +30,16 @@ def test_merge_sums_is_compensated():
         assert abs(got[j] - math.fsum(parts[:, j])) <= 2 * np.spacing(abs(math.fsum(parts[:, j])) + 1e-300)
 
 
+def test_merge_pairs_keeps_each_shards_compensation():
+    """A shard's compensation term can exceed the ulp of the total; merging
+    the collapsed values loses it, merging the pairs keeps it."""
+    sums = np.array([[1e16], [1.0], [-1e16]])
+    comps = np.array([[0.75], [0.0], [0.5]])
+    exact = math.fsum([1e16, 0.75, 1.0, -1e16, 0.5])
+    assert shard.merge_pairs(sums, comps)[0] == exact
+    assert shard.merge_sums(sums + comps)[0] != exact
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -51,7 +61,11 @@ def _rank_main(rank, world, port, out_path):
     mom, w = ev.generate(wl, b - a, start=a)
     pts = ev.reweight_points("gg_tt_1m")
     res = oracle.reweight("gg_tt", ev.param_vector(), pts, mom, w)
-    merged = shard.allreduce_sums(list(res["sigma"]) + [res["sigma_orig"]])
+    # each shard's sums as (sum, compensation) pairs, as the library returns them
+    parts = list(res["wnew"]) + [w]
+    s = [math.fsum(x) for x in parts]
+    c = [math.fsum(list(x) + [-v]) for x, v in zip(parts, s)]
+    merged = shard.allreduce_pairs(s, c)
     if rank == 0:
         np.save(out_path, merged)
     dist.barrier()
