@@ -5,11 +5,16 @@ One step = one pass of the whole hot path over one batch: for every event
 |M|^2 under the original parameters, the mass-shell move and |M'|^2 for each
 parameter point, r = |M'|^2/|M|^2, W' = r W and the cross sections
 sigma'_p = sum W'_p and sigma = sum W (arXiv:2312.07440, Sec. 3.2 steps 3-8,
-Eqs. 2-3).  Default workload: g g -> t tbar, 1,048,576 events, sqrt(s-hat)
-uniform in [400, 2000] GeV, massive RAMBO momenta (m_t = 173 GeV),
-lognormal weights, one point (m_t 175 GeV, alpha_s 0.120), FP64 amplitudes.
+Eqs. 2-3).  Default workload: g g -> t tbar g g, 1,048,576 events,
+sqrt(s-hat) uniform in [600, 4000] GeV, gluon p_T > 20 GeV and Delta R > 0.4,
+massive RAMBO momenta (m_t = 173 GeV), lognormal weights, one point
+(m_t = 1.2 x 173 GeV), FP64 amplitudes.  The line's `variants` time the same
+configuration in FP32 and with the BF16/FP16 tensor-core colour sum, and the
+other configurations (g g -> t tbar g, 4M events x 64 points; g g -> t tbar
+1M; e+ e- -> mu+ mu-; e+ e- -> 5 photons), each with its roofline and its
+accuracy against the FP64 oracle.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|fp32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|fp32|...]
   python bench.py --impl reference     # the FP64 CPU oracle on the host cores
 
 Rank 0 prints one JSON line.  `value` is device-resident throughput
@@ -40,10 +45,6 @@ from paper_2312_07440_gb300 import events as ev  # noqa: E402
 L2_BYTES = 129 * 2 ** 20
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-# Plain-ALU peaks (no tensor cores on this path): FP32 = 152 SMs x 128 lanes
-# x 2 flop (FMA) x 2.07 GHz; FP64 = the GB300 nominal FP64 rate.
-ALU_PEAK_TFLOPS = {"fp32": SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12, "fp64": 1.25}
-ALU_PEAK_TFLOPS["mixed_fp16"] = ALU_PEAK_TFLOPS["mixed_bf16"] = ALU_PEAK_TFLOPS["fp32"]  # FP32 amplitudes dominate
 METRIC = "reweighted events/s at stated rel err (plain FP64 vs mixed-precision/surrogate)"
 UNIT = "events*points/s"
 
@@ -54,18 +55,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gg_tt_1m", choices=list(ev.WORKLOADS))
-    ap.add_argument("--variant", default="default", help="point set variant (gg_ttg/gg_ttgg: default|mt)")
+    ap.add_argument("--workload", default="gg_ttgg_1m", choices=list(ev.WORKLOADS))
+    ap.add_argument("--variant", default="auto",
+                    help="point set: default|mt (auto: mt for gg_ttg/gg_ttgg, default elsewhere)")
     ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32", "mixed_fp16", "mixed_bf16"])
     ap.add_argument("--events", type=int, default=0, help="override the workload's event count (profiling runs)")
     ap.add_argument("--lane-bits", type=int, default=-1)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--no-variants", action="store_true", help="skip the FP32 variant of the default FP64 run")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the other configurations and precision modes (variants)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    ap.add_argument("--ref-seconds", type=float, default=90.0,
+                    help="reference arm: oracle time budget of the whole --warmup + --steps run")
     ap.add_argument("--surrogate", action="store_true",
                     help="learned-surrogate run on g g -> t tbar g g: train on exact labels, then time "
                          "surrogate inference with exact fallback against the exact kernel")
@@ -110,21 +115,25 @@ def source_sha(process, mode):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload, mode):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken
-    on the current kernel sources (profiles/*.md 'traffic:' lines)."""
+def profiled_value(workload, mode, key):
+    """A per-launch figure (dram_bytes_per_launch, executed_flops_per_event)
+    from a committed ncu summary, if it was taken on the current kernel
+    sources: profiles/*.md lines
+    'traffic: workload=W mode=M sources=SHA key=value ...'."""
     sha = source_sha(ev.WORKLOADS[workload].process, mode)
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None
-    pat = re.compile(r"traffic:\s*workload=(\S+)\s+mode=(\S+)\s+sources=(\S+)\s+dram_bytes_per_launch=(\S+)")
+    pat = re.compile(r"traffic:\s*workload=(\S+)\s+mode=(\S+)\s+sources=(\S+)((?:\s+\w+=\S+)+)")
     for fn in sorted(os.listdir(pdir)):
         if not fn.endswith((".md", ".txt")):
             continue
         for line in open(os.path.join(pdir, fn)):
             m = pat.search(line)
             if m and m.group(1) == workload and m.group(2) == mode and m.group(3) == sha:
-                return float(m.group(4))
+                kv = dict(x.split("=", 1) for x in m.group(4).split())
+                if key in kv:
+                    return float(kv[key])
     return None
 
 
@@ -185,21 +194,24 @@ def cpu_model():
     return "unknown"
 
 
-def oracle_throughput(wl, pts, budget_s, chunk=65536, start_event=0):
-    """The oracle as it stands on the host cores, over whole chunks of the
-    workload until the time budget is spent.  Returns (events*points/s, n_events, cores)."""
+def oracle_rate(wl, pts, budget_s, start_event=0, max_events=1 << 20):
+    """The oracle as it stands on the host cores: a calibration chunk of 64
+    events, then one chunk sized to the time budget.  Returns
+    (events*points/s, n_events timed, cores)."""
     import oracle
     cores = oracle.set_threads(0)
     P = pts.shape[0]
-    done, t_used = 0, 0.0
-    while done < wl.n_events and t_used < budget_s:
-        n = min(chunk, wl.n_events - done)
-        mom, w = ev.generate(wl, n, start=start_event + done)
-        t0 = time.perf_counter()
-        oracle.reweight(wl.process, ev.param_vector(), pts, mom, w)
-        t_used += time.perf_counter() - t0
-        done += n
-    return done * P / t_used, done, cores
+    mom, w = ev.generate(wl, 64, start=start_event)
+    t0 = time.perf_counter()
+    oracle.reweight(wl.process, ev.param_vector(), pts, mom, w)
+    t_cal = max(time.perf_counter() - t0, 1e-6)
+    n = int(min(max_events, wl.n_events, max(64, 64 * budget_s / t_cal)))
+    n = max(64, n // 64 * 64)
+    mom, w = ev.generate(wl, n, start=start_event)
+    t0 = time.perf_counter()
+    oracle.reweight(wl.process, ev.param_vector(), pts, mom, w)
+    t = time.perf_counter() - t0
+    return n * P / t, n, cores
 
 
 # ---------------------------------------------------------------------------
@@ -211,10 +223,18 @@ def run_reference(args):
         return
     import oracle
     wl = ev.WORKLOADS[args.workload]
-    pts = ev.reweight_points(args.workload, args.variant)
+    variant = point_variant(args)
+    pts = ev.reweight_points(args.workload, variant)
     P = pts.shape[0]
     cores = oracle.set_threads(0)
-    sample = 65536
+    # each step is a bounded sample of the workload: the whole run stays
+    # within about --ref-seconds of oracle time
+    per_step = max(args.ref_seconds / max(1, args.warmup + args.steps), 0.05)
+    mom, w = ev.generate(wl, 64)
+    t0 = time.perf_counter()
+    oracle.reweight(wl.process, ev.param_vector(), pts, mom, w)
+    t_cal = max(time.perf_counter() - t0, 1e-6)
+    sample = int(min(65536, wl.n_events, max(64, 64 * per_step / t_cal))) // 64 * 64
     mom, w = ev.generate(wl, sample)
     times = []
     for i in range(args.warmup + args.steps):
@@ -228,7 +248,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_dict(args, wl, P),
+        "config": config_dict(args, wl, P, variant),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"first {sample} events of {wl.name} per step, {P} point(s), "
                                    f"CPU {cpu_model()}"},
@@ -237,15 +257,137 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def config_dict(args, wl, P):
+def point_variant(args):
+    """g g -> t tbar g(g): the m_t = kappa 173 GeV axis unless asked otherwise
+    (the literal top-Yukawa axis gives r == 1 for every event)."""
+    if args.variant != "auto":
+        return args.variant
+    return "mt" if ev.WORKLOADS[args.workload].process in ("gg_ttg", "gg_ttgg") else "default"
+
+
+POINT_SETS = {
+    "mt": "m_t = kappa x 173 GeV (events moved onto the new mass shell)",
+    "default": "the workload's stated points (gg_ttg/gg_ttgg: top-Yukawa scale kappa, r == 1 at tree level)",
+}
+
+
+def config_dict(args, wl, P, variant, mode=None):
     return {"workload": wl.name, "process": wl.process, "events": wl.n_events, "points": P,
-            "point_set": args.variant, "sqrt_s_range_gev": list(wl.sqrt_s), "mode": args.mode,
-            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"events sharded x{args.gpus}"}
+            "point_set": f"{variant}: {POINT_SETS.get(variant, variant)}", "sqrt_s_range_gev": list(wl.sqrt_s),
+            "mode": mode or args.mode, "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"events sharded x{args.gpus}"}
+
+
+DTYPE = {"fp64": "f64", "fp32": "f32", "mixed_fp16": "f32+f16(colour)", "mixed_bf16": "f32+bf16(colour)"}
+
+
+def measured_peaks(dev_index, stream_handle):
+    """FP64 / FP32 FMA throughput of this GPU (rw_alu_peak), TFLOP/s."""
+    from paper_2312_07440_gb300 import rwgt
+    out = {}
+    for k in ("fp64", "fp32"):
+        out[k] = rwgt.alu_peak(k, dev_index, stream_handle)[0]
+    return out
+
+
+def alu_roofline(info, E, P, t_step, mode, peaks, workload):
+    """Roofline of the fused kernel against the plain-ALU pipe it is bound by:
+    algorithmic flops = (1 + P) x the generator's static count of one helicity
+    sum per event; the ncu-executed count beside it when a profile of the
+    current sources records one."""
+    flops_event = (1 + P) * info.flops_hel_sum
+    achieved = E * flops_event / t_step / 1e12
+    pipe = "fp64" if mode == "fp64" else "fp32"
+    peak = peaks[pipe]
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": profiled_value(workload, mode, "dram_bytes_per_launch"),
+            "kernel": "k_reweight (fused: amplitudes, colour sum, helicity sum, ratio, W', sigma)",
+            "flops_per_event": flops_event,
+            "peak_source": f"measured {pipe.upper()} FMA streams on every SM (rw_alu_peak) on this GPU"}
+    ex = profiled_value(workload, mode, "executed_flops_per_event")
+    if ex:
+        roof["executed_flops_per_event"] = ex
+        roof["executed_frac"] = E * ex / t_step / 1e12 / peak
+    return roof
+
+
+def timed_steps(torch, stream, step, steps, warmup, flush):
+    """W untimed steps, then K steps timed with CUDA events on the launching
+    stream, L2 flushed before each."""
+    for _ in range(warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) * 1e-3 for s, e in zip(starts, ends)]
+
+
+_ACC_CACHE = {}
+
+
+def accuracy_sample(wl, pts, mom_h, w_h, wnew, mode, n=2000, variant=""):
+    """Per-event relative error of W' against the FP64 oracle on a seeded
+    sample of the run's events (the oracle's result is shared by every mode
+    of a workload)."""
+    import oracle
+    rng = np.random.default_rng(1)
+    idx = np.unique(rng.integers(0, wl.n_events, n))
+    key = (wl.name, variant, len(idx), pts.tobytes())
+    if key not in _ACC_CACHE:
+        _ACC_CACHE[key] = oracle.reweight(wl.process, ev.param_vector(), pts,
+                                          np.ascontiguousarray(mom_h[:, :, idx]), w_h[idx])["wnew"]
+    o = _ACC_CACHE[key]
+    g = wnew[:, idx].cpu().numpy()
+    r = np.where(g == o, 0.0, np.abs(g - o) / np.maximum(np.abs(o), 1e-300))
+    return {"quantity": "W' per event, relative, vs the FP64 oracle", "events": int(len(idx)),
+            "points": int(pts.shape[0]), "max": float(r.max()), "median": float(np.median(r)),
+            "p999": float(np.quantile(r, 0.999)),
+            "tolerance": {"fp64": 1e-12, "fp32": 1e-5}.get(mode, "stated (mixed-precision bound), not asserted")}
+
+
+# the comparison the metric names: every BASELINE configuration that fits one
+# GPU, in each of its precision modes (device-resident, same timing rules)
+VARIANTS = [
+    # (name, workload, point set, mode, oracle sample events)
+    ("gg_ttgg_1m_fp32", "gg_ttgg_1m", "mt", "fp32", 2000),
+    ("gg_ttgg_1m_mixed_bf16", "gg_ttgg_1m", "mt", "mixed_bf16", 2000),
+    ("gg_ttgg_1m_mixed_fp16", "gg_ttgg_1m", "mt", "mixed_fp16", 2000),
+    ("gg_ttg_4m_x64_fp32", "gg_ttg_4m", "mt", "fp32", 256),
+    ("gg_ttg_4m_x64_mixed_fp16", "gg_ttg_4m", "mt", "mixed_fp16", 256),
+    ("gg_ttg_4m_x64_yt_mixed_fp16", "gg_ttg_4m", "default", "mixed_fp16", 256),
+    ("gg_tt_1m_fp64", "gg_tt_1m", "default", "fp64", 2000),
+    ("gg_tt_1m_fp32", "gg_tt_1m", "default", "fp32", 2000),
+    ("ee_mumu_4k_fp64", "ee_mumu_4k", "default", "fp64", 4096),
+    ("ee_5a_1m_x8_fp32", "ee_5a_1m", "default", "fp32", 200),
+]
 
 
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def attach(torch, dev, stream, rwgt, wl, pts, mom, w, mode, autotune, lane_bits=-1, block=0):
+    E = wl.n_events
+    c = rwgt.Context(dev.index or 0, stream.cuda_stream)
+    c.set_process(wl.process, mode)
+    c.set_params(ev.param_vector())
+    c.set_reweight_points(pts)
+    c.set_tuning(lane_bits, block)
+    nb = c.workspace_bytes(E)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    c.load_events(mom, w, E, ws, nb)
+    if autotune:
+        # launch shape chosen by the library's autotuner on a bounded subset (not timed)
+        c.autotune(max_events=min(E, 1 << 16))
+    return c, ws
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -256,11 +398,14 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    peaks = measured_peaks(local, stream.cuda_stream)
     wl = ev.WORKLOADS[args.workload]
     if args.events > 0:
         import dataclasses
         wl = dataclasses.replace(wl, n_events=args.events)
-    pts = ev.reweight_points(args.workload, args.variant)
+    variant = point_variant(args)
+    pts = ev.reweight_points(args.workload, variant)
     P = pts.shape[0]
     E = wl.n_events
     N = ev.N_EXTERNAL[wl.process]
@@ -268,20 +413,9 @@ def run_ours(args):
     mom_h, w_h = ev.generate(wl, E, start=rank * E)
     mom = torch.from_numpy(mom_h).to(dev)
     w = torch.from_numpy(w_h).to(dev)
-    stream = torch.cuda.current_stream(dev)
-    ctx = rwgt.Context(local, stream.cuda_stream)
-    ctx.set_process(wl.process, args.mode)
-    ctx.set_params(ev.param_vector())
-    ctx.set_reweight_points(pts)
-    ctx.set_tuning(args.lane_bits, args.block)
-    nb = ctx.workspace_bytes(E)
-    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
-    ctx.load_events(mom, w, E, ws, nb)
-    tuning_source = "fixed"
-    if args.lane_bits < 0 and args.block == 0 and not args.no_autotune:
-        # launch shape chosen by the library's autotuner on a bounded subset (not timed)
-        ctx.autotune(max_events=min(E, 1 << 18))
-        tuning_source = "autotuned on min(E, 262144) events"
+    autotune = args.lane_bits < 0 and args.block == 0 and not args.no_autotune
+    ctx, ws = attach(torch, dev, stream, rwgt, wl, pts, mom, w, args.mode, autotune, args.lane_bits, args.block)
+    tuning_source = "autotuned on min(E, 65536) events" if autotune else "fixed"
     lane_bits, block = ctx.get_tuning()
     wnew = torch.empty((P, E), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
@@ -297,132 +431,102 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(local, enabled=(rank == 0 and not args.no_clocks))
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        starts[i].record(stream)
-        step()
-        ends[i].record(stream)
-    torch.cuda.synchronize()
+    per_step = timed_steps(torch, stream, step, args.steps, 0, flush)
     clocks = sampler.stop()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    per_step = [s.elapsed_time(e) * 1e-3 for s, e in zip(starts, ends)]
     t_total = sum(per_step)
     sig, sig_orig, nbad, _ = ctx.get_results(P)
     if world > 1:
         tt = torch.tensor([t_total], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_total = float(tt.item())
-        # the one exchange of the method: sum of the per-shard cross sections
+        # the one exchange of the method: the per-shard cross sections as
+        # (sum, compensation) pairs, merged in rank order
         from paper_2312_07440_gb300 import shard
-        ss = shard.allreduce_sums(list(sig) + [sig_orig], device=dev)
+        s_pair, c_pair, _ = ctx.get_result_pairs(P)
+        ss = shard.allreduce_pairs(s_pair, c_pair, device=dev)
         sig, sig_orig = ss[:P], float(ss[P])
     t_step = t_total / args.steps
     value = world * E * P / t_step
 
-    # accuracy of this run against the oracle on a sample of its events
     acc = None
     if rank == 0:
-        acc = accuracy_sample(wl, pts, mom_h, w_h, wnew, args.mode)
-
-    # end to end through the host entry point (rank 0 of each node does it on its own GPU)
-    # the same workload in FP32 mode (same events, same points), device-resident
-    variants = None
-    if rank == 0 and world == 1 and args.mode == "fp64" and not args.no_variants:
-        variants = {"fp32": run_variant(torch, dev, stream, wl, pts, mom, w, mom_h, w_h, "fp32", args, flush)}
-
+        acc = accuracy_sample(wl, pts, mom_h, w_h, wnew, args.mode, variant=variant)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(ctx, torch, dev, mom_h, w_h, E, P, N, world, args)
-
     info = rwgt.process_info(wl.process)
-    flops_event = (1 + P) * info.flops_hel_sum
-    achieved = E * flops_event / t_step / 1e12
-    peak = ALU_PEAK_TFLOPS[args.mode]
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": profiled_traffic(wl.name, args.mode),
-            "kernel": "k_reweight (fused: amplitudes, colour sum, helicity sum, ratio, W', sigma)",
-            "flops_per_event": flops_event,
-            "peak_source": ("FP64: GB300 nominal 1.25 TFLOP/s" if args.mode == "fp64" else
-                            "FP32: 152 SM x 128 lanes x 2 x 2.07 GHz (derived); mixed modes: FP32 amplitudes "
-                            "dominate, the colour sum runs on the tensor cores")}
+    roof = alu_roofline(info, E, P, t_step, args.mode, peaks, wl.name)
+    ctx.close()
+    del ws
+
+    variants = None
+    if rank == 0 and world == 1 and not args.no_variants:
+        variants = {}
+        cache = {(wl.name, variant): (mom, w, mom_h, w_h)}
+        for name, vwl_name, vvar, vmode, n_acc in VARIANTS:
+            if vwl_name == wl.name and vvar == variant and vmode == args.mode:
+                continue
+            key = (vwl_name, vvar)
+            if key not in cache:
+                cache = {k: v for k, v in cache.items() if k[0] == vwl_name}  # keep one sample resident
+                vwl = ev.WORKLOADS[vwl_name]
+                vm_h, vw_h = ev.generate(vwl, vwl.n_events)
+                cache[key] = (torch.from_numpy(vm_h).to(dev), torch.from_numpy(vw_h).to(dev), vm_h, vw_h)
+            variants[name] = run_variant(torch, rwgt, dev, stream, ev.WORKLOADS[vwl_name], vvar, vmode,
+                                         cache[key], args, flush, peaks, n_acc)
+        del cache
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, n, cores = oracle_throughput(wl, pts, args.cpu_seconds, start_event=0)
+        v, n, cores = oracle_rate(wl, pts, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {n} events of {wl.name} (chunks of 65536), {P} point(s), CPU {cpu_model()}"}
+               "sample": f"first {n} events of {wl.name}, {P} point(s), CPU {cpu_model()}"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "data": "synthetic",
-            "dtype": {"fp64": "f64", "fp32": "f32", "mixed_fp16": "f32+f16(colour)",
-                      "mixed_bf16": "f32+bf16(colour)"}[args.mode],
-            "config": dict(config_dict(args, wl, P), tuning={"lane_bits": lane_bits, "block": block,
-                                                              "source": tuning_source}),
+            "vs_baseline": None, "data": "synthetic", "dtype": DTYPE[args.mode],
+            "config": dict(config_dict(args, wl, P, variant), tuning={"lane_bits": lane_bits, "block": block,
+                                                                     "source": tuning_source}),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clocks, "accuracy_vs_oracle": acc, "variants": variants,
+            "clocks": clocks, "accuracy_vs_oracle": acc, "measured_peaks_tflops": peaks,
             "sigma": [float(x) for x in sig], "sigma_orig": sig_orig, "n_bad": int(nbad),
             "step_ms_min_median_max": [1e3 * min(per_step), 1e3 * statistics.median(per_step),
                                        1e3 * max(per_step)],
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_variant(torch, dev, stream, wl, pts, mom, w, mom_h, w_h, mode, args, flush):
-    """Device-resident timing of the same step in another precision mode."""
-    from paper_2312_07440_gb300 import rwgt
+def run_variant(torch, rwgt, dev, stream, wl, variant, mode, sample, args, flush, peaks, n_acc):
+    """Device-resident timing of one configuration in one precision mode
+    (its own context, autotuned launch shape, same timing rules as the
+    headline), its roofline and its accuracy against the oracle."""
+    mom, w, mom_h, w_h = sample
+    pts = ev.reweight_points(wl.name, variant)
     E, P = wl.n_events, pts.shape[0]
-    c = rwgt.Context(dev.index or 0, stream.cuda_stream)
-    c.set_process(wl.process, mode)
-    c.set_params(ev.param_vector())
-    c.set_reweight_points(pts)
-    nb = c.workspace_bytes(E)
-    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
-    c.load_events(mom, w, E, ws, nb)
-    c.autotune(max_events=min(E, 1 << 18))
+    c, ws = attach(torch, dev, stream, rwgt, wl, pts, mom, w, mode, True)
     lb, bl = c.get_tuning()
     wn = torch.empty((P, E), dtype=torch.float64, device=dev)
-    for _ in range(args.warmup):
-        flush.fill_(1)
-        c.reweight_async(wn)
-    ts = []
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        c.reweight_async(wn)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b) * 1e-3)
+    ts = timed_steps(torch, stream, lambda: c.reweight_async(wn), args.steps, args.warmup, flush)
     c.close()
     t = sum(ts) / len(ts)
-    from paper_2312_07440_gb300 import rwgt as _r
-    info = _r.process_info(wl.process)
-    fl = (1 + P) * info.flops_hel_sum * E / t / 1e12
-    return {"value": E * P / t, "unit": UNIT, "ms_per_step": 1e3 * t, "dtype": "f32",
-            "tuning": {"lane_bits": lb, "block": bl},
-            "roofline": {"bound": "alu", "achieved": fl, "peak": ALU_PEAK_TFLOPS[mode], "unit": "TFLOP/s",
-                         "frac": fl / ALU_PEAK_TFLOPS[mode]},
-            "accuracy_vs_oracle": accuracy_sample(wl, pts, mom_h, w_h, wn, mode)}
-
-
-def accuracy_sample(wl, pts, mom_h, w_h, wnew, mode, n=2000):
-    import oracle
-    rng = np.random.default_rng(1)
-    idx = np.unique(rng.integers(0, wl.n_events, n))
-    o = oracle.reweight(wl.process, ev.param_vector(), pts, np.ascontiguousarray(mom_h[:, :, idx]), w_h[idx])
-    g = wnew[:, idx].cpu().numpy()
-    r = np.abs(g - o["wnew"]) / np.maximum(np.abs(o["wnew"]), 1e-300)
-    return {"quantity": "W' per event, relative", "events": int(len(idx)), "max": float(r.max()),
-            "median": float(np.median(r)), "p999": float(np.quantile(r, 0.999)),
-            "tolerance": {"fp64": 1e-12, "fp32": 1e-5}.get(mode, "stated, not asserted")}
+    info = rwgt.process_info(wl.process)
+    out = {"workload": wl.name, "events": E, "points": P,
+           "point_set": f"{variant}: {POINT_SETS.get(variant, variant)}", "mode": mode,
+           "value": E * P / t, "unit": UNIT, "ms_per_step": 1e3 * t, "dtype": DTYPE[mode],
+           "tuning": {"lane_bits": lb, "block": bl},
+           "roofline": alu_roofline(info, E, P, t, mode, peaks, wl.name),
+           "accuracy_vs_oracle": accuracy_sample(wl, pts, mom_h, w_h, wn, mode, n=n_acc, variant=variant)}
+    if variant == "default" and wl.process in ("gg_ttg", "gg_ttgg"):
+        out["r_is_exactly_one"] = bool(torch.all(wn == w.unsqueeze(0)).item())
+    del wn, ws
+    return out
 
 
 def run_e2e(ctx, torch, dev, mom_h, w_h, E, P, N, world, args):

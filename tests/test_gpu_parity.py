@@ -1,9 +1,11 @@
-"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
 Tolerances (per event, relative): 1e-12 in FP64 mode, 1e-5 in FP32 mode, on
-|M|^2, |M'|^2, r and W'.  Cross sections: the GPU sigma' must equal the
-exactly rounded sum of the GPU's own W' to 2 ulp (compensated summation), and
-agree with the oracle's exact sum to the per-event tolerance.
+|M|^2, |M'|^2, r and W', flat for every event (FP64 mode: against the
+extended-precision oracle where the FP64 oracle's own rounding matters, see
+check_against_oracle).  Cross sections: the GPU sigma' must equal the exactly
+rounded sum of the GPU's own W' to 2 ulp (compensated summation), and agree
+with the oracle's exact sum to the per-event tolerance.
 """
 import math
 
@@ -52,43 +54,45 @@ def run_gpu(proc, mode, mom, w, pts, lane_bits=-1, block=0):
     return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
 
 
-def input_sensitivity(proc, pts, mom, w, trials=6, seed=7):
-    """Per-event relative change of the oracle's |M|^2, |M'|^2 and r when every
-    input momentum component moves by at most one ulp (random signs).  FP64
-    inputs cannot satisfy momentum conservation and the mass shells exactly; near
-    an on-shell top propagator (a gluon radiated off a top) that ambiguity alone
-    moves |M|^2 by up to ~1e-12, so no two FP64 evaluations can agree better."""
-    rng = np.random.default_rng(seed)
-    base = oracle.reweight(proc, ev.param_vector(), pts, mom, w)
-    s = np.zeros((1 + len(pts), mom.shape[-1]))
-    for _ in range(trials):
-        pert = mom * (1 + rng.integers(-1, 2, size=mom.shape) * np.finfo(float).eps)
-        o = oracle.reweight(proc, ev.param_vector(), pts, pert, w)
-        s[0] = np.maximum(s[0], rel(o["me0"], base["me0"]))
-        s[1:] = np.maximum(s[1:], np.maximum(rel(o["me"], base["me"]), rel(o["ratio"], base["ratio"])))
-    return s
+def per_event_error(g, o):
+    """Largest relative difference per event over |M|^2, every |M'|^2, r and W'."""
+    e = rel(g["me0"], o["me0"])
+    for k in ("me", "ratio", "wnew"):
+        e = np.maximum(e, rel(g[k], o[k]).max(axis=0))
+    return e
 
 
-def check_against_oracle(g, o, mode, sens=None):
-    """Per-event bound: TOL[mode]; in FP64 mode max(1e-12, 4 s_e) when the
-    event's input sensitivity s_e (see input_sensitivity) exceeds 2.5e-13."""
+def check_against_oracle(g, o, mode, inputs=None):
+    """Per event, relative: |GPU - oracle| < TOL[mode] on |M|^2, |M'|^2, r, W';
+    sigma' within 2 ulp of the exact sum of the GPU's own W' and within TOL of
+    the oracle's exact sum.
+
+    FP64 mode: the FP64 oracle's own rounding error reaches ~6e-13 on a few
+    ill-conditioned events (a top propagator close to its mass shell), so an
+    event whose GPU result differs from it by more than TOL/4 is evaluated
+    again by the extended-precision build of the oracle (the same formulas
+    with a 64-bit significand on x86-64, 113-bit on AArch64) and must be
+    within TOL of that.  tests/test_oracle_extended.py shows on these seeded
+    samples that the FP64 oracle is within 3 TOL/4 of the extended result, so
+    the events within TOL/4 of the FP64 oracle are within TOL of it too.
+    inputs = (process, points, momenta, weights) enables the re-evaluation."""
     tol = TOL[mode]
-    tol0, tolp = tol, tol
-    if sens is not None:
-        tol0 = np.maximum(tol, 4 * sens[0])
-        tolp = np.maximum(tol, 4 * sens[1:])
-    assert np.all(rel(g["me0"], o["me0"]) < tol0)
-    assert np.all(rel(g["me"], o["me"]) < tolp)
-    assert np.all(rel(g["ratio"], o["ratio"]) < tolp)
-    assert np.all(rel(g["wnew"], o["wnew"]) < tolp)
+    err = per_event_error(g, o)
+    if mode == "fp64" and inputs is not None:
+        proc, pts, mom, w = inputs
+        flagged = np.nonzero(err >= tol / 4)[0]
+        if flagged.size:
+            x = oracle.reweight(proc, ev.param_vector(), pts, np.ascontiguousarray(mom[:, :, flagged]),
+                                w[flagged], precision="extended")
+            sub = {k: (g[k][..., flagged]) for k in ("me0", "me", "ratio", "wnew")}
+            err[flagged] = per_event_error(sub, x)
+    assert err.max() < tol, f"max per-event error {err.max():.3e} (event {int(err.argmax())})"
     for j in range(len(g["sigma"])):
         exact_gpu = math.fsum(g["wnew"][j])
         assert abs(g["sigma"][j] - exact_gpu) <= 2 * np.spacing(exact_gpu)
         assert abs(g["sigma"][j] / o["sigma"][j] - 1) < tol
     assert abs(g["sigma_orig"] - o["sigma_orig"]) <= 2 * np.spacing(o["sigma_orig"])
     assert g["n_bad"] == o["n_bad"]
-    if sens is not None:  # the relaxed bound stays the exception
-        assert np.mean(np.max(sens, axis=0) > tol / 4) < 0.02
 
 
 # --------------------------------------------------------------------------
@@ -100,7 +104,7 @@ def test_gg_tt_parity(mode, lane_bits):
     pts = ev.reweight_points("gg_tt_1m")
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 5003, pts)  # several blocks + a ragged tail
     g = run_gpu("gg_tt", mode, mom, w, pts, lane_bits=lane_bits)
-    check_against_oracle(g, o, mode)
+    check_against_oracle(g, o, mode, ("gg_tt", pts, mom, w))
 
 
 @pytest.mark.parametrize("block", [32, 64, 256])
@@ -108,7 +112,7 @@ def test_gg_tt_block_sizes(block):
     pts = ev.reweight_points("gg_tt_1m")
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 5003, pts)
     g = run_gpu("gg_tt", "fp64", mom, w, pts, block=block)
-    check_against_oracle(g, o, "fp64")
+    check_against_oracle(g, o, "fp64", ("gg_tt", pts, mom, w))
 
 
 def test_gg_tt_several_points_and_alpha_s_scaling():
@@ -116,7 +120,7 @@ def test_gg_tt_several_points_and_alpha_s_scaling():
                     ev.param_vector(m_t=175.0, alpha_s=0.120), ev.param_vector(m_t=160.0)])
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 777, pts)
     g = run_gpu("gg_tt", "fp64", mom, w, pts)
-    check_against_oracle(g, o, "fp64")
+    check_against_oracle(g, o, "fp64", ("gg_tt", pts, mom, w))
     assert np.abs(g["ratio"][0] / (0.120 / 0.118) ** 2 - 1).max() < 1e-14   # P9
     assert np.all(g["ratio"][2] == 1.0) and np.all(g["wnew"][2] == w)       # P8 (bitwise)
 
@@ -127,7 +131,7 @@ def test_ee_mumu_parity_full_sample(mode):
     mom, w, o = oracle_run("ee_mumu", "ee_mumu_4k", 4096, pts)
     for lb in ([0, 2, 4] if mode == "fp64" else [0]):
         g = run_gpu("ee_mumu", mode, mom, w, pts, lane_bits=lb)
-        check_against_oracle(g, o, mode)
+        check_against_oracle(g, o, mode, ("ee_mumu", pts, mom, w))
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
@@ -136,29 +140,16 @@ def test_gg_ttg_parity(mode, lane_bits):
     pts = ev.reweight_points("gg_ttg_4m", "mt")[::21]  # kappa = 0.8, 0.933, 1.067, 1.2 (m_t = kappa 173)
     mom, w, o = oracle_run("gg_ttg", "gg_ttg_4m", 611, pts)
     g = run_gpu("gg_ttg", mode, mom, w, pts, lane_bits=lane_bits)
-    sens = sensitivity("gg_ttg", "gg_ttg_4m", 611, pts) if mode == "fp64" else None
-    check_against_oracle(g, o, mode, sens)
-
-
-_SENS_CACHE = {}
-
-
-def sensitivity(proc, wl_name, n, pts):
-    key = (proc, wl_name, n, pts.tobytes())
-    if key not in _SENS_CACHE:
-        mom, w, _ = oracle_run(proc, wl_name, n, pts)
-        _SENS_CACHE[key] = input_sensitivity(proc, pts, mom, w)
-    return _SENS_CACHE[key]
+    check_against_oracle(g, o, mode, ("gg_ttg", pts, mom, w))
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
 def test_gg_ttgg_parity(mode):
     pts = ev.reweight_points("gg_ttgg_1m", "mt")
     mom, w, o = oracle_run("gg_ttgg", "gg_ttgg_1m", 197, pts)
-    sens = sensitivity("gg_ttgg", "gg_ttgg_1m", 197, pts) if mode == "fp64" else None
     for lb in (1, 2, 3):
         g = run_gpu("gg_ttgg", mode, mom, w, pts, lane_bits=lb)
-        check_against_oracle(g, o, mode, sens)
+        check_against_oracle(g, o, mode, ("gg_ttgg", pts, mom, w))
 
 
 # --------------------------------------------------------------------------
@@ -170,8 +161,7 @@ def test_ee_5a_parity(mode, lane_bits):
     pts = ev.reweight_points("ee_5a_1m")[:3]
     mom, w, o = oracle_run("ee_5a", "ee_5a_1m", 517, pts)  # several blocks + a ragged tail
     g = run_gpu("ee_5a", mode, mom, w, pts, lane_bits=lane_bits)
-    sens = sensitivity("ee_5a", "ee_5a_1m", 517, pts) if mode == "fp64" else None
-    check_against_oracle(g, o, mode, sens)
+    check_against_oracle(g, o, mode, ("ee_5a", pts, mom, w))
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
@@ -206,7 +196,7 @@ def test_tiny_batches(n):
     pts = ev.reweight_points("gg_tt_1m")
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", n, pts)
     g = run_gpu("gg_tt", "fp64", mom, w, pts)
-    check_against_oracle(g, o, "fp64")
+    check_against_oracle(g, o, "fp64", ("gg_tt", pts, mom, w))
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
@@ -219,7 +209,7 @@ def test_maximum_number_of_points(mode):
     assert pts.shape[0] == 256
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 77, pts)
     g = run_gpu("gg_tt", mode, mom, w, pts)
-    check_against_oracle(g, o, mode)
+    check_against_oracle(g, o, mode, ("gg_tt", pts, mom, w))
 
 
 def test_bad_events_are_counted_and_excluded():
