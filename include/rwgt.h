@@ -197,6 +197,43 @@ int rw_graph_launch(rw_graph* graph, void* cuda_stream);
 int rw_graph_destroy(rw_graph* graph);
 
 /* ---------------------------------------------------------------------------
+   Several processes in one persistent launch (Sec. 3.2 steps 3-7 for every
+   process of a sample at once; Sec. 4: the real-emission events of an NLO
+   sample are tree-level events of one more parton, reweighted by the same LO
+   machinery).  Each process is a context with its process, mode, parameters,
+   points, events and workspace set as for rw_reweight_async; one kernel walks
+   tiles of all of their events grid-stride, so a cheap process fills the gaps
+   a costly one leaves.  Per process: W'[P_i][E_i] and r[P_i][E_i] where the
+   pointers given to rw_multi_add are not NULL, and its sigma'_p, sigma and
+   bad-event count in its own workspace (rw_get_results(ctx) after the launch).
+   Compiled process sets, each in one precision mode for all of its processes:
+     {g g -> t tbar g, g g -> t tbar}                 RW_FP64, RW_FP32
+     {g g -> t tbar g g, g g -> t tbar g, g g -> t tbar} RW_FP64
+   (any other set or mode: RW_ERR_MODE at launch).  At most 420 parameter
+   points in total over the processes, one original point counted per
+   process (RW_ERR_ARG).  Threads per block: 128.  The launch is asynchronous
+   on the stream given to rw_multi_create, which must order the launch after
+   the work queued for the contexts' events.  Results are deterministic for a
+   given set of contexts.  Not thread-safe; contexts must outlive the
+   rw_multi that holds them. */
+typedef struct rw_multi rw_multi;
+int rw_multi_create(rw_multi** m, int device, void* cuda_stream);
+int rw_multi_destroy(rw_multi* m);
+const char* rw_multi_last_error(const rw_multi* m);
+/* add a prepared context (RW_ERR_STATE when its events or points are
+   missing, RW_ERR_MODE when its mode differs from those already added,
+   RW_ERR_ARG for a second context of the same process or a fifth process) */
+int rw_multi_add(rw_multi* m, rw_ctx* ctx, double* d_wnew, double* d_ratio);
+/* device workspace of the launch itself (its ticket), 16-byte aligned */
+size_t rw_multi_workspace_bytes(const rw_multi* m);
+int rw_multi_reweight_async(rw_multi* m, void* d_workspace, size_t workspace_bytes);
+/* the sample's totals: sigma'_p = sum over processes of each process's
+   sigma'_p (P must be the same for every process, else RW_ERR_STATE),
+   sigma and the bad-event count, merged from the (sum, compensation) pairs
+   in the order the processes were added; synchronises the contexts' streams */
+int rw_multi_get_results(rw_multi* m, double* h_sigma, double* h_sigma_orig, int64_t* h_n_bad);
+
+/* ---------------------------------------------------------------------------
    Learned surrogate for log r (spec extension; the paper has none).
    An MLP n_in -> [hidden, SiLU] x n_layers -> 2 predicts mu = log r and
    s = log of its own error for a feature vector built from an event and a
@@ -332,6 +369,16 @@ int64_t rw_lhe_n_events(const rw_lhe* lhe);
 int rw_lhe_read(rw_lhe* lhe, int process, int64_t first, int64_t n, double* h_mom, int64_t ld, double* h_w,
                 int n_threads);
 int rw_lhe_write(rw_lhe* lhe, const char* path, const double* h_wnew, int P, int64_t ld, const char* const* ids);
+/* Samples with several processes (e.g. the Born and real-emission events of
+   an NLO sample, Sec. 4): h_process_of_event[k] (one int per event) = the
+   first of processes[0..n_processes-1] (1..8 RW_* ids) whose external
+   particles event k matches exactly, or -1; n_threads threads. */
+int rw_lhe_classify(rw_lhe* lhe, const int* processes, int n_processes, int* h_process_of_event, int n_threads);
+/* rw_lhe_read for the events idx[0..n-1] (file indices, any order): event
+   idx[i] goes to column i of h_mom [N][4][ld] and h_w[i].  RW_ERR_ARG for an
+   index outside the file or an event that does not match the process. */
+int rw_lhe_read_list(rw_lhe* lhe, int process, const int64_t* idx, int64_t n, double* h_mom, int64_t ld, double* h_w,
+                     int n_threads);
 
 /* ---------------------------------------------------------------------------
    Input conversion of the FP32 modes, exposed for verification.  The paper has

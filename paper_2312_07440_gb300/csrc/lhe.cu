@@ -262,15 +262,17 @@ const char* rw_lhe_last_error(const rw_lhe* h) { return h ? h->err.c_str() : "nu
 
 int64_t rw_lhe_n_events(const rw_lhe* h) { return h ? (int64_t)h->body.size() : -1; }
 
-int rw_lhe_read(rw_lhe* h, int process, int64_t first, int64_t n, double* h_mom, int64_t ld, double* h_w,
+}  // extern "C"
+
+namespace {
+
+// parse the events idx(0..n-1) into columns 0..n-1 of h_mom [N][4][ld] and
+// h_w with up to n_threads threads (contiguous shares of the list)
+template <class Index>
+int read_events(rw_lhe* h, int process, int64_t n, Index idx, double* h_mom, int64_t ld, double* h_w,
                 int n_threads) {
-  if (!h) return RW_ERR_NULL;
   std::vector<int> codes;
   if (!process_codes(process, codes)) return lhe_fail(h, RW_ERR_ARG, "unknown process %d", process);
-  if (!h_mom || !h_w) return lhe_fail(h, RW_ERR_NULL, "momenta/weights are NULL");
-  if (first < 0 || n < 0 || first + n > (int64_t)h->body.size() || ld < n)
-    return lhe_fail(h, RW_ERR_ARG, "range [%lld, %lld) / ld %lld outside the %zu events", (long long)first,
-                    (long long)(first + n), (long long)ld, h->body.size());
   const int N = (int)codes.size();
   const int T = std::max(1, std::min<int>(n_threads > 0 ? n_threads : 1, (int)std::max<int64_t>(1, n / 1024)));
   std::vector<long long> bad(T, -1);
@@ -280,8 +282,9 @@ int rw_lhe_read(rw_lhe* h, int process, int64_t first, int64_t n, double* h_mom,
     double p[16][4];
     for (int64_t i = a; i < b; ++i) {
       double w;
-      if (parse_event(h, (size_t)(first + i), codes, p, w, why[t])) {
-        bad[t] = first + i;
+      const int64_t k = idx(i);
+      if (parse_event(h, (size_t)k, codes, p, w, why[t])) {
+        bad[t] = k;
         return;
       }
       for (int s = 0; s < N; ++s)
@@ -295,6 +298,59 @@ int rw_lhe_read(rw_lhe* h, int process, int64_t first, int64_t n, double* h_mom,
   for (auto& th : pool) th.join();
   for (int t = 0; t < T; ++t)
     if (bad[t] >= 0) return lhe_fail(h, RW_ERR_ARG, "event %lld: %s", bad[t], why[t].c_str());
+  return RW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rw_lhe_read(rw_lhe* h, int process, int64_t first, int64_t n, double* h_mom, int64_t ld, double* h_w,
+                int n_threads) {
+  if (!h) return RW_ERR_NULL;
+  if (!h_mom || !h_w) return lhe_fail(h, RW_ERR_NULL, "momenta/weights are NULL");
+  if (first < 0 || n < 0 || first + n > (int64_t)h->body.size() || ld < n)
+    return lhe_fail(h, RW_ERR_ARG, "range [%lld, %lld) / ld %lld outside the %zu events", (long long)first,
+                    (long long)(first + n), (long long)ld, h->body.size());
+  return read_events(h, process, n, [first](int64_t i) { return first + i; }, h_mom, ld, h_w, n_threads);
+}
+
+int rw_lhe_read_list(rw_lhe* h, int process, const int64_t* idx, int64_t n, double* h_mom, int64_t ld, double* h_w,
+                     int n_threads) {
+  if (!h) return RW_ERR_NULL;
+  if (!h_mom || !h_w || (n > 0 && !idx)) return lhe_fail(h, RW_ERR_NULL, "index list, momenta or weights are NULL");
+  if (n < 0 || ld < n) return lhe_fail(h, RW_ERR_ARG, "n %lld / ld %lld", (long long)n, (long long)ld);
+  const int64_t E = (int64_t)h->body.size();
+  for (int64_t i = 0; i < n; ++i)
+    if (idx[i] < 0 || idx[i] >= E)
+      return lhe_fail(h, RW_ERR_ARG, "index %lld: event %lld outside the %lld events", (long long)i,
+                      (long long)idx[i], (long long)E);
+  return read_events(h, process, n, [idx](int64_t i) { return idx[i]; }, h_mom, ld, h_w, n_threads);
+}
+
+int rw_lhe_classify(rw_lhe* h, const int* processes, int n_processes, int* h_process_of_event, int n_threads) {
+  if (!h) return RW_ERR_NULL;
+  if (!processes || !h_process_of_event) return lhe_fail(h, RW_ERR_NULL, "process list or output is NULL");
+  if (n_processes < 1 || n_processes > 8) return lhe_fail(h, RW_ERR_ARG, "1..8 processes");
+  std::vector<std::vector<int>> codes(n_processes);
+  for (int j = 0; j < n_processes; ++j)
+    if (!process_codes(processes[j], codes[j])) return lhe_fail(h, RW_ERR_ARG, "unknown process %d", processes[j]);
+  const int64_t E = (int64_t)h->body.size();
+  const int T = std::max(1, std::min<int>(n_threads > 0 ? n_threads : 1, (int)std::max<int64_t>(1, E / 1024)));
+  auto work = [&](int t) {
+    double p[16][4], w;
+    std::string why;
+    for (int64_t k = E * t / T; k < E * (t + 1) / T; ++k) {
+      int found = -1;
+      for (int j = 0; j < n_processes && found < 0; ++j)
+        if (!parse_event(h, (size_t)k, codes[j], p, w, why)) found = processes[j];
+      h_process_of_event[k] = found;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < T; ++t) pool.emplace_back(work, t);
+  work(0);
+  for (auto& th : pool) th.join();
   return RW_OK;
 }
 

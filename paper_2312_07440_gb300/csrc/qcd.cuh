@@ -75,6 +75,47 @@ __device__ __forceinline__ double dot4(const double (&a)[4], const double (&b)[4
   return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
 }
 
+// Double-double arithmetic for the FP64 set-up's invariants of several
+// gluons: Knuth's TwoSum, the FMA form of TwoProduct, one rounding at the end.
+// A gluon propagator 1/K^2 of an incoming and an outgoing gluon near the beam
+// axis has K^2 ~ 1e2-1e3 GeV^2 while k_i.k_j-style products are ~1e6 GeV^2,
+// so K^2 formed in plain FP64 carries relative errors of ~1e-13, which the
+// largest-|M|^2 events (near-collinear emission) pass on to |M|^2.
+struct dd {
+  double hi, lo;
+};
+
+__device__ __forceinline__ dd dd_two_sum(double a, double b) {
+  const double s = a + b;
+  const double bp = s - a;
+  return {s, (a - (s - bp)) + (b - bp)};
+}
+
+__device__ __forceinline__ dd dd_add(dd x, double y) {
+  const dd s = dd_two_sum(x.hi, y);
+  const double lo = s.lo + x.lo;
+  const double h = s.hi + lo;
+  return {h, lo - (h - s.hi)};
+}
+
+// v.v - c for a double-double 4-vector v and c = c_hi + c_lo, rounded once:
+// each (hi + lo)^2 is hi*hi (exact as hi*hi + e by FMA) + 2 hi lo (lo^2 is
+// below the last digit), the large terms are added by TwoSum.
+__device__ __forceinline__ double dd_msq_minus(const dd (&v)[4], double c_hi, double c_lo) {
+  dd acc = {0.0, 0.0};
+  double small = -c_lo;
+#pragma unroll
+  for (int m4 = 0; m4 < 4; ++m4) {
+    const double sg = m4 ? -1.0 : 1.0;
+    const double p = v[m4].hi * v[m4].hi;
+    const double e = fma(v[m4].hi, v[m4].hi, -p) + 2.0 * v[m4].hi * v[m4].lo;
+    acc = dd_add(acc, sg * p);
+    small += sg * e;
+  }
+  acc = dd_add(acc, -c_hi);
+  return acc.hi + (acc.lo + small);
+}
+
 template <class R, int NG, int NEXT>
 __device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, QcdExt<R, NG>& X,
                                           QcdKin<R, NG>& Kn) {
@@ -136,6 +177,25 @@ __device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, 
         if ((msk >> i) & 1) v += kw[i][m4];
       Kn.P[msk][m4] = v;
     }
+    // several gluons (g g -> t tbar g(g)): K^2 and (K - p4)^2 - m^2 from the
+    // momenta themselves, in double-double, rounded once
+    [[maybe_unused]] double den_dd = 0.0;
+    if constexpr (NG >= 3) {
+      if (cnt >= 2) {
+        dd Kd[4], q[4];
+#pragma unroll
+        for (int m4 = 0; m4 < 4; ++m4) {
+          Kd[m4] = {0.0, 0.0};
+#pragma unroll
+          for (int i = 0; i < NG; ++i)
+            if ((msk >> i) & 1) Kd[m4] = dd_add(Kd[m4], k[i][m4]);
+          q[m4] = dd_add(Kd[m4], -p[3][m4]);
+        }
+        K2 = dd_msq_minus(Kd, 0.0, 0.0);
+        const double m2 = m * m;
+        den_dd = dd_msq_minus(q, m2, fma(m, m, -m2));
+      }
+    }
     if (cnt >= 2) {
       const R inv = R(1) / R(K2);
       Kn.cg[msk] = -inv;
@@ -145,8 +205,8 @@ __device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, 
       Kn.c4[msk] = R(0);
     }
     if (msk != FULL) {
-      // (K - p4)^2 - m^2 = K^2 - 2 K.p4  (p4^2 = m^2)
-      const double den = K2 - 2.0 * dot4(P, p[3]);
+      // (K - p4)^2 - m^2 = K^2 - 2 K.p4  (p4^2 = m^2); several gluons: as above
+      const double den = (NG >= 3 && cnt >= 2) ? den_dd : K2 - 2.0 * dot4(P, p[3]);
       const R c = R(-1) / R(den);
 #pragma unroll
       for (int m4 = 0; m4 < 4; ++m4) Kn.qc[msk][m4] = c * R(P[m4] - p[3][m4]);

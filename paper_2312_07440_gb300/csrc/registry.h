@@ -15,12 +15,24 @@ struct KernelEntry {
   int smem_per_thread = 0;  // dynamic shared memory of the amplitude code (bytes per thread)
 };
 
+// a k_reweight_multi instantiation: processes in its template order, each
+// with its lanes per event (2^lane_bits), one precision mode for all
+struct MultiEntry {
+  int mode;
+  int n;
+  int process[4];
+  int lane_bits[4];
+  const void* func;
+  int smem_per_thread;  // dynamic shared memory of the amplitude code (bytes per thread)
+};
+
 struct ProcStatic {
   int n_external, n_helicities, n_colour_flows, n_diagrams, colour_den, n_ident, n_gluons;
   long long flops_hel_sum;
   int max_lane_bits;  // helicity loop levels that can be mapped to lanes
 };
 
+void register_multi(std::vector<MultiEntry>& t);
 void register_ee_mumu(std::vector<KernelEntry>& t, ProcStatic& s);
 void register_ee_5a_fp64(std::vector<KernelEntry>& t);
 void register_ee_5a_fp32(std::vector<KernelEntry>& t);

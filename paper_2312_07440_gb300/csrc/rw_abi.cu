@@ -1428,3 +1428,220 @@ int rw_reweight_interp(rw_ctx* c, int n_nodes, double tol, double* d_wnew, unsig
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Several processes in one persistent launch (multi.cuh)
+// ---------------------------------------------------------------------------
+#include "multi.cuh"
+
+namespace {
+
+struct MultiRegistry {
+  std::vector<rw::MultiEntry> kernels;
+  MultiRegistry() { rw::register_multi(kernels); }
+};
+
+const MultiRegistry& multi_registry() {
+  static MultiRegistry r;
+  return r;
+}
+
+}  // namespace
+
+struct rw_multi {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  struct Item {
+    rw_ctx* ctx;
+    double *wnew, *ratio;
+  };
+  std::vector<Item> items;
+  std::string err;
+  std::map<std::pair<const void*, size_t>, int> occ;
+};
+
+namespace {
+
+int mfail(rw_multi* m, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int mfail(rw_multi* m, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (m) m->err = buf;
+  return code;
+}
+
+constexpr size_t MULTI_WS_BYTES = 256;  // the launch's ticket
+
+}  // namespace
+
+extern "C" {
+
+int rw_multi_create(rw_multi** out, int device, void* stream) {
+  if (!out) return RW_ERR_NULL;
+  *out = nullptr;
+  rw_multi* m = new rw_multi();
+  m->device = device;
+  m->stream = static_cast<cudaStream_t>(stream);
+  if (cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return RW_ERR_CUDA;
+  }
+  *out = m;
+  return RW_OK;
+}
+
+int rw_multi_destroy(rw_multi* m) {
+  if (!m) return RW_ERR_NULL;
+  delete m;
+  return RW_OK;
+}
+
+const char* rw_multi_last_error(const rw_multi* m) { return m ? m->err.c_str() : "null handle"; }
+
+int rw_multi_add(rw_multi* m, rw_ctx* c, double* d_wnew, double* d_ratio) {
+  if (!m || !c) return RW_ERR_NULL;
+  if ((int)m->items.size() >= rw::MAX_MULTI) return mfail(m, RW_ERR_ARG, "at most %d processes", rw::MAX_MULTI);
+  int rc = ready(c, true);
+  if (rc) return mfail(m, rc, "context not ready: %s", c->err.c_str());
+  if (c->pts.empty()) return mfail(m, RW_ERR_STATE, "context has no reweight points");
+  if (c->device != m->device) return mfail(m, RW_ERR_ARG, "context on device %d, launch on %d", c->device, m->device);
+  for (const auto& it : m->items) {
+    if (it.ctx == c) return mfail(m, RW_ERR_ARG, "context added twice");
+    if (it.ctx->process == c->process) return mfail(m, RW_ERR_ARG, "process %d added twice", c->process);
+    if (it.ctx->mode != c->mode) return mfail(m, RW_ERR_MODE, "every process must use the same precision mode");
+  }
+  DeviceGuard g(c->device);
+  if (d_wnew && (rc = check_dev_ptr(c, d_wnew, "wnew"))) return mfail(m, rc, "%s", c->err.c_str());
+  if (d_ratio && (rc = check_dev_ptr(c, d_ratio, "ratio"))) return mfail(m, rc, "%s", c->err.c_str());
+  m->items.push_back({c, d_wnew, d_ratio});
+  return RW_OK;
+}
+
+size_t rw_multi_workspace_bytes(const rw_multi* m) { return m ? MULTI_WS_BYTES : 0; }
+
+int rw_multi_reweight_async(rw_multi* m, void* d_ws, size_t ws_bytes) {
+  if (!m) return RW_ERR_NULL;
+  const int n = (int)m->items.size();
+  if (n < 1) return mfail(m, RW_ERR_STATE, "no processes added");
+  if (!d_ws) return mfail(m, RW_ERR_NULL, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(d_ws) % 16) return mfail(m, RW_ERR_ALIGN, "workspace not 16-byte aligned");
+  if (ws_bytes < MULTI_WS_BYTES) return mfail(m, RW_ERR_WORKSPACE, "workspace smaller than rw_multi_workspace_bytes");
+  // the compiled variant whose process list holds exactly these processes
+  const rw::MultiEntry* k = nullptr;
+  int slot[rw::MAX_MULTI] = {};
+  for (const auto& e : multi_registry().kernels) {
+    if (e.mode != m->items[0].ctx->mode || e.n != n) continue;
+    bool all = true;
+    for (int i = 0; i < n && all; ++i) {
+      slot[i] = -1;
+      for (int j = 0; j < n; ++j)
+        if (m->items[j].ctx->process == e.process[i]) slot[i] = j;
+      all = slot[i] >= 0;
+    }
+    if (all) {
+      k = &e;
+      break;
+    }
+  }
+  if (!k) return mfail(m, RW_ERR_MODE, "no multi-process kernel for these %d processes in this mode", n);
+  DeviceGuard g(m->device);
+  const int block = 128;
+  size_t sums = 0;
+  rw::MultiArgs a{};
+  long long tiles = 0;
+  int pool = 0;
+  for (int i = 0; i < n; ++i) {
+    rw_ctx* c = m->items[slot[i]].ctx;
+    const int P = (int)c->pts.size();
+    if (ws_core_bytes(P) > c->ws_bytes)
+      return mfail(m, RW_ERR_WORKSPACE, "workspace of process %d too small", c->process);
+    if (pool + P + 1 > rw::MULTI_POOL)
+      return mfail(m, RW_ERR_ARG, "more than %d parameter points (plus one original each) in one launch",
+                   rw::MULTI_POOL);
+    RwArgs r{};
+    reweight_args(c, r, m->items[slot[i]].wnew, m->items[slot[i]].ratio, nullptr, nullptr);
+    rw::MultiItem& it = a.item[i];
+    it.mom = r.mom;
+    it.w = r.w;
+    it.E = r.E;
+    it.ld = r.ld;
+    it.ldo = 0;
+    it.me0 = nullptr;
+    it.me_pts = nullptr;
+    it.ratio = r.ratio;
+    it.wnew = r.wnew;
+    it.block_part = r.block_part;
+    it.sigma = r.sigma;
+    it.sigma_pair = r.sigma_pair;
+    it.nbad_count = r.nbad_count;
+    it.nbad_out = r.nbad_out;
+    it.P = P;
+    it.pt0 = pool;
+    for (int j = 0; j <= P; ++j) a.pool[pool + j] = r.pt[j];
+    pool += P + 1;
+    const long long gpb = block >> k->lane_bits[i];
+    tiles += (c->E + gpb - 1) / gpb;
+    a.tile_end[i] = tiles;
+    a.sacc_off[i] = (int)sums;
+    sums += (size_t)(block / 32) * (P + 1);
+  }
+  a.n = n;
+  a.ticket = static_cast<unsigned int*>(d_ws);
+  const size_t smem = (size_t)k->smem_per_thread * block + sums * sizeof(double2);
+  const auto key = std::make_pair(k->func, smem);
+  int per_sm = 0;
+  const auto it = m->occ.find(key);
+  if (it == m->occ.end()) {
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) e = cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, block, smem);
+    if (e != cudaSuccess) return mfail(m, RW_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
+    per_sm = std::max(per_sm, 1);
+    m->occ[key] = per_sm;
+  } else {
+    per_sm = it->second;
+  }
+  const int grid =
+      (int)std::max(1LL, std::min<long long>({(long long)GRID_CAP, (long long)per_sm * m->sm_count, tiles}));
+  // the ticket must start at zero (each launch leaves it at zero again)
+  cudaError_t e = cudaMemsetAsync(d_ws, 0, sizeof(unsigned int), m->stream);
+  if (e != cudaSuccess) return mfail(m, RW_ERR_CUDA, "workspace memset: %s", cudaGetErrorString(e));
+  void* args[] = {&a};
+  e = cudaLaunchKernel(k->func, dim3(grid), dim3(block), args, smem, m->stream);
+  if (e != cudaSuccess) return mfail(m, RW_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+  return RW_OK;
+}
+
+int rw_multi_get_results(rw_multi* m, double* h_sigma, double* h_sigma_orig, int64_t* h_n_bad) {
+  if (!m) return RW_ERR_NULL;
+  const int n = (int)m->items.size();
+  if (n < 1) return mfail(m, RW_ERR_STATE, "no processes added");
+  const int P = (int)m->items[0].ctx->pts.size();
+  for (const auto& it : m->items)
+    if ((int)it.ctx->pts.size() != P) return mfail(m, RW_ERR_STATE, "processes have different numbers of points");
+  std::vector<double> s(P + 1, 0.0), c(P + 1, 0.0), ps(P + 1), pc(P + 1);
+  int64_t bad = 0;
+  for (const auto& it : m->items) {
+    int64_t nb = 0;
+    const int rc = rw_get_result_pairs(it.ctx, ps.data(), pc.data(), &nb);
+    if (rc < 0) return mfail(m, rc, "process %d: %s", it.ctx->process, it.ctx->err.c_str());
+    bad += nb;
+    for (int j = 0; j <= P; ++j) {  // TwoSum merge of every process's pairs, in the order they were added
+      const double t = s[j] + ps[j], bp = t - s[j];
+      c[j] += pc[j] + ((s[j] - (t - bp)) + (ps[j] - bp));
+      s[j] = t;
+    }
+  }
+  if (h_sigma)
+    for (int j = 0; j < P; ++j) h_sigma[j] = s[j] + c[j];
+  if (h_sigma_orig) *h_sigma_orig = s[P] + c[P];
+  if (h_n_bad) *h_n_bad = bad;
+  return bad ? RW_WARN_BAD_EVENTS : RW_OK;
+}
+
+}  // extern "C"

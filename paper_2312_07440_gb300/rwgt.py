@@ -97,8 +97,17 @@ def load():
         "rw_lhe_n_events": ([P], i64),
         "rw_lhe_read": ([P, i, i64, i64, P, i64, P, i], i),
         "rw_lhe_write": ([P, ctypes.c_char_p, P, i, i64, P], i),
+        "rw_lhe_classify": ([P, P, i, P, i], i),
+        "rw_lhe_read_list": ([P, i, P, i64, P, i64, P, i], i),
         "rw_reweight_interp": ([P, i, d, P, P, P, P, P, P, P, sz], i),
         "rw_alu_peak": ([i, P, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
+        "rw_multi_create": ([ctypes.POINTER(P), i, P], i),
+        "rw_multi_destroy": ([P], i),
+        "rw_multi_last_error": ([P], ctypes.c_char_p),
+        "rw_multi_add": ([P, P, P, P], i),
+        "rw_multi_workspace_bytes": ([P], sz),
+        "rw_multi_reweight_async": ([P, P, sz], i),
+        "rw_multi_get_results": ([P, P, P, P], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -136,6 +145,64 @@ def _check_buffer(x, name, min_elems=0, dtype="float64"):
         raise ValueError(f"{name}: must be C-contiguous")
     if n < min_elems:
         raise ValueError(f"{name}: {n} elements, need at least {min_elems}")
+
+
+class Multi:
+    """Several prepared contexts (one process each) reweighted by one
+    persistent launch (rw_multi_*).  add() the contexts with their W' and r
+    outputs, then reweight_async(); each context's own sums come from
+    ctx.get_results(), the sample's totals from get_results()."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        self.h = ctypes.c_void_p()
+        self._keep = []
+        rc = self.lib.rw_multi_create(ctypes.byref(self.h), device, stream)
+        if rc:
+            self.h = None
+            raise RwError(rc, "rw_multi_create")
+
+    def _check(self, rc, what):
+        if rc < 0:
+            raise RwError(rc, f"{what}: {self.lib.rw_multi_last_error(self.h).decode()}")
+        return rc
+
+    def add(self, ctx, wnew=None, ratio=None):
+        P, E = ctx.n_points, ctx.n_events
+        _check_buffer(wnew, "wnew", P * E)
+        _check_buffer(ratio, "ratio", P * E)
+        self._keep.append((ctx, wnew, ratio))
+        self._check(self.lib.rw_multi_add(self.h, ctx.h, _ptr(wnew), _ptr(ratio)), "rw_multi_add")
+
+    def workspace_bytes(self) -> int:
+        return int(self.lib.rw_multi_workspace_bytes(self.h))
+
+    def reweight_async(self, workspace, workspace_bytes: int):
+        _check_buffer(workspace, "workspace", workspace_bytes, dtype="uint8")
+        self._check(self.lib.rw_multi_reweight_async(self.h, _ptr(workspace), workspace_bytes),
+                    "rw_multi_reweight_async")
+
+    def get_results(self, n_points: int):
+        sig = np.zeros(n_points)
+        so = ctypes.c_double()
+        nb = ctypes.c_int64()
+        rc = self._check(self.lib.rw_multi_get_results(self.h, sig.ctypes.data, ctypes.byref(so), ctypes.byref(nb)),
+                         "rw_multi_get_results")
+        return sig, so.value, nb.value, rc
+
+    def close(self):
+        if self.h:
+            self.lib.rw_multi_destroy(self.h)
+            self.h = None
+        self._keep = []
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def alu_peak(kind, device=0, stream=None):
@@ -403,6 +470,27 @@ class Lhe:
         w = np.empty(n)
         self._check(self.lib.rw_lhe_read(self.h, PROCESS[process], int(first), n, mom.ctypes.data, n,
                                          w.ctypes.data, int(threads)), "rw_lhe_read")
+        return mom, w
+
+    def classify(self, processes, threads: int = 8) -> np.ndarray:
+        """Process index into ``processes`` (names) of every event, -1 if it
+        matches none: int32 [len(self)]."""
+        ids = np.array([PROCESS[p] for p in processes], dtype=np.int32)
+        out = np.empty(len(self), dtype=np.int32)
+        self._check(self.lib.rw_lhe_classify(self.h, ids.ctypes.data, len(ids), out.ctypes.data, int(threads)),
+                    "rw_lhe_classify")
+        pos = {int(v): i for i, v in enumerate(ids)}
+        return np.array([pos.get(int(v), -1) for v in out], dtype=np.int32)
+
+    def read_list(self, process: str, idx, threads: int = 8):
+        """(mom [N][4][n], w [n]) for the events idx (file indices, any order)."""
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        n = idx.shape[0]
+        N = process_info(process).n_external
+        mom = np.empty((N, 4, n))
+        w = np.empty(n)
+        self._check(self.lib.rw_lhe_read_list(self.h, PROCESS[process], idx.ctypes.data, n, mom.ctypes.data, n,
+                                              w.ctypes.data, int(threads)), "rw_lhe_read_list")
         return mom, w
 
     def write(self, path, wnew, ids):

@@ -25,6 +25,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_2312_07440_gb300 import rwgt  # noqa: E402
+from parity_helpers import full_size_gg_ttgg_ids, per_event_error, recheck_extended, rel  # noqa: E402
 
 DEV = torch.device("cuda", 0)
 _SAMPLES = {}
@@ -36,11 +37,6 @@ def full_sample(wl_name):
         wl = ev.WORKLOADS[wl_name]
         _SAMPLES[wl_name] = ev.generate(wl)
     return _SAMPLES[wl_name]
-
-
-def rel(a, b):
-    a, b = np.asarray(a), np.asarray(b)
-    return np.where(a == b, 0.0, np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
 
 
 def mixed_bound(mode, n_gluons):
@@ -83,13 +79,6 @@ def run_full(proc, wl_name, variant, mode, n_random, seed=0):
          "wnew": wnew[:, ti].cpu().numpy()}
     o = oracle.reweight(proc, ev.param_vector(), pts, np.ascontiguousarray(mom_h[:, :, idx]), w_h[idx])
     return g, o, idx, pts, wnew, w_h, sig, so, nbad, tuning
-
-
-def per_event_error(g, o):
-    e = rel(g["me0"], o["me0"])
-    for k in ("me", "ratio", "wnew"):
-        e = np.maximum(e, rel(g[k], o[k]).max(axis=0))
-    return e
 
 
 def check_sums(wnew, w_h, sig, so, rows):
@@ -141,18 +130,12 @@ def test_gg_ttgg_1m_events(mode):
     assert nbad == 0
     err = per_event_error(g, o)
     if mode == "fp64":
-        # events the CPU witness (tests/test_oracle_extended.py) does not cover
-        # -- the smallest and largest |M|^2 -- and every event beyond a quarter
-        # of the bound are compared with the extended-precision oracle
-        rng = np.random.default_rng(0)
-        covered = np.isin(idx, np.concatenate([rng.integers(0, len(w_h), 600), np.arange(len(w_h) - 40, len(w_h))]))
-        flagged = np.nonzero((err >= 0.25e-12) | ~covered)[0]
-        if flagged.size:  # the FP64 oracle's own rounding: re-evaluate in extended precision
-            mom_h, _ = full_sample("gg_ttgg_1m")
-            x = oracle.reweight("gg_ttgg", ev.param_vector(), pts,
-                                np.ascontiguousarray(mom_h[:, :, idx[flagged]]), w_h[idx[flagged]],
-                                precision="extended")
-            err[flagged] = per_event_error({k: v[..., flagged] for k, v in g.items()}, x)
+        # the smallest and largest |M|^2 are outside the CPU witness's sample
+        # (tests/test_oracle_extended.py): always compared in extended precision
+        covered = np.isin(idx, full_size_gg_ttgg_ids())
+        mom_h, _ = full_sample("gg_ttgg_1m")
+        err = recheck_extended(g, o, err, ("gg_ttgg", pts, mom_h[:, :, idx], w_h[idx]), 1e-12, force=~covered,
+                               set_name="gg_ttgg_full_size", event_ids=idx)
         assert err.max() < 1e-12, f"{err.max():.3e} at event {idx[err.argmax()]}, tuning {tuning}"
     elif mode == "fp32":
         assert err.max() < 1e-5

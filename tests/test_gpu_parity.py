@@ -21,19 +21,13 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_2312_07440_gb300 import rwgt  # noqa: E402
+from parity_helpers import TOL, check_against_oracle, rel  # noqa: E402
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
 DEV = torch.device("cuda", 0)
 
 
 def to_dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
-
-
-def rel(a, b):
-    a, b = np.asarray(a), np.asarray(b)
-    den = np.maximum(np.abs(b), 1e-300)
-    return np.where((a == b), 0.0, np.abs(a - b) / den)
 
 
 _ORACLE_CACHE = {}
@@ -54,47 +48,6 @@ def run_gpu(proc, mode, mom, w, pts, lane_bits=-1, block=0):
     return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
 
 
-def per_event_error(g, o):
-    """Largest relative difference per event over |M|^2, every |M'|^2, r and W'."""
-    e = rel(g["me0"], o["me0"])
-    for k in ("me", "ratio", "wnew"):
-        e = np.maximum(e, rel(g[k], o[k]).max(axis=0))
-    return e
-
-
-def check_against_oracle(g, o, mode, inputs=None):
-    """Per event, relative: |GPU - oracle| < TOL[mode] on |M|^2, |M'|^2, r, W';
-    sigma' within 2 ulp of the exact sum of the GPU's own W' and within TOL of
-    the oracle's exact sum.
-
-    FP64 mode: the FP64 oracle's own rounding error reaches ~6e-13 on a few
-    ill-conditioned events (a top propagator close to its mass shell), so an
-    event whose GPU result differs from it by more than TOL/4 is evaluated
-    again by the extended-precision build of the oracle (the same formulas
-    with a 64-bit significand on x86-64, 113-bit on AArch64) and must be
-    within TOL of that.  tests/test_oracle_extended.py shows on these seeded
-    samples that the FP64 oracle is within 3 TOL/4 of the extended result, so
-    the events within TOL/4 of the FP64 oracle are within TOL of it too.
-    inputs = (process, points, momenta, weights) enables the re-evaluation."""
-    tol = TOL[mode]
-    err = per_event_error(g, o)
-    if mode == "fp64" and inputs is not None:
-        proc, pts, mom, w = inputs
-        flagged = np.nonzero(err >= tol / 4)[0]
-        if flagged.size:
-            x = oracle.reweight(proc, ev.param_vector(), pts, np.ascontiguousarray(mom[:, :, flagged]),
-                                w[flagged], precision="extended")
-            sub = {k: (g[k][..., flagged]) for k in ("me0", "me", "ratio", "wnew")}
-            err[flagged] = per_event_error(sub, x)
-    assert err.max() < tol, f"max per-event error {err.max():.3e} (event {int(err.argmax())})"
-    for j in range(len(g["sigma"])):
-        exact_gpu = math.fsum(g["wnew"][j])
-        assert abs(g["sigma"][j] - exact_gpu) <= 2 * np.spacing(exact_gpu)
-        assert abs(g["sigma"][j] / o["sigma"][j] - 1) < tol
-    assert abs(g["sigma_orig"] - o["sigma_orig"]) <= 2 * np.spacing(o["sigma_orig"])
-    assert g["n_bad"] == o["n_bad"]
-
-
 # --------------------------------------------------------------------------
 # g g -> t tbar (the 1M-event workload's process), every launch variant
 # --------------------------------------------------------------------------
@@ -104,7 +57,7 @@ def test_gg_tt_parity(mode, lane_bits):
     pts = ev.reweight_points("gg_tt_1m")
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 5003, pts)  # several blocks + a ragged tail
     g = run_gpu("gg_tt", mode, mom, w, pts, lane_bits=lane_bits)
-    check_against_oracle(g, o, mode, ("gg_tt", pts, mom, w))
+    check_against_oracle(g, o, mode, ("gg_tt", pts, mom, w), "gg_tt_5003")
 
 
 @pytest.mark.parametrize("block", [32, 64, 256])
@@ -112,7 +65,7 @@ def test_gg_tt_block_sizes(block):
     pts = ev.reweight_points("gg_tt_1m")
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 5003, pts)
     g = run_gpu("gg_tt", "fp64", mom, w, pts, block=block)
-    check_against_oracle(g, o, "fp64", ("gg_tt", pts, mom, w))
+    check_against_oracle(g, o, "fp64", ("gg_tt", pts, mom, w), "gg_tt_5003")
 
 
 def test_gg_tt_several_points_and_alpha_s_scaling():
@@ -120,7 +73,7 @@ def test_gg_tt_several_points_and_alpha_s_scaling():
                     ev.param_vector(m_t=175.0, alpha_s=0.120), ev.param_vector(m_t=160.0)])
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 777, pts)
     g = run_gpu("gg_tt", "fp64", mom, w, pts)
-    check_against_oracle(g, o, "fp64", ("gg_tt", pts, mom, w))
+    check_against_oracle(g, o, "fp64", ("gg_tt", pts, mom, w), "gg_tt_777_five")
     assert np.abs(g["ratio"][0] / (0.120 / 0.118) ** 2 - 1).max() < 1e-14   # P9
     assert np.all(g["ratio"][2] == 1.0) and np.all(g["wnew"][2] == w)       # P8 (bitwise)
 
@@ -131,7 +84,7 @@ def test_ee_mumu_parity_full_sample(mode):
     mom, w, o = oracle_run("ee_mumu", "ee_mumu_4k", 4096, pts)
     for lb in ([0, 2, 4] if mode == "fp64" else [0]):
         g = run_gpu("ee_mumu", mode, mom, w, pts, lane_bits=lb)
-        check_against_oracle(g, o, mode, ("ee_mumu", pts, mom, w))
+        check_against_oracle(g, o, mode, ("ee_mumu", pts, mom, w), "ee_mumu_4096")
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
@@ -140,7 +93,7 @@ def test_gg_ttg_parity(mode, lane_bits):
     pts = ev.reweight_points("gg_ttg_4m", "mt")[::21]  # kappa = 0.8, 0.933, 1.067, 1.2 (m_t = kappa 173)
     mom, w, o = oracle_run("gg_ttg", "gg_ttg_4m", 611, pts)
     g = run_gpu("gg_ttg", mode, mom, w, pts, lane_bits=lane_bits)
-    check_against_oracle(g, o, mode, ("gg_ttg", pts, mom, w))
+    check_against_oracle(g, o, mode, ("gg_ttg", pts, mom, w), "gg_ttg_611")
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
@@ -149,7 +102,7 @@ def test_gg_ttgg_parity(mode):
     mom, w, o = oracle_run("gg_ttgg", "gg_ttgg_1m", 197, pts)
     for lb in (1, 2, 3):
         g = run_gpu("gg_ttgg", mode, mom, w, pts, lane_bits=lb)
-        check_against_oracle(g, o, mode, ("gg_ttgg", pts, mom, w))
+        check_against_oracle(g, o, mode, ("gg_ttgg", pts, mom, w), "gg_ttgg_197")
 
 
 # --------------------------------------------------------------------------
@@ -161,7 +114,7 @@ def test_ee_5a_parity(mode, lane_bits):
     pts = ev.reweight_points("ee_5a_1m")[:3]
     mom, w, o = oracle_run("ee_5a", "ee_5a_1m", 517, pts)  # several blocks + a ragged tail
     g = run_gpu("ee_5a", mode, mom, w, pts, lane_bits=lane_bits)
-    check_against_oracle(g, o, mode, ("ee_5a", pts, mom, w))
+    check_against_oracle(g, o, mode, ("ee_5a", pts, mom, w), "ee_5a_517")
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
@@ -196,7 +149,7 @@ def test_tiny_batches(n):
     pts = ev.reweight_points("gg_tt_1m")
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", n, pts)
     g = run_gpu("gg_tt", "fp64", mom, w, pts)
-    check_against_oracle(g, o, "fp64", ("gg_tt", pts, mom, w))
+    check_against_oracle(g, o, "fp64", ("gg_tt", pts, mom, w), "gg_tt_5003")
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp32"])
@@ -209,7 +162,7 @@ def test_maximum_number_of_points(mode):
     assert pts.shape[0] == 256
     mom, w, o = oracle_run("gg_tt", "gg_tt_1m", 77, pts)
     g = run_gpu("gg_tt", mode, mom, w, pts)
-    check_against_oracle(g, o, mode, ("gg_tt", pts, mom, w))
+    check_against_oracle(g, o, mode, ("gg_tt", pts, mom, w), "gg_tt_77_256")
 
 
 def test_bad_events_are_counted_and_excluded():

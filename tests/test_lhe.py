@@ -282,3 +282,43 @@ def test_many_comments_index_in_linear_time(tmp_path):
         m2, w2 = f.read("gg_tt")
     assert time.perf_counter() - t0 < 2.0  # ~10 ms linear, minutes quadratic
     assert np.array_equal(w2, w)
+
+
+def mixed_file(tmp_path, n_born=40, n_real=25):
+    """An event file whose events come from two processes, interleaved as in
+    an NLO sample (g g -> t tbar Born-like events and g g -> t tbar g
+    real-emission events)."""
+    mb, wb = ev.generate(ev.WORKLOADS["gg_tt_1m"], n_born)
+    mr, wr = ev.generate(ev.WORKLOADS["gg_ttg_4m"], n_real)
+    write_lhe(tmp_path / "b.lhe", "gg_tt", mb, wb)
+    write_lhe(tmp_path / "r.lhe", "gg_ttg", mr, wr)
+    tb, tr = (tmp_path / "b.lhe").read_text(), (tmp_path / "r.lhe").read_text()
+    blocks_b = re.findall(r"<event>.*?</event>", tb, flags=re.S)
+    blocks_r = re.findall(r"<event>.*?</event>", tr, flags=re.S)
+    rng = np.random.default_rng(3)
+    kinds = rng.permutation([0] * n_born + [1] * n_real)
+    it = {0: iter(blocks_b), 1: iter(blocks_r)}
+    body = "\n".join(next(it[k]) for k in kinds)
+    head = tb[:tb.index("<event>")]
+    (tmp_path / "mixed.lhe").write_text(head + body + "\n</LesHouchesEvents>\n")
+    return tmp_path / "mixed.lhe", kinds, (mb, wb), (mr, wr)
+
+
+def test_mixed_process_file_is_classified_and_read_by_lists(tmp_path):
+    path, kinds, (mb, wb), (mr, wr) = mixed_file(tmp_path)
+    with rwgt.Lhe(path) as f:
+        lab = f.classify(["gg_tt", "gg_ttg"])
+        assert np.array_equal(lab, kinds)
+        assert np.all(f.classify(["ee_5a"]) == -1)
+        m1, w1 = f.read_list("gg_tt", np.nonzero(lab == 0)[0])
+        m2, w2 = f.read_list("gg_ttg", np.nonzero(lab == 1)[0])
+        # reversed order of the list: the columns follow the list
+        m3, w3 = f.read_list("gg_ttg", np.nonzero(lab == 1)[0][::-1])
+        with pytest.raises(rwgt.RwError, match="outside"):
+            f.read_list("gg_tt", [len(f)])
+        with pytest.raises(rwgt.RwError, match="extra external particles"):
+            f.read_list("gg_tt", np.nonzero(lab == 1)[0][:1])
+    assert np.array_equal(w1, wb) and np.array_equal(w2, wr) and np.array_equal(w3, wr[::-1])
+    # the lab-frame boost back to the centre-of-mass frame: the same momenta to rounding
+    assert np.allclose(m1, mb, rtol=0, atol=1e-9) and np.allclose(m2, mr, rtol=0, atol=1e-9)
+    assert np.array_equal(m3, m2[:, :, ::-1])
