@@ -265,6 +265,24 @@ int rw_mlp_gradient(rw_mlp* m, const float* d_x, const float* d_y, int64_t n, fl
 int rw_mlp_train(rw_mlp* m, const float* d_x, const float* d_y, int64_t n, int batch, int64_t n_steps, float lr,
                  float tau, float lam, uint64_t seed);
 
+/* Forward GEMMs of the hidden layers (training and inference): kind 0 (the
+   default) runs them on the 5th-generation tensor cores -- tcgen05.mma fed by
+   TMA, FP32 accumulators in tensor memory, bias + SiLU fused into the
+   epilogue and, in rw_mlp_forward, the output layer fused into the last
+   hidden layer -- whenever hidden is a multiple of 64 and at most 256;
+   kind 1 uses the mma.sync kernel for every layer.  Both compute the same
+   products of the same BF16 operands in FP32. */
+int rw_mlp_set_gemm(rw_mlp* m, int kind);
+/* Synchronise the model's stream and report a tensor-core pipeline wait that
+   gave up (RW_ERR_CUDA; the kernel then stops early and its results are
+   invalid), else RW_OK. */
+int rw_mlp_status(rw_mlp* m);
+/* One hidden layer l (1 <= l < n_layers) on the current GEMM path, for tests
+   and benchmarks: d_z [n][hidden] (FP32) = d_h_in [n][hidden] (BF16) W_l + b_l,
+   d_h_out [n][hidden] (BF16) = SiLU(d_z) rounded; device buffers, 16-byte
+   aligned; asynchronous on the model's stream. */
+int rw_mlp_hidden_layer(rw_mlp* m, int layer, const void* d_h_in, int64_t n, float* d_z, void* d_h_out);
+
 /* Surrogate features of the attached events for every point p, row p*E + e:
    x = (p_i^mu / p_scale for all N particles after the rotation about the beam
    axis that puts the top's p_T along +x, (kappa_p - 1)/k_scale, then -- when

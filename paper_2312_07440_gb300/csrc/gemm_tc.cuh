@@ -1,0 +1,344 @@
+// Blackwell tensor-core GEMM for the surrogate MLP's hidden layers:
+//   Z = A W + b,  H = bf16(SiLU(Z))   (A: BF16 activations [M][K], W: [K][N])
+// optionally followed by a fused FP32 output head out = H W_out + b_out
+// (N -> 2) for inference, so the last hidden layer never leaves the chip.
+//
+// One CTA per SM walks 128-row tiles of A (persistent).  Roles:
+//   warp 0    one thread issues TMA loads (cp.async.bulk.tensor, 128-byte
+//             swizzle): the whole transposed weight matrix W^T [N][K] once
+//             (resident in shared memory), then the A tiles through a ring of
+//             STAGES k-blocks of 64 columns;
+//   warp 1    owns the tensor memory (two accumulators of N FP32 columns x
+//             128 lanes); one thread issues tcgen05.mma (kind::f16, BF16 x
+//             BF16 -> FP32, M = 128, N, K = 16) and commits each k-block's
+//             MMAs to that A stage's "empty" barrier and each tile to its
+//             accumulator's "full" barrier;
+//   warps 2-5 the epilogue: tcgen05.ld 32 columns at a time from the lanes
+//             their warp may read (warp w reads lanes 32 (w % 4) ...), bias,
+//             SiLU, BF16/FP32 stores or the fused head, then free the
+//             accumulator, which the MMA thread reuses two tiles later.
+// Every mbarrier wait gives up after ~2^31 clock cycles (~1 s): it sets the
+// error flag, every role stops, the MMA thread drains its outstanding MMAs
+// (bounded), the TMA thread waits (bounded) for its loads in flight, and the
+// tensor memory is freed before the kernel returns.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tcg {
+
+constexpr int BM = 128;      // rows per tile = tensor-memory lanes
+constexpr int BK = 64;       // k per TMA box and swizzle row (64 BF16 = 128 bytes)
+constexpr int STAGES = 4;    // A ring depth (k-blocks)
+constexpr int MAX_N = 256;   // N <= 256 (one MMA covers the whole width)
+constexpr int MAX_KB = 4;    // K <= 256
+constexpr int THREADS = 192;
+constexpr int UMMA_K = 16;   // k of one kind::f16 MMA
+constexpr long long WAIT_CYCLES = 1ll << 31;
+
+// dynamic shared memory: 1024-byte alignment slack, W^T, the A ring, barriers
+constexpr size_t SMEM_B = (size_t)MAX_KB * MAX_N * 128;
+constexpr size_t SMEM_A = (size_t)STAGES * BM * 128;
+constexpr size_t SMEM_BYTES = 1024 + SMEM_B + SMEM_A + 256;
+
+struct Epi {
+  const float* bias;       // [N]
+  float* Z;                // [M][N] pre-activation (FP32), or null
+  unsigned short* H;       // [M][N] SiLU(Z) as BF16, or null
+  const float* w_out;      // fused output head [N][2] (FP32), or null
+  const float* b_out;      // [2]
+  float* out;              // [M][2]
+  int* err;                // set to a nonzero code when a wait gives up
+  int M, N, K;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// wait for the phase of the given parity; false (and the error flag set)
+// when it does not complete within WAIT_CYCLES
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, volatile int* abort) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      atomicCAS(err, 0, code);
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// shared-memory matrix descriptor of a K-major operand tile written by TMA
+// with 128-byte swizzle: 8-row x 128-byte swizzle atoms stacked along the
+// rows 1024 bytes apart (stride byte offset), leading byte offset unused
+// (encoded 1), descriptor version 1, layout 2 = 128-byte swizzle
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N and M
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// SiLU as the other kernels of the surrogate compute it: z sigma(z)
+__device__ __forceinline__ float silu_f(float z) { return z * (1.0f / (1.0f + __expf(-z))); }
+
+__device__ __forceinline__ unsigned short bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+__global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
+                                                         const __grid_constant__ CUtensorMap tmB, const Epi e) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sB = base;
+  unsigned char* sA = base + SMEM_B;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + SMEM_A);
+  // barrier slots: full_a[STAGES], empty_a[STAGES], full_b, acc_full[2], acc_empty[2], drain
+  const uint32_t b_full_a = smem_u32(bars), b_empty_a = smem_u32(bars + STAGES), b_full_b = smem_u32(bars + 2 * STAGES);
+  const uint32_t b_acc_full = smem_u32(bars + 2 * STAGES + 1), b_acc_empty = smem_u32(bars + 2 * STAGES + 3);
+  const uint32_t b_drain = smem_u32(bars + 2 * STAGES + 5);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int N = e.N, KB = e.K / BK;
+  const int tiles = (e.M + BM - 1) / BM;
+  const uint32_t tmem_cols = 2 * MAX_N;  // two accumulators of up to 256 columns
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(b_full_a + 8 * s, 1);
+      mbar_init(b_empty_a + 8 * s, 1);
+    }
+    mbar_init(b_full_b, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(b_acc_full + 8 * i, 1);
+      mbar_init(b_acc_empty + 8 * i, 4);  // one arrival per epilogue warp
+    }
+    mbar_init(b_drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  volatile int* abort = &abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // the transposed weights, once: KB boxes of 64 (k) x N (n)
+      mbar_expect_tx(b_full_b, (uint32_t)(KB * N * 128));
+      for (int kb = 0; kb < KB; ++kb) tma_load_2d(smem_u32(sB + (size_t)kb * N * 128), &tmB, kb * BK, 0, b_full_b);
+      int stage = 0;
+      uint32_t phase = 0;
+      int issued[STAGES] = {};  // loads issued per stage (for the drain on abort)
+      int uses[STAGES] = {};
+      for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        for (int kb = 0; kb < KB; ++kb) {
+          if (!mbar_wait(b_empty_a + 8 * stage, phase ^ 1, e.err, 1, abort)) goto tma_done;
+          mbar_expect_tx(b_full_a + 8 * stage, BM * 128);
+          tma_load_2d(smem_u32(sA + (size_t)stage * BM * 128), &tmA, kb * BK, t * BM, b_full_a + 8 * stage);
+          ++issued[stage];
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+    tma_done:
+      if (*abort) {
+        // loads still in flight land in shared memory: wait for them (bounded)
+        const long long t0 = clock64();
+        for (int s = 0; s < STAGES; ++s) {
+          uses[s] = issued[s];
+          if (uses[s] == 0) continue;
+          const uint32_t par = (uint32_t)((uses[s] - 1) & 1);
+          while (!mbar_test(b_full_a + 8 * s, par) && clock64() - t0 < WAIT_CYCLES) {
+          }
+        }
+        while (!mbar_test(b_full_b, 0) && clock64() - t0 < WAIT_CYCLES) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(BM, N);
+      bool ok = mbar_wait(b_full_b, 0, e.err, 2, abort);
+      int stage = 0, acc = 0;
+      uint32_t phase = 0, acc_phase = 0;
+      for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
+        if (!(ok = mbar_wait(b_acc_empty + 8 * acc, acc_phase ^ 1, e.err, 3, abort))) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * MAX_N);
+        for (int kb = 0; kb < KB; ++kb) {
+          if (!(ok = mbar_wait(b_full_a + 8 * stage, phase, e.err, 4, abort))) break;
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + (size_t)stage * BM * 128);
+          const uint32_t b0 = smem_u32(sB + (size_t)kb * N * 128);
+#pragma unroll
+          for (int k = 0; k < BK / UMMA_K; ++k)
+            umma_bf16(d, sw128_desc(a0 + 32 * k), sw128_desc(b0 + 32 * k), idesc, (kb | k) != 0);
+          umma_commit(b_empty_a + 8 * stage);  // the stage is free once these MMAs have read it
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        umma_commit(b_acc_full + 8 * acc);
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
+      }
+      // every MMA issued so far has completed once this commit arrives
+      umma_commit(b_drain);
+      const long long t0 = clock64();
+      while (!mbar_test(b_drain, 0) && clock64() - t0 < WAIT_CYCLES) {
+      }
+    }
+  } else {
+    const int q = warp & 3;  // the lane quarter this warp may read
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      if (!mbar_wait(b_acc_full + 8 * acc, acc_phase, e.err, 5, abort)) break;
+      tc_fence_after();
+      const long long row = (long long)t * BM + q * 32 + lane;
+      const bool live = row < e.M;
+      float h0 = 0.0f, h1 = 0.0f;
+      for (int c0 = 0; c0 < N; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + (uint32_t)(acc * MAX_N + c0) + ((uint32_t)(q * 32) << 16), v);
+        if (!live) continue;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += __ldg(e.bias + c0 + j);
+        if (e.Z) {
+          float4* zp = reinterpret_cast<float4*>(e.Z + row * N + c0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) zp[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = silu_f(v[j]);
+        if (e.H) {
+          uint4* hp = reinterpret_cast<uint4*>(e.H + row * N + c0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              w[i] = (uint32_t)bf16_bits(v[8 * j + 2 * i]) | ((uint32_t)bf16_bits(v[8 * j + 2 * i + 1]) << 16);
+            hp[j] = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
+        if (e.w_out) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            h0 = fmaf(v[j], __ldg(e.w_out + 2 * (c0 + j)), h0);
+            h1 = fmaf(v[j], __ldg(e.w_out + 2 * (c0 + j) + 1), h1);
+          }
+        }
+      }
+      if (live && e.w_out) *reinterpret_cast<float2*>(e.out + 2 * row) = make_float2(h0 + e.b_out[0], h1 + e.b_out[1]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_acc_empty + 8 * acc);
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  }
+}
+
+}  // namespace tcg

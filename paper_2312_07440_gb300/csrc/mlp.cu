@@ -1,11 +1,17 @@
 // Learned surrogate for log r = log(|M'|^2/|M|^2): a multilayer perceptron
 // n_in -> [hidden, SiLU] x n_layers -> 2 (mu = predicted log r, s = predicted
 // log of its error).  Hidden layers: BF16 weights and activations, FP32
-// accumulation on the tensor cores (mma.sync m16n8k16); the first layer (from
-// the unrounded FP32 features) and the output layer run in FP32 (about 4 % of
-// the flops); FP32 master weights with Adam.  Every step
-// of training and inference runs in the kernels of this file:
-//   k_gemm<EPI>    C = A B with strided (optionally transposed) BF16 operands,
+// accumulation on the tensor cores; the first layer (from the unrounded FP32
+// features) and the output layer run in FP32 (about 4 % of the flops); FP32
+// master weights with Adam.  Every step of training and inference runs in the
+// kernels of this file:
+//   k_gemm_tc      (gemm_tc.cuh) the hidden layers' forward GEMMs on the
+//                  5th-generation tensor cores (tcgen05.mma, TMA-fed, FP32
+//                  accumulators in tensor memory), bias + SiLU fused, and for
+//                  inference the output layer fused into the last one
+//   k_gemm<EPI>    C = A B with strided (optionally transposed) BF16 operands
+//                  on mma.sync (the backward GEMMs; the forward when the
+//                  layer shape is outside k_gemm_tc's),
 //                  fused epilogues: bias + SiLU (forward), bias (output layer),
 //                  x SiLU'(z) (backward data), FP32 store (weight gradients)
 //   k_colsum       bias gradients
@@ -24,6 +30,7 @@
 #include <vector>
 
 #include "../../include/rwgt.h"
+#include "gemm_tc.cuh"
 
 namespace {
 
@@ -247,6 +254,15 @@ __global__ void k_to_bf16(const float* __restrict__ x, bf16* __restrict__ y, lon
   if (i < n) y[i] = f2bf(x[i]);
 }
 
+// BF16 transpose of a K x N FP32 weight matrix: Wt[n][k] = bf16(W[k][n])
+// (the tensor-core GEMM reads the weights K-major)
+__global__ void k_transpose_bf16(const float* __restrict__ W, int K, int N, bf16* __restrict__ Wt) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)K * N) return;
+  const int n = (int)(t / K), k = (int)(t % K);
+  Wt[t] = f2bf(W[(long long)k * N + n]);
+}
+
 // rows idx[b] of X [*][nin] (FP32) -> Xf [B][nin] (FP32) and Xb (BF16), y[idx[b]] -> yb[b]
 __global__ void k_gather_rows(const float* __restrict__ X, const float* __restrict__ y, const int64_t* __restrict__ idx,
                               int B, int nin, float* __restrict__ Xf, bf16* __restrict__ Xb, float* __restrict__ yb) {
@@ -299,6 +315,12 @@ struct rw_mlp {
   float* loss = nullptr;              // [max_batch]
   float* yb = nullptr;
   int64_t* idx = nullptr;
+  // tensor-core forward: transposed BF16 hidden weights [l][N][K] (layer l at
+  // (l - 1) hidden^2), its error flag, and the GEMM choice
+  bf16* wt = nullptr;
+  int* tc_err = nullptr;
+  int gemm = 0;  // 0: tcgen05 where the shape allows, 1: mma.sync everywhere
+  int sm_count = 0;
   std::string err;
 };
 
@@ -307,6 +329,87 @@ namespace {
 int mlp_fail(rw_mlp* m, int code, const char* msg) {
   if (m) m->err = msg;
   return code;
+}
+
+// ---- tensor-core forward (gemm_tc.cuh) ------------------------------------
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiled>(f);
+  }();
+  return fn;
+}
+
+// a 2-D BF16 row-major matrix [rows][cols] as a TMA map with boxes of
+// 64 columns (128 bytes, 128-byte swizzle) x box_rows rows
+bool bf16_map(CUtensorMap* map, const bf16* ptr, long long rows, int cols, int box_rows) {
+  const EncodeTiled enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(bf16)};
+  const cuuint32_t box[2] = {(cuuint32_t)tcg::BK, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// hidden layers on the tensor cores: width a multiple of 64, at most 256
+bool tc_usable(const rw_mlp* m) {
+  return m->gemm == 0 && m->wt && m->hidden % tcg::BK == 0 && m->hidden <= tcg::MAX_N && encode_tiled();
+}
+
+// hidden layer l (1 <= l < n_layers) of B rows: A = bf16 activations [B][hidden]
+int launch_gemm_tc(rw_mlp* m, int l, const bf16* A, int B, tcg::Epi e) {
+  const int H = m->hidden;
+  CUtensorMap ta, tb;
+  if (!bf16_map(&ta, A, B, H, tcg::BM) || !bf16_map(&tb, m->wt + (size_t)(l - 1) * H * H, H, H, H))
+    return mlp_fail(m, RW_ERR_CUDA, "tensor map encoding");
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(tcg::k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tcg::SMEM_BYTES) !=
+        cudaSuccess)
+      return mlp_fail(m, RW_ERR_CUDA, "tensor-core GEMM shared memory attribute");
+    attr = true;
+  }
+  e.bias = m->p + m->b_off[l];
+  e.err = m->tc_err;
+  e.M = B;
+  e.N = H;
+  e.K = H;
+  const int tiles = (B + tcg::BM - 1) / tcg::BM;
+  const int grid = std::max(1, std::min(tiles, m->sm_count));
+  tcg::k_gemm_tc<<<grid, tcg::THREADS, tcg::SMEM_BYTES, m->stream>>>(ta, tb, e);
+  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "tensor-core GEMM launch");
+}
+
+// transposed BF16 copies of the hidden weights (after any change of p)
+int refresh_wt(rw_mlp* m) {
+  if (!m->wt) return RW_OK;
+  const int H = m->hidden;
+  for (int l = 1; l < m->n_layers; ++l)
+    k_transpose_bf16<<<(unsigned)(((long long)H * H + 255) / 256), 256, 0, m->stream>>>(
+        m->p + m->w_off[l], H, H, m->wt + (size_t)(l - 1) * H * H);
+  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "weight transpose");
+}
+
+// the tensor-core kernels' error flag (a wait that gave up); synchronises
+int tc_status(rw_mlp* m) {
+  if (!m->tc_err) return RW_OK;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream) != cudaSuccess ||
+      cudaStreamSynchronize(m->stream) != cudaSuccess)
+    return mlp_fail(m, RW_ERR_CUDA, "status copy");
+  if (h) return mlp_fail(m, RW_ERR_CUDA, "tensor-core GEMM: a pipeline wait timed out");
+  return RW_OK;
 }
 
 int launch_gemm(rw_mlp* m, int epi, GemmArgs a) {
@@ -321,12 +424,31 @@ int launch_gemm(rw_mlp* m, int epi, GemmArgs a) {
 }
 
 // Forward for B <= max_batch rows of FP32 features xf (device); output in
-// m->out.  First and last layers in FP32, hidden layers BF16 on the tensor cores.
-int forward_batch(rw_mlp* m, const float* xf, int B) {
+// m->out.  First and last layers in FP32, hidden layers BF16 on the tensor
+// cores.  infer: only the output is needed, so the last hidden layer's
+// tensor-core epilogue computes the output layer itself and writes neither
+// its pre-activation nor its activation.
+int forward_batch(rw_mlp* m, const float* xf, int B, bool infer = false) {
   const int L = m->n_layers;
   k_dense_in<<<(unsigned)(((long long)B * m->hidden + 255) / 256), 256, 0, m->stream>>>(
       xf, B, m->n_in, m->p + m->w_off[0], m->p + m->b_off[0], m->hidden, m->Z[0], m->H[0]);
+  const bool tc = tc_usable(m);
   for (int l = 1; l < L; ++l) {
+    if (tc) {
+      tcg::Epi e{};
+      if (infer && l == L - 1) {
+        e.w_out = m->p + m->w_off[L];
+        e.b_out = m->p + m->b_off[L];
+        e.out = m->out;
+      } else {
+        e.Z = m->Z[l];
+        e.H = m->H[l];
+      }
+      const int rc = launch_gemm_tc(m, l, m->H[l - 1], B, e);
+      if (rc) return rc;
+      if (infer && l == L - 1) return RW_OK;
+      continue;
+    }
     GemmArgs a{};
     a.A = m->H[l - 1];
     a.sam = m->hidden;
@@ -478,9 +600,13 @@ int rw_mlp_create(rw_mlp** out, int device, void* stream, int n_in, int hidden, 
   if (ok) ok = cudaMemcpy(m->p, hp.data(), off * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemset(m->m1, 0, off * sizeof(float)) == cudaSuccess &&
                cudaMemset(m->m2, 0, off * sizeof(float)) == cudaSuccess;
+  if (ok) ok = cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
+               dalloc(&m->tc_err, 1) && cudaMemset(m->tc_err, 0, sizeof(int)) == cudaSuccess;
+  if (ok && n_layers >= 2 && hidden % tcg::BK == 0 && hidden <= tcg::MAX_N)
+    ok = dalloc(&m->wt, (size_t)(n_layers - 1) * hidden * hidden);
   if (ok) {
-    k_to_bf16<<<(unsigned)((off + 255) / 256), 256>>>(m->p, m->pb, off);
-    ok = cudaDeviceSynchronize() == cudaSuccess;
+    k_to_bf16<<<(unsigned)((off + 255) / 256), 256, 0, m->stream>>>(m->p, m->pb, off);
+    ok = refresh_wt(m) == RW_OK && cudaStreamSynchronize(m->stream) == cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
@@ -497,7 +623,7 @@ int rw_mlp_destroy(rw_mlp* m) {
   for (void* q : {(void*)m->p, (void*)m->g, (void*)m->m1, (void*)m->m2, (void*)m->pb, (void*)m->X, (void*)m->Xf,
                   (void*)m->out,
                   (void*)m->dout_f, (void*)m->dout_b, (void*)m->dA, (void*)m->dB, (void*)m->loss, (void*)m->yb,
-                  (void*)m->idx})
+                  (void*)m->idx, (void*)m->wt, (void*)m->tc_err})
     if (q) cudaFree(q);
   for (auto* h : m->H) cudaFree(h);
   for (auto* z : m->Z) cudaFree(z);
@@ -542,7 +668,8 @@ int rw_mlp_set_state(rw_mlp* m, const float* h_params, const float* h_m1, const 
   if (!ok) return mlp_fail(m, RW_ERR_CUDA, "copy");
   k_to_bf16<<<(unsigned)((m->n_params + 255) / 256), 256, 0, m->stream>>>(m->p, m->pb, m->n_params);
   m->step = step < 0 ? 0 : step;
-  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "launch");
+  if (cudaGetLastError() != cudaSuccess) return mlp_fail(m, RW_ERR_CUDA, "launch");
+  return refresh_wt(m);
 }
 
 // out [n][2] = MLP(x [n][n_in] FP32), processed in chunks of max_batch rows
@@ -553,7 +680,7 @@ int rw_mlp_forward(rw_mlp* m, const float* d_x, int64_t n, float* d_out) {
   cudaSetDevice(m->device);
   for (int64_t s = 0; s < n; s += m->max_batch) {
     const int B = (int)std::min<int64_t>(m->max_batch, n - s);
-    int rc = forward_batch(m, d_x + s * m->n_in, B);
+    int rc = forward_batch(m, d_x + s * m->n_in, B, true);
     if (rc) return rc;
     if (cudaMemcpyAsync(d_out + 2 * s, m->out, (size_t)B * 2 * sizeof(float), cudaMemcpyDeviceToDevice,
                         m->stream) != cudaSuccess)
@@ -580,6 +707,7 @@ int rw_mlp_gradient(rw_mlp* m, const float* d_x, const float* d_y, int64_t n, fl
   rc = backward_batch(m, B);
   if (rc) return rc;
   if (cudaStreamSynchronize(m->stream) != cudaSuccess) return mlp_fail(m, RW_ERR_CUDA, "sync");
+  if ((rc = tc_status(m))) return rc;
   if (h_grad && cudaMemcpy(h_grad, m->g, m->n_params * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
     return mlp_fail(m, RW_ERR_CUDA, "copy");
   if (h_loss) {
@@ -618,8 +746,60 @@ int rw_mlp_train(rw_mlp* m, const float* d_x, const float* d_y, int64_t n, int b
     const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
     k_adam<<<(unsigned)((m->n_params + 255) / 256), 256, 0, m->stream>>>(m->p, m->g, m->m1, m->m2, m->pb,
                                                                          m->n_params, lr, b1, b2, eps, c1, c2);
+    if ((rc = refresh_wt(m))) return rc;
   }
   return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "train launch");
+}
+
+int rw_mlp_set_gemm(rw_mlp* m, int kind) {
+  if (!m) return RW_ERR_NULL;
+  if (kind != 0 && kind != 1) return mlp_fail(m, RW_ERR_ARG, "kind must be 0 or 1");
+  m->gemm = kind;
+  return RW_OK;
+}
+
+int rw_mlp_status(rw_mlp* m) {
+  if (!m) return RW_ERR_NULL;
+  cudaSetDevice(m->device);
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return mlp_fail(m, RW_ERR_CUDA, "sync");
+  return tc_status(m);
+}
+
+int rw_mlp_hidden_layer(rw_mlp* m, int layer, const void* d_h_in, int64_t n, float* d_z, void* d_h_out) {
+  if (!m) return RW_ERR_NULL;
+  if (!d_h_in || !d_z || !d_h_out) return mlp_fail(m, RW_ERR_NULL, "NULL buffer");
+  if (layer < 1 || layer >= m->n_layers) return mlp_fail(m, RW_ERR_ARG, "layer must be a hidden layer (1..n_layers-1)");
+  if (n <= 0 || n > (int64_t(1) << 30)) return mlp_fail(m, RW_ERR_ARG, "bad n");
+  if (reinterpret_cast<uintptr_t>(d_h_in) % 16 || reinterpret_cast<uintptr_t>(d_z) % 16 ||
+      reinterpret_cast<uintptr_t>(d_h_out) % 16)
+    return mlp_fail(m, RW_ERR_ALIGN, "buffers must be 16-byte aligned");
+  cudaSetDevice(m->device);
+  const bf16* A = static_cast<const bf16*>(d_h_in);
+  bf16* Hout = static_cast<bf16*>(d_h_out);
+  if (tc_usable(m)) {
+    tcg::Epi e{};
+    e.Z = d_z;
+    e.H = Hout;
+    return launch_gemm_tc(m, layer, A, (int)n, e);
+  }
+  for (int64_t s = 0; s < n; s += 65535LL * BM) {  // the mma.sync grid's row limit
+    GemmArgs a{};
+    a.A = A + s * m->hidden;
+    a.sam = m->hidden;
+    a.sak = 1;
+    a.B = m->pb + m->w_off[layer];
+    a.sbk = m->dout[layer];
+    a.sbn = 1;
+    a.M = (int)std::min<int64_t>(n - s, 65535LL * BM);
+    a.N = m->dout[layer];
+    a.K = m->din[layer];
+    a.bias = m->p + m->b_off[layer];
+    a.Zf = d_z + s * m->hidden;
+    a.H = Hout + s * m->hidden;
+    const int rc = launch_gemm(m, EPI_FWD_SILU, a);
+    if (rc) return rc;
+  }
+  return RW_OK;
 }
 
 }  // extern "C"

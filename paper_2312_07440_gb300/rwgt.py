@@ -81,6 +81,9 @@ def load():
         "rw_mlp_forward": ([P, P, i64, P], i),
         "rw_mlp_gradient": ([P, P, P, i64, ctypes.c_float, ctypes.c_float, P, ctypes.POINTER(ctypes.c_float)], i),
         "rw_mlp_train": ([P, P, P, i64, i, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_uint64], i),
+        "rw_mlp_set_gemm": ([P, i], i),
+        "rw_mlp_status": ([P], i),
+        "rw_mlp_hidden_layer": ([P, i, P, i64, P, P], i),
         "rw_surrogate_features": ([P, i, d, d, P, P, P], i),
         "rw_surrogate_workspace_bytes": ([P, i], sz),
         "rw_surrogate_reweight": ([P, P, d, d, d, P, P, P, P, P, sz], i),
@@ -589,6 +592,25 @@ class Mlp:
         _check_buffer(y, "y", n, "float32")
         self._check(self.lib.rw_mlp_train(self.h, _ptr(x), _ptr(y), int(x.shape[0]), int(batch), int(n_steps), lr,
                                           tau, lam, int(seed)), "rw_mlp_train")
+
+    def set_gemm(self, kind: str):
+        """Forward GEMMs of the hidden layers: "tcgen05" (5th-generation tensor
+        cores, where the width allows) or "mma_sync" (the legacy path)."""
+        self._check(self.lib.rw_mlp_set_gemm(self.h, {"tcgen05": 0, "mma_sync": 1}[kind]), "rw_mlp_set_gemm")
+
+    def status(self):
+        """Synchronise and raise if a tensor-core pipeline wait gave up."""
+        self._check(self.lib.rw_mlp_status(self.h), "rw_mlp_status")
+
+    def hidden_layer(self, layer: int, h_in, z_out, h_out):
+        """One hidden layer: z_out = h_in W_layer + b (FP32), h_out = bf16(SiLU(z_out));
+        h_in, h_out: [n][hidden] torch.bfloat16, z_out: [n][hidden] float32 (device)."""
+        n = int(h_in.shape[0])
+        _check_buffer(h_in, "h_in", n * self.hidden, "bfloat16")
+        _check_buffer(h_out, "h_out", n * self.hidden, "bfloat16")
+        _check_buffer(z_out, "z_out", n * self.hidden, "float32")
+        self._check(self.lib.rw_mlp_hidden_layer(self.h, int(layer), _ptr(h_in), n, _ptr(z_out), _ptr(h_out)),
+                    "rw_mlp_hidden_layer")
 
 
 class Graph:
