@@ -479,6 +479,10 @@ def run_ours(args):
                                          cache[key], args, flush, peaks, n_acc)
         del cache
 
+    lhe = None
+    if rank == 0 and world == 1 and not args.no_e2e:
+        lhe = run_lhe_e2e(torch, rwgt, dev, stream, wl, pts, mom_h, w_h, args.mode)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, cores = oracle_rate(wl, pts, args.cpu_seconds)
@@ -496,7 +500,7 @@ def run_ours(args):
             "sigma": [float(x) for x in sig], "sigma_orig": sig_orig, "n_bad": int(nbad),
             "step_ms_min_median_max": [1e3 * min(per_step), 1e3 * statistics.median(per_step),
                                        1e3 * max(per_step)],
-            "variants": variants,
+            "variants": variants, "event_file_e2e": lhe,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -527,6 +531,70 @@ def run_variant(torch, rwgt, dev, stream, wl, variant, mode, sample, args, flush
         out["r_is_exactly_one"] = bool(torch.all(wn == w.unsqueeze(0)).item())
     del wn, ws
     return out
+
+
+def write_event_file(path, process, mom, w):
+    """A Les Houches event file of the sample in its centre-of-mass frame
+    (one <event> block per event: the header line and one line per particle)."""
+    codes = {"gg_tt": [21, 21, 6, -6], "gg_ttg": [21, 21, 6, -6, 21], "gg_ttgg": [21, 21, 6, -6, 21, 21],
+             "ee_mumu": [11, -11, 13, -13], "ee_5a": [11, -11, 22, 22, 22, 22, 22]}[process]
+    N, _, E = mom.shape
+    st = [-1, -1] + [1] * (N - 2)
+    with open(path, "w") as f:
+        f.write('<LesHouchesEvents version="3.0">\n<header>\n</header>\n<init>\n'
+                "2212 2212 6.5e3 6.5e3 0 0 0 0 3 1\n1.0 0.1 1.0 1\n</init>\n")
+        for e in range(E):
+            lines = [f"<event>\n{N} 1 {w[e]!r} 91.188 7.546771e-03 1.18e-01"]
+            for i in range(N):
+                lines.append(f" {codes[i]} {st[i]} 0 0 0 0 {mom[i, 1, e]!r} {mom[i, 2, e]!r} {mom[i, 3, e]!r} "
+                             f"{mom[i, 0, e]!r} 0.0 0. 9.")
+            lines.append("</event>\n")
+            f.write("\n".join(lines))
+        f.write("</LesHouchesEvents>\n")
+
+
+def run_lhe_e2e(torch, rwgt, dev, stream, wl, pts, mom_h, w_h, mode, n_events=1 << 17, chunk=1 << 14, reps=3):
+    """Event file to event file: rw_lhe_reweight (host parsing of the next
+    chunk and writing of the previous one overlapped with the GPU) against
+    the same steps one after the other (parse everything, reweight through
+    the host entry point, write everything); wall clock, best of `reps`."""
+    import tempfile
+    n = min(n_events, mom_h.shape[-1])
+    P = pts.shape[0]
+    ids = [f"p{j}" for j in range(P)]
+    with tempfile.TemporaryDirectory() as tmp:
+        src = os.path.join(tmp, "in.lhe")
+        write_event_file(src, wl.process, np.ascontiguousarray(mom_h[:, :, :n]), w_h[:n])
+        size = os.path.getsize(src)
+        with rwgt.Context(dev.index or 0, stream.cuda_stream) as c:
+            c.set_process(wl.process, mode)
+            c.set_params(ev.param_vector())
+            c.set_reweight_points(pts)
+            nb = rwgt.lhe_workspace_bytes(c, chunk)
+            ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+            nbh = c.workspace_bytes_host(n)
+            wsh = torch.empty(nbh, dtype=torch.uint8, device=dev)
+            t_pipe, t_seq = [], []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                with rwgt.Lhe(src) as f:
+                    rwgt.lhe_reweight(c, f, os.path.join(tmp, "piped.lhe"), ids, chunk, ws, nb)
+                t_pipe.append(time.perf_counter() - t0)
+                t0 = time.perf_counter()
+                with rwgt.Lhe(src) as f:
+                    m, wf = f.read(wl.process)
+                    hw = np.empty((P, n))
+                    c.reweight_host(m, wf, n, hw, P, wsh, nbh)
+                    f.write(os.path.join(tmp, "plain.lhe"), hw, ids)
+                t_seq.append(time.perf_counter() - t0)
+            same = open(os.path.join(tmp, "piped.lhe"), "rb").read() == open(os.path.join(tmp, "plain.lhe"),
+                                                                              "rb").read()
+    tp, ts = min(t_pipe), min(t_seq)
+    return {"events": n, "points": P, "chunk": chunk, "file_mb": size / 2 ** 20, "mode": mode,
+            "pipelined": {"value": n * P / tp, "unit": UNIT, "s": tp},
+            "sequential": {"value": n * P / ts, "unit": UNIT, "s": ts}, "gain": ts / tp,
+            "files_identical": same,
+            "timing": "wall clock, open + parse + reweight + write, best of 3; host threads parse while the GPU runs"}
 
 
 def run_e2e(ctx, torch, dev, mom_h, w_h, E, P, N, world, args):

@@ -376,9 +376,10 @@ int rw_reweight_interp(rw_ctx* ctx, int n_nodes, double tol, double* d_wnew, uns
    assume.  RW_ERR_ARG with the event index in rw_lhe_last_error when an event
    does not match the process or a number does not parse.
    rw_lhe_write writes the file again to `path` with, for every event k, the
-   lines <wgt id='ids[j]'> h_wnew[j*ld + k] </wgt> (j < P, 11 significant digits) inside its
-   <rwgt> block (created before </event> when absent); everything else is
-   copied byte for byte.  ids must not contain ' < > &. */
+   lines <wgt id='ids[j]'> h_wnew[j*ld + k] </wgt> (j < P; the shortest
+   decimal form that reads back as the same double) inside its <rwgt> block
+   (created before </event> when absent); everything else is copied byte for
+   byte.  ids must not contain ' < > &. */
 typedef struct rw_lhe rw_lhe;
 int rw_lhe_open(rw_lhe** out, const char* path);
 int rw_lhe_close(rw_lhe* lhe);
@@ -387,6 +388,33 @@ int64_t rw_lhe_n_events(const rw_lhe* lhe);
 int rw_lhe_read(rw_lhe* lhe, int process, int64_t first, int64_t n, double* h_mom, int64_t ld, double* h_w,
                 int n_threads);
 int rw_lhe_write(rw_lhe* lhe, const char* path, const double* h_wnew, int P, int64_t ld, const char* const* ids);
+/* The same output written in pieces, events in file order:
+   rw_lhe_write_begin opens `path` (RW_ERR_STATE if a write is open),
+   rw_lhe_write_events adds events [first, first + n) with their weights
+   h_wnew[j*ld + i] (first must be the next unwritten event), rw_lhe_write_end
+   writes the rest of the file and closes it (RW_ERR_STATE, with the file
+   closed, when events are missing). */
+int rw_lhe_write_begin(rw_lhe* lhe, const char* path, int P, const char* const* ids);
+int rw_lhe_write_events(rw_lhe* lhe, int64_t first, int64_t n, const double* h_wnew, int64_t ld);
+int rw_lhe_write_end(rw_lhe* lhe);
+/* Event file to event file (Sec. 3.2: step 2, parse events; steps 3-7 on the
+   GPU; step 8, return the new weights) with the host work hidden behind the
+   GPU's: the file is cut into chunks of `chunk` events; while the GPU
+   reweights chunk k (its momenta copied in, the fused kernel, W' copied back
+   on the context's stream), n_threads host threads parse chunk k+1 and the
+   calling thread writes chunk k-1 to out_path (as rw_lhe_write, the weights
+   ids[0..P-1]).  The cross sections are carried from chunk to chunk in
+   (sum, compensation) form (deterministic for a given chunk size); sigma'_p,
+   sigma and the bad-event count as rw_get_results.  The events must match the
+   context's process (RW_ERR_ARG otherwise, the output then incomplete).
+   Device workspace of rw_lhe_workspace_bytes(ctx, chunk) bytes, 256-byte
+   aligned (two chunks' momenta, weights and W', and the sums); the call
+   attaches it as the context's events (as rw_reweight_host does), allocates
+   three pinned host chunks for its duration and synchronises. */
+size_t rw_lhe_workspace_bytes(const rw_ctx* ctx, int64_t chunk);
+int rw_lhe_reweight(rw_ctx* ctx, rw_lhe* lhe, const char* out_path, const char* const* ids, int64_t chunk,
+                    int n_threads, void* d_workspace, size_t workspace_bytes, double* h_sigma, double* h_sigma_orig,
+                    int64_t* h_n_bad);
 /* Samples with several processes (e.g. the Born and real-emission events of
    an NLO sample, Sec. 4): h_process_of_event[k] (one int per event) = the
    first of processes[0..n_processes-1] (1..8 RW_* ids) whose external

@@ -13,10 +13,12 @@
 //             BF16 -> FP32, M = 128, N, K = 16) and commits each k-block's
 //             MMAs to that A stage's "empty" barrier and each tile to its
 //             accumulator's "full" barrier;
-//   warps 2-5 the epilogue: tcgen05.ld 32 columns at a time from the lanes
-//             their warp may read (warp w reads lanes 32 (w % 4) ...), bias,
-//             SiLU, BF16/FP32 stores or the fused head, then free the
-//             accumulator, which the MMA thread reuses two tiles later.
+//   warps 2-17 the epilogue, four warps per lane quarter (warp w may read the
+//             tensor-memory lanes 32 (w % 4) ... 32 (w % 4) + 31), each of the
+//             four on a quarter of the N columns: tcgen05.ld 16 columns at a
+//             time, bias, SiLU, BF16/FP32 stores or the fused head (the four
+//             column quarters' partial sums meet in shared memory), then free
+//             the accumulator, which the MMA thread reuses two tiles later.
 // Every mbarrier wait gives up after ~2^31 clock cycles (~1 s): it sets the
 // error flag, every role stops, the MMA thread drains its outstanding MMAs
 // (bounded), the TMA thread waits (bounded) for its loads in flight, and the
@@ -33,14 +35,17 @@ constexpr int BK = 64;       // k per TMA box and swizzle row (64 BF16 = 128 byt
 constexpr int STAGES = 4;    // A ring depth (k-blocks)
 constexpr int MAX_N = 256;   // N <= 256 (one MMA covers the whole width)
 constexpr int MAX_KB = 4;    // K <= 256
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 16;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int UMMA_K = 16;   // k of one kind::f16 MMA
 constexpr long long WAIT_CYCLES = 1ll << 31;
 
-// dynamic shared memory: 1024-byte alignment slack, W^T, the A ring, barriers
+// dynamic shared memory: 1024-byte alignment slack, W^T, the A ring, barriers,
+// the fused head's partial sums [accumulator][column quarter][row][2]
 constexpr size_t SMEM_B = (size_t)MAX_KB * MAX_N * 128;
 constexpr size_t SMEM_A = (size_t)STAGES * BM * 128;
-constexpr size_t SMEM_BYTES = 1024 + SMEM_B + SMEM_A + 256;
+constexpr size_t SMEM_HEAD = (size_t)2 * 4 * BM * 2 * sizeof(float);
+constexpr size_t SMEM_BYTES = 1024 + SMEM_B + SMEM_A + 256 + SMEM_HEAD;
 
 struct Epi {
   const float* bias;       // [N]
@@ -138,24 +143,23 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 consecutive FP32 columns of this warp's 32 lanes
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// 16 consecutive FP32 columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// SiLU as the other kernels of the surrogate compute it: z sigma(z)
-__device__ __forceinline__ float silu_f(float z) { return z * (1.0f / (1.0f + __expf(-z))); }
+// SiLU z sigma(z) = z / (1 + e^-z) with the fast exponential and division
+// (a few units in the last place of FP32; the result is rounded to BF16)
+__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 __device__ __forceinline__ unsigned short bf16_bits(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
@@ -174,13 +178,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(const __grid_constant__ 
   const uint32_t b_acc_full = smem_u32(bars + 2 * STAGES + 1), b_acc_empty = smem_u32(bars + 2 * STAGES + 3);
   const uint32_t b_drain = smem_u32(bars + 2 * STAGES + 5);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  float* head = reinterpret_cast<float*>(sA + SMEM_A + 256);  // [2][4][BM][2]
   __shared__ int abort_flag;
+  __shared__ int head_count[8];  // [accumulator][lane quarter]: column quarters done
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = e.N, KB = e.K / BK;
   const int tiles = (e.M + BM - 1) / BM;
   const uint32_t tmem_cols = 2 * MAX_N;  // two accumulators of up to 256 columns
 
+  if (threadIdx.x < 8) head_count[threadIdx.x] = 0;
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < STAGES; ++s) {
@@ -190,7 +197,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(const __grid_constant__ 
     mbar_init(b_full_b, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(b_acc_full + 8 * i, 1);
-      mbar_init(b_acc_empty + 8 * i, 4);  // one arrival per epilogue warp
+      mbar_init(b_acc_empty + 8 * i, EPI_WARPS);  // one arrival per epilogue warp
     }
     mbar_init(b_drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -282,32 +289,35 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(const __grid_constant__ 
       }
     }
   } else {
-    const int q = warp & 3;  // the lane quarter this warp may read
+    const int q = warp & 3;             // the lane quarter this warp may read
+    const int cq = (warp - 2) >> 2;     // its quarter of the columns
+    const int cw = N >> 2;              // columns per quarter (a multiple of 16)
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
       if (!mbar_wait(b_acc_full + 8 * acc, acc_phase, e.err, 5, abort)) break;
       tc_fence_after();
-      const long long row = (long long)t * BM + q * 32 + lane;
+      const int r = q * 32 + lane;  // row within the tile
+      const long long row = (long long)t * BM + r;
       const bool live = row < e.M;
       float h0 = 0.0f, h1 = 0.0f;
-      for (int c0 = 0; c0 < N; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + (uint32_t)(acc * MAX_N + c0) + ((uint32_t)(q * 32) << 16), v);
+      for (int c0 = cq * cw; c0 < (cq + 1) * cw; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t)(acc * MAX_N + c0) + ((uint32_t)(q * 32) << 16), v);
         if (!live) continue;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] += __ldg(e.bias + c0 + j);
+        for (int j = 0; j < 16; ++j) v[j] += __ldg(e.bias + c0 + j);
         if (e.Z) {
           float4* zp = reinterpret_cast<float4*>(e.Z + row * N + c0);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) zp[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+          for (int j = 0; j < 4; ++j) zp[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         }
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = silu_f(v[j]);
+        for (int j = 0; j < 16; ++j) v[j] = silu_f(v[j]);
         if (e.H) {
           uint4* hp = reinterpret_cast<uint4*>(e.H + row * N + c0);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
+          for (int j = 0; j < 2; ++j) {
             uint32_t w[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -317,13 +327,41 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(const __grid_constant__ 
         }
         if (e.w_out) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < 16; ++j) {
             h0 = fmaf(v[j], __ldg(e.w_out + 2 * (c0 + j)), h0);
             h1 = fmaf(v[j], __ldg(e.w_out + 2 * (c0 + j) + 1), h1);
           }
         }
       }
-      if (live && e.w_out) *reinterpret_cast<float2*>(e.out + 2 * row) = make_float2(h0 + e.b_out[0], h1 + e.b_out[1]);
+      if (e.w_out) {
+        // the four column quarters of these 32 rows meet in shared memory;
+        // the last of the four warps to arrive adds them, in a fixed order
+        // (no warp waits for another)
+        float* hp = head + (size_t)((acc * 4 + cq) * BM + r) * 2;
+        hp[0] = h0;
+        hp[1] = h1;
+        __syncwarp();
+        int prior = 0;
+        if (lane == 0) {
+          __threadfence_block();
+          prior = atomicAdd(&head_count[acc * 4 + q], 1);
+        }
+        prior = __shfl_sync(0xffffffffu, prior, 0);
+        if (prior == 3) {
+          __threadfence_block();
+          if (live) {
+            float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              s0 += head[((acc * 4 + c) * BM + r) * 2];
+              s1 += head[((acc * 4 + c) * BM + r) * 2 + 1];
+            }
+            *reinterpret_cast<float2*>(e.out + 2 * row) = make_float2(s0 + e.b_out[0], s1 + e.b_out[1]);
+          }
+          __syncwarp();
+          if (lane == 0) head_count[acc * 4 + q] = 0;
+        }
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(b_acc_empty + 8 * acc);

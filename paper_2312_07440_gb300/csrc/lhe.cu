@@ -35,6 +35,11 @@ struct rw_lhe {
   std::string text;
   std::vector<size_t> body, end;  // per event: first byte after "<event...>", position of "</event>"
   std::string err;
+  // streaming writer (rw_lhe_write_begin/events/end)
+  FILE* wf = nullptr;
+  size_t w_at = 0;        // text written up to here
+  int64_t w_next = 0;     // next event to write
+  std::vector<std::string> w_ids;
 };
 
 namespace {
@@ -254,6 +259,7 @@ int rw_lhe_open(rw_lhe** out, const char* path) {
 
 int rw_lhe_close(rw_lhe* h) {
   if (!h) return RW_ERR_NULL;
+  if (h->wf) fclose(h->wf);
   delete h;
   return RW_OK;
 }
@@ -354,49 +360,67 @@ int rw_lhe_classify(rw_lhe* h, const int* processes, int n_processes, int* h_pro
   return RW_OK;
 }
 
-int rw_lhe_write(rw_lhe* h, const char* path, const double* h_wnew, int P, int64_t ld, const char* const* ids) {
+int rw_lhe_write_begin(rw_lhe* h, const char* path, int P, const char* const* ids) {
   if (!h) return RW_ERR_NULL;
-  if (!path || !h_wnew || !ids) return lhe_fail(h, RW_ERR_NULL, "path, weights and ids are required");
-  const int64_t E = (int64_t)h->body.size();
-  if (P < 1 || ld < E) return lhe_fail(h, RW_ERR_ARG, "need P >= 1 and ld >= %lld", (long long)E);
+  if (!path || !ids) return lhe_fail(h, RW_ERR_NULL, "path and ids are required");
+  if (h->wf) return lhe_fail(h, RW_ERR_STATE, "a write is already open");
+  if (P < 1) return lhe_fail(h, RW_ERR_ARG, "need P >= 1");
   for (int j = 0; j < P; ++j) {
     if (!ids[j] || !*ids[j]) return lhe_fail(h, RW_ERR_ARG, "id %d is empty", j);
     for (const char* q = ids[j]; *q; ++q)
       if (*q == '\'' || *q == '<' || *q == '>' || *q == '&') return lhe_fail(h, RW_ERR_ARG, "id %d: bad character", j);
   }
+  h->wf = fopen(path, "wb");
+  if (!h->wf) return lhe_fail(h, RW_ERR_ARG, "cannot open %s", path);
+  h->w_ids.assign(ids, ids + P);
+  h->w_at = 0;
+  h->w_next = 0;
+  return RW_OK;
+}
+
+int rw_lhe_write_events(rw_lhe* h, int64_t first, int64_t n, const double* h_wnew, int64_t ld) {
+  if (!h) return RW_ERR_NULL;
+  if (!h->wf) return lhe_fail(h, RW_ERR_STATE, "no write open");
+  if (!h_wnew && n > 0) return lhe_fail(h, RW_ERR_NULL, "weights are NULL");
+  const int64_t E = (int64_t)h->body.size();
+  if (first != h->w_next || n < 0 || first + n > E || ld < n)
+    return lhe_fail(h, RW_ERR_ARG, "events [%lld, %lld) with ld %lld: next expected %lld of %lld", (long long)first,
+                    (long long)(first + n), (long long)ld, (long long)h->w_next, (long long)E);
   const std::string& t = h->text;
+  const int P = (int)h->w_ids.size();
   // per event: where the weight lines go and whether an <rwgt> block exists
-  std::vector<size_t> cut(E);
-  std::vector<char> has(E);
   // (searched within the event's own block only: linear in the file size)
+  std::vector<size_t> cut(n);
+  std::vector<char> has(n);
   const std::string_view tv(t);
-  for (int64_t k = 0; k < E; ++k) {
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t k = first + i;
     const std::string_view blk = tv.substr(h->body[k], h->end[k] - h->body[k]);
     const size_t rb = blk.find("<rwgt>");
-    has[k] = rb != std::string_view::npos;
-    const size_t re = has[k] ? blk.find("</rwgt>", rb) : blk.size();
+    has[i] = rb != std::string_view::npos;
+    const size_t re = has[i] ? blk.find("</rwgt>", rb) : blk.size();
     if (re == std::string_view::npos)
       return lhe_fail(h, RW_ERR_ARG, "event %lld: unclosed <rwgt>", (long long)k);
-    cut[k] = h->body[k] + re;
+    cut[i] = h->body[k] + re;
   }
-  // the inserted text of every event, formatted in parallel (std::to_chars,
-  // scientific, 10 digits after the point), written in order
-  const int T = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), (int)(E / 4096) + 1));
-  std::vector<std::string> ins(E);
+  // the inserted text of every event, formatted in parallel: the shortest
+  // decimal form that reads back as the same double (std::to_chars)
+  const int T = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), (int)(n / 4096) + 1));
+  std::vector<std::string> ins(n);
   auto fmt = [&](int th) {
     char num[64];
-    for (int64_t k = E * th / T; k < E * (th + 1) / T; ++k) {
-      std::string& o = ins[k];
-      if (!has[k]) o += "<rwgt>\n";
+    for (int64_t i = n * th / T; i < n * (th + 1) / T; ++i) {
+      std::string& o = ins[i];
+      if (!has[i]) o += "<rwgt>\n";
       for (int j = 0; j < P; ++j) {
-        auto r = std::to_chars(num, num + sizeof num, h_wnew[(int64_t)j * ld + k], std::chars_format::scientific, 10);
+        auto r = std::to_chars(num, num + sizeof num, h_wnew[(int64_t)j * ld + i]);
         o += "<wgt id='";
-        o += ids[j];
+        o += h->w_ids[j];
         o += "'> ";
         o.append(num, r.ptr);
         o += " </wgt>\n";
       }
-      if (!has[k]) o += "</rwgt>\n";
+      if (!has[i]) o += "</rwgt>\n";
     }
   };
   {
@@ -405,18 +429,41 @@ int rw_lhe_write(rw_lhe* h, const char* path, const double* h_wnew, int P, int64
     fmt(0);
     for (auto& x : pool) x.join();
   }
-  FILE* f = fopen(path, "wb");
-  if (!f) return lhe_fail(h, RW_ERR_ARG, "cannot open %s", path);
-  size_t at = 0;
   bool ok = true;
-  for (int64_t k = 0; k < E && ok; ++k) {
-    ok = fwrite(t.data() + at, 1, cut[k] - at, f) == cut[k] - at &&
-         fwrite(ins[k].data(), 1, ins[k].size(), f) == ins[k].size();
-    at = cut[k];
+  for (int64_t i = 0; i < n && ok; ++i) {
+    ok = fwrite(t.data() + h->w_at, 1, cut[i] - h->w_at, h->wf) == cut[i] - h->w_at &&
+         fwrite(ins[i].data(), 1, ins[i].size(), h->wf) == ins[i].size();
+    h->w_at = cut[i];
   }
-  if (ok) ok = fwrite(t.data() + at, 1, t.size() - at, f) == t.size() - at;
-  if (fclose(f) != 0) ok = false;
-  return ok ? RW_OK : lhe_fail(h, RW_ERR_ARG, "write to %s failed", path);
+  if (!ok) return lhe_fail(h, RW_ERR_ARG, "write failed");
+  h->w_next = first + n;
+  return RW_OK;
+}
+
+int rw_lhe_write_end(rw_lhe* h) {
+  if (!h) return RW_ERR_NULL;
+  if (!h->wf) return lhe_fail(h, RW_ERR_STATE, "no write open");
+  const int64_t E = (int64_t)h->body.size();
+  const std::string& t = h->text;
+  bool ok = h->w_next == E;
+  if (ok) ok = fwrite(t.data() + h->w_at, 1, t.size() - h->w_at, h->wf) == t.size() - h->w_at;
+  if (fclose(h->wf) != 0) ok = false;
+  h->wf = nullptr;
+  if (h->w_next != E)
+    return lhe_fail(h, RW_ERR_STATE, "only %lld of %lld events written", (long long)h->w_next, (long long)E);
+  return ok ? RW_OK : lhe_fail(h, RW_ERR_ARG, "write failed");
+}
+
+int rw_lhe_write(rw_lhe* h, const char* path, const double* h_wnew, int P, int64_t ld, const char* const* ids) {
+  if (!h) return RW_ERR_NULL;
+  if (!path || !h_wnew || !ids) return lhe_fail(h, RW_ERR_NULL, "path, weights and ids are required");
+  const int64_t E = (int64_t)h->body.size();
+  if (P < 1 || ld < E) return lhe_fail(h, RW_ERR_ARG, "need P >= 1 and ld >= %lld", (long long)E);
+  int rc = rw_lhe_write_begin(h, path, P, ids);
+  if (rc) return rc;
+  rc = rw_lhe_write_events(h, 0, E, h_wnew, ld);
+  const int rc2 = rw_lhe_write_end(h);
+  return rc ? rc : rc2;
 }
 
 }  // extern "C"

@@ -158,7 +158,7 @@ __global__ void k_dense_in(const float* __restrict__ X, int B, int nin, const fl
   const int r = (int)(t / N), n = (int)(t % N);
   float z = b[n];
   for (int k = 0; k < nin; ++k) z = fmaf(X[(long long)r * nin + k], W[(long long)k * N + n], z);
-  Z[t] = z;
+  if (Z) Z[t] = z;  // pre-activation: kept for the backward pass and the unfused output layer
   H[t] = f2bf(z * sigmoidf_(z));
 }
 
@@ -430,9 +430,11 @@ int launch_gemm(rw_mlp* m, int epi, GemmArgs a) {
 // its pre-activation nor its activation.
 int forward_batch(rw_mlp* m, const float* xf, int B, bool infer = false) {
   const int L = m->n_layers;
-  k_dense_in<<<(unsigned)(((long long)B * m->hidden + 255) / 256), 256, 0, m->stream>>>(
-      xf, B, m->n_in, m->p + m->w_off[0], m->p + m->b_off[0], m->hidden, m->Z[0], m->H[0]);
   const bool tc = tc_usable(m);
+  // inference on the tensor-core path reads no pre-activation back
+  const bool keep_z = !(infer && tc && L >= 2);
+  k_dense_in<<<(unsigned)(((long long)B * m->hidden + 255) / 256), 256, 0, m->stream>>>(
+      xf, B, m->n_in, m->p + m->w_off[0], m->p + m->b_off[0], m->hidden, keep_z ? m->Z[0] : nullptr, m->H[0]);
   for (int l = 1; l < L; ++l) {
     if (tc) {
       tcg::Epi e{};
@@ -441,7 +443,7 @@ int forward_batch(rw_mlp* m, const float* xf, int B, bool infer = false) {
         e.b_out = m->p + m->b_off[L];
         e.out = m->out;
       } else {
-        e.Z = m->Z[l];
+        e.Z = keep_z ? m->Z[l] : nullptr;
         e.H = m->H[l];
       }
       const int rc = launch_gemm_tc(m, l, m->H[l - 1], B, e);

@@ -98,22 +98,72 @@ __device__ __forceinline__ dd dd_add(dd x, double y) {
   return {h, lo - (h - s.hi)};
 }
 
-// v.v - c for a double-double 4-vector v and c = c_hi + c_lo, rounded once:
-// each (hi + lo)^2 is hi*hi (exact as hi*hi + e by FMA) + 2 hi lo (lo^2 is
-// below the last digit), the large terms are added by TwoSum.
-__device__ __forceinline__ double dd_msq_minus(const dd (&v)[4], double c_hi, double c_lo) {
+__device__ __forceinline__ dd dd_add(dd x, dd y) {
+  const dd s = dd_two_sum(x.hi, y.hi);
+  const double lo = s.lo + (x.lo + y.lo);
+  const double h = s.hi + lo;
+  return {h, lo - (h - s.hi)};
+}
+
+// Minkowski product a.b carried to double-double: every product exact as
+// p + e (FMA), the p added by TwoSum
+__device__ __forceinline__ dd dd_dot4(const double (&a)[4], const double (&b)[4]) {
   dd acc = {0.0, 0.0};
-  double small = -c_lo;
+  double small = 0.0;
 #pragma unroll
   for (int m4 = 0; m4 < 4; ++m4) {
-    const double sg = m4 ? -1.0 : 1.0;
-    const double p = v[m4].hi * v[m4].hi;
-    const double e = fma(v[m4].hi, v[m4].hi, -p) + 2.0 * v[m4].hi * v[m4].lo;
-    acc = dd_add(acc, sg * p);
-    small += sg * e;
+    const double x = m4 ? -a[m4] : a[m4];
+    const double q = x * b[m4];
+    small += fma(x, b[m4], -q);
+    acc = dd_add(acc, q);
   }
-  acc = dd_add(acc, -c_hi);
-  return acc.hi + (acc.lo + small);
+  acc.lo += small;
+  return acc;
+}
+
+// K^2 and (K - p4)^2 - m^2 of every gluon subset K = sum_{i in S} k_i from the
+// momenta themselves (no mass-shell assumption), each rounded once from
+// double-double: K^2 = sum_i k_i.k_i + 2 sum_{i<j} k_i.k_j and
+// (K - p4)^2 - m^2 = K^2 - 2 sum_i k_i.p4 + (p4.p4 - m^2), with the pairwise
+// products formed once.  Out of line: its temporaries stay out of the
+// amplitude code's register allocation.
+template <int NG>
+__device__ __noinline__ void subset_invariants_dd(const double (&k)[NG][4], const double (&p4)[4], double m,
+                                                  double (&K2)[1 << NG], double (&den)[1 << NG]) {
+  dd kk[NG], kp[NG], d[NG][NG];
+#pragma unroll
+  for (int i = 0; i < NG; ++i) {
+    kk[i] = dd_dot4(k[i], k[i]);
+    kp[i] = dd_dot4(k[i], p4);
+#pragma unroll
+    for (int j = i + 1; j < NG; ++j) d[i][j] = dd_dot4(k[i], k[j]);
+  }
+  dd pm = dd_dot4(p4, p4);
+  const double m2 = m * m;
+  pm = dd_add(pm, dd{-m2, -fma(m, m, -m2)});
+  constexpr int FULL = (1 << NG) - 1;
+#pragma unroll
+  for (int msk = 1; msk <= FULL; ++msk) {
+    dd s = {0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      if (!((msk >> i) & 1)) continue;
+      s = dd_add(s, kk[i]);
+#pragma unroll
+      for (int j = i + 1; j < NG; ++j)
+        if ((msk >> j) & 1) s = dd_add(s, dd{2.0 * d[i][j].hi, 2.0 * d[i][j].lo});
+    }
+    K2[msk] = s.hi + s.lo;
+    if (msk != FULL) {
+#pragma unroll
+      for (int i = 0; i < NG; ++i)
+        if ((msk >> i) & 1) s = dd_add(s, dd{-2.0 * kp[i].hi, -2.0 * kp[i].lo});
+      s = dd_add(s, pm);
+      den[msk] = s.hi + s.lo;
+    } else {
+      den[msk] = 0.0;
+    }
+  }
 }
 
 template <class R, int NG, int NEXT>
@@ -145,8 +195,11 @@ __device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, 
     ubar_out<R>(p3, R(m), X.ub);
     v_out<R>(p4, R(m), X.v);
   }
-  // Invariants: the dot products, where cancellation happens, in FP64;
-  // the reciprocals in the working precision.
+  // Invariants: the dot products, where cancellation happens, in FP64 (two
+  // or three gluons: double-double, see subset_invariants_dd); the
+  // reciprocals in the working precision.
+  [[maybe_unused]] double K2dd[1 << NG], dendd[1 << NG];
+  if constexpr (NG >= 3) subset_invariants_dd<NG>(k, p[3], m, K2dd, dendd);
   double d[NG][NG];
 #pragma unroll
   for (int i = 0; i < NG; ++i)
@@ -177,25 +230,7 @@ __device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, 
         if ((msk >> i) & 1) v += kw[i][m4];
       Kn.P[msk][m4] = v;
     }
-    // several gluons (g g -> t tbar g(g)): K^2 and (K - p4)^2 - m^2 from the
-    // momenta themselves, in double-double, rounded once
-    [[maybe_unused]] double den_dd = 0.0;
-    if constexpr (NG >= 3) {
-      if (cnt >= 2) {
-        dd Kd[4], q[4];
-#pragma unroll
-        for (int m4 = 0; m4 < 4; ++m4) {
-          Kd[m4] = {0.0, 0.0};
-#pragma unroll
-          for (int i = 0; i < NG; ++i)
-            if ((msk >> i) & 1) Kd[m4] = dd_add(Kd[m4], k[i][m4]);
-          q[m4] = dd_add(Kd[m4], -p[3][m4]);
-        }
-        K2 = dd_msq_minus(Kd, 0.0, 0.0);
-        const double m2 = m * m;
-        den_dd = dd_msq_minus(q, m2, fma(m, m, -m2));
-      }
-    }
+    if constexpr (NG >= 3) K2 = K2dd[msk];
     if (cnt >= 2) {
       const R inv = R(1) / R(K2);
       Kn.cg[msk] = -inv;
@@ -206,7 +241,11 @@ __device__ __forceinline__ void qcd_setup(const double (&p)[NEXT][4], double m, 
     }
     if (msk != FULL) {
       // (K - p4)^2 - m^2 = K^2 - 2 K.p4  (p4^2 = m^2); several gluons: as above
-      const double den = (NG >= 3 && cnt >= 2) ? den_dd : K2 - 2.0 * dot4(P, p[3]);
+      double den;
+      if constexpr (NG >= 3)
+        den = dendd[msk];
+      else
+        den = K2 - 2.0 * dot4(P, p[3]);
       const R c = R(-1) / R(den);
 #pragma unroll
       for (int m4 = 0; m4 < 4; ++m4) Kn.qc[msk][m4] = c * R(P[m4] - p[3][m4]);

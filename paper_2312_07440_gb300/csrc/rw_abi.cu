@@ -1645,3 +1645,159 @@ int rw_multi_get_results(rw_multi* m, double* h_sigma, double* h_sigma_orig, int
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Event file to event file with the host work overlapped (rw_lhe_reweight)
+// ---------------------------------------------------------------------------
+#include <thread>
+
+namespace {
+
+// device slots: two chunks of momenta [N][4][chunk], weights and W' [P][chunk]
+struct LheLayout {
+  size_t core, mom, w, wnew, total;
+};
+
+LheLayout lhe_layout(const rw_ctx* c, int64_t chunk) {
+  const int N = registry().st[c->process].n_external;
+  const size_t P = std::max<size_t>(1, c->pts.size());
+  LheLayout L{};
+  L.core = ws_core_bytes((int)P) + align256(16 * (P + 1));  // + the carried (sum, compensation) pairs
+  L.mom = align256(8 * 4 * (size_t)N * chunk);
+  L.w = align256(8 * (size_t)chunk);
+  L.wnew = align256(8 * P * chunk);
+  L.total = L.core + 2 * (L.mom + L.w + L.wnew);
+  return L;
+}
+
+struct PinnedSlot {
+  double *mom = nullptr, *w = nullptr, *wnew = nullptr;
+};
+
+}  // namespace
+
+extern "C" {
+
+size_t rw_lhe_workspace_bytes(const rw_ctx* c, int64_t chunk) {
+  if (!c || c->process < 0 || chunk <= 0) return 0;
+  return lhe_layout(c, chunk).total;
+}
+
+int rw_lhe_reweight(rw_ctx* c, rw_lhe* lhe, const char* out_path, const char* const* ids, int64_t chunk,
+                    int n_threads, void* d_ws, size_t ws_bytes, double* h_sigma, double* h_sigma_orig,
+                    int64_t* h_n_bad) {
+  if (!c) return RW_ERR_NULL;
+  if (!lhe || !out_path || !ids || !d_ws) return fail(c, RW_ERR_NULL, "event file, path, ids and workspace are required");
+  if (c->process < 0 || !c->have_p0 || c->pts.empty()) return fail(c, RW_ERR_STATE, "process/params/points unset");
+  const int64_t E = rw_lhe_n_events(lhe);
+  if (E <= 0) return fail(c, RW_ERR_ARG, "the event file has no events");
+  if (chunk <= 0) return fail(c, RW_ERR_ARG, "chunk must be > 0");
+  chunk = std::min<int64_t>(chunk, E);
+  if (reinterpret_cast<uintptr_t>(d_ws) % 256) return fail(c, RW_ERR_ALIGN, "workspace not 256-byte aligned");
+  const LheLayout L = lhe_layout(c, chunk);
+  if (ws_bytes < L.total) return fail(c, RW_ERR_WORKSPACE, "workspace smaller than rw_lhe_workspace_bytes");
+  DeviceGuard g(c->device);
+  const int N = registry().st[c->process].n_external;
+  const int P = (int)c->pts.size();
+  char* base = static_cast<char*>(d_ws);
+  double2* d_sacc = reinterpret_cast<double2*>(base + ws_core_bytes(P));
+  double *d_mom[2], *d_w[2], *d_wnew[2];
+  for (int s = 0; s < 2; ++s) {
+    char* q = base + L.core + s * (L.mom + L.w + L.wnew);
+    d_mom[s] = reinterpret_cast<double*>(q);
+    d_w[s] = reinterpret_cast<double*>(q + L.mom);
+    d_wnew[s] = reinterpret_cast<double*>(q + L.mom + L.w);
+  }
+  int rc = rw_load_events(c, d_mom[0], d_w[0], chunk, d_ws, ws_bytes);
+  if (rc) return rc;
+  // three pinned host slots: chunk k+1 is parsed into one while chunk k's
+  // copies use the second and chunk k-1's weights are written from the third
+  PinnedSlot hs[3];
+  std::vector<cudaEvent_t> done(3, nullptr);
+  auto cleanup = [&]() {
+    for (auto& x : hs)
+      for (double* q : {x.mom, x.w, x.wnew})
+        if (q) cudaFreeHost(q);
+    for (auto& ev : done)
+      if (ev) cudaEventDestroy(ev);
+  };
+  for (int s = 0; s < 3; ++s) {
+    if (cudaHostAlloc(reinterpret_cast<void**>(&hs[s].mom), 8 * 4 * (size_t)N * chunk, cudaHostAllocDefault) !=
+            cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&hs[s].w), 8 * (size_t)chunk, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void**>(&hs[s].wnew), 8 * (size_t)P * chunk, cudaHostAllocDefault) !=
+            cudaSuccess ||
+        cudaEventCreateWithFlags(&done[s], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      cleanup();
+      return fail(c, RW_ERR_CUDA, "pinned host buffers for the event-file pipeline");
+    }
+  }
+  const int K = (int)((E + chunk - 1) / chunk);
+  auto first_of = [&](int k) { return (int64_t)k * chunk; };
+  auto size_of = [&](int k) { return std::min<int64_t>(chunk, E - first_of(k)); };
+  int parse_rc = RW_OK;
+  auto parse = [&](int k) {
+    parse_rc = rw_lhe_read(lhe, c->process, first_of(k), size_of(k), hs[k % 3].mom, chunk, hs[k % 3].w, n_threads);
+  };
+  rc = rw_lhe_write_begin(lhe, out_path, P, ids);
+  if (rc) {
+    cleanup();
+    return fail(c, rc, "%s", rw_lhe_last_error(lhe));
+  }
+  auto abort_all = [&](int code, const std::string& msg) {
+    cudaStreamSynchronize(c->stream);
+    rw_lhe_write_end(lhe);  // closes the partial output
+    cleanup();
+    return fail(c, code, "%s", msg.c_str());
+  };
+  parse(0);
+  if (parse_rc) return abort_all(parse_rc, rw_lhe_last_error(lhe));
+  const size_t row = 8 * (size_t)chunk;
+  for (int k = 0; k < K; ++k) {
+    const int s = k & 1, h = k % 3;
+    const int64_t n = size_of(k);
+    // chunk k on the GPU: copies in, the fused reweight (sums carried across
+    // chunks in (sum, compensation) form), W' copied back
+    cudaError_t e = cudaMemcpy2DAsync(d_mom[s], row, hs[h].mom, row, 8 * (size_t)n, 4 * (size_t)N,
+                                      cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_w[s], hs[h].w, 8 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return abort_all(RW_ERR_CUDA, cudaGetErrorString(e));
+    RwArgs a{};
+    reweight_args(c, a, d_wnew[s], nullptr, nullptr, nullptr);
+    a.mom = d_mom[s];
+    a.w = d_w[s];
+    a.E = n;
+    a.ld = chunk;
+    a.ldo = chunk;
+    a.sigma_acc = d_sacc;
+    a.accumulate = k > 0;
+    if ((rc = launch(c, a))) return abort_all(rc, c->err);
+    e = cudaMemcpy2DAsync(hs[h].wnew, row, d_wnew[s], row, 8 * (size_t)n, (size_t)P, cudaMemcpyDeviceToHost,
+                          c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(done[h], c->stream);
+    if (e != cudaSuccess) return abort_all(RW_ERR_CUDA, cudaGetErrorString(e));
+    // meanwhile on the host: parse chunk k+1, write chunk k-1
+    std::thread parser;
+    if (k + 1 < K) parser = std::thread(parse, k + 1);
+    int wrc = RW_OK;
+    if (k > 0) {
+      const int hp = (k - 1) % 3;
+      if ((e = cudaEventSynchronize(done[hp])) != cudaSuccess) wrc = RW_ERR_CUDA;
+      if (!wrc) wrc = rw_lhe_write_events(lhe, first_of(k - 1), size_of(k - 1), hs[hp].wnew, chunk);
+    }
+    if (parser.joinable()) parser.join();
+    if (wrc) return abort_all(wrc, wrc == RW_ERR_CUDA ? "event synchronisation" : rw_lhe_last_error(lhe));
+    if (parse_rc) return abort_all(parse_rc, rw_lhe_last_error(lhe));
+  }
+  cudaError_t e = cudaEventSynchronize(done[(K - 1) % 3]);
+  if (e != cudaSuccess) return abort_all(RW_ERR_CUDA, cudaGetErrorString(e));
+  rc = rw_lhe_write_events(lhe, first_of(K - 1), size_of(K - 1), hs[(K - 1) % 3].wnew, chunk);
+  if (rc) return abort_all(rc, rw_lhe_last_error(lhe));
+  rc = rw_lhe_write_end(lhe);
+  cleanup();
+  if (rc) return fail(c, rc, "%s", rw_lhe_last_error(lhe));
+  return rw_get_results(c, h_sigma, h_sigma_orig, h_n_bad);
+}
+
+}  // extern "C"

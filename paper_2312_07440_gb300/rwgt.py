@@ -101,6 +101,11 @@ def load():
         "rw_lhe_read": ([P, i, i64, i64, P, i64, P, i], i),
         "rw_lhe_write": ([P, ctypes.c_char_p, P, i, i64, P], i),
         "rw_lhe_classify": ([P, P, i, P, i], i),
+        "rw_lhe_write_begin": ([P, ctypes.c_char_p, i, P], i),
+        "rw_lhe_write_events": ([P, i64, i64, P, i64], i),
+        "rw_lhe_write_end": ([P], i),
+        "rw_lhe_workspace_bytes": ([P, i64], sz),
+        "rw_lhe_reweight": ([P, P, ctypes.c_char_p, P, i64, i, P, sz, P, P, P], i),
         "rw_lhe_read_list": ([P, i, P, i64, P, i64, P, i], i),
         "rw_reweight_interp": ([P, i, d, P, P, P, P, P, P, P, sz], i),
         "rw_alu_peak": ([i, P, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
@@ -206,6 +211,30 @@ class Multi:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def lhe_workspace_bytes(ctx, chunk: int) -> int:
+    return int(ctx.lib.rw_lhe_workspace_bytes(ctx.h, int(chunk)))
+
+
+def lhe_reweight(ctx, lhe, out_path, ids, chunk: int, workspace, workspace_bytes: int, threads: int = 8):
+    """rw_lhe_reweight: the context's process and points applied to every
+    event of the open event file `lhe`, written to out_path with the weight
+    ids, host parsing and writing overlapped with the GPU.  Returns
+    (sigma [P], sigma_orig, n_bad, status)."""
+    P = ctx.n_points
+    if len(ids) != P:
+        raise ValueError(f"need {P} weight ids, got {len(ids)}")
+    _check_buffer(workspace, "workspace", workspace_bytes, dtype="uint8")
+    enc = [i.encode() for i in ids]
+    arr = (ctypes.c_char_p * P)(*enc)
+    sig = np.zeros(P)
+    so = ctypes.c_double()
+    nb = ctypes.c_int64()
+    rc = ctx._check(ctx.lib.rw_lhe_reweight(ctx.h, lhe.h, os.fsencode(os.fspath(out_path)), arr, int(chunk),
+                                            int(threads), _ptr(workspace), int(workspace_bytes), sig.ctypes.data,
+                                            ctypes.byref(so), ctypes.byref(nb)), "rw_lhe_reweight")
+    return sig, so.value, nb.value, rc
 
 
 def alu_peak(kind, device=0, stream=None):
