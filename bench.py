@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other configurations and precision modes (variants)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate variant")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     ap.add_argument("--ref-seconds", type=float, default=90.0,
@@ -281,6 +282,16 @@ def config_dict(args, wl, P, variant, mode=None):
 DTYPE = {"fp64": "f64", "fp32": "f32", "mixed_fp16": "f32+f16(colour)", "mixed_bf16": "f32+bf16(colour)"}
 
 
+def bf16_peak():
+    """Dense BF16 tensor throughput of the GB300s (TFLOP/s): the
+    measured cuBLAS burst figure, else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def measured_peaks(dev_index, stream_handle):
     """FP64 / FP32 FMA throughput of this GPU (rw_alu_peak), TFLOP/s."""
     from paper_2312_07440_gb300 import rwgt
@@ -477,7 +488,13 @@ def run_ours(args):
                 cache[key] = (torch.from_numpy(vm_h).to(dev), torch.from_numpy(vw_h).to(dev), vm_h, vw_h)
             variants[name] = run_variant(torch, rwgt, dev, stream, ev.WORKLOADS[vwl_name], vvar, vmode,
                                          cache[key], args, flush, peaks, n_acc)
+
+    if rank == 0 and world == 1 and not args.no_variants and not args.no_surrogate:
         del cache
+        torch.cuda.empty_cache()
+        variants["surrogate_gg_ttgg"] = surrogate_study(args, steps=min(args.steps, 5), warmup=2)
+        variants["surrogate_gg_ttgg"]["network_inference"]["hidden_layer_frac_of_bf16_peak"] = (
+            variants["surrogate_gg_ttgg"]["network_inference"]["hidden_layer_tflops"] / bf16_peak())
 
     lhe = None
     if rank == 0 and world == 1 and not args.no_e2e:
@@ -543,11 +560,13 @@ def write_event_file(path, process, mom, w):
     with open(path, "w") as f:
         f.write('<LesHouchesEvents version="3.0">\n<header>\n</header>\n<init>\n'
                 "2212 2212 6.5e3 6.5e3 0 0 0 0 3 1\n1.0 0.1 1.0 1\n</init>\n")
+        ml = mom.tolist()  # Python floats: repr is the shortest exact decimal form
+        wl_ = w.tolist()
         for e in range(E):
-            lines = [f"<event>\n{N} 1 {w[e]!r} 91.188 7.546771e-03 1.18e-01"]
+            lines = [f"<event>\n{N} 1 {wl_[e]!r} 91.188 7.546771e-03 1.18e-01"]
             for i in range(N):
-                lines.append(f" {codes[i]} {st[i]} 0 0 0 0 {mom[i, 1, e]!r} {mom[i, 2, e]!r} {mom[i, 3, e]!r} "
-                             f"{mom[i, 0, e]!r} 0.0 0. 9.")
+                lines.append(f" {codes[i]} {st[i]} 0 0 0 0 {ml[i][1][e]!r} {ml[i][2][e]!r} {ml[i][3][e]!r} "
+                             f"{ml[i][0][e]!r} 0.0 0. 9.")
             lines.append("</event>\n")
             f.write("\n".join(lines))
         f.write("</LesHouchesEvents>\n")
@@ -623,15 +642,18 @@ def run_e2e(ctx, torch, dev, mom_h, w_h, E, P, N, world, args):
             "d2h_bytes_per_step": int(8 * (P * E + P + 2)), "ms_per_step": 1e3 * t, "steps": steps}
 
 
-def run_surrogate(args):
+def surrogate_study(args, train_events=1 << 20, train_steps=16000, infer_events=1 << 22, steps=5, warmup=2):
     """Learned surrogate (g g -> t tbar g g, m_t = kappa 173 GeV): exact FP32
-    labels log r on a 16-point kappa grid in [0.8, 1.2] for --train-events
-    events, MLP (24 momentum components + kappa + 15 invariants -> 4 x 256 SiLU
-    -> (mu, s)) trained by the library's kernels, error threshold calibrated on
-    held-out events for a 0.1 % violation rate of |d log r| <= 1e-3, then
-    --infer-events unseen events at kappa = 0.9, 1.1, 1.2 reweighted by the
-    surrogate with exact fallback; the exact FP32 path on the same events and
-    points is the comparison and the judge of every accepted event."""
+    labels log r on a 16-point kappa grid in [0.8, 1.2] for train_events
+    events (16 x train_events labels), MLP (24 momentum components + kappa + 15
+    invariants -> 4 x 256 SiLU -> (mu, s)) trained by the library's kernels
+    (hidden layers' forward on the tcgen05 tensor cores), error threshold
+    calibrated on 16,384 held-out events for a 0.1 % violation rate of
+    |d log r| <= 1e-3, then infer_events unseen events at kappa = 0.9, 1.1, 1.2
+    reweighted by the surrogate with exact fallback; the exact FP32 path on
+    the same events and points is the comparison and the judge of every
+    accepted event.  Also: the network's inference throughput alone on the
+    inference rows (events x points) and its hidden-layer TFLOP/s."""
     import torch
     from paper_2312_07440_gb300 import rwgt
     dev = torch.device("cuda", 0)
@@ -667,22 +689,23 @@ def run_surrogate(args):
         return x, y
 
     t0 = time.perf_counter()
-    mom_tr, w_tr = ev.generate(wl, args.train_events)
-    mom_ca, w_ca = ev.generate(wl, 16384, start=args.train_events)
+    mom_tr, w_tr = ev.generate(wl, train_events)
+    mom_ca, w_ca = ev.generate(wl, 16384, start=train_events)
     x_tr, y_tr = labelled(mom_tr, w_tr, grid)
     x_ca, y_ca = labelled(mom_ca, w_ca, grid)
+    del mom_tr, w_tr
     t_labels = time.perf_counter() - t0
     tau = float(y_tr.std())
     m = rwgt.Mlp(0, st, n_in, hidden, layers, batch, seed=2024)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for frac, lr in ((0.4, 1e-3), (0.3, 3e-4), (0.2, 1e-4), (0.1, 3e-5)):
-        m.train(x_tr, y_tr, batch, int(frac * args.train_steps), lr, tau, 0.05, seed=31)
-    torch.cuda.synchronize()
+        m.train(x_tr, y_tr, batch, int(frac * train_steps), lr, tau, 0.05, seed=31)
+    m.status()
     t_train = time.perf_counter() - t0
     out = torch.empty((x_ca.shape[0], 2), dtype=torch.float32, device=dev)
     m.forward(x_ca, out)
-    torch.cuda.synchronize()
+    m.status()
     o = out.cpu().numpy()
     dk = np.repeat(kg - 1.0, 16384)
     mu, s_err, yl = dk * o[:, 0], o[:, 1] + np.log(np.abs(dk)), dk * y_ca.cpu().numpy()
@@ -690,11 +713,13 @@ def run_surrogate(args):
     bad = np.cumsum(np.abs(mu - yl)[order] > 1e-3)
     okk = np.nonzero(bad <= 1e-3 * np.arange(1, len(order) + 1))[0]
     s_max = float(s_err[order][okk[-1]]) if okk.size else -1e30
+    calib_err = np.abs(mu - yl)
+    n_labels = int(x_tr.shape[0])
     del x_tr, y_tr
     # inference: surrogate + exact fallback vs exact, same events and points
     pts = np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in (0.9, 1.1, 1.2)])
     P = pts.shape[0]
-    mom_te, w_te = ev.generate(wl, args.infer_events, start=args.train_events + 16384)
+    mom_te, w_te = ev.generate(wl, infer_events, start=train_events + 16384)
     E = mom_te.shape[-1]
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
     with rwgt.Context(0, st) as c:
@@ -702,49 +727,79 @@ def run_surrogate(args):
         c.autotune(max_events=1 << 16)
         w_ex = torch.empty((P, E), dtype=torch.float64, device=dev)
         t_ex = []
-        for i in range(args.warmup + args.steps):
+        for i in range(warmup + steps):
             flush.fill_(1)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             c.reweight_async(w_ex)
             sig_ex, _, _, _ = c.get_results(P)
-            if i >= args.warmup:
+            if i >= warmup:
                 t_ex.append(time.perf_counter() - t1)
         sb = c.surrogate_workspace_bytes(n_in)
         sws = torch.empty(sb, dtype=torch.uint8, device=dev)
         w_su = torch.empty((P, E), dtype=torch.float64, device=dev)
         flag = torch.empty((P, E), dtype=torch.uint8, device=dev)
         t_su = []
-        for i in range(args.warmup + args.steps):
+        for i in range(warmup + steps):
             flush.fill_(1)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             sig_su, nfb = rwgt.surrogate_reweight(c, m, p_scale, k_scale, s_max, w_su, flag, P, sws, sb)
-            if i >= args.warmup:
+            if i >= warmup:
                 t_su.append(time.perf_counter() - t1)
-        del keep
+        # the network alone on the inference rows (features of every event and point)
+        xi = torch.empty((P * E, n_in), dtype=torch.float32, device=dev)
+        rwgt.surrogate_features(c, n_in, p_scale, k_scale, None, xi, None)
+        oi = torch.empty((P * E, 2), dtype=torch.float32, device=dev)
+        t_nn = []
+        for i in range(warmup + steps):
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record()
+            m.forward(xi, oi)
+            b_.record()
+            torch.cuda.synchronize()
+            if i >= warmup:
+                t_nn.append(a_.elapsed_time(b_) * 1e-3)
+        m.status()
+        del keep, xi, oi
     fl = flag.cpu().numpy().astype(bool)
     a, b = w_su.cpu().numpy(), w_ex.cpu().numpy()
     err = np.abs(np.log(a[~fl] / b[~fl])) if (~fl).any() else np.zeros(0)
-    t_ex_s, t_su_s = statistics.median(t_ex), statistics.median(t_su)
-    line = {
-        "metric": METRIC, "value": E * P / t_su_s, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t_su_s, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16 MLP (fp32 first/last layers) + f32 exact fallback", "data": "synthetic",
-        "config": {"workload": "surrogate gg_ttgg", "infer_events": E, "points_kappa": [0.9, 1.1, 1.2],
-                   "train_events": args.train_events, "train_labels": int(args.train_events * 16),
-                   "train_steps": args.train_steps, "batch": batch, "mlp": f"{n_in}->{layers}x{hidden} SiLU->2",
-                   "error_bound": "|d log r| <= 1e-3, calibrated for 0.1 % violations on 16384 held-out events"},
-        "surrogate": {"exact_value": E * P / t_ex_s, "gain_vs_exact": t_ex_s / t_su_s,
-                      "fallback_fraction": float(fl.mean()), "accepted_violation_rate":
-                          float(np.mean(err > 1e-3)) if err.size else 0.0,
-                      "accepted_err_max": float(err.max()) if err.size else 0.0,
-                      "sigma_rel_diff": [float(x / y - 1) for x, y in zip(sig_su, sig_ex)],
-                      "label_seconds": t_labels, "train_seconds": t_train, "s_max": s_max},
-        "timing": "wall clock per step incl. host sync (both paths), L2 flushed before each step",
-    }
-    print(json.dumps(line), flush=True)
+    t_ex_s, t_su_s, t_nn_s = statistics.median(t_ex), statistics.median(t_su), min(t_nn)
+    rows = P * E
+    hidden_flops = rows * 2 * hidden * hidden * (layers - 1)
     m.close()
+    return {
+        "workload": "surrogate gg_ttgg", "infer_events": E, "points_kappa": [0.9, 1.1, 1.2],
+        "value": E * P / t_su_s, "unit": UNIT, "ms_per_step": 1e3 * t_su_s,
+        "dtype": "bf16 MLP (fp32 first/last layers) + f32 exact fallback",
+        "train_events": train_events, "train_labels": n_labels, "train_steps": train_steps, "batch": batch,
+        "mlp": f"{n_in}->{layers}x{hidden} SiLU->2",
+        "error_bound": "|d log r| <= 1e-3, calibrated for 0.1 % violations on 16384 held-out events x 16 kappa",
+        "exact_value": E * P / t_ex_s, "exact_ms": 1e3 * t_ex_s, "gain_vs_exact": t_ex_s / t_su_s,
+        "fallback_fraction": float(fl.mean()), "accepted_fraction": float(1.0 - fl.mean()),
+        "accepted_violation_rate": float(np.mean(err > 1e-3)) if err.size else 0.0,
+        "accepted_err_max": float(err.max()) if err.size else 0.0,
+        "held_out_abs_dlogr_median": float(np.median(calib_err)),
+        "held_out_abs_dlogr_p90": float(np.quantile(calib_err, 0.9)),
+        "sigma_rel_diff": [float(x / y - 1) for x, y in zip(sig_su, sig_ex)],
+        "label_seconds": t_labels, "train_seconds": t_train, "s_max": s_max,
+        "network_inference": {"rows": rows, "ms": 1e3 * t_nn_s, "rows_per_s": rows / t_nn_s,
+                              "hidden_layer_tflops": hidden_flops / t_nn_s / 1e12,
+                              "hidden_layer_frac_of_bf16_peak": None},
+        "timing": "wall clock per step incl. host sync (both paths), L2 flushed before each step; the network "
+                  "alone timed with CUDA events",
+    }
+
+
+def run_surrogate(args):
+    """The surrogate study as its own bench line (--surrogate)."""
+    r = surrogate_study(args, args.train_events, args.train_steps, args.infer_events, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic",
+            "config": {"workload": "surrogate gg_ttgg", "infer_events": r["infer_events"]}, "surrogate": r}
+    print(json.dumps(line), flush=True)
 
 
 def scan_points(wl, n):

@@ -73,7 +73,7 @@ extern "C" {
 #define RW_FP64 0       /* FP64 amplitudes and colour sum */
 #define RW_FP32 1       /* FP32 amplitudes and colour sum */
 #define RW_MIXED_FP16 2 /* FP32 amplitudes, colour sum on the tensor cores in FP16 (power-of-two
-                           scaled rows) with FP32 accumulation; QCD processes; blocks <= 128 */
+                           scaled rows) with FP32 accumulation; QCD processes */
 #define RW_MIXED_BF16 3 /* as RW_MIXED_FP16 with BF16 operands */
 
 #define RW_MAX_POINTS 256

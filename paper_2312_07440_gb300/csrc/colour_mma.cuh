@@ -2,12 +2,13 @@
 //
 // Each of the 32 lanes of a warp holds the K colour-ordered amplitudes J of
 // one (event, helicity).  The warp stages them as 64 real rows (Re J, Im J per
-// lane) of FP16 or BF16 in shared memory, scaled per lane by an exact power
-// of two so that max |J_k| lies in [0.5, 1) (FP16 range), multiplies the
-// 64 x KP block by the integer colour matrix C_int (K x K, every entry exact
-// in FP16 and BF16) with mma.sync m16n8k16 and FP32 accumulation, and forms
-// each row's dot product J16 . (C J16) from the A and D fragments the thread
-// already holds.  Since C is real and symmetric,
+// lane) of FP16 or BF16 in shared memory (16-byte stores), scaled per lane by
+// an exact power of two so that max |J_k| lies in [0.5, 1) (FP16 range),
+// reads them back as A fragments with ldmatrix, multiplies the 64 x KP block
+// by the integer colour matrix C_int (K x K, every entry exact in FP16 and
+// BF16) with mma.sync m16n8k16 and FP32 accumulation, and forms each row's
+// dot product J16 . (C J16) of the rounded, scaled amplitudes J16 from the A
+// and D fragments the thread already holds.  Since C is real and symmetric,
 //   J^dagger C J = (Re J)^T C (Re J) + (Im J)^T C (Im J),
 // the lane's result is the sum of its two rows, unscaled by 2^(2e).
 // Error: the rounding of J to 11 (FP16) or 8 (BF16) significant bits, i.e. a
@@ -60,15 +61,29 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], 
 }
 
 // Shared staging for one warp: 64 rows x LDS 16-bit words, then 64 row sums.
+// LDS = KP + 8 keeps every row 16-byte aligned and makes the eight rows an
+// ldmatrix reads at a time fall into distinct bank groups.  The stages of a
+// block's warps sit in its dynamic shared memory right after the amplitude
+// code's current store (the kernel accounts per_thread bytes per thread).
 template <int KP>
 struct ColourStage {
-  static constexpr int LDS = KP + 8;  // row stride (words): +16 B breaks bank conflicts
+  static constexpr int LDS = KP + 8;
   unsigned short j[64 * LDS];
   float row[64];
+  static constexpr int bytes = 64 * LDS * 2 + 64 * 4;
+  static_assert(bytes % 32 == 0, "a whole number of bytes per thread of the warp");
+  static constexpr int per_thread = bytes / 32;
 };
 
+__device__ __forceinline__ void ldmatrix_x4(unsigned (&r)[4], const void* row_addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"((unsigned)__cvta_generic_to_shared(row_addr)));
+}
+
 // The tensor-core colour sum of one process.  CI: the integer colour matrix
-// (K x K, row-major, device memory).  Construct once per amplitude call (B
+// (K x K, row-major, device memory); js: the amplitude code's shared bytes
+// per thread that precede the stages.  Construct once per amplitude call (B
 // fragments kept in registers); sum() is warp-synchronous.
 template <int K, int CM>
 struct ColourMma {
@@ -79,14 +94,18 @@ struct ColourMma {
   static constexpr int LDS = Stage::LDS;
   unsigned bf[KT][NT][2];
   int l, g, c;
+  Stage* st;
 
   // B fragments of C_int (col-major K x N): b0,b1 = rows 2c, 2c+1 of column g;
   // b2,b3 = rows 2c+8, 2c+9 (zero outside K x K).
-  __device__ __forceinline__ explicit ColourMma(const short* __restrict__ CI) {
+  __device__ __forceinline__ ColourMma(const short* __restrict__ CI, int js) {
     l = threadIdx.x & 31;
     g = l >> 2;
     c = l & 3;
+    st = nullptr;
     if (!CI) return;  // FMA colour sum: nothing to stage
+    extern __shared__ __align__(16) unsigned char rw_dyn_bytes[];
+    st = reinterpret_cast<Stage*>(rw_dyn_bytes + (size_t)js * blockDim.x) + (threadIdx.x >> 5);
 #pragma unroll
     for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
@@ -101,10 +120,10 @@ struct ColourMma {
         }
   }
 
-  // this lane's sum_{i,j} C_int_ij Re(J_i^* J_j)
+  // this lane's sum_{i,j} C_int_ij Re(J16_i^* J16_j) with J16 the scaled,
+  // rounded amplitudes, unscaled again
   __device__ __forceinline__ float sum(const cx<float> (&J)[K]) const {
-    __shared__ __align__(16) Stage stage_all[4];  // blocks of at most 128 threads
-    Stage& st = stage_all[threadIdx.x >> 5];
+    Stage& S = *st;
     // per-lane power-of-two scale: max |J| -> [0.5, 1)
     float mx = 0.0f;
 #pragma unroll
@@ -112,28 +131,31 @@ struct ColourMma {
     int e = 0;
     if (mx > 0.0f && isfinite(mx)) frexpf(mx, &e);
     const float sc = ldexpf(1.0f, -e);
+    // rows 2l (Re J) and 2l+1 (Im J), 16 bytes at a time
+    unsigned re[KP / 2], im[KP / 2];
 #pragma unroll
     for (int k = 0; k < KP; k += 2) {
-      const unsigned re = (unsigned)(k < K ? to_16<CM>(J[k].r * sc) : 0) |
-                          ((unsigned)(k + 1 < K ? to_16<CM>(J[k + 1].r * sc) : 0) << 16);
-      const unsigned im = (unsigned)(k < K ? to_16<CM>(J[k].i * sc) : 0) |
-                          ((unsigned)(k + 1 < K ? to_16<CM>(J[k + 1].i * sc) : 0) << 16);
-      *reinterpret_cast<unsigned*>(&st.j[(2 * l) * LDS + k]) = re;
-      *reinterpret_cast<unsigned*>(&st.j[(2 * l + 1) * LDS + k]) = im;
+      re[k / 2] = (unsigned)(k < K ? to_16<CM>(J[k].r * sc) : 0) |
+                  ((unsigned)(k + 1 < K ? to_16<CM>(J[k + 1].r * sc) : 0) << 16);
+      im[k / 2] = (unsigned)(k < K ? to_16<CM>(J[k].i * sc) : 0) |
+                  ((unsigned)(k + 1 < K ? to_16<CM>(J[k + 1].i * sc) : 0) << 16);
+    }
+    uint4* rr = reinterpret_cast<uint4*>(&S.j[(2 * l) * LDS]);
+    uint4* ri = reinterpret_cast<uint4*>(&S.j[(2 * l + 1) * LDS]);
+#pragma unroll
+    for (int q = 0; q < KP / 8; ++q) {
+      rr[q] = make_uint4(re[4 * q], re[4 * q + 1], re[4 * q + 2], re[4 * q + 3]);
+      ri[q] = make_uint4(im[4 * q], im[4 * q + 1], im[4 * q + 2], im[4 * q + 3]);
     }
     __syncwarp();
 #pragma unroll
     for (int mt = 0; mt < 4; ++mt) {
       const int r0 = mt * 16 + g, r1 = r0 + 8;
+      // A fragments: lanes 0-15 address rows mt*16 + (0..15) at k0, lanes
+      // 16-31 the same rows at k0 + 8 -> (a0, a1, a2, a3) of m16n8k16
       unsigned af[KT][4];
 #pragma unroll
-      for (int kt = 0; kt < KT; ++kt) {
-        const int k0 = kt * 16 + 2 * c;
-        af[kt][0] = *reinterpret_cast<const unsigned*>(&st.j[r0 * LDS + k0]);
-        af[kt][1] = *reinterpret_cast<const unsigned*>(&st.j[r1 * LDS + k0]);
-        af[kt][2] = *reinterpret_cast<const unsigned*>(&st.j[r0 * LDS + k0 + 8]);
-        af[kt][3] = *reinterpret_cast<const unsigned*>(&st.j[r1 * LDS + k0 + 8]);
-      }
+      for (int kt = 0; kt < KT; ++kt) ldmatrix_x4(af[kt], &S.j[(mt * 16 + (l & 15)) * LDS + kt * 16 + (l >> 4) * 8]);
       float p0 = 0.0f, p1 = 0.0f;  // row partial dots (rows r0, r1)
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
@@ -151,12 +173,12 @@ struct ColourMma {
       p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
       p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
       if (c == 0) {
-        st.row[r0] = p0;
-        st.row[r1] = p1;
+        S.row[r0] = p0;
+        S.row[r1] = p1;
       }
     }
     __syncwarp();
-    const float v = st.row[2 * l] + st.row[2 * l + 1];
+    const float v = S.row[2 * l] + S.row[2 * l + 1];
     __syncwarp();  // the stage is reused by the next call
     return ldexpf(v, 2 * e);
   }

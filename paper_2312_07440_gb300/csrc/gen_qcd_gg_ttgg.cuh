@@ -26,7 +26,7 @@ static __device__ const short CI[K * K] = {512, -64, -64, 8, 8, 80, -64, 8, 8, -
 template <class R, int LB, int CM = CM_FMA, bool JS = false>
 __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
   static_assert(CM == CM_FMA || sizeof(R) == 4, "tensor-core colour sum takes FP32 amplitudes");
-  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI);
+  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI, JS ? NJS * 32 : 0);
   JStore<R, NJS, JS> js;
   R acc = R(0);
   [[maybe_unused]] R cz0_0 = R(0), cz0_1 = R(0), cz0_2 = R(0), cz0_3 = R(0), cz1_0 = R(0), cz1_1 = R(0), cz1_2 = R(0), cz1_3 = R(0);

@@ -12,6 +12,7 @@ struct Tag {
   static constexpr int NEXT = gg_tt::NEXT;
   static constexpr int MAX_LB = gg_tt::MAX_LB;
   static constexpr int NJS = gg_tt::NJS;
+  static constexpr int NCOL = gg_tt::K;
   static constexpr bool JSMEM = false;  // currents of 3+ gluons in shared memory (FP32)
   template <class R, int LB, int CM>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {

@@ -13,6 +13,7 @@ struct Tag {
   static constexpr int NEXT = gg_tt::NEXT;
   static constexpr int MAX_LB = gg_tt::MAX_LB;
   static constexpr int NJS = gg_tt::NJS;
+  static constexpr int NCOL = gg_tt::K;
   static constexpr bool JSMEM = false;  // currents of 3+ gluons in shared memory (FP32)
   template <class R, int LB, int CM>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
@@ -24,10 +25,10 @@ using PB16 = QcdProc<Tag, CM_BF16>;
 }  // namespace
 
 void register_gg_tt_mixed(std::vector<KernelEntry>& t) {
-  t.push_back({RW_GG_TT, RW_MIXED_FP16, 0, (const void*)&k_reweight<P16, float, 0, 2>, 128});
-  t.push_back({RW_GG_TT, RW_MIXED_BF16, 0, (const void*)&k_reweight<PB16, float, 0, 2>, 128});
-  t.push_back({RW_GG_TT, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1, 2>, 128});
-  t.push_back({RW_GG_TT, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1, 2>, 128});
+  t.push_back({RW_GG_TT, RW_MIXED_FP16, 0, (const void*)&k_reweight<P16, float, 0, 2>, 256, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TT, RW_MIXED_BF16, 0, (const void*)&k_reweight<PB16, float, 0, 2>, 256, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TT, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1, 2>, 256, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TT, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1, 2>, 256, 0, PB16::jstore_bytes<float>()});
 }
 
 }  // namespace rw

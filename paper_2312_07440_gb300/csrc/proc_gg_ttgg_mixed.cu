@@ -13,6 +13,7 @@ struct Tag {
   static constexpr int NEXT = gg_ttgg::NEXT;
   static constexpr int MAX_LB = gg_ttgg::MAX_LB;
   static constexpr int NJS = gg_ttgg::NJS;
+  static constexpr int NCOL = gg_ttgg::K;
   static constexpr bool JSMEM = true;  // currents of 3+ gluons in shared memory (FP32)
   template <class R, int LB, int CM>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
@@ -24,14 +25,14 @@ using PB16 = QcdProc<Tag, CM_BF16>;
 }  // namespace
 
 void register_gg_ttgg_mixed(std::vector<KernelEntry>& t) {
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1>, 128, 0, P16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1>, 128, 0, PB16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 2, (const void*)&k_reweight<P16, float, 2>, 128, 0, P16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 2, (const void*)&k_reweight<PB16, float, 2>, 128, 0, PB16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 3, (const void*)&k_reweight<P16, float, 3>, 128, 0, P16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 4, (const void*)&k_reweight<P16, float, 4>, 128, 0, P16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 3, (const void*)&k_reweight<PB16, float, 3>, 128, 0, PB16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 4, (const void*)&k_reweight<PB16, float, 4>, 128, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1>, 256, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1>, 256, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 2, (const void*)&k_reweight<P16, float, 2>, 256, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 2, (const void*)&k_reweight<PB16, float, 2>, 256, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 3, (const void*)&k_reweight<P16, float, 3>, 256, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 4, (const void*)&k_reweight<P16, float, 4>, 256, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 3, (const void*)&k_reweight<PB16, float, 3>, 256, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 4, (const void*)&k_reweight<PB16, float, 4>, 256, 0, PB16::jstore_bytes<float>()});
 }
 
 }  // namespace rw

@@ -18,6 +18,7 @@ namespace {
     static constexpr int NEXT = ns::NEXT;                                                                \
     static constexpr int MAX_LB = ns::MAX_LB;                                                            \
     static constexpr int NJS = ns::NJS;                                                                  \
+    static constexpr int NCOL = ns::K;                                                                   \
     static constexpr bool JSMEM = jsmem;                                                                 \
     template <class R, int LB, int CM>                                                                   \
     __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) { \

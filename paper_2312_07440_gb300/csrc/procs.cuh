@@ -3,6 +3,7 @@
 #pragma once
 #include <type_traits>
 
+#include "colour_mma.cuh"
 #include "helas.cuh"
 #include "kernels.cuh"
 #include "qcd.cuh"
@@ -24,10 +25,12 @@ struct QcdProc {
   // Momenta: FP64 in FP64 mode, double-float in the FP32 modes (dfloat.cuh).
   template <class R>
   using mom_t = typename std::conditional<sizeof(R) == 8, double, df>::type;
-  // dynamic shared memory per thread of the amplitude code (the current store)
+  // dynamic shared memory per thread of the amplitude code: the current store,
+  // then (tensor-core colour sum) the warp's colour staging, as a per-thread share
   template <class R>
   static constexpr int jstore_bytes() {
-    return (Tag::JSMEM && sizeof(R) == 4) ? Tag::NJS * 32 : 0;
+    return ((Tag::JSMEM && sizeof(R) == 4) ? Tag::NJS * 32 : 0) +
+           (CM != CM_FMA ? ColourStage<(Tag::NCOL + 15) / 16 * 16>::per_thread : 0);
   }
 
   template <class R, int LB>

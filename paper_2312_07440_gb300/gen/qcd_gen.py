@@ -267,7 +267,7 @@ def emit_process(name, n, outgoing_gluons, n_identical, hoist_weyl=True, share_f
     w("template <class R, int LB, int CM = CM_FMA, bool JS = false>")
     w("__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {")
     w("  static_assert(CM == CM_FMA || sizeof(R) == 4, \"tensor-core colour sum takes FP32 amplitudes\");")
-    w("  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI);")
+    w("  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI, JS ? NJS * 32 : 0);")
     w("  JStore<R, NJS, JS> js;")
     w("  R acc = R(0);")
     # Colour sum by FMA.  Up to PAIRS_MAX_K orderings: sum over the pairs

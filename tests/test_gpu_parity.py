@@ -21,7 +21,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from paper_2312_07440_gb300 import rwgt  # noqa: E402
-from parity_helpers import TOL, check_against_oracle, rel  # noqa: E402
+from parity_helpers import POINT_SETS, TOL, check_against_oracle, rel  # noqa: E402
 
 DEV = torch.device("cuda", 0)
 
@@ -397,12 +397,15 @@ def test_mixed_precision_colour_sum(mode, proc, wl, n, lbs, pts):
         assert rel(g["me0"], o["me0"]).mean() < b / 4
 
 
-def test_mixed_modes_reject_large_blocks():
-    with rwgt.Context(0) as c:
-        c.set_process("gg_ttg", "mixed_fp16")
-        with pytest.raises(rwgt.RwError) as e:
-            c.set_tuning(0, 256)
-        assert e.value.code == -2
+@pytest.mark.parametrize("block", [32, 256])
+def test_mixed_modes_every_block_size(block):
+    """Each warp's colour staging lives in the block's dynamic shared memory,
+    so the tensor-core colour sum runs with any block size."""
+    pts = POINT_SETS["gg_ttg_mt4"]()
+    mom, w, o = oracle_run("gg_ttg", "gg_ttg_4m", 611, pts)
+    b = mixed_bound("mixed_fp16", 3)
+    g = run_gpu("gg_ttg", "mixed_fp16", mom, w, pts, lane_bits=1, block=block)
+    assert rel(g["me0"], o["me0"]).max() < b and rel(g["me"], o["me"]).max() < b
 
 
 # --------------------------------------------------------------------------
