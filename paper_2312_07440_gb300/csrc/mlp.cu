@@ -162,6 +162,65 @@ __global__ void k_dense_in(const float* __restrict__ X, int B, int nin, const fl
   H[t] = f2bf(z * sigmoidf_(z));
 }
 
+// The same first layer, register-blocked for hidden = 256 and n_in <= 64:
+// a block of 256 threads computes 64 rows x 256 units; the weights [n_in][256]
+// and the block's feature rows sit in shared memory, and each thread
+// accumulates 8 rows x 8 consecutive units (64 FMAs per 16 shared loads),
+// then writes 8-unit runs of Z (FP32, when kept) and H (BF16, 16 bytes).
+constexpr int DI_ROWS = 64, DI_N = 256, DI_MAX_IN = 64;
+__global__ void __launch_bounds__(256) k_dense_in_256(const float* __restrict__ X, int B, int nin,
+                                                      const float* __restrict__ W, const float* __restrict__ b,
+                                                      float* __restrict__ Z, bf16* __restrict__ H) {
+  extern __shared__ __align__(16) float di_smem[];
+  float* Ws = di_smem;                      // [nin][256]
+  float* Xs = di_smem + nin * DI_N;         // [DI_ROWS][nin + 1]
+  const int ldx = nin + 1;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const long long r0 = (long long)blockIdx.x * DI_ROWS;
+  for (int i = tid; i < nin * DI_N / 4; i += 256)
+    reinterpret_cast<float4*>(Ws)[i] = __ldg(reinterpret_cast<const float4*>(W) + i);
+  for (int i = tid; i < DI_ROWS * nin; i += 256) {
+    const int r = i / nin, k = i % nin;
+    Xs[r * ldx + k] = r0 + r < B ? __ldg(X + (r0 + r) * nin + k) : 0.0f;
+  }
+  __syncthreads();
+  float acc[8][8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float bj = __ldg(b + tx * 8 + j);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i][j] = bj;
+  }
+  for (int k = 0; k < nin; ++k) {
+    const float4 w0 = reinterpret_cast<const float4*>(Ws + k * DI_N + tx * 8)[0];
+    const float4 w1 = reinterpret_cast<const float4*>(Ws + k * DI_N + tx * 8)[1];
+    const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float xv = Xs[(ty * 8 + i) * ldx + k];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(xv, wv[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const long long r = r0 + ty * 8 + i;
+    if (r >= B) continue;
+    const long long o = r * DI_N + tx * 8;
+    if (Z) {
+      reinterpret_cast<float4*>(Z + o)[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      reinterpret_cast<float4*>(Z + o)[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    }
+    unsigned hw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float z0 = acc[i][2 * j], z1 = acc[i][2 * j + 1];
+      hw[j] = (unsigned)f2bf(z0 * sigmoidf_(z0)) | ((unsigned)f2bf(z1 * sigmoidf_(z1)) << 16);
+    }
+    *reinterpret_cast<uint4*>(H + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  }
+}
+
 // Output layer in FP32 from the last pre-activation: out = SiLU(Z) W + b,
 // W [K][2]; one warp per row.
 __global__ void k_dense_out(const float* __restrict__ Z, int B, int K, const float* __restrict__ W,
@@ -433,8 +492,20 @@ int forward_batch(rw_mlp* m, const float* xf, int B, bool infer = false) {
   const bool tc = tc_usable(m);
   // inference on the tensor-core path reads no pre-activation back
   const bool keep_z = !(infer && tc && L >= 2);
-  k_dense_in<<<(unsigned)(((long long)B * m->hidden + 255) / 256), 256, 0, m->stream>>>(
-      xf, B, m->n_in, m->p + m->w_off[0], m->p + m->b_off[0], m->hidden, keep_z ? m->Z[0] : nullptr, m->H[0]);
+  if (m->hidden == DI_N && m->n_in <= DI_MAX_IN) {
+    const size_t sm = ((size_t)m->n_in * DI_N + (size_t)DI_ROWS * (m->n_in + 1)) * sizeof(float);
+    static bool attr = false;
+    if (!attr && sm > 48 * 1024) {
+      if (cudaFuncSetAttribute(k_dense_in_256, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024) != cudaSuccess)
+        return mlp_fail(m, RW_ERR_CUDA, "first-layer shared memory attribute");
+      attr = true;
+    }
+    k_dense_in_256<<<(unsigned)((B + DI_ROWS - 1) / DI_ROWS), 256, sm, m->stream>>>(
+        xf, B, m->n_in, m->p + m->w_off[0], m->p + m->b_off[0], keep_z ? m->Z[0] : nullptr, m->H[0]);
+  } else {
+    k_dense_in<<<(unsigned)(((long long)B * m->hidden + 255) / 256), 256, 0, m->stream>>>(
+        xf, B, m->n_in, m->p + m->w_off[0], m->p + m->b_off[0], m->hidden, keep_z ? m->Z[0] : nullptr, m->H[0]);
+  }
   for (int l = 1; l < L; ++l) {
     if (tc) {
       tcg::Epi e{};

@@ -24,15 +24,20 @@ using P16 = QcdProc<Tag, CM_FP16>;
 using PB16 = QcdProc<Tag, CM_BF16>;
 }  // namespace
 
+// The current store (768 B) and the colour staging (168 B) per thread fit a
+// 128-thread block's shared memory but not a 256-thread one's (227 KB).
+constexpr int kMaxBlock = 227 * 1024 / P16::jstore_bytes<float>() >= 256 ? 256 : 128;
+static_assert(P16::jstore_bytes<float>() == PB16::jstore_bytes<float>(), "one block limit for both types");
+
 void register_gg_ttgg_mixed(std::vector<KernelEntry>& t) {
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1>, 256, 0, P16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1>, 256, 0, PB16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 2, (const void*)&k_reweight<P16, float, 2>, 256, 0, P16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 2, (const void*)&k_reweight<PB16, float, 2>, 256, 0, PB16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 3, (const void*)&k_reweight<P16, float, 3>, 256, 0, P16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 4, (const void*)&k_reweight<P16, float, 4>, 256, 0, P16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 3, (const void*)&k_reweight<PB16, float, 3>, 256, 0, PB16::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 4, (const void*)&k_reweight<PB16, float, 4>, 256, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 1, (const void*)&k_reweight<P16, float, 1>, kMaxBlock, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 1, (const void*)&k_reweight<PB16, float, 1>, kMaxBlock, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 2, (const void*)&k_reweight<P16, float, 2>, kMaxBlock, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 2, (const void*)&k_reweight<PB16, float, 2>, kMaxBlock, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 3, (const void*)&k_reweight<P16, float, 3>, kMaxBlock, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_FP16, 4, (const void*)&k_reweight<P16, float, 4>, kMaxBlock, 0, P16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 3, (const void*)&k_reweight<PB16, float, 3>, kMaxBlock, 0, PB16::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_MIXED_BF16, 4, (const void*)&k_reweight<PB16, float, 4>, kMaxBlock, 0, PB16::jstore_bytes<float>()});
 }
 
 }  // namespace rw

@@ -105,6 +105,7 @@ struct rw_ctx {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   int lane_bits = -1, block = 0;
+  int smem_optin = 0;  // largest dynamic shared memory a block may opt in to (bytes)
   std::string err;
   double* h_stage = nullptr;  // pinned [RW_MAX_POINTS + 2]
   std::map<std::tuple<const void*, int, size_t>, int> occ;
@@ -127,6 +128,7 @@ int fail(rw_ctx* c, int code, const char* fmt, ...) {
 }
 
 int cuda_fail(rw_ctx* c, cudaError_t e, const char* what) {
+  cudaGetLastError();  // the error is reported here: do not leave it for the caller's next CUDA call
   return fail(c, RW_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
@@ -245,6 +247,9 @@ int shape(rw_ctx* c, int P, Shape& sh) {
   const int block = c->block > 0 ? c->block : 128;
   if (block > k->max_block) return fail(c, RW_ERR_ARG, "block %d above this variant's %d", block, k->max_block);
   const size_t smem = (size_t)k->smem_per_thread * block + (size_t)(block / 32) * (P + 1) * sizeof(double2);
+  if (c->smem_optin > 0 && smem > (size_t)c->smem_optin)
+    return fail(c, RW_ERR_ARG, "block %d needs %zu bytes of shared memory, more than the %d a block may have", block,
+                smem, c->smem_optin);
   auto key = std::make_tuple(k->func, block, smem);
   auto it = c->occ.find(key);
   int per_sm;
@@ -332,6 +337,7 @@ int rw_create(rw_ctx** out, int device, void* stream) {
   c->device = device;
   c->stream = static_cast<cudaStream_t>(stream);
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
       cudaMallocHost(&c->h_stage, sizeof(double) * (RW_MAX_POINTS + 4)) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -829,9 +835,12 @@ extern "C" int rw_reweight_noalloc(rw_ctx* c, const double* d_mom, const double*
   const int block = c->block > 0 ? c->block : 128;
   if (block > k->max_block) return noalloc_fail(c, RW_ERR_ARG, "block too large");
   const size_t smem = (size_t)k->smem_per_thread * block + (size_t)(block / 32) * (P + 1) * sizeof(double2);
+  if (c->smem_optin > 0 && smem > (size_t)c->smem_optin) return noalloc_fail(c, RW_ERR_ARG, "block too large");
   if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
     return noalloc_fail(c, RW_ERR_CUDA, "smem attribute");
+  }
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, block, smem) != cudaSuccess) {
     cudaGetLastError();
@@ -1600,7 +1609,10 @@ int rw_multi_reweight_async(rw_multi* m, void* d_ws, size_t ws_bytes) {
     cudaError_t e = cudaSuccess;
     if (smem > 48 * 1024) e = cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, block, smem);
-    if (e != cudaSuccess) return mfail(m, RW_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return mfail(m, RW_ERR_CUDA, "occupancy: %s", cudaGetErrorString(e));
+    }
     per_sm = std::max(per_sm, 1);
     m->occ[key] = per_sm;
   } else {

@@ -408,6 +408,22 @@ def test_mixed_modes_every_block_size(block):
     assert rel(g["me0"], o["me0"]).max() < b and rel(g["me"], o["me"]).max() < b
 
 
+def test_block_too_large_for_shared_memory_is_an_argument_error():
+    """g g -> t tbar g g in a mixed mode keeps 936 bytes per thread in shared
+    memory: a 256-thread block does not fit, and asking for one is an argument
+    error that leaves the CUDA context clean (the next call and the autotuner's
+    choice run normally)."""
+    pts = POINT_SETS["gg_ttgg_mt"]()[:4]
+    mom, w = ev.generate(ev.WORKLOADS["gg_ttgg_1m"], 64)
+    with pytest.raises(rwgt.RwError) as x:
+        run_gpu("gg_ttgg", "mixed_bf16", mom, w, pts, lane_bits=1, block=256)
+    assert x.value.code == -2
+    torch.cuda.synchronize()
+    assert float(torch.ones(4, device=DEV).sum()) == 4.0
+    g = run_gpu("gg_ttgg", "mixed_bf16", mom, w, pts, lane_bits=1, block=128)
+    assert np.all(np.isfinite(g["me0"])) and g["n_bad"] == 0
+
+
 # --------------------------------------------------------------------------
 # CUDA-graph batching: several processes and point sets in one replay
 # --------------------------------------------------------------------------
