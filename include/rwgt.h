@@ -253,7 +253,12 @@ int rw_mlp_info(const rw_mlp* m, int* n_in, int* hidden, int* n_layers, void** c
 /* checkpoint / resume: FP32 parameters, Adam moments (may be NULL) and step */
 int rw_mlp_get_state(rw_mlp* m, float* h_params, float* h_m1, float* h_m2, int64_t* h_step);
 int rw_mlp_set_state(rw_mlp* m, const float* h_params, const float* h_m1, const float* h_m2, int64_t step);
-/* out [n][2] = (mu, s) for features x [n][n_in] (device, FP32) */
+/* out [n][2] = (mu, s) for features x [n][n_in] (device, FP32).  With GEMM
+   kind 0, hidden = 256, n_in <= 40 and n_layers <= 8 the whole network runs
+   in one persistent tensor-core kernel for all n rows (activations stay in
+   shared memory; the input layer as one BF16 MMA over the split operands
+   [x_h | x_l | x_h] . [W_h ; W_h ; W_l], i.e. FP32 up to ~2^-16 relative; the
+   last activation is not rounded to BF16), else max_batch rows at a time. */
 int rw_mlp_forward(rw_mlp* m, const float* d_x, int64_t n, float* d_out);
 /* loss and its gradient at the current parameters for n <= max_batch rows
    (no update): loss = mean ((y-mu)/tau)^2 + lam (r^2 e^{-2s}/2 + s), r = y - mu
@@ -269,9 +274,11 @@ int rw_mlp_train(rw_mlp* m, const float* d_x, const float* d_y, int64_t n, int b
    default) runs them on the 5th-generation tensor cores -- tcgen05.mma fed by
    TMA, FP32 accumulators in tensor memory, bias + SiLU fused into the
    epilogue and, in rw_mlp_forward, the output layer fused into the last
-   hidden layer -- whenever hidden is a multiple of 64 and at most 256;
-   kind 1 uses the mma.sync kernel for every layer.  Both compute the same
-   products of the same BF16 operands in FP32. */
+   hidden layer -- whenever hidden is a multiple of 64 and at most 256, and
+   inference of the whole network in one kernel where rw_mlp_forward allows;
+   kind 2 is kind 0 with inference layer by layer (FP32 input layer); kind 1
+   uses the mma.sync kernel for every layer.  The hidden layers compute the
+   same products of the same BF16 operands in FP32 on every path. */
 int rw_mlp_set_gemm(rw_mlp* m, int kind);
 /* Synchronise the model's stream and report a tensor-core pipeline wait that
    gave up (RW_ERR_CUDA; the kernel then stops early and its results are

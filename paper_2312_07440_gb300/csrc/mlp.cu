@@ -31,6 +31,7 @@
 
 #include "../../include/rwgt.h"
 #include "gemm_tc.cuh"
+#include "mlp_infer_tc.cuh"
 
 namespace {
 
@@ -322,6 +323,33 @@ __global__ void k_transpose_bf16(const float* __restrict__ W, int K, int N, bf16
   Wt[t] = f2bf(W[(long long)k * N + n]);
 }
 
+// The inference kernel's weights: k-block g, row n, column k of
+//   g < kb0:  the split input layer [W_h ; W_h ; W_l ; 0] along k (rows of
+//             W_0 [nin][256]: W_h = bf16(W), W_l = bf16(W - W_h)),
+//   g >= kb0: W_l^T of hidden layer l = 1 + (g - kb0) / 4 in BF16.
+struct PackArgs {
+  const float* W[tcg::inf::MAX_LAYERS];
+  int nin, kb0, n_kb;
+};
+__global__ void k_pack_infer(const PackArgs a, bf16* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)a.n_kb * 256 * 64) return;
+  const int k = (int)(t & 63), n = (int)((t >> 6) & 255), g = (int)(t >> 14);
+  float v = 0.0f;
+  if (g < a.kb0) {
+    const int c = g * 64 + k, f = c % a.nin, part = c / a.nin;
+    if (part < 3) {
+      const float w = a.W[0][(long long)f * 256 + n];
+      const float wh = __bfloat162float(__float2bfloat16_rn(w));
+      v = part == 2 ? w - wh : wh;
+    }
+  } else {
+    const int l = 1 + (g - a.kb0) / 4, kk = ((g - a.kb0) % 4) * 64 + k;
+    v = a.W[l][(long long)kk * 256 + n];
+  }
+  out[t] = f2bf(v);
+}
+
 // rows idx[b] of X [*][nin] (FP32) -> Xf [B][nin] (FP32) and Xb (BF16), y[idx[b]] -> yb[b]
 __global__ void k_gather_rows(const float* __restrict__ X, const float* __restrict__ y, const int64_t* __restrict__ idx,
                               int B, int nin, float* __restrict__ Xf, bf16* __restrict__ Xb, float* __restrict__ yb) {
@@ -377,8 +405,13 @@ struct rw_mlp {
   // tensor-core forward: transposed BF16 hidden weights [l][N][K] (layer l at
   // (l - 1) hidden^2), its error flag, and the GEMM choice
   bf16* wt = nullptr;
+  // whole-network inference kernel: weight k-blocks [kb][256 n][64 k] BF16 in
+  // the order the MMAs take them (the split input layer's kb0, then 4 per
+  // hidden layer)
+  bf16* wpack = nullptr;
+  int kb0 = 0;
   int* tc_err = nullptr;
-  int gemm = 0;  // 0: tcgen05 where the shape allows, 1: mma.sync everywhere
+  int gemm = 0;  // 0: tcgen05, inference in one kernel; 2: tcgen05 layer by layer; 1: mma.sync everywhere
   int sm_count = 0;
   std::string err;
 };
@@ -423,7 +456,40 @@ bool bf16_map(CUtensorMap* map, const bf16* ptr, long long rows, int cols, int b
 
 // hidden layers on the tensor cores: width a multiple of 64, at most 256
 bool tc_usable(const rw_mlp* m) {
-  return m->gemm == 0 && m->wt && m->hidden % tcg::BK == 0 && m->hidden <= tcg::MAX_N && encode_tiled();
+  return m->gemm != 1 && m->wt && m->hidden % tcg::BK == 0 && m->hidden <= tcg::MAX_N && encode_tiled();
+}
+
+// the whole inference in one kernel: hidden 256, n_in <= 40, at most 8 layers
+bool infer_usable(const rw_mlp* m) { return m->gemm == 0 && m->wpack && encode_tiled(); }
+
+// out [n][2] = MLP(x [n][n_in]) for all n rows in one launch
+int launch_mlp_infer(rw_mlp* m, const float* x, long long n, float* out) {
+  const int L = m->n_layers;
+  CUtensorMap tw;
+  if (!bf16_map(&tw, m->wpack, (long long)(m->kb0 + 4 * (L - 1)) * 256, tcg::BK, 256))
+    return mlp_fail(m, RW_ERR_CUDA, "tensor map encoding");
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(tcg::k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tcg::inf::SMEM_BYTES) != cudaSuccess)
+      return mlp_fail(m, RW_ERR_CUDA, "inference kernel shared memory attribute");
+    attr = true;
+  }
+  tcg::InferArgs a{};
+  a.x = x;
+  for (int l = 0; l < L; ++l) a.bias[l] = m->p + m->b_off[l];
+  a.w_out = m->p + m->w_off[L];
+  a.b_out = m->p + m->b_off[L];
+  a.out = out;
+  a.err = m->tc_err;
+  a.M = n;
+  a.n_in = m->n_in;
+  a.kb0 = m->kb0;
+  a.L = L;
+  const long long pairs = ((n + tcg::BM - 1) / tcg::BM + 1) / 2;
+  const int grid = (int)std::max(1LL, std::min<long long>(pairs, m->sm_count));
+  tcg::k_mlp_infer<<<grid, tcg::THREADS, tcg::inf::SMEM_BYTES, m->stream>>>(tw, a);
+  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "inference kernel launch");
 }
 
 // hidden layer l (1 <= l < n_layers) of B rows: A = bf16 activations [B][hidden]
@@ -452,11 +518,19 @@ int launch_gemm_tc(rw_mlp* m, int l, const bf16* A, int B, tcg::Epi e) {
 
 // transposed BF16 copies of the hidden weights (after any change of p)
 int refresh_wt(rw_mlp* m) {
-  if (!m->wt) return RW_OK;
   const int H = m->hidden;
-  for (int l = 1; l < m->n_layers; ++l)
-    k_transpose_bf16<<<(unsigned)(((long long)H * H + 255) / 256), 256, 0, m->stream>>>(
-        m->p + m->w_off[l], H, H, m->wt + (size_t)(l - 1) * H * H);
+  if (m->wt)
+    for (int l = 1; l < m->n_layers; ++l)
+      k_transpose_bf16<<<(unsigned)(((long long)H * H + 255) / 256), 256, 0, m->stream>>>(
+          m->p + m->w_off[l], H, H, m->wt + (size_t)(l - 1) * H * H);
+  if (m->wpack) {
+    PackArgs a{};
+    for (int l = 0; l < m->n_layers; ++l) a.W[l] = m->p + m->w_off[l];
+    a.nin = m->n_in;
+    a.kb0 = m->kb0;
+    a.n_kb = m->kb0 + 4 * (m->n_layers - 1);
+    k_pack_infer<<<(unsigned)(((long long)a.n_kb * 256 * 64 + 255) / 256), 256, 0, m->stream>>>(a, m->wpack);
+  }
   return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "weight transpose");
 }
 
@@ -677,6 +751,10 @@ int rw_mlp_create(rw_mlp** out, int device, void* stream, int n_in, int hidden, 
                dalloc(&m->tc_err, 1) && cudaMemset(m->tc_err, 0, sizeof(int)) == cudaSuccess;
   if (ok && n_layers >= 2 && hidden % tcg::BK == 0 && hidden <= tcg::MAX_N)
     ok = dalloc(&m->wt, (size_t)(n_layers - 1) * hidden * hidden);
+  if (ok && hidden == tcg::inf::N && n_in <= tcg::inf::MAX_IN && n_layers <= tcg::inf::MAX_LAYERS) {
+    m->kb0 = (3 * n_in + tcg::BK - 1) / tcg::BK;
+    ok = dalloc(&m->wpack, (size_t)(m->kb0 + 4 * (n_layers - 1)) * 256 * 64);
+  }
   if (ok) {
     k_to_bf16<<<(unsigned)((off + 255) / 256), 256, 0, m->stream>>>(m->p, m->pb, off);
     ok = refresh_wt(m) == RW_OK && cudaStreamSynchronize(m->stream) == cudaSuccess;
@@ -696,7 +774,7 @@ int rw_mlp_destroy(rw_mlp* m) {
   for (void* q : {(void*)m->p, (void*)m->g, (void*)m->m1, (void*)m->m2, (void*)m->pb, (void*)m->X, (void*)m->Xf,
                   (void*)m->out,
                   (void*)m->dout_f, (void*)m->dout_b, (void*)m->dA, (void*)m->dB, (void*)m->loss, (void*)m->yb,
-                  (void*)m->idx, (void*)m->wt, (void*)m->tc_err})
+                  (void*)m->idx, (void*)m->wt, (void*)m->wpack, (void*)m->tc_err})
     if (q) cudaFree(q);
   for (auto* h : m->H) cudaFree(h);
   for (auto* z : m->Z) cudaFree(z);
@@ -751,6 +829,7 @@ int rw_mlp_forward(rw_mlp* m, const float* d_x, int64_t n, float* d_out) {
   if (!d_x || !d_out) return mlp_fail(m, RW_ERR_NULL, "NULL buffer");
   if (n <= 0) return mlp_fail(m, RW_ERR_ARG, "n must be > 0");
   cudaSetDevice(m->device);
+  if (infer_usable(m)) return launch_mlp_infer(m, d_x, n, d_out);
   for (int64_t s = 0; s < n; s += m->max_batch) {
     const int B = (int)std::min<int64_t>(m->max_batch, n - s);
     int rc = forward_batch(m, d_x + s * m->n_in, B, true);
@@ -826,7 +905,7 @@ int rw_mlp_train(rw_mlp* m, const float* d_x, const float* d_y, int64_t n, int b
 
 int rw_mlp_set_gemm(rw_mlp* m, int kind) {
   if (!m) return RW_ERR_NULL;
-  if (kind != 0 && kind != 1) return mlp_fail(m, RW_ERR_ARG, "kind must be 0 or 1");
+  if (kind < 0 || kind > 2) return mlp_fail(m, RW_ERR_ARG, "kind must be 0, 1 or 2");
   m->gemm = kind;
   return RW_OK;
 }

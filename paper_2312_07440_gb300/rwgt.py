@@ -623,9 +623,11 @@ class Mlp:
                                           tau, lam, int(seed)), "rw_mlp_train")
 
     def set_gemm(self, kind: str):
-        """Forward GEMMs of the hidden layers: "tcgen05" (5th-generation tensor
-        cores, where the width allows) or "mma_sync" (the legacy path)."""
-        self._check(self.lib.rw_mlp_set_gemm(self.h, {"tcgen05": 0, "mma_sync": 1}[kind]), "rw_mlp_set_gemm")
+        """Forward GEMMs: "tcgen05" (5th-generation tensor cores; inference of
+        the whole network in one kernel where the shape allows), "tcgen05_layers"
+        (tensor cores, one kernel per layer) or "mma_sync" (the legacy path)."""
+        self._check(self.lib.rw_mlp_set_gemm(self.h, {"tcgen05": 0, "mma_sync": 1, "tcgen05_layers": 2}[kind]),
+                    "rw_mlp_set_gemm")
 
     def status(self):
         """Synchronise and raise if a tensor-core pipeline wait gave up."""
