@@ -25,6 +25,7 @@
 // tensor memory is freed before the kernel returns.
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -157,12 +158,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// SiLU z sigma(z) = z / (1 + e^-z) with the fast exponential and division
-// (a few units in the last place of FP32; the result is rounded to BF16)
-__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+// SiLU z sigma(z) = z / (1 + 2^(-z log2 e)) with the special-function unit's
+// approximate base-2 exponential and reciprocal (each within a few units in
+// the last place of FP32; the result is rounded to BF16).  Below z = -88 the
+// exponential overflows to +inf and the result is -0.
+__device__ __forceinline__ float silu_f(float z) {
+  float e, r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(z * -1.4426950408889634f));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
+  return z * r;
+}
 
 __device__ __forceinline__ unsigned short bf16_bits(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// two FP32 values rounded to BF16 in one word (lo in the low half)
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(const __grid_constant__ CUtensorMap tmA,
@@ -320,8 +334,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(const __grid_constant__ 
           for (int j = 0; j < 2; ++j) {
             uint32_t w[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-              w[i] = (uint32_t)bf16_bits(v[8 * j + 2 * i]) | ((uint32_t)bf16_bits(v[8 * j + 2 * i + 1]) << 16);
+            for (int i = 0; i < 4; ++i) w[i] = bf16x2(v[8 * j + 2 * i], v[8 * j + 2 * i + 1]);
             hp[j] = make_uint4(w[0], w[1], w[2], w[3]);
           }
         }

@@ -5,16 +5,21 @@
 // features) and the output layer run in FP32 (about 4 % of the flops); FP32
 // master weights with Adam.  Every step of training and inference runs in the
 // kernels of this file:
+//   k_mlp_infer    (mlp_infer_tc.cuh) inference of the whole network in one
+//                  tensor-core kernel, activations in shared memory, the
+//                  input layer as a BF16 MMA over split operands
 //   k_gemm_tc      (gemm_tc.cuh) the hidden layers' forward GEMMs on the
 //                  5th-generation tensor cores (tcgen05.mma, TMA-fed, FP32
 //                  accumulators in tensor memory), bias + SiLU fused, and for
-//                  inference the output layer fused into the last one
+//                  layer-by-layer inference the output layer fused into the last one
 //   k_gemm<EPI>    C = A B with strided (optionally transposed) BF16 operands
 //                  on mma.sync (the backward GEMMs; the forward when the
 //                  layer shape is outside k_gemm_tc's),
 //                  fused epilogues: bias + SiLU (forward), bias (output layer),
-//                  x SiLU'(z) (backward data), FP32 store (weight gradients)
-//   k_colsum       bias gradients
+//                  x SiLU'(z) (backward data), FP32 store (weight gradients,
+//                  the batch split into row slices)
+//   k_colsum_part  bias gradients over row slices of the batch
+//   k_sum_parts    the slices added in order (deterministic)
 //   k_loss         MSE on mu + Gaussian NLL on s with the residual detached
 //   k_adam         Adam on FP32 master weights, BF16 copies for the GEMMs
 //   k_gather_rows  minibatch gather
@@ -38,6 +43,8 @@ namespace {
 using bf16 = unsigned short;
 
 __device__ __forceinline__ float bf2f(bf16 x) { return __bfloat162float(__ushort_as_bfloat16(x)); }
+__device__ __forceinline__ float to_f32(bf16 x) { return bf2f(x); }
+__device__ __forceinline__ float to_f32(float x) { return x; }
 __device__ __forceinline__ bf16 f2bf(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
@@ -60,7 +67,8 @@ struct GemmArgs {
   const float* bias;  // [N] (forward epilogues)
   float* Zf;          // FWD_SILU: pre-activation out [M][N]; BWD_DATA: pre-activation in [M][N]
   bf16* H;            // FWD_SILU: activation out; BWD_DATA: dZ out  [M][N] bf16
-  float* C;           // FWD_LINEAR / WGRAD: FP32 out [M][N]
+  float* C;           // FWD_LINEAR / WGRAD: FP32 out [M][N] (WGRAD: one [M][N] slice per split)
+  int kps;            // WGRAD: k (batch rows) per split; block z takes [z kps, (z + 1) kps)
 };
 
 constexpr int BM = 64, BN = 64, BK = 32, LDA = BK + 8;
@@ -74,6 +82,8 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
   const int gr = l >> 2, gc = l & 3;
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int kb = EPI == EPI_WGRAD ? blockIdx.z * g.kps : 0;
+  const int ke = EPI == EPI_WGRAD ? min(g.K, kb + g.kps) : g.K;
   float acc[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -81,7 +91,7 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
+  for (int k0 = kb; k0 < ke; k0 += BK) {
     // cooperative tile loads (bounds -> zero); consecutive threads walk the
     // operand's contiguous dimension
     const bool a_k_fast = g.sak == 1, b_k_fast = g.sbk == 1;
@@ -89,13 +99,13 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
     for (int i = tid; i < BM * BK; i += 128) {
       const int mm = a_k_fast ? i / BK : i % BM, kk = a_k_fast ? i % BK : i / BM;
       const int m = m0 + mm, k = k0 + kk;
-      As[mm * LDA + kk] = (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : (bf16)0;
+      As[mm * LDA + kk] = (m < g.M && k < ke) ? g.A[m * g.sam + k * g.sak] : (bf16)0;
     }
 #pragma unroll 4
     for (int i = tid; i < BN * BK; i += 128) {
       const int nn = b_k_fast ? i / BK : i % BN, kk = b_k_fast ? i % BK : i / BN;
       const int n = n0 + nn, k = k0 + kk;
-      Bs[nn * LDA + kk] = (n < g.N && k < g.K) ? g.B[k * g.sbk + n * g.sbn] : (bf16)0;
+      Bs[nn * LDA + kk] = (n < g.N && k < ke) ? g.B[k * g.sbk + n * g.sbn] : (bf16)0;
     }
     __syncthreads();
 #pragma unroll
@@ -145,7 +155,7 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
           const float s = sigmoidf_(z);
           g.H[o] = f2bf(v * s * (1.0f + z * (1.0f - s)));
         } else {
-          g.C[o] = v;
+          g.C[(long long)blockIdx.z * g.M * g.N + o] = v;
         }
       }
 }
@@ -258,21 +268,25 @@ __global__ void k_dense_out_bwd(const float* __restrict__ dout, const float* __r
 }
 
 // db[n] = sum_m dZ[m][n]   (one thread per column, fixed order)
-__global__ void k_colsum(const bf16* __restrict__ dZ, int M, int N, float* __restrict__ out) {
+// Column sums of D [M][N] (BF16 or FP32) over row slice z = blockIdx.y of
+// rps rows: parts [S][N]; k_sum_parts adds the slices in order.
+template <class T>
+__global__ void k_colsum_part(const T* __restrict__ D, int M, int N, int rps, float* __restrict__ parts) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
+  const int r0 = blockIdx.y * rps, r1 = min(M, r0 + rps);
   float s = 0.0f;
-  for (int m = 0; m < M; ++m) s += bf2f(dZ[(long long)m * N + n]);
-  out[n] = s;
+  for (int m = r0; m < r1; ++m) s += to_f32(D[(long long)m * N + n]);
+  parts[(long long)blockIdx.y * N + n] = s;
 }
 
-// db[n] = sum_m D[m][n] for an FP32 matrix
-__global__ void k_colsum_f32(const float* __restrict__ D, int M, int N, float* __restrict__ out) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
+// out[i] = sum_{z < S} parts[z][i], slices in order (deterministic)
+__global__ void k_sum_parts(const float* __restrict__ parts, int S, long long count, float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
   float s = 0.0f;
-  for (int m = 0; m < M; ++m) s += D[(long long)m * N + n];
-  out[n] = s;
+  for (int z = 0; z < S; ++z) s += parts[(long long)z * count + i];
+  out[i] = s;
 }
 
 // Loss per sample (mean over the batch): ((y - mu)/tau)^2 + lam (r^2 e^{-2s}/2 + s),
@@ -399,6 +413,8 @@ struct rw_mlp {
   float* dout_f = nullptr;
   bf16* dout_b = nullptr;
   bf16 *dA = nullptr, *dB = nullptr;  // dZ ping-pong [max_batch][hidden]
+  float* gparts = nullptr;            // weight-gradient slices of the split batch [<= 512 x 64 x 64]
+  float* cparts = nullptr;            // bias-gradient slices [64][max(hidden, 2)]
   float* loss = nullptr;              // [max_batch]
   float* yb = nullptr;
   int64_t* idx = nullptr;
@@ -551,7 +567,7 @@ int launch_gemm(rw_mlp* m, int epi, GemmArgs a) {
     case EPI_FWD_SILU: k_gemm<EPI_FWD_SILU><<<grid, 128, 0, m->stream>>>(a); break;
     case EPI_FWD_LINEAR: k_gemm<EPI_FWD_LINEAR><<<grid, 128, 0, m->stream>>>(a); break;
     case EPI_BWD_DATA: k_gemm<EPI_BWD_DATA><<<grid, 128, 0, m->stream>>>(a); break;
-    default: k_gemm<EPI_WGRAD><<<grid, 128, 0, m->stream>>>(a); break;
+    default: a.kps = a.K; k_gemm<EPI_WGRAD><<<grid, 128, 0, m->stream>>>(a); break;
   }
   return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "gemm launch");
 }
@@ -617,6 +633,32 @@ int forward_batch(rw_mlp* m, const float* xf, int B, bool infer = false) {
   return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "forward launch");
 }
 
+// Weight gradient w.C [M][N] = sum over the batch (k) of the GemmArgs
+// product, the batch split into S slices of a multiple of 32 rows so that
+// about 512 blocks run; the slices go to m->gparts and are added in order.
+constexpr int WGRAD_BLOCKS = 512;
+int launch_wgrad(rw_mlp* m, GemmArgs w) {
+  const int tiles = ((w.N + BN - 1) / BN) * ((w.M + BM - 1) / BM);
+  int S = std::max(1, std::min(WGRAD_BLOCKS / tiles, (w.K + BK - 1) / BK));
+  w.kps = ((w.K + S - 1) / S + BK - 1) / BK * BK;
+  S = (w.K + w.kps - 1) / w.kps;
+  float* dst = w.C;
+  w.C = m->gparts;
+  k_gemm<EPI_WGRAD><<<dim3((w.N + BN - 1) / BN, (w.M + BM - 1) / BM, S), 128, 0, m->stream>>>(w);
+  const long long cnt = (long long)w.M * w.N;
+  k_sum_parts<<<(unsigned)((cnt + 255) / 256), 256, 0, m->stream>>>(m->gparts, S, cnt, dst);
+  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "weight-gradient launch");
+}
+
+// bias gradient out [N] = column sums of D [M][N], in up to 64 row slices
+template <class T>
+int launch_colsum(rw_mlp* m, const T* D, int M, int N, float* out) {
+  const int rps = (M + 63) / 64, S = (M + rps - 1) / rps;
+  k_colsum_part<T><<<dim3((N + 127) / 128, S), 128, 0, m->stream>>>(D, M, N, rps, m->cparts);
+  k_sum_parts<<<(unsigned)((N + 255) / 256), 256, 0, m->stream>>>(m->cparts, S, N, out);
+  return cudaGetLastError() == cudaSuccess ? RW_OK : mlp_fail(m, RW_ERR_CUDA, "bias-gradient launch");
+}
+
 // Backward: gradients of the loss (m->dout_f set, m->X holds the BF16
 // inputs) into m->g.  Weight gradients on the tensor cores (BF16 operands,
 // FP32 accumulation); the output layer's backward in FP32.
@@ -636,8 +678,8 @@ int backward_batch(rw_mlp* m, int B) {
     w.N = m->n_out;
     w.K = B;
     w.C = m->g + m->w_off[L];
-    if ((rc = launch_gemm(m, EPI_WGRAD, w))) return rc;
-    k_colsum_f32<<<1, 128, 0, m->stream>>>(m->dout_f, B, m->n_out, m->g + m->b_off[L]);
+    if ((rc = launch_wgrad(m, w))) return rc;
+    if ((rc = launch_colsum<float>(m, m->dout_f, B, m->n_out, m->g + m->b_off[L]))) return rc;
     k_dense_out_bwd<<<(unsigned)(((long long)B * m->hidden + 255) / 256), 256, 0, m->stream>>>(
         m->dout_f, m->Z[L - 1], B, m->hidden, m->p + m->w_off[L], m->dA);
   }
@@ -658,8 +700,8 @@ int backward_batch(rw_mlp* m, int B) {
     w.N = m->hidden;
     w.K = B;
     w.C = m->g + m->w_off[l];
-    if ((rc = launch_gemm(m, EPI_WGRAD, w))) return rc;
-    k_colsum<<<(m->hidden + 127) / 128, 128, 0, m->stream>>>(dZ, B, m->hidden, m->g + m->b_off[l]);
+    if ((rc = launch_wgrad(m, w))) return rc;
+    if ((rc = launch_colsum<bf16>(m, dZ, B, m->hidden, m->g + m->b_off[l]))) return rc;
     if (l == 0) break;
     GemmArgs d{};
     d.A = dZ;
@@ -736,7 +778,9 @@ int rw_mlp_create(rw_mlp** out, int device, void* stream, int n_in, int hidden, 
             dalloc(&m->out, (size_t)max_batch * 2) && dalloc(&m->dout_f, (size_t)max_batch * 2) &&
             dalloc(&m->dout_b, (size_t)max_batch * 2) && dalloc(&m->dA, (size_t)max_batch * hidden) &&
             dalloc(&m->dB, (size_t)max_batch * hidden) && dalloc(&m->loss, (size_t)max_batch) &&
-            dalloc(&m->yb, (size_t)max_batch) && dalloc(&m->idx, (size_t)max_batch);
+            dalloc(&m->yb, (size_t)max_batch) && dalloc(&m->idx, (size_t)max_batch) &&
+            dalloc(&m->gparts, (size_t)WGRAD_BLOCKS * BM * BN) &&
+            dalloc(&m->cparts, (size_t)64 * std::max(hidden, m->n_out));
   for (int l = 0; ok && l < n_layers; ++l) {
     bf16* h = nullptr;
     float* z = nullptr;
@@ -774,7 +818,7 @@ int rw_mlp_destroy(rw_mlp* m) {
   for (void* q : {(void*)m->p, (void*)m->g, (void*)m->m1, (void*)m->m2, (void*)m->pb, (void*)m->X, (void*)m->Xf,
                   (void*)m->out,
                   (void*)m->dout_f, (void*)m->dout_b, (void*)m->dA, (void*)m->dB, (void*)m->loss, (void*)m->yb,
-                  (void*)m->idx, (void*)m->wt, (void*)m->wpack, (void*)m->tc_err})
+                  (void*)m->idx, (void*)m->wt, (void*)m->wpack, (void*)m->gparts, (void*)m->cparts, (void*)m->tc_err})
     if (q) cudaFree(q);
   for (auto* h : m->H) cudaFree(h);
   for (auto* z : m->Z) cudaFree(z);

@@ -88,10 +88,6 @@ __device__ __forceinline__ uint32_t act_off(int r, int c) {
   return (uint32_t)((c >> 6) * inf::KB_BYTES + r * 128 + ((((w >> 3) ^ r) & 7) << 4) + ((w & 7) << 1));
 }
 
-__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
-  return (uint32_t)bf16_bits(lo) | ((uint32_t)bf16_bits(hi) << 16);
-}
-
 // the split features of one row (this thread's share of the feature pairs)
 struct FeatureShare {
   float v[2 * 5];  // up to 5 pairs: ceil(MAX_IN / 2 / 4)
@@ -288,36 +284,51 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_infer(const __grid_constant_
           tc_fence_after();
           const uint32_t tacc = tmem + (uint32_t)(s * N) + lane_base;
           float h0 = 0.0f, h1 = 0.0f;
+          if (!last) {
 #pragma unroll
-          for (int half = 0; half < 2; ++half) {
-            const int c0 = cq * 64 + half * 32;
-            uint32_t u[2][16];
-            tmem_ld16_nw(tacc + (uint32_t)c0, u[0]);
-            tmem_ld16_nw(tacc + (uint32_t)(c0 + 16), u[1]);
-            tmem_wait_ld();
-            float v[32];
+            for (int half = 0; half < 2; ++half) {
+              // 32 columns; the bias loads are in flight with the tensor-memory loads
+              const int c0 = cq * 64 + half * 32;
+              uint32_t u[2][16];
+              tmem_ld16_nw(tacc + (uint32_t)c0, u[0]);
+              tmem_ld16_nw(tacc + (uint32_t)(c0 + 16), u[1]);
+              float4 b4[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + c0) + j);
-              v[4 * j] = silu_f(__uint_as_float(u[j >> 2][(4 * j) & 15]) + b4.x);
-              v[4 * j + 1] = silu_f(__uint_as_float(u[j >> 2][(4 * j + 1) & 15]) + b4.y);
-              v[4 * j + 2] = silu_f(__uint_as_float(u[j >> 2][(4 * j + 2) & 15]) + b4.z);
-              v[4 * j + 3] = silu_f(__uint_as_float(u[j >> 2][(4 * j + 3) & 15]) + b4.w);
-            }
-            if (!last) {
+              for (int j = 0; j < 8; ++j) b4[j] = __ldg(reinterpret_cast<const float4*>(bias + c0) + j);
+              tmem_wait_ld();
               // the next layer's A operand: 32 columns = four 16-byte chunks
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
-                const uint4 w4 = make_uint4(bf16x2(v[8 * j], v[8 * j + 1]), bf16x2(v[8 * j + 2], v[8 * j + 3]),
-                                            bf16x2(v[8 * j + 4], v[8 * j + 5]), bf16x2(v[8 * j + 6], v[8 * j + 7]));
+                const float4 p = b4[2 * j], q = b4[2 * j + 1];
+                const uint32_t* x = &u[j >> 1][(8 * j) & 15];
+                const uint4 w4 = make_uint4(bf16x2(silu_f(__uint_as_float(x[0]) + p.x), silu_f(__uint_as_float(x[1]) + p.y)),
+                                            bf16x2(silu_f(__uint_as_float(x[2]) + p.z), silu_f(__uint_as_float(x[3]) + p.w)),
+                                            bf16x2(silu_f(__uint_as_float(x[4]) + q.x), silu_f(__uint_as_float(x[5]) + q.y)),
+                                            bf16x2(silu_f(__uint_as_float(x[6]) + q.z), silu_f(__uint_as_float(x[7]) + q.w)));
                 *reinterpret_cast<uint4*>(as + act_off(r, c0 + 8 * j)) = w4;
               }
-            } else {
+            }
+          } else {
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const float2 w2 = __ldg(reinterpret_cast<const float2*>(a.w_out) + c0 + j);
-                h0 = fmaf(v[j], w2.x, h0);
-                h1 = fmaf(v[j], w2.y, h1);
+            for (int ch = 0; ch < 4; ++ch) {
+              // 16 columns with their bias and output weights ([c][2]: two columns per float4)
+              const int c0 = cq * 64 + ch * 16;
+              uint32_t u[16];
+              tmem_ld16_nw(tacc + (uint32_t)c0, u);
+              float4 b4[4], w4[8];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) b4[j] = __ldg(reinterpret_cast<const float4*>(bias + c0) + j);
+#pragma unroll
+              for (int j = 0; j < 8; ++j) w4[j] = __ldg(reinterpret_cast<const float4*>(a.w_out + 2 * c0) + j);
+              tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float bl = (j & 1) ? b4[j >> 1].z : b4[j >> 1].x, bh = (j & 1) ? b4[j >> 1].w : b4[j >> 1].y;
+                const float v0 = silu_f(__uint_as_float(u[2 * j]) + bl), v1 = silu_f(__uint_as_float(u[2 * j + 1]) + bh);
+                h0 = fmaf(v0, w4[j].x, h0);
+                h1 = fmaf(v0, w4[j].y, h1);
+                h0 = fmaf(v1, w4[j].z, h0);
+                h1 = fmaf(v1, w4[j].w, h1);
               }
             }
           }
