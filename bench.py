@@ -82,6 +82,11 @@ def parse():
                     help="interpolation surrogate: exact |M|^2 at K Chebyshev nodes of the point range per "
                          "event, log r interpolated for every point, exact fallback above --interp-tol")
     ap.add_argument("--interp-tol", type=float, default=2.5e-4)
+    ap.add_argument("--mlp", choices=["infer", "train"], default=None,
+                    help="the surrogate network alone (40 -> 4 x 256 SiLU -> 2, random weights and features): "
+                         "inference of --mlp-rows rows, or --steps training steps of 16,384 rows")
+    ap.add_argument("--mlp-rows", type=int, default=1 << 24)
+    ap.add_argument("--mlp-gemm", default="tcgen05", choices=["tcgen05", "tcgen05_layers", "mma_sync"])
     ap.add_argument("--scan", choices=["events", "points"], default=None,
                     help="scaling study of the paper's Figs. 2-3: time to reweight n events for one "
                          "point (events), or 100,000 events for n points (points), through the host entry "
@@ -102,7 +107,9 @@ def dist_info():
 def source_sha(process, mode):
     """Hash of the sources one kernel is compiled from: its translation unit,
     the launch code and every header except other processes' generated
-    amplitude code (the host-only event-file I/O holds no device code)."""
+    amplitude code and the surrogate network's tensor-core kernels (the
+    host-only event-file I/O holds no device code)."""
+    mlp_only = ("gemm_tc.cuh", "mlp_infer_tc.cuh")
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2312_07440_gb300", "csrc")
     tu = f"proc_{process}_{'mixed' if mode.startswith('mixed') else mode}.cu"
@@ -110,6 +117,8 @@ def source_sha(process, mode):
         tu = f"proc_{process}.cu"
     for fn in sorted(os.listdir(d)):
         gen = fn.startswith("gen_") and fn.endswith(".cuh")
+        if fn in mlp_only:
+            continue
         if fn in (tu, "rw_abi.cu") or (fn.endswith((".cuh", ".h")) and (not gen or fn.endswith(f"_{process}.cuh"))):
             with open(os.path.join(d, fn), "rb") as f:
                 h.update(fn.encode() + f.read())
@@ -812,6 +821,50 @@ def run_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mlp(args):
+    """The surrogate network alone: one bench line for its inference (rows/s
+    through rw_mlp_forward, every layer on the tensor cores in one kernel
+    by default) or its training step (Adam on 16,384-row minibatches)."""
+    import torch
+    from paper_2312_07440_gb300 import rwgt
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev)
+    n_in, hidden, layers, batch = 40, 256, 4, 16384
+    m = rwgt.Mlp(0, st.cuda_stream, n_in, hidden, layers, batch, seed=3)
+    m.set_gemm(args.mlp_gemm)
+    g = torch.Generator(device=dev).manual_seed(5)
+    per_row = 2 * (n_in * hidden + hidden * hidden * (layers - 1) + hidden * 2)
+    if args.mlp == "infer":
+        rows = args.mlp_rows
+        x = torch.randn(rows, n_in, device=dev, generator=g)
+        o = torch.empty(rows, 2, device=dev)
+        step = lambda: m.forward(x, o)  # noqa: E731
+        flops, unit = rows * per_row, "rows/s"
+    else:
+        rows = 1 << 20
+        x = torch.randn(rows, n_in, device=dev, generator=g)
+        y = torch.randn(rows, device=dev, generator=g)
+        step = lambda: m.train(x, y, batch, 1, 1e-4, 1.0, 0.05, seed=7)  # noqa: E731
+        # forward, weight gradients of every layer, data gradients of all but the input layer
+        flops, unit = batch * (3 * per_row - 2 * n_in * hidden), "rows/s"
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    ts = timed_steps(torch, st, step, args.steps, args.warmup, flush)
+    m.status()
+    t = statistics.median(ts)
+    n = rows if args.mlp == "infer" else batch
+    pk = bf16_peak()
+    line = {"metric": f"surrogate network {args.mlp} throughput", "value": n / t, "unit": unit, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulation)", "data": "synthetic",
+            "config": {"workload": f"mlp_{args.mlp}", "mlp": f"{n_in}->{layers}x{hidden} SiLU->2",
+                       "rows": n, "gemm": args.mlp_gemm, "l2": "flushed between timed steps (256 MiB write)"},
+            "roofline": {"bound": "tensor", "achieved": flops / t / 1e12, "peak": pk, "unit": "TFLOP/s",
+                         "frac": flops / t / 1e12 / pk, "traffic": None,
+                         "peak_source": "measured cuBLAS BF16 burst (MEASURED_PEAKS.json)"}}
+    m.close()
+    print(json.dumps(line), flush=True)
+
+
 def scan_points(wl, n):
     """n parameter points for a scan: random couplings (e- e+ -> 5 photons),
     else m_t = kappa 173 GeV with kappa spread over [0.8, 1.2]."""
@@ -975,6 +1028,8 @@ def main():
         run_interp(args)
     elif args.scan:
         run_scan(args)
+    elif args.mlp:
+        run_mlp(args)
     else:
         run_ours(args)
 
