@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256, MINB) k_reweight(const __grid_constant__ 
   // dynamic shared memory: the amplitude code's current store (if any), then
   // the warp partial sums [nwarps][P+1]
   extern __shared__ __align__(16) unsigned char rw_dyn_bytes[];
-  double2* sacc = reinterpret_cast<double2*>(rw_dyn_bytes + (size_t)Proc::template jstore_bytes<R>() * blockDim.x);
+  double2* sacc = reinterpret_cast<double2*>(rw_dyn_bytes + (size_t)Proc::template jstore_bytes<R, LB>() * blockDim.x);
   __shared__ double2 red[32];
   __shared__ int is_last;
   const int P = a.P;

@@ -116,7 +116,7 @@ __device__ __forceinline__ void multi_dispatch(int i, const MultiItem* items, co
 
 template <class First, class... Rest>
 __host__ __device__ constexpr int max_jstore_bytes() {
-  constexpr int a = First::Proc::template jstore_bytes<float>();
+  constexpr int a = First::Proc::template jstore_bytes<float, First::LB>();
   if constexpr (sizeof...(Rest) > 0) {
     constexpr int b = max_jstore_bytes<Rest...>();
     return a > b ? a : b;

@@ -14,6 +14,7 @@ struct Tag {
   static constexpr int NJS = gg_ttgg::NJS;
   static constexpr int NCOL = gg_ttgg::K;
   static constexpr bool JSMEM = true;  // currents of 3+ gluons in shared memory (FP32)
+  static constexpr bool KSMEM = true;  // per-event constants in shared memory (FP32)
   template <class R, int LB, int CM>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
     return gg_ttgg::hel_sum<R, LB, CM, JSMEM && sizeof(R) == 4>(X, K, lane);
@@ -23,14 +24,14 @@ using P = QcdProc<Tag>;
 }  // namespace
 
 void register_gg_ttgg_fp32(std::vector<KernelEntry>& t) {
-  t.push_back({RW_GG_TTGG, RW_FP32, 1, (const void*)&k_reweight<P, float, 1>, 256, 0, P::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_FP32, 1, (const void*)&k_interp<P, float, 1>, 256, 1, P::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_FP32, 2, (const void*)&k_reweight<P, float, 2>, 256, 0, P::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_FP32, 2, (const void*)&k_interp<P, float, 2>, 256, 1, P::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_FP32, 3, (const void*)&k_reweight<P, float, 3>, 256, 0, P::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_FP32, 4, (const void*)&k_reweight<P, float, 4>, 256, 0, P::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_FP32, 3, (const void*)&k_interp<P, float, 3>, 256, 1, P::jstore_bytes<float>()});
-  t.push_back({RW_GG_TTGG, RW_FP32, 4, (const void*)&k_interp<P, float, 4>, 256, 1, P::jstore_bytes<float>()});
+  t.push_back({RW_GG_TTGG, RW_FP32, 1, (const void*)&k_reweight<P, float, 1>, 256, 0, P::jstore_bytes<float, 1>()});
+  t.push_back({RW_GG_TTGG, RW_FP32, 1, (const void*)&k_interp<P, float, 1>, 256, 1, P::jstore_bytes<float, 1>()});
+  t.push_back({RW_GG_TTGG, RW_FP32, 2, (const void*)&k_reweight<P, float, 2>, 256, 0, P::jstore_bytes<float, 2>()});
+  t.push_back({RW_GG_TTGG, RW_FP32, 2, (const void*)&k_interp<P, float, 2>, 256, 1, P::jstore_bytes<float, 2>()});
+  t.push_back({RW_GG_TTGG, RW_FP32, 3, (const void*)&k_reweight<P, float, 3>, 256, 0, P::jstore_bytes<float, 3>()});
+  t.push_back({RW_GG_TTGG, RW_FP32, 4, (const void*)&k_reweight<P, float, 4>, 256, 0, P::jstore_bytes<float, 4>()});
+  t.push_back({RW_GG_TTGG, RW_FP32, 3, (const void*)&k_interp<P, float, 3>, 256, 1, P::jstore_bytes<float, 3>()});
+  t.push_back({RW_GG_TTGG, RW_FP32, 4, (const void*)&k_interp<P, float, 4>, 256, 1, P::jstore_bytes<float, 4>()});
 }
 
 }  // namespace rw

@@ -11,6 +11,13 @@
 
 namespace rw {
 
+// Tag::KSMEM (optional, default false): keep the per-event constants in
+// shared memory in the FP32 modes
+template <class T, class = void>
+struct tag_ksmem : std::false_type {};
+template <class T>
+struct tag_ksmem<T, std::void_t<decltype(T::KSMEM)>> : std::integral_constant<bool, T::KSMEM> {};
+
 // g g -> t tbar + n g.  Tag provides NG, NEXT, MAX_LB and hel_sum<R, LB, CM>();
 // CM selects the colour sum (FMA, or tensor cores in FP16/BF16).
 template <class Tag, int CM = 0>
@@ -18,6 +25,15 @@ struct QcdProc {
   static constexpr int NG = Tag::NG;
   static constexpr int NEXT = Tag::NEXT;
   static constexpr bool kSymmetricHelicities = true;
+  // per-event constants (external wavefunctions and propagator invariants):
+  // one slot per event group in shared memory, written by the group's lanes
+  // and read by them at every use, instead of a copy in every lane's
+  // registers (FP32, at least 4 lanes per event)
+  template <class R, int LB>
+  static constexpr bool ksmem() {
+    return tag_ksmem<Tag>::value && sizeof(R) == 4 && LB >= 2;
+  }
+  static constexpr int kSlot = (int)((sizeof(QcdExt<float, NG>) + sizeof(QcdKin<float, NG>) + 15) / 16 * 16);
 
   // Out of line: every evaluation runs the same instructions, so identical
   // inputs give bitwise identical |M|^2 (r == 1 exactly for unchanged
@@ -28,19 +44,38 @@ struct QcdProc {
   // dynamic shared memory per thread of the amplitude code: the current store,
   // then (tensor-core colour sum) the warp's colour staging, as a per-thread share
   template <class R>
-  static constexpr int jstore_bytes() {
+  static constexpr int store_bytes() {
     return ((Tag::JSMEM && sizeof(R) == 4) ? Tag::NJS * 32 : 0) +
            (CM != CM_FMA ? ColourStage<(Tag::NCOL + 15) / 16 * 16>::per_thread : 0);
+  }
+  template <class R, int LB = 0>
+  static constexpr int jstore_bytes() {
+    static_assert(kSlot % 16 == 0 && kSlot % (1 << Tag::MAX_LB) == 0, "the slots split evenly over the lanes");
+    return store_bytes<R>() + (ksmem<R, LB>() ? kSlot >> LB : 0);
   }
 
   template <class R, int LB>
   __device__ __noinline__ static double me(const mom_t<R> (&p)[NEXT][4], const PointDev& pt, int lane,
                                            unsigned gmask) {
     static_assert(LB <= Tag::MAX_LB, "more lane bits than helicity levels");
-    QcdExt<R, NG> X;
-    QcdKin<R, NG> Kn;
-    qcd_setup<R, NG, NEXT>(p, pt.m_t, X, Kn);
-    double s = double(Tag::template hel_sum<R, LB, CM>(X, Kn, lane));
+    double s;
+    if constexpr (ksmem<R, LB>()) {
+      extern __shared__ __align__(16) unsigned char rw_dyn_bytes[];
+      unsigned char* slot =
+          rw_dyn_bytes + (size_t)store_bytes<R>() * blockDim.x + (size_t)(threadIdx.x >> LB) * kSlot;
+      QcdExt<R, NG>& X = *reinterpret_cast<QcdExt<R, NG>*>(slot);
+      QcdKin<R, NG>& Kn = *reinterpret_cast<QcdKin<R, NG>*>(slot + sizeof(QcdExt<R, NG>));
+      __syncwarp(gmask);  // the group's reads of the previous evaluation are done
+      // every lane of the group writes the same values (same inputs, same code)
+      qcd_setup<R, NG, NEXT>(p, pt.m_t, X, Kn);
+      __syncwarp(gmask);
+      s = double(Tag::template hel_sum<R, LB, CM>(X, Kn, lane));
+    } else {
+      QcdExt<R, NG> X;
+      QcdKin<R, NG> Kn;
+      qcd_setup<R, NG, NEXT>(p, pt.m_t, X, Kn);
+      s = double(Tag::template hel_sum<R, LB, CM>(X, Kn, lane));
+    }
 #pragma unroll
     for (int o = 1; o < (1 << LB); o <<= 1) s += __shfl_xor_sync(gmask, s, o);
     return s * pt.cscale;
@@ -65,7 +100,7 @@ struct QedProc {
   static constexpr int NEXT = Tag::NEXT;
   template <class R>
   using mom_t = typename std::conditional<sizeof(R) == 8, double, df>::type;
-  template <class R>
+  template <class R, int LB = 0>
   static constexpr int jstore_bytes() {
     return 0;
   }
@@ -105,7 +140,7 @@ struct EeMumu {
   // few FP64 invariants per event are not a bottleneck)
   template <class R>
   using mom_t = double;
-  template <class R>
+  template <class R, int LB = 0>
   static constexpr int jstore_bytes() {
     return 0;
   }
