@@ -123,7 +123,11 @@ __device__ __forceinline__ double eval_point(const typename Proc::template mom_t
 #pragma unroll
       for (int m = 0; m < 4; ++m) q[i][m] = p[i][m];
   }
-  const double v = Proc::template me<R, LB>(q, pt, lane, gmask);
+  double v;
+  if constexpr (Proc::template inline_me<R>())
+    v = Proc::template me_body<R, LB>(q, pt, lane, gmask);
+  else
+    v = Proc::template me<R, LB>(q, pt, lane, gmask);
   return inside ? v : 0.0;
 }
 

@@ -14,6 +14,7 @@ struct Tag {
   static constexpr int NJS = gg_tt::NJS;
   static constexpr int NCOL = gg_tt::K;
   static constexpr bool JSMEM = false;  // currents of 3+ gluons in shared memory (FP32)
+  static constexpr bool INLINE_ME = true;  // amplitude code inlined into the kernel (FP32)
   template <class R, int LB, int CM>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
     return gg_tt::hel_sum<R, LB, CM, JSMEM && sizeof(R) == 4>(X, K, lane);

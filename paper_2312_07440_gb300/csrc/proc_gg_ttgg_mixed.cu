@@ -15,7 +15,6 @@ struct Tag {
   static constexpr int NJS = gg_ttgg::NJS;
   static constexpr int NCOL = gg_ttgg::K;
   static constexpr bool JSMEM = true;  // currents of 3+ gluons in shared memory (FP32)
-  static constexpr bool KSMEM = true;  // per-event constants in shared memory (FP32)
   template <class R, int LB, int CM>
   __device__ __forceinline__ static R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& K, int lane) {
     return gg_ttgg::hel_sum<R, LB, CM, JSMEM && sizeof(R) == 4>(X, K, lane);
@@ -25,9 +24,10 @@ using P16 = QcdProc<Tag, CM_FP16>;
 using PB16 = QcdProc<Tag, CM_BF16>;
 }  // namespace
 
-// The current store (768 B), the colour staging (168 B) and, with 4 lanes per
-// event, a quarter of the event's constants (272 B) per thread fit a
-// 128-thread block's shared memory but not a 256-thread one's (227 KB).
+// The current store (768 B) and the colour staging (168 B) per thread fit a
+// 128-thread block's shared memory but not a 256-thread one's (227 KB).  (The
+// per-event constants stay in registers here: in shared memory they cost the
+// mixed kernel more than they save, at the same occupancy.)
 constexpr int kMaxBlock = 227 * 1024 / P16::jstore_bytes<float, 2>() >= 256 ? 256 : 128;
 static_assert(P16::jstore_bytes<float, 2>() == PB16::jstore_bytes<float, 2>(), "one block limit for both types");
 

@@ -18,6 +18,13 @@ struct tag_ksmem : std::false_type {};
 template <class T>
 struct tag_ksmem<T, std::void_t<decltype(T::KSMEM)>> : std::integral_constant<bool, T::KSMEM> {};
 
+// Tag::INLINE_ME (optional, default false): the FP32 amplitude code inlined
+// into the kernel's single call site (small processes: no call-site saves)
+template <class T, class = void>
+struct tag_inline_me : std::false_type {};
+template <class T>
+struct tag_inline_me<T, std::void_t<decltype(T::INLINE_ME)>> : std::integral_constant<bool, T::INLINE_ME> {};
+
 // g g -> t tbar + n g.  Tag provides NG, NEXT, MAX_LB and hel_sum<R, LB, CM>();
 // CM selects the colour sum (FMA, or tensor cores in FP16/BF16).
 template <class Tag, int CM = 0>
@@ -35,9 +42,6 @@ struct QcdProc {
   }
   static constexpr int kSlot = (int)((sizeof(QcdExt<float, NG>) + sizeof(QcdKin<float, NG>) + 15) / 16 * 16);
 
-  // Out of line: every evaluation runs the same instructions, so identical
-  // inputs give bitwise identical |M|^2 (r == 1 exactly for unchanged
-  // parameters), and the kernel keeps one copy of the amplitude code.
   // Momenta: FP64 in FP64 mode, double-float in the FP32 modes (dfloat.cuh).
   template <class R>
   using mom_t = typename std::conditional<sizeof(R) == 8, double, df>::type;
@@ -55,7 +59,7 @@ struct QcdProc {
   }
 
   template <class R, int LB>
-  __device__ __noinline__ static double me(const mom_t<R> (&p)[NEXT][4], const PointDev& pt, int lane,
+  __device__ __forceinline__ static double me_body(const mom_t<R> (&p)[NEXT][4], const PointDev& pt, int lane,
                                            unsigned gmask) {
     static_assert(LB <= Tag::MAX_LB, "more lane bits than helicity levels");
     double s;
@@ -79,7 +83,20 @@ struct QcdProc {
 #pragma unroll
     for (int o = 1; o < (1 << LB); o <<= 1) s += __shfl_xor_sync(gmask, s, o);
     return s * pt.cscale;
+  }  // Out of line by default: every evaluation runs the same instructions, so
+  // identical inputs give bitwise identical |M|^2 (r == 1 exactly for
+  // unchanged parameters).  Inlined (Tag::INLINE_ME, FP32) the kernel's one
+  // call site, inside its loop over the points, keeps that property.
+  template <class R>
+  static constexpr bool inline_me() {
+    return tag_inline_me<Tag>::value && sizeof(R) == 4;
   }
+  template <class R, int LB>
+  __device__ __noinline__ static double me(const mom_t<R> (&p)[NEXT][4], const PointDev& pt, int lane,
+                                           unsigned gmask) {
+    return me_body<R, LB>(p, pt, lane, gmask);
+  }
+
   // FP64 mode refines the FP32 Newton solution with two FP64 steps, the FP32
   // modes with one double-float step.
   template <class R>
@@ -103,6 +120,10 @@ struct QedProc {
   template <class R, int LB = 0>
   static constexpr int jstore_bytes() {
     return 0;
+  }
+  template <class R>
+  static constexpr bool inline_me() {
+    return false;
   }
 
   template <class R, int LB>
@@ -143,6 +164,10 @@ struct EeMumu {
   template <class R, int LB = 0>
   static constexpr int jstore_bytes() {
     return 0;
+  }
+  template <class R>
+  static constexpr bool inline_me() {
+    return false;
   }
 
   template <class R, int LB>
