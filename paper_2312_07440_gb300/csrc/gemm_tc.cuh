@@ -49,7 +49,8 @@ constexpr size_t SMEM_HEAD = (size_t)2 * 4 * BM * 2 * sizeof(float);
 constexpr size_t SMEM_BYTES = 1024 + SMEM_B + SMEM_A + 256 + SMEM_HEAD;
 
 struct Epi {
-  const float* bias;       // [N]
+  const float* bias;       // [N] (forward)
+  const float* Zin;        // backward data gradient: pre-activation [M][N]; H = bf16(acc SiLU'(Zin)), or null
   float* Z;                // [M][N] pre-activation (FP32), or null
   unsigned short* H;       // [M][N] SiLU(Z) as BF16, or null
   const float* w_out;      // fused output head [N][2] (FP32), or null
@@ -171,6 +172,14 @@ __device__ __forceinline__ float silu_f(float z) {
 
 __device__ __forceinline__ unsigned short bf16_bits(float x) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// SiLU'(z) = sigma(z) (1 + z (1 - sigma(z))), sigma from the same exp2 and reciprocal
+__device__ __forceinline__ float dsilu_f(float z) {
+  float e, s;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(z * -1.4426950408889634f));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(1.0f + e));
+  return s * fmaf(z, 1.0f - s, 1.0f);
 }
 
 // two FP32 values rounded to BF16 in one word (lo in the low half)
@@ -319,6 +328,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_gemm_tc(const __grid_constant__ 
         float v[16];
         tmem_ld16(tmem + (uint32_t)(acc * MAX_N + c0) + ((uint32_t)(q * 32) << 16), v);
         if (!live) continue;
+        if (e.Zin) {
+          // backward: the data gradient times SiLU' of the pre-activation, as BF16
+          const float4* zp = reinterpret_cast<const float4*>(e.Zin + row * N + c0);
+          uint4* hp = reinterpret_cast<uint4*>(e.H + row * N + c0);
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const float4 za = __ldg(zp + 2 * j), zb = __ldg(zp + 2 * j + 1);
+            const float* x = v + 8 * j;
+            hp[j] = make_uint4(bf16x2(x[0] * dsilu_f(za.x), x[1] * dsilu_f(za.y)),
+                               bf16x2(x[2] * dsilu_f(za.z), x[3] * dsilu_f(za.w)),
+                               bf16x2(x[4] * dsilu_f(zb.x), x[5] * dsilu_f(zb.y)),
+                               bf16x2(x[6] * dsilu_f(zb.z), x[7] * dsilu_f(zb.w)));
+          }
+          continue;
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] += __ldg(e.bias + c0 + j);
         if (e.Z) {

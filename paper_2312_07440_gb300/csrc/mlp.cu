@@ -509,10 +509,13 @@ int launch_mlp_infer(rw_mlp* m, const float* x, long long n, float* out) {
 }
 
 // hidden layer l (1 <= l < n_layers) of B rows: A = bf16 activations [B][hidden]
+// backward (e.Zin set): dZ_{l-1} = bf16((dZ_l W_l^T) SiLU'(Z_{l-1})), whose B
+// operand [k = input unit][n = output unit] is W_l's BF16 copy as stored
 int launch_gemm_tc(rw_mlp* m, int l, const bf16* A, int B, tcg::Epi e) {
   const int H = m->hidden;
   CUtensorMap ta, tb;
-  if (!bf16_map(&ta, A, B, H, tcg::BM) || !bf16_map(&tb, m->wt + (size_t)(l - 1) * H * H, H, H, H))
+  const bf16* Bop = e.Zin ? m->pb + m->w_off[l] : m->wt + (size_t)(l - 1) * H * H;
+  if (!bf16_map(&ta, A, B, H, tcg::BM) || !bf16_map(&tb, Bop, H, H, H))
     return mlp_fail(m, RW_ERR_CUDA, "tensor map encoding");
   static bool attr = false;
   if (!attr) {
@@ -703,6 +706,14 @@ int backward_batch(rw_mlp* m, int B) {
     if ((rc = launch_wgrad(m, w))) return rc;
     if ((rc = launch_colsum<bf16>(m, dZ, B, m->hidden, m->g + m->b_off[l]))) return rc;
     if (l == 0) break;
+    if (tc_usable(m)) {
+      tcg::Epi e{};
+      e.Zin = m->Z[l - 1];
+      e.H = bufs[cur ^ 1];
+      if ((rc = launch_gemm_tc(m, l, dZ, B, e))) return rc;
+      cur ^= 1;
+      continue;
+    }
     GemmArgs d{};
     d.A = dZ;
     d.sam = m->hidden;
