@@ -957,7 +957,8 @@ def run_interp(args):
     if args.events > 0:
         import dataclasses
         wl = dataclasses.replace(wl, n_events=args.events)
-    pts = ev.reweight_points(args.workload, args.variant)
+    variant = point_variant(args)
+    pts = ev.reweight_points(args.workload, variant)
     P, E = pts.shape[0], wl.n_events
     mom_h, w_h = ev.generate(wl, E)
     mom, w = torch.from_numpy(mom_h).to(dev), torch.from_numpy(w_h).to(dev)
@@ -1008,7 +1009,7 @@ def run_interp(args):
         "metric": METRIC, "value": E * P / t_in, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_in, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "data": "synthetic", "dtype": {"fp64": "f64", "fp32": "f32"}.get(args.mode, args.mode),
-        "config": dict(config_dict(args, wl, P), nodes=args.interp, tol=args.interp_tol,
+        "config": dict(config_dict(args, wl, P, variant), nodes=args.interp, tol=args.interp_tol,
                        tuning={"lane_bits": lb, "block": bl},
                        timing="wall clock per call incl. the fallback pass and the host sync, L2 flushed"),
         "surrogate": {"kind": "Chebyshev interpolation of log r along the point axis, exact fallback",
