@@ -100,9 +100,23 @@ def test_gg_ttg_parity(mode, lane_bits):
 def test_gg_ttgg_parity(mode):
     pts = ev.reweight_points("gg_ttgg_1m", "mt")
     mom, w, o = oracle_run("gg_ttgg", "gg_ttgg_1m", 197, pts)
-    for lb in (1, 2, 3):
+    for lb in (1, 2, 3, 4) if mode == "fp32" else (1, 2, 3):
         g = run_gpu("gg_ttgg", mode, mom, w, pts, lane_bits=lb)
         check_against_oracle(g, o, mode, ("gg_ttgg", pts, mom, w), "gg_ttgg_197")
+
+
+@pytest.mark.parametrize("lane_bits,block", [(2, 64), (2, 128), (3, 64), (3, 256), (4, 64), (4, 256)])
+def test_gg_ttgg_fp32_shared_event_constants(lane_bits, block):
+    """FP32 with 4-16 lanes per event keeps each event's constants in one
+    shared-memory slot per event group: every slot placement (groups of 4, 8
+    and 16 lanes; up to the largest block that fits, 128 threads with 4 lanes
+    per event and 256 with 8 or 16; a ragged last block) against the oracle,
+    for the original point and a moved top mass (the slot is rewritten between
+    the two evaluations)."""
+    pts = ev.reweight_points("gg_ttgg_1m", "mt")
+    mom, w, o = oracle_run("gg_ttgg", "gg_ttgg_1m", 197, pts)
+    g = run_gpu("gg_ttgg", "fp32", mom, w, pts, lane_bits=lane_bits, block=block)
+    check_against_oracle(g, o, "fp32", ("gg_ttgg", pts, mom, w), "gg_ttgg_197")
 
 
 # --------------------------------------------------------------------------
