@@ -186,11 +186,30 @@ __device__ __forceinline__ ws<R> weyl_form(const cv<R>& a) {
 // Jslash psi = gamma^mu J_mu psi: 56 flops from the Weyl-block form, 64 from
 // the vector.  slash returns it, slash_acc adds it to o (+8 flops).
 template <class R, bool ACC>
-__device__ __forceinline__ void slash_impl(sp<R>& o, const ws<R>& a, const sp<R>& s) {
+__device__ __forceinline__ void slash_body(sp<R>& o, const ws<R>& a, const sp<R>& s) {
   o.c[0] = cmsc(a.bm, s.c[3], ACC ? cmac(a.am, s.c[2], o.c[0]) : cmul(a.am, s.c[2]));
   o.c[1] = cmsc(a.bp, s.c[2], ACC ? cmac(a.ap, s.c[3], o.c[1]) : cmul(a.ap, s.c[3]));
   o.c[2] = cmac(a.bm, s.c[1], ACC ? cmac(a.ap, s.c[0], o.c[2]) : cmul(a.ap, s.c[0]));
   o.c[3] = cmac(a.am, s.c[1], ACC ? cmac(a.bp, s.c[0], o.c[3]) : cmul(a.bp, s.c[0]));
+}
+#ifdef RW_FP32_OUTLINED_SLASH
+// one out-of-line copy of the FP32 slash for amplitude code whose unrolled
+// chains would not fit the instruction cache (defined by the translation unit)
+template <bool ACC>
+__device__ __noinline__ sp<float> slash_call(sp<float> o, ws<float> a, sp<float> s) {
+  slash_body<float, ACC>(o, a, s);
+  return o;
+}
+#endif
+template <class R, bool ACC>
+__device__ __forceinline__ void slash_impl(sp<R>& o, const ws<R>& a, const sp<R>& s) {
+#ifdef RW_FP32_OUTLINED_SLASH
+  if constexpr (sizeof(R) == 4) {
+    o = slash_call<ACC>(o, a, s);
+    return;
+  }
+#endif
+  slash_body<R, ACC>(o, a, s);
 }
 template <class R>
 __device__ __forceinline__ sp<R> slash(const ws<R>& a, const sp<R>& s) {
