@@ -128,8 +128,14 @@ __device__ __forceinline__ void spsub(sp<R>& a, const sp<R>& b) {
 // c = -1/K^2 (Feynman gauge, g stripped), K = P1 + P2:
 //   out = c [ -J1 (2P1+P2).J2 + (J1.J2)(P1-P2) + J2 (2P2+P1).J1 ]     (156 flops)
 // vvv returns it, vvv_acc adds it to o (+8 flops).
+// four reals passed by value (out-of-line calls)
+template <class R>
+struct v4 {
+  R m[4];
+};
+
 template <class R, bool ACC>
-__device__ __forceinline__ void vvv_impl(cv<R>& o, const cv<R>& J1, const R (&P1)[4], const cv<R>& J2,
+__device__ __forceinline__ void vvv_body(cv<R>& o, const cv<R>& J1, const R (&P1)[4], const cv<R>& J2,
                                          const R (&P2)[4], R c) {
   R a[4], b[4], d[4];
 #pragma unroll
@@ -148,6 +154,25 @@ __device__ __forceinline__ void vvv_impl(cv<R>& o, const cv<R>& J1, const R (&P1
     o.c[m] = cmsc(J1.c[m], s1, t);
   }
 }
+#ifdef RW_FP32_OUTLINED_CURRENTS
+template <bool ACC>
+__device__ __noinline__ cv<float> vvv_call(cv<float> o, cv<float> J1, v4<float> P1, cv<float> J2, v4<float> P2,
+                                           float c) {
+  vvv_body<float, ACC>(o, J1, P1.m, J2, P2.m, c);
+  return o;
+}
+#endif
+template <class R, bool ACC>
+__device__ __forceinline__ void vvv_impl(cv<R>& o, const cv<R>& J1, const R (&P1)[4], const cv<R>& J2,
+                                         const R (&P2)[4], R c) {
+#ifdef RW_FP32_OUTLINED_CURRENTS
+  if constexpr (sizeof(R) == 4) {
+    o = vvv_call<ACC>(o, J1, v4<float>{{P1[0], P1[1], P1[2], P1[3]}}, J2, v4<float>{{P2[0], P2[1], P2[2], P2[3]}}, c);
+    return;
+  }
+#endif
+  vvv_body<R, ACC>(o, J1, P1, J2, P2, c);
+}
 template <class R>
 __device__ __forceinline__ cv<R> vvv(const cv<R>& J1, const R (&P1)[4], const cv<R>& J2, const R (&P2)[4], R c) {
   cv<R> o;
@@ -163,12 +188,28 @@ __device__ __forceinline__ void vvv_acc(cv<R>& o, const cv<R>& J1, const R (&P1)
 // Colour-ordered 4-gluon vertex with the propagator c = +1/K^2:
 //   out += c [ 2 J2 (J1.J3) - J1 (J2.J3) - J3 (J1.J2) ]                 (193 flops)
 template <class R>
-__device__ __forceinline__ void vvvv_acc(cv<R>& o, const cv<R>& J1, const cv<R>& J2, const cv<R>& J3, R c) {
+__device__ __forceinline__ void vvvv_body(cv<R>& o, const cv<R>& J1, const cv<R>& J2, const cv<R>& J3, R c) {
   const cx<R> t13 = (R(2) * c) * dot(J1, J3);
   const cx<R> t23 = c * dot(J2, J3);
   const cx<R> t12 = c * dot(J1, J2);
 #pragma unroll
   for (int m = 0; m < 4; ++m) o.c[m] = cmsc(J3.c[m], t12, cmsc(J1.c[m], t23, cmac(J2.c[m], t13, o.c[m])));
+}
+#ifdef RW_FP32_OUTLINED_CURRENTS
+__device__ __noinline__ inline cv<float> vvvv_call(cv<float> o, cv<float> J1, cv<float> J2, cv<float> J3, float c) {
+  vvvv_body<float>(o, J1, J2, J3, c);
+  return o;
+}
+#endif
+template <class R>
+__device__ __forceinline__ void vvvv_acc(cv<R>& o, const cv<R>& J1, const cv<R>& J2, const cv<R>& J3, R c) {
+#ifdef RW_FP32_OUTLINED_CURRENTS
+  if constexpr (sizeof(R) == 4) {
+    o = vvvv_call(o, J1, J2, J3, c);
+    return;
+  }
+#endif
+  vvvv_body<R>(o, J1, J2, J3, c);
 }
 
 // A complex vector in Weyl-block form: a0 - a3, a0 + a3, a1 + i a2, a1 - i a2

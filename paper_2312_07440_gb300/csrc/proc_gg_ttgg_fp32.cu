@@ -1,7 +1,8 @@
 // g g -> t tbar + n g kernel variants (gg_ttgg, fp32).
-// the FP32 slash out of line: the 24 orderings' unrolled chains otherwise
-// overflow the instruction cache and spill (helas.cuh)
+// the FP32 slash and gluon vertices out of line: the 24 orderings' unrolled
+// chains otherwise overflow the instruction cache and spill (helas.cuh)
 #define RW_FP32_OUTLINED_SLASH 1
+#define RW_FP32_OUTLINED_CURRENTS 1
 #include "../../include/rwgt.h"
 #include "gen_qcd_gg_ttgg.cuh"
 #include "kernels.cuh"

@@ -1,7 +1,8 @@
 // g g -> t tbar + n g kernel variants (gg_ttgg, mixed precision: FP32 amplitudes,
 // FP16/BF16 tensor-core colour sum with FP32 accumulation).
 // the FP32 slash out of line: the 24 orderings' unrolled chains otherwise
-// overflow the instruction cache and spill (helas.cuh)
+// overflow the instruction cache and spill (helas.cuh; the gluon vertices too
+// made this kernel 11 % slower, unlike the FP32 one)
 #define RW_FP32_OUTLINED_SLASH 1
 #include "../../include/rwgt.h"
 #include "gen_qcd_gg_ttgg.cuh"
