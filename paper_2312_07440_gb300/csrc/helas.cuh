@@ -124,16 +124,16 @@ __device__ __forceinline__ void spsub(sp<R>& a, const sp<R>& b) {
   for (int m = 0; m < 4; ++m) a.c[m] = a.c[m] - b.c[m];
 }
 
-// Colour-ordered 3-gluon vertex and the off-shell gluon propagator,
-// c = -1/K^2 (Feynman gauge, g stripped), K = P1 + P2:
-//   out = c [ -J1 (2P1+P2).J2 + (J1.J2)(P1-P2) + J2 (2P2+P1).J1 ]     (156 flops)
-// vvv returns it, vvv_acc adds it to o (+8 flops).
 // four reals passed by value (out-of-line calls)
 template <class R>
 struct v4 {
   R m[4];
 };
 
+// Colour-ordered 3-gluon vertex and the off-shell gluon propagator,
+// c = -1/K^2 (Feynman gauge, g stripped), K = P1 + P2:
+//   out = c [ -J1 (2P1+P2).J2 + (J1.J2)(P1-P2) + J2 (2P2+P1).J1 ]     (156 flops)
+// vvv returns it, vvv_acc adds it to o (+8 flops).
 template <class R, bool ACC>
 __device__ __forceinline__ void vvv_body(cv<R>& o, const cv<R>& J1, const R (&P1)[4], const cv<R>& J2,
                                          const R (&P2)[4], R c) {
@@ -155,19 +155,28 @@ __device__ __forceinline__ void vvv_body(cv<R>& o, const cv<R>& J1, const R (&P1
   }
 }
 #ifdef RW_FP32_OUTLINED_CURRENTS
-template <bool ACC>
-__device__ __noinline__ cv<float> vvv_call(cv<float> o, cv<float> J1, v4<float> P1, cv<float> J2, v4<float> P2,
-                                           float c) {
-  vvv_body<float, ACC>(o, J1, P1.m, J2, P2.m, c);
+constexpr bool kOutlinedCur32 = true;
+#else
+constexpr bool kOutlinedCur32 = false;
+#endif
+#ifdef RW_FP64_OUTLINED_CURRENTS
+constexpr bool kOutlinedCur64 = true;
+#else
+constexpr bool kOutlinedCur64 = false;
+#endif
+#if defined(RW_FP32_OUTLINED_CURRENTS) || defined(RW_FP64_OUTLINED_CURRENTS)
+template <class R, bool ACC>
+__device__ __noinline__ cv<R> vvv_call(cv<R> o, cv<R> J1, v4<R> P1, cv<R> J2, v4<R> P2, R c) {
+  vvv_body<R, ACC>(o, J1, P1.m, J2, P2.m, c);
   return o;
 }
 #endif
 template <class R, bool ACC>
 __device__ __forceinline__ void vvv_impl(cv<R>& o, const cv<R>& J1, const R (&P1)[4], const cv<R>& J2,
                                          const R (&P2)[4], R c) {
-#ifdef RW_FP32_OUTLINED_CURRENTS
-  if constexpr (sizeof(R) == 4) {
-    o = vvv_call<ACC>(o, J1, v4<float>{{P1[0], P1[1], P1[2], P1[3]}}, J2, v4<float>{{P2[0], P2[1], P2[2], P2[3]}}, c);
+#if defined(RW_FP32_OUTLINED_CURRENTS) || defined(RW_FP64_OUTLINED_CURRENTS)
+  if constexpr (sizeof(R) == 4 ? kOutlinedCur32 : kOutlinedCur64) {
+    o = vvv_call<R, ACC>(o, J1, v4<R>{{P1[0], P1[1], P1[2], P1[3]}}, J2, v4<R>{{P2[0], P2[1], P2[2], P2[3]}}, c);
     return;
   }
 #endif
@@ -195,17 +204,18 @@ __device__ __forceinline__ void vvvv_body(cv<R>& o, const cv<R>& J1, const cv<R>
 #pragma unroll
   for (int m = 0; m < 4; ++m) o.c[m] = cmsc(J3.c[m], t12, cmsc(J1.c[m], t23, cmac(J2.c[m], t13, o.c[m])));
 }
-#ifdef RW_FP32_OUTLINED_CURRENTS
-__device__ __noinline__ inline cv<float> vvvv_call(cv<float> o, cv<float> J1, cv<float> J2, cv<float> J3, float c) {
-  vvvv_body<float>(o, J1, J2, J3, c);
+#if defined(RW_FP32_OUTLINED_CURRENTS) || defined(RW_FP64_OUTLINED_CURRENTS)
+template <class R>
+__device__ __noinline__ cv<R> vvvv_call(cv<R> o, cv<R> J1, cv<R> J2, cv<R> J3, R c) {
+  vvvv_body<R>(o, J1, J2, J3, c);
   return o;
 }
 #endif
 template <class R>
 __device__ __forceinline__ void vvvv_acc(cv<R>& o, const cv<R>& J1, const cv<R>& J2, const cv<R>& J3, R c) {
-#ifdef RW_FP32_OUTLINED_CURRENTS
-  if constexpr (sizeof(R) == 4) {
-    o = vvvv_call(o, J1, J2, J3, c);
+#if defined(RW_FP32_OUTLINED_CURRENTS) || defined(RW_FP64_OUTLINED_CURRENTS)
+  if constexpr (sizeof(R) == 4 ? kOutlinedCur32 : kOutlinedCur64) {
+    o = vvvv_call<R>(o, J1, J2, J3, c);
     return;
   }
 #endif
@@ -233,20 +243,32 @@ __device__ __forceinline__ void slash_body(sp<R>& o, const ws<R>& a, const sp<R>
   o.c[2] = cmac(a.bm, s.c[1], ACC ? cmac(a.ap, s.c[0], o.c[2]) : cmul(a.ap, s.c[0]));
   o.c[3] = cmac(a.am, s.c[1], ACC ? cmac(a.bp, s.c[0], o.c[3]) : cmul(a.bp, s.c[0]));
 }
-#ifdef RW_FP32_OUTLINED_SLASH
-// one out-of-line copy of the FP32 slash for amplitude code whose unrolled
-// chains would not fit the instruction cache (defined by the translation unit)
-template <bool ACC>
-__device__ __noinline__ sp<float> slash_call(sp<float> o, ws<float> a, sp<float> s) {
-  slash_body<float, ACC>(o, a, s);
+// Out-of-line copies of the slash and the gluon vertices, for amplitude code
+// whose unrolled chains would not fit the instruction cache: a translation
+// unit defines RW_FP32_OUTLINED_SLASH / RW_FP32_OUTLINED_CURRENTS (FP32) or
+// RW_FP64_OUTLINED_SLASH / RW_FP64_OUTLINED_CURRENTS (FP64) before including.
+#if defined(RW_FP32_OUTLINED_SLASH) || defined(RW_FP64_OUTLINED_SLASH)
+template <class R, bool ACC>
+__device__ __noinline__ sp<R> slash_call(sp<R> o, ws<R> a, sp<R> s) {
+  slash_body<R, ACC>(o, a, s);
   return o;
 }
 #endif
+#ifdef RW_FP32_OUTLINED_SLASH
+constexpr bool kOutlinedSlash32 = true;
+#else
+constexpr bool kOutlinedSlash32 = false;
+#endif
+#ifdef RW_FP64_OUTLINED_SLASH
+constexpr bool kOutlinedSlash64 = true;
+#else
+constexpr bool kOutlinedSlash64 = false;
+#endif
 template <class R, bool ACC>
 __device__ __forceinline__ void slash_impl(sp<R>& o, const ws<R>& a, const sp<R>& s) {
-#ifdef RW_FP32_OUTLINED_SLASH
-  if constexpr (sizeof(R) == 4) {
-    o = slash_call<ACC>(o, a, s);
+#if defined(RW_FP32_OUTLINED_SLASH) || defined(RW_FP64_OUTLINED_SLASH)
+  if constexpr (sizeof(R) == 4 ? kOutlinedSlash32 : kOutlinedSlash64) {
+    o = slash_call<R, ACC>(o, a, s);
     return;
   }
 #endif
