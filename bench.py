@@ -404,7 +404,7 @@ def attach(torch, dev, stream, rwgt, wl, pts, mom, w, mode, autotune, lane_bits=
     c.load_events(mom, w, E, ws, nb)
     if autotune:
         # launch shape chosen by the library's autotuner on a bounded subset (not timed)
-        c.autotune(max_events=min(E, 1 << 16))
+        c.autotune(max_events=min(E, 1 << 18))
     return c, ws
 
 
@@ -435,7 +435,7 @@ def run_ours(args):
     w = torch.from_numpy(w_h).to(dev)
     autotune = args.lane_bits < 0 and args.block == 0 and not args.no_autotune
     ctx, ws = attach(torch, dev, stream, rwgt, wl, pts, mom, w, args.mode, autotune, args.lane_bits, args.block)
-    tuning_source = "autotuned on min(E, 65536) events" if autotune else "fixed"
+    tuning_source = "autotuned on min(E, 262144) events" if autotune else "fixed"
     lane_bits, block = ctx.get_tuning()
     wnew = torch.empty((P, E), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
