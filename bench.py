@@ -498,6 +498,12 @@ def run_ours(args):
             variants[name] = run_variant(torch, rwgt, dev, stream, ev.WORKLOADS[vwl_name], vvar, vmode,
                                          cache[key], args, flush, peaks, n_acc)
 
+    if rank == 0 and world == 1 and not args.no_variants:
+        del cache
+        cache = {}
+        torch.cuda.empty_cache()
+        variants["multi_gg_tt_gg_ttg_fp64"] = run_multi_variant(torch, rwgt, dev, stream, args, flush)
+
     if rank == 0 and world == 1 and not args.no_variants and not args.no_surrogate:
         del cache
         torch.cuda.empty_cache()
@@ -562,6 +568,58 @@ def run_variant(torch, rwgt, dev, stream, wl, variant, mode, sample, args, flush
         out["r_is_exactly_one"] = bool(torch.all(wn == w.unsqueeze(0)).item())
     del wn, ws
     return out
+
+
+def run_multi_variant(torch, rwgt, dev, stream, args, flush):
+    """Several processes in one persistent launch (rw_multi): g g -> t tbar
+    (1,048,576 events, the Born process) and g g -> t tbar g (262,144 events,
+    its real emission) at m_t = 1.2 x 173, FP64, against the same two
+    processes launched back to back, each with its own autotuned shape (the
+    one launch takes 1 lane per event for both; W' of the two ways differ only
+    by the order of the helicity sum)."""
+    items = []
+    for wl_name, E in (("gg_tt_1m", 1 << 20), ("gg_ttg_4m", 1 << 18)):
+        wl = ev.WORKLOADS[wl_name]
+        mom_h, w_h = ev.generate(wl, E)
+        pts = ev.reweight_points(wl_name, "mt")[:1] if wl.process != "gg_tt" else \
+            np.stack([ev.param_vector(m_t=1.2 * ev.M_TOP)])
+        mom, w = torch.from_numpy(mom_h).to(dev), torch.from_numpy(w_h).to(dev)
+        c = rwgt.Context(dev.index or 0, stream.cuda_stream)
+        c.set_process(wl.process, "fp64")
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(pts)
+        nb = c.workspace_bytes(E)
+        ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        c.load_events(mom, w, E, ws, nb)
+        c.autotune(max_events=min(E, 1 << 18))
+        wn_sep = torch.empty((pts.shape[0], E), dtype=torch.float64, device=dev)
+        wn_one = torch.empty_like(wn_sep)
+        items.append({"ctx": c, "keep": (mom, w, ws), "sep": wn_sep, "one": wn_one, "E": E, "P": pts.shape[0],
+                      "process": wl.process, "tuning": c.get_tuning()})
+    m = rwgt.Multi(dev.index or 0, stream.cuda_stream)
+    for it in items:
+        m.add(it["ctx"], it["one"])
+    mb = m.workspace_bytes()
+    mws = torch.zeros(mb, dtype=torch.uint8, device=dev)
+    t_one = timed_steps(torch, stream, lambda: m.reweight_async(mws, mb), args.steps, args.warmup, flush)
+
+    def separate():
+        for it in items:
+            it["ctx"].reweight_async(it["sep"])
+    t_sep = timed_steps(torch, stream, separate, args.steps, args.warmup, flush)
+    diff = max(float(torch.max(torch.abs(it["one"] - it["sep"]) / torch.clamp(torch.abs(it["sep"]), min=1e-300)).item())
+               for it in items)
+    n = sum(it["E"] * it["P"] for it in items)
+    a, b = statistics.median(t_one), statistics.median(t_sep)
+    m.close()
+    for it in items:
+        it["ctx"].close()
+    return {"workload": "gg_tt_1m + gg_ttg 262144 events (Born + real emission)", "mode": "fp64",
+            "processes": [{"process": it["process"], "events": it["E"], "points": it["P"],
+                           "tuning_separate": {"lane_bits": it["tuning"][0], "block": it["tuning"][1]}}
+                          for it in items],
+            "value": n / a, "unit": UNIT, "ms_per_step": 1e3 * a, "separate_ms_per_step": 1e3 * b,
+            "gain_vs_separate": b / a, "max_rel_diff_wnew": diff, "dtype": "f64"}
 
 
 def write_event_file(path, process, mom, w):

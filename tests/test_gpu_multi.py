@@ -201,11 +201,12 @@ def test_born_and_real_emission_sample_from_one_event_file(tmp_path):
     for j in range(len(POINTS)):
         assert abs(tot[j] / math.fsum(ref[j]) - 1) < TOL["fp64"]
     assert abs(tot_orig - math.fsum(np.concatenate([wb, wr]))) <= 2 * np.spacing(tot_orig)
-    # the written weights (11 significant digits), event by event in file order
+    # the written weights (shortest form that reads back as the same double),
+    # event by event in file order: the kernel's W' exactly
     text = (tmp_path / "out.lhe").read_text()
     for j, name in enumerate(ids):
         vals = np.array([float(v) for v in re.findall(rf"<wgt id='{name}'>\s*(\S+)\s*</wgt>", text)])
         assert vals.shape == (len(kinds),)
-        assert np.max(np.abs(vals / ref[j] - 1)) < 1e-10
+        assert np.array_equal(vals, wfile[j])
     for it in items:
         it["ctx"].close()
