@@ -76,6 +76,7 @@ def parse():
                     help="learned-surrogate run on g g -> t tbar g g: train on exact labels, then time "
                          "surrogate inference with exact fallback against the exact kernel")
     ap.add_argument("--train-events", type=int, default=1 << 20)
+    ap.add_argument("--surrogate-layers", type=int, default=4, help="the surrogate network's layers of 256")
     ap.add_argument("--train-steps", type=int, default=64000)
     ap.add_argument("--infer-events", type=int, default=1 << 22)
     ap.add_argument("--interp", type=int, default=0, metavar="K",
@@ -714,11 +715,13 @@ def run_e2e(ctx, torch, dev, mom_h, w_h, E, P, N, world, args):
             "d2h_bytes_per_step": int(8 * (P * E + P + 2)), "ms_per_step": 1e3 * t, "steps": steps}
 
 
-def surrogate_study(args, train_events=1 << 20, train_steps=64000, infer_events=1 << 22, steps=5, warmup=2):
+def surrogate_study(args, train_events=1 << 20, train_steps=64000, infer_events=1 << 22, steps=5, warmup=2,
+                    layers=4):
     """Learned surrogate (g g -> t tbar g g, m_t = kappa 173 GeV): exact FP32
     labels log r on a 16-point kappa grid in [0.8, 1.2] for train_events
-    events (16 x train_events labels), MLP (24 momentum components + kappa + 15
-    invariants -> 4 x 256 SiLU -> (mu, s)) trained by the library's kernels
+    events (16 x train_events labels), MLP (24 momentum components + kappa + the
+    logarithms of the 15 pairwise invariants -> layers x 256 SiLU -> (mu, s))
+    trained by the library's kernels
     (hidden layers' forward on the tcgen05 tensor cores), error threshold
     calibrated on 16,384 held-out events for a 0.1 % violation rate of
     |d log r| <= 1e-3, then infer_events unseen events at kappa = 0.9, 1.1, 1.2
@@ -734,7 +737,7 @@ def surrogate_study(args, train_events=1 << 20, train_steps=64000, infer_events=
     wl = ev.WORKLOADS["gg_ttgg_1m"]
     kg = np.linspace(0.8, 1.2, 16)
     grid = np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in kg])
-    n_in, hidden, layers, batch, p_scale, k_scale = 40, 256, 4, 16384, 2000.0, 0.2
+    n_in, hidden, batch, p_scale, k_scale = 40, 256, 16384, 2000.0, 0.2
 
     def attach(c, mom, w, pts, mode="fp32"):
         E = mom.shape[-1]
@@ -788,77 +791,91 @@ def surrogate_study(args, train_events=1 << 20, train_steps=64000, infer_events=
     calib_err = np.abs(mu - yl)
     n_labels = int(x_tr.shape[0])
     del x_tr, y_tr
-    # inference: surrogate + exact fallback vs exact, same events and points
-    pts = np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in (0.9, 1.1, 1.2)])
-    P = pts.shape[0]
+    # inference: surrogate + exact fallback vs exact, same events and points,
+    # for far shifts of m_t (kappa 0.9, 1.1, 1.2) and for shifts of a few GeV
+    # (m_t = 171, 172, 174, 175 GeV: the top-mass variations of a measurement,
+    # the 175 GeV of the g g -> t tbar sample among them)
     mom_te, w_te = ev.generate(wl, infer_events, start=train_events + 16384)
     E = mom_te.shape[-1]
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
-    with rwgt.Context(0, st) as c:
-        keep = attach(c, mom_te, w_te, pts)
-        c.autotune(max_events=1 << 16)
-        w_ex = torch.empty((P, E), dtype=torch.float64, device=dev)
-        t_ex = []
-        for i in range(warmup + steps):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            c.reweight_async(w_ex)
-            sig_ex, _, _, _ = c.get_results(P)
-            if i >= warmup:
-                t_ex.append(time.perf_counter() - t1)
-        sb = c.surrogate_workspace_bytes(n_in)
-        sws = torch.empty(sb, dtype=torch.uint8, device=dev)
-        w_su = torch.empty((P, E), dtype=torch.float64, device=dev)
-        flag = torch.empty((P, E), dtype=torch.uint8, device=dev)
-        t_su = []
-        for i in range(warmup + steps):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            sig_su, nfb = rwgt.surrogate_reweight(c, m, p_scale, k_scale, s_max, w_su, flag, P, sws, sb)
-            if i >= warmup:
-                t_su.append(time.perf_counter() - t1)
-        # the network alone on the inference rows (features of every event and point)
-        xi = torch.empty((P * E, n_in), dtype=torch.float32, device=dev)
-        rwgt.surrogate_features(c, n_in, p_scale, k_scale, None, xi, None)
-        oi = torch.empty((P * E, 2), dtype=torch.float32, device=dev)
-        t_nn = []
-        for i in range(warmup + steps):
-            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a_.record()
-            m.forward(xi, oi)
-            b_.record()
-            torch.cuda.synchronize()
-            if i >= warmup:
-                t_nn.append(a_.elapsed_time(b_) * 1e-3)
-        m.status()
-        del keep, xi, oi
-    fl = flag.cpu().numpy().astype(bool)
-    a, b = w_su.cpu().numpy(), w_ex.cpu().numpy()
-    err = np.abs(np.log(a[~fl] / b[~fl])) if (~fl).any() else np.zeros(0)
-    t_ex_s, t_su_s, t_nn_s = statistics.median(t_ex), statistics.median(t_su), min(t_nn)
-    rows = P * E
+
+    def infer(kappas):
+        pts = np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in kappas])
+        P = pts.shape[0]
+        with rwgt.Context(0, st) as c:
+            keep = attach(c, mom_te, w_te, pts)
+            c.autotune(max_events=1 << 16)
+            w_ex = torch.empty((P, E), dtype=torch.float64, device=dev)
+            t_ex = []
+            for i in range(warmup + steps):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                c.reweight_async(w_ex)
+                sig_ex, _, _, _ = c.get_results(P)
+                if i >= warmup:
+                    t_ex.append(time.perf_counter() - t1)
+            sb = c.surrogate_workspace_bytes(n_in)
+            sws = torch.empty(sb, dtype=torch.uint8, device=dev)
+            w_su = torch.empty((P, E), dtype=torch.float64, device=dev)
+            flag = torch.empty((P, E), dtype=torch.uint8, device=dev)
+            t_su = []
+            for i in range(warmup + steps):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                sig_su, nfb = rwgt.surrogate_reweight(c, m, p_scale, k_scale, s_max, w_su, flag, P, sws, sb)
+                if i >= warmup:
+                    t_su.append(time.perf_counter() - t1)
+            # the network alone on the inference rows (features of every event and point)
+            xi = torch.empty((P * E, n_in), dtype=torch.float32, device=dev)
+            rwgt.surrogate_features(c, n_in, p_scale, k_scale, None, xi, None)
+            oi = torch.empty((P * E, 2), dtype=torch.float32, device=dev)
+            t_nn = []
+            for i in range(warmup + steps):
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record()
+                m.forward(xi, oi)
+                b_.record()
+                torch.cuda.synchronize()
+                if i >= warmup:
+                    t_nn.append(a_.elapsed_time(b_) * 1e-3)
+            m.status()
+            del keep, xi, oi
+        fl = flag.cpu().numpy().astype(bool)
+        a, b = w_su.cpu().numpy(), w_ex.cpu().numpy()
+        err = np.abs(np.log(a[~fl] / b[~fl])) if (~fl).any() else np.zeros(0)
+        t_ex_s, t_su_s = statistics.median(t_ex), statistics.median(t_su)
+        return {
+            "points_kappa": [float(k) for k in kappas], "m_t": [float(k * ev.M_TOP) for k in kappas],
+            "value": E * P / t_su_s, "ms_per_step": 1e3 * t_su_s,
+            "exact_value": E * P / t_ex_s, "exact_ms": 1e3 * t_ex_s, "gain_vs_exact": t_ex_s / t_su_s,
+            "fallback_fraction": float(fl.mean()), "accepted_fraction": float(1.0 - fl.mean()),
+            "events_fully_accepted": float((~fl).all(axis=0).mean()),
+            "accepted_violation_rate": float(np.mean(err > 1e-3)) if err.size else 0.0,
+            "accepted_err_max": float(err.max()) if err.size else 0.0,
+            "sigma_rel_diff": [float(x / y - 1) for x, y in zip(sig_su, sig_ex)],
+        }, P * E, min(t_nn)
+
+    far, rows, t_nn_s = infer((0.9, 1.1, 1.2))
+    near, _, _ = infer(tuple(mt / ev.M_TOP for mt in (171.0, 172.0, 174.0, 175.0)))
     # algorithmic flops of the network per row: input layer, hidden layers, output layer
     net_flops = rows * 2 * (n_in * hidden + hidden * hidden * (layers - 1) + hidden * 2)
     # the MMAs the one-kernel inference issues: the split input layer over K = 128
     mma_flops = rows * 2 * (128 * hidden + hidden * hidden * (layers - 1))
     m.close()
-    return {
-        "workload": "surrogate gg_ttgg", "infer_events": E, "points_kappa": [0.9, 1.1, 1.2],
-        "value": E * P / t_su_s, "unit": UNIT, "ms_per_step": 1e3 * t_su_s,
+    out = {"workload": "surrogate gg_ttgg", "infer_events": E}
+    out.update(far)
+    out.update({
         "dtype": "bf16 MLP (fp32 first/last layers) + f32 exact fallback",
         "train_events": train_events, "train_labels": n_labels, "train_steps": train_steps, "batch": batch,
         "mlp": f"{n_in}->{layers}x{hidden} SiLU->2",
         "error_bound": "|d log r| <= 1e-3, calibrated for 0.1 % violations on 16384 held-out events x 16 kappa",
-        "exact_value": E * P / t_ex_s, "exact_ms": 1e3 * t_ex_s, "gain_vs_exact": t_ex_s / t_su_s,
-        "fallback_fraction": float(fl.mean()), "accepted_fraction": float(1.0 - fl.mean()),
-        "accepted_violation_rate": float(np.mean(err > 1e-3)) if err.size else 0.0,
-        "accepted_err_max": float(err.max()) if err.size else 0.0,
         "held_out_abs_dlogr_median": float(np.median(calib_err)),
+        "held_out_accepted_fraction": float(np.mean(s_err <= s_max)),
         "held_out_abs_dlogr_p90": float(np.quantile(calib_err, 0.9)),
-        "sigma_rel_diff": [float(x / y - 1) for x, y in zip(sig_su, sig_ex)],
         "label_seconds": t_labels, "train_seconds": t_train, "s_max": s_max,
+        "near_shifts": near,
         "network_inference": {"rows": rows, "ms": 1e3 * t_nn_s, "rows_per_s": rows / t_nn_s,
                               "kernel": "k_mlp_infer (whole network, tcgen05, activations in shared memory)",
                               "algorithmic_tflops": net_flops / t_nn_s / 1e12,
@@ -866,12 +883,14 @@ def surrogate_study(args, train_events=1 << 20, train_steps=64000, infer_events=
                               "roofline": None},
         "timing": "wall clock per step incl. host sync (both paths), L2 flushed before each step; the network "
                   "alone timed with CUDA events",
-    }
+    })
+    return out
 
 
 def run_surrogate(args):
     """The surrogate study as its own bench line (--surrogate)."""
-    r = surrogate_study(args, args.train_events, args.train_steps, args.infer_events, args.steps, args.warmup)
+    r = surrogate_study(args, args.train_events, args.train_steps, args.infer_events, args.steps, args.warmup,
+                        args.surrogate_layers)
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic",

@@ -293,8 +293,8 @@ int rw_mlp_hidden_layer(rw_mlp* m, int layer, const void* d_h_in, int64_t n, flo
 /* Surrogate features of the attached events for every point p, row p*E + e:
    x = (p_i^mu / p_scale for all N particles after the rotation about the beam
    axis that puts the top's p_T along +x, (kappa_p - 1)/k_scale, then -- when
-   n_in leaves room for them -- the N(N-1)/2 pairwise invariants
-   2 p_i.p_j / s-hat, zero padding) [n_in],
+   n_in leaves room for them -- the logarithms of the N(N-1)/2 pairwise
+   invariants, log(2 p_i.p_j / s-hat), zero padding) [n_in],
    kappa_p = m_t(point p) / m_t(original); and, when d_ratio [P][E] is not NULL,
    labels y [P*E] = log r / (kappa_p - 1) (0 where r <= 0 or kappa_p = 1): the
    network's mu predicts log r per unit shift and s the log of its error in
@@ -303,10 +303,14 @@ int rw_surrogate_features(rw_ctx* ctx, int n_in, double p_scale, double k_scale,
                           float* d_y);
 /* Surrogate reweighting of the attached events for every point (Sec. 3.2
    steps 5-7 with the MLP in place of |M'|^2/|M|^2): r = exp((kappa-1) mu);
-   events whose predicted log error of log r, s + log|kappa - 1|, exceeds s_max
-   fall back to the exact fused kernel; W'[P][E],
-   optional fallback flags [P][E] (1 = exact), sigma'_p (h_sigma [P]) and the
-   fallback counts (h_n_fallback [P]).  The model must be created on the
+   where the predicted log error of log r, s + log|kappa - 1|, exceeds s_max
+   the event is recomputed by the exact fused kernel (its W' there is the exact
+   path's, bit for bit): with P <= 6 points the events are grouped by the set
+   of points they need and each group is one exact launch at just those
+   points; with more points an event over the bound at any point is
+   recomputed at every point.  W'[P][E], optional fallback flags [P][E]
+   (1 = exact), sigma'_p (h_sigma [P]) and the fallback counts (h_n_fallback
+   [P]: events recomputed at point p).  The model must be created on the
    context's stream with the width n_in used here.  Device workspace of
    rw_surrogate_workspace_bytes(ctx, n_in); synchronises. */
 size_t rw_surrogate_workspace_bytes(const rw_ctx* ctx, int n_in);

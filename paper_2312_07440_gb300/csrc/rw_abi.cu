@@ -231,6 +231,32 @@ int ready(rw_ctx* c, bool need_events) {
   return RW_OK;
 }
 
+// Raise a kernel's dynamic shared-memory limit to at least `smem` bytes.  The
+// limit belongs to the function, not to a context or a launch shape, so it is
+// only ever raised: lowering it for a smaller launch would make the next
+// larger launch of the same kernel fail.
+cudaError_t ensure_smem(const void* func, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= smem) return cudaSuccess;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// a kernel's static shared memory (its __shared__ arrays), which counts
+// against the same per-block limit as the dynamic part
+size_t static_smem(const void* func) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return fa.sharedSizeBytes;
+}
+
 // launch the fused kernel; `points` empty => single evaluation mode
 // launch shape of the current kernel variant: the entry, threads per block,
 // lanes per event, shared memory and resident blocks per SM for P points
@@ -247,17 +273,18 @@ int shape(rw_ctx* c, int P, Shape& sh) {
   const int block = c->block > 0 ? c->block : 128;
   if (block > k->max_block) return fail(c, RW_ERR_ARG, "block %d above this variant's %d", block, k->max_block);
   const size_t smem = (size_t)k->smem_per_thread * block + (size_t)(block / 32) * (P + 1) * sizeof(double2);
-  if (c->smem_optin > 0 && smem > (size_t)c->smem_optin)
-    return fail(c, RW_ERR_ARG, "block %d needs %zu bytes of shared memory, more than the %d a block may have", block,
-                smem, c->smem_optin);
+  const size_t smem_total = smem + static_smem(k->func);
+  if (c->smem_optin > 0 && smem_total > (size_t)c->smem_optin)
+    return fail(c, RW_ERR_ARG,
+                "block %d with %d points needs %zu bytes of shared memory, more than the %d a block may have", block, P,
+                smem_total, c->smem_optin);
+  // opt in to more than the default 48 KB of dynamic shared memory
+  if (cudaError_t e = ensure_smem(k->func, smem); e != cudaSuccess)
+    return cuda_fail(c, e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
   auto key = std::make_tuple(k->func, block, smem);
   auto it = c->occ.find(key);
   int per_sm;
   if (it == c->occ.end()) {
-    if (smem > 48 * 1024) {  // opt in to more than the default 48 KB of dynamic shared memory
-      cudaError_t e = cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return cuda_fail(c, e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
-    }
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, block, smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1) per_sm = 1;
@@ -285,6 +312,7 @@ int launch(rw_ctx* c, RwArgs& a) {
 }
 
 void fill_ws(rw_ctx* c, RwArgs& a, int P);
+void fill_core(char* b, RwArgs& a, int P);
 
 // the fused reweight of all attached events and points
 void reweight_args(rw_ctx* c, RwArgs& a, double* d_wnew, double* d_ratio, double* d_me0, double* d_me_pts) {
@@ -307,8 +335,10 @@ void reweight_args(rw_ctx* c, RwArgs& a, double* d_wnew, double* d_ratio, double
   fill_ws(c, a, P);
 }
 
-void fill_ws(rw_ctx* c, RwArgs& a, int P) {
-  char* b = c->ws;
+void fill_ws(rw_ctx* c, RwArgs& a, int P) { fill_core(c->ws, a, P); }
+
+// the reduction slots of a launch of P points in a core region of ws_core_bytes(P)
+void fill_core(char* b, RwArgs& a, int P) {
   a.ticket = reinterpret_cast<unsigned int*>(b);
   a.nbad_count = reinterpret_cast<unsigned long long*>(b + 8);
   a.sigma = reinterpret_cast<double*>(b + 64);
@@ -835,9 +865,9 @@ extern "C" int rw_reweight_noalloc(rw_ctx* c, const double* d_mom, const double*
   const int block = c->block > 0 ? c->block : 128;
   if (block > k->max_block) return noalloc_fail(c, RW_ERR_ARG, "block too large");
   const size_t smem = (size_t)k->smem_per_thread * block + (size_t)(block / 32) * (P + 1) * sizeof(double2);
-  if (c->smem_optin > 0 && smem > (size_t)c->smem_optin) return noalloc_fail(c, RW_ERR_ARG, "block too large");
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (c->smem_optin > 0 && smem + static_smem(k->func) > (size_t)c->smem_optin)
+    return noalloc_fail(c, RW_ERR_ARG, "block too large");
+  if (ensure_smem(k->func, smem) != cudaSuccess) {
     cudaGetLastError();
     return noalloc_fail(c, RW_ERR_CUDA, "smem attribute");
   }
@@ -890,7 +920,8 @@ struct KappaList {
 
 // Features x[(p*E + e)][0..n_in): the event's momenta / p_scale after the
 // azimuthal rotation about the beam that puts the top's p_T along +x (|M|^2 is
-// invariant under it), then (kappa_p - 1)/k_scale, zero padding.  Label
+// invariant under it), then (kappa_p - 1)/k_scale, then (room permitting) the
+// logarithms of the pairwise invariants, zero padding.  Label
 // y = log r / (kappa_p - 1): the network learns the log ratio per unit shift,
 // so r = 1 at kappa = 1 holds exactly (y = 0 when kappa_p = 1 or r <= 0).
 __global__ void k_features(const double* __restrict__ mom, long long ld, long long E, int N, int P, KappaList kap,
@@ -914,7 +945,10 @@ __global__ void k_features(const double* __restrict__ mom, long long ld, long lo
   }
   const double dk = (double)kap.k[p] - 1.0;
   if (j < n_in) xr[j++] = (float)(dk * inv_ks);
-  // with room for them, the pairwise invariants 2 p_i.p_j / s-hat (i < j)
+  // with room for them, the logarithms of the pairwise invariants 2 p_i.p_j / s-hat
+  // (i < j; all positive for physical momenta): the propagator denominators are
+  // sums of these, and |M|^2 varies over decades as one of them goes to zero,
+  // which a logarithmic input spreads out for the network
   if (n_in - j >= N * (N - 1) / 2) {
     double q[8][4];
     for (int i = 0; i < N && i < 8; ++i)
@@ -924,7 +958,8 @@ __global__ void k_features(const double* __restrict__ mom, long long ld, long lo
     const double ish = sh > 0.0 ? 2.0 / sh : 0.0;
     for (int a = 0; a < N && a < 8; ++a)
       for (int b2 = a + 1; b2 < N && b2 < 8; ++b2)
-        xr[j++] = (float)((q[a][0] * q[b2][0] - q[a][1] * q[b2][1] - q[a][2] * q[b2][2] - q[a][3] * q[b2][3]) * ish);
+        xr[j++] = (float)log(fmax((q[a][0] * q[b2][0] - q[a][1] * q[b2][1] - q[a][2] * q[b2][2] -
+                                   q[a][3] * q[b2][3]) * ish, 1e-30));
   }
   for (; j < n_in; ++j) xr[j] = 0.0f;
   if (ratio && y) {
@@ -933,12 +968,18 @@ __global__ void k_features(const double* __restrict__ mom, long long ld, long lo
   }
 }
 
+// Events are recomputed exactly at the points where the network's estimate is
+// over the bound: with up to MASK_POINTS points, the events are grouped by
+// that set of points (one exact launch per group, with just those points);
+// with more, an event over the bound at any point is recomputed at all points.
+constexpr int MASK_POINTS = 6;
+constexpr int N_GROUPS = 1 << MASK_POINTS;
+
 // Accept W' = exp((kappa-1) mu) W where s + log|kappa-1| <= s_max (the
-// network's predicted log error of log r), else list the event for the exact
-// path; kappa = 1 gives W' = W exactly.
+// network's predicted log error of log r), else mark (event, point) for the
+// exact path in the event's bit mask; kappa = 1 gives W' = W exactly.
 __global__ void k_decide(const float* __restrict__ out, const double* __restrict__ w, long long E, int P,
-                         KappaList kap, float s_max, double* __restrict__ wnew, unsigned char* __restrict__ flag,
-                         unsigned long long* __restrict__ count, long long* __restrict__ list) {
+                         KappaList kap, float s_max, double* __restrict__ wnew, unsigned* __restrict__ mask) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)P * E) return;
   const int p = (int)(t / E);
@@ -953,13 +994,42 @@ __global__ void k_decide(const float* __restrict__ out, const double* __restrict
     lr = dk * (double)mu;
     accept = isfinite(mu) && isfinite(s) && (double)s + log(fabs(dk)) <= (double)s_max;
   }
-  if (flag) flag[t] = accept ? 0 : 1;
-  if (accept) {
-    wnew[t] = exp(lr) * w[e];
-  } else {
-    const unsigned long long i = atomicAdd(count + p, 1ull);
-    list[(long long)p * E + (long long)i] = e;
-  }
+  wnew[t] = accept ? exp(lr) * w[e] : 0.0;
+  if (!accept) atomicOr(mask + e, P <= MASK_POINTS ? 1u << p : 1u);
+}
+
+// the group of a marked event: its mask (<= MASK_POINTS points) or group 1 (all points)
+__device__ __forceinline__ unsigned group_of(unsigned m, int P) { return (m && P > MASK_POINTS) ? 1u : m; }
+__device__ __forceinline__ bool exact_at(unsigned m, int P, int p) {
+  return P <= MASK_POINTS ? ((m >> p) & 1u) != 0 : m != 0;
+}
+
+// events per group and each marked event's rank in its group
+__global__ void k_count_groups(const unsigned* __restrict__ mask, long long E, int P,
+                               unsigned long long* __restrict__ count, long long* __restrict__ rank) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const unsigned g = group_of(mask[e], P);
+  if (g) rank[e] = (long long)atomicAdd(count + g, 1ull);
+}
+
+struct GroupOffsets {
+  long long off[N_GROUPS];
+};
+
+// the groups' event lists, one after the other (order within a group
+// unspecified: each event's exact result does not depend on its place in the
+// batch); fallback flags [P][E] (1 = exact)
+__global__ void k_place_groups(const unsigned* __restrict__ mask, const long long* __restrict__ rank, long long E,
+                               int P, GroupOffsets go, unsigned char* __restrict__ flag,
+                               long long* __restrict__ list) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const unsigned m = mask[e];
+  const unsigned g = group_of(m, P);
+  if (g) list[go.off[g] + rank[e]] = e;
+  if (flag)
+    for (int p = 0; p < P; ++p) flag[(long long)p * E + e] = exact_at(m, P, p) ? 1 : 0;
 }
 
 __global__ void k_gather_events(const double* __restrict__ mom, long long ld, const double* __restrict__ w, int N,
@@ -972,10 +1042,17 @@ __global__ void k_gather_events(const double* __restrict__ mom, long long ld, co
   w_g[i] = w[e];
 }
 
-__global__ void k_scatter(const double* __restrict__ v, const long long* __restrict__ list, long long n,
-                          double* __restrict__ dst) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[list[i]] = v[i];
+struct RowMap {
+  int row[RW_MAX_POINTS];
+};
+
+// row k of v [np][n] to row rows.row[k] of dst [P][E] at the listed events
+__global__ void k_scatter(const double* __restrict__ v, const long long* __restrict__ list, long long n, int np,
+                          RowMap rows, long long E, double* __restrict__ dst) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)np * n) return;
+  const long long k = t / n, i = t % n;
+  dst[(long long)rows.row[k] * E + list[i]] = v[t];
 }
 
 __device__ __forceinline__ void ts_acc(double& s, double& c, double x, double cx) {
@@ -1030,7 +1107,7 @@ cudaError_t row_sums(cudaStream_t st, const double* wnew, long long E, int P, co
 }
 
 struct SurrogateLayout {
-  size_t core, x, out, counts, list, mom_g, w_g, wn_g, part, sig, total;
+  size_t core, x, out, mask, counts, rank, list, mom_g, w_g, wn_g, part, sig, total;
 };
 
 SurrogateLayout surrogate_layout(const rw_ctx* c, int n_in) {
@@ -1042,14 +1119,16 @@ SurrogateLayout surrogate_layout(const rw_ctx* c, int n_in) {
     o += align256(bytes);
     return at;
   };
-  L.core = take(ws_core_bytes(1));
+  L.core = take(ws_core_bytes((int)P));
   L.x = take(4 * P * E * n_in);
   L.out = take(4 * P * E * 2);
-  L.counts = take(8 * P);
-  L.list = take(8 * P * E);
+  L.mask = take(4 * E);
+  L.counts = take(8 * N_GROUPS);
+  L.rank = take(8 * E);
+  L.list = take(8 * E);
   L.mom_g = take(8 * 4 * N * E);
   L.w_g = take(8 * E);
-  L.wn_g = take(8 * E);
+  L.wn_g = take(8 * P * E);
   L.part = take(16 * SUM_BLOCKS * (P + 1));
   L.sig = take(8 * (P + 1));
   L.total = o;
@@ -1107,7 +1186,9 @@ int rw_surrogate_reweight(rw_ctx* c, rw_mlp* m, double p_scale, double k_scale, 
   char* b = static_cast<char*>(d_ws);
   float* x = reinterpret_cast<float*>(b + L.x);
   float* out = reinterpret_cast<float*>(b + L.out);
+  unsigned* mask = reinterpret_cast<unsigned*>(b + L.mask);
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(b + L.counts);
+  long long* rank = reinterpret_cast<long long*>(b + L.rank);
   long long* list = reinterpret_cast<long long*>(b + L.list);
   double* mom_g = reinterpret_cast<double*>(b + L.mom_g);
   double* w_g = reinterpret_cast<double*>(b + L.w_g);
@@ -1118,47 +1199,62 @@ int rw_surrogate_reweight(rw_ctx* c, rw_mlp* m, double p_scale, double k_scale, 
   const long long E = c->E, tot = (long long)P * E;
   // 1. features, 2. MLP
   if ((rc = rw_surrogate_features(c, nin, p_scale, k_scale, nullptr, x, nullptr))) return rc;
-  cudaError_t e = cudaMemsetAsync(cnt, 0, 8 * (size_t)P, c->stream);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, 8 * (size_t)N_GROUPS, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(mask, 0, 4 * (size_t)E, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "memset");
   if ((rc = rw_mlp_forward(m, x, tot, out))) return fail(c, rc, "mlp forward: %s", rw_mlp_last_error(m));
-  // 3. decision
+  // 3. decision per (event, point), then the events grouped by the points they need exactly
+  const unsigned eb = (unsigned)((E + 255) / 256);
   k_decide<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(out, c->w, E, P, kappas(c), (float)s_max, d_wnew,
-                                                                 d_fallback, cnt, list);
+                                                                 mask);
+  k_count_groups<<<eb, 256, 0, c->stream>>>(mask, E, P, cnt, rank);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "decide launch");
-  if ((e = cudaMemcpyAsync(c->h_stage, cnt, 8 * (size_t)P, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+  if ((e = cudaMemcpyAsync(c->h_stage, cnt, 8 * (size_t)N_GROUPS, cudaMemcpyDeviceToHost, c->stream)) !=
+          cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "fallback counts");
-  std::vector<unsigned long long> counts(P);
-  memcpy(counts.data(), c->h_stage, 8 * (size_t)P);
-  // 4. exact path for the listed events, point by point
-  const double* mom_saved = c->mom;
-  const double* w_saved = c->w;
-  const int64_t ld_saved = c->ld;
-  for (int p = 0; p < P; ++p) {
-    const long long n = (long long)counts[p];
-    if (h_n_fallback) h_n_fallback[p] = n;
+  unsigned long long gn[N_GROUPS];
+  memcpy(gn, c->h_stage, sizeof gn);
+  GroupOffsets go{};
+  long long o = 0;
+  for (int g = 1; g < N_GROUPS; ++g) {
+    go.off[g] = o;
+    o += (long long)gn[g];
+  }
+  k_place_groups<<<eb, 256, 0, c->stream>>>(mask, rank, E, P, go, d_fallback, list);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "group launch");
+  if (h_n_fallback)
+    for (int p = 0; p < P; ++p) h_n_fallback[p] = 0;
+  // 4. per group, the exact fused kernel on its events at its points (one
+  // launch; those W' are the exact path's, bit for bit)
+  for (int g = 1; g < N_GROUPS; ++g) {
+    const long long n = (long long)gn[g];
     if (n == 0) continue;
-    const long long* lp = list + (long long)p * E;
-    k_gather_events<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(mom_saved, ld_saved, w_saved, N, lp, n,
-                                                                         mom_g, w_g);
+    const long long* lg = list + go.off[g];
     RwArgs a{};
+    RowMap rows{};
+    int np = 0;
+    a.pt[0] = make_point(c, c->p0, false);
+    for (int p = 0; p < P; ++p)
+      if (P > MASK_POINTS || ((g >> p) & 1)) {
+        a.pt[1 + np] = make_point(c, c->pts[p], moves_event(c, c->pts[p]));
+        rows.row[np++] = p;
+        if (h_n_fallback) h_n_fallback[p] += n;
+      }
+    k_gather_events<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->mom, c->ld, c->w, N, lg, n, mom_g, w_g);
     a.mom = mom_g;
     a.w = w_g;
     a.E = n;
     a.ld = n;
     a.wnew = wn_g;
-    a.P = 1;
-    a.pt[0] = make_point(c, c->p0, false);
-    a.pt[1] = make_point(c, c->pts[p], moves_event(c, c->pts[p]));
+    a.P = np;
     char* core = b + L.core;
-    a.ticket = reinterpret_cast<unsigned int*>(core);
-    a.nbad_count = reinterpret_cast<unsigned long long*>(core + 8);
-    a.sigma = reinterpret_cast<double*>(core + 64);
-    a.nbad_out = reinterpret_cast<unsigned long long*>(core + 64 + 16);
-    a.block_part = reinterpret_cast<double2*>(core + 256 + align256(8 * 3));
+    fill_core(core, a, np);
+    a.sigma_pair = nullptr;
     if ((e = cudaMemsetAsync(core, 0, 256, c->stream)) != cudaSuccess) return cuda_fail(c, e, "memset");
     if ((rc = launch(c, a))) return rc;
-    k_scatter<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(wn_g, lp, n, d_wnew + (long long)p * E);
+    k_scatter<<<(unsigned)((np * n + 255) / 256), 256, 0, c->stream>>>(wn_g, lg, n, np, rows, E, d_wnew);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "scatter launch");
   }
   // 5. sigma'_p (and sigma of W in the last slot)
   if ((e = row_sums(c->stream, d_wnew, E, P, c->w, part, sig)) != cudaSuccess) return cuda_fail(c, e, "sum launch");
@@ -1380,8 +1476,7 @@ int rw_reweight_interp(rw_ctx* c, int n_nodes, double tol, double* d_wnew, unsig
     Shape sh;
     if ((rc = shape(c, 0, sh))) return rc;
     const size_t ismem = (size_t)k->smem_per_thread * sh.block;
-    if (ismem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem)) != cudaSuccess)
+    if ((e = ensure_smem(k->func, ismem)) != cudaSuccess)
       return cuda_fail(c, e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
     int per_sm = 1;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, sh.block, ismem)) != cudaSuccess)
@@ -1606,8 +1701,7 @@ int rw_multi_reweight_async(rw_multi* m, void* d_ws, size_t ws_bytes) {
   int per_sm = 0;
   const auto it = m->occ.find(key);
   if (it == m->occ.end()) {
-    cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024) e = cudaFuncSetAttribute(k->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem(k->func, smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k->func, block, smem);
     if (e != cudaSuccess) {
       cudaGetLastError();

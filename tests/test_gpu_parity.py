@@ -422,6 +422,48 @@ def test_mixed_modes_every_block_size(block):
     assert rel(g["me0"], o["me0"]).max() < b and rel(g["me"], o["me"]).max() < b
 
 
+def test_point_count_changes_on_one_context():
+    """A kernel whose shared memory is far above the 48 KB default, launched on
+    one context with 2 points, then 1, then 2 again: every launch runs (a
+    kernel's shared-memory limit is only ever raised) and gives the same W' as
+    a fresh context with that point set, bit for bit.  With 3 points the block
+    (its static shared memory included) no longer fits: an argument error,
+    after which the context still works."""
+    wl = ev.WORKLOADS["gg_ttgg_1m"]
+    E = 300
+    mom, w = ev.generate(wl, E, start=777)
+    sets = [np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in ks]) for ks in ((0.9, 1.2), (1.1,))]
+    three = np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in (0.9, 1.1, 1.2)])
+    dm, dw = to_dev(mom), to_dev(w)
+    st = torch.cuda.current_stream(DEV).cuda_stream
+    with rwgt.Context(0, st) as c:
+        c.set_process("gg_ttgg", "fp32")
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(three)  # the workspace sized for up to 3 points
+        c.set_tuning(3, 256)  # 256 threads x (current store + constants): about 227 KB
+        nb = c.workspace_bytes(E)
+        ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+        c.load_events(dm, dw, E, ws, nb)
+        for pts in (sets[0], sets[1], sets[0]):
+            c.set_reweight_points(pts)
+            wn = torch.empty((pts.shape[0], E), dtype=torch.float64, device=DEV)
+            c.reweight_async(wn)
+            torch.cuda.synchronize()
+            ref = run_gpu("gg_ttgg", "fp32", mom, w, pts, lane_bits=3, block=256)
+            assert np.array_equal(wn.cpu().numpy(), ref["wnew"])
+        c.set_reweight_points(three)
+        wn = torch.empty((3, E), dtype=torch.float64, device=DEV)
+        with pytest.raises(rwgt.RwError) as x:
+            c.reweight_async(wn)
+        assert x.value.code == -2
+        c.set_reweight_points(sets[1])
+        wn = torch.empty((1, E), dtype=torch.float64, device=DEV)
+        c.reweight_async(wn)
+        torch.cuda.synchronize()
+        assert np.array_equal(wn.cpu().numpy(), run_gpu("gg_ttgg", "fp32", mom, w, sets[1], lane_bits=3,
+                                                         block=256)["wnew"])
+
+
 def test_block_too_large_for_shared_memory_is_an_argument_error():
     """g g -> t tbar g g in a mixed mode keeps 936 bytes per thread in shared
     memory: a 256-thread block does not fit, and asking for one is an argument

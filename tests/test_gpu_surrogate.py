@@ -327,3 +327,61 @@ def test_surrogate_pipeline_gg_ttgg():
         print(f"kappa {k_te[j]:.2f}: exact evaluations for sigma' at equal error reduced {gain:.0f}x "
               f"(median |r_net/r - 1| {np.median(np.abs(r_net[j] / r_ex[j] - 1)):.1e})")
         assert gain > 4.0
+
+
+@pytest.mark.parametrize("kappas", [(0.85, 0.95, 1.05, 1.2), (0.82, 0.86, 0.9, 0.95, 1.05, 1.1, 1.15, 1.2)])
+def test_surrogate_fallback_groups(kappas):
+    """The fallback bookkeeping with an untrained network and a threshold that
+    splits the (event, point) pairs: accepted pairs get exp((kappa-1) mu) W,
+    every other pair the exact kernel's W' bit for bit; with up to 6 points an
+    event is recomputed exactly at just its rejected points, with more at all
+    of them; counts and sums match the flags and weights."""
+    wl = ev.WORKLOADS["gg_ttgg_1m"]
+    n_in, E = 40, 1500
+    mom, w = ev.generate(wl, E, start=50000)
+    pts = np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in kappas])
+    P = pts.shape[0]
+    st = stream()
+    ex = exact_ratios("fp32", wl, mom, w, pts)
+    with rwgt.Mlp(0, st, n_in, 256, 4, 8192, seed=77) as m, rwgt.Context(0, st) as c:
+        c.set_process("gg_ttgg", "fp32")
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(pts)
+        dm, dw = torch.from_numpy(mom).to(DEV), torch.from_numpy(w).to(DEV)
+        nb = c.workspace_bytes(E)
+        ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+        c.load_events(dm, dw, E, ws, nb)
+        x = torch.empty((P * E, n_in), dtype=torch.float32, device=DEV)
+        rwgt.surrogate_features(c, n_in, P_SCALE, K_SCALE, None, x, None)
+        o = torch.empty((P * E, 2), dtype=torch.float32, device=DEV)
+        m.forward(x, o)
+        torch.cuda.synchronize()
+        o = o.cpu().numpy().astype(np.float64)
+        dk = np.repeat(np.float32(np.asarray(kappas) * ev.M_TOP / ev.M_TOP).astype(np.float64) - 1.0, E)
+        crit = np.sort(o[:, 1] + np.log(np.abs(dk)))
+        i = len(crit) // 2
+        while i + 2 < len(crit) and crit[i + 1] - crit[i] < 1e-9 * max(1.0, abs(crit[i])):
+            i += 1
+        s_max = 0.5 * (crit[i] + crit[i + 1])  # about half the pairs over the bound, none near it
+        sb = c.surrogate_workspace_bytes(n_in)
+        sws = torch.empty(sb, dtype=torch.uint8, device=DEV)
+        wnew = torch.empty((P, E), dtype=torch.float64, device=DEV)
+        flag = torch.empty((P, E), dtype=torch.uint8, device=DEV)
+        sig, nfb = rwgt.surrogate_reweight(c, m, P_SCALE, K_SCALE, s_max, wnew, flag, P, sws, sb)
+        torch.cuda.synchronize()
+    wn, fl = wnew.cpu().numpy(), flag.cpu().numpy().astype(bool)
+    exw = ex["wnew"].cpu().numpy()
+    over = ((o[:, 1] + np.log(np.abs(dk))) > s_max).reshape(P, E)
+    assert 0.2 < over.mean() < 0.8
+    if P <= 6:
+        assert np.array_equal(fl, over)  # exactly the rejected pairs
+        assert not (fl == fl[0]).all()
+    else:
+        assert np.array_equal(fl, np.broadcast_to(over.any(axis=0), (P, E)))  # whole events
+    assert np.array_equal(nfb, fl.sum(axis=1))
+    assert np.array_equal(wn[fl], exw[fl])
+    acc = ~fl
+    net = np.exp(dk * o[:, 0]).reshape(P, E) * w[None, :]
+    assert np.allclose(wn[acc], net[acc], rtol=1e-14, atol=0)
+    for j in range(P):
+        assert abs(sig[j] - math.fsum(wn[j])) <= 4 * np.spacing(sig[j])
