@@ -24,7 +24,16 @@
 
 namespace rw {
 
-enum ColourMode { CM_FMA = 0, CM_FP16 = 1, CM_BF16 = 2 };
+// CM_STORE_FP16 / CM_STORE_BF16: the amplitude code writes each J vector
+// (rounded to FP16 / BF16) to global memory for a separate tensor-core colour
+// pass instead of summing colours itself (colour_tc.cuh).
+enum ColourMode { CM_FMA = 0, CM_FP16 = 1, CM_BF16 = 2, CM_STORE_FP16 = 3, CM_STORE_BF16 = 4 };
+
+// the sink of the fused kernels: nothing is stored
+struct NoSink {
+  template <int K>
+  __device__ __forceinline__ void put(const cx<float> (&)[K]) {}
+};
 
 template <int CM>
 __device__ __forceinline__ unsigned short to_16(float x) {

@@ -22,11 +22,15 @@ static __device__ const short CI[K * K] = {16, -2, -2, 16};  // row-major C_int 
 
 // Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;
 // helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).
-// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float).
-template <class R, int LB, int CM = CM_FMA, bool JS = false>
-__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
+// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float);
+// CM_STORE_FP16/CM_STORE_BF16: no colour sum here, each J vector goes to sink->put()
+// for a later tensor-core pass (the return value is then 0).
+template <class R, int LB, int CM = CM_FMA, bool JS = false, class Sink = NoSink>
+__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane,
+                                     [[maybe_unused]] Sink* sink = nullptr) {
   static_assert(CM == CM_FMA || sizeof(R) == 4, "tensor-core colour sum takes FP32 amplitudes");
-  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI, JS ? NJS * 32 : 0);
+  constexpr bool MMA = CM == CM_FP16 || CM == CM_BF16;
+  const ColourMma<K, MMA ? CM : CM_FP16> cmma(MMA ? CI : nullptr, JS ? NJS * 32 : 0);
   JStore<R, NJS, JS> js;
   R acc = R(0);
   [[maybe_unused]] R cc0_0 = R(0), cc1_0 = R(0), cc0_1 = R(0), cc1_1 = R(0);  // per distinct c_ij and top helicity
@@ -70,7 +74,12 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
         if constexpr (CM != CM_FMA) {
           const cx<float> Aa0[K] = {A0_0, A1_0};
           const cx<float> Aa1[K] = {A0_1, A1_1};
-          acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip
+          if constexpr (MMA) {
+            acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip
+          } else {
+            sink->put(Aa0);
+            sink->put(Aa1);
+          }
         } else {
           cc0_0 = fmadd(A0_0.r, A0_0.r, fmadd(A0_0.i, A0_0.i, cc0_0));
           cc1_0 = fmadd(A0_0.r, A1_0.r, fmadd(A0_0.i, A1_0.i, cc1_0));

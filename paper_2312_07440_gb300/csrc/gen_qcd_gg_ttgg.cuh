@@ -22,11 +22,15 @@ static __device__ const short CI[K * K] = {512, -64, -64, 8, 8, 80, -64, 8, 8, -
 
 // Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;
 // helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).
-// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float).
-template <class R, int LB, int CM = CM_FMA, bool JS = false>
-__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {
+// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float);
+// CM_STORE_FP16/CM_STORE_BF16: no colour sum here, each J vector goes to sink->put()
+// for a later tensor-core pass (the return value is then 0).
+template <class R, int LB, int CM = CM_FMA, bool JS = false, class Sink = NoSink>
+__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane,
+                                     [[maybe_unused]] Sink* sink = nullptr) {
   static_assert(CM == CM_FMA || sizeof(R) == 4, "tensor-core colour sum takes FP32 amplitudes");
-  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI, JS ? NJS * 32 : 0);
+  constexpr bool MMA = CM == CM_FP16 || CM == CM_BF16;
+  const ColourMma<K, MMA ? CM : CM_FP16> cmma(MMA ? CI : nullptr, JS ? NJS * 32 : 0);
   JStore<R, NJS, JS> js;
   R acc = R(0);
   [[maybe_unused]] R cz0_0 = R(0), cz0_1 = R(0), cz0_2 = R(0), cz0_3 = R(0), cz1_0 = R(0), cz1_1 = R(0), cz1_2 = R(0), cz1_3 = R(0);
@@ -1021,7 +1025,12 @@ __device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>
             if constexpr (CM != CM_FMA) {
               const cx<float> Aa0[K] = {A0_0, A1_0, A2_0, A3_0, A4_0, A5_0, A6_0, A7_0, A8_0, A9_0, A10_0, A11_0, A12_0, A13_0, A14_0, A15_0, A16_0, A17_0, A18_0, A19_0, A20_0, A21_0, A22_0, A23_0};
               const cx<float> Aa1[K] = {A0_1, A1_1, A2_1, A3_1, A4_1, A5_1, A6_1, A7_1, A8_1, A9_1, A10_1, A11_1, A12_1, A13_1, A14_1, A15_1, A16_1, A17_1, A18_1, A19_1, A20_1, A21_1, A22_1, A23_1};
-              acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip
+              if constexpr (MMA) {
+                acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip
+              } else {
+                sink->put(Aa0);
+                sink->put(Aa1);
+              }
             } else {
               { const R zr = R(1024) * A0_0.r + R(-256) * A1_0.r + R(-256) * A2_0.r + R(32) * A3_0.r + R(32) * A4_0.r + R(320) * A5_0.r + R(-256) * A6_0.r + R(32) * A7_0.r + R(32) * A8_0.r + R(-4) * A9_0.r + R(-4) * A10_0.r + R(-40) * A11_0.r + R(32) * A12_0.r + R(-4) * A13_0.r + R(320) * A14_0.r + R(-40) * A15_0.r + R(284) * A16_0.r + R(248) * A17_0.r + R(-4) * A18_0.r + R(-40) * A19_0.r + R(-40) * A20_0.r + R(248) * A21_0.r + R(248) * A22_0.r + R(-112) * A23_0.r; const R zi = R(1024) * A0_0.i + R(-256) * A1_0.i + R(-256) * A2_0.i + R(32) * A3_0.i + R(32) * A4_0.i + R(320) * A5_0.i + R(-256) * A6_0.i + R(32) * A7_0.i + R(32) * A8_0.i + R(-4) * A9_0.i + R(-4) * A10_0.i + R(-40) * A11_0.i + R(32) * A12_0.i + R(-4) * A13_0.i + R(320) * A14_0.i + R(-40) * A15_0.i + R(284) * A16_0.i + R(248) * A17_0.i + R(-4) * A18_0.i + R(-40) * A19_0.i + R(-40) * A20_0.i + R(248) * A21_0.i + R(248) * A22_0.i + R(-112) * A23_0.i;
                 cz0_0 = fmadd(A0_0.r, zr, fmadd(A0_0.i, zi, cz0_0)); }

@@ -54,6 +54,8 @@ struct RwArgs {
   int accumulate;      // 1: add this launch's sums and bad events to the previous launch's
   int P;
   int me_only;  // evaluate pt[0] only and write me0 (no reductions)
+  unsigned char* defer;  // mixed modes with a separate colour pass: its amplitude buffers, or null
+  long long defer_ld;    // rows per amplitude plane (events rounded up to 128)
   PointDev pt[MAX_POINTS + 1];  // [0] original, [1..P] modified points
 };
 

@@ -31,6 +31,7 @@ template <class Tag, int CM = 0>
 struct QcdProc {
   static constexpr int NG = Tag::NG;
   static constexpr int NEXT = Tag::NEXT;
+  static constexpr int NCOL = Tag::NCOL;
   static constexpr bool kSymmetricHelicities = true;
   // per-event constants (external wavefunctions and propagator invariants):
   // one slot per event group in shared memory, written by the group's lanes
@@ -50,7 +51,7 @@ struct QcdProc {
   template <class R>
   static constexpr int store_bytes() {
     return ((Tag::JSMEM && sizeof(R) == 4) ? Tag::NJS * 32 : 0) +
-           (CM != CM_FMA ? ColourStage<(Tag::NCOL + 15) / 16 * 16>::per_thread : 0);
+           ((CM == CM_FP16 || CM == CM_BF16) ? ColourStage<(Tag::NCOL + 15) / 16 * 16>::per_thread : 0);
   }
   template <class R, int LB = 0>
   static constexpr int jstore_bytes() {
@@ -95,6 +96,42 @@ struct QcdProc {
   __device__ __noinline__ static double me(const mom_t<R> (&p)[NEXT][4], const PointDev& pt, int lane,
                                            unsigned gmask) {
     return me_body<R, LB>(p, pt, lane, gmask);
+  }
+
+  // The amplitudes of one event and point for a separate colour pass
+  // (CM_STORE_*): the set-up as in me_body, then every J vector to sink.put();
+  // false when the point's masses do not fit the event (its |M'|^2 is 0).
+  template <class R, int LB, class Sink>
+  __device__ __noinline__ static bool me_store(const mom_t<R> (&p)[NEXT][4], const PointDev& pt, int lane,
+                                               unsigned gmask, Sink& sink) {
+    static_assert(LB <= Tag::MAX_LB, "more lane bits than helicity levels");
+    mom_t<R> q[NEXT][4];
+    bool inside = true;
+    if (pt.reshuffle) {
+      inside = reshuffle<R>(p, pt.m_t, q);
+    } else {
+#pragma unroll
+      for (int i = 0; i < NEXT; ++i)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) q[i][m] = p[i][m];
+    }
+    if constexpr (ksmem<R, LB>()) {
+      extern __shared__ __align__(16) unsigned char rw_dyn_bytes[];
+      unsigned char* slot =
+          rw_dyn_bytes + (size_t)store_bytes<R>() * blockDim.x + (size_t)(threadIdx.x >> LB) * kSlot;
+      QcdExt<R, NG>& X = *reinterpret_cast<QcdExt<R, NG>*>(slot);
+      QcdKin<R, NG>& Kn = *reinterpret_cast<QcdKin<R, NG>*>(slot + sizeof(QcdExt<R, NG>));
+      __syncwarp(gmask);
+      qcd_setup<R, NG, NEXT>(q, pt.m_t, X, Kn);
+      __syncwarp(gmask);
+      Tag::template hel_sum<R, LB, CM>(X, Kn, lane, &sink);
+    } else {
+      QcdExt<R, NG> X;
+      QcdKin<R, NG> Kn;
+      qcd_setup<R, NG, NEXT>(q, pt.m_t, X, Kn);
+      Tag::template hel_sum<R, LB, CM>(X, Kn, lane, &sink);
+    }
+    return inside;
   }
 
   // FP64 mode refines the FP32 Newton solution with two FP64 steps, the FP32

@@ -11,8 +11,9 @@ struct KernelEntry {
   int lane_bits;     // helicity slices per event = 2^lane_bits
   const void* func;  // __global__ k_reweight<...>(RwArgs) or k_interp<...>(InterpArgs)
   int max_block = 256;  // threads per block the variant supports
-  int kind = 0;         // 0: k_reweight, 1: k_interp (interpolation surrogate)
+  int kind = 0;         // 0: k_reweight, 1: k_interp (interpolation surrogate), 2: k_amp_store
   int smem_per_thread = 0;  // dynamic shared memory of the amplitude code (bytes per thread)
+  const void* func2 = nullptr;  // kind 2: the colour pass k_colour_tc<...>(RwArgs, int*)
 };
 
 // a k_reweight_multi instantiation: processes in its template order, each
@@ -42,6 +43,8 @@ void static_ee_5a(ProcStatic& s);
   void register_##name##_fp32(std::vector<KernelEntry>& t); \
   void static_##name(ProcStatic& s);                          \
   void register_##name##_mixed(std::vector<KernelEntry>& t);
+void register_gg_ttgg_store_fp16(std::vector<KernelEntry>& t);
+void register_gg_ttgg_store_bf16(std::vector<KernelEntry>& t);
 RW_DECLARE_QCD(gg_tt)
 RW_DECLARE_QCD(gg_ttg)
 RW_DECLARE_QCD(gg_ttgg)

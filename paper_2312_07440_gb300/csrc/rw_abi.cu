@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/rwgt.h"
+#include "colour_tc.cuh"
 #include "kernels.cuh"
 #include "registry.h"
 
@@ -37,6 +38,8 @@ struct Registry {
     rw::register_gg_tt_mixed(kernels);
     rw::register_gg_ttg_mixed(kernels);
     rw::register_gg_ttgg_mixed(kernels);
+    rw::register_gg_ttgg_store_fp16(kernels);
+    rw::register_gg_ttgg_store_bf16(kernels);
     rw::register_gg_tt_fp64(kernels);
     rw::register_gg_tt_fp32(kernels);
     rw::static_gg_tt(st[RW_GG_TT]);
@@ -106,9 +109,11 @@ struct rw_ctx {
   size_t ws_bytes = 0;
   int lane_bits = -1, block = 0;
   int smem_optin = 0;  // largest dynamic shared memory a block may opt in to (bytes)
+  int smem_per_sm = 0;  // shared memory of one SM (bytes)
   std::string err;
   double* h_stage = nullptr;  // pinned [RW_MAX_POINTS + 2]
   std::map<std::tuple<const void*, int, size_t>, int> occ;
+  bool deferred_last = false;  // the last launch ran the separate tensor-core colour pass
   // rw_reweight_host pipeline: copy stream and events, created on first use
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> events;
@@ -207,6 +212,20 @@ PointDev make_point(const rw_ctx* c, const rw_params& p, bool reshuffle) {
 size_t ws_pairs_offset(int P) { return 256 + align256(8 * (size_t)(P + 2)) + (size_t)GRID_CAP * (P + 1) * 16; }
 size_t ws_core_bytes(int P) { return ws_pairs_offset(P) + align256(16 * (size_t)(P + 1)); }
 
+// Mixed modes with a compiled separate colour pass (k_amp_store + k_colour_tc)
+// run it for up to DEFER_MAX_POINTS points when the attached workspace holds
+// its amplitude buffers, placed after a core region sized for that many points.
+bool defer_compiled(int process, int mode) {
+  for (const auto& k : registry().kernels)
+    if (k.process == process && k.mode == mode && k.kind == 2) return true;
+  return false;
+}
+rw::DeferLayout defer_layout(int process, int npts, long long E) {
+  const ProcStatic& st = registry().st[process];
+  return rw::DeferLayout(npts, rw::align_up(E, 128), st.n_colour_flows, st.n_helicities / 2);
+}
+size_t defer_offset() { return ws_core_bytes(rw::DEFER_MAX_POINTS); }
+
 int check_dev_ptr(rw_ctx* c, const void* p, const char* name) {
   if (!p) return fail(c, RW_ERR_NULL, "%s is NULL", name);
   if (reinterpret_cast<uintptr_t>(p) % 8) return fail(c, RW_ERR_ALIGN, "%s not 8-byte aligned", name);
@@ -236,7 +255,7 @@ int ready(rw_ctx* c, bool need_events) {
 // only ever raised: lowering it for a smaller launch would make the next
 // larger launch of the same kernel fail.
 cudaError_t ensure_smem(const void* func, size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
+  if (smem == 0) return cudaSuccess;
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
   cudaFuncAttributes fa;
@@ -296,7 +315,70 @@ int shape(rw_ctx* c, int P, Shape& sh) {
   return RW_OK;
 }
 
+// the amplitude pass, then the tensor-core colour pass (colour_tc.cuh)
+int launch_deferred(rw_ctx* c, RwArgs& a, const KernelEntry* d) {
+  const int block = c->block > 0 ? c->block : 128;
+  const int lanes = 1 << d->lane_bits;
+  if (block > d->max_block || lanes > block) return fail(c, RW_ERR_ARG, "block %d does not fit this variant", block);
+  const size_t smem = (size_t)d->smem_per_thread * block;
+  const size_t smem_total = smem + static_smem(d->func);
+  if (c->smem_optin > 0 && smem_total > (size_t)c->smem_optin)
+    return fail(c, RW_ERR_ARG, "block %d needs %zu bytes of shared memory (%d per thread), more than the %d a block may have",
+                block, smem_total, d->smem_per_thread, c->smem_optin);
+  for (const auto& [f, bytes] : {std::make_pair(d->func, smem), std::make_pair(d->func2, rw::CT_SMEM)})
+    if (cudaError_t e = ensure_smem(f, bytes); e != cudaSuccess)
+      return cuda_fail(c, e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
+  // the colour pass: as many blocks per SM as its shared memory allows (the
+  // default carveout may leave room for one)
+  if (cudaError_t e = cudaFuncSetAttribute(d->func2, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           (int)cudaSharedmemCarveoutMaxShared);
+      e != cudaSuccess)
+    return cuda_fail(c, e, "cudaFuncSetAttribute(PreferredSharedMemoryCarveout)");
+  auto occupancy = [c](const void* f, int threads, size_t bytes, int& per_sm) {
+    const auto key = std::make_tuple(f, threads, bytes);
+    const auto it = c->occ.find(key);
+    if (it != c->occ.end()) {
+      per_sm = it->second;
+      return cudaSuccess;
+    }
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, bytes);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+    c->occ[key] = per_sm;
+    return cudaSuccess;
+  };
+  int per_sm = 1;
+  cudaError_t e = occupancy(d->func, block, smem, per_sm);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  // colour-pass blocks per SM: by shared memory (1 KB of it reserved per
+  // block) and by tensor memory (128 of 512 columns each); the occupancy
+  // query does not see the carveout set above
+  const int per_sm_c = std::max(
+      1, std::min<int>(4, c->smem_per_sm / (int)(rw::CT_SMEM + static_smem(d->func2) + 1024)));
+  const long long need = (a.E * lanes + block - 1) / block;
+  const int grid = (int)std::max(1LL, std::min<long long>({(long long)GRID_CAP, (long long)per_sm * c->sm_count, need}));
+  const long long tiles = (a.E + 127) / 128;
+  const int grid_c =
+      (int)std::max(1LL, std::min<long long>({(long long)GRID_CAP, (long long)per_sm_c * c->sm_count, tiles}));
+  int* err = reinterpret_cast<int*>(reinterpret_cast<char*>(a.ticket) + 16);
+  if ((e = cudaMemsetAsync(err, 0, sizeof(int), c->stream)) != cudaSuccess) return cuda_fail(c, e, "memset");
+  void* args[] = {&a};
+  if ((e = cudaLaunchKernel(d->func, dim3(grid), dim3(block), args, smem, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "amplitude kernel launch");
+  void* args2[] = {&a, &err};
+  if ((e = cudaLaunchKernel(d->func2, dim3(grid_c), dim3(rw::CT_THREADS), args2, rw::CT_SMEM, c->stream)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "colour kernel launch");
+  c->deferred_last = true;
+  return RW_OK;
+}
+
 int launch(rw_ctx* c, RwArgs& a) {
+  c->deferred_last = false;
+  if (a.defer) {
+    const int lb = c->lane_bits >= 0 ? c->lane_bits : default_lane_bits(c->process, c->mode);
+    if (const KernelEntry* d = registry().find(c->process, c->mode, lb, 2)) return launch_deferred(c, a, d);
+  }
   Shape sh;
   int rc = shape(c, a.P, sh);
   if (rc) return rc;
@@ -313,6 +395,18 @@ int launch(rw_ctx* c, RwArgs& a) {
 
 void fill_ws(rw_ctx* c, RwArgs& a, int P);
 void fill_core(char* b, RwArgs& a, int P);
+
+// the separate colour pass's buffers for npts evaluations of the attached
+// events, when it applies (else the fused kernel runs)
+void set_defer(rw_ctx* c, RwArgs& a, int npts) {
+  a.defer = nullptr;
+  a.defer_ld = 0;
+  if (npts - 1 > rw::DEFER_MAX_POINTS || !defer_compiled(c->process, c->mode)) return;
+  const rw::DeferLayout L = defer_layout(c->process, npts, c->E);
+  if (c->ws_bytes < defer_offset() + (size_t)L.total) return;
+  a.defer = reinterpret_cast<unsigned char*>(c->ws + defer_offset());
+  a.defer_ld = L.ld;
+}
 
 // the fused reweight of all attached events and points
 void reweight_args(rw_ctx* c, RwArgs& a, double* d_wnew, double* d_ratio, double* d_me0, double* d_me_pts) {
@@ -333,6 +427,7 @@ void reweight_args(rw_ctx* c, RwArgs& a, double* d_wnew, double* d_ratio, double
     a.pt[1 + j] = make_point(c, c->pts[j], moved);
   }
   fill_ws(c, a, P);
+  set_defer(c, a, P + 1);
 }
 
 void fill_ws(rw_ctx* c, RwArgs& a, int P) { fill_core(c->ws, a, P); }
@@ -368,6 +463,7 @@ int rw_create(rw_ctx** out, int device, void* stream) {
   c->stream = static_cast<cudaStream_t>(stream);
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess ||
       cudaMallocHost(&c->h_stage, sizeof(double) * (RW_MAX_POINTS + 4)) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -456,7 +552,9 @@ int rw_set_tuning(rw_ctx* c, int lane_bits, int block) {
   if (lane_bits >= 0 && c->process >= 0) {
     const KernelEntry* k = registry().find(c->process, c->mode, lane_bits);
     if (!k) return fail(c, RW_ERR_MODE, "lane_bits %d not compiled for this process/mode", lane_bits);
-    if (block > k->max_block) return fail(c, RW_ERR_ARG, "block above this variant's %d", k->max_block);
+    const KernelEntry* d = registry().find(c->process, c->mode, lane_bits, 2);  // separate colour pass
+    const int max_block = d ? std::max(k->max_block, d->max_block) : k->max_block;
+    if (block > max_block) return fail(c, RW_ERR_ARG, "block above this variant's %d", max_block);
     if ((1 << lane_bits) > (block ? block : 128)) return fail(c, RW_ERR_ARG, "more lanes than threads");
   }
   c->lane_bits = lane_bits;
@@ -517,8 +615,14 @@ int rw_autotune(rw_ctx* c, int64_t max_events, const char* cache_path, double* m
   static const int blocks[] = {64, 128, 256};
   for (const auto& k : registry().kernels) {
     if (k.process != c->process || k.mode != c->mode || k.kind != 0) continue;
+    // with the separate colour pass attached, its amplitude kernel's limit
+    const KernelEntry* d = registry().find(c->process, c->mode, k.lane_bits, 2);
+    RwArgs probe{};
+    probe.P = (int)c->pts.size();
+    set_defer(c, probe, probe.P + 1);
+    const int max_block = (d && probe.defer) ? d->max_block : k.max_block;
     for (int bl : blocks) {
-      if ((1 << k.lane_bits) > bl || bl > k.max_block) continue;
+      if ((1 << k.lane_bits) > bl || bl > max_block) continue;
       c->lane_bits = k.lane_bits;
       c->block = bl;
       float t[3];
@@ -558,9 +662,12 @@ int rw_autotune(rw_ctx* c, int64_t max_events, const char* cache_path, double* m
   return RW_OK;
 }
 
-size_t rw_workspace_bytes(const rw_ctx* c, int64_t) {
+size_t rw_workspace_bytes(const rw_ctx* c, int64_t E) {
   if (!c) return 0;
-  return ws_core_bytes(std::max<int>(1, (int)c->pts.size()));
+  const int P = std::max<int>(1, (int)c->pts.size());
+  if (c->process >= 0 && E > 0 && P <= rw::DEFER_MAX_POINTS && defer_compiled(c->process, c->mode))
+    return defer_offset() + (size_t)defer_layout(c->process, P + 1, E).total;
+  return ws_core_bytes(P);
 }
 
 int rw_load_events(rw_ctx* c, const double* d_mom, const double* d_w, int64_t E, void* d_ws, size_t ws_bytes) {
@@ -608,6 +715,7 @@ int rw_eval_me(rw_ctx* c, int point, double* d_me) {
     a.pt[0] = make_point(c, c->pts[point], moved);
   }
   fill_ws(c, a, 0);
+  set_defer(c, a, 1);
   return launch(c, a);
 }
 
@@ -635,8 +743,17 @@ int rw_get_results(rw_ctx* c, double* h_sigma, double* h_sigma_orig, int64_t* h_
   const int P = (int)c->pts.size();
   cudaError_t e = cudaMemcpyAsync(c->h_stage, c->ws + 64, 8 * (size_t)(P + 2), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
+  if (c->deferred_last &&
+      (e = cudaMemcpyAsync(c->h_stage + P + 2, c->ws + 16, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) !=
+          cudaSuccess)
+    return cuda_fail(c, e, "cudaMemcpyAsync");
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+  if (c->deferred_last) {
+    int flag = 0;
+    memcpy(&flag, c->h_stage + P + 2, sizeof(int));
+    if (flag) return fail(c, RW_ERR_CUDA, "a tensor-core colour pass wait gave up (code %d): results invalid", flag);
+  }
   if (h_sigma) memcpy(h_sigma, c->h_stage, 8 * (size_t)P);
   if (h_sigma_orig) *h_sigma_orig = c->h_stage[P];
   unsigned long long nb;

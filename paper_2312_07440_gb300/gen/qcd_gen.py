@@ -263,11 +263,15 @@ def emit_process(name, n, outgoing_gluons, n_identical, hoist_weyl=True, share_f
     w("")
     w("// Sum over this lane's helicities of sum_{s,t} Cint_st Re(A_s^* A_t), g = 1;")
     w("// helicities with gluon 0 at +1 only, doubled (J^dagger C J(h) = J^dagger C J(-h)).")
-    w("// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float).")
-    w("template <class R, int LB, int CM = CM_FMA, bool JS = false>")
-    w("__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane) {")
+    w("// CM: colour sum by FMA (CM_FMA, any R) or on the tensor cores (CM_FP16/CM_BF16, R = float);")
+    w("// CM_STORE_FP16/CM_STORE_BF16: no colour sum here, each J vector goes to sink->put()")
+    w("// for a later tensor-core pass (the return value is then 0).")
+    w("template <class R, int LB, int CM = CM_FMA, bool JS = false, class Sink = NoSink>")
+    w("__device__ __forceinline__ R hel_sum(const QcdExt<R, NG>& X, const QcdKin<R, NG>& Kn, int lane,")
+    w("                                     [[maybe_unused]] Sink* sink = nullptr) {")
     w("  static_assert(CM == CM_FMA || sizeof(R) == 4, \"tensor-core colour sum takes FP32 amplitudes\");")
-    w("  const ColourMma<K, CM == CM_FMA ? CM_FP16 : CM> cmma(CM == CM_FMA ? nullptr : CI, JS ? NJS * 32 : 0);")
+    w("  constexpr bool MMA = CM == CM_FP16 || CM == CM_BF16;")
+    w("  const ColourMma<K, MMA ? CM : CM_FP16> cmma(MMA ? CI : nullptr, JS ? NJS * 32 : 0);")
     w("  JStore<R, NJS, JS> js;")
     w("  R acc = R(0);")
     # Colour sum by FMA.  Up to PAIRS_MAX_K orderings: sum over the pairs
@@ -503,7 +507,12 @@ def emit_process(name, n, outgoing_gluons, n_identical, hoist_weyl=True, share_f
     w(f"{ind}if constexpr (CM != CM_FMA) {{")
     for h in (0, 1):
         w(f"{ind}  const cx<float> Aa{h}[K] = {{{', '.join(f'A{k}_{h}' for k in range(K))}}};")
-    w(f"{ind}  acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip")
+    w(f"{ind}  if constexpr (MMA) {{")
+    w(f"{ind}    acc += R(2) * (cmma.sum(Aa0) + cmma.sum(Aa1));  // x2 helicity flip")
+    w(f"{ind}  }} else {{")
+    w(f"{ind}    sink->put(Aa0);")
+    w(f"{ind}    sink->put(Aa1);")
+    w(f"{ind}  }}")
     w(f"{ind}}} else {{")
     ind += "  "
     if pairs:

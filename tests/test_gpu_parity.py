@@ -411,6 +411,53 @@ def test_mixed_precision_colour_sum(mode, proc, wl, n, lbs, pts):
         assert rel(g["me0"], o["me0"]).mean() < b / 4
 
 
+@pytest.mark.parametrize("mode", ["mixed_fp16", "mixed_bf16"])
+def test_separate_colour_pass_gg_ttgg(mode):
+    """g g -> t tbar g g in a mixed mode with 4 or 8 lanes per event runs the
+    amplitudes as in FP32 mode, stores the J vectors in 16 bits and sums
+    colours in a separate tcgen05 pass: per event within the stated bound of
+    the oracle for 1, 2 and 3 points, over 12 tiles with a ragged last one and
+    grid-stride trips; unchanged parameters give r == 1 exactly; eval_me gives
+    the reweight's |M|^2 bit for bit; and it agrees with the in-kernel
+    tensor-core colour sum (2 lanes per event) within twice the bound."""
+    pts = np.stack([ev.param_vector(m_t=k * ev.M_TOP) for k in (0.9, 1.1, 1.2)])
+    mom, w, o = oracle_run("gg_ttgg", "gg_ttgg_1m", 1500, pts, start=3000)
+    b = mixed_bound(mode, 4)
+    fused = run_gpu("gg_ttgg", mode, mom, w, pts, lane_bits=1, block=128)
+    for lb, block in ((2, 128), (3, 256), (3, 64)):
+        g = run_gpu("gg_ttgg", mode, mom, w, pts, lane_bits=lb, block=block)
+        assert rel(g["me0"], o["me0"]).max() < b
+        assert rel(g["me"], o["me"]).max() < b
+        assert rel(g["ratio"], o["ratio"]).max() < 2 * b
+        assert rel(g["me0"], fused["me0"]).max() < 2 * b
+        assert rel(g["me0"], o["me0"]).mean() < b / 4
+        for j in range(3):
+            exact_gpu = math.fsum(g["wnew"][j])
+            assert abs(g["sigma"][j] - exact_gpu) <= 2 * np.spacing(exact_gpu)
+            assert abs(g["sigma"][j] / o["sigma"][j] - 1) < 2 * b
+        assert g["sigma_orig"] == pytest.approx(math.fsum(w), rel=1e-15)
+    for P in (1, 2):
+        g = run_gpu("gg_ttgg", mode, mom, w, pts[:P], lane_bits=3, block=128)
+        assert rel(g["me"], o["me"][:P]).max() < b
+    same = run_gpu("gg_ttgg", mode, mom, w, ev.param_vector()[None], lane_bits=3, block=128)
+    assert np.all(same["ratio"] == 1.0)
+    st = torch.cuda.current_stream(DEV).cuda_stream
+    with rwgt.Context(0, st) as c:
+        c.set_process("gg_ttgg", mode)
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(pts)
+        c.set_tuning(3, 128)
+        E = mom.shape[-1]
+        nb = c.workspace_bytes(E)
+        ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+        c.load_events(to_dev(mom), to_dev(w), E, ws, nb)
+        me = torch.empty(E, dtype=torch.float64, device=DEV)
+        c.eval_me(-1, me)
+        torch.cuda.synchronize()
+    g = run_gpu("gg_ttgg", mode, mom, w, pts, lane_bits=3, block=128)
+    assert np.array_equal(me.cpu().numpy(), g["me0"])
+
+
 @pytest.mark.parametrize("block", [32, 256])
 def test_mixed_modes_every_block_size(block):
     """Each warp's colour staging lives in the block's dynamic shared memory,
