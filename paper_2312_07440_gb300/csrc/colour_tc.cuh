@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(CT_THREADS) k_colour_tc(const __grid_constant_
     tcg::tc_fence_before();
     __syncthreads();
     tcg::tc_fence_after();
+    if (*abort) break;  // set before the barrier by a wait that gave up: every thread leaves
     if (it < total && t == 0) {
       const int b = (int)(it & 1);
       const uint32_t a0 = tcg::smem_u32(sA + b * CT_TILE_BYTES), b0 = tcg::smem_u32(sB);
@@ -266,22 +267,27 @@ __global__ void __launch_bounds__(CT_THREADS) k_colour_tc(const __grid_constant_
     }
     if (it >= 1) {
       const int b = (int)((it - 1) & 1);
-      const bool ok = tcg::mbar_wait(bar0 + 8 * b, par[b], err, 1, abort);
-      if (__syncthreads_or(!ok)) break;
-      par[b] ^= 1u;
-      ++seen[b];
+      // on a timeout the loop ends at the next barrier (this item's sums are void)
+      if (tcg::mbar_wait(bar0 + 8 * b, par[b], err, 1, abort)) {
+        par[b] ^= 1u;
+        ++seen[b];
+      }
       tcg::tc_fence_after();
       // the accumulator row (C Re J16 in columns 0..31, C Im J16 in 32..63)
       // and this thread's staged row of the previous item
       const uint32_t taddr = tmem + 64u * b + ((uint32_t)(warp * 32) << 16);
       const unsigned char* row = sA + b * CT_TILE_BYTES + t * 128;
       const int sw = t & 7;
+      uint32_t dr[4][16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tcg::tmem_ld16_nw(taddr + 16 * q, dr[q]);
+      tcg::tmem_wait_ld();
       float dot = 0.0f;
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         float d[32];
-        tcg::tmem_ld16(taddr + 32 * half, *reinterpret_cast<float(*)[16]>(d));
-        tcg::tmem_ld16(taddr + 32 * half + 16, *reinterpret_cast<float(*)[16]>(d + 16));
+#pragma unroll
+        for (int i = 0; i < 32; ++i) d[i] = __uint_as_float(dr[2 * half + i / 16][i % 16]);
 #pragma unroll
         for (int c = 0; c < KC; ++c) {
           const uint4 v = *reinterpret_cast<const uint4*>(row + (((4 * half + c) ^ sw) << 4));

@@ -68,17 +68,6 @@ struct InferArgs {
   int L;                                // layers before the output layer (input + hidden)
 };
 
-// 16 consecutive FP32 columns of this warp's 32 lanes, without the wait
-__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
 // byte offset of the BF16 pair at column c (even) of row r in a tile's
 // activations: k-block c / 64, each row 128 bytes, its 16-byte chunks
 // permuted by the 128-byte swizzle (chunk ^ row % 8) that TMA and the MMA
