@@ -116,11 +116,14 @@ def source_sha(process, mode):
     tu = f"proc_{process}_{'mixed' if mode.startswith('mixed') else mode}.cu"
     if not os.path.exists(os.path.join(d, tu)):
         tu = f"proc_{process}.cu"
+    tus = {tu, "rw_abi.cu"}
+    if mode.startswith("mixed"):  # the separate colour pass's translation units
+        tus |= {fn for fn in os.listdir(d) if fn.startswith(f"proc_{process}_store_") and fn.endswith(".cu")}
     for fn in sorted(os.listdir(d)):
         gen = fn.startswith("gen_") and fn.endswith(".cuh")
         if fn in mlp_only:
             continue
-        if fn in (tu, "rw_abi.cu") or (fn.endswith((".cuh", ".h")) and (not gen or fn.endswith(f"_{process}.cuh"))):
+        if fn in tus or (fn.endswith((".cuh", ".h")) and (not gen or fn.endswith(f"_{process}.cuh"))):
             with open(os.path.join(d, fn), "rb") as f:
                 h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
@@ -320,9 +323,13 @@ def alu_roofline(info, E, P, t_step, mode, peaks, workload):
     achieved = E * flops_event / t_step / 1e12
     pipe = "fp64" if mode == "fp64" else "fp32"
     peak = peaks[pipe]
+    kernel = "k_reweight (fused: amplitudes, colour sum, helicity sum, ratio, W', sigma)"
+    if mode.startswith("mixed") and workload == "gg_ttgg_1m" and P <= 3:
+        kernel = ("k_amp_store (amplitudes, J vectors stored in 16 bits; the executed count and traffic are its own) "
+                  "+ k_colour_tc (tcgen05 colour pass, HBM-bound), per step")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": profiled_value(workload, mode, "dram_bytes_per_launch"),
-            "kernel": "k_reweight (fused: amplitudes, colour sum, helicity sum, ratio, W', sigma)",
+            "kernel": kernel,
             "flops_per_event": flops_event,
             "peak_source": f"measured {pipe.upper()} FMA streams on every SM (rw_alu_peak) on this GPU"}
     ex = profiled_value(workload, mode, "executed_flops_per_event")
@@ -567,6 +574,14 @@ def run_variant(torch, rwgt, dev, stream, wl, variant, mode, sample, args, flush
            "accuracy_vs_oracle": accuracy_sample(wl, pts, mom_h, w_h, wn, mode, n=n_acc, variant=variant)}
     if variant == "default" and wl.process in ("gg_ttg", "gg_ttgg"):
         out["r_is_exactly_one"] = bool(torch.all(wn == w.unsqueeze(0)).item())
+    if mode.startswith("mixed") and wl.process == "gg_ttgg" and P <= 3 and lb in (2, 3):
+        # the colour sum as its own tcgen05 pass over the stored J vectors:
+        # 32 helicity slots x (Re + Im rows of 24 16-bit values + exponent)
+        # per event and evaluation, read once (HBM-bound)
+        out["colour_sum"] = {"path": "k_amp_store + k_colour_tc (tcgen05, separate pass)",
+                             "colour_pass_bytes_per_step": E * (P + 1) * (32 * (2 * 48 + 2) + 1)}
+    elif mode.startswith("mixed"):
+        out["colour_sum"] = {"path": "in the amplitude kernel (mma.sync, warp staging)"}
     del wn, ws
     return out
 
