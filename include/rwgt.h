@@ -133,7 +133,11 @@ int rw_get_tuning(const rw_ctx* ctx, int* lane_bits, int* block);
    computes the same sums; the sigma reduction order follows the grid). */
 int rw_autotune(rw_ctx* ctx, int64_t max_events, const char* cache_path, double* ms);
 
-/* Device workspace needed for E events with the current points (bytes). */
+/* Device workspace needed for E events with the current points (bytes).  In
+   the mixed modes of g g -> t tbar g g with at most 3 points it includes the
+   separate colour pass's amplitude buffers, (P+1) x 32 x 98 + (P+1) bytes per
+   event (Sec. 3.1's colour sum done as its own tensor-core pass); with a
+   smaller workspace those modes sum colours inside the amplitude kernel. */
 size_t rw_workspace_bytes(const rw_ctx* ctx, int64_t n_events);
 /* Step 2: attach a device event batch (SoA momenta [N][4][E], weights [E])
    and a device workspace of at least rw_workspace_bytes(E), 16-byte aligned.
