@@ -114,6 +114,11 @@ struct rw_ctx {
   double* h_stage = nullptr;  // pinned [RW_MAX_POINTS + 2]
   std::map<std::tuple<const void*, int, size_t>, int> occ;
   bool deferred_last = false;  // the last launch ran the separate tensor-core colour pass
+  // the separate colour pass's buffers: the attached workspace past its core,
+  // when the caller attached it through rw_load_events (the host-buffer and
+  // event-file entry points lay out their own buffers there)
+  unsigned char* defer_ws = nullptr;
+  size_t defer_room = 0;
   // rw_reweight_host pipeline: copy stream and events, created on first use
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> events;
@@ -401,10 +406,10 @@ void fill_core(char* b, RwArgs& a, int P);
 void set_defer(rw_ctx* c, RwArgs& a, int npts) {
   a.defer = nullptr;
   a.defer_ld = 0;
-  if (npts - 1 > rw::DEFER_MAX_POINTS || !defer_compiled(c->process, c->mode)) return;
+  if (!c->defer_ws || npts - 1 > rw::DEFER_MAX_POINTS || !defer_compiled(c->process, c->mode)) return;
   const rw::DeferLayout L = defer_layout(c->process, npts, c->E);
-  if (c->ws_bytes < defer_offset() + (size_t)L.total) return;
-  a.defer = reinterpret_cast<unsigned char*>(c->ws + defer_offset());
+  if ((size_t)L.total > c->defer_room) return;
+  a.defer = c->defer_ws;
   a.defer_ld = L.ld;
 }
 
@@ -670,7 +675,17 @@ size_t rw_workspace_bytes(const rw_ctx* c, int64_t E) {
   return ws_core_bytes(P);
 }
 
+static int load_events(rw_ctx* c, const double* d_mom, const double* d_w, int64_t E, void* d_ws, size_t ws_bytes,
+                       bool own_layout);
+
 int rw_load_events(rw_ctx* c, const double* d_mom, const double* d_w, int64_t E, void* d_ws, size_t ws_bytes) {
+  return load_events(c, d_mom, d_w, E, d_ws, ws_bytes, false);
+}
+
+// own_layout: the caller (an entry point of this library) keeps its own
+// buffers after the workspace's core, so the colour pass gets none
+static int load_events(rw_ctx* c, const double* d_mom, const double* d_w, int64_t E, void* d_ws, size_t ws_bytes,
+                bool own_layout) {
   if (!c) return RW_ERR_NULL;
   if (c->process < 0) return fail(c, RW_ERR_STATE, "set the process first");
   if (E <= 0) return fail(c, RW_ERR_ARG, "n_events must be > 0, got %lld", (long long)E);
@@ -681,8 +696,8 @@ int rw_load_events(rw_ctx* c, const double* d_mom, const double* d_w, int64_t E,
   if ((rc = check_dev_ptr(c, d_w, "weights"))) return rc;
   if ((rc = check_dev_ptr(c, d_ws, "workspace"))) return rc;
   if (reinterpret_cast<uintptr_t>(d_ws) % 16) return fail(c, RW_ERR_ALIGN, "workspace not 16-byte aligned");
-  if (ws_bytes < rw_workspace_bytes(c, E))
-    return fail(c, RW_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, rw_workspace_bytes(c, E));
+  const size_t need = ws_core_bytes(std::max<int>(1, (int)c->pts.size()));  // the colour pass's buffers are optional
+  if (ws_bytes < need) return fail(c, RW_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", ws_bytes, need);
   cudaError_t e = cudaMemsetAsync(d_ws, 0, 256, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
   c->mom = d_mom;
@@ -691,6 +706,12 @@ int rw_load_events(rw_ctx* c, const double* d_mom, const double* d_w, int64_t E,
   c->ld = E;
   c->ws = static_cast<char*>(d_ws);
   c->ws_bytes = ws_bytes;
+  c->defer_ws = nullptr;
+  c->defer_room = 0;
+  if (!own_layout && ws_bytes > defer_offset()) {
+    c->defer_ws = reinterpret_cast<unsigned char*>(d_ws) + defer_offset();
+    c->defer_room = ws_bytes - defer_offset();
+  }
   return RW_OK;
 }
 
@@ -825,7 +846,7 @@ int rw_reweight_host(rw_ctx* c, const double* h_mom, const double* h_w, int64_t 
   double* d_mom = reinterpret_cast<double*>(base + core + align256(16 * (size_t)(P + 1)));
   double* d_w = reinterpret_cast<double*>(reinterpret_cast<char*>(d_mom) + align256(8 * 4 * (size_t)N * E));
   double* d_wnew = reinterpret_cast<double*>(reinterpret_cast<char*>(d_w) + align256(8 * (size_t)E));
-  int rc = rw_load_events(c, d_mom, d_w, E, d_ws, ws_bytes);
+  int rc = load_events(c, d_mom, d_w, E, d_ws, ws_bytes, true);
   if (rc) return rc;
   Shape sh;
   if ((rc = shape(c, P, sh))) return rc;
@@ -1931,7 +1952,7 @@ int rw_lhe_reweight(rw_ctx* c, rw_lhe* lhe, const char* out_path, const char* co
     d_w[s] = reinterpret_cast<double*>(q + L.mom);
     d_wnew[s] = reinterpret_cast<double*>(q + L.mom + L.w);
   }
-  int rc = rw_load_events(c, d_mom[0], d_w[0], chunk, d_ws, ws_bytes);
+  int rc = load_events(c, d_mom[0], d_w[0], chunk, d_ws, ws_bytes, true);
   if (rc) return rc;
   // three pinned host slots: chunk k+1 is parsed into one while chunk k's
   // copies use the second and chunk k-1's weights are written from the third

@@ -411,6 +411,36 @@ def test_mixed_precision_colour_sum(mode, proc, wl, n, lbs, pts):
         assert rel(g["me0"], o["me0"]).mean() < b / 4
 
 
+def test_host_entry_point_mixed_gg_ttgg_keeps_its_buffers():
+    """The host-buffer entry point lays out its own buffers after the
+    workspace's core, so a mixed mode of g g -> t tbar g g sums colours inside
+    the amplitude kernel there (no separate pass writing over them): W' within
+    the stated bound of the oracle over two chunks, sums within 2 ulp of the
+    exact sums of the returned W', and within twice the bound of the device
+    path, which takes the separate tensor-core pass."""
+    pts = np.stack([ev.param_vector(m_t=0.9 * ev.M_TOP), ev.param_vector(m_t=1.2 * ev.M_TOP)])
+    E = 3001
+    mom, w, o = oracle_run("gg_ttgg", "gg_ttgg_1m", E, pts, start=9000)
+    b = mixed_bound("mixed_bf16", 4)
+    with rwgt.Context(0, torch.cuda.current_stream().cuda_stream) as c:
+        c.set_process("gg_ttgg", "mixed_bf16")
+        c.set_params(ev.param_vector())
+        c.set_reweight_points(pts)
+        c.set_tuning(3, 128)
+        nb = c.workspace_bytes_host(E)
+        ws = torch.empty(nb, dtype=torch.uint8, device=DEV)
+        hm, hwt = torch.from_numpy(mom).pin_memory(), torch.from_numpy(w).pin_memory()
+        hw = torch.empty((2, E), dtype=torch.float64).pin_memory()
+        sig, so, nbad, rc = c.reweight_host(hm, hwt, E, hw, 2, ws, nb)
+    hw = hw.numpy()
+    assert rc == 0 and nbad == 0
+    assert rel(hw, o["wnew"]).max() < 2 * b
+    for j in range(2):
+        assert abs(sig[j] - math.fsum(hw[j])) <= 2 * np.spacing(sig[j])
+    g = run_gpu("gg_ttgg", "mixed_bf16", mom, w, pts, lane_bits=3, block=128)
+    assert rel(g["wnew"], hw).max() < 4 * b
+
+
 @pytest.mark.parametrize("mode", ["mixed_fp16", "mixed_bf16"])
 def test_separate_colour_pass_gg_ttgg(mode):
     """g g -> t tbar g g in a mixed mode with 4 or 8 lanes per event runs the
