@@ -140,8 +140,12 @@ int rw_autotune(rw_ctx* ctx, int64_t max_events, const char* cache_path, double*
    smaller workspace those modes sum colours inside the amplitude kernel. */
 size_t rw_workspace_bytes(const rw_ctx* ctx, int64_t n_events);
 /* Step 2: attach a device event batch (SoA momenta [N][4][E], weights [E])
-   and a device workspace of at least rw_workspace_bytes(E), 16-byte aligned.
-   Clears the workspace counters (asynchronously). */
+   and a device workspace, 16-byte aligned, of rw_workspace_bytes(E) bytes:
+   the reduction slots for the current points are required (RW_ERR_WORKSPACE
+   below them); the separate colour pass's buffers that the mixed modes of
+   g g -> t tbar g g use beyond them are optional (without them those modes
+   sum colours inside the amplitude kernel).  Clears the workspace counters
+   (asynchronously). */
 int rw_load_events(rw_ctx* ctx, const double* d_mom, const double* d_w, int64_t n_events, void* d_workspace,
                    size_t workspace_bytes);
 
