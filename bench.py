@@ -380,8 +380,9 @@ def accuracy_sample(wl, pts, mom_h, w_h, wnew, mode, n=2000, variant=""):
             "tolerance": {"fp64": 1e-12, "fp32": 1e-5}.get(mode, "stated (mixed-precision bound), not asserted")}
 
 
-# the comparison the metric names: every BASELINE configuration that fits one
-# GPU, in each of its precision modes (device-resident, same timing rules)
+# the comparison the metric names (plain FP64 against the mixed-precision and
+# surrogate forms): every workload of this benchmark that fits one GPU, in each
+# of its precision modes (device-resident, same timing rules)
 VARIANTS = [
     # (name, workload, point set, mode, oracle sample events)
     ("gg_ttgg_1m_fp32", "gg_ttgg_1m", "mt", "fp32", 2000),
